@@ -1,0 +1,202 @@
+"""CPU oracle of the voxel-block-hashing hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py` may import this
+package.  The product library never routes through it.  It wraps `vbh_oracle.cpp` (plain C++,
+FP64 values, std::unordered_map store) through ctypes and shares no code with the CUDA path.
+
+Parity status of each function (what pins it; see the tests named in brackets):
+  map_batch          pinned: brute-force set/dict model on random sequences [test_oracle_hash]
+  alloc_keys         pinned: exact FP64 ray/band traversal bounds on tiny frames [test_oracle_alloc]
+  vol_integrate      pinned: closed-form plane and sphere SDFs, running-average closed forms
+                     [test_oracle_tsdf]
+  vol_erase_radius   pinned: FP64 distance away from the boundary [test_oracle_erase]
+  mc_dense / mc_set  pinned: analytic sphere classification, complement symmetry, S^c, and
+                     incremental == full re-extraction [test_oracle_mc]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vbh_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+OP_FIND, OP_INSERT, OP_ERASE = 0, 1, 2
+ST_FOUND, ST_NOT_FOUND, ST_INSERTED, ST_EXISTS, ST_ERASED, ST_CAPACITY, ST_INVALID = 1, 2, 3, 4, 5, 6, 7
+NONE = 0xFFFFFFFF
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the flags its canonical binary32 arithmetic needs."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([
+            "g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", "-fexcess-precision=standard", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P, U32, I32, F = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_float
+        L.orc_map_create.restype = P
+        L.orc_map_destroy.argtypes = [P]
+        L.orc_map_size.argtypes = [P]
+        L.orc_map_size.restype = U32
+        L.orc_map_batch.argtypes = [P, U32, P, P, P, P, P]
+        L.orc_map_dump.argtypes = [P, P, P, U32]
+        L.orc_map_dump.restype = U32
+        L.orc_vol_create.argtypes = [P, I32, I32]
+        L.orc_vol_create.restype = P
+        L.orc_vol_destroy.argtypes = [P]
+        L.orc_vol_size.argtypes = [P]
+        L.orc_vol_size.restype = U32
+        L.orc_alloc_keys.argtypes = [P, P, P, P, U32]
+        L.orc_alloc_keys.restype = U32
+        L.orc_vol_integrate.argtypes = [P, P, P]
+        L.orc_vol_integrate.restype = U32
+        L.orc_vol_touched.argtypes = [P, P, U32]
+        L.orc_vol_touched.restype = U32
+        L.orc_vol_erase_radius.argtypes = [P, P, F, P, U32]
+        L.orc_vol_erase_radius.restype = U32
+        L.orc_vol_erase_keys.argtypes = [P, P, U32]
+        L.orc_vol_erase_keys.restype = U32
+        L.orc_vol_dump.argtypes = [P, P, P, P, U32]
+        L.orc_vol_dump.restype = U32
+        L.orc_vol_load.argtypes = [P, P, P, P, U32]
+        L.orc_vol_mc_set.argtypes = [P, I32, P, U32, P, U32, P]
+        L.orc_vol_mc_set.restype = U32
+        L.orc_vol_mc_dense.argtypes = [P, P, U32, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleMap:
+    """Sec. 5 map of unique int3 keys to uint32 values, with the phased batch reading."""
+
+    def __init__(self):
+        self._h = lib().orc_map_create()
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_map_destroy(self._h)
+            self._h = None
+
+    def __len__(self):
+        return lib().orc_map_size(self._h)
+
+    def batch(self, ops, keys3, vals=None):
+        ops = np.ascontiguousarray(ops, np.uint8)
+        keys3 = np.ascontiguousarray(keys3, np.int32).reshape(-1, 3)
+        n = ops.shape[0]
+        vals = None if vals is None else np.ascontiguousarray(vals, np.uint32)
+        res = np.zeros(n, np.uint32)
+        st = np.zeros(n, np.uint8)
+        lib().orc_map_batch(self._h, n, _p(ops), _p(keys3), _p(vals), _p(res), _p(st))
+        return res, st
+
+    def dump(self):
+        n = len(self)
+        k = np.zeros((n, 3), np.int32)
+        v = np.zeros(n, np.uint32)
+        lib().orc_map_dump(self._h, _p(k), _p(v), n)
+        return k, v
+
+
+class OracleVolume:
+    """Voxel-block volume with FP64 TSDF values (allocation, fusion, erase, MC indices)."""
+
+    def __init__(self, voxel_size, trunc, max_weight, depth_scale, zmax, width, height,
+                 fx, fy, cx, cy):
+        self.params = np.array([voxel_size, trunc, max_weight, depth_scale, zmax, fx, fy, cx, cy],
+                               np.float32)
+        self.width, self.height = int(width), int(height)
+        self._h = lib().orc_vol_create(_p(self.params), self.width, self.height)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_vol_destroy(self._h)
+            self._h = None
+
+    def __len__(self):
+        return lib().orc_vol_size(self._h)
+
+    def _frame(self, depth, T):
+        depth = np.ascontiguousarray(depth, np.uint16)
+        assert depth.shape == (self.height, self.width)
+        T = np.ascontiguousarray(T, np.float32).reshape(12)
+        return depth, T
+
+    def alloc_keys(self, depth, T):
+        depth, T = self._frame(depth, T)
+        n = lib().orc_alloc_keys(self._h, _p(depth), _p(T), None, 0)
+        out = np.zeros((n, 3), np.int32)
+        lib().orc_alloc_keys(self._h, _p(depth), _p(T), _p(out), n)
+        return out
+
+    def integrate(self, depth, T) -> int:
+        depth, T = self._frame(depth, T)
+        return lib().orc_vol_integrate(self._h, _p(depth), _p(T))
+
+    def touched(self):
+        n = lib().orc_vol_touched(self._h, None, 0)
+        out = np.zeros((n, 3), np.int32)
+        lib().orc_vol_touched(self._h, _p(out), n)
+        return out
+
+    def erase_radius(self, centre, R):
+        c = np.ascontiguousarray(centre, np.float32).reshape(3)
+        cap = len(self)
+        out = np.zeros((cap, 3), np.int32)
+        n = lib().orc_vol_erase_radius(self._h, _p(c), float(R), _p(out), cap)
+        return out[:n]
+
+    def erase_keys(self, keys3) -> int:
+        k = np.ascontiguousarray(keys3, np.int32).reshape(-1, 3)
+        return lib().orc_vol_erase_keys(self._h, _p(k), k.shape[0])
+
+    def dump(self):
+        n = len(self)
+        k = np.zeros((n, 3), np.int32)
+        F = np.zeros((n, 512), np.float64)
+        W = np.zeros((n, 512), np.float64)
+        lib().orc_vol_dump(self._h, _p(k), _p(F), _p(W), n)
+        return k, F, W
+
+    def load(self, keys3, F, W):
+        k = np.ascontiguousarray(keys3, np.int32).reshape(-1, 3)
+        F = np.ascontiguousarray(F, np.float64).reshape(-1, 512)
+        W = np.ascontiguousarray(W, np.float64).reshape(-1, 512)
+        lib().orc_vol_load(self._h, _p(k), _p(F), _p(W), k.shape[0])
+
+    def mc_set(self, mode: int):
+        """mode 0: touched blocks + seven negative neighbours (+ removals); 1: all blocks."""
+        cap = len(self) + 1
+        k = np.zeros((cap, 3), np.int32)
+        rcap = 1 << 20
+        rem = np.zeros((rcap, 3), np.int32)
+        nr = np.zeros(1, np.uint32)
+        n = lib().orc_vol_mc_set(self._h, mode, _p(k), cap, _p(rem), rcap, _p(nr))
+        return k[:n], rem[:int(nr[0])]
+
+    def mc_dense(self, keys3):
+        k = np.ascontiguousarray(keys3, np.int32).reshape(-1, 3)
+        n = k.shape[0]
+        idx = np.zeros((n, 512), np.uint8)
+        margin = np.zeros((n, 512), np.float32)
+        lib().orc_vol_mc_dense(self._h, _p(k), n, _p(idx), _p(margin))
+        return idx, margin

@@ -1,0 +1,452 @@
+// CPU ORACLE for the voxel-block-hashing hot path -- TEST INFRASTRUCTURE ONLY.
+//
+// Plain, slow and deliberately obvious: a std::unordered_map key store, FP64 projective TSDF
+// values, sequential allocation / integration / erase / Marching-Cubes classification.  Only the
+// tests, the smoke check and the benchmark's CPU-baseline leg load this library; the product
+// path never does.  It shares no code, header, table or constant with the CUDA library.
+//
+// What it follows (SLAMCast, Stotko et al.):
+//   * Sec. 5 "Retrieval / Insertion / Removal": a map of unique keys with guaranteed find,
+//     insert (no overwrite; succeeds once the key is present) and erase.
+//   * Sec. 4.1 (reconstruction client): voxel block hashing -- allocation of the blocks around
+//     each depth sample and projective TSDF fusion (inherited from Niessner et al. / InfiniTAM,
+//     the paper gives no formula; the standard running average is written out below).
+//   * Sec. 4.2 (server): the per-voxel 8-bit Marching Cubes index, with indices 0 and 255 (the
+//     set S^c of the S^c equation) written as 0, recomputed for each updated block and its seven
+//     neighbours in negative direction.
+//
+// Readings of what the paper leaves open (each stated where it is used):
+//   R-batch  A batch of hash operations runs all finds on the pre-batch state, then all inserts,
+//            then all erases.  Among duplicate inserts (erases) of one key, the first in batch
+//            order reports INSERTED (ERASED); the rest report EXISTS (NOT_FOUND).
+//   R-canon  Every discrete decision (which pixel a voxel projects to, band membership, which
+//            block a depth sample falls in, the erase distance test) is defined as a fixed
+//            sequence of IEEE-754 binary32 operations, each rounded to nearest even: + - * /,
+//            fmaf (one rounding), floorf and exact int->float conversion.  This file is built
+//            with -ffp-contract=off so that the compiler fuses nothing on its own.
+//   R-value  TSDF values and weights are carried in FP64.
+//   R1 voxel g sits at world position g*s (corner convention).
+//   R2 depth in metres d = fl32(raw * depth_scale); raw == 0 is invalid; pixels with
+//      d > zmax are ignored when zmax > 0.
+//   R3 allocation samples z_j = fmaf(j, s, fl32(d - mu)), j = 0..J, J = ceil(2 mu / s) taken in
+//      double from the float inputs with a 1e-6 guard; every sample's block is allocated.
+//   R4 the integration set of a frame is the set of blocks its allocation touched.
+//   R5 projective SDF sdf = d(pixel) - p_z, observation f = clamp(sdf / mu, -1, 1), skipped when
+//      the canonical sdf32 < -mu; running average with weight 1 per observation, capped at Wmax:
+//      F <- (w F + f) / (w + 1), W <- min(w + 1, Wmax) with w = W.
+//   R6 a block is erased when its centre (8k + 3.5) s is farther than R from a given point.
+//   R-mc corner i of the cube at voxel g is g + c_i with the classic numbering
+//      c = (000,100,110,010,001,101,111,011) (x fastest); bit i is set iff F(corner) < 0; a cube
+//      with any corner in a missing block or with W == 0 is invalid and gets index 0.
+
+#include <array>
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <set>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Keys: an int3 block coordinate.  The oracle keeps its own 64-bit packing only as a hash key
+// for std::unordered_map; it is never exposed.
+struct K3 {
+  int32_t x, y, z;
+  bool operator==(const K3& o) const { return x == o.x && y == o.y && z == o.z; }
+  bool operator<(const K3& o) const {
+    if (x != o.x) return x < o.x;
+    if (y != o.y) return y < o.y;
+    return z < o.z;
+  }
+};
+struct K3Hash {
+  size_t operator()(const K3& k) const {
+    uint64_t h = (uint64_t)(uint32_t)k.x * 0x9E3779B97F4A7C15ull;
+    h ^= (uint64_t)(uint32_t)k.y + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
+    h ^= (uint64_t)(uint32_t)k.z + 0x85157AF5ull + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+
+const int kOpFind = 0, kOpInsert = 1, kOpErase = 2;
+const uint8_t kStFound = 1, kStNotFound = 2, kStInserted = 3, kStExists = 4, kStErased = 5,
+              kStInvalid = 7;
+const uint32_t kNone = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------------------------
+// Sec. 5: a map of unique keys to 32-bit values.
+struct OracleMap {
+  std::unordered_map<K3, uint32_t, K3Hash> m;
+};
+
+// Block of 8^3 voxels, FP64 values (R-value).
+struct Block {
+  double F[512];
+  double W[512];
+};
+
+struct Volume {
+  float s, mu, wmax, ds, zmax, fx, fy, cx, cy;
+  int width, height;
+  std::unordered_map<K3, Block, K3Hash> blocks;
+  std::set<K3> touched;   // blocks allocated/updated by the last integrated frame (R4)
+  std::set<K3> removed;   // blocks erased since the last touched-set extraction
+};
+
+inline int floordiv8(int g) { return g >= 0 ? g / 8 : -((-g + 7) / 8); }
+inline int mod8(int g) { return g - 8 * floordiv8(g); }
+
+bool key_in_range(float fq) { return fq >= -1048576.0f && fq < 1048576.0f; }
+
+// R3: number of sample steps J along the band [d - mu, d + mu].
+int band_steps(float mu, float s) {
+  return (int)std::ceil(2.0 * (double)mu / (double)s - 1e-6);
+}
+
+// R-canon, allocation: collect the block of every band sample of every valid pixel.
+void allocate_blocks(const Volume& v, const uint16_t* depth, const float* T, std::set<K3>& out) {
+  const float inv_bs = 1.0f / (8.0f * v.s);
+  const int J = band_steps(v.mu, v.s);
+  for (int pv = 0; pv < v.height; ++pv) {
+    for (int pu = 0; pu < v.width; ++pu) {
+      uint16_t raw = depth[(size_t)pv * v.width + pu];
+      if (raw == 0) continue;
+      float d = (float)raw * v.ds;
+      if (v.zmax > 0.0f && d > v.zmax) continue;
+      float du = (float)pu - v.cx;
+      float au = du / v.fx;
+      float dv = (float)pv - v.cy;
+      float av = dv / v.fy;
+      float z0 = d - v.mu;
+      for (int j = 0; j <= J; ++j) {
+        float z = std::fma((float)j, v.s, z0);
+        if (!(z > 0.0f)) continue;
+        float px = au * z;
+        float py = av * z;
+        float X[3];
+        for (int i = 0; i < 3; ++i) {
+          float acc = std::fma(T[4 * i + 0], px, T[4 * i + 3]);
+          acc = std::fma(T[4 * i + 1], py, acc);
+          X[i] = std::fma(T[4 * i + 2], z, acc);
+        }
+        float q[3];
+        bool ok = true;
+        for (int i = 0; i < 3; ++i) {
+          q[i] = std::floor(X[i] * inv_bs);
+          ok = ok && key_in_range(q[i]);
+        }
+        if (!ok) continue;
+        out.insert(K3{(int)q[0], (int)q[1], (int)q[2]});
+      }
+    }
+  }
+}
+
+// R-canon + R5 + R-value: fuse one frame into one block.
+void integrate_block(const Volume& v, const K3& k, Block& b, const uint16_t* depth, const float* T) {
+  const float cxh = v.cx + 0.5f;
+  const float cyh = v.cy + 0.5f;
+  const float fw = (float)v.width, fh = (float)v.height;
+  for (int lz = 0; lz < 8; ++lz)
+    for (int ly = 0; ly < 8; ++ly)
+      for (int lx = 0; lx < 8; ++lx) {
+        const int g[3] = {8 * k.x + lx, 8 * k.y + ly, 8 * k.z + lz};
+        // decision path, binary32
+        float dX[3];
+        for (int i = 0; i < 3; ++i) dX[i] = std::fma((float)g[i], v.s, -T[4 * i + 3]);
+        float p[3];
+        for (int j = 0; j < 3; ++j) {   // p = R^T (X - t)
+          float acc = T[0 * 4 + j] * dX[0];
+          acc = std::fma(T[1 * 4 + j], dX[1], acc);
+          p[j] = std::fma(T[2 * 4 + j], dX[2], acc);
+        }
+        if (!(p[2] > 0.0f)) continue;
+        float r = 1.0f / p[2];
+        float uf = std::floor(std::fma(v.fx * p[0], r, cxh));
+        float vf = std::floor(std::fma(v.fy * p[1], r, cyh));
+        if (!(uf >= 0.0f && uf < fw && vf >= 0.0f && vf < fh)) continue;
+        uint16_t raw = depth[(size_t)(int)vf * v.width + (int)uf];
+        if (raw == 0) continue;
+        float d = (float)raw * v.ds;
+        if (v.zmax > 0.0f && d > v.zmax) continue;
+        float sdf32 = d - p[2];
+        if (sdf32 < -v.mu) continue;
+        // value path, binary64
+        double pz = 0.0;
+        for (int i = 0; i < 3; ++i)
+          pz += (double)T[4 * i + 2] * ((double)g[i] * (double)v.s - (double)T[4 * i + 3]);
+        double sdf = (double)d - pz;
+        double f = sdf / (double)v.mu;
+        f = std::min(1.0, std::max(-1.0, f));
+        const int idx = lx + 8 * ly + 64 * lz;
+        double w = b.W[idx];
+        b.F[idx] = (w * b.F[idx] + f) / (w + 1.0);
+        b.W[idx] = std::min(w + 1.0, (double)v.wmax);
+      }
+}
+
+// R6: canonical squared distance of the block centre from a point.
+bool erase_test(const Volume& v, const K3& k, const float* c, float R) {
+  const int kk[3] = {k.x, k.y, k.z};
+  float dc[3];
+  for (int i = 0; i < 3; ++i) {
+    float centre = ((float)(8 * kk[i]) + 3.5f) * v.s;
+    dc[i] = centre - c[i];
+  }
+  float d2 = dc[0] * dc[0];
+  d2 = std::fma(dc[1], dc[1], d2);
+  d2 = std::fma(dc[2], dc[2], d2);
+  return d2 > R * R;
+}
+
+// R-mc corner offsets, classic numbering.
+const int kCorner[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                           {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+
+// Sec. 4.2: the MC index of the cube at voxel g, with S^c (0 and 255) written as 0.
+// `margin` receives min |F| over the 8 corners (+inf for an invalid cube).
+uint8_t mc_index(const Volume& v, const int g[3], double* margin) {
+  int idx = 0;
+  double mn = INFINITY;
+  for (int i = 0; i < 8; ++i) {
+    int gc[3] = {g[0] + kCorner[i][0], g[1] + kCorner[i][1], g[2] + kCorner[i][2]};
+    K3 kc{floordiv8(gc[0]), floordiv8(gc[1]), floordiv8(gc[2])};
+    auto it = v.blocks.find(kc);
+    if (it == v.blocks.end()) { *margin = INFINITY; return 0; }
+    int li = mod8(gc[0]) + 8 * mod8(gc[1]) + 64 * mod8(gc[2]);
+    if (it->second.W[li] == 0.0) { *margin = INFINITY; return 0; }
+    double F = it->second.F[li];
+    mn = std::min(mn, std::fabs(F));
+    if (F < 0.0) idx |= 1 << i;
+  }
+  *margin = mn;
+  if (idx == 255) idx = 0;   // S^c
+  return (uint8_t)idx;
+}
+
+void fill_keys(const std::vector<K3>& ks, int32_t* out, uint32_t cap) {
+  for (size_t i = 0; i < ks.size() && i < cap; ++i) {
+    out[3 * i + 0] = ks[i].x;
+    out[3 * i + 1] = ks[i].y;
+    out[3 * i + 2] = ks[i].z;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// ----------------------------------------------------------------------------------- hash map
+void* orc_map_create() { return new OracleMap(); }
+void orc_map_destroy(void* h) { delete (OracleMap*)h; }
+uint32_t orc_map_size(void* h) { return (uint32_t)((OracleMap*)h)->m.size(); }
+
+// Sec. 5 + R-batch.  vals may be null (then inserted values are 0).  results[i] is the value
+// found / kept / erased, or 0xFFFFFFFF.  Keys outside [-2^20, 2^20) and unknown ops are
+// reported INVALID and change nothing.
+void orc_map_batch(void* h, uint32_t n, const uint8_t* ops, const int32_t* keys3,
+                   const uint32_t* vals, uint32_t* results, uint8_t* status) {
+  auto& m = ((OracleMap*)h)->m;
+  auto valid = [&](uint32_t i) {
+    for (int a = 0; a < 3; ++a)
+      if (keys3[3 * i + a] < -1048576 || keys3[3 * i + a] >= 1048576) return false;
+    return ops[i] <= 2;
+  };
+  for (uint32_t i = 0; i < n; ++i) {   // phase 1: finds against the pre-batch state
+    if (!valid(i)) { status[i] = kStInvalid; results[i] = kNone; continue; }
+    if (ops[i] != kOpFind) continue;
+    auto it = m.find(K3{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]});
+    if (it == m.end()) { status[i] = kStNotFound; results[i] = kNone; }
+    else { status[i] = kStFound; results[i] = it->second; }
+  }
+  for (uint32_t i = 0; i < n; ++i) {   // phase 2: inserts, batch order
+    if (!valid(i) || ops[i] != kOpInsert) continue;
+    K3 k{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]};
+    auto it = m.find(k);
+    if (it != m.end()) { status[i] = kStExists; continue; }
+    m[k] = vals ? vals[i] : 0u;
+    status[i] = kStInserted;
+  }
+  for (uint32_t i = 0; i < n; ++i) {   // inserts report the value the key ended up with
+    if (!valid(i) || ops[i] != kOpInsert) continue;
+    results[i] = m[K3{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]}];
+  }
+  for (uint32_t i = 0; i < n; ++i) {   // phase 3: erases, batch order
+    if (!valid(i) || ops[i] != kOpErase) continue;
+    K3 k{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]};
+    auto it = m.find(k);
+    if (it == m.end()) { status[i] = kStNotFound; results[i] = kNone; continue; }
+    results[i] = it->second;
+    status[i] = kStErased;
+    m.erase(it);
+  }
+}
+
+// Dump in ascending key order.
+uint32_t orc_map_dump(void* h, int32_t* keys3, uint32_t* vals, uint32_t cap) {
+  auto& m = ((OracleMap*)h)->m;
+  std::vector<std::pair<K3, uint32_t>> all(m.begin(), m.end());
+  std::sort(all.begin(), all.end(), [](auto& a, auto& b) { return a.first < b.first; });
+  for (size_t i = 0; i < all.size() && i < cap; ++i) {
+    keys3[3 * i] = all[i].first.x;
+    keys3[3 * i + 1] = all[i].first.y;
+    keys3[3 * i + 2] = all[i].first.z;
+    vals[i] = all[i].second;
+  }
+  return (uint32_t)all.size();
+}
+
+// -------------------------------------------------------------------------------------- volume
+// params: s, mu, wmax, depth_scale, zmax, fx, fy, cx, cy
+void* orc_vol_create(const float* params, int width, int height) {
+  Volume* v = new Volume();
+  v->s = params[0]; v->mu = params[1]; v->wmax = params[2]; v->ds = params[3];
+  v->zmax = params[4]; v->fx = params[5]; v->fy = params[6]; v->cx = params[7];
+  v->cy = params[8]; v->width = width; v->height = height;
+  return v;
+}
+void orc_vol_destroy(void* h) { delete (Volume*)h; }
+uint32_t orc_vol_size(void* h) { return (uint32_t)((Volume*)h)->blocks.size(); }
+
+// Allocation only (R3): the set of blocks one frame touches, sorted; nothing is modified.
+uint32_t orc_alloc_keys(void* h, const uint16_t* depth, const float* T, int32_t* out, uint32_t cap) {
+  std::set<K3> s;
+  allocate_blocks(*(Volume*)h, depth, T, s);
+  std::vector<K3> ks(s.begin(), s.end());
+  fill_keys(ks, out, cap);
+  return (uint32_t)ks.size();
+}
+
+// One frame: allocation (R3, new blocks start at F = 0, W = 0) then fusion of the touched set
+// (R4, R5).  Returns the number of touched blocks.
+uint32_t orc_vol_integrate(void* h, const uint16_t* depth, const float* T) {
+  Volume& v = *(Volume*)h;
+  std::set<K3> s;
+  allocate_blocks(v, depth, T, s);
+  for (const K3& k : s) {
+    auto it = v.blocks.find(k);
+    if (it == v.blocks.end()) {
+      Block& b = v.blocks[k];
+      std::fill(b.F, b.F + 512, 0.0);
+      std::fill(b.W, b.W + 512, 0.0);
+    }
+  }
+  for (const K3& k : s) integrate_block(v, k, v.blocks[k], depth, T);
+  v.touched = s;
+  return (uint32_t)s.size();
+}
+
+uint32_t orc_vol_touched(void* h, int32_t* out, uint32_t cap) {
+  Volume& v = *(Volume*)h;
+  std::vector<K3> ks(v.touched.begin(), v.touched.end());
+  fill_keys(ks, out, cap);
+  return (uint32_t)ks.size();
+}
+
+// R6: erase every block whose centre is farther than R from `centre`; erased keys sorted.
+uint32_t orc_vol_erase_radius(void* h, const float* centre, float R, int32_t* out, uint32_t cap) {
+  Volume& v = *(Volume*)h;
+  std::vector<K3> gone;
+  for (auto& kv : v.blocks)
+    if (erase_test(v, kv.first, centre, R)) gone.push_back(kv.first);
+  std::sort(gone.begin(), gone.end());
+  for (const K3& k : gone) { v.blocks.erase(k); v.removed.insert(k); }
+  if (out) fill_keys(gone, out, cap);
+  return (uint32_t)gone.size();
+}
+
+// Erase an explicit key list (absent keys are ignored); returns the number erased.
+uint32_t orc_vol_erase_keys(void* h, const int32_t* keys3, uint32_t n) {
+  Volume& v = *(Volume*)h;
+  uint32_t c = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    K3 k{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]};
+    if (v.blocks.erase(k)) { v.removed.insert(k); ++c; }
+  }
+  return c;
+}
+
+// Dump in ascending key order; F and W are 512 doubles per block (x fastest).
+uint32_t orc_vol_dump(void* h, int32_t* keys3, double* F, double* W, uint32_t cap) {
+  Volume& v = *(Volume*)h;
+  std::vector<K3> ks;
+  for (auto& kv : v.blocks) ks.push_back(kv.first);
+  std::sort(ks.begin(), ks.end());
+  for (size_t i = 0; i < ks.size() && i < cap; ++i) {
+    keys3[3 * i] = ks[i].x; keys3[3 * i + 1] = ks[i].y; keys3[3 * i + 2] = ks[i].z;
+    const Block& b = v.blocks[ks[i]];
+    if (F) std::memcpy(F + 512 * i, b.F, sizeof b.F);
+    if (W) std::memcpy(W + 512 * i, b.W, sizeof b.W);
+  }
+  return (uint32_t)ks.size();
+}
+
+// Replace / add blocks (test upload).
+void orc_vol_load(void* h, const int32_t* keys3, const double* F, const double* W, uint32_t n) {
+  Volume& v = *(Volume*)h;
+  for (uint32_t i = 0; i < n; ++i) {
+    Block& b = v.blocks[K3{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]}];
+    std::memcpy(b.F, F + 512 * i, sizeof b.F);
+    std::memcpy(b.W, W + 512 * i, sizeof b.W);
+  }
+}
+
+// The MC block set of Sec. 4.2.  mode 0: every block the last frame touched together with its
+// seven neighbours in negative direction (k - o, o in {0,1}^3), live ones only; the erased
+// blocks since the last mode-0 call are returned separately as removals (only those not live
+// again).  mode 1: every live block.  Returns |M|; keys sorted; clears the removal list in
+// mode 0.
+uint32_t orc_vol_mc_set(void* h, int mode, int32_t* keys3, uint32_t cap, int32_t* removed3,
+                        uint32_t rcap, uint32_t* n_removed) {
+  Volume& v = *(Volume*)h;
+  std::set<K3> M;
+  std::vector<K3> rem;
+  if (mode == 0) {
+    for (const K3& k : v.touched)
+      for (int o = 0; o < 8; ++o) {
+        K3 n{k.x - (o & 1), k.y - ((o >> 1) & 1), k.z - ((o >> 2) & 1)};
+        if (v.blocks.count(n)) M.insert(n);
+      }
+    for (const K3& k : v.removed)
+      if (!v.blocks.count(k)) {
+        rem.push_back(k);
+        for (int o = 1; o < 8; ++o) {
+          K3 n{k.x - (o & 1), k.y - ((o >> 1) & 1), k.z - ((o >> 2) & 1)};
+          if (v.blocks.count(n)) M.insert(n);
+        }
+      }
+    v.removed.clear();
+  } else {
+    for (auto& kv : v.blocks) M.insert(kv.first);
+  }
+  std::vector<K3> ks(M.begin(), M.end());
+  fill_keys(ks, keys3, cap);
+  if (removed3) fill_keys(rem, removed3, rcap);
+  if (n_removed) *n_removed = (uint32_t)rem.size();
+  return (uint32_t)ks.size();
+}
+
+// Dense MC indices (512 per block, x fastest) and the per-cube margin min|F| for given blocks.
+void orc_vol_mc_dense(void* h, const int32_t* keys3, uint32_t n, uint8_t* idx, float* margin) {
+  Volume& v = *(Volume*)h;
+  for (uint32_t b = 0; b < n; ++b)
+    for (int lz = 0; lz < 8; ++lz)
+      for (int ly = 0; ly < 8; ++ly)
+        for (int lx = 0; lx < 8; ++lx) {
+          int g[3] = {8 * keys3[3 * b] + lx, 8 * keys3[3 * b + 1] + ly, 8 * keys3[3 * b + 2] + lz};
+          double m;
+          uint8_t c = mc_index(v, g, &m);
+          size_t o = (size_t)b * 512 + lx + 8 * ly + 64 * lz;
+          idx[o] = c;
+          if (margin) margin[o] = (float)m;
+        }
+}
+
+// The version of the oracle library (for the tests' build check).
+int orc_abi_version() { return 1; }
+
+}  // extern "C"
