@@ -1,0 +1,240 @@
+/* vbh.h -- C ABI of the B300 voxel-block-hashing library (libvbh.so).
+ *
+ * The library implements, on one GPU, the per-frame data-parallel path of the SLAMCast
+ * reconstruction server (Stotko et al., "SLAMCast: Large-Scale, Real-Time 3D Reconstruction and
+ * Streaming for Immersive Multi-Client Live Telepresence"):
+ *   - a GPU hash map of int3 voxel-block coordinates with guaranteed concurrent find / insert /
+ *     erase and unique keys (Sec. 5, "Retrieval", "Insertion", "Removal");
+ *   - block allocation from a depth frame and projective TSDF fusion into 8^3 voxel blocks
+ *     (voxel block hashing, Sec. 4.1);
+ *   - removal of blocks that leave the active region (Sec. 4.1, stream-out);
+ *   - per-voxel 8-bit Marching Cubes indices of the updated blocks and their seven neighbours in
+ *     negative direction, with indices 0 and 255 written as 0 (Sec. 4.2, the S^c equation),
+ *     compacted into per-block streams.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_dev are device pointers owned by the caller (for example a torch
+ *     tensor's data_ptr()); pointers named *_host are host pointers owned by the caller.  The
+ *     handle owns its hash table, block pool, free list and per-frame lists.
+ *   - All work is enqueued on the handle's CUDA stream and is asynchronous with respect to the
+ *     host, except where a host output pointer is given: then the call synchronises the stream
+ *     before it returns.  A handle is used from one host thread at a time.
+ *   - Errors are returned as vbh_status; nothing throws across the ABI.  Capacity exhaustion
+ *     inside a kernel (block pool or table full, output buffer too small) never drops work
+ *     silently: the affected operation gets a per-op status or the stream reports the count it
+ *     needed, and a sticky flag is raised that vbh_get_counters() reports.
+ *   - Block coordinates are int32 triples (x, y, z) laid out as keys3[3*i + {0,1,2}], each in
+ *     [-2^20, 2^20).  Voxel (lx, ly, lz) of a block has linear index lx + 8 ly + 64 lz.
+ *   - A pose T_wc is 12 float32 (row-major 3x4 [R | t]) mapping camera to world: X = R p + t.
+ *     Camera frame: x right, y down, z forward; pixel (u, v) is centred at (u, v).
+ */
+#ifndef VBH_H_
+#define VBH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VBH_ABI_VERSION 1
+
+typedef enum {
+  VBH_OK = 0,
+  VBH_ERR_INVALID_ARG = 1,      /* a pointer, size or configuration value is unusable */
+  VBH_ERR_CAPACITY = 2,         /* block pool or hash table exhausted (per-op status set) */
+  VBH_ERR_CUDA = 3,             /* a CUDA runtime call failed; see vbh_last_error() */
+  VBH_ERR_TIMEOUT = 4,          /* a bounded device-side wait gave up */
+  VBH_ERR_BUFFER_TOO_SMALL = 5, /* an output stream is smaller than what was produced */
+  VBH_ERR_UNSUPPORTED = 6       /* the call does not apply to this kind of handle */
+} vbh_status;
+
+/* Hash operations (Sec. 5) and their per-op results. */
+enum { VBH_OP_FIND = 0, VBH_OP_INSERT = 1, VBH_OP_ERASE = 2 };
+enum {
+  VBH_ST_FOUND = 1,      /* find: key present, result = its value */
+  VBH_ST_NOT_FOUND = 2,  /* find / erase: key absent, result = 0xFFFFFFFF */
+  VBH_ST_INSERTED = 3,   /* insert: this op added the key, result = its value */
+  VBH_ST_EXISTS = 4,     /* insert: key already present (or added by a duplicate op of the
+                            same batch), result = the value the key holds */
+  VBH_ST_ERASED = 5,     /* erase: this op removed the key, result = the value it held */
+  VBH_ST_CAPACITY = 6,   /* insert: table or block pool full; the key was not added */
+  VBH_ST_INVALID = 7     /* unknown op code or key coordinate outside [-2^20, 2^20) */
+};
+#define VBH_NONE 0xFFFFFFFFu
+
+enum { VBH_HASH_PRIMES = 0, /* b = (x p1 ^ y p2 ^ z p3) mod n, Sec. 5 "Retrieval" equation */
+       VBH_HASH_MIX = 1     /* 64-bit avalanche mix of the packed key (default) */ };
+
+typedef struct {
+  float voxel_size;        /* s, metres (> 0) */
+  float trunc;             /* truncation mu, metres (> 0) */
+  float max_weight;        /* fusion weight cap Wmax (>= 1) */
+  float depth_scale;       /* metres per raw uint16 depth unit (e.g. 0.001) */
+  float zmax;              /* pixels with depth > zmax are ignored; 0 = no limit */
+  int32_t width, height;   /* depth image size (pixels) */
+  float fx, fy, cx, cy;    /* pinhole intrinsics (pixels) */
+  uint32_t n_buckets;      /* hash buckets, a power of two >= 2 */
+  uint32_t slots_per_bucket; /* must be 4 */
+  uint32_t max_blocks;     /* voxel-block pool size; 0 = plain key -> uint32 map, no voxels */
+  uint32_t hash_fn;        /* VBH_HASH_PRIMES or VBH_HASH_MIX */
+  uint32_t max_batch;      /* largest n accepted by vbh_hash_batch (0 = 2^22) */
+} vbh_config;
+
+typedef struct vbh_handle vbh_handle;
+
+/* Counters, read synchronously from the device. */
+typedef struct {
+  uint32_t live;            /* keys in the table */
+  uint32_t tombstones;      /* erased slots not yet reused */
+  uint32_t empty;           /* never-used slots */
+  uint32_t free_blocks;     /* block pool entries available */
+  uint32_t last_touched;    /* blocks allocated/updated by the last vbh_integrate_frame */
+  uint32_t last_new;        /* of which newly allocated */
+  uint32_t last_candidates; /* distinct block keys per image tile summed over tiles */
+  uint32_t error_flags;     /* sticky: bit0 pool exhausted, bit1 table full, bit2 stream
+                               overflow, bit3 bounded wait timed out */
+  uint64_t kernel_launches; /* kernels this handle has launched since creation */
+  uint32_t rebuilds;        /* table rebuilds performed (tombstone clean-up) */
+  uint32_t last_mc_blocks;  /* records produced by the last extraction */
+  uint32_t last_mc_entries; /* entries produced by the last extraction */
+  uint32_t last_erased;     /* blocks removed by the last vbh_erase_blocks */
+  uint64_t voxels_updated;  /* voxels fused by the last vbh_integrate_frame */
+} vbh_counters;
+
+typedef struct {
+  uint32_t touched;         /* blocks of this frame (allocated or already live) */
+  uint32_t new_blocks;      /* of which new */
+  uint32_t candidates;      /* per-tile distinct keys before the global de-duplication */
+  uint32_t error_flags;     /* as in vbh_counters */
+} vbh_frame_stats;
+
+/* Lifecycle ---------------------------------------------------------------------------------
+ * vbh_create: validates `cfg`, allocates the table (n_buckets * 4 slots * 16 B, plus an equal
+ * rebuild buffer), the block pool (max_blocks * 4 KiB of (TSDF, weight) float pairs plus 160 B
+ * of metadata per block) and the per-frame lists on the current device, and binds
+ * `cuda_stream` (a cudaStream_t, or NULL for the legacy default stream).  *out receives the
+ * handle.  The call synchronises. */
+vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out);
+vbh_status vbh_destroy(vbh_handle* h);
+vbh_status vbh_set_stream(vbh_handle* h, void* cuda_stream);
+
+/* Hash batch (Sec. 5; phased reading: all finds see the pre-batch state, then all inserts run,
+ * then all erases).  ops_dev: n uint8 op codes; keys3_dev: n int3; vals_dev: n uint32 values to
+ * insert (plain maps only; may be NULL = 0); results_dev: n uint32; status_dev: n uint8.
+ * Among duplicate inserts of one key exactly one reports INSERTED and all return the same value;
+ * among duplicate erases exactly one reports ERASED.  On a voxel-block handle (max_blocks > 0)
+ * an insert takes a block from the pool (value = pool index; the new block reads as TSDF 0,
+ * weight 0) and an erase returns it.  n may be 0.  n > max_batch -> VBH_ERR_INVALID_ARG. */
+vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* keys3_dev,
+                          const uint32_t* vals_dev, uint32_t* results_dev, uint8_t* status_dev,
+                          uint32_t n);
+
+/* Rebuild the table from its live entries, turning every tombstone back into an empty slot
+ * (live keys keep their values).  Runs automatically before a batch or frame once tombstones
+ * outnumber half of the non-live slots; exposed for tests and maintenance. */
+vbh_status vbh_hash_rebuild(vbh_handle* h);
+
+/* Fusion of one frame (Sec. 4.1, voxel block hashing): every valid pixel samples its band
+ * [d - mu, d + mu] at spacing s; each sample's block is found or inserted (new blocks start at
+ * TSDF 0, weight 0); then every voxel of every touched block is projected into the frame and
+ * fused with the projective TSDF running average.  depth_dev: height*width uint16 (raw units,
+ * 0 = invalid), row-major; T_wc_host: 12 floats; frame_id: stored as the blocks' version by the
+ * next touched-set extraction.  stats_host may be NULL (asynchronous) or receive the frame's
+ * counts (synchronising).  Returns VBH_ERR_CAPACITY (only when stats_host is given) if the pool
+ * or table ran out; the blocks that could be allocated are fused. */
+vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const float* T_wc_host,
+                               uint32_t frame_id, vbh_frame_stats* stats_host);
+
+enum { VBH_ERASE_RADIUS = 0, VBH_ERASE_KEYS = 1 };
+typedef struct {
+  uint32_t mode;           /* VBH_ERASE_RADIUS or VBH_ERASE_KEYS */
+  float centre[3];         /* RADIUS: erase blocks whose centre (8k + 3.5) s is farther ... */
+  float radius;            /* ... than `radius` metres from `centre` */
+  const int32_t* keys3_dev;/* KEYS: n_keys block coordinates (absent keys are ignored) */
+  uint32_t n_keys;
+} vbh_erase_selector;
+
+/* Removal of blocks that leave the active region (Sec. 4.1: blocks no longer in view are
+ * streamed out and leave the GPU model).  Erased blocks go back to the pool and are remembered
+ * for the next touched-set extraction, which reports them as removed.  erased_keys3_dev
+ * (capacity: max_blocks keys) and n_erased_dev (one uint32) may be NULL. */
+vbh_status vbh_erase_blocks(vbh_handle* h, const vbh_erase_selector* sel_host,
+                            int32_t* erased_keys3_dev, uint32_t* n_erased_dev);
+
+enum { VBH_MC_TOUCHED = 0, /* blocks of the last fused frame + their seven negative neighbours,
+                              plus removal records for blocks erased since the last call */
+       VBH_MC_ALL = 1,     /* every live block */
+       VBH_MC_KEYS = 2,    /* the given blocks + their seven negative neighbours (live only) */
+       VBH_MC_SINCE = 3    /* every live block whose version is > since_version */ };
+#define VBH_REC_REMOVED 0x80000000u  /* info bit: the block was erased (count = 0) */
+
+typedef struct {
+  uint32_t mode;
+  const int32_t* keys3_dev; /* KEYS mode */
+  uint32_t n_keys;
+  uint32_t since_version;   /* SINCE mode */
+} vbh_mc_selector;
+
+/* Output stream of an extraction (all device buffers owned by the caller).
+ * Record r (r < *n_blocks_dev): keys3[3r..3r+2] = block, info[r] = version | VBH_REC_REMOVED,
+ * offsets[r], counts[r] = its entries' range in local/index.  Entry e: local[e] = voxel linear
+ * index (0..511), index[e] = its MC cube index (never 0 or 255).  Only nonzero indices are
+ * stored.  Records and entries are in no particular order.  *n_blocks_dev and *n_entries_dev
+ * receive the totals produced; when they exceed the capacities the excess is not written. */
+typedef struct {
+  int32_t* keys3;
+  uint32_t* info;
+  uint32_t* offsets;
+  uint32_t* counts;
+  uint16_t* local;
+  uint8_t* index;
+  uint32_t cap_blocks;
+  uint32_t cap_entries;
+  uint32_t* n_blocks_dev;
+  uint32_t* n_entries_dev;
+} vbh_mc_stream;
+
+/* Marching Cubes index extraction (Sec. 4.2).  Corner i of the cube at voxel g is g + c_i with
+ * c = (000, 100, 110, 010, 001, 101, 111, 011) (x fastest); bit i is set iff the TSDF at that
+ * corner is < 0; a cube with a corner in a missing block or with weight 0 gets index 0; indices
+ * 0 and 255 are written as 0 and not stored.  In TOUCHED mode the extracted blocks get the
+ * version of the last fused frame.  needed_bytes_host may be NULL (asynchronous); otherwise the
+ * call synchronises, stores the bytes the stream needed, and returns VBH_ERR_BUFFER_TOO_SMALL
+ * if a capacity was exceeded. */
+vbh_status vbh_extract_mc_indices(vbh_handle* h, const vbh_mc_selector* sel_host,
+                                  const vbh_mc_stream* out, uint64_t* needed_bytes_host);
+
+/* Host copies of the live blocks (test and checkpoint path; synchronises).  keys3_host: cap
+ * keys; tsdf_host, weight_host: cap*512 floats each (may be NULL); vals_host: cap uint32 (the
+ * value of each key: pool index or the plain map's value; may be NULL); *n_host = live keys
+ * (the first min(cap, live) are written, in no particular order). */
+vbh_status vbh_dump(vbh_handle* h, int32_t* keys3_host, float* tsdf_host, float* weight_host,
+                    uint32_t* vals_host, uint32_t cap, uint32_t* n_host);
+/* Insert (or overwrite) n blocks with the given voxel values (synchronises). */
+vbh_status vbh_load(vbh_handle* h, const int32_t* keys3_host, const float* tsdf_host,
+                    const float* weight_host, uint32_t n);
+
+vbh_status vbh_get_counters(vbh_handle* h, vbh_counters* out_host);
+vbh_status vbh_clear_errors(vbh_handle* h);
+
+/* Per-stage device timing (CUDA events recorded on the handle's stream around each stage).
+ * vbh_timing_read synchronises and returns the accumulated milliseconds and kernel launch
+ * counts per stage since the last reset. */
+enum { VBH_STAGE_ERASE = 0, VBH_STAGE_ALLOC = 1, VBH_STAGE_INTEGRATE = 2, VBH_STAGE_MCSET = 3,
+       VBH_STAGE_MC = 4, VBH_STAGE_HASH = 5, VBH_N_STAGES = 6 };
+vbh_status vbh_timing_enable(vbh_handle* h, int enable);
+vbh_status vbh_timing_read(vbh_handle* h, double* ms_host /* VBH_N_STAGES */,
+                           uint64_t* launches_host /* VBH_N_STAGES */, int reset);
+
+/* Host-side helpers (no device work). */
+int vbh_abi_version(void);
+const char* vbh_last_error(void);
+/* The bucket a key maps to under `hash_fn` for a table of n_buckets (power of two). */
+uint32_t vbh_bucket_of(int32_t x, int32_t y, int32_t z, uint32_t n_buckets, uint32_t hash_fn);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VBH_H_ */

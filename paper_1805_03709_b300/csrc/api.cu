@@ -1,0 +1,664 @@
+// C ABI of libvbh (declared in include/vbh.h): handle lifetime, device memory, the ordering of
+// the launches of each call, timing and counters.  No entry point calls into PyTorch; all
+// compute runs in the kernels of hash.cu, frame.cu, erase.cu and mc.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vbh.h"
+#include "vbh_internal.cuh"
+
+using namespace vbh;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+vbh_status fail(vbh_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define VBH_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(VBH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+struct StageEvents {
+  int stage;
+  cudaEvent_t a, b;
+  uint64_t launches;
+};
+
+}  // namespace
+
+struct vbh_handle {
+  vbh_config cfg{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;     // snapshot copies of the counters, off the critical path
+  int device = 0;
+  Launch L{};
+  unsigned int n_slots = 0;
+  Slot* slots = nullptr;
+  Slot* shadow = nullptr;
+  DevCounters* cnt = nullptr;
+  DevCounters* snap = nullptr;     // pinned host snapshot
+  cudaEvent_t snap_ev = nullptr;
+  bool snap_pending = false;
+  // pool
+  float2* vox = nullptr;
+  unsigned int* masks = nullptr;
+  unsigned long long* pkeys = nullptr;
+  unsigned int *state = nullptr, *mark = nullptr, *version = nullptr, *stack = nullptr;
+  // per-frame lists
+  int J = 0;
+  unsigned long long* cand = nullptr;
+  unsigned int cand_cap = 0;
+  unsigned int* cand_res = nullptr;
+  unsigned char* cand_st = nullptr;
+  unsigned int* touched = nullptr;
+  unsigned int* mset = nullptr;
+  unsigned long long* removed = nullptr;
+  unsigned long long* tombrec = nullptr;
+  unsigned int epoch = 0;
+  unsigned int frame_version = 0;
+  bool have_frame = false;
+  // bookkeeping
+  uint64_t launches = 0;
+  uint32_t rebuilds = 0;
+  bool timing = false;
+  std::vector<StageEvents> pending;
+  std::vector<cudaEvent_t> ev_free;
+  double ms[VBH_N_STAGES] = {0};
+  uint64_t stage_launches[VBH_N_STAGES] = {0};
+  int cur_stage = -1;
+  cudaEvent_t cur_a = nullptr;
+  uint64_t cur_launch0 = 0;
+
+  TableView table() const { return TableView{slots, cfg.n_buckets - 1u, cfg.hash_fn}; }
+  PoolView pool() const {
+    return PoolView{vox, masks, pkeys, state, mark, version, stack, cfg.max_blocks};
+  }
+  unsigned int next_epoch() {
+    ++epoch;
+    if (epoch == 0) epoch = 1;
+    return epoch;
+  }
+  cudaEvent_t get_event() {
+    if (!ev_free.empty()) {
+      cudaEvent_t e = ev_free.back();
+      ev_free.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void stage_begin(int s) {
+    cur_stage = s;
+    cur_launch0 = launches;
+    if (timing) {
+      cur_a = get_event();
+      cudaEventRecord(cur_a, stream);
+    }
+  }
+  void stage_end() {
+    if (timing && cur_stage >= 0) {
+      cudaEvent_t b = get_event();
+      cudaEventRecord(b, stream);
+      pending.push_back(StageEvents{cur_stage, cur_a, b, launches - cur_launch0});
+    } else if (cur_stage >= 0) {
+      stage_launches[cur_stage] += launches - cur_launch0;
+    }
+    cur_stage = -1;
+  }
+};
+
+namespace {
+
+vbh_status check_launch(vbh_handle* h, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(VBH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  (void)h;
+  return VBH_OK;
+}
+
+__global__ void k_init_pool(unsigned int* stack, unsigned int n) {
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    stack[i] = n - 1u - i;
+}
+
+// Non-blocking view of the counters: a copy enqueued on a side stream after each call, read by
+// the next call if it has landed.  Used only for the tombstone clean-up heuristic.
+void snapshot_counters(vbh_handle* h) {
+  if (h->snap_pending) return;
+  cudaEvent_t e = h->get_event();
+  cudaEventRecord(e, h->stream);
+  cudaStreamWaitEvent(h->side, e, 0);
+  cudaMemcpyAsync(h->snap, h->cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, h->side);
+  cudaEventRecord(h->snap_ev, h->side);
+  h->ev_free.push_back(e);
+  h->snap_pending = true;
+}
+
+vbh_status rebuild(vbh_handle* h) {
+  const size_t bytes = (size_t)h->n_slots * sizeof(Slot);
+  VBH_CUDA(cudaMemcpyAsync(h->shadow, h->slots, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  VBH_CUDA(cudaMemsetAsync(h->slots, 0xFF, bytes, h->stream));
+  launch_rebuild(h->L, h->table(), h->shadow, h->n_slots, h->cnt);
+  h->launches += 2;
+  h->rebuilds++;
+  return check_launch(h, "rebuild");
+}
+
+vbh_status maybe_rebuild(vbh_handle* h) {
+  if (h->snap_pending && cudaEventQuery(h->snap_ev) == cudaSuccess) {
+    h->snap_pending = false;
+    const unsigned int tomb = h->snap->n_tomb, empty = h->snap->n_empty;
+    if (tomb > h->n_slots / 64u && tomb > (tomb + empty) / 2u) return rebuild(h);
+  }
+  return VBH_OK;
+}
+
+FrameParams frame_params(const vbh_handle* h, const float* T) {
+  const vbh_config& c = h->cfg;
+  FrameParams fp{};
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) fp.R[3 * i + j] = T[4 * i + j];
+    fp.t[i] = T[4 * i + 3];
+  }
+  fp.s = c.voxel_size;
+  fp.mu = c.trunc;
+  fp.inv_mu = 1.0f / c.trunc;
+  fp.wmax = c.max_weight;
+  fp.ds = c.depth_scale;
+  fp.zmax = c.zmax;
+  fp.fx = c.fx;
+  fp.fy = c.fy;
+  fp.cx = c.cx;
+  fp.cy = c.cy;
+  // binary32 host arithmetic, one rounding per operation (these feed the canonical decisions)
+  fp.cxh = c.cx + 0.5f;
+  fp.cyh = c.cy + 0.5f;
+  const float bs = 8.0f * c.voxel_size;
+  fp.inv_bs = 1.0f / bs;
+  fp.fw = (float)c.width;
+  fp.fh = (float)c.height;
+  fp.width = c.width;
+  fp.height = c.height;
+  fp.J = h->J;
+  return fp;
+}
+
+void read_frame_stats(vbh_handle* h, const DevCounters& d, vbh_frame_stats* st) {
+  st->touched = d.n_touched;
+  st->new_blocks = d.n_new;
+  st->candidates = d.n_cand;
+  st->error_flags = d.err;
+  (void)h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vbh_abi_version(void) { return VBH_ABI_VERSION; }
+const char* vbh_last_error(void) { return g_last_error.c_str(); }
+
+uint32_t vbh_bucket_of(int32_t x, int32_t y, int32_t z, uint32_t n_buckets, uint32_t hash_fn) {
+  if (n_buckets == 0 || (n_buckets & (n_buckets - 1u)) || !key_ok(x, y, z)) return VBH_NONE;
+  return home_bucket(pack_key(x, y, z), n_buckets - 1u, hash_fn);
+}
+
+vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out) {
+  if (!cfg || !out) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const vbh_config& c = *cfg;
+  if (c.n_buckets < 2 || (c.n_buckets & (c.n_buckets - 1u)) || c.n_buckets > (1u << 28))
+    return fail(VBH_ERR_INVALID_ARG, "n_buckets must be a power of two in [2, 2^28]");
+  if (c.slots_per_bucket != 4) return fail(VBH_ERR_INVALID_ARG, "slots_per_bucket must be 4");
+  if (c.hash_fn > 1) return fail(VBH_ERR_INVALID_ARG, "unknown hash_fn");
+  if (c.max_blocks > (1u << 26)) return fail(VBH_ERR_INVALID_ARG, "max_blocks above 2^26");
+  if (c.max_blocks > 0) {
+    if (!(c.voxel_size > 0.f) || !(c.trunc > 0.f) || !(c.max_weight >= 1.f) ||
+        !(c.depth_scale > 0.f) || !(c.zmax >= 0.f) || c.width <= 0 || c.height <= 0 ||
+        c.width > 16384 || c.height > 16384 || !(c.fx > 0.f) || !(c.fy > 0.f) ||
+        !std::isfinite(c.cx) || !std::isfinite(c.cy))
+      return fail(VBH_ERR_INVALID_ARG, "invalid camera / volume parameters");
+  }
+  vbh_handle* h = new vbh_handle();
+  h->cfg = c;
+  if (h->cfg.max_batch == 0) h->cfg.max_batch = 1u << 22;
+  h->stream = (cudaStream_t)cuda_stream;
+  auto bail = [&](vbh_status st) {
+    vbh_destroy(h);
+    return st;
+  };
+#define CREATE_CUDA(call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      fail(VBH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+      return bail(VBH_ERR_CUDA);                                                       \
+    }                                                                                  \
+  } while (0)
+  CREATE_CUDA(cudaGetDevice(&h->device));
+  int sms = 0;
+  CREATE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  h->L = Launch{h->stream, sms};
+  CREATE_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  CREATE_CUDA(cudaEventCreateWithFlags(&h->snap_ev, cudaEventDisableTiming));
+  h->n_slots = c.n_buckets * 4u;
+  const size_t tbytes = (size_t)h->n_slots * sizeof(Slot);
+  CREATE_CUDA(cudaMalloc(&h->slots, tbytes));
+  CREATE_CUDA(cudaMalloc(&h->shadow, tbytes));
+  CREATE_CUDA(cudaMemsetAsync(h->slots, 0xFF, tbytes, h->stream));
+  CREATE_CUDA(cudaMalloc(&h->cnt, sizeof(DevCounters)));
+  CREATE_CUDA(cudaMallocHost(&h->snap, sizeof(DevCounters)));
+  DevCounters init{};
+  init.free_top = (int)c.max_blocks;
+  init.n_empty = h->n_slots;
+  CREATE_CUDA(cudaMemcpyAsync(h->cnt, &init, sizeof init, cudaMemcpyHostToDevice, h->stream));
+  const unsigned int nb = c.max_blocks;
+  if (nb > 0) {
+    CREATE_CUDA(cudaMalloc(&h->vox, (size_t)nb * 512 * sizeof(float2)));
+    CREATE_CUDA(cudaMalloc(&h->masks, (size_t)nb * 32 * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->pkeys, (size_t)nb * sizeof(unsigned long long)));
+    CREATE_CUDA(cudaMalloc(&h->state, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->mark, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->version, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->stack, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMemsetAsync(h->pkeys, 0xFF, (size_t)nb * sizeof(unsigned long long), h->stream));
+    CREATE_CUDA(cudaMemsetAsync(h->state, 0, (size_t)nb * sizeof(unsigned int), h->stream));
+    CREATE_CUDA(cudaMemsetAsync(h->mark, 0, (size_t)nb * sizeof(unsigned int), h->stream));
+    CREATE_CUDA(cudaMemsetAsync(h->version, 0, (size_t)nb * sizeof(unsigned int), h->stream));
+    CREATE_CUDA(cudaMemsetAsync(h->masks, 0, (size_t)nb * 32 * sizeof(unsigned int), h->stream));
+    k_init_pool<<<sms * 4, 256, 0, h->stream>>>(h->stack, nb);
+    CREATE_CUDA(cudaGetLastError());
+    h->J = (int)std::ceil(2.0 * (double)c.trunc / (double)c.voxel_size - 1e-6);
+    if (h->J < 0 || h->J > 4096) {
+      fail(VBH_ERR_INVALID_ARG, "truncation / voxel size ratio out of range");
+      return bail(VBH_ERR_INVALID_ARG);
+    }
+    h->cand_cap = (unsigned int)std::min<uint64_t>(
+        (uint64_t)c.width * c.height * (uint64_t)(h->J + 1), 0xFFFFFFF0ull);
+    CREATE_CUDA(cudaMalloc(&h->cand, (size_t)h->cand_cap * sizeof(unsigned long long)));
+    CREATE_CUDA(cudaMalloc(&h->cand_res, (size_t)h->cand_cap * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->cand_st, (size_t)h->cand_cap));
+    CREATE_CUDA(cudaMalloc(&h->touched, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->mset, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->removed, (size_t)nb * sizeof(unsigned long long)));
+    CREATE_CUDA(cudaMalloc(&h->tombrec, (size_t)nb * sizeof(unsigned long long)));
+  }
+  CREATE_CUDA(cudaStreamSynchronize(h->stream));
+#undef CREATE_CUDA
+  *out = h;
+  return VBH_OK;
+}
+
+vbh_status vbh_destroy(vbh_handle* h) {
+  if (!h) return VBH_OK;
+  if (h->stream || h->slots) cudaStreamSynchronize(h->stream);
+  if (h->side) cudaStreamSynchronize(h->side);
+  void* ptrs[] = {h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
+                  h->version, h->stack, h->cand, h->cand_res, h->cand_st, h->touched, h->mset,
+                  h->removed, h->tombrec};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->snap) cudaFreeHost(h->snap);
+  for (auto& s : h->pending) {
+    cudaEventDestroy(s.a);
+    cudaEventDestroy(s.b);
+  }
+  for (auto e : h->ev_free) cudaEventDestroy(e);
+  if (h->snap_ev) cudaEventDestroy(h->snap_ev);
+  if (h->side) cudaStreamDestroy(h->side);
+  delete h;
+  return VBH_OK;
+}
+
+vbh_status vbh_set_stream(vbh_handle* h, void* cuda_stream) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  VBH_CUDA(cudaStreamSynchronize(h->stream));
+  h->stream = (cudaStream_t)cuda_stream;
+  h->L.stream = h->stream;
+  return VBH_OK;
+}
+
+vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* keys3_dev,
+                          const uint32_t* vals_dev, uint32_t* results_dev, uint8_t* status_dev,
+                          uint32_t n) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  if (n == 0) return VBH_OK;
+  if (n > h->cfg.max_batch) return fail(VBH_ERR_INVALID_ARG, "batch larger than max_batch");
+  if (!ops_dev || !keys3_dev || !results_dev || !status_dev)
+    return fail(VBH_ERR_INVALID_ARG, "null device pointer");
+  vbh_status st = maybe_rebuild(h);
+  if (st != VBH_OK) return st;
+  const TableView t = h->table();
+  const PoolView pool = h->pool();
+  h->stage_begin(VBH_STAGE_HASH);
+  launch_hash_find(h->L, t, ops_dev, keys3_dev, results_dev, status_dev, n);
+  launch_hash_insert(h->L, t, pool, h->cnt, ops_dev, keys3_dev, nullptr, nullptr, vals_dev,
+                     results_dev, status_dev, n);
+  launch_hash_insert_finish(h->L, t, pool, h->cnt, nullptr, results_dev, status_dev, n, nullptr,
+                            nullptr, 0u);
+  launch_hash_erase(h->L, t, pool, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n);
+  h->launches += 4;
+  h->stage_end();
+  st = check_launch(h, "vbh_hash_batch");
+  snapshot_counters(h);
+  return st;
+}
+
+vbh_status vbh_hash_rebuild(vbh_handle* h) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  return rebuild(h);
+}
+
+vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const float* T_wc_host,
+                               uint32_t frame_id, vbh_frame_stats* stats_host) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
+  if (!depth_dev || !T_wc_host) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(T_wc_host[i])) return fail(VBH_ERR_INVALID_ARG, "non-finite pose");
+  if (frame_id >= 0x80000000u) return fail(VBH_ERR_INVALID_ARG, "frame_id must be < 2^31");
+  vbh_status st = maybe_rebuild(h);
+  if (st != VBH_OK) return st;
+  FrameParams fp = frame_params(h, T_wc_host);
+  fp.depth = depth_dev;
+  const TableView t = h->table();
+  const PoolView pool = h->pool();
+  const unsigned int epoch = h->next_epoch();
+  h->stage_begin(VBH_STAGE_ALLOC);
+  launch_frame_begin(h->L, h->cnt);
+  launch_alloc_keys(h->L, fp, h->cand, h->cand_cap, h->cnt);
+  launch_hash_insert(h->L, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
+                     h->cand_res, h->cand_st, h->cand_cap);
+  launch_hash_insert_finish(h->L, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
+                            h->cand_cap, h->touched, &h->cnt->n_touched, epoch);
+  h->launches += 4;
+  h->stage_end();
+  h->stage_begin(VBH_STAGE_INTEGRATE);
+  launch_integrate(h->L, fp, pool, h->touched, &h->cnt->n_touched, h->cnt);
+  h->launches += 1;
+  h->stage_end();
+  h->frame_version = frame_id;
+  h->have_frame = true;
+  st = check_launch(h, "vbh_integrate_frame");
+  if (st != VBH_OK) return st;
+  if (stats_host) {
+    DevCounters d;
+    VBH_CUDA(cudaMemcpyAsync(&d, h->cnt, sizeof d, cudaMemcpyDeviceToHost, h->stream));
+    VBH_CUDA(cudaStreamSynchronize(h->stream));
+    read_frame_stats(h, d, stats_host);
+    if (d.err & (kErrPool | kErrTable)) return fail(VBH_ERR_CAPACITY, "block pool or table full");
+  }
+  snapshot_counters(h);
+  return VBH_OK;
+}
+
+vbh_status vbh_erase_blocks(vbh_handle* h, const vbh_erase_selector* sel,
+                            int32_t* erased_keys3_dev, uint32_t* n_erased_dev) {
+  if (!h || !sel) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
+  const TableView t = h->table();
+  const PoolView pool = h->pool();
+  h->stage_begin(VBH_STAGE_ERASE);
+  if (sel->mode == VBH_ERASE_RADIUS) {
+    if (!(sel->radius >= 0.f) || !std::isfinite(sel->centre[0]) || !std::isfinite(sel->centre[1]) ||
+        !std::isfinite(sel->centre[2]))
+      return fail(VBH_ERR_INVALID_ARG, "invalid erase radius / centre");
+    launch_erase_radius(h->L, t, pool, h->cnt, sel->centre[0], sel->centre[1], sel->centre[2],
+                        sel->radius, h->cfg.voxel_size, h->removed, h->cfg.max_blocks,
+                        erased_keys3_dev, n_erased_dev);
+    h->launches += 2;
+  } else if (sel->mode == VBH_ERASE_KEYS) {
+    if (sel->n_keys && !sel->keys3_dev) return fail(VBH_ERR_INVALID_ARG, "null key list");
+    launch_erase_keys(h->L, t, pool, h->cnt, sel->keys3_dev, sel->n_keys, h->removed,
+                      h->cfg.max_blocks, erased_keys3_dev, n_erased_dev);
+    h->launches += sel->n_keys ? 2 : 1;
+  } else {
+    return fail(VBH_ERR_INVALID_ARG, "unknown erase mode");
+  }
+  h->stage_end();
+  vbh_status st = check_launch(h, "vbh_erase_blocks");
+  snapshot_counters(h);
+  return st;
+}
+
+vbh_status vbh_extract_mc_indices(vbh_handle* h, const vbh_mc_selector* sel,
+                                  const vbh_mc_stream* out, uint64_t* needed_bytes_host) {
+  if (!h || !sel || !out) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
+  if (!out->n_blocks_dev || !out->n_entries_dev ||
+      (out->cap_blocks && (!out->keys3 || !out->info || !out->offsets || !out->counts)) ||
+      (out->cap_entries && (!out->local || !out->index)))
+    return fail(VBH_ERR_INVALID_ARG, "incomplete output stream");
+  const TableView t = h->table();
+  const PoolView pool = h->pool();
+  const unsigned int epoch = h->next_epoch();
+  h->stage_begin(VBH_STAGE_MCSET);
+  VBH_CUDA(cudaMemsetAsync(out->n_entries_dev, 0, sizeof(uint32_t), h->stream));
+  switch (sel->mode) {
+    case VBH_MC_TOUCHED:
+      launch_mset_touched(h->L, t, pool, h->cnt, h->have_frame ? h->touched : nullptr,
+                          h->have_frame ? &h->cnt->n_touched : nullptr, h->removed,
+                          &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec, epoch,
+                          h->frame_version);
+      h->launches += 2;
+      break;
+    case VBH_MC_ALL:
+    case VBH_MC_SINCE:
+      launch_mset_scan(h->L, pool, h->cnt, h->mset, sel->mode == VBH_MC_SINCE, sel->since_version);
+      h->launches += 2;
+      break;
+    case VBH_MC_KEYS:
+      if (sel->n_keys && !sel->keys3_dev) return fail(VBH_ERR_INVALID_ARG, "null key list");
+      launch_mset_keys(h->L, t, pool, h->cnt, sel->keys3_dev, sel->n_keys, h->mset, epoch);
+      h->launches += sel->n_keys ? 2 : 1;
+      break;
+    default:
+      return fail(VBH_ERR_INVALID_ARG, "unknown extraction mode");
+  }
+  h->stage_end();
+  h->stage_begin(VBH_STAGE_MC);
+  launch_mc_extract(h->L, t, pool, h->cnt, h->mset, h->tombrec, out->keys3, out->info,
+                    out->offsets, out->counts, out->local, out->index, out->cap_blocks,
+                    out->cap_entries, out->n_blocks_dev, out->n_entries_dev, h->frame_version);
+  h->launches += 1;
+  if (sel->mode == VBH_MC_TOUCHED)
+    VBH_CUDA(cudaMemsetAsync(&h->cnt->n_removed, 0, sizeof(unsigned int), h->stream));
+  VBH_CUDA(cudaMemcpyAsync(&h->cnt->mc_entries, out->n_entries_dev, sizeof(unsigned int),
+                           cudaMemcpyDeviceToDevice, h->stream));
+  h->stage_end();
+  vbh_status st = check_launch(h, "vbh_extract_mc_indices");
+  if (st != VBH_OK) return st;
+  if (needed_bytes_host) {
+    uint32_t nb = 0, ne = 0;
+    VBH_CUDA(cudaMemcpyAsync(&nb, out->n_blocks_dev, 4, cudaMemcpyDeviceToHost, h->stream));
+    VBH_CUDA(cudaMemcpyAsync(&ne, out->n_entries_dev, 4, cudaMemcpyDeviceToHost, h->stream));
+    VBH_CUDA(cudaStreamSynchronize(h->stream));
+    *needed_bytes_host = (uint64_t)nb * (3 * sizeof(int32_t) + 3 * sizeof(uint32_t)) +
+                         (uint64_t)ne * (sizeof(uint16_t) + sizeof(uint8_t));
+    if (nb > out->cap_blocks || ne > out->cap_entries)
+      return fail(VBH_ERR_BUFFER_TOO_SMALL, "MC stream capacity exceeded");
+  }
+  snapshot_counters(h);
+  return VBH_OK;
+}
+
+vbh_status vbh_dump(vbh_handle* h, int32_t* keys3_host, float* tsdf_host, float* weight_host,
+                    uint32_t* vals_host, uint32_t cap, uint32_t* n_host) {
+  if (!h || !n_host) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if ((tsdf_host || weight_host) && h->cfg.max_blocks == 0)
+    return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
+  if (cap && !keys3_host) return fail(VBH_ERR_INVALID_ARG, "null key buffer");
+  DevCounters d;
+  VBH_CUDA(cudaMemcpyAsync(&d, h->cnt, sizeof d, cudaMemcpyDeviceToHost, h->stream));
+  VBH_CUDA(cudaStreamSynchronize(h->stream));
+  const unsigned int live = d.n_live;
+  unsigned long long* dk = nullptr;
+  unsigned int* dv = nullptr;
+  unsigned int* dn = nullptr;
+  float *dt = nullptr, *dw = nullptr;
+  vbh_status st = VBH_OK;
+  const unsigned int room = live + 1;
+  std::vector<unsigned long long> hk;
+  std::vector<unsigned int> hv;
+  unsigned int n = 0;
+  do {
+    if (cudaMalloc(&dk, (size_t)room * 8) != cudaSuccess || cudaMalloc(&dv, (size_t)room * 4) != cudaSuccess ||
+        cudaMalloc(&dn, 4) != cudaSuccess) {
+      st = fail(VBH_ERR_CUDA, "vbh_dump: cudaMalloc failed");
+      break;
+    }
+    cudaMemsetAsync(dn, 0, 4, h->stream);
+    // the dump kernel appends every live slot; `room` bounds it (live is exact after a sync)
+    launch_dump_table(h->L, h->table(), h->n_slots, dk, dv, dn);
+    h->launches += 1;
+    cudaMemcpyAsync(&n, dn, 4, cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      st = fail(VBH_ERR_CUDA, "vbh_dump: kernel failed");
+      break;
+    }
+    if (n > room) n = room;
+    hk.resize(n);
+    hv.resize(n);
+    cudaMemcpy(hk.data(), dk, (size_t)n * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(hv.data(), dv, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    const unsigned int m = n < cap ? n : cap;
+    for (unsigned int i = 0; i < m; ++i) {
+      int3 k = unpack_key(hk[i]);
+      keys3_host[3 * i] = k.x;
+      keys3_host[3 * i + 1] = k.y;
+      keys3_host[3 * i + 2] = k.z;
+      if (vals_host) vals_host[i] = hv[i];
+    }
+    if ((tsdf_host || weight_host) && m) {
+      if (cudaMalloc(&dt, (size_t)m * 512 * 4) != cudaSuccess ||
+          cudaMalloc(&dw, (size_t)m * 512 * 4) != cudaSuccess) {
+        st = fail(VBH_ERR_CUDA, "vbh_dump: cudaMalloc failed");
+        break;
+      }
+      launch_gather_blocks(h->L, h->pool(), dv, m, dt, dw);
+      h->launches += 1;
+      if (tsdf_host) cudaMemcpyAsync(tsdf_host, dt, (size_t)m * 512 * 4, cudaMemcpyDeviceToHost, h->stream);
+      if (weight_host) cudaMemcpyAsync(weight_host, dw, (size_t)m * 512 * 4, cudaMemcpyDeviceToHost, h->stream);
+      if (cudaStreamSynchronize(h->stream) != cudaSuccess) st = fail(VBH_ERR_CUDA, "vbh_dump: gather failed");
+    }
+  } while (0);
+  for (void* p : {(void*)dk, (void*)dv, (void*)dn, (void*)dt, (void*)dw})
+    if (p) cudaFree(p);
+  *n_host = n;
+  return st;
+}
+
+vbh_status vbh_load(vbh_handle* h, const int32_t* keys3_host, const float* tsdf_host,
+                    const float* weight_host, uint32_t n) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
+  if (n == 0) return VBH_OK;
+  if (!keys3_host || !tsdf_host || !weight_host) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if (n > h->cfg.max_batch) return fail(VBH_ERR_INVALID_ARG, "more blocks than max_batch");
+  int* dk = nullptr;
+  unsigned char *dops = nullptr, *dst = nullptr;
+  unsigned int* dres = nullptr;
+  float *dt = nullptr, *dw = nullptr;
+  vbh_status st = VBH_OK;
+  std::vector<unsigned char> ops(n, (unsigned char)VBH_OP_INSERT), hst(n);
+  do {
+    if (cudaMalloc(&dk, (size_t)n * 12) != cudaSuccess || cudaMalloc(&dops, n) != cudaSuccess ||
+        cudaMalloc(&dst, n) != cudaSuccess || cudaMalloc(&dres, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&dt, (size_t)n * 2048) != cudaSuccess || cudaMalloc(&dw, (size_t)n * 2048) != cudaSuccess) {
+      st = fail(VBH_ERR_CUDA, "vbh_load: cudaMalloc failed");
+      break;
+    }
+    cudaMemcpyAsync(dk, keys3_host, (size_t)n * 12, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dops, ops.data(), n, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dt, tsdf_host, (size_t)n * 2048, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dw, weight_host, (size_t)n * 2048, cudaMemcpyHostToDevice, h->stream);
+    st = vbh_hash_batch(h, dops, dk, nullptr, dres, dst, n);
+    if (st != VBH_OK) break;
+    cudaMemcpyAsync(hst.data(), dst, n, cudaMemcpyDeviceToHost, h->stream);
+    launch_scatter_blocks(h->L, h->pool(), dres, n, dt, dw);
+    launch_block_masks(h->L, h->pool(), dres, n);
+    h->launches += 2;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      st = fail(VBH_ERR_CUDA, "vbh_load: kernels failed");
+      break;
+    }
+    for (unsigned int i = 0; i < n; ++i) {
+      if (hst[i] == VBH_ST_INVALID) { st = fail(VBH_ERR_INVALID_ARG, "vbh_load: key out of range"); break; }
+      if (hst[i] == VBH_ST_CAPACITY) { st = fail(VBH_ERR_CAPACITY, "vbh_load: pool or table full"); break; }
+    }
+  } while (0);
+  for (void* p : {(void*)dk, (void*)dops, (void*)dst, (void*)dres, (void*)dt, (void*)dw})
+    if (p) cudaFree(p);
+  return st;
+}
+
+vbh_status vbh_get_counters(vbh_handle* h, vbh_counters* out) {
+  if (!h || !out) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  DevCounters d;
+  VBH_CUDA(cudaMemcpyAsync(&d, h->cnt, sizeof d, cudaMemcpyDeviceToHost, h->stream));
+  VBH_CUDA(cudaStreamSynchronize(h->stream));
+  std::memset(out, 0, sizeof *out);
+  out->live = d.n_live;
+  out->tombstones = d.n_tomb;
+  out->empty = d.n_empty;
+  out->free_blocks = h->cfg.max_blocks ? (uint32_t)(d.free_top > 0 ? d.free_top : 0) : 0u;
+  out->last_touched = d.n_touched;
+  out->last_new = d.n_new;
+  out->last_candidates = d.n_cand;
+  out->error_flags = d.err;
+  out->kernel_launches = h->launches;
+  out->rebuilds = h->rebuilds;
+  out->last_mc_blocks = d.mc_blocks;
+  out->last_mc_entries = d.mc_entries;
+  out->last_erased = d.n_erased;
+  out->voxels_updated = d.vox_updated;
+  return VBH_OK;
+}
+
+vbh_status vbh_clear_errors(vbh_handle* h) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  VBH_CUDA(cudaMemsetAsync(&h->cnt->err, 0, sizeof(unsigned int), h->stream));
+  return VBH_OK;
+}
+
+vbh_status vbh_timing_enable(vbh_handle* h, int enable) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  h->timing = enable != 0;
+  return VBH_OK;
+}
+
+vbh_status vbh_timing_read(vbh_handle* h, double* ms_host, uint64_t* launches_host, int reset) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  VBH_CUDA(cudaStreamSynchronize(h->stream));
+  for (auto& s : h->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s.a, s.b);
+    h->ms[s.stage] += ms;
+    h->stage_launches[s.stage] += s.launches;
+    h->ev_free.push_back(s.a);
+    h->ev_free.push_back(s.b);
+  }
+  h->pending.clear();
+  for (int i = 0; i < VBH_N_STAGES; ++i) {
+    if (ms_host) ms_host[i] = h->ms[i];
+    if (launches_host) launches_host[i] = h->stage_launches[i];
+    if (reset) {
+      h->ms[i] = 0;
+      h->stage_launches[i] = 0;
+    }
+  }
+  return VBH_OK;
+}
+
+}  // extern "C"

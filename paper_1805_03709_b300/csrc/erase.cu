@@ -1,0 +1,156 @@
+// Removal of voxel blocks that leave the active region (Sec. 4.1: blocks that are no longer in
+// the sensor's view leave the GPU model).  An erase launch only turns keys into tombstones and
+// returns pool entries to the free stack; each pool entry is owned by exactly one key, so the
+// radius scan needs no de-duplication.
+//
+// Canonical binary32 distance test of block k against point c and radius R:
+//   centre_i = fl(fl((float)(8 k_i) + 3.5) * s); e_i = fl(centre_i - c_i)
+//   d2 = fma(e_2, e_2, fma(e_1, e_1, fl(e_0 * e_0)));   erased iff d2 > fl(R * R)
+#include "vbh_internal.cuh"
+
+namespace vbh {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Remove one block: tombstone its key, free its pool entry, record it.
+__device__ __forceinline__ void finish_removal(bool erased, unsigned int p, unsigned long long key,
+                                               PoolView& pool, DevCounters* cnt,
+                                               unsigned long long* removed,
+                                               unsigned int removed_cap, int* out_keys3,
+                                               unsigned int* s_erased, unsigned int* s_err) {
+  unsigned int k = warp_append(reinterpret_cast<unsigned int*>(&cnt->free_top), erased,
+                               0xFFFFFFFFu);
+  if (erased) {
+    pool.stack[k] = p;
+    pool.pkeys[p] = kEmpty;
+    pool.state[p] = 0u;
+  }
+  unsigned int r = warp_append(&cnt->n_removed, erased, 0xFFFFFFFFu);
+  if (erased) {
+    if (r < removed_cap) removed[r] = key;
+    else atomicOr(s_err, kErrStream);
+  }
+  unsigned int o = warp_append(&cnt->n_erased, erased, 0xFFFFFFFFu);
+  if (erased) {
+    atomicAdd(s_erased, 1u);
+    if (out_keys3) {
+      int3 kk = unpack_key(key);
+      out_keys3[3u * o] = kk.x;
+      out_keys3[3u * o + 1] = kk.y;
+      out_keys3[3u * o + 2] = kk.z;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView pool,
+                                                           DevCounters* cnt, float cx, float cy,
+                                                           float cz, float R2, float s,
+                                                           unsigned long long* removed,
+                                                           unsigned int removed_cap,
+                                                           int* out_keys3) {
+  __shared__ unsigned int s_erased, s_err;
+  if (threadIdx.x == 0) { s_erased = 0; s_err = 0; }
+  __syncthreads();
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const unsigned int rounds = (pool.max_blocks + stride - 1u) / stride;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    const unsigned int p = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long key = kEmpty;
+    if (p < pool.max_blocks) key = pool.pkeys[p];
+    bool erased = false;
+    if (key != kEmpty) {
+      const int3 k = unpack_key(key);
+      const float e0 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.x), 3.5f), s), cx);
+      const float e1 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.y), 3.5f), s), cy);
+      const float e2 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.z), 3.5f), s), cz);
+      const float d2 = __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0)));
+      if (d2 > R2) {
+        unsigned int val;
+        unsigned int pos = thread_find(t, key, &val);
+        if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;
+      }
+    }
+    finish_removal(erased, p, key, pool, cnt, removed, removed_cap, out_keys3, &s_erased, &s_err);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_erased) {
+      atomicSub(&cnt->n_live, s_erased);
+      atomicAdd(&cnt->n_tomb, s_erased);
+    }
+    if (s_err) atomicOr(&cnt->err, s_err);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_erase_keys(TableView t, PoolView pool,
+                                                         DevCounters* cnt, const int* keys3,
+                                                         unsigned int n,
+                                                         unsigned long long* removed,
+                                                         unsigned int removed_cap,
+                                                         int* out_keys3) {
+  __shared__ unsigned int s_erased, s_err;
+  if (threadIdx.x == 0) { s_erased = 0; s_err = 0; }
+  __syncthreads();
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const unsigned int rounds = (n + stride - 1u) / stride;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long key = kEmpty;
+    bool erased = false;
+    unsigned int val = kNone;
+    if (i < n) {
+      const int x = keys3[3u * i], y = keys3[3u * i + 1], z = keys3[3u * i + 2];
+      if (key_ok(x, y, z)) {
+        key = pack_key(x, y, z);
+        unsigned int pos = thread_find(t, key, &val);
+        if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;
+      }
+    }
+    finish_removal(erased, val, key, pool, cnt, removed, removed_cap, out_keys3, &s_erased, &s_err);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_erased) {
+      atomicSub(&cnt->n_live, s_erased);
+      atomicAdd(&cnt->n_tomb, s_erased);
+    }
+    if (s_err) atomicOr(&cnt->err, s_err);
+  }
+}
+
+__global__ void k_erase_begin(DevCounters* cnt) { cnt->n_erased = 0; }
+
+}  // namespace
+
+void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                         float cx, float cy, float cz, float radius, float s,
+                         unsigned long long* removed, unsigned int removed_cap,
+                         int* out_keys3, unsigned int* out_n) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_erase_radius, kThreads, L.sms);
+  k_erase_begin<<<1, 1, 0, L.stream>>>(cnt);
+  const float R2 = radius * radius;   // host binary32 product, rounded once
+  k_erase_radius<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, cx, cy, cz, R2, s, removed,
+                                                  removed_cap, out_keys3);
+  if (out_n)
+    cudaMemcpyAsync(out_n, &cnt->n_erased, sizeof(unsigned int), cudaMemcpyDeviceToDevice,
+                    L.stream);
+}
+
+void launch_erase_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                       const int* keys3, unsigned int n, unsigned long long* removed,
+                       unsigned int removed_cap, int* out_keys3, unsigned int* out_n) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_erase_keys, kThreads, L.sms);
+  k_erase_begin<<<1, 1, 0, L.stream>>>(cnt);
+  if (n)
+    k_erase_keys<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, keys3, n, removed, removed_cap,
+                                                  out_keys3);
+  if (out_n)
+    cudaMemcpyAsync(out_n, &cnt->n_erased, sizeof(unsigned int), cudaMemcpyDeviceToDevice,
+                    L.stream);
+}
+
+}  // namespace vbh

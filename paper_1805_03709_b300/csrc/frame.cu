@@ -1,0 +1,219 @@
+// Per-frame voxel block hashing kernels (Sec. 4.1): band allocation and projective TSDF fusion.
+//
+// Canonical binary32 decisions.  Which block a depth sample falls in, which pixel a voxel
+// projects to, and whether a voxel lies inside the truncation band are discontinuous functions
+// of the inputs.  They are defined as the following sequences of correctly rounded binary32
+// operations, written with rounding-explicit intrinsics so that nothing is contracted:
+//   depth     d   = fl(raw * ds);  raw == 0 or (zmax > 0 and d > zmax) -> invalid pixel
+//   sample j  z_j = fma(j, s, fl(d - mu)), j = 0..J, J = ceil(2 mu / s - 1e-6); z_j <= 0 skipped
+//   ray       a_u = fl(fl(u - cx) / fx), a_v likewise; P = (fl(a_u z), fl(a_v z), z)
+//   world     X_i = fma(R_i2, z, fma(R_i1, P_y, fma(R_i0, P_x, t_i)))
+//   block     k_i = floor(fl(X_i * inv_bs)), inv_bs = fl(1 / (8 s)); outside [-2^20, 2^20) skipped
+//   voxel     dX_i = fma(g_i, s, -t_i); p_j = fma(R_2j, dX_2, fma(R_1j, dX_1, fl(R_0j dX_0)))
+//   pixel     p_z > 0; r = fl(1 / p_z); u = floor(fma(fl(fx p_x), r, fl(cx + 0.5))), v likewise;
+//             valid iff 0 <= u < width and 0 <= v < height (compared as floats)
+//   band      fl(d - p_z) >= -mu
+// Values (the SDF fed into the running average) are computed more accurately than binary32:
+// the block's camera depth offset is formed in FP64 once per warp and split into two floats,
+// so the per-voxel SDF error stays near 1e-8 m.
+#include "vbh_internal.cuh"
+
+namespace vbh {
+
+namespace {
+
+constexpr int kTile = 16;            // 16 x 16 pixel tiles, one thread per pixel
+constexpr int kTileThreads = kTile * kTile;
+constexpr int kTileSet = 1024;       // shared-memory key set per tile (power of two)
+constexpr int kIntThreads = 128;     // fusion: 4 voxels per thread, one block per CTA step
+
+__global__ void k_frame_begin(DevCounters* cnt) {
+  cnt->n_cand = 0;
+  cnt->n_touched = 0;
+  cnt->n_new = 0;
+  cnt->vox_updated = 0ull;
+}
+
+// Band allocation: every valid pixel's samples -> block keys -> per-tile distinct set in shared
+// memory -> appended to the candidate list (the global de-duplication is the hash insert).
+__global__ void __launch_bounds__(kTileThreads) k_alloc_keys(FrameParams fp,
+                                                             unsigned long long* cand,
+                                                             unsigned int cap,
+                                                             DevCounters* cnt) {
+  __shared__ unsigned long long set[kTileSet];
+  for (int i = threadIdx.x; i < kTileSet; i += kTileThreads) set[i] = kEmpty;
+  __syncthreads();
+  const int tiles_x = (fp.width + kTile - 1) / kTile;
+  const int tiles_y = (fp.height + kTile - 1) / kTile;
+  const int n_tiles = tiles_x * tiles_y;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int pu = (tile % tiles_x) * kTile + (threadIdx.x % kTile);
+    const int pv = (tile / tiles_x) * kTile + (threadIdx.x / kTile);
+    if (pu < fp.width && pv < fp.height) {
+      const unsigned short raw = __ldg(fp.depth + (size_t)pv * fp.width + pu);
+      const float d = __fmul_rn((float)raw, fp.ds);
+      if (raw != 0 && !(fp.zmax > 0.0f && d > fp.zmax)) {
+        const float au = __fdiv_rn(__fsub_rn((float)pu, fp.cx), fp.fx);
+        const float av = __fdiv_rn(__fsub_rn((float)pv, fp.cy), fp.fy);
+        const float z0 = __fsub_rn(d, fp.mu);
+        unsigned long long prev = kEmpty;
+        for (int j = 0; j <= fp.J; ++j) {
+          const float z = __fmaf_rn((float)j, fp.s, z0);
+          if (!(z > 0.0f)) continue;
+          const float px = __fmul_rn(au, z);
+          const float py = __fmul_rn(av, z);
+          float q[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            float x = __fmaf_rn(fp.R[3 * i + 0], px, fp.t[i]);
+            x = __fmaf_rn(fp.R[3 * i + 1], py, x);
+            x = __fmaf_rn(fp.R[3 * i + 2], z, x);
+            q[i] = floorf(__fmul_rn(x, fp.inv_bs));
+          }
+          bool ok = true;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) ok = ok && q[i] >= -1048576.0f && q[i] < 1048576.0f;
+          if (!ok) continue;
+          const unsigned long long key = pack_key((int)q[0], (int)q[1], (int)q[2]);
+          if (key == prev) continue;   // consecutive samples usually share a block
+          prev = key;
+          unsigned int h = hash_mix(key) & (kTileSet - 1);
+          bool placed = false;
+          for (int probe = 0; probe < 64; ++probe) {
+            unsigned long long old = atomicCAS(&set[h], kEmpty, key);
+            if (old == kEmpty || old == key) { placed = true; break; }
+            h = (h + 1) & (kTileSet - 1);
+          }
+          if (!placed) {   // tile set saturated: hand the key straight to the global list
+            unsigned int k = atomicAdd(&cnt->n_cand, 1u);
+            if (k < cap) cand[k] = key;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileSet; i += kTileThreads) {
+      const unsigned long long key = set[i];
+      const bool has = key != kEmpty;
+      const unsigned int k = warp_append(&cnt->n_cand, has, 0xFFFFFFFFu);
+      if (has) {
+        if (k < cap) cand[k] = key;
+        set[i] = kEmpty;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Projective TSDF fusion of every voxel of every touched block; also rewrites the block's
+// sign / weight bit masks.  Thread t owns voxels t, t + 128, t + 256, t + 384, so every warp
+// load or store covers 256 contiguous bytes and each ballot yields one 32-voxel mask word.
+__global__ void __launch_bounds__(kIntThreads) k_integrate(FrameParams fp, PoolView pool,
+                                                           const unsigned int* touched,
+                                                           const unsigned int* n_touched,
+                                                           DevCounters* cnt) {
+  __shared__ unsigned int s_upd;
+  __shared__ unsigned int s_fresh;
+  if (threadIdx.x == 0) s_upd = 0;
+  __syncthreads();
+  const unsigned int n = *n_touched;
+  const int t = threadIdx.x;
+  const unsigned int lane = t & 31, warp = t >> 5;
+  const int lx = t & 7, ly = (t >> 3) & 7, lz0 = t >> 6;
+  const float flx = (float)lx, fly = (float)ly;
+  // per-voxel part of the camera depth, s * (R_02 lx + R_12 ly + R_22 lz) (value path only)
+  float tau[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    tau[j] = fp.s * fmaf(fp.R[8], (float)(lz0 + 2 * j), fmaf(fp.R[5], fly, fp.R[2] * flx));
+  unsigned int my_upd = 0;
+  for (unsigned int b = blockIdx.x; b < n; b += gridDim.x) {
+    const unsigned int p = touched[b];
+    const int3 k = unpack_key(pool.pkeys[p]);
+    if (t == 0) s_fresh = pool.state[p] & kFresh;
+    __syncthreads();
+    const bool fresh = s_fresh != 0;
+    float2* vox = pool.vox + 512ull * p;
+    float2 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = fresh ? make_float2(0.f, 0.f) : vox[t + 128 * j];
+    // camera depth of the block origin, FP64, split into hi + lo
+    float bhi = 0.f, blo = 0.f;
+    if (lane == 0) {
+      const double s = fp.s;
+      const double B = (double)fp.R[2] * ((double)(8 * k.x) * s - (double)fp.t[0]) +
+                       (double)fp.R[5] * ((double)(8 * k.y) * s - (double)fp.t[1]) +
+                       (double)fp.R[8] * ((double)(8 * k.z) * s - (double)fp.t[2]);
+      bhi = __double2float_rn(B);
+      blo = __double2float_rn(B - (double)bhi);
+    }
+    bhi = __shfl_sync(0xFFFFFFFFu, bhi, 0);
+    blo = __shfl_sync(0xFFFFFFFFu, blo, 0);
+    const float gx = (float)(8 * k.x + lx), gy = (float)(8 * k.y + ly);
+    const float dX = __fmaf_rn(gx, fp.s, -fp.t[0]);
+    const float dY = __fmaf_rn(gy, fp.s, -fp.t[1]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float gz = (float)(8 * k.z + lz0 + 2 * j);
+      const float dZ = __fmaf_rn(gz, fp.s, -fp.t[2]);
+      const float px = __fmaf_rn(fp.R[6], dZ, __fmaf_rn(fp.R[3], dY, __fmul_rn(fp.R[0], dX)));
+      const float py = __fmaf_rn(fp.R[7], dZ, __fmaf_rn(fp.R[4], dY, __fmul_rn(fp.R[1], dX)));
+      const float pz = __fmaf_rn(fp.R[8], dZ, __fmaf_rn(fp.R[5], dY, __fmul_rn(fp.R[2], dX)));
+      bool upd = false;
+      if (pz > 0.0f) {
+        const float r = __frcp_rn(pz);
+        const float uf = floorf(__fmaf_rn(__fmul_rn(fp.fx, px), r, fp.cxh));
+        const float vf = floorf(__fmaf_rn(__fmul_rn(fp.fy, py), r, fp.cyh));
+        if (uf >= 0.0f && uf < fp.fw && vf >= 0.0f && vf < fp.fh) {
+          const unsigned short raw = __ldg(fp.depth + (size_t)(int)vf * fp.width + (int)uf);
+          const float d = __fmul_rn((float)raw, fp.ds);
+          if (raw != 0 && !(fp.zmax > 0.0f && d > fp.zmax) && !(__fsub_rn(d, pz) < -fp.mu)) {
+            const float sdf = ((d - bhi) - blo) - tau[j];
+            const float f = fminf(1.0f, fmaxf(-1.0f, sdf * fp.inv_mu));
+            const float w = v[j].y;
+            v[j].x = v[j].x + __fdividef(f - v[j].x, w + 1.0f);
+            v[j].y = fminf(w + 1.0f, fp.wmax);
+            upd = true;
+          }
+        }
+      }
+      if (upd || fresh) vox[t + 128 * j] = v[j];
+      const unsigned int negm = __ballot_sync(0xFFFFFFFFu, v[j].x < 0.0f);
+      const unsigned int valm = __ballot_sync(0xFFFFFFFFu, v[j].y > 0.0f);
+      if (lane == 0) {
+        pool.masks[32u * p + warp + 4 * j] = negm;
+        pool.masks[32u * p + 16u + warp + 4 * j] = valm;
+      }
+      my_upd += upd;
+    }
+    __syncthreads();
+    if (t == 0 && fresh) pool.state[p] = 0u;
+  }
+  atomicAdd(&s_upd, my_upd);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_upd) atomicAdd(&cnt->vox_updated, (unsigned long long)s_upd);
+}
+
+}  // namespace
+
+void launch_frame_begin(const Launch& L, DevCounters* cnt) {
+  k_frame_begin<<<1, 1, 0, L.stream>>>(cnt);
+}
+
+void launch_alloc_keys(const Launch& L, const FrameParams& fp, unsigned long long* cand,
+                       unsigned int cap, DevCounters* cnt) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_alloc_keys, kTileThreads, L.sms);
+  const int tiles = ((fp.width + kTile - 1) / kTile) * ((fp.height + kTile - 1) / kTile);
+  k_alloc_keys<<<tiles < grid ? tiles : grid, kTileThreads, 0, L.stream>>>(fp, cand, cap, cnt);
+}
+
+void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
+                      const unsigned int* touched, const unsigned int* n_touched,
+                      DevCounters* cnt) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_integrate, kIntThreads, L.sms);
+  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(fp, pool, touched, n_touched, cnt);
+}
+
+}  // namespace vbh

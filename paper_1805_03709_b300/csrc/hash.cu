@@ -1,0 +1,480 @@
+// GPU hash map of packed int3 block keys: bucketed (4 x 16 B slots per 64 B bucket), linear
+// probing over buckets, probed by groups of 4 lanes with one 16 B load per lane.
+//
+// Guarantees (Sec. 5: concurrent retrieval, insertion and removal succeed and keys stay unique,
+// which the paper obtains with per-entry locks and an excess list; here with CAS claims):
+//   * A launch runs one phase only: finds (read-only), inserts (slots only go free -> key),
+//     or erases (slots only go key -> tombstone).  The host orders the phases of a batch.
+//   * A live key never moves (the paper's invariant that entry positions are preserved), so a
+//     find needs no lock: it walks the buckets from the key's home bucket until it meets the
+//     key or a bucket with a never-used (EMPTY) slot.  Tombstones keep chains intact.
+//   * Insert: pass 1 walks the chain to its end; if the key is absent it remembers the first
+//     free slot (tombstone or EMPTY).  Pass 2 claims free slots in probe order from there with
+//     a 64-bit CAS, re-reading a bucket after a lost CAS.  Because no slot becomes free during
+//     an insert launch, two inserters of one key always meet at the same first free slot, so
+//     exactly one CAS succeeds and the other sees the key (uniqueness).
+//   * The winner writes the value after the claim; duplicates record only the slot and read the
+//     value in a follow-up launch, so nobody reads a half-written entry.
+#include "vbh_internal.cuh"
+
+namespace vbh {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ bool load_key3(const int* keys3, unsigned int i,
+                                          unsigned long long* key) {
+  int x = keys3[3u * i], y = keys3[3u * i + 1], z = keys3[3u * i + 2];
+  if (!key_ok(x, y, z)) return false;
+  *key = pack_key(x, y, z);
+  return true;
+}
+
+// outcome codes of group_insert
+constexpr int kInserted = 1, kExists = 2, kFull = 3;
+
+__device__ int group_insert(const Group& g, const TableView& t, unsigned long long key,
+                            unsigned int* pos_out, unsigned long long* observed_out) {
+  unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
+  unsigned int first_free = kNone;
+  // pass 1: the whole chain, to be sure the key is absent
+  for (unsigned int probe = 0; probe <= t.bmask; ++probe) {
+    ulonglong2 s = load_slot_cg(&t.slots[4u * b + g.lane4]);
+    unsigned int hit = g.ballot(s.x == key);
+    if (hit) {
+      *pos_out = 4u * b + (__ffs(hit) - 1);
+      return kExists;
+    }
+    if (first_free == kNone) {
+      unsigned int fr = g.ballot(s.x >= kTomb);
+      if (fr) first_free = 4u * b + (__ffs(fr) - 1);
+    }
+    if (g.ballot(s.x == kEmpty)) break;
+    b = (b + 1u) & t.bmask;
+  }
+  if (first_free == kNone) return kFull;
+  // pass 2: claim in probe order starting at the first free slot
+  b = first_free >> 2;
+  for (unsigned int steps = 0; steps <= t.bmask;) {
+    ulonglong2 s = load_slot_cg(&t.slots[4u * b + g.lane4]);
+    unsigned int hit = g.ballot(s.x == key);
+    if (hit) {
+      *pos_out = 4u * b + (__ffs(hit) - 1);
+      return kExists;
+    }
+    unsigned int fr = g.ballot(s.x >= kTomb);
+    if (!fr) {
+      b = (b + 1u) & t.bmask;
+      ++steps;
+      continue;
+    }
+    unsigned int l = __ffs(fr) - 1;
+    unsigned long long old = 0ull;
+    if (g.lane4 == l) old = atomicCAS(&t.slots[4u * b + l].key, s.x, key);
+    old = g.bcast(old, l);
+    unsigned long long obs = g.bcast((unsigned long long)s.x, l);
+    if (old == obs) {
+      *pos_out = 4u * b + l;
+      *observed_out = obs;
+      return kInserted;
+    }
+    if (old == key) {
+      *pos_out = 4u * b + l;
+      return kExists;
+    }
+    // another key took the slot: look at the same bucket again
+  }
+  return kFull;
+}
+
+// --------------------------------------------------------------------------------- find phase
+__global__ void __launch_bounds__(kThreads) k_find(TableView t, const unsigned char* ops,
+                                                   const int* keys3, unsigned int* res,
+                                                   unsigned char* st, unsigned int n) {
+  Group g;
+  const unsigned int warps = gridDim.x * (blockDim.x / 32u);
+  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32u;
+  const unsigned int gi = (threadIdx.x & 31u) >> 2;
+  for (unsigned int base = warp * 8u; base < n; base += warps * 8u) {
+    const unsigned int i = base + gi;
+    if (i >= n) continue;   // whole group skips together
+    unsigned char op = ops[i];
+    unsigned long long key = 0;
+    bool ok = op <= kOpErase && load_key3(keys3, i, &key);
+    if (!ok) {
+      if (g.lane4 == 0) { res[i] = kNone; st[i] = kStInvalid; }
+      continue;
+    }
+    if (op != kOpFind) continue;
+    unsigned int val;
+    unsigned int pos = group_find_ro(g, t, key, &val);
+    if (g.lane4 == 0) {
+      res[i] = pos == kNone ? kNone : val;
+      st[i] = pos == kNone ? kStNotFound : kStFound;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- insert phase
+// Either keys3 + ops (a user batch; non-insert ops and invalid keys are skipped) or pkeys (a
+// list of packed keys, all inserts, length *count_dev capped at n).
+__global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
+                                                     DevCounters* cnt, const unsigned char* ops,
+                                                     const int* keys3,
+                                                     const unsigned long long* pkeys,
+                                                     const unsigned int* count_dev,
+                                                     const unsigned int* vals, unsigned int* res,
+                                                     unsigned char* st, unsigned int n_cap) {
+  __shared__ unsigned int s_live, s_from_empty, s_from_tomb, s_err;
+  if (threadIdx.x == 0) { s_live = 0; s_from_empty = 0; s_from_tomb = 0; s_err = 0; }
+  __syncthreads();
+  const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
+  const unsigned int free_top = pool.max_blocks ? (unsigned)max(cnt->free_top, 0) : 0u;
+  Group g;
+  const unsigned int warps = gridDim.x * (blockDim.x / 32u);
+  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32u;
+  const unsigned int gi = (threadIdx.x & 31u) >> 2;
+  for (unsigned int base = warp * 8u; base < n; base += warps * 8u) {
+    const unsigned int i = base + gi;
+    unsigned long long key = 0;
+    bool doit = false;
+    if (i < n) {
+      if (pkeys) {
+        key = pkeys[i];
+        doit = true;
+      } else if (ops[i] == kOpInsert) {
+        doit = load_key3(keys3, i, &key);
+      }
+    }
+    int outcome = 0;
+    unsigned int pos = kNone;
+    unsigned long long observed = 0;
+    if (doit) outcome = group_insert(g, t, key, &pos, &observed);
+    __syncwarp();
+    const bool leader = doit && g.lane4 == 0;
+    const bool won = leader && outcome == kInserted;
+    if (pool.max_blocks) {
+      unsigned int k = warp_append(&cnt->n_popped, won, 0xFFFFFFFFu);
+      if (won) {
+        if (k < free_top) {
+          unsigned int p = pool.stack[free_top - 1u - k];
+          t.slots[pos].val = p;
+          pool.pkeys[p] = key;
+          pool.state[p] = kFresh;
+          uint4* m = reinterpret_cast<uint4*>(pool.masks + 32u * p);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) m[q] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+          t.slots[pos].val = kPoolFail;
+        }
+      }
+    } else if (won) {
+      t.slots[pos].val = vals ? vals[i] : 0u;
+    }
+    if (won) {
+      atomicAdd(&s_live, 1u);
+      atomicAdd(observed == kEmpty ? &s_from_empty : &s_from_tomb, 1u);
+    }
+    if (leader) {
+      res[i] = pos;
+      st[i] = outcome == kInserted ? kStInserted : outcome == kExists ? kStExists : kStCapacity;
+      if (outcome == kFull) atomicOr(&s_err, kErrTable);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_live) atomicAdd(&cnt->n_live, s_live);
+    if (s_from_empty) atomicSub(&cnt->n_empty, s_from_empty);
+    if (s_from_tomb) atomicSub(&cnt->n_tomb, s_from_tomb);
+    if (s_err) atomicOr(&cnt->err, s_err);
+  }
+}
+
+// Resolve every insert's value once all claims are visible; undo claims whose pool pop failed;
+// optionally append each distinct pool index to a frame's touched list (epoch de-duplication).
+__global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolView pool,
+                                                            DevCounters* cnt,
+                                                            const unsigned int* count_dev,
+                                                            unsigned int* res, unsigned char* st,
+                                                            unsigned int n_cap,
+                                                            unsigned int* touched,
+                                                            unsigned int* n_touched,
+                                                            unsigned int epoch) {
+  __shared__ unsigned int s_undo, s_new, s_err;
+  if (threadIdx.x == 0) { s_undo = 0; s_new = 0; s_err = 0; }
+  __syncthreads();
+  const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && pool.max_blocks) {
+    int popped = (int)cnt->n_popped;
+    cnt->free_top = max(cnt->free_top - popped, 0);
+    cnt->n_popped = 0;
+  }
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const unsigned int rounds = (n + stride - 1u) / stride;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int p = kNone;
+    bool fresh_win = false;
+    if (i < n) {
+      unsigned char s = st[i];
+      if (s == kStInserted || s == kStExists) {
+        unsigned int pos = res[i];
+        unsigned int v = t.slots[pos].val;
+        if (v == kPoolFail) {
+          if (s == kStInserted) {
+            t.slots[pos].key = kTomb;
+            atomicAdd(&s_undo, 1u);
+          }
+          st[i] = kStCapacity;
+          res[i] = kNone;
+          atomicOr(&s_err, kErrPool);
+        } else {
+          res[i] = v;
+          p = v;
+          fresh_win = s == kStInserted;
+        }
+      } else if (s == kStCapacity) {
+        res[i] = kNone;
+      }
+    }
+    if (touched) {
+      bool first = false;
+      if (p != kNone) first = atomicExch(&pool.mark[p], epoch) != epoch;
+      unsigned int k = warp_append(n_touched, first, 0xFFFFFFFFu);
+      if (first) touched[k] = p;
+      if (fresh_win) atomicAdd(&s_new, 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_undo) {
+      atomicSub(&cnt->n_live, s_undo);
+      atomicAdd(&cnt->n_tomb, s_undo);
+    }
+    if (s_new) atomicAdd(&cnt->n_new, s_new);
+    if (s_err) atomicOr(&cnt->err, s_err);
+  }
+}
+
+// -------------------------------------------------------------------------------- erase phase
+__global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, DevCounters* cnt,
+                                                    const unsigned char* ops, const int* keys3,
+                                                    unsigned int* res, unsigned char* st,
+                                                    unsigned int n) {
+  __shared__ unsigned int s_erased;
+  if (threadIdx.x == 0) s_erased = 0;
+  __syncthreads();
+  Group g;
+  const unsigned int warps = gridDim.x * (blockDim.x / 32u);
+  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32u;
+  const unsigned int gi = (threadIdx.x & 31u) >> 2;
+  for (unsigned int base = warp * 8u; base < n; base += warps * 8u) {
+    const unsigned int i = base + gi;
+    unsigned long long key = 0;
+    bool doit = i < n && ops[i] == kOpErase && load_key3(keys3, i, &key);
+    bool erased = false;
+    unsigned int val = kNone;
+    if (doit) {
+      unsigned int pos = group_find_ro(g, t, key, &val);
+      if (pos != kNone) {
+        unsigned long long old = 0ull;
+        if (g.lane4 == (pos & 3u)) old = atomicCAS(&t.slots[pos].key, key, kTomb);
+        erased = g.bcast(old, pos & 3u) == key;
+      }
+    }
+    __syncwarp();
+    const bool leader = doit && g.lane4 == 0;
+    const bool push = leader && erased && pool.max_blocks;
+    unsigned int k = warp_append(reinterpret_cast<unsigned int*>(&cnt->free_top), push,
+                                 0xFFFFFFFFu);
+    if (push) {
+      pool.stack[k] = val;
+      pool.pkeys[val] = kEmpty;
+      pool.state[val] = 0u;
+    }
+    if (leader) {
+      res[i] = erased ? val : kNone;
+      st[i] = erased ? kStErased : kStNotFound;
+      if (erased) atomicAdd(&s_erased, 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_erased) {
+    atomicSub(&cnt->n_live, s_erased);
+    atomicAdd(&cnt->n_tomb, s_erased);
+  }
+}
+
+// ------------------------------------------------------------------------------------ rebuild
+// The table has been filled with EMPTY; re-insert every live entry of the shadow copy.  Keys are
+// unique, so each one simply claims the first EMPTY slot along its probe sequence.
+__global__ void __launch_bounds__(kThreads) k_rebuild(TableView t, const Slot* shadow,
+                                                      unsigned int n_slots, DevCounters* cnt) {
+  __shared__ unsigned int s_live;
+  if (threadIdx.x == 0) s_live = 0;
+  __syncthreads();
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += stride) {
+    ulonglong2 s = __ldg(reinterpret_cast<const ulonglong2*>(&shadow[i]));
+    if (s.x >= kTomb) continue;
+    unsigned int b = home_bucket(s.x, t.bmask, t.hash_fn);
+    bool done = false;
+    for (unsigned int probe = 0; probe <= t.bmask && !done; ++probe, b = (b + 1u) & t.bmask) {
+      for (unsigned int l = 0; l < 4u && !done; ++l) {
+        Slot* dst = &t.slots[4u * b + l];
+        if (__ldcg(&dst->key) != kEmpty) continue;
+        if (atomicCAS(&dst->key, kEmpty, s.x) == kEmpty) {
+          dst->val = (unsigned int)s.y;
+          done = true;
+        }
+      }
+    }
+    atomicAdd(&s_live, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_live) atomicAdd(&cnt->rebuild_n, s_live);
+}
+
+__global__ void k_rebuild_counters(DevCounters* cnt, unsigned int n_slots) {
+  cnt->n_live = cnt->rebuild_n;
+  cnt->n_tomb = 0;
+  cnt->n_empty = n_slots - cnt->rebuild_n;
+  cnt->rebuild_n = 0;
+}
+
+// --------------------------------------------------------------------- dump / load utilities
+__global__ void k_dump_table(TableView t, unsigned int n_slots, unsigned long long* out_keys,
+                             unsigned int* out_vals, unsigned int* out_n) {
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const unsigned int rounds = (n_slots + stride - 1u) / stride;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    ulonglong2 s = make_ulonglong2(kEmpty, 0ull);
+    if (i < n_slots) s = __ldg(reinterpret_cast<const ulonglong2*>(&t.slots[i]));
+    bool live = i < n_slots && s.x < kTomb;
+    unsigned int k = warp_append(out_n, live, 0xFFFFFFFFu);
+    if (live) {
+      out_keys[k] = s.x;
+      out_vals[k] = (unsigned int)s.y;
+    }
+  }
+}
+
+__global__ void k_gather_blocks(PoolView pool, const unsigned int* idx, unsigned int n,
+                                float* tsdf, float* w) {
+  for (unsigned int b = blockIdx.x; b < n; b += gridDim.x) {
+    unsigned int p = idx[b];
+    bool fresh = pool.state[p] & kFresh;
+    for (unsigned int v = threadIdx.x; v < 512u; v += blockDim.x) {
+      float2 x = fresh ? make_float2(0.f, 0.f) : pool.vox[512ull * p + v];
+      if (tsdf) tsdf[512ull * b + v] = x.x;
+      if (w) w[512ull * b + v] = x.y;
+    }
+  }
+}
+
+__global__ void k_scatter_blocks(PoolView pool, const unsigned int* idx, unsigned int n,
+                                 const float* tsdf, const float* w) {
+  for (unsigned int b = blockIdx.x; b < n; b += gridDim.x) {
+    unsigned int p = idx[b];
+    if (p >= pool.max_blocks) continue;
+    for (unsigned int v = threadIdx.x; v < 512u; v += blockDim.x)
+      pool.vox[512ull * p + v] = make_float2(tsdf[512ull * b + v], w[512ull * b + v]);
+    __syncthreads();
+    if (threadIdx.x == 0) pool.state[p] &= ~kFresh;
+  }
+}
+
+// Sign / weight bit masks of whole blocks from their voxel data (after an upload).
+__global__ void k_block_masks(PoolView pool, const unsigned int* idx, unsigned int n) {
+  const unsigned int warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  for (unsigned int b = blockIdx.x; b < n; b += gridDim.x) {
+    unsigned int p = idx[b];
+    if (p >= pool.max_blocks) continue;
+    for (unsigned int w = warp; w < 16u; w += blockDim.x >> 5) {
+      float2 x = pool.vox[512ull * p + 32u * w + lane];
+      unsigned int neg = __ballot_sync(0xFFFFFFFFu, x.x < 0.f);
+      unsigned int val = __ballot_sync(0xFFFFFFFFu, x.y > 0.f);
+      if (lane == 0) {
+        pool.masks[32u * p + w] = neg;
+        pool.masks[32u * p + 16u + w] = val;
+      }
+    }
+  }
+}
+
+__global__ void k_pack_keys(const int* keys3, unsigned int n, unsigned long long* out) {
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = pack_key(keys3[3u * i], keys3[3u * i + 1], keys3[3u * i + 2]);
+}
+
+}  // namespace
+
+#define VBH_GRID(kernel, threads)                                  \
+  static int grid_##kernel = 0;                                    \
+  if (!grid_##kernel) grid_##kernel = persistent_grid(kernel, threads, L.sms)
+
+void launch_hash_find(const Launch& L, TableView t, const unsigned char* ops, const int* keys3,
+                      unsigned int* res, unsigned char* st, unsigned int n) {
+  VBH_GRID(k_find, kThreads);
+  k_find<<<grid_k_find, kThreads, 0, L.stream>>>(t, ops, keys3, res, st, n);
+}
+void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                        const unsigned char* ops, const int* keys3,
+                        const unsigned long long* pkeys, const unsigned int* count_dev,
+                        const unsigned int* vals, unsigned int* res, unsigned char* st,
+                        unsigned int n) {
+  VBH_GRID(k_insert, kThreads);
+  k_insert<<<grid_k_insert, kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, pkeys, count_dev,
+                                                      vals, res, st, n);
+}
+void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                               const unsigned int* count_dev, unsigned int* res,
+                               unsigned char* st, unsigned int n, unsigned int* touched,
+                               unsigned int* n_touched, unsigned int epoch) {
+  VBH_GRID(k_insert_finish, kThreads);
+  k_insert_finish<<<grid_k_insert_finish, kThreads, 0, L.stream>>>(t, pool, cnt, count_dev, res,
+                                                                    st, n, touched, n_touched,
+                                                                    epoch);
+}
+void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                       const unsigned char* ops, const int* keys3, unsigned int* res,
+                       unsigned char* st, unsigned int n) {
+  VBH_GRID(k_erase, kThreads);
+  k_erase<<<grid_k_erase, kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, res, st, n);
+}
+void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
+                    DevCounters* cnt) {
+  VBH_GRID(k_rebuild, kThreads);
+  k_rebuild<<<grid_k_rebuild, kThreads, 0, L.stream>>>(t, shadow, n_slots, cnt);
+  k_rebuild_counters<<<1, 1, 0, L.stream>>>(cnt, n_slots);
+}
+void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,
+                       unsigned long long* out_keys, unsigned int* out_vals,
+                       unsigned int* out_n) {
+  VBH_GRID(k_dump_table, kThreads);
+  k_dump_table<<<grid_k_dump_table, kThreads, 0, L.stream>>>(t, n_slots, out_keys, out_vals,
+                                                              out_n);
+}
+void launch_gather_blocks(const Launch& L, PoolView pool, const unsigned int* idx,
+                          unsigned int n, float* tsdf, float* w) {
+  VBH_GRID(k_gather_blocks, 128);
+  if (n) k_gather_blocks<<<grid_k_gather_blocks, 128, 0, L.stream>>>(pool, idx, n, tsdf, w);
+}
+void launch_scatter_blocks(const Launch& L, PoolView pool, const unsigned int* idx,
+                           unsigned int n, const float* tsdf, const float* w) {
+  VBH_GRID(k_scatter_blocks, 128);
+  if (n) k_scatter_blocks<<<grid_k_scatter_blocks, 128, 0, L.stream>>>(pool, idx, n, tsdf, w);
+}
+void launch_block_masks(const Launch& L, PoolView pool, const unsigned int* idx, unsigned int n) {
+  VBH_GRID(k_block_masks, 128);
+  if (n) k_block_masks<<<grid_k_block_masks, 128, 0, L.stream>>>(pool, idx, n);
+}
+void launch_pack_keys(const Launch& L, const int* keys3, unsigned int n,
+                      unsigned long long* out) {
+  VBH_GRID(k_pack_keys, kThreads);
+  if (n) k_pack_keys<<<grid_k_pack_keys, kThreads, 0, L.stream>>>(keys3, n, out);
+}
+
+}  // namespace vbh

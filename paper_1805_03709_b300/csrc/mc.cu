@@ -1,0 +1,322 @@
+// Marching Cubes index extraction (Sec. 4.2): per-voxel 8-bit cube indices of a set of blocks,
+// with indices 0 and 255 (the set S^c) written as 0 and left out of the compacted stream.
+//
+// Block set.  After a fusion step the set is the touched blocks together with their seven
+// neighbours in negative direction (k - o, o in {0,1}^3 \ 0): the cube at a voxel reads the
+// corners g + {0,1}^3, so a change in block k alters cubes stored in those neighbours.  Blocks
+// erased since the last extraction are reported as removal records, and their live negative
+// neighbours are refreshed too (their cubes lose corners).  Lists are de-duplicated with epoch
+// stamps on the pool entries.
+//
+// Cube index.  Corner i of the cube at voxel g is g + c_i with c = (000, 100, 110, 010, 001,
+// 101, 111, 011) (x fastest); bit i is set iff TSDF(g + c_i) < 0; a cube with a corner in a
+// missing block or with weight 0 is invalid and gets 0.  The kernel never reads TSDF values:
+// fusion keeps a 128 B sign/weight bit mask per block, and one warp per block assembles the
+// 9 x 9 x 9 corner lattice from the masks of the block and its 7 positive neighbours, then
+// classifies a whole 8-voxel row at once with byte-sliced 64-bit arithmetic.
+#include "vbh_internal.cuh"
+
+namespace vbh {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMcThreads = 128;   // 4 warps, one block each
+constexpr unsigned long long kLo7 = 0x7F7F7F7F7F7F7F7Full;
+constexpr unsigned long long kHi1 = 0x8080808080808080ull;
+
+__global__ void k_mset_begin(DevCounters* cnt) {
+  cnt->n_mset = 0;
+  cnt->n_tombrec = 0;
+}
+
+__device__ __forceinline__ void add_to_set(PoolView& pool, unsigned int q, unsigned int epoch,
+                                           bool pred, unsigned int* mset, unsigned int* n_mset,
+                                           int stamp_version, unsigned int version) {
+  bool first = false;
+  if (pred) first = atomicExch(&pool.mark[q], epoch) != epoch;
+  unsigned int k = warp_append(n_mset, first, 0xFFFFFFFFu);
+  if (first) {
+    mset[k] = q;
+    if (stamp_version) pool.version[q] = version;
+  }
+}
+
+// touched blocks x 8 offsets, then removed keys x 8 offsets
+__global__ void __launch_bounds__(kThreads) k_mset_touched(TableView t, PoolView pool,
+                                                           DevCounters* cnt,
+                                                           const unsigned int* touched,
+                                                           const unsigned int* n_touched,
+                                                           const unsigned long long* removed,
+                                                           const unsigned int* n_removed,
+                                                           unsigned int removed_cap,
+                                                           unsigned int* mset,
+                                                           unsigned long long* tombrec,
+                                                           unsigned int epoch,
+                                                           unsigned int version) {
+  const unsigned int nt = n_touched ? *n_touched : 0u;
+  const unsigned int nr = min(*n_removed, removed_cap);
+  const unsigned int items = 8u * (nt + nr);
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const unsigned int rounds = (items + stride - 1u) / stride;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    const unsigned int e = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int q = kNone;
+    bool tomb = false;
+    unsigned long long tkey = 0;
+    if (e < items) {
+      const unsigned int o = e & 7u, b = e >> 3;
+      unsigned long long key;
+      bool is_removed = b >= nt;
+      if (!is_removed) {
+        const unsigned int p = touched[b];
+        key = pool.pkeys[p];
+        if (o == 0) q = key == kEmpty ? kNone : p;
+      } else {
+        key = removed[b - nt];
+      }
+      if (key != kEmpty && (o != 0 || is_removed)) {
+        int3 k = unpack_key(key);
+        k.x -= (int)(o & 1u);
+        k.y -= (int)((o >> 1) & 1u);
+        k.z -= (int)((o >> 2) & 1u);
+        if (key_ok(k.x, k.y, k.z)) {
+          unsigned int val;
+          const unsigned long long nk = pack_key(k.x, k.y, k.z);
+          unsigned int pos = thread_find(t, nk, &val);
+          if (o == 0) {   // a removed key itself: a removal record unless it is live again
+            tomb = pos == kNone;
+            tkey = nk;
+          } else if (pos != kNone) {
+            q = val;
+          }
+        }
+      }
+    }
+    add_to_set(pool, q, epoch, q != kNone, mset, &cnt->n_mset, 1, version);
+    unsigned int k = warp_append(&cnt->n_tombrec, tomb, 0xFFFFFFFFu);
+    if (tomb) tombrec[k] = tkey;
+  }
+}
+
+// explicit keys x 8 offsets (o = 0 is the key itself)
+__global__ void __launch_bounds__(kThreads) k_mset_keys(TableView t, PoolView pool,
+                                                        DevCounters* cnt, const int* keys3,
+                                                        unsigned int n, unsigned int* mset,
+                                                        unsigned int epoch) {
+  const unsigned int items = 8u * n;
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const unsigned int rounds = (items + stride - 1u) / stride;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    const unsigned int e = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int q = kNone;
+    if (e < items) {
+      const unsigned int o = e & 7u, b = e >> 3;
+      int x = keys3[3u * b] - (int)(o & 1u);
+      int y = keys3[3u * b + 1] - (int)((o >> 1) & 1u);
+      int z = keys3[3u * b + 2] - (int)((o >> 2) & 1u);
+      if (key_ok(x, y, z)) {
+        unsigned int val;
+        if (thread_find(t, pack_key(x, y, z), &val) != kNone) q = val;
+      }
+    }
+    add_to_set(pool, q, epoch, q != kNone, mset, &cnt->n_mset, 0, 0u);
+  }
+}
+
+// every live pool entry (since_mode: only those with version > since)
+__global__ void __launch_bounds__(kThreads) k_mset_scan(PoolView pool, DevCounters* cnt,
+                                                        unsigned int* mset, int since_mode,
+                                                        unsigned int since) {
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const unsigned int rounds = (pool.max_blocks + stride - 1u) / stride;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    const unsigned int p = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    bool take = false;
+    if (p < pool.max_blocks && pool.pkeys[p] != kEmpty)
+      take = !since_mode || pool.version[p] > since;
+    unsigned int k = warp_append(&cnt->n_mset, take, 0xFFFFFFFFu);
+    if (take) mset[k] = p;
+  }
+}
+
+// Zero-byte detector: 0x80 in every byte of v that is zero, 0 elsewhere (exact, no carries
+// between bytes because the low seven bits are added separately from the top bit).
+__device__ __forceinline__ unsigned long long zero_bytes(unsigned long long v) {
+  unsigned long long y = (v & kLo7) + kLo7;
+  return ~(y | v | kLo7);
+}
+
+// 9-bit lattice row (x = 0..8) of mask `kind` (0 sign, 1 weight) at lattice (Y, Z), Y, Z in
+// 0..8, from the masks of the block and its positive neighbours held in m[8][32] (neighbour
+// n = ox + 2 oy + 4 oz).
+__device__ __forceinline__ unsigned int row9(const unsigned int (*m)[32], int kind, int Y, int Z) {
+  const int nb = 2 * (Y >> 3) + 4 * (Z >> 3);
+  const int ly = Y & 7, lz = Z & 7;
+  const int word = 16 * kind + (ly >> 2) + 2 * lz;
+  const int sh = (ly & 3) * 8;
+  return ((m[nb][word] >> sh) & 0xFFu) | (((m[nb + 1][word] >> sh) & 1u) << 8);
+}
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_extract(
+    TableView t, PoolView pool, DevCounters* cnt, const unsigned int* mset,
+    const unsigned long long* tombrec, int* rec_keys3, unsigned int* rec_info,
+    unsigned int* rec_off, unsigned int* rec_cnt, unsigned short* ent_local,
+    unsigned char* ent_idx, unsigned int cap_blocks, unsigned int cap_entries,
+    unsigned int* n_blocks_dev, unsigned int* n_entries_dev, unsigned int tomb_version) {
+  __shared__ unsigned long long spread[256];   // bit i of b -> bit 8 i
+  __shared__ unsigned int msk[kMcThreads / 32][8][32];
+  for (int b = threadIdx.x; b < 256; b += kMcThreads) {
+    unsigned long long v = 0;
+    for (int i = 0; i < 8; ++i) v |= (unsigned long long)((b >> i) & 1) << (8 * i);
+    spread[b] = v;
+  }
+  __syncthreads();
+  const unsigned int n_m = cnt->n_mset, n_t = cnt->n_tombrec, total = n_m + n_t;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *n_blocks_dev = total;
+    cnt->mc_blocks = total;
+  }
+  const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned int nwarps = gridDim.x * (kMcThreads / 32);
+  unsigned int(*m)[32] = msk[warp];
+  bool overflow = false;
+  for (unsigned int r = blockIdx.x * (kMcThreads / 32) + warp; r < total; r += nwarps) {
+    if (r >= n_m) {   // removal record
+      if (lane == 0 && r < cap_blocks) {
+        const int3 k = unpack_key(tombrec[r - n_m]);
+        rec_keys3[3u * r] = k.x;
+        rec_keys3[3u * r + 1] = k.y;
+        rec_keys3[3u * r + 2] = k.z;
+        rec_info[r] = 0x80000000u | tomb_version;
+        rec_off[r] = 0u;
+        rec_cnt[r] = 0u;
+      }
+      continue;
+    }
+    const unsigned int q = mset[r];
+    const unsigned long long key = pool.pkeys[q];
+    const int3 k = unpack_key(key);
+    unsigned int nb = kNone;
+    if (lane == 0) {
+      nb = q;
+    } else if (lane < 8) {
+      const int x = k.x + (int)(lane & 1u), y = k.y + (int)((lane >> 1) & 1u),
+                z = k.z + (int)((lane >> 2) & 1u);
+      unsigned int val;
+      if (key_ok(x, y, z) && thread_find(t, pack_key(x, y, z), &val) != kNone) nb = val;
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const unsigned int qn = __shfl_sync(0xFFFFFFFFu, nb, n);
+      m[n][lane] = qn != kNone ? __ldcg(pool.masks + 32u * qn + lane) : 0u;
+    }
+    __syncwarp();
+    unsigned long long idx8[2], nz[2];
+    unsigned int mine = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int row = (int)lane + 32 * h, y = row & 7, z = row >> 3;
+      const unsigned int n00 = row9(m, 0, y, z), n10 = row9(m, 0, y + 1, z);
+      const unsigned int n01 = row9(m, 0, y, z + 1), n11 = row9(m, 0, y + 1, z + 1);
+      const unsigned int va = row9(m, 1, y, z) & row9(m, 1, y + 1, z) & row9(m, 1, y, z + 1) &
+                              row9(m, 1, y + 1, z + 1);
+      unsigned long long c = spread[n00 & 0xFFu] | (spread[(n00 >> 1) & 0xFFu] << 1) |
+                             (spread[(n10 >> 1) & 0xFFu] << 2) | (spread[n10 & 0xFFu] << 3) |
+                             (spread[n01 & 0xFFu] << 4) | (spread[(n01 >> 1) & 0xFFu] << 5) |
+                             (spread[(n11 >> 1) & 0xFFu] << 6) | (spread[n11 & 0xFFu] << 7);
+      c &= spread[(va & (va >> 1)) & 0xFFu] * 0xFFull;        // all 8 corners valid
+      c &= ~((zero_bytes(~c) >> 7) * 0xFFull);                 // S^c: 255 -> 0
+      nz[h] = ~zero_bytes(c) & kHi1;
+      idx8[h] = c;
+      mine += __popcll(nz[h]);
+    }
+    unsigned int incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if ((int)lane >= d) incl += v;
+    }
+    const unsigned int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    unsigned int base = 0;
+    if (lane == 0 && tot) base = atomicAdd(n_entries_dev, tot);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    const bool fits = (unsigned long long)base + tot <= cap_entries;
+    if (fits) {
+      unsigned int o = base + incl - mine;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = (int)lane + 32 * h;
+        unsigned long long bits = nz[h];
+        while (bits) {
+          const int x = (__ffsll((long long)bits) - 1) >> 3;
+          ent_local[o] = (unsigned short)(x + 8 * row);
+          ent_idx[o] = (unsigned char)(idx8[h] >> (8 * x));
+          ++o;
+          bits &= bits - 1ull;
+        }
+      }
+    } else {
+      overflow = true;
+    }
+    if (lane == 0 && r < cap_blocks) {
+      rec_keys3[3u * r] = k.x;
+      rec_keys3[3u * r + 1] = k.y;
+      rec_keys3[3u * r + 2] = k.z;
+      rec_info[r] = pool.version[q] & 0x7FFFFFFFu;
+      rec_off[r] = base;
+      rec_cnt[r] = tot;
+    }
+    __syncwarp();
+  }
+  if ((overflow || (total > cap_blocks && blockIdx.x == 0)) && lane == 0)
+    atomicOr(&cnt->err, kErrStream);
+}
+
+}  // namespace
+
+void launch_mset_touched(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                         const unsigned int* touched, const unsigned int* n_touched,
+                         const unsigned long long* removed, const unsigned int* n_removed,
+                         unsigned int removed_cap, unsigned int* mset,
+                         unsigned long long* tombrec, unsigned int epoch, unsigned int version) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_mset_touched, kThreads, L.sms);
+  k_mset_begin<<<1, 1, 0, L.stream>>>(cnt);
+  k_mset_touched<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, touched, n_touched, removed,
+                                                  n_removed, removed_cap, mset, tombrec, epoch,
+                                                  version);
+}
+
+void launch_mset_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                      const int* keys3, unsigned int n, unsigned int* mset, unsigned int epoch) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_mset_keys, kThreads, L.sms);
+  k_mset_begin<<<1, 1, 0, L.stream>>>(cnt);
+  if (n) k_mset_keys<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, keys3, n, mset, epoch);
+}
+
+void launch_mset_scan(const Launch& L, PoolView pool, DevCounters* cnt, unsigned int* mset,
+                      int since_mode, unsigned int since_version) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_mset_scan, kThreads, L.sms);
+  k_mset_begin<<<1, 1, 0, L.stream>>>(cnt);
+  k_mset_scan<<<grid, kThreads, 0, L.stream>>>(pool, cnt, mset, since_mode, since_version);
+}
+
+void launch_mc_extract(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                       const unsigned int* mset, const unsigned long long* tombrec,
+                       int* rec_keys3, unsigned int* rec_info, unsigned int* rec_off,
+                       unsigned int* rec_cnt, unsigned short* ent_local,
+                       unsigned char* ent_idx, unsigned int cap_blocks,
+                       unsigned int cap_entries, unsigned int* n_blocks_dev,
+                       unsigned int* n_entries_dev, unsigned int tomb_version) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_mc_extract, kMcThreads, L.sms);
+  k_mc_extract<<<grid, kMcThreads, 0, L.stream>>>(t, pool, cnt, mset, tombrec, rec_keys3,
+                                                  rec_info, rec_off, rec_cnt, ent_local, ent_idx,
+                                                  cap_blocks, cap_entries, n_blocks_dev,
+                                                  n_entries_dev, tomb_version);
+}
+
+}  // namespace vbh

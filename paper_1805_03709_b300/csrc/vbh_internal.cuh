@@ -1,0 +1,287 @@
+// Internal device-side definitions of libvbh (not part of the C ABI).
+//
+// Data layout in HBM (one handle):
+//   table   : n_buckets x 4 slots x 16 B.  Slot = {u64 key, u32 value, u32 pad}; a bucket is one
+//             64 B line, probed by a group of 4 lanes with one 16 B load each.  Keys are the
+//             int3 block coordinate packed as three 21-bit fields (x + 2^20 | y + 2^20 << 21 |
+//             z + 2^20 << 42); bit 63 is never set in a key, so EMPTY (all ones) and TOMB
+//             (all ones but bit 0) cannot collide with one.
+//   pool    : max_blocks x 512 float2 (TSDF, weight), 4 KiB per block, voxel lx + 8 ly + 64 lz.
+//   masks   : max_blocks x 32 u32: words 0-15 hold "TSDF < 0" bits, words 16-31 "weight > 0"
+//             bits of the 512 voxels (voxel i -> word i / 32, bit i % 32).  Written by every
+//             fusion of the block; the Marching Cubes pass reads only these 128 B per block.
+//   pkeys   : max_blocks u64, the packed key owning each pool entry (EMPTY when free).
+//   state   : max_blocks u32, bit 0 = fresh (allocated, voxel data not yet written: reads as 0).
+//   mark    : max_blocks u32 epoch stamps used to de-duplicate per-frame block lists.
+//   version : max_blocks u32, frame version of the block's last MC refresh.
+//   stack   : max_blocks u32 free pool indices, `free_top` of them valid.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vbh {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr unsigned long long kTomb = ~0ull - 1ull;
+constexpr unsigned int kNone = 0xFFFFFFFFu;
+constexpr unsigned int kPoolFail = 0xFFFFFFFEu;   // value of a slot whose pool pop failed
+constexpr int kKeyBits = 21;
+constexpr int kKeyOffset = 1 << 20;
+constexpr unsigned int kFresh = 1u;
+
+// sticky error flags (vbh_counters.error_flags)
+constexpr unsigned int kErrPool = 1u, kErrTable = 2u, kErrStream = 4u, kErrTimeout = 8u;
+
+// op codes and per-op statuses (same numbers as the C ABI)
+constexpr unsigned char kOpFind = 0, kOpInsert = 1, kOpErase = 2;
+constexpr unsigned char kStFound = 1, kStNotFound = 2, kStInserted = 3, kStExists = 4,
+                        kStErased = 5, kStCapacity = 6, kStInvalid = 7;
+
+struct __align__(16) Slot {
+  unsigned long long key;
+  unsigned int val;
+  unsigned int pad;
+};
+
+// Device counters (one instance per handle, in device memory).
+struct DevCounters {
+  int free_top;                 // valid entries of the free stack
+  unsigned int n_popped;        // pops in the current insert launch
+  unsigned int n_live, n_tomb, n_empty;
+  unsigned int n_cand, n_touched, n_new;
+  unsigned int n_mset, n_tombrec, n_removed;
+  unsigned int n_erased;
+  unsigned int err;
+  unsigned int mc_blocks, mc_entries;
+  unsigned int rebuild_n;       // live entries copied by the last rebuild
+  unsigned long long vox_updated;   // voxels fused by the last frame
+  unsigned int pad[2];
+};
+
+struct TableView {
+  Slot* slots;
+  unsigned int bmask;     // n_buckets - 1
+  unsigned int hash_fn;   // 0 primes, 1 mix
+};
+
+struct PoolView {
+  float2* vox;
+  unsigned int* masks;
+  unsigned long long* pkeys;
+  unsigned int* state;
+  unsigned int* mark;
+  unsigned int* version;
+  unsigned int* stack;
+  unsigned int max_blocks;  // 0 for a plain map
+};
+
+// ------------------------------------------------------------------------------ keys, hashing
+__host__ __device__ __forceinline__ bool key_ok(int x, int y, int z) {
+  return x >= -kKeyOffset && x < kKeyOffset && y >= -kKeyOffset && y < kKeyOffset &&
+         z >= -kKeyOffset && z < kKeyOffset;
+}
+__host__ __device__ __forceinline__ unsigned long long pack_key(int x, int y, int z) {
+  return (unsigned long long)(unsigned)(x + kKeyOffset) |
+         ((unsigned long long)(unsigned)(y + kKeyOffset) << kKeyBits) |
+         ((unsigned long long)(unsigned)(z + kKeyOffset) << (2 * kKeyBits));
+}
+__host__ __device__ __forceinline__ int3 unpack_key(unsigned long long k) {
+  const unsigned long long m = (1ull << kKeyBits) - 1ull;
+  return make_int3((int)(k & m) - kKeyOffset, (int)((k >> kKeyBits) & m) - kKeyOffset,
+                   (int)((k >> (2 * kKeyBits)) & m) - kKeyOffset);
+}
+
+// Sec. 5 "Retrieval": b = (x p1 XOR y p2 XOR z p3) mod n with p1 = 73856093, p2 = 19349669,
+// p3 = 83492791, evaluated in uint32 wrap-around arithmetic; n is a power of two (mask).
+__host__ __device__ __forceinline__ unsigned int hash_primes(unsigned long long packed) {
+  int3 k = unpack_key(packed);
+  return ((unsigned)k.x * 73856093u) ^ ((unsigned)k.y * 19349669u) ^ ((unsigned)k.z * 83492791u);
+}
+// SplitMix64 finaliser (Steele, Lea and Flood, 2014) of the packed key: neighbouring
+// coordinates land in unrelated buckets.
+__host__ __device__ __forceinline__ unsigned int hash_mix(unsigned long long z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (unsigned int)(z ^ (z >> 32));
+}
+__host__ __device__ __forceinline__ unsigned int home_bucket(unsigned long long packed,
+                                                             unsigned int bmask, unsigned int fn) {
+  return (fn == 0 ? hash_primes(packed) : hash_mix(packed)) & bmask;
+}
+
+#ifdef __CUDACC__
+// ------------------------------------------------------------------------- 4-lane group probe
+// A group is 4 consecutive lanes of a warp; each lane owns one slot of the probed bucket.
+struct Group {
+  unsigned int lane4;   // 0..3
+  unsigned int base;    // first lane of the group in the warp
+  unsigned int mask;    // the group's lanes
+  __device__ __forceinline__ Group() {
+    unsigned int lane = threadIdx.x & 31u;
+    lane4 = lane & 3u;
+    base = lane & ~3u;
+    mask = 0xFu << base;
+  }
+  __device__ __forceinline__ unsigned int ballot(bool p) const {
+    return (__ballot_sync(mask, p) >> base) & 0xFu;
+  }
+  template <class T>
+  __device__ __forceinline__ T bcast(T v, unsigned int src) const {
+    return __shfl_sync(mask, v, (int)(base + src));
+  }
+};
+
+__device__ __forceinline__ ulonglong2 load_slot_ro(const Slot* s) {
+  return __ldg(reinterpret_cast<const ulonglong2*>(s));
+}
+__device__ __forceinline__ ulonglong2 load_slot_cg(const Slot* s) {
+  return __ldcg(reinterpret_cast<const ulonglong2*>(s));
+}
+
+// Read-only find by a group (table not modified during the launch).  Returns the slot index
+// or kNone; *val receives the value.
+__device__ __forceinline__ unsigned int group_find_ro(const Group& g, const TableView& t,
+                                                      unsigned long long key, unsigned int* val) {
+  unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
+  for (unsigned int probe = 0; probe <= t.bmask; ++probe, b = (b + 1u) & t.bmask) {
+    ulonglong2 s = load_slot_ro(&t.slots[4u * b + g.lane4]);
+    unsigned int hit = g.ballot(s.x == key);
+    if (hit) {
+      unsigned int l = __ffs(hit) - 1;
+      *val = g.bcast((unsigned int)s.y, l);
+      return 4u * b + l;
+    }
+    if (g.ballot(s.x == kEmpty)) break;
+  }
+  *val = kNone;
+  return kNone;
+}
+
+// Single-thread find (4 x 16 B loads per bucket), for lookups scattered over a launch.
+__device__ __forceinline__ unsigned int thread_find(const TableView& t, unsigned long long key,
+                                                    unsigned int* val) {
+  unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
+  for (unsigned int probe = 0; probe <= t.bmask; ++probe, b = (b + 1u) & t.bmask) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(&t.slots[4u * b]);
+    ulonglong2 s0 = __ldcg(p), s1 = __ldcg(p + 1), s2 = __ldcg(p + 2), s3 = __ldcg(p + 3);
+    if (s0.x == key) { *val = (unsigned)s0.y; return 4u * b; }
+    if (s1.x == key) { *val = (unsigned)s1.y; return 4u * b + 1; }
+    if (s2.x == key) { *val = (unsigned)s2.y; return 4u * b + 2; }
+    if (s3.x == key) { *val = (unsigned)s3.y; return 4u * b + 3; }
+    if (s0.x == kEmpty || s1.x == kEmpty || s2.x == kEmpty || s3.x == kEmpty) break;
+  }
+  *val = kNone;
+  return kNone;
+}
+
+// Warp-aggregated append: every lane with `pred` gets a distinct index from *counter.
+__device__ __forceinline__ unsigned int warp_append(unsigned int* counter, bool pred,
+                                                    unsigned int active_mask) {
+  unsigned int bal = __ballot_sync(active_mask, pred);
+  if (!bal) return kNone;
+  unsigned int lane = threadIdx.x & 31u;
+  unsigned int leader = __ffs(bal) - 1;
+  unsigned int base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(bal));
+  base = __shfl_sync(active_mask, base, (int)leader);
+  return pred ? base + (unsigned)__popc(bal & ((1u << lane) - 1u)) : kNone;
+}
+template <class K>
+inline int persistent_grid(K kernel, int threads, int sms) {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
+  return (occ < 1 ? 1 : occ) * sms;
+}
+#endif  // __CUDACC__
+
+// ------------------------------------------------------------------------ per-frame constants
+// Canonical binary32 decision arithmetic: the kernels evaluate every discrete decision with
+// explicitly rounded intrinsics (__fmul_rn, __fadd_rn, __fsub_rn, __fmaf_rn, __frcp_rn, floorf)
+// in the order the host documentation fixes, so that no compiler contraction changes a result.
+struct FrameParams {
+  float R[9];          // row-major R of T_wc
+  float t[3];
+  float s, mu, inv_mu, wmax, ds, zmax;
+  float fx, fy, cxh, cyh;   // cxh = fl(cx + 0.5f)
+  float cx, cy;
+  float inv_bs;        // fl(1 / fl(8 s))
+  float fw, fh;        // (float)width, (float)height
+  int width, height;
+  int J;               // band steps: samples j = 0..J
+  const unsigned short* depth;
+};
+
+// ------------------------------------------------------------------------------- host launchers
+struct Launch {
+  cudaStream_t stream;
+  int sms;            // persistent grids are (resident CTAs per SM) x sms
+};
+
+// hash.cu
+void launch_hash_find(const Launch& L, TableView t, const unsigned char* ops, const int* keys3,
+                      unsigned int* res, unsigned char* st, unsigned int n);
+void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                        const unsigned char* ops, const int* keys3,
+                        const unsigned long long* pkeys, const unsigned int* count_dev,
+                        const unsigned int* vals, unsigned int* res, unsigned char* st,
+                        unsigned int n);
+void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                               const unsigned int* count_dev, unsigned int* res,
+                               unsigned char* st, unsigned int n, unsigned int* touched,
+                               unsigned int* n_touched, unsigned int epoch);
+void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                       const unsigned char* ops, const int* keys3, unsigned int* res,
+                       unsigned char* st, unsigned int n);
+void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
+                    DevCounters* cnt);
+void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,
+                       unsigned long long* out_keys, unsigned int* out_vals,
+                       unsigned int* out_n);
+void launch_gather_blocks(const Launch& L, PoolView pool, const unsigned int* idx,
+                          unsigned int n, float* tsdf, float* w);
+void launch_scatter_blocks(const Launch& L, PoolView pool, const unsigned int* idx,
+                           unsigned int n, const float* tsdf, const float* w);
+void launch_pack_keys(const Launch& L, const int* keys3, unsigned int n,
+                      unsigned long long* out);
+
+// frame.cu
+void launch_frame_begin(const Launch& L, DevCounters* cnt);
+void launch_alloc_keys(const Launch& L, const FrameParams& fp, unsigned long long* cand,
+                       unsigned int cap, DevCounters* cnt);
+void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
+                      const unsigned int* touched, const unsigned int* n_touched,
+                      DevCounters* cnt);
+
+// erase.cu
+void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                         float cx, float cy, float cz, float radius, float s,
+                         unsigned long long* removed, unsigned int removed_cap,
+                         int* out_keys3, unsigned int* out_n);
+void launch_erase_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                       const int* keys3, unsigned int n, unsigned long long* removed,
+                       unsigned int removed_cap, int* out_keys3, unsigned int* out_n);
+
+// mc.cu
+void launch_mset_touched(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                         const unsigned int* touched, const unsigned int* n_touched,
+                         const unsigned long long* removed, const unsigned int* n_removed,
+                         unsigned int removed_cap, unsigned int* mset,
+                         unsigned long long* tombrec, unsigned int epoch, unsigned int version);
+void launch_mset_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                      const int* keys3, unsigned int n, unsigned int* mset, unsigned int epoch);
+void launch_mset_scan(const Launch& L, PoolView pool, DevCounters* cnt, unsigned int* mset,
+                      int since_mode, unsigned int since_version);
+void launch_mc_extract(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                       const unsigned int* mset, const unsigned long long* tombrec,
+                       int* rec_keys3, unsigned int* rec_info, unsigned int* rec_off,
+                       unsigned int* rec_cnt, unsigned short* ent_local,
+                       unsigned char* ent_idx, unsigned int cap_blocks,
+                       unsigned int cap_entries, unsigned int* n_blocks_dev,
+                       unsigned int* n_entries_dev, unsigned int tomb_version);
+void launch_block_masks(const Launch& L, PoolView pool, const unsigned int* idx, unsigned int n);
+
+}  // namespace vbh
