@@ -520,7 +520,7 @@ vbh_status vbh_dump(vbh_handle* h, int32_t* keys3_host, float* tsdf_host, float*
     }
     cudaMemsetAsync(dn, 0, 4, h->stream);
     // the dump kernel appends every live slot; `room` bounds it (live is exact after a sync)
-    launch_dump_table(h->L, h->table(), h->n_slots, dk, dv, dn);
+    launch_dump_table(h->L, h->table(), h->n_slots, dk, dv, room, dn);
     h->launches += 1;
     cudaMemcpyAsync(&n, dn, 4, cudaMemcpyDeviceToHost, h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {

@@ -106,7 +106,10 @@ __global__ void __launch_bounds__(kThreads) k_find(TableView t, const unsigned c
       if (g.lane4 == 0) { res[i] = kNone; st[i] = kStInvalid; }
       continue;
     }
-    if (op != kOpFind) continue;
+    if (op != kOpFind) {   // inserts / erases are resolved by their own phases
+      if (g.lane4 == 0) { res[i] = kNone; st[i] = 0; }
+      continue;
+    }
     unsigned int val;
     unsigned int pos = group_find_ro(g, t, key, &val);
     if (g.lane4 == 0) {
@@ -345,7 +348,7 @@ __global__ void k_rebuild_counters(DevCounters* cnt, unsigned int n_slots) {
 
 // --------------------------------------------------------------------- dump / load utilities
 __global__ void k_dump_table(TableView t, unsigned int n_slots, unsigned long long* out_keys,
-                             unsigned int* out_vals, unsigned int* out_n) {
+                             unsigned int* out_vals, unsigned int cap, unsigned int* out_n) {
   const unsigned int stride = gridDim.x * blockDim.x;
   const unsigned int rounds = (n_slots + stride - 1u) / stride;
   for (unsigned int r = 0; r < rounds; ++r) {
@@ -354,7 +357,7 @@ __global__ void k_dump_table(TableView t, unsigned int n_slots, unsigned long lo
     if (i < n_slots) s = __ldg(reinterpret_cast<const ulonglong2*>(&t.slots[i]));
     bool live = i < n_slots && s.x < kTomb;
     unsigned int k = warp_append(out_n, live, 0xFFFFFFFFu);
-    if (live) {
+    if (live && k < cap) {
       out_keys[k] = s.x;
       out_vals[k] = (unsigned int)s.y;
     }
@@ -451,11 +454,11 @@ void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned i
   k_rebuild_counters<<<1, 1, 0, L.stream>>>(cnt, n_slots);
 }
 void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,
-                       unsigned long long* out_keys, unsigned int* out_vals,
+                       unsigned long long* out_keys, unsigned int* out_vals, unsigned int cap,
                        unsigned int* out_n) {
   VBH_GRID(k_dump_table, kThreads);
   k_dump_table<<<grid_k_dump_table, kThreads, 0, L.stream>>>(t, n_slots, out_keys, out_vals,
-                                                              out_n);
+                                                              cap, out_n);
 }
 void launch_gather_blocks(const Launch& L, PoolView pool, const unsigned int* idx,
                           unsigned int n, float* tsdf, float* w) {

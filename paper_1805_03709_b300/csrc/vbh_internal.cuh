@@ -239,7 +239,7 @@ void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters*
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt);
 void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,
-                       unsigned long long* out_keys, unsigned int* out_vals,
+                       unsigned long long* out_keys, unsigned int* out_vals, unsigned int cap,
                        unsigned int* out_n);
 void launch_gather_blocks(const Launch& L, PoolView pool, const unsigned int* idx,
                           unsigned int n, float* tsdf, float* w);

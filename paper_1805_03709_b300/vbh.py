@@ -1,0 +1,217 @@
+"""Python binding of libvbh (include/vbh.h): ctypes argument marshalling only.
+
+Every function below forwards to the C entry point of the same name; device buffers are torch
+CUDA tensors (their data_ptr() is passed), host buffers are numpy arrays.  Nothing here computes
+any part of the method, and there is no fallback: if libvbh.so is missing or cannot be loaded,
+`lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvbh.so")
+
+VBH_OK, VBH_ERR_INVALID_ARG, VBH_ERR_CAPACITY, VBH_ERR_CUDA, VBH_ERR_TIMEOUT, \
+    VBH_ERR_BUFFER_TOO_SMALL, VBH_ERR_UNSUPPORTED = range(7)
+VBH_OP_FIND, VBH_OP_INSERT, VBH_OP_ERASE = 0, 1, 2
+VBH_ST_FOUND, VBH_ST_NOT_FOUND, VBH_ST_INSERTED, VBH_ST_EXISTS, VBH_ST_ERASED, \
+    VBH_ST_CAPACITY, VBH_ST_INVALID = range(1, 8)
+VBH_NONE = 0xFFFFFFFF
+VBH_HASH_PRIMES, VBH_HASH_MIX = 0, 1
+VBH_ERASE_RADIUS, VBH_ERASE_KEYS = 0, 1
+VBH_MC_TOUCHED, VBH_MC_ALL, VBH_MC_KEYS, VBH_MC_SINCE = 0, 1, 2, 3
+VBH_REC_REMOVED = 0x80000000
+VBH_STAGES = ("erase", "alloc", "integrate", "mcset", "mc", "hash")
+
+_u32, _i32, _f32, _u64, _p = ctypes.c_uint32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, ctypes.c_void_p
+
+
+class vbh_config(ctypes.Structure):
+    _fields_ = [("voxel_size", _f32), ("trunc", _f32), ("max_weight", _f32),
+                ("depth_scale", _f32), ("zmax", _f32), ("width", _i32), ("height", _i32),
+                ("fx", _f32), ("fy", _f32), ("cx", _f32), ("cy", _f32), ("n_buckets", _u32),
+                ("slots_per_bucket", _u32), ("max_blocks", _u32), ("hash_fn", _u32),
+                ("max_batch", _u32)]
+
+
+class vbh_counters(ctypes.Structure):
+    _fields_ = [("live", _u32), ("tombstones", _u32), ("empty", _u32), ("free_blocks", _u32),
+                ("last_touched", _u32), ("last_new", _u32), ("last_candidates", _u32),
+                ("error_flags", _u32), ("kernel_launches", _u64), ("rebuilds", _u32),
+                ("last_mc_blocks", _u32), ("last_mc_entries", _u32), ("last_erased", _u32),
+                ("voxels_updated", _u64)]
+
+
+class vbh_frame_stats(ctypes.Structure):
+    _fields_ = [("touched", _u32), ("new_blocks", _u32), ("candidates", _u32),
+                ("error_flags", _u32)]
+
+
+class vbh_erase_selector(ctypes.Structure):
+    _fields_ = [("mode", _u32), ("centre", _f32 * 3), ("radius", _f32), ("keys3_dev", _p),
+                ("n_keys", _u32)]
+
+
+class vbh_mc_selector(ctypes.Structure):
+    _fields_ = [("mode", _u32), ("keys3_dev", _p), ("n_keys", _u32), ("since_version", _u32)]
+
+
+class vbh_mc_stream(ctypes.Structure):
+    _fields_ = [("keys3", _p), ("info", _p), ("offsets", _p), ("counts", _p), ("local", _p),
+                ("index", _p), ("cap_blocks", _u32), ("cap_entries", _u32),
+                ("n_blocks_dev", _p), ("n_entries_dev", _p)]
+
+
+# every symbol include/vbh.h declares: (name, restype, argtypes)
+SYMBOLS = [
+    ("vbh_abi_version", ctypes.c_int, []),
+    ("vbh_last_error", ctypes.c_char_p, []),
+    ("vbh_bucket_of", _u32, [_i32, _i32, _i32, _u32, _u32]),
+    ("vbh_create", ctypes.c_int, [ctypes.POINTER(vbh_config), _p, ctypes.POINTER(_p)]),
+    ("vbh_destroy", ctypes.c_int, [_p]),
+    ("vbh_set_stream", ctypes.c_int, [_p, _p]),
+    ("vbh_hash_batch", ctypes.c_int, [_p, _p, _p, _p, _p, _p, _u32]),
+    ("vbh_hash_rebuild", ctypes.c_int, [_p]),
+    ("vbh_integrate_frame", ctypes.c_int, [_p, _p, _p, _u32, ctypes.POINTER(vbh_frame_stats)]),
+    ("vbh_erase_blocks", ctypes.c_int, [_p, ctypes.POINTER(vbh_erase_selector), _p, _p]),
+    ("vbh_extract_mc_indices", ctypes.c_int,
+     [_p, ctypes.POINTER(vbh_mc_selector), ctypes.POINTER(vbh_mc_stream), ctypes.POINTER(_u64)]),
+    ("vbh_dump", ctypes.c_int, [_p, _p, _p, _p, _p, _u32, ctypes.POINTER(_u32)]),
+    ("vbh_load", ctypes.c_int, [_p, _p, _p, _p, _u32]),
+    ("vbh_get_counters", ctypes.c_int, [_p, ctypes.POINTER(vbh_counters)]),
+    ("vbh_clear_errors", ctypes.c_int, [_p]),
+    ("vbh_timing_enable", ctypes.c_int, [_p, ctypes.c_int]),
+    ("vbh_timing_read", ctypes.c_int, [_p, _p, _p, ctypes.c_int]),
+]
+
+_lib = None
+
+
+class VbhError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where} -> status {status}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load libvbh.so from the package directory (build it with `python -m
+    paper_1805_03709_b300.build`); raises if it is absent -- there is no CPU fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libvbh.so not built at {LIB_PATH}; run paper_1805_03709_b300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SYMBOLS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != VBH_OK:
+        raise VbhError(st, where, lib().vbh_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    """data_ptr of a torch tensor (device) or numpy array (host); None stays None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------- same-name calls
+def vbh_abi_version() -> int:
+    return lib().vbh_abi_version()
+
+
+def vbh_bucket_of(x: int, y: int, z: int, n_buckets: int, hash_fn: int) -> int:
+    return lib().vbh_bucket_of(x, y, z, n_buckets, hash_fn)
+
+
+def vbh_create(cfg: vbh_config, stream: int | None = None) -> int:
+    h = _p()
+    _check(lib().vbh_create(ctypes.byref(cfg), stream, ctypes.byref(h)), "vbh_create")
+    return h.value
+
+
+def vbh_destroy(h: int):
+    _check(lib().vbh_destroy(h), "vbh_destroy")
+
+
+def vbh_set_stream(h: int, stream: int | None):
+    _check(lib().vbh_set_stream(h, stream), "vbh_set_stream")
+
+
+def vbh_hash_batch(h, ops, keys3, vals, results, status, n=None):
+    n = int(ops.shape[0]) if n is None else int(n)
+    _check(lib().vbh_hash_batch(h, _ptr(ops), _ptr(keys3), _ptr(vals), _ptr(results),
+                                _ptr(status), n), "vbh_hash_batch")
+
+
+def vbh_hash_rebuild(h):
+    _check(lib().vbh_hash_rebuild(h), "vbh_hash_rebuild")
+
+
+def vbh_integrate_frame(h, depth, T_wc, frame_id: int, want_stats: bool = False):
+    T = np.ascontiguousarray(np.asarray(T_wc, np.float32).reshape(12))
+    st = vbh_frame_stats() if want_stats else None
+    _check(lib().vbh_integrate_frame(h, _ptr(depth), T.ctypes.data, int(frame_id),
+                                     ctypes.byref(st) if st is not None else None),
+           "vbh_integrate_frame")
+    return st
+
+
+def vbh_erase_blocks(h, sel: vbh_erase_selector, erased_keys3=None, n_erased=None):
+    _check(lib().vbh_erase_blocks(h, ctypes.byref(sel), _ptr(erased_keys3), _ptr(n_erased)),
+           "vbh_erase_blocks")
+
+
+def vbh_extract_mc_indices(h, sel: vbh_mc_selector, out: vbh_mc_stream, want_needed=False):
+    need = _u64(0) if want_needed else None
+    _check(lib().vbh_extract_mc_indices(h, ctypes.byref(sel), ctypes.byref(out),
+                                        ctypes.byref(need) if need is not None else None),
+           "vbh_extract_mc_indices")
+    return None if need is None else need.value
+
+
+def vbh_dump(h, keys3, tsdf, weight, vals, cap: int) -> int:
+    n = _u32(0)
+    _check(lib().vbh_dump(h, _ptr(keys3), _ptr(tsdf), _ptr(weight), _ptr(vals), cap,
+                          ctypes.byref(n)), "vbh_dump")
+    return n.value
+
+
+def vbh_load(h, keys3, tsdf, weight):
+    _check(lib().vbh_load(h, _ptr(keys3), _ptr(tsdf), _ptr(weight), int(keys3.shape[0])),
+           "vbh_load")
+
+
+def vbh_get_counters(h) -> vbh_counters:
+    c = vbh_counters()
+    _check(lib().vbh_get_counters(h, ctypes.byref(c)), "vbh_get_counters")
+    return c
+
+
+def vbh_clear_errors(h):
+    _check(lib().vbh_clear_errors(h), "vbh_clear_errors")
+
+
+def vbh_timing_enable(h, enable: bool):
+    _check(lib().vbh_timing_enable(h, int(bool(enable))), "vbh_timing_enable")
+
+
+def vbh_timing_read(h, reset: bool = False):
+    ms = np.zeros(len(VBH_STAGES), np.float64)
+    n = np.zeros(len(VBH_STAGES), np.uint64)
+    _check(lib().vbh_timing_read(h, ms.ctypes.data, n.ctypes.data, int(reset)), "vbh_timing_read")
+    return dict(zip(VBH_STAGES, ms.tolist())), dict(zip(VBH_STAGES, n.tolist()))

@@ -1,0 +1,185 @@
+"""Object wrappers over the C ABI for Python callers (tests, benchmark, applications).
+
+`HashMap` and `Volume` own a libvbh handle plus the torch CUDA tensors that receive outputs
+(per-op results, the Marching Cubes stream).  They only allocate buffers and marshal arguments;
+every step of the method runs in libvbh's kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import vbh as V
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class HashMap:
+    """GPU map of int3 keys (Sec. 5).  With max_blocks > 0 the values are voxel-block pool
+    indices (a voxel-block map); otherwise they are the caller's uint32 values."""
+
+    def __init__(self, n_buckets: int, hash_fn: int = V.VBH_HASH_MIX, max_batch: int = 1 << 22,
+                 max_blocks: int = 0):
+        cfg = V.vbh_config(n_buckets=n_buckets, slots_per_bucket=4, hash_fn=hash_fn,
+                           max_batch=max_batch, max_blocks=max_blocks)
+        if max_blocks:
+            cfg.voxel_size, cfg.trunc, cfg.max_weight, cfg.depth_scale = 0.01, 0.04, 64.0, 0.001
+            cfg.width, cfg.height, cfg.fx, cfg.fy, cfg.cx, cfg.cy = 1, 1, 1.0, 1.0, 0.0, 0.0
+        self.cfg = cfg
+        self.h = V.vbh_create(cfg, _stream())
+
+    def close(self):
+        if getattr(self, "h", None):
+            V.vbh_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def batch(self, ops: torch.Tensor, keys3: torch.Tensor, vals: torch.Tensor | None = None,
+              results: torch.Tensor | None = None, status: torch.Tensor | None = None):
+        n = int(ops.shape[0])
+        if results is None:
+            results = torch.empty(n, dtype=torch.int32, device=ops.device)
+        if status is None:
+            status = torch.empty(n, dtype=torch.uint8, device=ops.device)
+        V.vbh_hash_batch(self.h, ops, keys3, vals, results, status, n)
+        return results, status
+
+    def rebuild(self):
+        V.vbh_hash_rebuild(self.h)
+
+    def counters(self) -> V.vbh_counters:
+        return V.vbh_get_counters(self.h)
+
+    def dump(self):
+        n = self.counters().live
+        k = np.zeros((max(n, 1), 3), np.int32)
+        v = np.zeros(max(n, 1), np.uint32)
+        m = V.vbh_dump(self.h, k, None, None, v, n)
+        return k[:m], v[:m]
+
+
+@dataclasses.dataclass
+class McStream:
+    """Device buffers of one extraction (see vbh_mc_stream)."""
+    keys3: torch.Tensor
+    info: torch.Tensor
+    offsets: torch.Tensor
+    counts: torch.Tensor
+    local: torch.Tensor
+    index: torch.Tensor
+    n: torch.Tensor        # [n_blocks, n_entries] (uint32 on the device)
+
+    @classmethod
+    def allocate(cls, cap_blocks: int, cap_entries: int, device="cuda"):
+        z = lambda n, dt: torch.zeros(max(n, 1), dtype=dt, device=device)
+        return cls(z(3 * cap_blocks, torch.int32).view(-1, 3), z(cap_blocks, torch.int32),
+                   z(cap_blocks, torch.int32), z(cap_blocks, torch.int32),
+                   z(cap_entries, torch.int16), z(cap_entries, torch.uint8), z(2, torch.int32))
+
+    def c_struct(self) -> V.vbh_mc_stream:
+        return V.vbh_mc_stream(self.keys3.data_ptr(), self.info.data_ptr(), self.offsets.data_ptr(),
+                               self.counts.data_ptr(), self.local.data_ptr(), self.index.data_ptr(),
+                               self.info.shape[0], self.local.shape[0], self.n.data_ptr(),
+                               self.n.data_ptr() + 4)
+
+    def to_host(self):
+        """{(x, y, z): (info, local idx array, cube idx array)} of the produced records."""
+        nb, ne = (int(x) & 0xFFFFFFFF for x in self.n.cpu().tolist())
+        if nb > self.info.shape[0] or ne > self.local.shape[0]:
+            raise RuntimeError(f"stream overflow: {nb} blocks / {ne} entries")
+        keys = self.keys3[:nb].cpu().numpy()
+        info = self.info[:nb].cpu().numpy().view(np.uint32)
+        off = self.offsets[:nb].cpu().numpy().view(np.uint32)
+        cnt = self.counts[:nb].cpu().numpy().view(np.uint32)
+        loc = self.local[:ne].cpu().numpy().view(np.uint16)
+        idx = self.index[:ne].cpu().numpy()
+        out = {}
+        for i in range(nb):
+            k = tuple(int(x) for x in keys[i])
+            if k in out:
+                raise RuntimeError(f"block {k} emitted twice")
+            o, c = int(off[i]), int(cnt[i])
+            out[k] = (int(info[i]), loc[o:o + c].copy(), idx[o:o + c].copy())
+        return out
+
+
+class Volume:
+    """Voxel-block TSDF volume on one GPU (Sec. 4.1 fusion, Sec. 4.2 MC indices)."""
+
+    def __init__(self, voxel_size, trunc, width, height, fx, fy, cx, cy, n_buckets, max_blocks,
+                 max_weight=64.0, depth_scale=0.001, zmax=0.0, hash_fn=V.VBH_HASH_MIX,
+                 mc_cap_blocks=None, mc_cap_entries=None):
+        cfg = V.vbh_config(voxel_size=voxel_size, trunc=trunc, max_weight=max_weight,
+                           depth_scale=depth_scale, zmax=zmax, width=width, height=height,
+                           fx=fx, fy=fy, cx=cx, cy=cy, n_buckets=n_buckets, slots_per_bucket=4,
+                           max_blocks=max_blocks, hash_fn=hash_fn, max_batch=max(max_blocks, 1))
+        self.cfg = cfg
+        self.h = V.vbh_create(cfg, _stream())
+        cb = mc_cap_blocks if mc_cap_blocks is not None else max_blocks
+        ce = mc_cap_entries if mc_cap_entries is not None else max_blocks * 512
+        self.stream = McStream.allocate(cb, ce)
+        self.erased_keys = torch.zeros((max_blocks, 3), dtype=torch.int32, device="cuda")
+        self.n_erased = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def close(self):
+        if getattr(self, "h", None):
+            V.vbh_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def integrate(self, depth: torch.Tensor, T_wc, frame_id: int, stats: bool = False):
+        assert depth.dtype == torch.uint16 and depth.is_cuda and depth.is_contiguous()
+        return V.vbh_integrate_frame(self.h, depth, T_wc, frame_id, stats)
+
+    def erase_radius(self, centre, radius, keys_out: bool = True):
+        sel = V.vbh_erase_selector(mode=V.VBH_ERASE_RADIUS, radius=float(radius))
+        sel.centre[:] = [float(c) for c in centre]
+        V.vbh_erase_blocks(self.h, sel, self.erased_keys if keys_out else None,
+                           self.n_erased if keys_out else None)
+
+    def erase_keys(self, keys3: torch.Tensor, keys_out: bool = True):
+        sel = V.vbh_erase_selector(mode=V.VBH_ERASE_KEYS, keys3_dev=keys3.data_ptr(),
+                                   n_keys=int(keys3.shape[0]))
+        V.vbh_erase_blocks(self.h, sel, self.erased_keys if keys_out else None,
+                           self.n_erased if keys_out else None)
+
+    def erased(self) -> np.ndarray:
+        n = int(self.n_erased.item())
+        return self.erased_keys[:n].cpu().numpy()
+
+    def extract(self, mode=V.VBH_MC_TOUCHED, keys3: torch.Tensor | None = None, since=0,
+                stream: McStream | None = None, sync=False):
+        s = stream or self.stream
+        sel = V.vbh_mc_selector(mode=mode, keys3_dev=keys3.data_ptr() if keys3 is not None else None,
+                                n_keys=int(keys3.shape[0]) if keys3 is not None else 0,
+                                since_version=since)
+        need = V.vbh_extract_mc_indices(self.h, sel, s.c_struct(), want_needed=sync)
+        return s if not sync else (s, need)
+
+    def counters(self) -> V.vbh_counters:
+        return V.vbh_get_counters(self.h)
+
+    def dump(self):
+        n = self.counters().live
+        k = np.zeros((max(n, 1), 3), np.int32)
+        F = np.zeros((max(n, 1), 512), np.float32)
+        W = np.zeros((max(n, 1), 512), np.float32)
+        m = V.vbh_dump(self.h, k, F, W, None, n)
+        order = np.lexsort((k[:m, 2], k[:m, 1], k[:m, 0]))
+        return k[:m][order], F[:m][order], W[:m][order]
+
+    def load(self, keys3, tsdf, weight):
+        V.vbh_load(self.h, np.ascontiguousarray(keys3, np.int32),
+                   np.ascontiguousarray(tsdf, np.float32), np.ascontiguousarray(weight, np.float32))
+
+    def timing(self, enable=True):
+        V.vbh_timing_enable(self.h, enable)
+
+    def timing_read(self, reset=False):
+        return V.vbh_timing_read(self.h, reset)

@@ -1,0 +1,225 @@
+"""GPU parity of the hash batch (Sec. 5 find / insert / erase, phased reading) against the CPU
+oracle, through the C ABI.  Bit-exact: per-op statuses and results (finds exactly; duplicate
+inserts / erases of one key compared as a multiset per key, since which duplicate wins is not
+fixed), and the final key -> value contents."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import OracleMap
+from paper_1805_03709_b300 import synth
+from paper_1805_03709_b300 import vbh as V
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1805_03709_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def HashMap(*a, **k):
+    from paper_1805_03709_b300.volume import HashMap as H
+    return H(*a, **k)
+
+
+def key_value(keys):
+    k = keys.astype(np.int64)
+    return ((k[:, 0] * 73 + k[:, 1] * 977 + k[:, 2] * 10007) & 0x7FFFFFFF).astype(np.uint32)
+
+
+def gpu_batch(hm, ops, keys, vals):
+    o = torch.from_numpy(ops).cuda()
+    k = torch.from_numpy(np.ascontiguousarray(keys, np.int32)).cuda()
+    v = torch.from_numpy(vals.view(np.int32)).cuda() if vals is not None else None
+    res, st = hm.batch(o, k, v)
+    return res.cpu().numpy().view(np.uint32), st.cpu().numpy()
+
+
+def assert_same(ops, keys, res_g, st_g, res_o, st_o):
+    """Finds and invalid ops exactly; inserts and erases as per-key multisets."""
+    exact = (ops == V.VBH_OP_FIND) | (st_o == V.VBH_ST_INVALID)
+    np.testing.assert_array_equal(st_g[exact], st_o[exact])
+    np.testing.assert_array_equal(res_g[exact], res_o[exact])
+    for op in (V.VBH_OP_INSERT, V.VBH_OP_ERASE):
+        sel = (ops == op) & (st_o != V.VBH_ST_INVALID)
+        if not sel.any():
+            continue
+        def rows(res, st):
+            k = keys[sel].astype(np.int64)
+            a = np.stack([k[:, 0], k[:, 1], k[:, 2], st[sel].astype(np.int64),
+                          res[sel].astype(np.int64)], 1)
+            return a[np.lexsort(a.T[::-1])]
+        np.testing.assert_array_equal(rows(res_g, st_g), rows(res_o, st_o))
+
+
+def check_contents(hm, om):
+    kg, vg = hm.dump()
+    ko, vo = om.dump()
+    order = np.lexsort(kg.T[::-1])
+    np.testing.assert_array_equal(kg[order], ko)
+    np.testing.assert_array_equal(vg[order], vo)
+    c = hm.counters()
+    assert c.live == len(om)
+    assert c.live + c.tombstones + c.empty == hm.cfg.n_buckets * 4
+
+
+def mixed_ops(rng, n, pool, present, p=(0.5, 0.3, 0.2)):
+    ops = rng.choice([0, 1, 2], size=n, p=p).astype(np.uint8)
+    idx = rng.integers(0, len(pool), size=n)
+    return ops, pool[idx]
+
+
+@pytest.mark.parametrize("hash_fn", [V.VBH_HASH_MIX, V.VBH_HASH_PRIMES])
+@pytest.mark.parametrize("universe,batch,n_batches", [(16, 37, 30), (3000, 1000, 12), (200000, 65537, 4)])
+def test_random_batches(hash_fn, universe, batch, n_batches):
+    rng = np.random.default_rng(universe + hash_fn)
+    pool = synth.random_hash_keys(universe, seed=universe)
+    hm = HashMap(n_buckets=max(16, 1 << int(np.ceil(np.log2(universe / 2)))), hash_fn=hash_fn)
+    om = OracleMap()
+    for _ in range(n_batches):
+        ops, keys = mixed_ops(rng, batch, pool, None)
+        vals = key_value(keys)
+        rg, sg = gpu_batch(hm, ops, keys, vals)
+        ro, so = om.batch(ops, keys, vals)
+        assert_same(ops, keys, rg, sg, ro, so)
+    check_contents(hm, om)
+
+
+def test_zipf_clustered_keys_heavy_duplication():
+    rng = np.random.default_rng(7)
+    hm = HashMap(n_buckets=1 << 14)
+    om = OracleMap()
+    for b in range(6):
+        keys = synth.zipf_cluster_keys(50000, seed=b, hot_side=32)
+        ops = rng.choice([0, 1, 2], size=len(keys), p=[0.5, 0.3, 0.2]).astype(np.uint8)
+        vals = key_value(keys)
+        rg, sg = gpu_batch(hm, ops, keys, vals)
+        ro, so = om.batch(ops, keys, vals)
+        assert_same(ops, keys, rg, sg, ro, so)
+    check_contents(hm, om)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 8, 9, 31, 33, 255, 257])
+def test_ragged_sizes_and_invalid(n):
+    rng = np.random.default_rng(n)
+    keys = rng.integers(-40, 40, size=(n, 3)).astype(np.int32)
+    keys[::5, 1] = 1 << 20          # out of range
+    ops = rng.integers(0, 4, size=n).astype(np.uint8)   # 3 = unknown op
+    hm = HashMap(n_buckets=64)
+    om = OracleMap()
+    for _ in range(3):
+        vals = key_value(keys)
+        rg, sg = gpu_batch(hm, ops, keys, vals)
+        ro, so = om.batch(ops, keys, vals)
+        assert_same(ops, keys, rg, sg, ro, so)
+        ops = np.roll(ops, 1)
+    check_contents(hm, om)
+
+
+def test_empty_batch():
+    hm = HashMap(n_buckets=16)
+    e = torch.zeros(0, dtype=torch.uint8, device="cuda")
+    res, st = hm.batch(e, torch.zeros((0, 3), dtype=torch.int32, device="cuda"))
+    assert res.numel() == 0 and hm.counters().live == 0
+
+
+def test_full_table_reports_capacity_and_recovers():
+    hm = HashMap(n_buckets=4)      # 16 slots
+    keys = np.array([[i, 2 * i, -i] for i in range(20)], np.int32)
+    ops = np.full(20, V.VBH_OP_INSERT, np.uint8)
+    rg, sg = gpu_batch(hm, ops, keys, key_value(keys))
+    assert (sg == V.VBH_ST_INSERTED).sum() == 16 and (sg == V.VBH_ST_CAPACITY).sum() == 4
+    assert np.all(rg[sg == V.VBH_ST_CAPACITY] == V.VBH_NONE)
+    assert hm.counters().error_flags & 2
+    ins = keys[sg == V.VBH_ST_INSERTED]
+    lost = keys[sg == V.VBH_ST_CAPACITY]
+    # erase two, then the lost keys can go in (tombstones are reused)
+    gpu_batch(hm, np.full(2, V.VBH_OP_ERASE, np.uint8), ins[:2], None)
+    rg, sg = gpu_batch(hm, np.full(2, V.VBH_OP_INSERT, np.uint8), lost[:2], key_value(lost[:2]))
+    assert np.all(sg == V.VBH_ST_INSERTED)
+    rg, sg = gpu_batch(hm, np.zeros(18, np.uint8), np.concatenate([ins[2:], lost[:2]]), None)
+    assert np.all(sg == V.VBH_ST_FOUND)
+
+
+@pytest.mark.parametrize("lf", [0.5, 0.7, 0.9])
+def test_load_factor_mixed_and_rebuild(lf):
+    rng = np.random.default_rng(int(lf * 10))
+    n_buckets = 1 << 12
+    cap = n_buckets * 4
+    pool = synth.random_hash_keys(int(cap * 1.5), seed=3)
+    hm = HashMap(n_buckets=n_buckets)
+    om = OracleMap()
+    pre = pool[:int(cap * lf)]
+    for ch in np.array_split(np.arange(len(pre)), 4):
+        k = pre[ch]
+        gpu_batch(hm, np.full(len(k), 1, np.uint8), k, key_value(k))
+        om.batch(np.full(len(k), 1, np.uint8), k, key_value(k))
+    check_contents(hm, om)
+    for b in range(6):
+        ops = rng.choice([0, 1, 2], size=4000, p=[0.5, 0.25, 0.25]).astype(np.uint8)
+        keys = pool[rng.integers(0, len(pool), size=4000)]
+        vals = key_value(keys)
+        rg, sg = gpu_batch(hm, ops, keys, vals)
+        ro, so = om.batch(ops, keys, vals)
+        assert_same(ops, keys, rg, sg, ro, so)
+        if b == 3:
+            hm.rebuild()
+            assert hm.counters().tombstones == 0
+            check_contents(hm, om)
+    check_contents(hm, om)
+
+
+def test_voxel_block_map_pool_indices():
+    hm = HashMap(n_buckets=256, max_blocks=100)
+    keys = np.array([[i, -i, 3] for i in range(120)], np.int32)
+    ops = np.full(120, V.VBH_OP_INSERT, np.uint8)
+    rg, sg = gpu_batch(hm, ops, keys, None)
+    ok = sg == V.VBH_ST_INSERTED
+    assert ok.sum() == 100 and (sg == V.VBH_ST_CAPACITY).sum() == 20
+    assert sorted(rg[ok].tolist()) == list(range(100))       # each pool entry once
+    assert hm.counters().free_blocks == 0 and hm.counters().live == 100
+    # duplicates of one key share its pool index
+    dup = np.repeat(keys[:3], 4, axis=0)
+    rg2, sg2 = gpu_batch(hm, np.full(12, V.VBH_OP_INSERT, np.uint8), dup, None)
+    assert np.all(sg2 == V.VBH_ST_EXISTS)
+    np.testing.assert_array_equal(rg2, np.repeat(rg[:3], 4))
+    # erase returns entries to the pool; re-insert reuses them
+    rg3, sg3 = gpu_batch(hm, np.full(10, V.VBH_OP_ERASE, np.uint8), keys[:10], None)
+    assert np.all(sg3 == V.VBH_ST_ERASED) and hm.counters().free_blocks == 10
+    rg4, sg4 = gpu_batch(hm, ops[100:110], keys[100:110], None)
+    assert np.all(sg4 == V.VBH_ST_INSERTED)
+    assert sorted(rg4.tolist()) == sorted(rg3.tolist())
+
+
+def test_full_size_table_lf07_batch_2e20():
+    """2^22 buckets x 4 slots, prefilled to load factor 0.7 with uniform keys in [-2^20, 2^20)^3,
+    then a 2^20-op batch (50 % find half hits, 30 % insert of absent keys, 20 % erase)."""
+    n_buckets = 1 << 22
+    cap = n_buckets * 4
+    n_pre = int(0.7 * cap)
+    rng = np.random.default_rng(1805)
+    pool = synth.random_hash_keys(n_pre + (1 << 20), seed=1805)
+    pre, fresh = pool[:n_pre], pool[n_pre:]
+    hm = HashMap(n_buckets=n_buckets)
+    om = OracleMap()
+    for ch in np.array_split(np.arange(n_pre), 4):
+        k = pre[ch]
+        gpu_batch(hm, np.full(len(k), 1, np.uint8), k, key_value(k))
+        om.batch(np.full(len(k), 1, np.uint8), k, key_value(k))
+    n = 1 << 20
+    nf, ni = n // 2, int(0.3 * n)
+    ne = n - nf - ni
+    keys = np.concatenate([pre[rng.integers(0, n_pre, nf // 2)], fresh[rng.integers(0, len(fresh), nf - nf // 2)],
+                           fresh[:ni], pre[rng.integers(0, n_pre, ne)]])
+    ops = np.concatenate([np.zeros(nf), np.ones(ni), np.full(ne, 2)]).astype(np.uint8)
+    perm = rng.permutation(n)
+    keys, ops = keys[perm], ops[perm]
+    vals = key_value(keys)
+    rg, sg = gpu_batch(hm, ops, keys, vals)
+    ro, so = om.batch(ops, keys, vals)
+    assert_same(ops, keys, rg, sg, ro, so)
+    c = hm.counters()
+    assert c.live == len(om)

@@ -1,0 +1,80 @@
+"""CPU-only checks of the C ABI library: it builds, loads, exports every symbol include/vbh.h
+declares, validates configurations without touching a GPU, and its host-side bucket function
+matches the paper's spatial hash (Sec. 5) with the primes from tests/golden/k1_spatial_hash.txt."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_1805_03709_b300 import build
+    build.build()
+    from paper_1805_03709_b300 import vbh
+    vbh.lib()
+    return vbh
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "vbh.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vbh_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(V):
+    names = declared_functions()
+    assert len(names) >= 15
+    bound = {s[0] for s in V.SYMBOLS}
+    for n in names:
+        assert hasattr(V.lib(), n), n
+        assert n in bound, n
+
+
+def test_abi_version(V):
+    src = open(os.path.join(ROOT, "include", "vbh.h")).read()
+    ver = int(re.search(r"#define VBH_ABI_VERSION (\d+)", src).group(1))
+    assert V.vbh_abi_version() == ver
+
+
+def test_paper_spatial_hash(V):
+    primes = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "k1_spatial_hash.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            primes[k] = int(v)
+    rng = np.random.default_rng(0)
+    for n_buckets in (2, 1 << 10, 1 << 22):
+        for x, y, z in rng.integers(-(1 << 20), 1 << 20, size=(200, 3)).tolist() + [[0, 0, 0], [-1, -1, -1]]:
+            m = 0xFFFFFFFF
+            b = ((x * primes["p1"]) & m) ^ ((y * primes["p2"]) & m) ^ ((z * primes["p3"]) & m)
+            assert V.vbh_bucket_of(x, y, z, n_buckets, V.VBH_HASH_PRIMES) == b % n_buckets
+            assert V.vbh_bucket_of(x, y, z, n_buckets, V.VBH_HASH_MIX) < n_buckets
+    assert V.vbh_bucket_of(1 << 20, 0, 0, 1024, 0) == V.VBH_NONE
+    assert V.vbh_bucket_of(0, 0, 0, 1000, 0) == V.VBH_NONE
+
+
+def test_mix_hash_spreads_a_contiguous_cube(V):
+    n = 1 << 12
+    counts = np.zeros(n, np.int64)
+    for x in range(16):
+        for y in range(16):
+            for z in range(16):
+                counts[V.vbh_bucket_of(x, y, z, n, V.VBH_HASH_MIX)] += 1
+    assert counts.max() <= 8   # 4096 keys over 4096 buckets
+
+
+@pytest.mark.parametrize("field,value", [("n_buckets", 1000), ("n_buckets", 0),
+                                         ("slots_per_bucket", 8), ("hash_fn", 5),
+                                         ("voxel_size", 0.0), ("width", 0), ("trunc", -1.0)])
+def test_create_rejects_bad_config_before_any_device_work(V, field, value):
+    cfg = V.vbh_config(voxel_size=0.01, trunc=0.04, max_weight=64, depth_scale=0.001, zmax=0,
+                       width=8, height=8, fx=4, fy=4, cx=4, cy=4, n_buckets=1024,
+                       slots_per_bucket=4, max_blocks=16, hash_fn=1, max_batch=0)
+    setattr(cfg, field, value)
+    with pytest.raises(V.VbhError) as e:
+        V.vbh_create(cfg, None)
+    assert e.value.status == V.VBH_ERR_INVALID_ARG
