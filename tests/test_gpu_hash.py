@@ -181,15 +181,16 @@ def test_voxel_block_map_pool_indices():
     assert ok.sum() == 100 and (sg == V.VBH_ST_CAPACITY).sum() == 20
     assert sorted(rg[ok].tolist()) == list(range(100))       # each pool entry once
     assert hm.counters().free_blocks == 0 and hm.counters().live == 100
-    # duplicates of one key share its pool index
-    dup = np.repeat(keys[:3], 4, axis=0)
+    # duplicates of one key share its pool index (which 100 keys won the pool is not fixed)
+    won, lost = keys[ok], keys[~ok]
+    dup = np.repeat(won[:3], 4, axis=0)
     rg2, sg2 = gpu_batch(hm, np.full(12, V.VBH_OP_INSERT, np.uint8), dup, None)
     assert np.all(sg2 == V.VBH_ST_EXISTS)
-    np.testing.assert_array_equal(rg2, np.repeat(rg[:3], 4))
+    np.testing.assert_array_equal(rg2, np.repeat(rg[ok][:3], 4))
     # erase returns entries to the pool; re-insert reuses them
-    rg3, sg3 = gpu_batch(hm, np.full(10, V.VBH_OP_ERASE, np.uint8), keys[:10], None)
+    rg3, sg3 = gpu_batch(hm, np.full(10, V.VBH_OP_ERASE, np.uint8), won[:10], None)
     assert np.all(sg3 == V.VBH_ST_ERASED) and hm.counters().free_blocks == 10
-    rg4, sg4 = gpu_batch(hm, ops[100:110], keys[100:110], None)
+    rg4, sg4 = gpu_batch(hm, np.full(10, V.VBH_OP_INSERT, np.uint8), lost[:10], None)
     assert np.all(sg4 == V.VBH_ST_INSERTED)
     assert sorted(rg4.tolist()) == sorted(rg3.tolist())
 
