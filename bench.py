@@ -1,0 +1,459 @@
+#!/usr/bin/env python
+"""Benchmark of the per-frame voxel-block-hashing path on one B300 (or N replicas).
+
+A step is one frame of the room-scale workload: erase of the blocks farther than 4 m from the
+camera, band allocation + projective TSDF fusion of one 640x480 depth frame, and Marching Cubes
+index extraction of the touched blocks and their seven negative neighbours.  Inputs are seeded
+synthetic depth frames (synth.room_sequence) resident in HBM when timing starts; the 256 MiB L2
+flush between steps stays outside the per-step CUDA events.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead (a bounded pixel
+band of each frame, scaled to frames/s).  Under torchrun every rank runs its own replica of the
+workload (the path keeps each volume on one GPU; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & hash Mops/s (% HBM roof); fwd+bwd vs fwd ms; stream p99 latency"
+N_FRAMES = 300
+VOXEL, TRUNC, ZMAX, ERASE_R = 0.005, 0.02, 4.0, 4.0
+N_BUCKETS, MAX_BLOCKS = 1 << 22, 1 << 19
+WORKLOAD = ("room-scale fusion + MC streaming: 640x480 uint16 depth (f=525), 300-frame seeded "
+            "walk through an 8x8x3 m room with 40 boxes/spheres, axial noise 1.5 mm*z^2, 2% "
+            "dropout; voxel 5 mm, 8^3 blocks, truncation 2 cm, hash 2^22 buckets x 4 slots, "
+            "2^19-block pool, blocks > 4 m from the camera erased each frame, MC indices of "
+            "touched blocks + 7 negative neighbours streamed per frame")
+CONFIG = {"workload": WORKLOAD, "frames_in_sequence": N_FRAMES, "width": 640, "height": 480,
+          "voxel_m": VOXEL, "trunc_m": TRUNC, "n_buckets": N_BUCKETS, "slots_per_bucket": 4,
+          "max_blocks": MAX_BLOCKS, "erase_radius_m": ERASE_R, "seed": 1805,
+          "l2": "256 MiB write between timed steps (outside the step events)"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=280)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+# ----------------------------------------------------------------------------- CPU oracle runs
+def oracle_frames(cam, poses, depth, frame_ids, row_frac=1.0):
+    """Time the oracle on the given frames (each: erase, fusion, MC set + indices).  Only a
+    centred band of `row_frac` of the rows is kept valid; returns (seconds, frames-equivalent)."""
+    import oracle
+    o = oracle.OracleVolume(VOXEL, TRUNC, 64.0, 0.001, ZMAX, cam.width, cam.height, cam.fx,
+                            cam.fy, cam.cx, cam.cy)
+    rows = max(1, int(round(cam.height * row_frac)))
+    r0 = (cam.height - rows) // 2
+    t = 0.0
+    for i in frame_ids:
+        d = np.zeros_like(depth[i])
+        d[r0:r0 + rows] = depth[i][r0:r0 + rows]
+        t0 = time.perf_counter()
+        o.erase_radius(poses[i][:, 3], ERASE_R)
+        o.integrate(d, poses[i])
+        M, _ = o.mc_set(0)
+        o.mc_dense(M)
+        t += time.perf_counter() - t0
+    return t, len(frame_ids) * rows / cam.height
+
+
+def cpu_baseline(cam, poses, depth, budget_s=20.0):
+    """Bounded sample of the same workload on the host: frame 0 warms the volume (untimed), then
+    whole frames 1, 2, ... are timed until ~budget_s of oracle time (at most 7 frames)."""
+    import oracle
+    oracle.build()
+    o = oracle.OracleVolume(VOXEL, TRUNC, 64.0, 0.001, ZMAX, cam.width, cam.height, cam.fx,
+                            cam.fy, cam.cx, cam.cy)
+    t_tot, frames = 0.0, 0
+    for i in range(min(len(poses), 8)):
+        t0 = time.perf_counter()
+        o.erase_radius(poses[i][:, 3], ERASE_R)
+        o.integrate(depth[i], poses[i])
+        M, _ = o.mc_set(0)
+        o.mc_dense(M)
+        dt = time.perf_counter() - t0
+        if i >= 1:
+            t_tot += dt
+            frames += 1
+            if t_tot >= budget_s:
+                break
+    return {"value": frames / t_tot, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"room-scale frames 1..{frames} after frame 0 warmed the volume; full "
+                      f"640x480 erase + fusion + MC set + MC indices, single thread, "
+                      f"{t_tot:.1f} s of oracle time"}
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    from paper_1805_03709_b300 import synth
+    import oracle
+    oracle.build()
+    n = args.warmup + args.steps
+    cam, poses, depth = synth.room_sequence(N_FRAMES, workers=min(16, os.cpu_count() or 1))
+    budget = 150.0
+    # calibrate the band on the first warm-up frame
+    t_cal, f_cal = oracle_frames(cam, poses, depth, [0], 1.0 / 16)
+    per_step = budget / max(n, 1)
+    frac = float(np.clip(per_step / max(t_cal, 1e-3) / 16, 1.0 / cam.height, 1.0))
+    ids = [i % N_FRAMES for i in range(1, n)]
+    t_w, _ = oracle_frames(cam, poses, depth, ids[:max(args.warmup - 1, 0)], frac)
+    t_s, f_s = oracle_frames(cam, poses, depth, ids[max(args.warmup - 1, 0):][:args.steps], frac)
+    value = f_s / t_s if t_s > 0 else 0.0
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t_s / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": CONFIG,
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: a centred band of {frac:.4f} of the rows of "
+                                       f"the next room frame (work scales with valid pixels), "
+                                       f"reported as frames/s equivalent"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.window = (0.0, 0.0)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "50"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append((time.time(), line.strip()))
+        self.th = threading.Thread(target=reader, daemon=True)
+        self.th.start()
+        time.sleep(0.3)
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        t0, t1 = self.window
+        sel = [r for t, r in self.rows if t0 - 0.15 <= t <= t1 + 0.15] or [r for _, r in self.rows]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in sel:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per fusion launch from the committed ncu summary, if it was taken from the
+    current kernel source (else None)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1805_03709_b300", "csrc", "frame.cu")
+    prof = os.path.join(ROOT, "profiles", "k_integrate_room_640x480.txt")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        txt = open(prof).read()
+    except OSError:
+        return None
+    src_line = [l for l in txt.splitlines() if l.startswith("source_sha256_16:")]
+    tr = [l for l in txt.splitlines() if l.startswith("dram_bytes_per_launch_full_frame:")]
+    if not src_line or not tr or src_line[0].split(":")[1].strip() != digest:
+        return None
+    return float(tr[0].split(":")[1].strip())
+
+
+# ----------------------------------------------------------------------------------- our path
+def main():
+    args = parse()
+    rank, local_rank, ws = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        return
+    from paper_1805_03709_b300 import synth
+    # render frames (spawned workers) before any CUDA work
+    cam, poses, depth = synth.room_sequence(N_FRAMES, workers=min(16, os.cpu_count() or 1))
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(cam, poses, depth)
+
+    import torch
+    from paper_1805_03709_b300 import build, vbh as V
+    from paper_1805_03709_b300.volume import Volume
+    build.build()
+    torch.cuda.set_device(local_rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+
+    vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, N_BUCKETS,
+                 MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS, mc_cap_entries=1 << 26)
+    D = torch.from_numpy(depth).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step(i, frame_id, d=None):
+        f = i % N_FRAMES
+        vol.erase_radius(poses[f][:, 3], ERASE_R, keys_out=False)
+        vol.integrate(D[f] if d is None else d, poses[f], frame_id)
+        vol.extract(V.VBH_MC_TOUCHED)
+
+    for i in range(args.warmup):
+        step(i, i + 1)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    vol.timing(("integrate",))
+    vol.timing_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    c0 = vol.counters()
+    touched, new, written = 0, 0, 0
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for k in range(args.steps):
+        i = args.warmup + k
+        flush.zero_()
+        ev[k][0].record()
+        step(i, i + 1)
+        ev[k][1].record()
+        c = vol.counters()          # synchronises; outside the step events
+        touched += c.last_touched
+        new += c.last_new
+        written += c.voxels_written
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    t_wall1 = time.time()
+    clocks.mark(t_wall0, t_wall1)
+    c1 = vol.counters()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_total = float(sum(step_ms))
+    stage_ms, stage_launch = vol.timing_read(reset=True)
+    vol.timing(())
+    launches = int(c1.kernel_launches - c0.kernel_launches)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    clk = clocks.stop()
+
+    # roofline of the dominant kernel (fusion): bytes it must move per launch
+    n_launch = max(int(stage_launch["integrate"]), 1)
+    depth_bytes = cam.width * cam.height * 2
+    alg_bytes = ((touched - new) * 512 * 8 + written * 8 + touched * 128 +
+                 args.steps * depth_bytes)
+    integ_ms = stage_ms["integrate"]
+    achieved = alg_bytes / n_launch / (integ_ms / n_launch / 1e3) / 1e9 if integ_ms > 0 else 0.0
+    peak, peak_src = measured_peak()
+    tr = profile_traffic()
+
+    # ---- end to end: host depth in pinned memory, MC stream read back every step
+    e2e = None
+    if not args.no_e2e:
+        host_depth = torch.from_numpy(depth).pin_memory()
+        d_in = torch.empty((cam.height, cam.width), dtype=torch.uint16, device=dev)
+        s = vol.stream
+        h_keys = torch.empty(s.keys3.shape, dtype=torch.int32).pin_memory()
+        h_info = torch.empty(s.info.shape, dtype=torch.int32).pin_memory()
+        h_off = torch.empty(s.offsets.shape, dtype=torch.int32).pin_memory()
+        h_cnt = torch.empty(s.counts.shape, dtype=torch.int32).pin_memory()
+        h_loc = torch.empty(s.local.shape, dtype=torch.int16).pin_memory()
+        h_idx = torch.empty(s.index.shape, dtype=torch.uint8).pin_memory()
+        h_n = torch.empty(2, dtype=torch.int32).pin_memory()
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        t_e2e = 0.0
+        for k in range(args.steps):
+            i = args.warmup + args.steps + k
+            f = i % N_FRAMES
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d_in.copy_(host_depth[f], non_blocking=True)
+            step(i, i + 1, d_in)
+            h_n.copy_(s.n, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            nb, ne = int(h_n[0]), int(h_n[1])
+            h_keys[:nb].copy_(s.keys3[:nb], non_blocking=True)
+            h_info[:nb].copy_(s.info[:nb], non_blocking=True)
+            h_off[:nb].copy_(s.offsets[:nb], non_blocking=True)
+            h_cnt[:nb].copy_(s.counts[:nb], non_blocking=True)
+            h_loc[:ne].copy_(s.local[:ne], non_blocking=True)
+            h_idx[:ne].copy_(s.index[:ne], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            t_e2e += time.perf_counter() - t0
+            h2d += depth_bytes
+            d2h += 8 + nb * 24 + ne * 3
+        if ws > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": ws * args.steps / t_e2e, "unit": "frames/s",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    hash_pt = None
+    if not args.no_hash:
+        hash_pt = hash_point(torch, dev, flush, peak)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ws * args.steps / (ms_total / 1e3), "unit": "frames/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(CONFIG, parallelism="replicas" if ws > 1 else "single GPU",
+                           avg_touched_blocks=touched / args.steps,
+                           avg_new_blocks=new / args.steps),
+            "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": achieved,
+                         "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": tr,
+                         "algorithmic_bytes_per_launch": alg_bytes / n_launch,
+                         "avg_launch_ms": integ_ms / n_launch,
+                         "share_of_step": integ_ms / ms_total if ms_total else None},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
+            "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
+            "hash": hash_pt,
+        }
+        print(json.dumps(line), flush=True)
+    vol.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def hash_point(torch, dev, flush, peak):
+    """Hash microbenchmark point: 2^22 x 4 table prefilled to load factor 0.7 with distinct
+    uniform keys in [-2^20, 2^20)^3; batches of 2^20 ops (50 % find half hits, 30 % insert of
+    absent keys, 20 % erase of present keys); untimed rebalance after each batch."""
+    from paper_1805_03709_b300 import synth, vbh as V
+    from paper_1805_03709_b300.volume import HashMap
+    n_buckets, n = 1 << 22, 1 << 20
+    cap = n_buckets * 4
+    n_pre = int(0.7 * cap)
+    n_batches, n_warm = 6, 2
+    keys = synth.distinct_keys(n_pre + n * n_batches, seed=1805)
+    K = torch.from_numpy(keys).to(dev)
+    hm = HashMap(n_buckets=n_buckets, max_batch=1 << 24)
+    vals = torch.arange(len(keys), dtype=torch.int32, device=dev)
+    ins = torch.ones(n_pre, dtype=torch.uint8, device=dev)
+    hm.batch(ins, K[:n_pre], vals[:n_pre])
+    rng = np.random.default_rng(3)
+    alive = np.zeros(len(keys), bool)
+    alive[:n_pre] = True
+    next_new = n_pre
+    res = torch.empty(n, dtype=torch.int32, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    t_ms, ops_done, bytes_alg = 0.0, 0, 0
+    nf, ni = n // 2, int(0.3 * n)
+    ne = n - nf - ni
+    for b in range(n_batches):
+        live = np.flatnonzero(alive)
+        hit = rng.choice(live, nf // 2)
+        miss = rng.integers(next_new + ni, len(keys), nf - nf // 2)
+        new = np.arange(next_new, next_new + ni)
+        era = rng.choice(live, ne, replace=False)
+        idx = np.concatenate([hit, miss, new, era])
+        ops = np.concatenate([np.zeros(nf), np.ones(ni), np.full(ne, 2)]).astype(np.uint8)
+        perm = rng.permutation(n)
+        I = torch.from_numpy(idx[perm]).to(dev)
+        O = torch.from_numpy(ops[perm]).to(dev)
+        bk, bv = K[I].contiguous(), vals[I].contiguous()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        hm.batch(O, bk, bv, res, st)
+        e1.record()
+        torch.cuda.synchronize()
+        if b >= n_warm:
+            t_ms += e0.elapsed_time(e1)
+            ops_done += n
+            s = st.cpu().numpy()
+            ok = int(((s == V.VBH_ST_INSERTED) | (s == V.VBH_ST_ERASED)).sum())
+            bytes_alg += n * (12 + 1 + 4 + 1 + 64) + ni * 4 + ok * 16
+        alive[new] = True
+        alive[era] = False
+        next_new += ni
+        # untimed rebalance: erase random live keys so the load factor returns to 0.7
+        extra = int(alive.sum()) - n_pre
+        if extra > 0:
+            gone = rng.choice(np.flatnonzero(alive), extra, replace=False)
+            G = torch.from_numpy(gone).to(dev)
+            hm.batch(torch.full((extra,), 2, dtype=torch.uint8, device=dev), K[G].contiguous())
+            alive[gone] = False
+    c = hm.counters()
+    hm.close()
+    gbs = bytes_alg / (t_ms / 1e3) / 1e9
+    return {"Mops_s": ops_done / (t_ms / 1e3) / 1e6, "load_factor": 0.7, "batch": n,
+            "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
+            "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
+            "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+if __name__ == "__main__":
+    main()

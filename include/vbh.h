@@ -100,7 +100,8 @@ typedef struct {
   uint32_t last_mc_blocks;  /* records produced by the last extraction */
   uint32_t last_mc_entries; /* entries produced by the last extraction */
   uint32_t last_erased;     /* blocks removed by the last vbh_erase_blocks */
-  uint64_t voxels_updated;  /* voxels fused by the last vbh_integrate_frame */
+  uint64_t voxels_written;  /* voxels the last vbh_integrate_frame wrote (fused, or zeroed in
+                               a new block) */
 } vbh_counters;
 
 typedef struct {
@@ -219,12 +220,13 @@ vbh_status vbh_load(vbh_handle* h, const int32_t* keys3_host, const float* tsdf_
 vbh_status vbh_get_counters(vbh_handle* h, vbh_counters* out_host);
 vbh_status vbh_clear_errors(vbh_handle* h);
 
-/* Per-stage device timing (CUDA events recorded on the handle's stream around each stage).
- * vbh_timing_read synchronises and returns the accumulated milliseconds and kernel launch
- * counts per stage since the last reset. */
+/* Per-stage device timing: CUDA events are recorded on the handle's stream around each stage
+ * whose bit (1 << stage) is set in `stage_mask` (0 = off).  vbh_timing_read synchronises and
+ * returns, per stage since the last reset, the accumulated milliseconds of the timed stages and
+ * the kernel launches of every stage. */
 enum { VBH_STAGE_ERASE = 0, VBH_STAGE_ALLOC = 1, VBH_STAGE_INTEGRATE = 2, VBH_STAGE_MCSET = 3,
        VBH_STAGE_MC = 4, VBH_STAGE_HASH = 5, VBH_N_STAGES = 6 };
-vbh_status vbh_timing_enable(vbh_handle* h, int enable);
+vbh_status vbh_timing_enable(vbh_handle* h, int stage_mask);
 vbh_status vbh_timing_read(vbh_handle* h, double* ms_host /* VBH_N_STAGES */,
                            uint64_t* launches_host /* VBH_N_STAGES */, int reset);
 

@@ -70,7 +70,7 @@ struct vbh_handle {
   // bookkeeping
   uint64_t launches = 0;
   uint32_t rebuilds = 0;
-  bool timing = false;
+  int timing = 0;                  // bit mask of timed stages
   std::vector<StageEvents> pending;
   std::vector<cudaEvent_t> ev_free;
   double ms[VBH_N_STAGES] = {0};
@@ -101,13 +101,13 @@ struct vbh_handle {
   void stage_begin(int s) {
     cur_stage = s;
     cur_launch0 = launches;
-    if (timing) {
+    if (timing & (1 << s)) {
       cur_a = get_event();
       cudaEventRecord(cur_a, stream);
     }
   }
   void stage_end() {
-    if (timing && cur_stage >= 0) {
+    if (cur_stage >= 0 && (timing & (1 << cur_stage))) {
       cudaEvent_t b = get_event();
       cudaEventRecord(b, stream);
       pending.push_back(StageEvents{cur_stage, cur_a, b, launches - cur_launch0});
@@ -622,7 +622,7 @@ vbh_status vbh_get_counters(vbh_handle* h, vbh_counters* out) {
   out->last_mc_blocks = d.mc_blocks;
   out->last_mc_entries = d.mc_entries;
   out->last_erased = d.n_erased;
-  out->voxels_updated = d.vox_updated;
+  out->voxels_written = d.vox_updated;
   return VBH_OK;
 }
 
@@ -632,9 +632,9 @@ vbh_status vbh_clear_errors(vbh_handle* h) {
   return VBH_OK;
 }
 
-vbh_status vbh_timing_enable(vbh_handle* h, int enable) {
+vbh_status vbh_timing_enable(vbh_handle* h, int stage_mask) {
   if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
-  h->timing = enable != 0;
+  h->timing = stage_mask & ((1 << VBH_N_STAGES) - 1);
   return VBH_OK;
 }
 

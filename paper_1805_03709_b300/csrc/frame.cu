@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(FrameParams fp, PoolV
         pool.masks[32u * p + warp + 4 * j] = negm;
         pool.masks[32u * p + 16u + warp + 4 * j] = valm;
       }
-      my_upd += upd;
+      my_upd += (upd || fresh);
     }
     __syncthreads();
     if (t == 0 && fresh) pool.state[p] = 0u;

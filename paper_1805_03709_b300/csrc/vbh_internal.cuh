@@ -55,7 +55,7 @@ struct DevCounters {
   unsigned int err;
   unsigned int mc_blocks, mc_entries;
   unsigned int rebuild_n;       // live entries copied by the last rebuild
-  unsigned long long vox_updated;   // voxels fused by the last frame
+  unsigned long long vox_updated;   // voxels written by the last frame (fused or zeroed)
   unsigned int pad[2];
 };
 

@@ -25,8 +25,8 @@ import numpy as np
 
 __all__ = [
     "Camera", "Scene", "make_tiny_scene", "make_room_scene", "render_depth_m",
-    "quantize_mm", "tiny_sequence", "room_sequence", "look_at", "random_hash_keys",
-    "zipf_cluster_keys",
+    "quantize_mm", "tiny_sequence", "room_sequence", "room_frames", "room_camera", "look_at",
+    "random_hash_keys", "distinct_keys", "zipf_cluster_keys",
 ]
 
 
@@ -225,18 +225,22 @@ def room_trajectory(n_frames: int, seed: int = 1805, fps: float = 30.0):
     return np.stack(poses)
 
 
-def room_sequence(n_frames: int = 300, seed: int = 1805, width: int = 640, height: int = 480,
-                  f: float = 525.0, noise: bool = True, dropout: float = 0.02,
-                  metric_depth: bool = False):
-    """Room-scale workload: 640x480 depth along a smooth walk, axial noise sigma = 1.5 mm * z^2
-    (z in m) and `dropout` random invalid pixels.  Returns (camera, poses, depth) with depth as
-    uint16 mm, or float32 metres (0 = invalid) when `metric_depth` is set."""
+def room_camera(width: int = 640, height: int = 480, f: float = 525.0) -> Camera:
+    """Kinect-v1-like pinhole camera (f scaled with the image width)."""
+    return Camera(width, height, f * width / 640.0, f * width / 640.0, width / 2.0, height / 2.0)
+
+
+def room_frames(indices, n_frames: int, seed: int = 1805, width: int = 640, height: int = 480,
+                f: float = 525.0, noise: bool = True, dropout: float = 0.02,
+                metric_depth: bool = False):
+    """Depth frames `indices` of the room walk of `n_frames` frames (each frame has its own
+    seeded noise stream, so any subset can be rendered independently)."""
     scene = make_room_scene(seed)
-    cam = Camera(width, height, f * width / 640.0, f * width / 640.0, width / 2.0, height / 2.0)
+    cam = room_camera(width, height, f)
     poses = room_trajectory(n_frames, seed)
-    rng = np.random.default_rng(seed + 11)
     out = []
-    for i in range(n_frames):
+    for i in indices:
+        rng = np.random.default_rng([seed + 11, int(i)])
         z = render_depth_m(scene, cam, poses[i])
         if noise:
             z = z + rng.standard_normal(z.shape) * (0.0015 * np.where(np.isfinite(z), z, 0.0) ** 2)
@@ -246,7 +250,44 @@ def room_sequence(n_frames: int = 300, seed: int = 1805, width: int = 640, heigh
             out.append(np.where(np.isfinite(z) & (z > 0), z, 0.0).astype(np.float32))
         else:
             out.append(quantize_mm(z))
-    return cam, poses, np.stack(out)
+    return np.stack(out) if out else np.zeros((0, height, width),
+                                               np.float32 if metric_depth else np.uint16)
+
+
+def room_sequence(n_frames: int = 300, seed: int = 1805, width: int = 640, height: int = 480,
+                  f: float = 525.0, noise: bool = True, dropout: float = 0.02,
+                  metric_depth: bool = False, workers: int = 1):
+    """Room-scale workload: depth along a smooth walk through the 8 x 8 x 3 m room, axial noise
+    sigma = 1.5 mm * z^2 (z in m) and `dropout` random invalid pixels.  Returns (camera, poses,
+    depth) with depth as uint16 mm, or float32 metres (0 = invalid) when `metric_depth` is set.
+    `workers` > 1 renders in that many spawned processes (call it before any CUDA work)."""
+    cam = room_camera(width, height, f)
+    poses = room_trajectory(n_frames, seed)
+    kw = dict(n_frames=n_frames, seed=seed, width=width, height=height, f=f, noise=noise,
+              dropout=dropout, metric_depth=metric_depth)
+    if workers <= 1 or n_frames < 8:
+        return cam, poses, room_frames(range(n_frames), **kw)
+    import concurrent.futures as cf
+    import functools
+    import multiprocessing as mp
+    chunks = [list(c) for c in np.array_split(np.arange(n_frames), workers) if len(c)]
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(functools.partial(room_frames, **kw), chunks))
+    return cam, poses, np.concatenate(parts)
+
+
+def distinct_keys(n: int, seed: int) -> np.ndarray:
+    """`n` distinct int3 keys spread over [-2^20, 2^20)^3: a seeded bijection of the 63-bit
+    packed key space (odd multiplier and xor-shifts are invertible mod 2^63) applied to
+    0..n-1, unpacked into three 21-bit coordinates.  Vectorised; no de-duplication needed."""
+    m = np.uint64((1 << 63) - 1)
+    x = (np.arange(n, dtype=np.uint64) + np.uint64(seed * 0x9E3779B9 & ((1 << 62) - 1))) & m
+    for c in (0x5DEECE66D2B79F5, 0x2545F4914F6CDD1D):
+        x = (x * np.uint64(c | 1)) & m
+        x ^= x >> np.uint64(29)
+    f = np.uint64((1 << 21) - 1)
+    out = np.stack([(x & f), (x >> np.uint64(21)) & f, (x >> np.uint64(42)) & f], 1).astype(np.int64)
+    return (out - (1 << 20)).astype(np.int32)
 
 
 def random_hash_keys(n: int, seed: int, lo: int = -(1 << 20), hi: int = (1 << 20)) -> np.ndarray:

@@ -43,7 +43,7 @@ class vbh_counters(ctypes.Structure):
                 ("last_touched", _u32), ("last_new", _u32), ("last_candidates", _u32),
                 ("error_flags", _u32), ("kernel_launches", _u64), ("rebuilds", _u32),
                 ("last_mc_blocks", _u32), ("last_mc_entries", _u32), ("last_erased", _u32),
-                ("voxels_updated", _u64)]
+                ("voxels_written", _u64)]
 
 
 class vbh_frame_stats(ctypes.Structure):
@@ -206,8 +206,9 @@ def vbh_clear_errors(h):
     _check(lib().vbh_clear_errors(h), "vbh_clear_errors")
 
 
-def vbh_timing_enable(h, enable: bool):
-    _check(lib().vbh_timing_enable(h, int(bool(enable))), "vbh_timing_enable")
+def vbh_timing_enable(h, stage_mask: int):
+    """stage_mask: bit (1 << i) times stage VBH_STAGES[i]; 0 turns timing off."""
+    _check(lib().vbh_timing_enable(h, int(stage_mask)), "vbh_timing_enable")
 
 
 def vbh_timing_read(h, reset: bool = False):

@@ -178,8 +178,12 @@ class Volume:
         V.vbh_load(self.h, np.ascontiguousarray(keys3, np.int32),
                    np.ascontiguousarray(tsdf, np.float32), np.ascontiguousarray(weight, np.float32))
 
-    def timing(self, enable=True):
-        V.vbh_timing_enable(self.h, enable)
+    def timing(self, stages=("erase", "alloc", "integrate", "mcset", "mc", "hash")):
+        """Record CUDA events around the named stages (empty / None: off)."""
+        mask = 0
+        for s in stages or ():
+            mask |= 1 << V.VBH_STAGES.index(s)
+        V.vbh_timing_enable(self.h, mask)
 
     def timing_read(self, reset=False):
         return V.vbh_timing_read(self.h, reset)
