@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small-memory", action="store_true",
+                    help="profiling case: 32-frame sequence, 2^20-bucket table, 2^17-block pool "
+                         "(same per-frame work, ~1 GB on the device)")
     return ap.parse_args()
 
 
@@ -60,12 +63,16 @@ def dist_info():
 
 
 # ----------------------------------------------------------------------------- CPU oracle runs
-def oracle_frames(cam, poses, depth, frame_ids, row_frac=1.0):
-    """Time the oracle on the given frames (each: erase, fusion, MC set + indices).  Only a
-    centred band of `row_frac` of the rows is kept valid; returns (seconds, frames-equivalent)."""
+def oracle_volume(cam):
     import oracle
-    o = oracle.OracleVolume(VOXEL, TRUNC, 64.0, 0.001, ZMAX, cam.width, cam.height, cam.fx,
-                            cam.fy, cam.cx, cam.cy)
+    return oracle.OracleVolume(VOXEL, TRUNC, 64.0, 0.001, ZMAX, cam.width, cam.height, cam.fx,
+                               cam.fy, cam.cx, cam.cy)
+
+
+def oracle_frames(o, cam, poses, depth, frame_ids, row_frac=1.0):
+    """Time the oracle volume `o` on the given frames (each: erase, fusion, MC set + indices).
+    Only a centred band of `row_frac` of the rows is kept valid; returns (seconds,
+    frames-equivalent)."""
     rows = max(1, int(round(cam.height * row_frac)))
     r0 = (cam.height - rows) // 2
     t = 0.0
@@ -86,8 +93,7 @@ def cpu_baseline(cam, poses, depth, budget_s=20.0):
     whole frames 1, 2, ... are timed until ~budget_s of oracle time (at most 7 frames)."""
     import oracle
     oracle.build()
-    o = oracle.OracleVolume(VOXEL, TRUNC, 64.0, 0.001, ZMAX, cam.width, cam.height, cam.fx,
-                            cam.fy, cam.cx, cam.cy)
+    o = oracle_volume(cam)
     t_tot, frames = 0.0, 0
     for i in range(min(len(poses), 8)):
         t0 = time.perf_counter()
@@ -116,13 +122,14 @@ def run_reference(args, rank, ws):
     n = args.warmup + args.steps
     cam, poses, depth = synth.room_sequence(N_FRAMES, workers=min(16, os.cpu_count() or 1))
     budget = 150.0
+    o = oracle_volume(cam)
     # calibrate the band on the first warm-up frame
-    t_cal, f_cal = oracle_frames(cam, poses, depth, [0], 1.0 / 16)
+    t_cal, f_cal = oracle_frames(o, cam, poses, depth, [0], 1.0 / 16)
     per_step = budget / max(n, 1)
     frac = float(np.clip(per_step / max(t_cal, 1e-3) / 16, 1.0 / cam.height, 1.0))
     ids = [i % N_FRAMES for i in range(1, n)]
-    t_w, _ = oracle_frames(cam, poses, depth, ids[:max(args.warmup - 1, 0)], frac)
-    t_s, f_s = oracle_frames(cam, poses, depth, ids[max(args.warmup - 1, 0):][:args.steps], frac)
+    t_w, _ = oracle_frames(o, cam, poses, depth, ids[:max(args.warmup - 1, 0)], frac)
+    t_s, f_s = oracle_frames(o, cam, poses, depth, ids[max(args.warmup - 1, 0):][:args.steps], frac)
     value = f_s / t_s if t_s > 0 else 0.0
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -226,6 +233,12 @@ def profile_traffic():
 def main():
     args = parse()
     rank, local_rank, ws = dist_info()
+    if args.small_memory:
+        global N_FRAMES, N_BUCKETS, MAX_BLOCKS
+        N_FRAMES, N_BUCKETS, MAX_BLOCKS = 32, 1 << 20, 1 << 17
+        CONFIG.update(frames_in_sequence=N_FRAMES, n_buckets=N_BUCKETS, max_blocks=MAX_BLOCKS,
+                      workload=WORKLOAD + " [small-memory profiling case: 32 frames, 2^20 "
+                      "buckets, 2^17 blocks]")
     if args.impl == "reference":
         run_reference(args, rank, ws)
         return
@@ -247,7 +260,7 @@ def main():
     dev = torch.device("cuda", local_rank)
 
     vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, N_BUCKETS,
-                 MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS, mc_cap_entries=1 << 26)
+                 MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS, mc_cap_entries=MAX_BLOCKS * 64)
     D = torch.from_numpy(depth).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
