@@ -14,13 +14,46 @@
 //             valid iff 0 <= u < width and 0 <= v < height (compared as floats)
 //   band      fl(d - p_z) >= -mu
 // Values (the SDF fed into the running average) are computed more accurately than binary32:
-// the block's camera depth offset is formed in FP64 once per warp and split into two floats,
-// so the per-voxel SDF error stays near 1e-8 m.
+// the camera depth of each block's origin is formed as an unevaluated sum of two floats with
+// error-free transformations (TwoSum, Knuth; TwoProduct via FMA, Ogita, Rump and Oishi 2005),
+// so the per-voxel SDF error stays near 1e-8 m without any FP64 instruction.
 #include "vbh_internal.cuh"
 
 namespace vbh {
 
 namespace {
+
+// s + e == a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+// p + e == a * b exactly (TwoProduct with a fused multiply-add)
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return make_float2(p, __fmaf_rn(a, b, -p));
+}
+
+// Camera depth of the block origin, sum_i R_i2 (8 k_i s - t_i), as hi + lo floats.
+__device__ __forceinline__ float2 block_depth(const FrameParams& fp, int3 k) {
+  const int kk[3] = {k.x, k.y, k.z};
+  float hi = 0.f, lo = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float2 P = two_prod((float)(8 * kk[i]), fp.s);     // 8 k s, exact
+    const float2 S = two_sum(P.x, -fp.t[i]);                 // (8 k s)_hi - t, exact
+    const float al = __fadd_rn(S.y, P.y);                    // a = S.x + al
+    const float r = fp.R[3 * i + 2];
+    const float2 Q = two_prod(r, S.x);
+    const float ql = __fmaf_rn(r, al, Q.y);
+    const float2 T = two_sum(hi, Q.x);
+    hi = T.x;
+    lo = __fadd_rn(lo, __fadd_rn(T.y, ql));
+  }
+  return two_sum(hi, lo);
+}
 
 constexpr int kTile = 16;            // 16 x 16 pixel tiles, one thread per pixel
 constexpr int kTileThreads = kTile * kTile;
@@ -137,18 +170,9 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(FrameParams fp, PoolV
     float2 v[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) v[j] = fresh ? make_float2(0.f, 0.f) : vox[t + 128 * j];
-    // camera depth of the block origin, FP64, split into hi + lo
-    float bhi = 0.f, blo = 0.f;
-    if (lane == 0) {
-      const double s = fp.s;
-      const double B = (double)fp.R[2] * ((double)(8 * k.x) * s - (double)fp.t[0]) +
-                       (double)fp.R[5] * ((double)(8 * k.y) * s - (double)fp.t[1]) +
-                       (double)fp.R[8] * ((double)(8 * k.z) * s - (double)fp.t[2]);
-      bhi = __double2float_rn(B);
-      blo = __double2float_rn(B - (double)bhi);
-    }
-    bhi = __shfl_sync(0xFFFFFFFFu, bhi, 0);
-    blo = __shfl_sync(0xFFFFFFFFu, blo, 0);
+    // camera depth of the block origin (every lane computes the same value; no divergence)
+    const float2 bd = block_depth(fp, k);
+    const float bhi = bd.x, blo = bd.y;
     const float gx = (float)(8 * k.x + lx), gy = (float)(8 * k.y + ly);
     const float dX = __fmaf_rn(gx, fp.s, -fp.t[0]);
     const float dY = __fmaf_rn(gy, fp.s, -fp.t[1]);
