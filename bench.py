@@ -211,22 +211,23 @@ def measured_peak():
         return 6400.0, "fallback"
 
 
-def profile_traffic():
-    """DRAM bytes per fusion launch from the committed ncu summary, if it was taken from the
-    current kernel source (else None)."""
+def profile_traffic(avg_touched):
+    """DRAM bytes per fusion launch: the committed ncu summary's bytes per touched block (taken
+    on the small-memory case of the same frames) scaled by this run's average touched blocks,
+    if the summary was taken from the current kernel source (else None)."""
     import hashlib
     src = os.path.join(ROOT, "paper_1805_03709_b300", "csrc", "frame.cu")
     prof = os.path.join(ROOT, "profiles", "k_integrate_room_640x480.txt")
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        txt = open(prof).read()
+        lines = open(prof).read().splitlines()
     except OSError:
         return None
-    src_line = [l for l in txt.splitlines() if l.startswith("source_sha256_16:")]
-    tr = [l for l in txt.splitlines() if l.startswith("dram_bytes_per_launch_full_frame:")]
-    if not src_line or not tr or src_line[0].split(":")[1].strip() != digest:
+    src_line = [l for l in lines if l.startswith("source_sha256_16:")]
+    per_block = [l for l in lines if l.startswith("dram_bytes_per_touched_block:")]
+    if not src_line or not per_block or src_line[0].split(":")[1].strip() != digest:
         return None
-    return float(tr[0].split(":")[1].strip())
+    return float(per_block[0].split(":")[1].strip()) * avg_touched
 
 
 # ----------------------------------------------------------------------------------- our path
@@ -325,7 +326,7 @@ def main():
     integ_ms = stage_ms["integrate"]
     achieved = alg_bytes / n_launch / (integ_ms / n_launch / 1e3) / 1e9 if integ_ms > 0 else 0.0
     peak, peak_src = measured_peak()
-    tr = profile_traffic()
+    tr = profile_traffic(touched / max(args.steps, 1))
 
     # ---- end to end: host depth in pinned memory, MC stream read back every step
     e2e = None
