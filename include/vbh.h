@@ -230,6 +230,29 @@ vbh_status vbh_timing_enable(vbh_handle* h, int stage_mask);
 vbh_status vbh_timing_read(vbh_handle* h, double* ms_host /* VBH_N_STAGES */,
                            uint64_t* launches_host /* VBH_N_STAGES */, int reset);
 
+/* Marching Cubes indices of a caller's TSDF blocks, allocating nothing.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc -- code that runs inside another
+ * framework's memory pool, real-time threads that must not risk an allocation's device-wide
+ * synchronisation, hosts that reserve all memory at start-up -- and therefore cannot create a
+ * vbh_handle.  It computes, for every input block, the stream record that
+ * vbh_extract_mc_indices(VBH_MC_ALL) would produce for a volume holding exactly these blocks
+ * (same corner order, S^c rule and compaction; info = 0), on `cuda_stream`.
+ *   keys3_dev: n_blocks distinct block coordinates in [-2^20, 2^20); tsdf_dev, weight_dev:
+ *   n_blocks * 512 floats each (voxel lx + 8 ly + 64 lz); out: as for vbh_extract_mc_indices;
+ *   error_flags_dev (may be NULL): one uint32 that receives bit0 = a key out of range, bit1 = a
+ *   repeated key.  All pointers are caller-owned device memory.
+ * Scratch: a fixed 8 MiB + 256 B array in the library's device memory (every GPU that loads
+ * the library holds it until exit); n_blocks is limited to 32768 and larger sizes return
+ * VBH_ERR_INVALID_ARG without touching the device.  The call issues only memsets, kernels and a
+ * device-to-device copy; it never calls cudaMalloc or cudaFree.  The first call on a device
+ * looks up the array's device address on that device (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call reuses the same array,
+ * so calls whose work overlaps on the GPU race: serialise them. */
+vbh_status vbh_mc_from_tsdf_static(const int32_t* keys3_dev, const float* tsdf_dev,
+                                   const float* weight_dev, uint32_t n_blocks,
+                                   const vbh_mc_stream* out, void* cuda_stream,
+                                   uint32_t* error_flags_dev);
+
 /* Host-side helpers (no device work). */
 int vbh_abi_version(void);
 const char* vbh_last_error(void);

@@ -86,6 +86,8 @@ SYMBOLS = [
     ("vbh_clear_errors", ctypes.c_int, [_p]),
     ("vbh_timing_enable", ctypes.c_int, [_p, ctypes.c_int]),
     ("vbh_timing_read", ctypes.c_int, [_p, _p, _p, ctypes.c_int]),
+    ("vbh_mc_from_tsdf_static", ctypes.c_int,
+     [_p, _p, _p, _u32, ctypes.POINTER(vbh_mc_stream), _p, _p]),
 ]
 
 _lib = None
@@ -216,3 +218,12 @@ def vbh_timing_read(h, reset: bool = False):
     n = np.zeros(len(VBH_STAGES), np.uint64)
     _check(lib().vbh_timing_read(h, ms.ctypes.data, n.ctypes.data, int(reset)), "vbh_timing_read")
     return dict(zip(VBH_STAGES, ms.tolist())), dict(zip(VBH_STAGES, n.tolist()))
+
+
+def vbh_mc_from_tsdf_static(keys3, tsdf, weight, out: vbh_mc_stream, stream=None,
+                            error_flags=None):
+    """MC stream of caller-owned TSDF blocks using only the library's fixed scratch array (no
+    device allocation inside the call; at most 32768 blocks)."""
+    _check(lib().vbh_mc_from_tsdf_static(_ptr(keys3), _ptr(tsdf), _ptr(weight),
+                                         int(keys3.shape[0]), ctypes.byref(out), stream,
+                                         _ptr(error_flags)), "vbh_mc_from_tsdf_static")
