@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clock-ms", type=int, default=200,
+                    help="nvidia-smi sampling interval during the timed region (0 = off)")
     ap.add_argument("--small-memory", action="store_true",
                     help="profiling case: 32-frame sequence, 2^20-bucket table, 2^17-block pool "
                          "(same per-frame work, ~1 GB on the device)")
@@ -151,17 +153,20 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 200):
         self.gpu = gpu_index
+        self.interval = interval_ms
         self.rows = []
         self.proc = None
         self.window = (0.0, 0.0)
 
     def start(self):
+        if self.interval <= 0:
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "50"], stdout=subprocess.PIPE,
+                 "-i", str(self.gpu), "-lms", str(self.interval)], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -178,7 +183,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None,
+                    "reasons": ["not sampled" if self.interval <= 0 else "nvidia-smi unavailable"]}
         time.sleep(0.2)
         self.proc.terminate()
         self.proc.wait(timeout=5)
@@ -283,7 +289,7 @@ def main():
     vol.timing_read(reset=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(local_rank, args.clock_ms)
     clocks.start()
     c0 = vol.counters()
     touched, new, written = 0, 0, 0
