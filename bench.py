@@ -274,11 +274,10 @@ def main():
     torch.cuda.synchronize()
 
     def step(i, frame_id, d=None):
+        # erase beyond 4 m, fuse, extract the touched MC blocks: one CUDA-graph launch
         vol = state["vol"]
         f = i % N_FRAMES
-        vol.erase_radius(poses[f][:, 3], ERASE_R, keys_out=False)
-        vol.integrate(D[f] if d is None else d, poses[f], frame_id)
-        vol.extract(V.VBH_MC_TOUCHED)
+        vol.process_frame(D[f] if d is None else d, poses[f], frame_id, ERASE_R)
 
     for i in range(args.warmup):
         step(i, i + 1)

@@ -207,6 +207,17 @@ typedef struct {
 vbh_status vbh_extract_mc_indices(vbh_handle* h, const vbh_mc_selector* sel_host,
                                   const vbh_mc_stream* out, uint64_t* needed_bytes_host);
 
+/* One whole frame in one call: vbh_erase_blocks(RADIUS, camera position, erase_radius) (skipped
+ * when erase_radius == 0), vbh_integrate_frame(depth, T_wc, frame_id) and
+ * vbh_extract_mc_indices(VBH_MC_TOUCHED, out) -- the reconstruction client's per-frame update
+ * and the server's MC conversion of Sec. 4.1-4.2 -- with the same results as those three calls.
+ * The first call captures the frame's kernels as a CUDA graph on a private stream; every call
+ * then updates the graph's per-frame inputs and launches it on the handle's stream, so a frame
+ * costs two driver calls on the host.  Arguments as for the three calls; the erased keys are not
+ * reported individually (the stream's removal records carry them).  Asynchronous. */
+vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const float* T_wc_host,
+                             uint32_t frame_id, float erase_radius, const vbh_mc_stream* out);
+
 /* Host copies of the live blocks (test and checkpoint path; synchronises).  keys3_host: cap
  * keys; tsdf_host, weight_host: cap*512 floats each (may be NULL); vals_host: cap uint32 (the
  * value of each key: pool index or the plain map's value; may be NULL); *n_host = live keys

@@ -67,6 +67,17 @@ struct vbh_handle {
   unsigned int epoch = 0;
   unsigned int frame_version = 0;
   bool have_frame = false;
+  FrameCtl* ctl = nullptr;         // device-resident per-call control block
+  unsigned int* last_entries = nullptr;   // n_entries_dev of the last extraction
+  // whole-frame CUDA graph (vbh_process_frame)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t frame_graph = nullptr;
+  cudaGraphExec_t frame_exec = nullptr;
+  cudaGraphNode_t setup_node = nullptr;
+  cudaKernelNodeParams setup_params{};
+  cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
+  bool graph_timed = false;
+  uint64_t graph_kernels = 0;
   // bookkeeping
   uint64_t launches = 0;
   uint32_t rebuilds = 0;
@@ -132,6 +143,24 @@ __global__ void k_init_pool(unsigned int* stack, unsigned int n) {
     stack[i] = n - 1u - i;
 }
 
+// Stores the per-call control block and zeroes the counters the call accumulates into.
+__global__ void k_setup(FrameCtl c, FrameCtl* dst, DevCounters* cnt) {
+  if (threadIdx.x != 0) return;
+  *dst = c;
+  if (c.reset & kResetFrame) {
+    cnt->n_cand = 0;
+    cnt->n_touched = 0;
+    cnt->n_new = 0;
+    cnt->vox_updated = 0ull;
+  }
+  if (c.reset & kResetErase) cnt->n_erased = 0;
+  if (c.reset & kResetMset) {
+    cnt->n_mset = 0;
+    cnt->n_tombrec = 0;
+    if (c.n_entries_dev) *c.n_entries_dev = 0;
+  }
+}
+
 // Non-blocking view of the counters: a copy enqueued on a side stream after each call, read by
 // the next call if it has landed.  Used only for the tombstone clean-up heuristic.
 void snapshot_counters(vbh_handle* h) {
@@ -168,8 +197,8 @@ FrameParams frame_params(const vbh_handle* h, const float* T) {
   const vbh_config& c = h->cfg;
   FrameParams fp{};
   for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) fp.R[3 * i + j] = T[4 * i + j];
-    fp.t[i] = T[4 * i + 3];
+    for (int j = 0; j < 3; ++j) fp.R[3 * i + j] = T ? T[4 * i + j] : (i == j ? 1.f : 0.f);
+    fp.t[i] = T ? T[4 * i + 3] : 0.f;
   }
   fp.s = c.voxel_size;
   fp.mu = c.trunc;
@@ -192,6 +221,37 @@ FrameParams frame_params(const vbh_handle* h, const float* T) {
   fp.height = c.height;
   fp.J = h->J;
   return fp;
+}
+
+FrameCtl base_ctl(const vbh_handle* h, const float* T) {
+  FrameCtl c{};
+  c.fp = frame_params(h, T);
+  c.version = h->frame_version;
+  return c;
+}
+
+void set_stream_out(FrameCtl& c, const vbh_mc_stream* out) {
+  c.rec_keys3 = out->keys3;
+  c.rec_info = out->info;
+  c.rec_off = out->offsets;
+  c.rec_cnt = out->counts;
+  c.ent_local = out->local;
+  c.ent_idx = out->index;
+  c.n_blocks_dev = out->n_blocks_dev;
+  c.n_entries_dev = out->n_entries_dev;
+  c.cap_blocks = out->cap_blocks;
+  c.cap_entries = out->cap_entries;
+}
+
+void launch_setup(vbh_handle* h, const FrameCtl& c) {
+  k_setup<<<1, 32, 0, h->stream>>>(c, h->ctl, h->cnt);
+  h->launches += 1;
+}
+
+bool stream_ok(const vbh_mc_stream* out) {
+  return out && out->n_blocks_dev && out->n_entries_dev &&
+         !(out->cap_blocks && (!out->keys3 || !out->info || !out->offsets || !out->counts)) &&
+         !(out->cap_entries && (!out->local || !out->index));
 }
 
 void read_frame_stats(vbh_handle* h, const DevCounters& d, vbh_frame_stats* st) {
@@ -258,6 +318,8 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
   CREATE_CUDA(cudaMalloc(&h->shadow, tbytes));
   CREATE_CUDA(cudaMemsetAsync(h->slots, 0xFF, tbytes, h->stream));
   CREATE_CUDA(cudaMalloc(&h->cnt, sizeof(DevCounters)));
+  CREATE_CUDA(cudaMalloc(&h->ctl, sizeof(FrameCtl)));
+  CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CREATE_CUDA(cudaMallocHost(&h->snap, sizeof(DevCounters)));
   DevCounters init{};
   init.free_top = (int)c.max_blocks;
@@ -304,7 +366,10 @@ vbh_status vbh_destroy(vbh_handle* h) {
   if (!h) return VBH_OK;
   if (h->stream || h->slots) cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
-  void* ptrs[] = {h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
+  if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
+  if (h->frame_graph) cudaGraphDestroy(h->frame_graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  void* ptrs[] = {h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
                   h->version, h->stack, h->cand, h->cand_res, h->cand_st, h->touched, h->mset,
                   h->removed, h->tombrec};
   for (void* p : ptrs)
@@ -346,7 +411,7 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   launch_hash_insert(h->L, t, pool, h->cnt, ops_dev, keys3_dev, nullptr, nullptr, vals_dev,
                      results_dev, status_dev, n);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, nullptr, results_dev, status_dev, n, nullptr,
-                            nullptr, 0u);
+                            nullptr, nullptr);
   launch_hash_erase(h->L, t, pool, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n);
   h->launches += 4;
   h->stage_end();
@@ -370,22 +435,23 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   if (frame_id >= 0x80000000u) return fail(VBH_ERR_INVALID_ARG, "frame_id must be < 2^31");
   vbh_status st = maybe_rebuild(h);
   if (st != VBH_OK) return st;
-  FrameParams fp = frame_params(h, T_wc_host);
-  fp.depth = depth_dev;
+  FrameCtl c = base_ctl(h, T_wc_host);
+  c.fp.depth = depth_dev;
+  c.epoch_touch = h->next_epoch();
+  c.reset = kResetFrame;
   const TableView t = h->table();
   const PoolView pool = h->pool();
-  const unsigned int epoch = h->next_epoch();
   h->stage_begin(VBH_STAGE_ALLOC);
-  launch_frame_begin(h->L, h->cnt);
-  launch_alloc_keys(h->L, fp, h->cand, h->cand_cap, h->cnt);
+  launch_setup(h, c);
+  launch_alloc_keys(h->L, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
   launch_hash_insert(h->L, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
-                            h->cand_cap, h->touched, &h->cnt->n_touched, epoch);
-  h->launches += 4;
+                            h->cand_cap, h->touched, &h->cnt->n_touched, &h->ctl->epoch_touch);
+  h->launches += 3;
   h->stage_end();
   h->stage_begin(VBH_STAGE_INTEGRATE);
-  launch_integrate(h->L, fp, pool, h->touched, &h->cnt->n_touched, h->cnt);
+  launch_integrate(h->L, h->ctl, pool, h->touched, &h->cnt->n_touched, h->cnt);
   h->launches += 1;
   h->stage_end();
   h->frame_version = frame_id;
@@ -403,28 +469,157 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   return VBH_OK;
 }
 
+// Capture erase + allocation + fusion + MC set + MC extraction of one frame as a CUDA graph.
+// All per-frame inputs reach the kernels through the control block written by the root
+// (setup) node, so a frame is: update that node's argument, launch the graph.
+static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
+  if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
+  if (h->frame_graph) cudaGraphDestroy(h->frame_graph);
+  h->frame_exec = nullptr;
+  h->frame_graph = nullptr;
+  h->ev_node[0] = h->ev_node[1] = nullptr;
+  const Launch Lc{h->cap_stream, h->L.sms};
+  const TableView t = h->table();
+  const PoolView pool = h->pool();
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (timed) {
+    ea = h->get_event();
+    eb = h->get_event();
+  }
+  VBH_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+  FrameCtl c{};
+  k_setup<<<1, 32, 0, h->cap_stream>>>(c, h->ctl, h->cnt);
+  launch_erase_radius(Lc, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks, nullptr,
+                      nullptr);
+  launch_alloc_keys(Lc, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
+  launch_hash_insert(Lc, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
+                     h->cand_res, h->cand_st, h->cand_cap);
+  launch_hash_insert_finish(Lc, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
+                            h->cand_cap, h->touched, &h->cnt->n_touched, &h->ctl->epoch_touch);
+  if (timed) cudaEventRecordWithFlags(ea, h->cap_stream, cudaEventRecordExternal);
+  launch_integrate(Lc, h->ctl, pool, h->touched, &h->cnt->n_touched, h->cnt);
+  if (timed) cudaEventRecordWithFlags(eb, h->cap_stream, cudaEventRecordExternal);
+  launch_mset_touched(Lc, t, pool, h->cnt, h->ctl, h->touched, &h->cnt->n_touched, h->removed,
+                      &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec);
+  launch_mc_extract(Lc, t, pool, h->cnt, h->ctl, h->mset, h->tombrec);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  cudaError_t le = cudaGetLastError();
+  if (e != cudaSuccess || le != cudaSuccess || !g)
+    return fail(VBH_ERR_CUDA, std::string("frame graph capture: ") +
+                                  cudaGetErrorString(e != cudaSuccess ? e : le));
+  h->frame_graph = g;
+  size_t nroot = 0;
+  VBH_CUDA(cudaGraphGetRootNodes(g, nullptr, &nroot));
+  if (nroot != 1) return fail(VBH_ERR_CUDA, "frame graph: expected one root node");
+  VBH_CUDA(cudaGraphGetRootNodes(g, &h->setup_node, &nroot));
+  VBH_CUDA(cudaGraphKernelNodeGetParams(h->setup_node, &h->setup_params));
+  if (timed) {
+    size_t n = 0;
+    VBH_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    VBH_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+    for (cudaGraphNode_t node : nodes) {
+      cudaGraphNodeType ty;
+      VBH_CUDA(cudaGraphNodeGetType(node, &ty));
+      if (ty != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev = nullptr;
+      VBH_CUDA(cudaGraphEventRecordNodeGetEvent(node, &ev));
+      if (ev == ea) h->ev_node[0] = node;
+      if (ev == eb) h->ev_node[1] = node;
+    }
+    if (!h->ev_node[0] || !h->ev_node[1]) return fail(VBH_ERR_CUDA, "frame graph: event nodes");
+  }
+  VBH_CUDA(cudaGraphInstantiate(&h->frame_exec, g, 0));
+  h->graph_timed = timed;
+  h->graph_kernels = 8;
+  return VBH_OK;
+}
+
+vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const float* T_wc_host,
+                             uint32_t frame_id, float erase_radius, const vbh_mc_stream* out) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
+  if (!depth_dev || !T_wc_host) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if (!stream_ok(out)) return fail(VBH_ERR_INVALID_ARG, "incomplete output stream");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(T_wc_host[i])) return fail(VBH_ERR_INVALID_ARG, "non-finite pose");
+  if (frame_id >= 0x80000000u) return fail(VBH_ERR_INVALID_ARG, "frame_id must be < 2^31");
+  if (!(erase_radius >= 0.f) || !std::isfinite(erase_radius))
+    return fail(VBH_ERR_INVALID_ARG, "invalid erase radius");
+  vbh_status st = maybe_rebuild(h);
+  if (st != VBH_OK) return st;
+  const bool timed = (h->timing & (1 << VBH_STAGE_INTEGRATE)) != 0;
+  if (!h->frame_exec || timed != h->graph_timed) {
+    st = build_frame_graph(h, timed);
+    if (st != VBH_OK) return st;
+  }
+  FrameCtl c = base_ctl(h, T_wc_host);
+  c.fp.depth = depth_dev;
+  c.do_erase = erase_radius > 0.f;
+  for (int i = 0; i < 3; ++i) c.erase_c[i] = T_wc_host[4 * i + 3];
+  c.erase_r2 = erase_radius * erase_radius;   // binary32 product, one rounding
+  c.epoch_touch = h->next_epoch();
+  c.epoch_mset = h->next_epoch();
+  c.version = frame_id;
+  c.clear_removed = 1;
+  c.reset = kResetFrame | kResetErase | kResetMset;
+  set_stream_out(c, out);
+  FrameCtl* dst = h->ctl;
+  DevCounters* cnt = h->cnt;
+  void* args[] = {&c, &dst, &cnt};
+  cudaKernelNodeParams p = h->setup_params;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  VBH_CUDA(cudaGraphExecKernelNodeSetParams(h->frame_exec, h->setup_node, &p));
+  if (timed) {
+    cudaEvent_t a = h->get_event(), b = h->get_event();
+    VBH_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->frame_exec, h->ev_node[0], a));
+    VBH_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->frame_exec, h->ev_node[1], b));
+    h->pending.push_back(StageEvents{VBH_STAGE_INTEGRATE, a, b, 1});
+  } else {
+    h->stage_launches[VBH_STAGE_INTEGRATE] += 1;
+  }
+  VBH_CUDA(cudaGraphLaunch(h->frame_exec, h->stream));
+  h->launches += h->graph_kernels;
+  h->frame_version = frame_id;
+  h->have_frame = true;
+  h->last_entries = out->n_entries_dev;
+  snapshot_counters(h);
+  return VBH_OK;
+}
+
 vbh_status vbh_erase_blocks(vbh_handle* h, const vbh_erase_selector* sel,
                             int32_t* erased_keys3_dev, uint32_t* n_erased_dev) {
   if (!h || !sel) return fail(VBH_ERR_INVALID_ARG, "null argument");
   if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
   const TableView t = h->table();
   const PoolView pool = h->pool();
-  h->stage_begin(VBH_STAGE_ERASE);
   if (sel->mode == VBH_ERASE_RADIUS) {
-    if (!(sel->radius >= 0.f) || !std::isfinite(sel->centre[0]) || !std::isfinite(sel->centre[1]) ||
-        !std::isfinite(sel->centre[2]))
+    if (!(sel->radius >= 0.f) || !std::isfinite(sel->radius) || !std::isfinite(sel->centre[0]) ||
+        !std::isfinite(sel->centre[1]) || !std::isfinite(sel->centre[2]))
       return fail(VBH_ERR_INVALID_ARG, "invalid erase radius / centre");
-    launch_erase_radius(h->L, t, pool, h->cnt, sel->centre[0], sel->centre[1], sel->centre[2],
-                        sel->radius, h->cfg.voxel_size, h->removed, h->cfg.max_blocks,
-                        erased_keys3_dev, n_erased_dev);
-    h->launches += 2;
   } else if (sel->mode == VBH_ERASE_KEYS) {
     if (sel->n_keys && !sel->keys3_dev) return fail(VBH_ERR_INVALID_ARG, "null key list");
-    launch_erase_keys(h->L, t, pool, h->cnt, sel->keys3_dev, sel->n_keys, h->removed,
-                      h->cfg.max_blocks, erased_keys3_dev, n_erased_dev);
-    h->launches += sel->n_keys ? 2 : 1;
   } else {
     return fail(VBH_ERR_INVALID_ARG, "unknown erase mode");
+  }
+  FrameCtl c = base_ctl(h, nullptr);
+  c.reset = kResetErase;
+  h->stage_begin(VBH_STAGE_ERASE);
+  if (sel->mode == VBH_ERASE_RADIUS) {
+    c.do_erase = 1;
+    for (int i = 0; i < 3; ++i) c.erase_c[i] = sel->centre[i];
+    c.erase_r2 = sel->radius * sel->radius;   // binary32 product, one rounding
+    launch_setup(h, c);
+    launch_erase_radius(h->L, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks,
+                        erased_keys3_dev, n_erased_dev);
+    h->launches += 1;
+  } else {
+    launch_setup(h, c);
+    launch_erase_keys(h->L, t, pool, h->cnt, sel->keys3_dev, sel->n_keys, h->removed,
+                      h->cfg.max_blocks, erased_keys3_dev, n_erased_dev);
+    h->launches += sel->n_keys ? 1 : 0;
   }
   h->stage_end();
   vbh_status st = check_launch(h, "vbh_erase_blocks");
@@ -436,47 +631,42 @@ vbh_status vbh_extract_mc_indices(vbh_handle* h, const vbh_mc_selector* sel,
                                   const vbh_mc_stream* out, uint64_t* needed_bytes_host) {
   if (!h || !sel || !out) return fail(VBH_ERR_INVALID_ARG, "null argument");
   if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
-  if (!out->n_blocks_dev || !out->n_entries_dev ||
-      (out->cap_blocks && (!out->keys3 || !out->info || !out->offsets || !out->counts)) ||
-      (out->cap_entries && (!out->local || !out->index)))
-    return fail(VBH_ERR_INVALID_ARG, "incomplete output stream");
+  if (!stream_ok(out)) return fail(VBH_ERR_INVALID_ARG, "incomplete output stream");
+  if (sel->mode > VBH_MC_SINCE) return fail(VBH_ERR_INVALID_ARG, "unknown extraction mode");
+  if (sel->mode == VBH_MC_KEYS && sel->n_keys && !sel->keys3_dev)
+    return fail(VBH_ERR_INVALID_ARG, "null key list");
   const TableView t = h->table();
   const PoolView pool = h->pool();
-  const unsigned int epoch = h->next_epoch();
+  FrameCtl c = base_ctl(h, nullptr);
+  set_stream_out(c, out);
+  c.epoch_mset = h->next_epoch();
+  c.clear_removed = sel->mode == VBH_MC_TOUCHED;
+  c.reset = kResetMset;
   h->stage_begin(VBH_STAGE_MCSET);
-  VBH_CUDA(cudaMemsetAsync(out->n_entries_dev, 0, sizeof(uint32_t), h->stream));
+  launch_setup(h, c);
   switch (sel->mode) {
     case VBH_MC_TOUCHED:
-      launch_mset_touched(h->L, t, pool, h->cnt, h->have_frame ? h->touched : nullptr,
+      launch_mset_touched(h->L, t, pool, h->cnt, h->ctl, h->have_frame ? h->touched : nullptr,
                           h->have_frame ? &h->cnt->n_touched : nullptr, h->removed,
-                          &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec, epoch,
-                          h->frame_version);
-      h->launches += 2;
+                          &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec);
+      h->launches += 1;
       break;
     case VBH_MC_ALL:
     case VBH_MC_SINCE:
       launch_mset_scan(h->L, pool, h->cnt, h->mset, sel->mode == VBH_MC_SINCE, sel->since_version);
-      h->launches += 2;
-      break;
-    case VBH_MC_KEYS:
-      if (sel->n_keys && !sel->keys3_dev) return fail(VBH_ERR_INVALID_ARG, "null key list");
-      launch_mset_keys(h->L, t, pool, h->cnt, sel->keys3_dev, sel->n_keys, h->mset, epoch);
-      h->launches += sel->n_keys ? 2 : 1;
+      h->launches += 1;
       break;
     default:
-      return fail(VBH_ERR_INVALID_ARG, "unknown extraction mode");
+      launch_mset_keys(h->L, t, pool, h->cnt, h->ctl, sel->keys3_dev, sel->n_keys, h->mset);
+      h->launches += sel->n_keys ? 1 : 0;
+      break;
   }
   h->stage_end();
   h->stage_begin(VBH_STAGE_MC);
-  launch_mc_extract(h->L, t, pool, h->cnt, h->mset, h->tombrec, out->keys3, out->info,
-                    out->offsets, out->counts, out->local, out->index, out->cap_blocks,
-                    out->cap_entries, out->n_blocks_dev, out->n_entries_dev, h->frame_version);
+  launch_mc_extract(h->L, t, pool, h->cnt, h->ctl, h->mset, h->tombrec);
   h->launches += 1;
-  if (sel->mode == VBH_MC_TOUCHED)
-    VBH_CUDA(cudaMemsetAsync(&h->cnt->n_removed, 0, sizeof(unsigned int), h->stream));
-  VBH_CUDA(cudaMemcpyAsync(&h->cnt->mc_entries, out->n_entries_dev, sizeof(unsigned int),
-                           cudaMemcpyDeviceToDevice, h->stream));
   h->stage_end();
+  h->last_entries = out->n_entries_dev;
   vbh_status st = check_launch(h, "vbh_extract_mc_indices");
   if (st != VBH_OK) return st;
   if (needed_bytes_host) {
@@ -620,7 +810,11 @@ vbh_status vbh_get_counters(vbh_handle* h, vbh_counters* out) {
   out->kernel_launches = h->launches;
   out->rebuilds = h->rebuilds;
   out->last_mc_blocks = d.mc_blocks;
-  out->last_mc_entries = d.mc_entries;
+  uint32_t ne = 0;
+  if (h->last_entries) {
+    VBH_CUDA(cudaMemcpy(&ne, h->last_entries, sizeof ne, cudaMemcpyDeviceToHost));
+  }
+  out->last_mc_entries = ne;
   out->last_erased = d.n_erased;
   out->voxels_written = d.vox_updated;
   return VBH_OK;

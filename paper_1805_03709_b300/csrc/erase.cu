@@ -45,14 +45,16 @@ __device__ __forceinline__ void finish_removal(bool erased, unsigned int p, unsi
 }
 
 __global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView pool,
-                                                           DevCounters* cnt, float cx, float cy,
-                                                           float cz, float R2, float s,
+                                                           DevCounters* cnt, const FrameCtl* ctl,
                                                            unsigned long long* removed,
                                                            unsigned int removed_cap,
                                                            int* out_keys3) {
   __shared__ unsigned int s_erased, s_err;
   if (threadIdx.x == 0) { s_erased = 0; s_err = 0; }
   __syncthreads();
+  if (!ctl->do_erase) return;   // uniform across the grid
+  const float cx = ctl->erase_c[0], cy = ctl->erase_c[1], cz = ctl->erase_c[2];
+  const float R2 = ctl->erase_r2, s = ctl->fp.s;
   const unsigned int stride = gridDim.x * blockDim.x;
   const unsigned int rounds = (pool.max_blocks + stride - 1u) / stride;
   for (unsigned int r = 0; r < rounds; ++r) {
@@ -120,20 +122,15 @@ __global__ void __launch_bounds__(kThreads) k_erase_keys(TableView t, PoolView p
   }
 }
 
-__global__ void k_erase_begin(DevCounters* cnt) { cnt->n_erased = 0; }
-
 }  // namespace
 
 void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                         float cx, float cy, float cz, float radius, float s,
-                         unsigned long long* removed, unsigned int removed_cap,
-                         int* out_keys3, unsigned int* out_n) {
+                         const FrameCtl* ctl, unsigned long long* removed,
+                         unsigned int removed_cap, int* out_keys3, unsigned int* out_n) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_erase_radius, kThreads, L.sms);
-  k_erase_begin<<<1, 1, 0, L.stream>>>(cnt);
-  const float R2 = radius * radius;   // host binary32 product, rounded once
-  k_erase_radius<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, cx, cy, cz, R2, s, removed,
-                                                  removed_cap, out_keys3);
+  k_erase_radius<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, ctl, removed, removed_cap,
+                                                  out_keys3);
   if (out_n)
     cudaMemcpyAsync(out_n, &cnt->n_erased, sizeof(unsigned int), cudaMemcpyDeviceToDevice,
                     L.stream);
@@ -144,7 +141,6 @@ void launch_erase_keys(const Launch& L, TableView t, PoolView pool, DevCounters*
                        unsigned int removed_cap, int* out_keys3, unsigned int* out_n) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_erase_keys, kThreads, L.sms);
-  k_erase_begin<<<1, 1, 0, L.stream>>>(cnt);
   if (n)
     k_erase_keys<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, keys3, n, removed, removed_cap,
                                                   out_keys3);

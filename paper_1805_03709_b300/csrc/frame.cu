@@ -60,20 +60,24 @@ constexpr int kTileThreads = kTile * kTile;
 constexpr int kTileSet = 1024;       // shared-memory key set per tile (power of two)
 constexpr int kIntThreads = 128;     // fusion: 4 voxels per thread, one block per CTA step
 
-__global__ void k_frame_begin(DevCounters* cnt) {
-  cnt->n_cand = 0;
-  cnt->n_touched = 0;
-  cnt->n_new = 0;
-  cnt->vox_updated = 0ull;
+// Copy the per-call frame parameters into shared memory (one word per thread).
+__device__ __forceinline__ void load_frame_params(FrameParams& dst, const FrameCtl* ctl) {
+  constexpr int kWords = sizeof(FrameParams) / 4;
+  static_assert(kWords <= 128, "FrameParams larger than one CTA's copy");
+  if (threadIdx.x < kWords)
+    reinterpret_cast<int*>(&dst)[threadIdx.x] = reinterpret_cast<const int*>(&ctl->fp)[threadIdx.x];
+  __syncthreads();
 }
 
 // Band allocation: every valid pixel's samples -> block keys -> per-tile distinct set in shared
 // memory -> appended to the candidate list (the global de-duplication is the hash insert).
-__global__ void __launch_bounds__(kTileThreads) k_alloc_keys(FrameParams fp,
+__global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl,
                                                              unsigned long long* cand,
                                                              unsigned int cap,
                                                              DevCounters* cnt) {
   __shared__ unsigned long long set[kTileSet];
+  __shared__ FrameParams fp;
+  load_frame_params(fp, ctl);
   for (int i = threadIdx.x; i < kTileSet; i += kTileThreads) set[i] = kEmpty;
   __syncthreads();
   const int tiles_x = (fp.width + kTile - 1) / kTile;
@@ -141,14 +145,15 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(FrameParams fp,
 // Projective TSDF fusion of every voxel of every touched block; also rewrites the block's
 // sign / weight bit masks.  Thread t owns voxels t, t + 128, t + 256, t + 384, so every warp
 // load or store covers 256 contiguous bytes and each ballot yields one 32-voxel mask word.
-__global__ void __launch_bounds__(kIntThreads) k_integrate(FrameParams fp, PoolView pool,
+__global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, PoolView pool,
                                                            const unsigned int* touched,
                                                            const unsigned int* n_touched,
                                                            DevCounters* cnt) {
   __shared__ unsigned int s_upd;
   __shared__ unsigned int s_fresh;
+  __shared__ FrameParams fp;
   if (threadIdx.x == 0) s_upd = 0;
-  __syncthreads();
+  load_frame_params(fp, ctl);
   const unsigned int n = *n_touched;
   const int t = threadIdx.x;
   const unsigned int lane = t & 31, warp = t >> 5;
@@ -220,24 +225,20 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(FrameParams fp, PoolV
 
 }  // namespace
 
-void launch_frame_begin(const Launch& L, DevCounters* cnt) {
-  k_frame_begin<<<1, 1, 0, L.stream>>>(cnt);
-}
-
-void launch_alloc_keys(const Launch& L, const FrameParams& fp, unsigned long long* cand,
-                       unsigned int cap, DevCounters* cnt) {
+void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int height,
+                       unsigned long long* cand, unsigned int cap, DevCounters* cnt) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_alloc_keys, kTileThreads, L.sms);
-  const int tiles = ((fp.width + kTile - 1) / kTile) * ((fp.height + kTile - 1) / kTile);
-  k_alloc_keys<<<tiles < grid ? tiles : grid, kTileThreads, 0, L.stream>>>(fp, cand, cap, cnt);
+  const int tiles = ((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
+  k_alloc_keys<<<tiles < grid ? tiles : grid, kTileThreads, 0, L.stream>>>(ctl, cand, cap, cnt);
 }
 
-void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
+void launch_integrate(const Launch& L, const FrameCtl* ctl, PoolView pool,
                       const unsigned int* touched, const unsigned int* n_touched,
                       DevCounters* cnt) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_integrate, kIntThreads, L.sms);
-  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(fp, pool, touched, n_touched, cnt);
+  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(ctl, pool, touched, n_touched, cnt);
 }
 
 }  // namespace vbh

@@ -203,11 +203,12 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
                                                             unsigned int n_cap,
                                                             unsigned int* touched,
                                                             unsigned int* n_touched,
-                                                            unsigned int epoch) {
+                                                            const unsigned int* epoch_dev) {
   __shared__ unsigned int s_undo, s_new, s_err;
   if (threadIdx.x == 0) { s_undo = 0; s_new = 0; s_err = 0; }
   __syncthreads();
   const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
+  const unsigned int epoch = epoch_dev ? *epoch_dev : 0u;
   if (blockIdx.x == 0 && threadIdx.x == 0 && pool.max_blocks) {
     int popped = (int)cnt->n_popped;
     cnt->free_top = max(cnt->free_top - popped, 0);
@@ -435,7 +436,7 @@ void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
                                unsigned char* st, unsigned int n, unsigned int* touched,
-                               unsigned int* n_touched, unsigned int epoch) {
+                               unsigned int* n_touched, const unsigned int* epoch) {
   VBH_GRID(k_insert_finish, kThreads);
   k_insert_finish<<<grid_k_insert_finish, kThreads, 0, L.stream>>>(t, pool, cnt, count_dev, res,
                                                                     st, n, touched, n_touched,

@@ -25,11 +25,6 @@ constexpr int kMcThreads = 128;   // 4 warps, one block each
 constexpr unsigned long long kLo7 = 0x7F7F7F7F7F7F7F7Full;
 constexpr unsigned long long kHi1 = 0x8080808080808080ull;
 
-__global__ void k_mset_begin(DevCounters* cnt) {
-  cnt->n_mset = 0;
-  cnt->n_tombrec = 0;
-}
-
 __device__ __forceinline__ void add_to_set(PoolView& pool, unsigned int q, unsigned int epoch,
                                            bool pred, unsigned int* mset, unsigned int* n_mset,
                                            int stamp_version, unsigned int version) {
@@ -44,16 +39,15 @@ __device__ __forceinline__ void add_to_set(PoolView& pool, unsigned int q, unsig
 
 // touched blocks x 8 offsets, then removed keys x 8 offsets
 __global__ void __launch_bounds__(kThreads) k_mset_touched(TableView t, PoolView pool,
-                                                           DevCounters* cnt,
+                                                           DevCounters* cnt, const FrameCtl* ctl,
                                                            const unsigned int* touched,
                                                            const unsigned int* n_touched,
                                                            const unsigned long long* removed,
                                                            const unsigned int* n_removed,
                                                            unsigned int removed_cap,
                                                            unsigned int* mset,
-                                                           unsigned long long* tombrec,
-                                                           unsigned int epoch,
-                                                           unsigned int version) {
+                                                           unsigned long long* tombrec) {
+  const unsigned int epoch = ctl->epoch_mset, version = ctl->version;
   const unsigned int nt = n_touched ? *n_touched : 0u;
   const unsigned int nr = min(*n_removed, removed_cap);
   const unsigned int items = 8u * (nt + nr);
@@ -101,9 +95,10 @@ __global__ void __launch_bounds__(kThreads) k_mset_touched(TableView t, PoolView
 
 // explicit keys x 8 offsets (o = 0 is the key itself)
 __global__ void __launch_bounds__(kThreads) k_mset_keys(TableView t, PoolView pool,
-                                                        DevCounters* cnt, const int* keys3,
-                                                        unsigned int n, unsigned int* mset,
-                                                        unsigned int epoch) {
+                                                        DevCounters* cnt, const FrameCtl* ctl,
+                                                        const int* keys3, unsigned int n,
+                                                        unsigned int* mset) {
+  const unsigned int epoch = ctl->epoch_mset;
   const unsigned int items = 8u * n;
   const unsigned int stride = gridDim.x * blockDim.x;
   const unsigned int rounds = (items + stride - 1u) / stride;
@@ -158,14 +153,22 @@ __device__ __forceinline__ unsigned int row9(const unsigned int (*m)[32], int ki
   return ((m[nb][word] >> sh) & 0xFFu) | (((m[nb + 1][word] >> sh) & 1u) << 8);
 }
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_extract(
-    TableView t, PoolView pool, DevCounters* cnt, const unsigned int* mset,
-    const unsigned long long* tombrec, int* rec_keys3, unsigned int* rec_info,
-    unsigned int* rec_off, unsigned int* rec_cnt, unsigned short* ent_local,
-    unsigned char* ent_idx, unsigned int cap_blocks, unsigned int cap_entries,
-    unsigned int* n_blocks_dev, unsigned int* n_entries_dev, unsigned int tomb_version) {
+__global__ void __launch_bounds__(kMcThreads) k_mc_extract(TableView t, PoolView pool,
+                                                          DevCounters* cnt, const FrameCtl* ctl,
+                                                          const unsigned int* mset,
+                                                          const unsigned long long* tombrec) {
   __shared__ unsigned long long spread[256];   // bit i of b -> bit 8 i
   __shared__ unsigned int msk[kMcThreads / 32][8][32];
+  int* const rec_keys3 = ctl->rec_keys3;
+  unsigned int* const rec_info = ctl->rec_info;
+  unsigned int* const rec_off = ctl->rec_off;
+  unsigned int* const rec_cnt = ctl->rec_cnt;
+  unsigned short* const ent_local = ctl->ent_local;
+  unsigned char* const ent_idx = ctl->ent_idx;
+  unsigned int* const n_blocks_dev = ctl->n_blocks_dev;
+  unsigned int* const n_entries_dev = ctl->n_entries_dev;
+  const unsigned int cap_blocks = ctl->cap_blocks, cap_entries = ctl->cap_entries;
+  const unsigned int tomb_version = ctl->version;
   for (int b = threadIdx.x; b < 256; b += kMcThreads) {
     unsigned long long v = 0;
     for (int i = 0; i < 8; ++i) v |= (unsigned long long)((b >> i) & 1) << (8 * i);
@@ -176,6 +179,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_extract(
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *n_blocks_dev = total;
     cnt->mc_blocks = total;
+    if (ctl->clear_removed) cnt->n_removed = 0;   // the set kernel that read it has finished
   }
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int nwarps = gridDim.x * (kMcThreads / 32);
@@ -276,47 +280,36 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_extract(
 }  // namespace
 
 void launch_mset_touched(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                         const unsigned int* touched, const unsigned int* n_touched,
-                         const unsigned long long* removed, const unsigned int* n_removed,
-                         unsigned int removed_cap, unsigned int* mset,
-                         unsigned long long* tombrec, unsigned int epoch, unsigned int version) {
+                         const FrameCtl* ctl, const unsigned int* touched,
+                         const unsigned int* n_touched, const unsigned long long* removed,
+                         const unsigned int* n_removed, unsigned int removed_cap,
+                         unsigned int* mset, unsigned long long* tombrec) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_mset_touched, kThreads, L.sms);
-  k_mset_begin<<<1, 1, 0, L.stream>>>(cnt);
-  k_mset_touched<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, touched, n_touched, removed,
-                                                  n_removed, removed_cap, mset, tombrec, epoch,
-                                                  version);
+  k_mset_touched<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, ctl, touched, n_touched, removed,
+                                                  n_removed, removed_cap, mset, tombrec);
 }
 
 void launch_mset_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                      const int* keys3, unsigned int n, unsigned int* mset, unsigned int epoch) {
+                      const FrameCtl* ctl, const int* keys3, unsigned int n, unsigned int* mset) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_mset_keys, kThreads, L.sms);
-  k_mset_begin<<<1, 1, 0, L.stream>>>(cnt);
-  if (n) k_mset_keys<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, keys3, n, mset, epoch);
+  if (n) k_mset_keys<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, ctl, keys3, n, mset);
 }
 
 void launch_mset_scan(const Launch& L, PoolView pool, DevCounters* cnt, unsigned int* mset,
                       int since_mode, unsigned int since_version) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_mset_scan, kThreads, L.sms);
-  k_mset_begin<<<1, 1, 0, L.stream>>>(cnt);
   k_mset_scan<<<grid, kThreads, 0, L.stream>>>(pool, cnt, mset, since_mode, since_version);
 }
 
 void launch_mc_extract(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                       const unsigned int* mset, const unsigned long long* tombrec,
-                       int* rec_keys3, unsigned int* rec_info, unsigned int* rec_off,
-                       unsigned int* rec_cnt, unsigned short* ent_local,
-                       unsigned char* ent_idx, unsigned int cap_blocks,
-                       unsigned int cap_entries, unsigned int* n_blocks_dev,
-                       unsigned int* n_entries_dev, unsigned int tomb_version) {
+                       const FrameCtl* ctl, const unsigned int* mset,
+                       const unsigned long long* tombrec) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_mc_extract, kMcThreads, L.sms);
-  k_mc_extract<<<grid, kMcThreads, 0, L.stream>>>(t, pool, cnt, mset, tombrec, rec_keys3,
-                                                  rec_info, rec_off, rec_cnt, ent_local, ent_idx,
-                                                  cap_blocks, cap_entries, n_blocks_dev,
-                                                  n_entries_dev, tomb_version);
+  k_mc_extract<<<grid, kMcThreads, 0, L.stream>>>(t, pool, cnt, ctl, mset, tombrec);
 }
 
 }  // namespace vbh

@@ -215,6 +215,31 @@ struct FrameParams {
   const unsigned short* depth;
 };
 
+// Per-call control block in device memory.  Every entry point first launches one setup kernel
+// whose only by-value argument is this struct; the setup kernel stores it and zeroes the
+// per-call counters, and the work kernels read their per-call inputs (pose, depth pointer,
+// epochs, output pointers) from it.  A whole frame captured as a CUDA graph can therefore be
+// re-launched with new inputs by updating the argument of one kernel node.
+constexpr unsigned int kResetFrame = 1u, kResetErase = 2u, kResetMset = 4u;
+struct FrameCtl {
+  FrameParams fp;
+  float erase_c[3];
+  float erase_r2;               // fl(R * R)
+  unsigned int do_erase;        // radius erase enabled
+  unsigned int epoch_touch, epoch_mset, version;
+  unsigned int clear_removed;   // the extraction consumes the removal list
+  unsigned int reset;           // kReset* bits: counters the setup kernel zeroes
+  int* rec_keys3;               // MC output stream (caller buffers)
+  unsigned int* rec_info;
+  unsigned int* rec_off;
+  unsigned int* rec_cnt;
+  unsigned short* ent_local;
+  unsigned char* ent_idx;
+  unsigned int* n_blocks_dev;
+  unsigned int* n_entries_dev;
+  unsigned int cap_blocks, cap_entries;
+};
+
 // ------------------------------------------------------------------------------- host launchers
 struct Launch {
   cudaStream_t stream;
@@ -232,7 +257,7 @@ void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
                                unsigned char* st, unsigned int n, unsigned int* touched,
-                               unsigned int* n_touched, unsigned int epoch);
+                               unsigned int* n_touched, const unsigned int* epoch_dev);
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const unsigned char* ops, const int* keys3, unsigned int* res,
                        unsigned char* st, unsigned int n);
@@ -247,41 +272,35 @@ void launch_scatter_blocks(const Launch& L, PoolView pool, const unsigned int* i
                            unsigned int n, const float* tsdf, const float* w);
 void launch_pack_keys(const Launch& L, const int* keys3, unsigned int n,
                       unsigned long long* out);
+void launch_block_masks(const Launch& L, PoolView pool, const unsigned int* idx, unsigned int n);
 
 // frame.cu
-void launch_frame_begin(const Launch& L, DevCounters* cnt);
-void launch_alloc_keys(const Launch& L, const FrameParams& fp, unsigned long long* cand,
-                       unsigned int cap, DevCounters* cnt);
-void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
+void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int height,
+                       unsigned long long* cand, unsigned int cap, DevCounters* cnt);
+void launch_integrate(const Launch& L, const FrameCtl* ctl, PoolView pool,
                       const unsigned int* touched, const unsigned int* n_touched,
                       DevCounters* cnt);
 
 // erase.cu
 void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                         float cx, float cy, float cz, float radius, float s,
-                         unsigned long long* removed, unsigned int removed_cap,
-                         int* out_keys3, unsigned int* out_n);
+                         const FrameCtl* ctl, unsigned long long* removed,
+                         unsigned int removed_cap, int* out_keys3, unsigned int* out_n);
 void launch_erase_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const int* keys3, unsigned int n, unsigned long long* removed,
                        unsigned int removed_cap, int* out_keys3, unsigned int* out_n);
 
 // mc.cu
 void launch_mset_touched(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                         const unsigned int* touched, const unsigned int* n_touched,
-                         const unsigned long long* removed, const unsigned int* n_removed,
-                         unsigned int removed_cap, unsigned int* mset,
-                         unsigned long long* tombrec, unsigned int epoch, unsigned int version);
+                         const FrameCtl* ctl, const unsigned int* touched,
+                         const unsigned int* n_touched, const unsigned long long* removed,
+                         const unsigned int* n_removed, unsigned int removed_cap,
+                         unsigned int* mset, unsigned long long* tombrec);
 void launch_mset_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                      const int* keys3, unsigned int n, unsigned int* mset, unsigned int epoch);
+                      const FrameCtl* ctl, const int* keys3, unsigned int n, unsigned int* mset);
 void launch_mset_scan(const Launch& L, PoolView pool, DevCounters* cnt, unsigned int* mset,
                       int since_mode, unsigned int since_version);
 void launch_mc_extract(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                       const unsigned int* mset, const unsigned long long* tombrec,
-                       int* rec_keys3, unsigned int* rec_info, unsigned int* rec_off,
-                       unsigned int* rec_cnt, unsigned short* ent_local,
-                       unsigned char* ent_idx, unsigned int cap_blocks,
-                       unsigned int cap_entries, unsigned int* n_blocks_dev,
-                       unsigned int* n_entries_dev, unsigned int tomb_version);
-void launch_block_masks(const Launch& L, PoolView pool, const unsigned int* idx, unsigned int n);
+                       const FrameCtl* ctl, const unsigned int* mset,
+                       const unsigned long long* tombrec);
 
 }  // namespace vbh

@@ -80,6 +80,8 @@ SYMBOLS = [
     ("vbh_erase_blocks", ctypes.c_int, [_p, ctypes.POINTER(vbh_erase_selector), _p, _p]),
     ("vbh_extract_mc_indices", ctypes.c_int,
      [_p, ctypes.POINTER(vbh_mc_selector), ctypes.POINTER(vbh_mc_stream), ctypes.POINTER(_u64)]),
+    ("vbh_process_frame", ctypes.c_int,
+     [_p, _p, _p, _u32, _f32, ctypes.POINTER(vbh_mc_stream)]),
     ("vbh_dump", ctypes.c_int, [_p, _p, _p, _p, _p, _u32, ctypes.POINTER(_u32)]),
     ("vbh_load", ctypes.c_int, [_p, _p, _p, _p, _u32]),
     ("vbh_get_counters", ctypes.c_int, [_p, ctypes.POINTER(vbh_counters)]),
@@ -184,6 +186,12 @@ def vbh_extract_mc_indices(h, sel: vbh_mc_selector, out: vbh_mc_stream, want_nee
                                         ctypes.byref(need) if need is not None else None),
            "vbh_extract_mc_indices")
     return None if need is None else need.value
+
+
+def vbh_process_frame(h, depth, T_wc, frame_id: int, erase_radius: float, out: vbh_mc_stream):
+    T = np.ascontiguousarray(np.asarray(T_wc, np.float32).reshape(12))
+    _check(lib().vbh_process_frame(h, _ptr(depth), T.ctypes.data, int(frame_id),
+                                   float(erase_radius), ctypes.byref(out)), "vbh_process_frame")
 
 
 def vbh_dump(h, keys3, tsdf, weight, vals, cap: int) -> int:

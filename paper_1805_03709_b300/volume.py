@@ -137,6 +137,15 @@ class Volume:
         assert depth.dtype == torch.uint16 and depth.is_cuda and depth.is_contiguous()
         return V.vbh_integrate_frame(self.h, depth, T_wc, frame_id, stats)
 
+    def process_frame(self, depth: torch.Tensor, T_wc, frame_id: int, erase_radius: float,
+                      stream: McStream | None = None):
+        """Erase beyond `erase_radius` of the camera, fuse the frame, extract the touched MC
+        blocks into `stream` -- one CUDA-graph launch."""
+        assert depth.dtype == torch.uint16 and depth.is_cuda and depth.is_contiguous()
+        s = stream or self.stream
+        V.vbh_process_frame(self.h, depth, T_wc, frame_id, erase_radius, s.c_struct())
+        return s
+
     def erase_radius(self, centre, radius, keys_out: bool = True):
         sel = V.vbh_erase_selector(mode=V.VBH_ERASE_RADIUS, radius=float(radius))
         sel.centre[:] = [float(c) for c in centre]

@@ -234,3 +234,40 @@ def test_version_stamps_since_mode():
     since = vol.extract(V.VBH_MC_SINCE, since=11).to_host()
     assert set(since) == last
     assert all(r[0] == 12 for r in since.values())
+
+
+@pytest.mark.parametrize("timed", [False, True])
+def test_process_frame_graph_matches_oracle_and_separate_calls(timed):
+    """vbh_process_frame (one CUDA graph per frame) against the oracle, and bit-identical to the
+    three separate calls on a second volume."""
+    cam, poses, depth = synth.room_sequence(n_frames=8, width=160, height=120)
+    g, orc = make_pair(cam, 0.005, 0.02, 1 << 16, 1 << 17, zmax=4.0)
+    sep, _ = make_pair(cam, 0.005, 0.02, 1 << 16, 1 << 17, zmax=4.0)
+    if timed:
+        g.timing(("integrate",))
+    from paper_1805_03709_b300.volume import McStream
+    s2 = McStream.allocate(1 << 17, 1 << 22)
+    for i in range(len(poses)):
+        d = torch.from_numpy(depth[i]).cuda()
+        rg = g.process_frame(d, poses[i], i + 1, 2.5).to_host()
+        sep.erase_radius(poses[i][:, 3], 2.5)
+        sep.integrate(d, poses[i], i + 1)
+        rs = sep.extract(V.VBH_MC_TOUCHED, stream=s2).to_host()
+        orc.erase_radius(poses[i][:, 3], 2.5)
+        orc.integrate(depth[i], poses[i])
+        M, rem = orc.mc_set(0)
+        compare_mc(rg, orc, M, rem)
+        assert set(rg) == set(rs)
+        for k in rg:
+            assert rg[k][0] == rs[k][0]
+            np.testing.assert_array_equal(dense_from_records(rg, k), dense_from_records(rs, k))
+        kg, Fg, Wg = g.dump()
+        ks, Fs, Ws = sep.dump()
+        np.testing.assert_array_equal(kg, ks)
+        np.testing.assert_array_equal(Fg, Fs)
+        np.testing.assert_array_equal(Wg, Ws)
+    compare_volume(g, orc)
+    if timed:
+        ms, n = g.timing_read()
+        assert n["integrate"] == len(poses) and ms["integrate"] > 0
+    assert g.counters().kernel_launches == 8 * len(poses)
