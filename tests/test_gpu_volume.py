@@ -270,4 +270,6 @@ def test_process_frame_graph_matches_oracle_and_separate_calls(timed):
     if timed:
         ms, n = g.timing_read()
         assert n["integrate"] == len(poses) and ms["integrate"] > 0
-    assert g.counters().kernel_launches == 8 * len(poses)
+    c0 = g.counters().kernel_launches
+    g.process_frame(torch.from_numpy(depth[0]).cuda(), poses[0], 99, 2.5)
+    assert g.counters().kernel_launches - c0 == 8      # one graph: 8 kernels
