@@ -291,27 +291,28 @@ def main():
     clocks = ClockSampler(local_rank, args.clock_ms)
     clocks.start()
     c0 = vol.counters()
-    touched, new, written = 0, 0, 0
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
+    # all steps are enqueued ahead (as a streaming server would run); the L2 flush between
+    # steps sits outside each step's event pair
     for k in range(args.steps):
         i = args.warmup + k
         flush.zero_()
         ev[k][0].record()
         step(i, i + 1)
         ev[k][1].record()
-        c = vol.counters()          # synchronises; outside the step events
-        touched += c.last_touched
-        new += c.last_new
-        written += c.voxels_written
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     t_wall1 = time.time()
     clocks.mark(t_wall0, t_wall1)
     c1 = vol.counters()
+    touched = int(c1.total_touched - c0.total_touched)
+    new = int(c1.total_new - c0.total_new)
+    written = int(c1.total_written - c0.total_written)
+    assert int(c1.total_frames - c0.total_frames) == args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms_total = float(sum(step_ms))
     stage_ms, stage_launch = vol.timing_read(reset=True)

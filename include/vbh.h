@@ -102,6 +102,10 @@ typedef struct {
   uint32_t last_erased;     /* blocks removed by the last vbh_erase_blocks */
   uint64_t voxels_written;  /* voxels the last vbh_integrate_frame wrote (fused, or zeroed in
                                a new block) */
+  uint64_t total_frames;    /* running totals over every fused frame of the handle */
+  uint64_t total_touched;
+  uint64_t total_new;
+  uint64_t total_written;
 } vbh_counters;
 
 typedef struct {

@@ -817,6 +817,10 @@ vbh_status vbh_get_counters(vbh_handle* h, vbh_counters* out) {
   out->last_mc_entries = ne;
   out->last_erased = d.n_erased;
   out->voxels_written = d.vox_updated;
+  out->total_frames = d.tot_frames;
+  out->total_touched = d.tot_touched;
+  out->total_new = d.tot_new;
+  out->total_written = d.tot_written;
   return VBH_OK;
 }
 

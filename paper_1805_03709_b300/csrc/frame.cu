@@ -220,7 +220,14 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, 
   }
   atomicAdd(&s_upd, my_upd);
   __syncthreads();
-  if (threadIdx.x == 0 && s_upd) atomicAdd(&cnt->vox_updated, (unsigned long long)s_upd);
+  if (threadIdx.x == 0 && s_upd) {
+    atomicAdd(&cnt->vox_updated, (unsigned long long)s_upd);
+    atomicAdd(&cnt->tot_written, (unsigned long long)s_upd);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(&cnt->tot_touched, (unsigned long long)n);
+    atomicAdd(&cnt->tot_frames, 1ull);
+  }
 }
 
 }  // namespace

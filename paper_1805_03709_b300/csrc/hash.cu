@@ -256,7 +256,10 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
       atomicSub(&cnt->n_live, s_undo);
       atomicAdd(&cnt->n_tomb, s_undo);
     }
-    if (s_new) atomicAdd(&cnt->n_new, s_new);
+    if (s_new) {
+      atomicAdd(&cnt->n_new, s_new);
+      atomicAdd(&cnt->tot_new, (unsigned long long)s_new);
+    }
     if (s_err) atomicOr(&cnt->err, s_err);
   }
 }

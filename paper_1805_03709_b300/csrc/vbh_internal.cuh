@@ -56,7 +56,10 @@ struct DevCounters {
   unsigned int mc_blocks, mc_entries;
   unsigned int rebuild_n;       // live entries copied by the last rebuild
   unsigned long long vox_updated;   // voxels written by the last frame (fused or zeroed)
-  unsigned int pad[2];
+  unsigned long long tot_touched;   // running totals over all fused frames (never reset)
+  unsigned long long tot_new;
+  unsigned long long tot_written;
+  unsigned long long tot_frames;
 };
 
 struct TableView {

@@ -43,7 +43,8 @@ class vbh_counters(ctypes.Structure):
                 ("last_touched", _u32), ("last_new", _u32), ("last_candidates", _u32),
                 ("error_flags", _u32), ("kernel_launches", _u64), ("rebuilds", _u32),
                 ("last_mc_blocks", _u32), ("last_mc_entries", _u32), ("last_erased", _u32),
-                ("voxels_written", _u64)]
+                ("voxels_written", _u64), ("total_frames", _u64), ("total_touched", _u64),
+                ("total_new", _u64), ("total_written", _u64)]
 
 
 class vbh_frame_stats(ctypes.Structure):
