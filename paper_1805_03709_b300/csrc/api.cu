@@ -1,6 +1,9 @@
 // C ABI of libvbh (declared in include/vbh.h): handle lifetime, device memory, the ordering of
 // the launches of each call, timing and counters.  No entry point calls into PyTorch; all
 // compute runs in the kernels of hash.cu, frame.cu, erase.cu and mc.cu.
+#include <unistd.h>
+
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -73,8 +76,15 @@ struct vbh_handle {
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t frame_graph = nullptr;
   cudaGraphExec_t frame_exec = nullptr;
-  cudaGraphNode_t setup_node = nullptr;
-  cudaKernelNodeParams setup_params{};
+  // control blocks of vbh_process_frame travel through a pinned, device-mapped ring: the host
+  // writes slot (seq % kRing) and launches the graph; the graph's root kernel reads the next
+  // slot itself and reports the consumed sequence number back through mapped memory
+  FrameCtl* ring_host = nullptr;
+  FrameCtl* ring_dev = nullptr;
+  volatile unsigned long long* consumed_host = nullptr;
+  unsigned long long* consumed_dev = nullptr;
+  unsigned long long* dev_seq = nullptr;   // device memory
+  unsigned long long host_seq = 0;
   cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
   bool graph_timed = false;
   uint64_t graph_kernels = 0;
@@ -158,6 +168,36 @@ __global__ void k_setup(FrameCtl c, FrameCtl* dst, DevCounters* cnt) {
     cnt->n_mset = 0;
     cnt->n_tombrec = 0;
     if (c.n_entries_dev) *c.n_entries_dev = 0;
+  }
+}
+
+constexpr unsigned int kRing = 64;
+
+// Root node of the frame graph: fetch the next control block from the host ring (uncached
+// reads of mapped host memory), store it, zero the per-frame counters, acknowledge the slot.
+__global__ void k_setup_ring(const FrameCtl* ring, unsigned long long* dev_seq,
+                             unsigned long long* consumed, FrameCtl* dst, DevCounters* cnt) {
+  __shared__ FrameCtl c;
+  constexpr int kWords = sizeof(FrameCtl) / 4;
+  const unsigned long long seq = *dev_seq;
+  const unsigned int* src = reinterpret_cast<const unsigned int*>(ring + (seq % kRing));
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    reinterpret_cast<unsigned int*>(&c)[i] = __ldcv(src + i);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    reinterpret_cast<unsigned int*>(dst)[i] = reinterpret_cast<const unsigned int*>(&c)[i];
+  if (threadIdx.x == 0) {
+    cnt->n_cand = 0;
+    cnt->n_touched = 0;
+    cnt->n_new = 0;
+    cnt->vox_updated = 0ull;
+    cnt->n_erased = 0;
+    cnt->n_mset = 0;
+    cnt->n_tombrec = 0;
+    if (c.n_entries_dev) *c.n_entries_dev = 0;
+    *dev_seq = seq + 1;
+    __threadfence_system();
+    *reinterpret_cast<volatile unsigned long long*>(consumed) = seq + 1;
   }
 }
 
@@ -320,6 +360,17 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
   CREATE_CUDA(cudaMalloc(&h->cnt, sizeof(DevCounters)));
   CREATE_CUDA(cudaMalloc(&h->ctl, sizeof(FrameCtl)));
   CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CREATE_CUDA(cudaHostAlloc(&h->ring_host, kRing * sizeof(FrameCtl), cudaHostAllocMapped));
+  CREATE_CUDA(cudaHostGetDevicePointer((void**)&h->ring_dev, h->ring_host, 0));
+  {
+    unsigned long long* ch = nullptr;
+    CREATE_CUDA(cudaHostAlloc(&ch, sizeof(unsigned long long), cudaHostAllocMapped));
+    *ch = 0ull;
+    h->consumed_host = ch;
+    CREATE_CUDA(cudaHostGetDevicePointer((void**)&h->consumed_dev, ch, 0));
+  }
+  CREATE_CUDA(cudaMalloc(&h->dev_seq, sizeof(unsigned long long)));
+  CREATE_CUDA(cudaMemsetAsync(h->dev_seq, 0, sizeof(unsigned long long), h->stream));
   CREATE_CUDA(cudaMallocHost(&h->snap, sizeof(DevCounters)));
   DevCounters init{};
   init.free_top = (int)c.max_blocks;
@@ -369,7 +420,9 @@ vbh_status vbh_destroy(vbh_handle* h) {
   if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
   if (h->frame_graph) cudaGraphDestroy(h->frame_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-  void* ptrs[] = {h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
+  if (h->ring_host) cudaFreeHost(h->ring_host);
+  if (h->consumed_host) cudaFreeHost((void*)h->consumed_host);
+  void* ptrs[] = {h->dev_seq, h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
                   h->version, h->stack, h->cand, h->cand_res, h->cand_st, h->touched, h->mset,
                   h->removed, h->tombrec};
   for (void* p : ptrs)
@@ -487,8 +540,8 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
     eb = h->get_event();
   }
   VBH_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
-  FrameCtl c{};
-  k_setup<<<1, 32, 0, h->cap_stream>>>(c, h->ctl, h->cnt);
+  k_setup_ring<<<1, 64, 0, h->cap_stream>>>(h->ring_dev, h->dev_seq, h->consumed_dev, h->ctl,
+                                            h->cnt);
   launch_erase_radius(Lc, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks, nullptr,
                       nullptr);
   launch_alloc_keys(Lc, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
@@ -509,11 +562,6 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
     return fail(VBH_ERR_CUDA, std::string("frame graph capture: ") +
                                   cudaGetErrorString(e != cudaSuccess ? e : le));
   h->frame_graph = g;
-  size_t nroot = 0;
-  VBH_CUDA(cudaGraphGetRootNodes(g, nullptr, &nroot));
-  if (nroot != 1) return fail(VBH_ERR_CUDA, "frame graph: expected one root node");
-  VBH_CUDA(cudaGraphGetRootNodes(g, &h->setup_node, &nroot));
-  VBH_CUDA(cudaGraphKernelNodeGetParams(h->setup_node, &h->setup_params));
   if (timed) {
     size_t n = 0;
     VBH_CUDA(cudaGraphGetNodes(g, nullptr, &n));
@@ -565,13 +613,18 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
   c.clear_removed = 1;
   c.reset = kResetFrame | kResetErase | kResetMset;
   set_stream_out(c, out);
-  FrameCtl* dst = h->ctl;
-  DevCounters* cnt = h->cnt;
-  void* args[] = {&c, &dst, &cnt};
-  cudaKernelNodeParams p = h->setup_params;
-  p.kernelParams = args;
-  p.extra = nullptr;
-  VBH_CUDA(cudaGraphExecKernelNodeSetParams(h->frame_exec, h->setup_node, &p));
+  // wait (bounded) until the graph launched kRing frames ago has consumed this slot
+  const unsigned long long seq = h->host_seq;
+  if (seq >= kRing) {
+    const unsigned long long need = seq - kRing + 1;
+    int spins = 0;
+    while (*h->consumed_host < need) {
+      if (++spins > 2000000) return fail(VBH_ERR_TIMEOUT, "frame ring slot not consumed");
+      if (spins > 1000) usleep(5);
+    }
+  }
+  h->ring_host[seq % kRing] = c;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
   if (timed) {
     cudaEvent_t a = h->get_event(), b = h->get_event();
     VBH_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->frame_exec, h->ev_node[0], a));
@@ -581,6 +634,7 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
     h->stage_launches[VBH_STAGE_INTEGRATE] += 1;
   }
   VBH_CUDA(cudaGraphLaunch(h->frame_exec, h->stream));
+  h->host_seq = seq + 1;
   h->launches += h->graph_kernels;
   h->frame_version = frame_id;
   h->have_frame = true;

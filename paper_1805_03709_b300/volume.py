@@ -82,6 +82,12 @@ class McStream:
                    z(cap_entries, torch.int16), z(cap_entries, torch.uint8), z(2, torch.int32))
 
     def c_struct(self) -> V.vbh_mc_stream:
+        cs = self.__dict__.get("_cs")
+        if cs is None:
+            cs = self.__dict__["_cs"] = self._make_struct()
+        return cs
+
+    def _make_struct(self) -> V.vbh_mc_stream:
         return V.vbh_mc_stream(self.keys3.data_ptr(), self.info.data_ptr(), self.offsets.data_ptr(),
                                self.counts.data_ptr(), self.local.data_ptr(), self.index.data_ptr(),
                                self.info.shape[0], self.local.shape[0], self.n.data_ptr(),
