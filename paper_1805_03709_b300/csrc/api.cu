@@ -64,6 +64,7 @@ struct vbh_handle {
   unsigned int* cand_res = nullptr;
   unsigned char* cand_st = nullptr;
   unsigned int* touched = nullptr;
+  float2* tdepth = nullptr;        // camera depth of each touched block's origin (hi, lo)
   unsigned int* mset = nullptr;
   unsigned long long* removed = nullptr;
   unsigned long long* tombrec = nullptr;
@@ -403,6 +404,7 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
     CREATE_CUDA(cudaMalloc(&h->cand_res, (size_t)h->cand_cap * sizeof(unsigned int)));
     CREATE_CUDA(cudaMalloc(&h->cand_st, (size_t)h->cand_cap));
     CREATE_CUDA(cudaMalloc(&h->touched, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->tdepth, (size_t)nb * sizeof(float2)));
     CREATE_CUDA(cudaMalloc(&h->mset, (size_t)nb * sizeof(unsigned int)));
     CREATE_CUDA(cudaMalloc(&h->removed, (size_t)nb * sizeof(unsigned long long)));
     CREATE_CUDA(cudaMalloc(&h->tombrec, (size_t)nb * sizeof(unsigned long long)));
@@ -423,7 +425,7 @@ vbh_status vbh_destroy(vbh_handle* h) {
   if (h->ring_host) cudaFreeHost(h->ring_host);
   if (h->consumed_host) cudaFreeHost((void*)h->consumed_host);
   void* ptrs[] = {h->dev_seq, h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
-                  h->version, h->stack, h->cand, h->cand_res, h->cand_st, h->touched, h->mset,
+                  h->version, h->stack, h->cand, h->cand_res, h->cand_st, h->touched, h->tdepth, h->mset,
                   h->removed, h->tombrec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -464,7 +466,7 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   launch_hash_insert(h->L, t, pool, h->cnt, ops_dev, keys3_dev, nullptr, nullptr, vals_dev,
                      results_dev, status_dev, n);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, nullptr, results_dev, status_dev, n, nullptr,
-                            nullptr, nullptr);
+                            nullptr, nullptr, nullptr);
   launch_hash_erase(h->L, t, pool, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n);
   h->launches += 4;
   h->stage_end();
@@ -500,11 +502,11 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   launch_hash_insert(h->L, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
-                            h->cand_cap, h->touched, &h->cnt->n_touched, &h->ctl->epoch_touch);
+                            h->cand_cap, h->touched, h->tdepth, &h->cnt->n_touched, h->ctl);
   h->launches += 3;
   h->stage_end();
   h->stage_begin(VBH_STAGE_INTEGRATE);
-  launch_integrate(h->L, h->ctl, pool, h->touched, &h->cnt->n_touched, h->cnt);
+  launch_integrate(h->L, h->ctl, pool, h->touched, h->tdepth, &h->cnt->n_touched, h->cnt);
   h->launches += 1;
   h->stage_end();
   h->frame_version = frame_id;
@@ -548,9 +550,9 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
   launch_hash_insert(Lc, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(Lc, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
-                            h->cand_cap, h->touched, &h->cnt->n_touched, &h->ctl->epoch_touch);
+                            h->cand_cap, h->touched, h->tdepth, &h->cnt->n_touched, h->ctl);
   if (timed) cudaEventRecordWithFlags(ea, h->cap_stream, cudaEventRecordExternal);
-  launch_integrate(Lc, h->ctl, pool, h->touched, &h->cnt->n_touched, h->cnt);
+  launch_integrate(Lc, h->ctl, pool, h->touched, h->tdepth, &h->cnt->n_touched, h->cnt);
   if (timed) cudaEventRecordWithFlags(eb, h->cap_stream, cudaEventRecordExternal);
   launch_mset_touched(Lc, t, pool, h->cnt, h->ctl, h->touched, &h->cnt->n_touched, h->removed,
                       &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec);

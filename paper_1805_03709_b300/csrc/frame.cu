@@ -14,46 +14,14 @@
 //             valid iff 0 <= u < width and 0 <= v < height (compared as floats)
 //   band      fl(d - p_z) >= -mu
 // Values (the SDF fed into the running average) are computed more accurately than binary32:
-// the camera depth of each block's origin is formed as an unevaluated sum of two floats with
-// error-free transformations (TwoSum, Knuth; TwoProduct via FMA, Ogita, Rump and Oishi 2005),
-// so the per-voxel SDF error stays near 1e-8 m without any FP64 instruction.
+// the camera depth of each block's origin is formed once per touched block (block_depth, in the
+// kernel that builds the touched list) as an unevaluated sum of two floats with error-free
+// transformations, so the per-voxel SDF error stays near 1e-8 m without any FP64 instruction.
 #include "vbh_internal.cuh"
 
 namespace vbh {
 
 namespace {
-
-// s + e == a + b exactly (Knuth's TwoSum)
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return make_float2(s, e);
-}
-// p + e == a * b exactly (TwoProduct with a fused multiply-add)
-__device__ __forceinline__ float2 two_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return make_float2(p, __fmaf_rn(a, b, -p));
-}
-
-// Camera depth of the block origin, sum_i R_i2 (8 k_i s - t_i), as hi + lo floats.
-__device__ __forceinline__ float2 block_depth(const FrameParams& fp, int3 k) {
-  const int kk[3] = {k.x, k.y, k.z};
-  float hi = 0.f, lo = 0.f;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float2 P = two_prod((float)(8 * kk[i]), fp.s);     // 8 k s, exact
-    const float2 S = two_sum(P.x, -fp.t[i]);                 // (8 k s)_hi - t, exact
-    const float al = __fadd_rn(S.y, P.y);                    // a = S.x + al
-    const float r = fp.R[3 * i + 2];
-    const float2 Q = two_prod(r, S.x);
-    const float ql = __fmaf_rn(r, al, Q.y);
-    const float2 T = two_sum(hi, Q.x);
-    hi = T.x;
-    lo = __fadd_rn(lo, __fadd_rn(T.y, ql));
-  }
-  return two_sum(hi, lo);
-}
 
 constexpr int kTile = 16;            // 16 x 16 pixel tiles, one thread per pixel
 constexpr int kTileThreads = kTile * kTile;
@@ -142,11 +110,28 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
   }
 }
 
+// Interleave two 16-bit masks: bit i of `even` -> bit 2i, bit i of `odd` -> bit 2i + 1.
+__device__ __forceinline__ unsigned int interleave16(unsigned int even, unsigned int odd) {
+  unsigned int x = even & 0xFFFFu, y = odd & 0xFFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  y = (y | (y << 8)) & 0x00FF00FFu;
+  y = (y | (y << 4)) & 0x0F0F0F0Fu;
+  y = (y | (y << 2)) & 0x33333333u;
+  y = (y | (y << 1)) & 0x55555555u;
+  return x | (y << 1);
+}
+
 // Projective TSDF fusion of every voxel of every touched block; also rewrites the block's
-// sign / weight bit masks.  Thread t owns voxels t, t + 128, t + 256, t + 384, so every warp
-// load or store covers 256 contiguous bytes and each ballot yields one 32-voxel mask word.
+// sign / weight bit masks.  Thread t owns the voxel pairs q = t and t + 128 (voxels 2q, 2q + 1),
+// moved with one 16-byte access each, so a warp access covers 512 contiguous bytes.  The depth
+// fetch of all four voxels is issued unconditionally (clamped index, predicated use) so the
+// loads overlap.
 __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, PoolView pool,
                                                            const unsigned int* touched,
+                                                           const float2* tdepth,
                                                            const unsigned int* n_touched,
                                                            DevCounters* cnt) {
   __shared__ unsigned int s_upd;
@@ -157,13 +142,15 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, 
   const unsigned int n = *n_touched;
   const int t = threadIdx.x;
   const unsigned int lane = t & 31, warp = t >> 5;
-  const int lx = t & 7, ly = (t >> 3) & 7, lz0 = t >> 6;
-  const float flx = (float)lx, fly = (float)ly;
+  const int lx0 = 2 * (t & 3), ly = (t >> 2) & 7, lz0 = t >> 5;   // voxel (lx0 + e, ly, lz0 + 4j)
   // per-voxel part of the camera depth, s * (R_02 lx + R_12 ly + R_22 lz) (value path only)
-  float tau[4];
+  float tau[2][2];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    tau[j] = fp.s * fmaf(fp.R[8], (float)(lz0 + 2 * j), fmaf(fp.R[5], fly, fp.R[2] * flx));
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      tau[j][e] = fp.s * fmaf(fp.R[8], (float)(lz0 + 4 * j),
+                              fmaf(fp.R[5], (float)ly, fp.R[2] * (float)(lx0 + e)));
   unsigned int my_upd = 0;
   for (unsigned int b = blockIdx.x; b < n; b += gridDim.x) {
     const unsigned int p = touched[b];
@@ -171,49 +158,59 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, 
     if (t == 0) s_fresh = pool.state[p] & kFresh;
     __syncthreads();
     const bool fresh = s_fresh != 0;
-    float2* vox = pool.vox + 512ull * p;
-    float2 v[4];
+    float4* vox = reinterpret_cast<float4*>(pool.vox + 512ull * p);
+    float4 v[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = fresh ? make_float2(0.f, 0.f) : vox[t + 128 * j];
-    // camera depth of the block origin (every lane computes the same value; no divergence)
-    const float2 bd = block_depth(fp, k);
-    const float bhi = bd.x, blo = bd.y;
-    const float gx = (float)(8 * k.x + lx), gy = (float)(8 * k.y + ly);
-    const float dX = __fmaf_rn(gx, fp.s, -fp.t[0]);
+    for (int j = 0; j < 2; ++j) v[j] = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : vox[t + 128 * j];
+    const float2 bd = tdepth[b];
+    const float gy = (float)(8 * k.y + ly);
     const float dY = __fmaf_rn(gy, fp.s, -fp.t[1]);
+    float dX[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float gz = (float)(8 * k.z + lz0 + 2 * j);
-      const float dZ = __fmaf_rn(gz, fp.s, -fp.t[2]);
-      const float px = __fmaf_rn(fp.R[6], dZ, __fmaf_rn(fp.R[3], dY, __fmul_rn(fp.R[0], dX)));
-      const float py = __fmaf_rn(fp.R[7], dZ, __fmaf_rn(fp.R[4], dY, __fmul_rn(fp.R[1], dX)));
-      const float pz = __fmaf_rn(fp.R[8], dZ, __fmaf_rn(fp.R[5], dY, __fmul_rn(fp.R[2], dX)));
-      bool upd = false;
-      if (pz > 0.0f) {
+    for (int e = 0; e < 2; ++e) dX[e] = __fmaf_rn((float)(8 * k.x + lx0 + e), fp.s, -fp.t[0]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float dZ = __fmaf_rn((float)(8 * k.z + lz0 + 4 * j), fp.s, -fp.t[2]);
+      bool ok[2];
+      float dm[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float px = __fmaf_rn(fp.R[6], dZ, __fmaf_rn(fp.R[3], dY, __fmul_rn(fp.R[0], dX[e])));
+        const float py = __fmaf_rn(fp.R[7], dZ, __fmaf_rn(fp.R[4], dY, __fmul_rn(fp.R[1], dX[e])));
+        const float pz = __fmaf_rn(fp.R[8], dZ, __fmaf_rn(fp.R[5], dY, __fmul_rn(fp.R[2], dX[e])));
         const float r = __frcp_rn(pz);
         const float uf = floorf(__fmaf_rn(__fmul_rn(fp.fx, px), r, fp.cxh));
         const float vf = floorf(__fmaf_rn(__fmul_rn(fp.fy, py), r, fp.cyh));
-        if (uf >= 0.0f && uf < fp.fw && vf >= 0.0f && vf < fp.fh) {
-          const unsigned short raw = __ldg(fp.depth + (size_t)(int)vf * fp.width + (int)uf);
-          const float d = __fmul_rn((float)raw, fp.ds);
-          if (raw != 0 && !(fp.zmax > 0.0f && d > fp.zmax) && !(__fsub_rn(d, pz) < -fp.mu)) {
-            const float sdf = ((d - bhi) - blo) - tau[j];
-            const float f = fminf(1.0f, fmaxf(-1.0f, sdf * fp.inv_mu));
-            const float w = v[j].y;
-            v[j].x = v[j].x + __fdividef(f - v[j].x, w + 1.0f);
-            v[j].y = fminf(w + 1.0f, fp.wmax);
-            upd = true;
-          }
-        }
+        const bool in = pz > 0.0f && uf >= 0.0f && uf < fp.fw && vf >= 0.0f && vf < fp.fh;
+        const int idx = in ? (int)vf * fp.width + (int)uf : 0;
+        const unsigned short raw = __ldg(fp.depth + idx);
+        const float d = __fmul_rn((float)raw, fp.ds);
+        ok[e] = in && raw != 0 && !(fp.zmax > 0.0f && d > fp.zmax) && !(__fsub_rn(d, pz) < -fp.mu);
+        dm[e] = d;
       }
-      if (upd || fresh) vox[t + 128 * j] = v[j];
-      const unsigned int negm = __ballot_sync(0xFFFFFFFFu, v[j].x < 0.0f);
-      const unsigned int valm = __ballot_sync(0xFFFFFFFFu, v[j].y > 0.0f);
-      if (lane == 0) {
-        pool.masks[32u * p + warp + 4 * j] = negm;
-        pool.masks[32u * p + 16u + warp + 4 * j] = valm;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (!ok[e]) continue;
+        const float sdf = ((dm[e] - bd.x) - bd.y) - tau[j][e];
+        const float f = fminf(1.0f, fmaxf(-1.0f, sdf * fp.inv_mu));
+        float& F = e ? v[j].z : v[j].x;
+        float& W = e ? v[j].w : v[j].y;
+        F = F + __fdividef(f - F, W + 1.0f);
+        W = fminf(W + 1.0f, fp.wmax);
       }
-      my_upd += (upd || fresh);
+      const bool wr = fresh || ok[0] || ok[1];
+      if (wr) vox[t + 128 * j] = v[j];
+      my_upd += wr ? 2u : 0u;
+      const unsigned int ne = __ballot_sync(0xFFFFFFFFu, v[j].x < 0.0f);
+      const unsigned int no = __ballot_sync(0xFFFFFFFFu, v[j].z < 0.0f);
+      const unsigned int ve = __ballot_sync(0xFFFFFFFFu, v[j].y > 0.0f);
+      const unsigned int vo = __ballot_sync(0xFFFFFFFFu, v[j].w > 0.0f);
+      if (lane < 2) {   // lane 0: voxels of lanes 0-15, lane 1: lanes 16-31
+        const unsigned int sh = 16u * lane;
+        const unsigned int word = 2u * warp + 8u * j + lane;   // first voxel 64 warp + 256 j
+        pool.masks[32u * p + word] = interleave16(ne >> sh, no >> sh);
+        pool.masks[32u * p + 16u + word] = interleave16(ve >> sh, vo >> sh);
+      }
     }
     __syncthreads();
     if (t == 0 && fresh) pool.state[p] = 0u;
@@ -241,11 +238,11 @@ void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int heig
 }
 
 void launch_integrate(const Launch& L, const FrameCtl* ctl, PoolView pool,
-                      const unsigned int* touched, const unsigned int* n_touched,
-                      DevCounters* cnt) {
+                      const unsigned int* touched, const float2* tdepth,
+                      const unsigned int* n_touched, DevCounters* cnt) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_integrate, kIntThreads, L.sms);
-  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(ctl, pool, touched, n_touched, cnt);
+  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(ctl, pool, touched, tdepth, n_touched, cnt);
 }
 
 }  // namespace vbh

@@ -202,13 +202,14 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
                                                             unsigned int* res, unsigned char* st,
                                                             unsigned int n_cap,
                                                             unsigned int* touched,
+                                                            float2* tdepth,
                                                             unsigned int* n_touched,
-                                                            const unsigned int* epoch_dev) {
+                                                            const FrameCtl* ctl) {
   __shared__ unsigned int s_undo, s_new, s_err;
   if (threadIdx.x == 0) { s_undo = 0; s_new = 0; s_err = 0; }
   __syncthreads();
   const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
-  const unsigned int epoch = epoch_dev ? *epoch_dev : 0u;
+  const unsigned int epoch = ctl ? ctl->epoch_touch : 0u;
   if (blockIdx.x == 0 && threadIdx.x == 0 && pool.max_blocks) {
     int popped = (int)cnt->n_popped;
     cnt->free_top = max(cnt->free_top - popped, 0);
@@ -246,7 +247,11 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
       bool first = false;
       if (p != kNone) first = atomicExch(&pool.mark[p], epoch) != epoch;
       unsigned int k = warp_append(n_touched, first, 0xFFFFFFFFu);
-      if (first) touched[k] = p;
+      if (first) {
+        touched[k] = p;
+        // camera depth of the block origin for the fusion's value path, once per block
+        if (tdepth) tdepth[k] = block_depth(ctl->fp, unpack_key(pool.pkeys[p]));
+      }
       if (fresh_win) atomicAdd(&s_new, 1u);
     }
   }
@@ -439,11 +444,11 @@ void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
                                unsigned char* st, unsigned int n, unsigned int* touched,
-                               unsigned int* n_touched, const unsigned int* epoch) {
+                               float2* tdepth, unsigned int* n_touched, const FrameCtl* ctl) {
   VBH_GRID(k_insert_finish, kThreads);
   k_insert_finish<<<grid_k_insert_finish, kThreads, 0, L.stream>>>(t, pool, cnt, count_dev, res,
-                                                                    st, n, touched, n_touched,
-                                                                    epoch);
+                                                                    st, n, touched, tdepth,
+                                                                    n_touched, ctl);
 }
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const unsigned char* ops, const int* keys3, unsigned int* res,

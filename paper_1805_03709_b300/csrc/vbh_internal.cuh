@@ -193,6 +193,19 @@ __device__ __forceinline__ unsigned int warp_append(unsigned int* counter, bool 
   base = __shfl_sync(active_mask, base, (int)leader);
   return pred ? base + (unsigned)__popc(bal & ((1u << lane) - 1u)) : kNone;
 }
+// Error-free transformations: s + e == a + b exactly (Knuth's TwoSum); p + e == a * b exactly
+// (TwoProduct with a fused multiply-add; Ogita, Rump and Oishi 2005).
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return make_float2(p, __fmaf_rn(a, b, -p));
+}
+
 template <class K>
 inline int persistent_grid(K kernel, int threads, int sms) {
   int occ = 0;
@@ -243,6 +256,28 @@ struct FrameCtl {
   unsigned int cap_blocks, cap_entries;
 };
 
+#ifdef __CUDACC__
+// Camera depth of a block's origin, sum_i R_i2 (8 k_i s - t_i), as an unevaluated hi + lo sum
+// of floats (exact up to ~1e-13 m); feeds the value path of the fusion, never a decision.
+__device__ __forceinline__ float2 block_depth(const FrameParams& fp, int3 k) {
+  const int kk[3] = {k.x, k.y, k.z};
+  float hi = 0.f, lo = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float2 P = two_prod((float)(8 * kk[i]), fp.s);     // 8 k s, exact
+    const float2 S = two_sum(P.x, -fp.t[i]);                 // (8 k s)_hi - t, exact
+    const float al = __fadd_rn(S.y, P.y);                    // a = S.x + al
+    const float r = fp.R[3 * i + 2];
+    const float2 Q = two_prod(r, S.x);
+    const float ql = __fmaf_rn(r, al, Q.y);
+    const float2 T = two_sum(hi, Q.x);
+    hi = T.x;
+    lo = __fadd_rn(lo, __fadd_rn(T.y, ql));
+  }
+  return two_sum(hi, lo);
+}
+#endif
+
 // ------------------------------------------------------------------------------- host launchers
 struct Launch {
   cudaStream_t stream;
@@ -260,7 +295,7 @@ void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
                                unsigned char* st, unsigned int n, unsigned int* touched,
-                               unsigned int* n_touched, const unsigned int* epoch_dev);
+                               float2* tdepth, unsigned int* n_touched, const FrameCtl* ctl);
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const unsigned char* ops, const int* keys3, unsigned int* res,
                        unsigned char* st, unsigned int n);
@@ -281,8 +316,8 @@ void launch_block_masks(const Launch& L, PoolView pool, const unsigned int* idx,
 void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int height,
                        unsigned long long* cand, unsigned int cap, DevCounters* cnt);
 void launch_integrate(const Launch& L, const FrameCtl* ctl, PoolView pool,
-                      const unsigned int* touched, const unsigned int* n_touched,
-                      DevCounters* cnt);
+                      const unsigned int* touched, const float2* tdepth,
+                      const unsigned int* n_touched, DevCounters* cnt);
 
 // erase.cu
 void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
