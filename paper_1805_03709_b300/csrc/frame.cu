@@ -151,6 +151,14 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, 
     for (int e = 0; e < 2; ++e)
       tau[j][e] = fp.s * fmaf(fp.R[8], (float)(lz0 + 4 * j),
                               fmaf(fp.R[5], (float)ly, fp.R[2] * (float)(lx0 + e)));
+  // frame constants in registers (the shared copy would be re-read after every barrier)
+  const float R0 = fp.R[0], R1 = fp.R[1], R2 = fp.R[2], R3 = fp.R[3], R4 = fp.R[4],
+              R5 = fp.R[5], R6 = fp.R[6], R7 = fp.R[7], R8 = fp.R[8];
+  const float s = fp.s, t0 = fp.t[0], t1 = fp.t[1], t2 = fp.t[2];
+  const float fx = fp.fx, fy = fp.fy, cxh = fp.cxh, cyh = fp.cyh, fw = fp.fw, fh = fp.fh;
+  const float ds = fp.ds, zmax = fp.zmax, mu = fp.mu, inv_mu = fp.inv_mu, wmax = fp.wmax;
+  const int width = fp.width;
+  const unsigned short* __restrict__ depth = fp.depth;
   unsigned int my_upd = 0;
   for (unsigned int b = blockIdx.x; b < n; b += gridDim.x) {
     const unsigned int p = touched[b];
@@ -163,40 +171,44 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, 
 #pragma unroll
     for (int j = 0; j < 2; ++j) v[j] = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : vox[t + 128 * j];
     const float2 bd = tdepth[b];
-    const float gy = (float)(8 * k.y + ly);
-    const float dY = __fmaf_rn(gy, fp.s, -fp.t[1]);
-    float dX[2];
+    const float dY = __fmaf_rn((float)(8 * k.y + ly), s, -t1);
+    float ix[2], iy[2], iz[2];   // R_0j dX + R_1j dY, per voxel column e
 #pragma unroll
-    for (int e = 0; e < 2; ++e) dX[e] = __fmaf_rn((float)(8 * k.x + lx0 + e), fp.s, -fp.t[0]);
+    for (int e = 0; e < 2; ++e) {
+      const float dX = __fmaf_rn((float)(8 * k.x + lx0 + e), s, -t0);
+      ix[e] = __fmaf_rn(R3, dY, __fmul_rn(R0, dX));
+      iy[e] = __fmaf_rn(R4, dY, __fmul_rn(R1, dX));
+      iz[e] = __fmaf_rn(R5, dY, __fmul_rn(R2, dX));
+    }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      const float dZ = __fmaf_rn((float)(8 * k.z + lz0 + 4 * j), fp.s, -fp.t[2]);
+      const float dZ = __fmaf_rn((float)(8 * k.z + lz0 + 4 * j), s, -t2);
       bool ok[2];
       float dm[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        const float px = __fmaf_rn(fp.R[6], dZ, __fmaf_rn(fp.R[3], dY, __fmul_rn(fp.R[0], dX[e])));
-        const float py = __fmaf_rn(fp.R[7], dZ, __fmaf_rn(fp.R[4], dY, __fmul_rn(fp.R[1], dX[e])));
-        const float pz = __fmaf_rn(fp.R[8], dZ, __fmaf_rn(fp.R[5], dY, __fmul_rn(fp.R[2], dX[e])));
+        const float px = __fmaf_rn(R6, dZ, ix[e]);
+        const float py = __fmaf_rn(R7, dZ, iy[e]);
+        const float pz = __fmaf_rn(R8, dZ, iz[e]);
         const float r = __frcp_rn(pz);
-        const float uf = floorf(__fmaf_rn(__fmul_rn(fp.fx, px), r, fp.cxh));
-        const float vf = floorf(__fmaf_rn(__fmul_rn(fp.fy, py), r, fp.cyh));
-        const bool in = pz > 0.0f && uf >= 0.0f && uf < fp.fw && vf >= 0.0f && vf < fp.fh;
-        const int idx = in ? (int)vf * fp.width + (int)uf : 0;
-        const unsigned short raw = __ldg(fp.depth + idx);
-        const float d = __fmul_rn((float)raw, fp.ds);
-        ok[e] = in && raw != 0 && !(fp.zmax > 0.0f && d > fp.zmax) && !(__fsub_rn(d, pz) < -fp.mu);
+        const float uf = floorf(__fmaf_rn(__fmul_rn(fx, px), r, cxh));
+        const float vf = floorf(__fmaf_rn(__fmul_rn(fy, py), r, cyh));
+        const bool in = pz > 0.0f && uf >= 0.0f && uf < fw && vf >= 0.0f && vf < fh;
+        const int idx = in ? (int)vf * width + (int)uf : 0;
+        const unsigned short raw = __ldg(depth + idx);
+        const float d = __fmul_rn((float)raw, ds);
+        ok[e] = in && raw != 0 && !(zmax > 0.0f && d > zmax) && !(__fsub_rn(d, pz) < -mu);
         dm[e] = d;
       }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         if (!ok[e]) continue;
         const float sdf = ((dm[e] - bd.x) - bd.y) - tau[j][e];
-        const float f = fminf(1.0f, fmaxf(-1.0f, sdf * fp.inv_mu));
+        const float f = fminf(1.0f, fmaxf(-1.0f, sdf * inv_mu));
         float& F = e ? v[j].z : v[j].x;
         float& W = e ? v[j].w : v[j].y;
         F = F + __fdividef(f - F, W + 1.0f);
-        W = fminf(W + 1.0f, fp.wmax);
+        W = fminf(W + 1.0f, wmax);
       }
       const bool wr = fresh || ok[0] || ok[1];
       if (wr) vox[t + 128 * j] = v[j];
