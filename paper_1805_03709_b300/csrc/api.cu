@@ -64,6 +64,7 @@ struct vbh_handle {
   unsigned int* cand_res = nullptr;
   unsigned char* cand_st = nullptr;
   unsigned int* touched = nullptr;
+  unsigned long long* tkey = nullptr;   // key of each touched block
   float2* tdepth = nullptr;        // camera depth of each touched block's origin (hi, lo)
   unsigned int* mset = nullptr;
   unsigned long long* removed = nullptr;
@@ -405,6 +406,7 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
     CREATE_CUDA(cudaMalloc(&h->cand_st, (size_t)h->cand_cap));
     CREATE_CUDA(cudaMalloc(&h->touched, (size_t)nb * sizeof(unsigned int)));
     CREATE_CUDA(cudaMalloc(&h->tdepth, (size_t)nb * sizeof(float2)));
+    CREATE_CUDA(cudaMalloc(&h->tkey, (size_t)nb * sizeof(unsigned long long)));
     CREATE_CUDA(cudaMalloc(&h->mset, (size_t)nb * sizeof(unsigned int)));
     CREATE_CUDA(cudaMalloc(&h->removed, (size_t)nb * sizeof(unsigned long long)));
     CREATE_CUDA(cudaMalloc(&h->tombrec, (size_t)nb * sizeof(unsigned long long)));
@@ -425,7 +427,7 @@ vbh_status vbh_destroy(vbh_handle* h) {
   if (h->ring_host) cudaFreeHost(h->ring_host);
   if (h->consumed_host) cudaFreeHost((void*)h->consumed_host);
   void* ptrs[] = {h->dev_seq, h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
-                  h->version, h->stack, h->cand, h->cand_res, h->cand_st, h->touched, h->tdepth, h->mset,
+                  h->version, h->stack, h->cand, h->cand_res, h->cand_st, h->touched, h->tdepth, h->tkey, h->mset,
                   h->removed, h->tombrec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -466,7 +468,7 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   launch_hash_insert(h->L, t, pool, h->cnt, ops_dev, keys3_dev, nullptr, nullptr, vals_dev,
                      results_dev, status_dev, n);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, nullptr, results_dev, status_dev, n, nullptr,
-                            nullptr, nullptr, nullptr);
+                            nullptr, nullptr, nullptr, nullptr);
   launch_hash_erase(h->L, t, pool, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n);
   h->launches += 4;
   h->stage_end();
@@ -502,11 +504,13 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   launch_hash_insert(h->L, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
-                            h->cand_cap, h->touched, h->tdepth, &h->cnt->n_touched, h->ctl);
+                            h->cand_cap, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
+                            h->ctl);
   h->launches += 3;
   h->stage_end();
   h->stage_begin(VBH_STAGE_INTEGRATE);
-  launch_integrate(h->L, h->ctl, pool, h->touched, h->tdepth, &h->cnt->n_touched, h->cnt);
+  launch_integrate(h->L, h->ctl, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
+                   h->cnt);
   h->launches += 1;
   h->stage_end();
   h->frame_version = frame_id;
@@ -550,9 +554,11 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
   launch_hash_insert(Lc, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(Lc, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
-                            h->cand_cap, h->touched, h->tdepth, &h->cnt->n_touched, h->ctl);
+                            h->cand_cap, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
+                            h->ctl);
   if (timed) cudaEventRecordWithFlags(ea, h->cap_stream, cudaEventRecordExternal);
-  launch_integrate(Lc, h->ctl, pool, h->touched, h->tdepth, &h->cnt->n_touched, h->cnt);
+  launch_integrate(Lc, h->ctl, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
+                   h->cnt);
   if (timed) cudaEventRecordWithFlags(eb, h->cap_stream, cudaEventRecordExternal);
   launch_mset_touched(Lc, t, pool, h->cnt, h->ctl, h->touched, &h->cnt->n_touched, h->removed,
                       &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec);

@@ -110,48 +110,78 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
   }
 }
 
-// Interleave two 16-bit masks: bit i of `even` -> bit 2i, bit i of `odd` -> bit 2i + 1.
-__device__ __forceinline__ unsigned int interleave16(unsigned int even, unsigned int odd) {
-  unsigned int x = even & 0xFFFFu, y = odd & 0xFFFFu;
-  x = (x | (x << 8)) & 0x00FF00FFu;
-  x = (x | (x << 4)) & 0x0F0F0F0Fu;
-  x = (x | (x << 2)) & 0x33333333u;
-  x = (x | (x << 1)) & 0x55555555u;
-  y = (y | (y << 8)) & 0x00FF00FFu;
-  y = (y | (y << 4)) & 0x0F0F0F0Fu;
-  y = (y | (y << 2)) & 0x33333333u;
-  y = (y | (y << 1)) & 0x55555555u;
-  return x | (y << 1);
+// ---- asynchronous bulk copies into shared memory (completion counted on an mbarrier)
+__device__ __forceinline__ unsigned int smem_addr(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Arm the barrier for `bytes` and start one bulk copy global -> shared that completes them.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned int bytes,
+                                          unsigned long long* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait: false (and the sticky timeout flag) if the copy has not landed in time.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity,
+                                          DevCounters* cnt) {
+  for (unsigned int i = 0; i < (1u << 24); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(&cnt->err, kErrTimeout);
+  return false;
 }
 
 // Projective TSDF fusion of every voxel of every touched block; also rewrites the block's
-// sign / weight bit masks.  Thread t owns the voxel pairs q = t and t + 128 (voxels 2q, 2q + 1),
-// moved with one 16-byte access each, so a warp access covers 512 contiguous bytes.  The depth
-// fetch of all four voxels is issued unconditionally (clamped index, predicated use) so the
-// loads overlap.
+// sign / weight bit masks.  One warp owns one block at a time (no barriers between warps):
+// its 4 KiB of (TSDF, weight) arrive in shared memory by one bulk asynchronous copy, double
+// buffered so the next block streams in while this one is fused.  Lane L fuses voxels
+// L + 32 m (m = 0..15): shared-memory reads are conflict-free, global writes cover 256
+// contiguous bytes, and the ballot over voxel set m is mask word m.  The touched list carries
+// the pool index with the block's "fresh" bit, its key and its origin's camera depth.
+constexpr int kWarps = kIntThreads / 32;
+constexpr int kGroup = 4;   // voxels per lane whose depth fetches are in flight together
+
 __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, PoolView pool,
                                                            const unsigned int* touched,
+                                                           const unsigned long long* tkey,
                                                            const float2* tdepth,
                                                            const unsigned int* n_touched,
                                                            DevCounters* cnt) {
+  __shared__ __align__(128) float2 sbuf[kWarps][2][512];
+  __shared__ __align__(8) unsigned long long sbar[kWarps][2];
   __shared__ unsigned int s_upd;
-  __shared__ unsigned int s_fresh;
   __shared__ FrameParams fp;
   if (threadIdx.x == 0) s_upd = 0;
-  load_frame_params(fp, ctl);
+  const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    mbar_init(&sbar[warp][0]);
+    mbar_init(&sbar[warp][1]);
+    mbar_fence_init();
+  }
+  load_frame_params(fp, ctl);   // includes __syncthreads
   const unsigned int n = *n_touched;
-  const int t = threadIdx.x;
-  const unsigned int lane = t & 31, warp = t >> 5;
-  const int lx0 = 2 * (t & 3), ly = (t >> 2) & 7, lz0 = t >> 5;   // voxel (lx0 + e, ly, lz0 + 4j)
-  // per-voxel part of the camera depth, s * (R_02 lx + R_12 ly + R_22 lz) (value path only)
-  float tau[2][2];
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 2; ++e)
-      tau[j][e] = fp.s * fmaf(fp.R[8], (float)(lz0 + 4 * j),
-                              fmaf(fp.R[5], (float)ly, fp.R[2] * (float)(lx0 + e)));
-  // frame constants in registers (the shared copy would be re-read after every barrier)
+  const int lx = lane & 7, ly0 = lane >> 3;      // voxel (lx, ly0 + 4 (m & 1), m >> 1)
   const float R0 = fp.R[0], R1 = fp.R[1], R2 = fp.R[2], R3 = fp.R[3], R4 = fp.R[4],
               R5 = fp.R[5], R6 = fp.R[6], R7 = fp.R[7], R8 = fp.R[8];
   const float s = fp.s, t0 = fp.t[0], t1 = fp.t[1], t2 = fp.t[2];
@@ -159,37 +189,63 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, 
   const float ds = fp.ds, zmax = fp.zmax, mu = fp.mu, inv_mu = fp.inv_mu, wmax = fp.wmax;
   const int width = fp.width;
   const unsigned short* __restrict__ depth = fp.depth;
+  const float tx = R2 * (float)lx;
   unsigned int my_upd = 0;
-  for (unsigned int b = blockIdx.x; b < n; b += gridDim.x) {
-    const unsigned int p = touched[b];
-    const int3 k = unpack_key(pool.pkeys[p]);
-    if (t == 0) s_fresh = pool.state[p] & kFresh;
-    __syncthreads();
-    const bool fresh = s_fresh != 0;
-    float4* vox = reinterpret_cast<float4*>(pool.vox + 512ull * p);
-    float4 v[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) v[j] = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : vox[t + 128 * j];
+  unsigned int parity = 0u;   // bit q: phase to wait for on buffer q
+  const unsigned int stride = gridDim.x * kWarps;
+  unsigned int b = blockIdx.x * kWarps + warp;
+  unsigned int rec = 0;
+  if (b < n) {
+    rec = touched[b];
+    if (lane == 0 && !(rec & kTouchedFresh))
+      bulk_load(sbuf[warp][0], pool.vox + 512ull * (rec & ~kTouchedFresh), 4096u,
+                &sbar[warp][0]);
+  }
+  bool alive = true;
+  for (unsigned int it = 0; b < n && alive; ++it, b += stride) {
+    const unsigned int cur = it & 1u;
+    // start the next block's copy into the other buffer (read completely last iteration)
+    const unsigned int bn = b + stride;
+    unsigned int rec_next = 0;
+    if (bn < n) {
+      rec_next = touched[bn];
+      if (lane == 0 && !(rec_next & kTouchedFresh))
+        bulk_load(sbuf[warp][cur ^ 1u], pool.vox + 512ull * (rec_next & ~kTouchedFresh), 4096u,
+                  &sbar[warp][cur ^ 1u]);
+    }
+    const unsigned int p = rec & ~kTouchedFresh;
+    const bool fresh = (rec & kTouchedFresh) != 0;
+    const int3 k = unpack_key(tkey[b]);
     const float2 bd = tdepth[b];
-    const float dY = __fmaf_rn((float)(8 * k.y + ly), s, -t1);
-    float ix[2], iy[2], iz[2];   // R_0j dX + R_1j dY, per voxel column e
+    if (!fresh) {
+      if (!mbar_wait(&sbar[warp][cur], (parity >> cur) & 1u, cnt)) {
+        alive = false;   // a copy that never landed: stop this warp (flag already raised)
+        break;
+      }
+      parity ^= 1u << cur;
+    }
+    const float2* vin = sbuf[warp][cur];
+    float2* vout = pool.vox + 512ull * p;
+    const float dX = __fmaf_rn((float)(8 * k.x + lx), s, -t0);
+    float ix[2], iy[2], iz[2];   // R_0j dX + R_1j dY for the rows ly0 and ly0 + 4
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const float dX = __fmaf_rn((float)(8 * k.x + lx0 + e), s, -t0);
-      ix[e] = __fmaf_rn(R3, dY, __fmul_rn(R0, dX));
-      iy[e] = __fmaf_rn(R4, dY, __fmul_rn(R1, dX));
-      iz[e] = __fmaf_rn(R5, dY, __fmul_rn(R2, dX));
+    for (int h = 0; h < 2; ++h) {
+      const float dY = __fmaf_rn((float)(8 * k.y + ly0 + 4 * h), s, -t1);
+      ix[h] = __fmaf_rn(R3, dY, __fmul_rn(R0, dX));
+      iy[h] = __fmaf_rn(R4, dY, __fmul_rn(R1, dX));
+      iz[h] = __fmaf_rn(R5, dY, __fmul_rn(R2, dX));
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const float dZ = __fmaf_rn((float)(8 * k.z + lz0 + 4 * j), s, -t2);
-      bool ok[2];
-      float dm[2];
+    for (int g = 0; g < 16; g += kGroup) {
+      bool ok[kGroup];
+      float dm[kGroup];
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const float px = __fmaf_rn(R6, dZ, ix[e]);
-        const float py = __fmaf_rn(R7, dZ, iy[e]);
-        const float pz = __fmaf_rn(R8, dZ, iz[e]);
+      for (int i = 0; i < kGroup; ++i) {
+        const int m = g + i, h = m & 1, lz = m >> 1;
+        const float dZ = __fmaf_rn((float)(8 * k.z + lz), s, -t2);
+        const float px = __fmaf_rn(R6, dZ, ix[h]);
+        const float py = __fmaf_rn(R7, dZ, iy[h]);
+        const float pz = __fmaf_rn(R8, dZ, iz[h]);
         const float r = __frcp_rn(pz);
         const float uf = floorf(__fmaf_rn(__fmul_rn(fx, px), r, cxh));
         const float vf = floorf(__fmaf_rn(__fmul_rn(fy, py), r, cyh));
@@ -197,35 +253,40 @@ __global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, 
         const int idx = in ? (int)vf * width + (int)uf : 0;
         const unsigned short raw = __ldg(depth + idx);
         const float d = __fmul_rn((float)raw, ds);
-        ok[e] = in && raw != 0 && !(zmax > 0.0f && d > zmax) && !(__fsub_rn(d, pz) < -mu);
-        dm[e] = d;
+        ok[i] = in && raw != 0 && !(zmax > 0.0f && d > zmax) && !(__fsub_rn(d, pz) < -mu);
+        dm[i] = d;
       }
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        if (!ok[e]) continue;
-        const float sdf = ((dm[e] - bd.x) - bd.y) - tau[j][e];
-        const float f = fminf(1.0f, fmaxf(-1.0f, sdf * inv_mu));
-        float& F = e ? v[j].z : v[j].x;
-        float& W = e ? v[j].w : v[j].y;
-        F = F + __fdividef(f - F, W + 1.0f);
-        W = fminf(W + 1.0f, wmax);
-      }
-      const bool wr = fresh || ok[0] || ok[1];
-      if (wr) vox[t + 128 * j] = v[j];
-      my_upd += wr ? 2u : 0u;
-      const unsigned int ne = __ballot_sync(0xFFFFFFFFu, v[j].x < 0.0f);
-      const unsigned int no = __ballot_sync(0xFFFFFFFFu, v[j].z < 0.0f);
-      const unsigned int ve = __ballot_sync(0xFFFFFFFFu, v[j].y > 0.0f);
-      const unsigned int vo = __ballot_sync(0xFFFFFFFFu, v[j].w > 0.0f);
-      if (lane < 2) {   // lane 0: voxels of lanes 0-15, lane 1: lanes 16-31
-        const unsigned int sh = 16u * lane;
-        const unsigned int word = 2u * warp + 8u * j + lane;   // first voxel 64 warp + 256 j
-        pool.masks[32u * p + word] = interleave16(ne >> sh, no >> sh);
-        pool.masks[32u * p + 16u + word] = interleave16(ve >> sh, vo >> sh);
+      for (int i = 0; i < kGroup; ++i) {
+        const int m = g + i, h = m & 1, lz = m >> 1;
+        float2 v = fresh ? make_float2(0.f, 0.f) : vin[lane + 32 * m];
+        if (ok[i]) {
+          const float tau = s * fmaf(R8, (float)lz, fmaf(R5, (float)(ly0 + 4 * h), tx));
+          const float sdf = ((dm[i] - bd.x) - bd.y) - tau;
+          const float f = fminf(1.0f, fmaxf(-1.0f, sdf * inv_mu));
+          v.x = v.x + __fdividef(f - v.x, v.y + 1.0f);
+          v.y = fminf(v.y + 1.0f, wmax);
+        }
+        if (ok[i] || fresh) vout[lane + 32 * m] = v;
+        my_upd += (ok[i] || fresh) ? 1u : 0u;
+        const unsigned int negm = __ballot_sync(0xFFFFFFFFu, v.x < 0.0f);
+        const unsigned int valm = __ballot_sync(0xFFFFFFFFu, v.y > 0.0f);
+        if (lane == 0) {
+          pool.masks[32u * p + m] = negm;
+          pool.masks[32u * p + 16u + m] = valm;
+        }
       }
     }
-    __syncthreads();
-    if (t == 0 && fresh) pool.state[p] = 0u;
+    if (lane == 0 && fresh) pool.state[p] = 0u;
+    __syncwarp();   // every lane is done with buffer `cur` before it is refilled
+    rec = rec_next;
+  }
+  if (!alive) {
+    // wait (bounded) for this warp's copies still in flight before the CTA may exit
+    for (int q = 0; q < 2; ++q)
+      for (unsigned int i = 0; i < (1u << 20) && !mbar_try_wait(&sbar[warp][q], (parity >> q) & 1u);
+           ++i) {
+      }
   }
   atomicAdd(&s_upd, my_upd);
   __syncthreads();
@@ -250,11 +311,12 @@ void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int heig
 }
 
 void launch_integrate(const Launch& L, const FrameCtl* ctl, PoolView pool,
-                      const unsigned int* touched, const float2* tdepth,
-                      const unsigned int* n_touched, DevCounters* cnt) {
+                      const unsigned int* touched, const unsigned long long* tkey,
+                      const float2* tdepth, const unsigned int* n_touched, DevCounters* cnt) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_integrate, kIntThreads, L.sms);
-  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(ctl, pool, touched, tdepth, n_touched, cnt);
+  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(ctl, pool, touched, tkey, tdepth, n_touched,
+                                                  cnt);
 }
 
 }  // namespace vbh

@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
                                                             unsigned int* res, unsigned char* st,
                                                             unsigned int n_cap,
                                                             unsigned int* touched,
+                                                            unsigned long long* tkey,
                                                             float2* tdepth,
                                                             unsigned int* n_touched,
                                                             const FrameCtl* ctl) {
@@ -248,9 +249,11 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
       if (p != kNone) first = atomicExch(&pool.mark[p], epoch) != epoch;
       unsigned int k = warp_append(n_touched, first, 0xFFFFFFFFu);
       if (first) {
-        touched[k] = p;
-        // camera depth of the block origin for the fusion's value path, once per block
-        if (tdepth) tdepth[k] = block_depth(ctl->fp, unpack_key(pool.pkeys[p]));
+        // the record the fusion kernel reads: index + fresh bit, key, origin camera depth
+        const unsigned long long key = pool.pkeys[p];
+        touched[k] = p | ((pool.state[p] & kFresh) ? kTouchedFresh : 0u);
+        if (tkey) tkey[k] = key;
+        if (tdepth) tdepth[k] = block_depth(ctl->fp, unpack_key(key));
       }
       if (fresh_win) atomicAdd(&s_new, 1u);
     }
@@ -444,10 +447,11 @@ void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
                                unsigned char* st, unsigned int n, unsigned int* touched,
-                               float2* tdepth, unsigned int* n_touched, const FrameCtl* ctl) {
+                               unsigned long long* tkey, float2* tdepth,
+                               unsigned int* n_touched, const FrameCtl* ctl) {
   VBH_GRID(k_insert_finish, kThreads);
   k_insert_finish<<<grid_k_insert_finish, kThreads, 0, L.stream>>>(t, pool, cnt, count_dev, res,
-                                                                    st, n, touched, tdepth,
+                                                                    st, n, touched, tkey, tdepth,
                                                                     n_touched, ctl);
 }
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_mset_touched(TableView t, PoolView
       unsigned long long key;
       bool is_removed = b >= nt;
       if (!is_removed) {
-        const unsigned int p = touched[b];
+        const unsigned int p = touched[b] & ~kTouchedFresh;
         key = pool.pkeys[p];
         if (o == 0) q = key == kEmpty ? kNone : p;
       } else {

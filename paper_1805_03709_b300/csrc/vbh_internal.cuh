@@ -79,6 +79,10 @@ struct PoolView {
   unsigned int max_blocks;  // 0 for a plain map
 };
 
+// Touched-list entry: pool index in bits 0-30, bit 31 set when the block is fresh (allocated by
+// this frame, voxel data not yet written).
+constexpr unsigned int kTouchedFresh = 0x80000000u;
+
 // ------------------------------------------------------------------------------ keys, hashing
 __host__ __device__ __forceinline__ bool key_ok(int x, int y, int z) {
   return x >= -kKeyOffset && x < kKeyOffset && y >= -kKeyOffset && y < kKeyOffset &&
@@ -295,7 +299,8 @@ void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
                                unsigned char* st, unsigned int n, unsigned int* touched,
-                               float2* tdepth, unsigned int* n_touched, const FrameCtl* ctl);
+                               unsigned long long* tkey, float2* tdepth,
+                               unsigned int* n_touched, const FrameCtl* ctl);
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const unsigned char* ops, const int* keys3, unsigned int* res,
                        unsigned char* st, unsigned int n);
@@ -316,8 +321,8 @@ void launch_block_masks(const Launch& L, PoolView pool, const unsigned int* idx,
 void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int height,
                        unsigned long long* cand, unsigned int cap, DevCounters* cnt);
 void launch_integrate(const Launch& L, const FrameCtl* ctl, PoolView pool,
-                      const unsigned int* touched, const float2* tdepth,
-                      const unsigned int* n_touched, DevCounters* cnt);
+                      const unsigned int* touched, const unsigned long long* tkey,
+                      const float2* tdepth, const unsigned int* n_touched, DevCounters* cnt);
 
 // erase.cu
 void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
