@@ -159,12 +159,18 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int 
 // L + 32 m (m = 0..15): shared-memory reads are conflict-free, global writes cover 256
 // contiguous bytes, and the ballot over voxel set m is mask word m.  The touched list carries
 // the pool index with the block's "fresh" bit, its key and its origin's camera depth.
+#ifndef VBH_FUSE_GROUP
+#define VBH_FUSE_GROUP 4
+#endif
+#ifndef VBH_FUSE_MIN_CTAS
+#define VBH_FUSE_MIN_CTAS 1
+#endif
 constexpr int kWarps = kIntThreads / 32;
-constexpr int kGroup = 4;   // voxels per lane whose depth fetches are in flight together
+constexpr int kGroup = VBH_FUSE_GROUP;   // voxels per lane whose depth fetches overlap
 
-__global__ void __launch_bounds__(kIntThreads) k_integrate(const FrameCtl* ctl, PoolView pool,
-                                                           const unsigned int* touched,
-                                                           const unsigned long long* tkey,
+__global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
+    k_integrate(const FrameCtl* ctl, PoolView pool, const unsigned int* touched,
+                const unsigned long long* tkey,
                                                            const float2* tdepth,
                                                            const unsigned int* n_touched,
                                                            DevCounters* cnt) {
