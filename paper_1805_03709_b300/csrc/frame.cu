@@ -195,7 +195,12 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
   const float ds = fp.ds, zmax = fp.zmax, mu = fp.mu, inv_mu = fp.inv_mu, wmax = fp.wmax;
   const int width = fp.width;
   const unsigned short* __restrict__ depth = fp.depth;
-  const float tx = R2 * (float)lx;
+  // per-voxel part of the camera depth: tau(h, lz) = s (R_02 lx + R_12 ly + R_22 lz)
+  //                                              = base[h] + lz * s R_22   (value path only)
+  const float sR22 = s * R8;
+  float tbase[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) tbase[h] = s * fmaf(R5, (float)(ly0 + 4 * h), R2 * (float)lx);
   unsigned int my_upd = 0;
   unsigned int parity = 0u;   // bit q: phase to wait for on buffer q
   const unsigned int stride = gridDim.x * kWarps;
@@ -241,6 +246,9 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
       iy[h] = __fmaf_rn(R4, dY, __fmul_rn(R1, dX));
       iz[h] = __fmaf_rn(R5, dY, __fmul_rn(R2, dX));
     }
+    // low-order part of the block depth folded into the per-voxel offsets (value path)
+    const float tb0 = tbase[0] + bd.y, tb1 = tbase[1] + bd.y;
+    unsigned int mword = 0u;   // lane q < 16: sign mask word q; lane 16 + q: weight word q
 #pragma unroll
     for (int g = 0; g < 16; g += kGroup) {
       bool ok[kGroup];
@@ -267,22 +275,23 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
         const int m = g + i, h = m & 1, lz = m >> 1;
         float2 v = fresh ? make_float2(0.f, 0.f) : vin[lane + 32 * m];
         if (ok[i]) {
-          const float tau = s * fmaf(R8, (float)lz, fmaf(R5, (float)(ly0 + 4 * h), tx));
-          const float sdf = ((dm[i] - bd.x) - bd.y) - tau;
+          const float tau = fmaf((float)lz, sR22, h ? tb1 : tb0);
+          const float sdf = (dm[i] - bd.x) - tau;
           const float f = fminf(1.0f, fmaxf(-1.0f, sdf * inv_mu));
           v.x = v.x + __fdividef(f - v.x, v.y + 1.0f);
           v.y = fminf(v.y + 1.0f, wmax);
         }
-        if (ok[i] || fresh) vout[lane + 32 * m] = v;
-        my_upd += (ok[i] || fresh) ? 1u : 0u;
+        const bool wr = ok[i] || fresh;
+        if (wr) vout[lane + 32 * m] = v;
         const unsigned int negm = __ballot_sync(0xFFFFFFFFu, v.x < 0.0f);
         const unsigned int valm = __ballot_sync(0xFFFFFFFFu, v.y > 0.0f);
-        if (lane == 0) {
-          pool.masks[32u * p + m] = negm;
-          pool.masks[32u * p + 16u + m] = valm;
-        }
+        const unsigned int wrm = __ballot_sync(0xFFFFFFFFu, wr);
+        if (lane == (unsigned)m) mword = negm;
+        if (lane == 16u + m) mword = valm;
+        if (lane == 0) my_upd += __popc(wrm);
       }
     }
+    pool.masks[32u * p + lane] = mword;   // one coalesced 128 B store per block
     if (lane == 0 && fresh) pool.state[p] = 0u;
     __syncwarp();   // every lane is done with buffer `cur` before it is refilled
     rec = rec_next;
