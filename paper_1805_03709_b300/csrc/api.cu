@@ -181,6 +181,7 @@ __global__ void k_setup_ring(const FrameCtl* ring, unsigned long long* dev_seq,
                              unsigned long long* consumed, FrameCtl* dst, DevCounters* cnt) {
   __shared__ FrameCtl c;
   constexpr int kWords = sizeof(FrameCtl) / 4;
+  static_assert(kWords <= 128, "one word per thread of the 128-thread setup kernel");
   const unsigned long long seq = *dev_seq;
   const unsigned int* src = reinterpret_cast<const unsigned int*>(ring + (seq % kRing));
   for (int i = threadIdx.x; i < kWords; i += blockDim.x)
@@ -546,8 +547,9 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
     eb = h->get_event();
   }
   VBH_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
-  k_setup_ring<<<1, 64, 0, h->cap_stream>>>(h->ring_dev, h->dev_seq, h->consumed_dev, h->ctl,
-                                            h->cnt);
+  // one thread per word of the control block: a single round trip to host memory
+  k_setup_ring<<<1, 128, 0, h->cap_stream>>>(h->ring_dev, h->dev_seq, h->consumed_dev, h->ctl,
+                                             h->cnt);
   launch_erase_radius(Lc, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks, nullptr,
                       nullptr);
   launch_alloc_keys(Lc, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
