@@ -200,3 +200,72 @@ class OracleVolume:
         margin = np.zeros((n, 512), np.float32)
         lib().orc_vol_mc_dense(self._h, _p(k), n, _p(idx), _p(margin))
         return idx, margin
+
+
+# ------------------------------------------------------------------ differentiable window fusion
+def _diff_lib():
+    L = lib()
+    if not getattr(L, "_diff_bound", False):
+        P, U32, I32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
+        L.orc_se3_exp.argtypes = [P, P, P, P, P]
+        L.orc_diff_masks.argtypes = [P, I32, I32, I32, P, U32, P, P, P]
+        L.orc_diff_forward.argtypes = [P, I32, I32, I32, P, U32, P, P, P, P, P]
+        L.orc_diff_forward.restype = ctypes.c_double
+        L.orc_diff_backward.argtypes = [P, I32, I32, I32, P, U32, P, P, P, P, P, P]
+        L._diff_bound = True
+    return L
+
+
+def se3_exp(xi):
+    """Exponential map of an se(3) vector (rho, omega): R (3x3), t (3,), dR (6,3,3), dt (6,3)."""
+    xi = np.ascontiguousarray(xi, np.float64).reshape(6)
+    R = np.zeros(9)
+    t = np.zeros(3)
+    dR = np.zeros(54)
+    dt = np.zeros(18)
+    _diff_lib().orc_se3_exp(_p(xi), _p(R), _p(t), _p(dR), _p(dt))
+    return R.reshape(3, 3), t, dR.reshape(6, 3, 3), dt.reshape(6, 3)
+
+
+def nominal_pose_f32(xi):
+    """float32 3x4 [R | t] of exp(xi), the nominal pose at which cells and masks are fixed."""
+    R, t, _, _ = se3_exp(xi)
+    T = np.zeros((3, 4))
+    T[:, :3] = R
+    T[:, 3] = t
+    return T.astype(np.float32)
+
+
+class OracleDiffFusion:
+    """FP64 window fusion of float32 depth at fixed sample voxels, with its analytic gradient."""
+
+    def __init__(self, voxel_size, trunc, width, height, fx, fy, cx, cy, samples, depth, T0):
+        self.params = np.array([voxel_size, trunc, fx, fy, cx, cy], np.float32)
+        self.W, self.H = int(width), int(height)
+        self.samples = np.ascontiguousarray(samples, np.int32).reshape(-1, 3)
+        self.depth = np.ascontiguousarray(depth, np.float32)
+        self.nf = self.depth.shape[0]
+        assert self.depth.shape == (self.nf, self.H, self.W)
+        self.T0 = np.ascontiguousarray(T0, np.float32).reshape(self.nf, 12)
+        self.words = (self.nf + 31) // 32
+        self.masks = np.zeros((len(self.samples), self.words), np.uint32)
+        _diff_lib().orc_diff_masks(_p(self.params), self.W, self.H, self.nf, _p(self.samples),
+                                   len(self.samples), _p(self.depth), _p(self.T0), _p(self.masks))
+
+    def forward(self, xi, depth=None):
+        xi = np.ascontiguousarray(xi, np.float64).reshape(self.nf, 6)
+        d = self.depth if depth is None else np.ascontiguousarray(depth, np.float32)
+        F = np.zeros(len(self.samples))
+        L = _diff_lib().orc_diff_forward(_p(self.params), self.W, self.H, self.nf,
+                                         _p(self.samples), len(self.samples), _p(d), _p(self.T0),
+                                         _p(xi), _p(self.masks), _p(F))
+        return L, F
+
+    def backward(self, xi):
+        xi = np.ascontiguousarray(xi, np.float64).reshape(self.nf, 6)
+        gd = np.zeros((self.nf, self.H, self.W))
+        gx = np.zeros((self.nf, 6))
+        _diff_lib().orc_diff_backward(_p(self.params), self.W, self.H, self.nf, _p(self.samples),
+                                      len(self.samples), _p(self.depth), _p(self.T0), _p(xi),
+                                      _p(self.masks), _p(gd), _p(gx))
+        return gd, gx

@@ -450,3 +450,292 @@ void orc_vol_mc_dense(void* h, const int32_t* keys3, uint32_t n, uint8_t* idx, f
 int orc_abi_version() { return 1; }
 
 }  // extern "C"
+
+// =============================================================================================
+// Differentiable window fusion (the backward-pass extension of the fusion step; not in the
+// paper).  Readings:
+//   R-diff-1 a window of n_f frames of float32 metric depth (0 = invalid) is fused at a fixed
+//            set of sample voxels g (world position g s); the value of a sample is the plain
+//            mean F = sum_f m_f f_f / sum_f m_f over the frames where it is valid (the weight cap
+//            never binds: n_f <= Wmax), with f_f = clamp(sdf_f / mu, -1, 1) and
+//            sdf_f = D_f(u, v) - p_z, D_f bilinear in the depth image; L = sum_samples F^2.
+//   R-diff-2 poses are absolute se(3) vectors xi = (rho, omega): R = exp([omega]x) (Rodrigues),
+//            t = V(omega) rho with V = I + B [omega]x + C [omega]x^2.
+//   R-diff-3 the validity m_f and the bilinear cell (iu, iv) of every sample and frame are fixed
+//            at nominal float32 poses T0 with canonical binary32 arithmetic: p = R0^T (g s - t0)
+//            (fma chain as in fusion), u = fma(fl(fx p_x), fl(1/p_z), cx), iu = floor(u) (same
+//            for v); valid iff p_z > 0, the 2 x 2 cell is inside the image, its four depths are
+//            > 0 and the canonical bilinear sdf at T0 is >= -mu.  At other poses the same cell
+//            is interpolated (linearly extended), which keeps L smooth in (xi, depth).
+namespace {
+
+struct Pose64 {
+  double R[9], t[3];
+  double dR[6][9];   // dR / dxi_k (zero for the rho components)
+  double dt[6][3];   // dt / dxi_k
+};
+
+void skew(const double w[3], double S[9]) {
+  S[0] = 0; S[1] = -w[2]; S[2] = w[1];
+  S[3] = w[2]; S[4] = 0; S[5] = -w[0];
+  S[6] = -w[1]; S[7] = w[0]; S[8] = 0;
+}
+void matmul3(const double A[9], const double B[9], double C[9]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+      C[3 * i + j] = s;
+    }
+}
+
+// Coefficients A = sin t / t, B = (1 - cos t) / t^2, C = (t - sin t) / t^3 of the exponential map
+// and their derivatives divided by t (A'/t, B'/t, C'/t), with Taylor series for small t.
+void exp_coeffs(double th, double* A, double* B, double* C, double* Ap, double* Bp, double* Cp) {
+  const double t2 = th * th;
+  if (th < 1e-3) {
+    *A = 1 - t2 / 6 + t2 * t2 / 120;
+    *B = 0.5 - t2 / 24 + t2 * t2 / 720;
+    *C = 1.0 / 6 - t2 / 120 + t2 * t2 / 5040;
+    *Ap = -1.0 / 3 + t2 / 30 - t2 * t2 / 840;
+    *Bp = -1.0 / 12 + t2 / 180 - t2 * t2 / 6720;
+    *Cp = -1.0 / 60 + t2 / 1260 - t2 * t2 / 60480;
+    return;
+  }
+  const double s = std::sin(th), c = std::cos(th);
+  *A = s / th;
+  *B = (1 - c) / t2;
+  *C = (th - s) / (t2 * th);
+  *Ap = (th * c - s) / (t2 * th);
+  *Bp = (th * s - 2 * (1 - c)) / (t2 * t2);
+  *Cp = (1 - c) / (t2 * t2) - 3 * (th - s) / (t2 * t2 * th);
+}
+
+void se3_exp(const double xi[6], Pose64& P) {
+  const double* rho = xi;
+  const double* w = xi + 3;
+  const double th = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double A, B, C, Ap, Bp, Cp;
+  exp_coeffs(th, &A, &B, &C, &Ap, &Bp, &Cp);
+  double W[9], W2[9];
+  skew(w, W);
+  matmul3(W, W, W2);
+  double V[9];
+  for (int i = 0; i < 9; ++i) {
+    const double I = (i % 4 == 0) ? 1.0 : 0.0;
+    P.R[i] = I + A * W[i] + B * W2[i];
+    V[i] = I + B * W[i] + C * W2[i];
+  }
+  for (int i = 0; i < 3; ++i) P.t[i] = V[3 * i] * rho[0] + V[3 * i + 1] * rho[1] + V[3 * i + 2] * rho[2];
+  for (int k = 0; k < 3; ++k) {   // rho components
+    for (int i = 0; i < 9; ++i) P.dR[k][i] = 0;
+    for (int i = 0; i < 3; ++i) P.dt[k][i] = V[3 * i + k];
+  }
+  for (int k = 0; k < 3; ++k) {   // omega components
+    double e[3] = {0, 0, 0};
+    e[k] = 1;
+    double E[9], EW[9], WE[9];
+    skew(e, E);
+    matmul3(E, W, EW);
+    matmul3(W, E, WE);
+    double dV[9];
+    for (int i = 0; i < 9; ++i) {
+      P.dR[3 + k][i] = Ap * w[k] * W[i] + A * E[i] + Bp * w[k] * W2[i] + B * (EW[i] + WE[i]);
+      dV[i] = Bp * w[k] * W[i] + B * E[i] + Cp * w[k] * W2[i] + C * (EW[i] + WE[i]);
+    }
+    for (int i = 0; i < 3; ++i)
+      P.dt[3 + k][i] = dV[3 * i] * rho[0] + dV[3 * i + 1] * rho[1] + dV[3 * i + 2] * rho[2];
+  }
+}
+
+struct DiffCfg {
+  float s, mu, fx, fy, cx, cy;
+  int W, H, nf;
+};
+
+// R-diff-3: canonical binary32 cell and validity at the nominal pose.
+bool diff_cell(const DiffCfg& c, const int* g, const float* T0, const float* D, int* iu, int* iv) {
+  float dX[3];
+  for (int i = 0; i < 3; ++i) dX[i] = std::fma((float)g[i], c.s, -T0[4 * i + 3]);
+  float p[3];
+  for (int j = 0; j < 3; ++j) {
+    float acc = T0[j] * dX[0];
+    acc = std::fma(T0[4 + j], dX[1], acc);
+    p[j] = std::fma(T0[8 + j], dX[2], acc);
+  }
+  if (!(p[2] > 0.0f)) return false;
+  const float r = 1.0f / p[2];
+  const float u = std::fma(c.fx * p[0], r, c.cx);
+  const float v = std::fma(c.fy * p[1], r, c.cy);
+  const float uf = std::floor(u), vf = std::floor(v);
+  if (!(uf >= 0.0f && uf <= (float)(c.W - 2) && vf >= 0.0f && vf <= (float)(c.H - 2))) return false;
+  const int a = (int)uf, b = (int)vf;
+  const float d00 = D[b * c.W + a], d10 = D[b * c.W + a + 1];
+  const float d01 = D[(b + 1) * c.W + a], d11 = D[(b + 1) * c.W + a + 1];
+  if (!(d00 > 0.0f && d10 > 0.0f && d01 > 0.0f && d11 > 0.0f)) return false;
+  const float fa = u - uf, fb = v - vf;
+  const float wa = 1.0f - fa, wb = 1.0f - fb;
+  const float w00 = wa * wb, w10 = fa * wb, w01 = wa * fb, w11 = fa * fb;
+  float Dv = w00 * d00;
+  Dv = std::fma(w10, d10, Dv);
+  Dv = std::fma(w01, d01, Dv);
+  Dv = std::fma(w11, d11, Dv);
+  const float sdf = Dv - p[2];
+  if (sdf < -c.mu) return false;
+  *iu = a;
+  *iv = b;
+  return true;
+}
+
+// One sample and frame at pose P (FP64): f, and (if grad) the derivatives of f wrt the four
+// cell depths, and wrt p; y = X - t.
+struct Term {
+  double f, dfdD[4], dfdp[3], y[3];
+  int idx[4];
+  bool live;   // |sdf / mu| < 1 (inside the clamp)
+};
+
+Term diff_term(const DiffCfg& c, const int* g, const Pose64& P, const float* D, int iu, int iv) {
+  Term T;
+  double p[3];
+  for (int i = 0; i < 3; ++i) T.y[i] = (double)g[i] * (double)c.s - P.t[i];
+  for (int j = 0; j < 3; ++j) p[j] = P.R[j] * T.y[0] + P.R[3 + j] * T.y[1] + P.R[6 + j] * T.y[2];
+  const double u = (double)c.fx * p[0] / p[2] + (double)c.cx;
+  const double v = (double)c.fy * p[1] / p[2] + (double)c.cy;
+  const double a = u - iu, b = v - iv;
+  T.idx[0] = iv * c.W + iu;
+  T.idx[1] = iv * c.W + iu + 1;
+  T.idx[2] = (iv + 1) * c.W + iu;
+  T.idx[3] = (iv + 1) * c.W + iu + 1;
+  const double d00 = D[T.idx[0]], d10 = D[T.idx[1]], d01 = D[T.idx[2]], d11 = D[T.idx[3]];
+  const double w[4] = {(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b};
+  const double Dv = w[0] * d00 + w[1] * d10 + w[2] * d01 + w[3] * d11;
+  const double sdf = Dv - p[2];
+  const double q = sdf / (double)c.mu;
+  T.live = q > -1.0 && q < 1.0;
+  T.f = std::min(1.0, std::max(-1.0, q));
+  const double k = T.live ? 1.0 / (double)c.mu : 0.0;
+  for (int i = 0; i < 4; ++i) T.dfdD[i] = k * w[i];
+  const double dDdu = (1 - b) * (d10 - d00) + b * (d11 - d01);
+  const double dDdv = (1 - a) * (d01 - d00) + a * (d11 - d10);
+  const double iz = 1.0 / p[2];
+  T.dfdp[0] = k * dDdu * c.fx * iz;
+  T.dfdp[1] = k * dDdv * c.fy * iz;
+  T.dfdp[2] = k * (-dDdu * c.fx * p[0] * iz * iz - dDdv * c.fy * p[1] * iz * iz - 1.0);
+  return T;
+}
+
+DiffCfg diff_cfg(const float* params, int W, int H, int nf) {
+  DiffCfg c;
+  c.s = params[0]; c.mu = params[1]; c.fx = params[2]; c.fy = params[3]; c.cx = params[4];
+  c.cy = params[5]; c.W = W; c.H = H; c.nf = nf;
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Exponential map with derivatives (for tests).  R[9], t[3], dR[6*9], dt[6*3] (row-major).
+void orc_se3_exp(const double* xi, double* R, double* t, double* dR, double* dt) {
+  Pose64 P;
+  se3_exp(xi, P);
+  std::memcpy(R, P.R, sizeof P.R);
+  std::memcpy(t, P.t, sizeof P.t);
+  if (dR) std::memcpy(dR, P.dR, sizeof P.dR);
+  if (dt) std::memcpy(dt, P.dt, sizeof P.dt);
+}
+
+// params: s, mu, fx, fy, cx, cy.  depth: nf * H * W float32; T0: nf * 12 float32;
+// masks: n * ceil(nf / 32) uint32 (bit f of sample i: frame f valid).
+void orc_diff_masks(const float* params, int W, int H, int nf, const int32_t* samples, uint32_t n,
+                    const float* depth, const float* T0, uint32_t* masks) {
+  const DiffCfg c = diff_cfg(params, W, H, nf);
+  const int words = (nf + 31) / 32;
+  for (uint32_t i = 0; i < n; ++i) {
+    for (int w = 0; w < words; ++w) masks[(size_t)i * words + w] = 0;
+    for (int f = 0; f < nf; ++f) {
+      int iu, iv;
+      if (diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv))
+        masks[(size_t)i * words + f / 32] |= 1u << (f % 32);
+    }
+  }
+}
+
+// Forward (FP64): F per sample (may be null); returns L.  xi: nf * 6 doubles.
+double orc_diff_forward(const float* params, int W, int H, int nf, const int32_t* samples,
+                        uint32_t n, const float* depth, const float* T0, const double* xi,
+                        const uint32_t* masks, double* F) {
+  const DiffCfg c = diff_cfg(params, W, H, nf);
+  const int words = (nf + 31) / 32;
+  std::vector<Pose64> P(nf);
+  for (int f = 0; f < nf; ++f) se3_exp(xi + 6 * f, P[f]);
+  double L = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    double sum = 0;
+    int cnt = 0;
+    for (int f = 0; f < nf; ++f) {
+      if (!(masks[(size_t)i * words + f / 32] >> (f % 32) & 1u)) continue;
+      int iu, iv;
+      diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv);
+      sum += diff_term(c, samples + 3 * i, P[f], depth + (size_t)f * W * H, iu, iv).f;
+      ++cnt;
+    }
+    const double Fi = cnt ? sum / cnt : 0.0;
+    if (F) F[i] = Fi;
+    L += Fi * Fi;
+  }
+  return L;
+}
+
+// Backward (FP64): dL/d depth (nf * H * W doubles, overwritten) and dL/d xi (nf * 6 doubles).
+void orc_diff_backward(const float* params, int W, int H, int nf, const int32_t* samples,
+                       uint32_t n, const float* depth, const float* T0, const double* xi,
+                       const uint32_t* masks, double* gdepth, double* gxi) {
+  const DiffCfg c = diff_cfg(params, W, H, nf);
+  const int words = (nf + 31) / 32;
+  std::vector<Pose64> P(nf);
+  for (int f = 0; f < nf; ++f) se3_exp(xi + 6 * f, P[f]);
+  std::fill(gdepth, gdepth + (size_t)nf * W * H, 0.0);
+  std::fill(gxi, gxi + 6 * nf, 0.0);
+  std::vector<double> M(9 * nf, 0.0), G(3 * nf, 0.0);
+  for (uint32_t i = 0; i < n; ++i) {
+    std::vector<Term> terms;
+    std::vector<int> fr;
+    for (int f = 0; f < nf; ++f) {
+      if (!(masks[(size_t)i * words + f / 32] >> (f % 32) & 1u)) continue;
+      int iu, iv;
+      diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv);
+      terms.push_back(diff_term(c, samples + 3 * i, P[f], depth + (size_t)f * W * H, iu, iv));
+      fr.push_back(f);
+    }
+    if (terms.empty()) continue;
+    double sum = 0;
+    for (const Term& T : terms) sum += T.f;
+    const double Fi = sum / terms.size();
+    const double gf = 2.0 * Fi / terms.size();   // dL / df_f
+    for (size_t q = 0; q < terms.size(); ++q) {
+      const Term& T = terms[q];
+      const int f = fr[q];
+      for (int k = 0; k < 4; ++k) gdepth[(size_t)f * W * H + T.idx[k]] += gf * T.dfdD[k];
+      for (int a = 0; a < 3; ++a) {
+        const double gp = gf * T.dfdp[a];
+        G[3 * f + a] += gp;
+        for (int b = 0; b < 3; ++b) M[9 * f + 3 * b + a] += T.y[b] * gp;   // M = sum y g^T
+      }
+    }
+  }
+  for (int f = 0; f < nf; ++f) {
+    double RG[3];
+    for (int i = 0; i < 3; ++i)
+      RG[i] = P[f].R[3 * i] * G[3 * f] + P[f].R[3 * i + 1] * G[3 * f + 1] + P[f].R[3 * i + 2] * G[3 * f + 2];
+    for (int k = 0; k < 6; ++k) {
+      double acc = 0;
+      for (int e = 0; e < 9; ++e) acc += P[f].dR[k][e] * M[9 * f + e];
+      for (int i = 0; i < 3; ++i) acc -= RG[i] * P[f].dt[k][i];
+      gxi[6 * f + k] = acc;
+    }
+  }
+}
+
+}  // extern "C"

@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "Camera", "Scene", "make_tiny_scene", "make_room_scene", "render_depth_m",
     "quantize_mm", "tiny_sequence", "room_sequence", "room_frames", "room_camera", "look_at",
-    "random_hash_keys", "distinct_keys", "zipf_cluster_keys",
+    "random_hash_keys", "distinct_keys", "zipf_cluster_keys", "diff_window", "surface_samples",
 ]
 
 
@@ -314,3 +314,47 @@ def zipf_cluster_keys(n_draws: int, seed: int, hot_side: int = 64, s: float = 1.
     idx = order[rng.choice(n_hot, size=n_draws, p=p)]
     g = np.stack([idx % hot_side, (idx // hot_side) % hot_side, idx // (hot_side * hot_side)], -1)
     return (g + origin).astype(np.int32)
+
+
+def diff_window(n_frames: int = 64, width: int = 320, height: int = 240, f: float = 262.5,
+                seed: int = 1805, noise: bool = True, dropout: float = 0.02):
+    """Window of the room walk for differentiable fusion: float32 metric depth (0 = invalid),
+    the camera, the look-at poses (float32 3x4) and the same poses as se(3) vectors
+    xi = (rho, omega), read off the matrix logarithm of the 4x4 pose (scipy.linalg.logm)."""
+    import scipy.linalg
+    cam, poses, depth = room_sequence(n_frames, seed=seed, width=width, height=height,
+                                      f=f * 640.0 / width, noise=noise, dropout=dropout,
+                                      metric_depth=True)
+    xi = np.zeros((n_frames, 6))
+    for i, T in enumerate(poses):
+        M = np.eye(4)
+        M[:3, :] = T.astype(np.float64)
+        L = np.real(scipy.linalg.logm(M))
+        xi[i, :3] = L[:3, 3]
+        xi[i, 3:] = [L[2, 1], L[0, 2], L[1, 0]]
+    return cam, poses, xi, depth
+
+
+def surface_samples(cam: Camera, poses, depth_m, n: int, seed: int, voxel: float, band: float):
+    """`n` distinct voxel coordinates (int32, shape (n, 3)) near observed surfaces: random valid
+    pixels of random frames are lifted to world points, shifted by a uniform offset in
+    [-band, band]^3 and snapped to the voxel grid."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((0, 3), np.int64)
+    nf = len(poses)
+    while len(out) < n:
+        m = int((n - len(out)) * 1.3) + 64
+        f = rng.integers(0, nf, m)
+        u = rng.integers(0, cam.width, m)
+        v = rng.integers(0, cam.height, m)
+        d = depth_m[f, v, u].astype(np.float64)
+        ok = d > 0
+        f, u, v, d = f[ok], u[ok], v[ok], d[ok]
+        pc = np.stack([(u - cam.cx) / cam.fx * d, (v - cam.cy) / cam.fy * d, d], -1)
+        T = np.asarray(poses, np.float64)[f]
+        P = np.einsum("nij,nj->ni", T[:, :, :3], pc) + T[:, :, 3]
+        P += rng.uniform(-band, band, size=P.shape)
+        g = np.round(P / voxel).astype(np.int64)
+        out = np.unique(np.concatenate([out, g]), axis=0)
+    keep = rng.permutation(len(out))[:n]
+    return np.ascontiguousarray(out[keep].astype(np.int32))
