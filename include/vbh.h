@@ -245,6 +245,43 @@ vbh_status vbh_timing_enable(vbh_handle* h, int stage_mask);
 vbh_status vbh_timing_read(vbh_handle* h, double* ms_host /* VBH_N_STAGES */,
                            uint64_t* launches_host /* VBH_N_STAGES */, int reset);
 
+/* Differentiable window fusion -- forward and hand-written backward of the fusion of Sec. 4.1
+ * with respect to per-pixel depth and per-frame pose (an extension: the paper has no backward
+ * pass).  A window of n_frames float32 metric depth images (0 = invalid) is fused at fixed
+ * sample voxels g (world position g s); F(g) = mean over its valid frames of
+ * clamp(sdf / trunc, -1, 1), sdf = D(u, v) - p_z with D bilinear in the depth; L = sum F^2.
+ * Pose f is exp(xi_f) for an se(3) vector xi = (rho, omega) (rotation vector omega,
+ * t = V(omega) rho).  Validity and the bilinear cell of every (sample, frame) are fixed at
+ * nominal float32 poses T0 (3x4 row-major [R | t]) by canonical binary32 decisions, so L is
+ * smooth in (xi, depth) and the backward pass is exact for it; projections are recomputed in
+ * the backward pass, not stored.  All pointers are caller-owned device memory; calls are
+ * asynchronous on the handle's stream. */
+typedef struct {
+  float voxel_size, trunc;
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  uint32_t n_frames;             /* 1..256 */
+} vbh_diff_config;
+typedef struct vbh_diff vbh_diff;
+vbh_status vbh_diff_create(const vbh_diff_config* cfg, void* cuda_stream, vbh_diff** out);
+vbh_status vbh_diff_destroy(vbh_diff* d);
+/* exp of n_frames se(3) vectors xi_dev (n_frames x 6 float: rho, omega) into T_dev
+ * (n_frames x 12 float, [R | t]); T_dev may be NULL (the handle keeps the pose derivatives). */
+vbh_status vbh_diff_poses(vbh_diff* d, const float* xi_dev, float* T_dev);
+/* masks_dev: n x ceil(n_frames / 32) uint32, bit f of sample i set iff frame f is valid. */
+vbh_status vbh_diff_masks(vbh_diff* d, const int32_t* samples_dev, uint32_t n,
+                          const float* depth_dev, const float* T0_dev, uint32_t* masks_dev);
+/* F_dev: n floats; loss_dev: one double (may be NULL). */
+vbh_status vbh_diff_forward(vbh_diff* d, const int32_t* samples_dev, uint32_t n,
+                            const float* depth_dev, const float* T0_dev, const float* xi_dev,
+                            const uint32_t* masks_dev, float* F_dev, double* loss_dev);
+/* dL/d depth into gdepth_dev (n_frames x height x width floats, overwritten) and dL/d xi into
+ * gxi_dev (n_frames x 6 floats), given F_dev from the forward pass at the same xi. */
+vbh_status vbh_diff_backward(vbh_diff* d, const int32_t* samples_dev, uint32_t n,
+                             const float* depth_dev, const float* T0_dev, const float* xi_dev,
+                             const uint32_t* masks_dev, const float* F_dev, float* gdepth_dev,
+                             float* gxi_dev);
+
 /* Marching Cubes indices of a caller's TSDF blocks, allocating nothing.  The paper has no
  * counterpart: this is for callers that cannot call cudaMalloc -- code that runs inside another
  * framework's memory pool, real-time threads that must not risk an allocation's device-wide

@@ -1,0 +1,64 @@
+"""Differentiable window fusion behind torch.autograd.Function (marshalling only: the forward
+and the hand-written backward run in libvbh's kernels, see vbh_diff_* in include/vbh.h)."""
+from __future__ import annotations
+
+import torch
+
+from . import vbh as V
+
+
+class DiffFusion:
+    """Fixed sample voxels and nominal poses of one window; call `loss(depth, xi)`."""
+
+    def __init__(self, voxel_size, trunc, width, height, fx, fy, cx, cy, n_frames, samples,
+                 depth0, T0):
+        cfg = V.vbh_diff_config(voxel_size=voxel_size, trunc=trunc, width=width, height=height,
+                                fx=fx, fy=fy, cx=cx, cy=cy, n_frames=n_frames)
+        self.cfg = cfg
+        self.h = V.vbh_diff_create(cfg, torch.cuda.current_stream().cuda_stream)
+        self.samples = samples.to(torch.int32).contiguous()
+        self.T0 = T0.to(torch.float32).contiguous()
+        words = (n_frames + 31) // 32
+        self.masks = torch.empty((self.samples.shape[0], words), dtype=torch.int32,
+                                 device=self.samples.device)
+        V.vbh_diff_masks(self.h, self.samples, depth0.contiguous(), self.T0, self.masks)
+
+    def close(self):
+        if getattr(self, "h", None):
+            V.vbh_diff_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def forward_raw(self, depth, xi):
+        F = torch.empty(self.samples.shape[0], dtype=torch.float32, device=depth.device)
+        loss = torch.zeros((), dtype=torch.float64, device=depth.device)
+        V.vbh_diff_forward(self.h, self.samples, depth.contiguous(), self.T0, xi.contiguous(),
+                           self.masks, F, loss)
+        return loss, F
+
+    def backward_raw(self, depth, xi, F):
+        gd = torch.empty_like(depth)
+        gx = torch.empty_like(xi)
+        V.vbh_diff_backward(self.h, self.samples, depth.contiguous(), self.T0, xi.contiguous(),
+                            self.masks, F, gd, gx)
+        return gd, gx
+
+    def loss(self, depth: torch.Tensor, xi: torch.Tensor) -> torch.Tensor:
+        return _DiffFusionFn.apply(depth, xi, self)
+
+
+class _DiffFusionFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, depth, xi, module):
+        loss, F = module.forward_raw(depth, xi)
+        ctx.module = module
+        ctx.save_for_backward(depth, xi, F)
+        return loss
+
+    @staticmethod
+    def backward(ctx, g):
+        depth, xi, F = ctx.saved_tensors
+        gd, gx = ctx.module.backward_raw(depth, xi, F)
+        s = g.to(torch.float32)
+        return gd * s, gx * s, None

@@ -67,6 +67,11 @@ class vbh_mc_stream(ctypes.Structure):
                 ("n_blocks_dev", _p), ("n_entries_dev", _p)]
 
 
+class vbh_diff_config(ctypes.Structure):
+    _fields_ = [("voxel_size", _f32), ("trunc", _f32), ("width", _i32), ("height", _i32),
+                ("fx", _f32), ("fy", _f32), ("cx", _f32), ("cy", _f32), ("n_frames", _u32)]
+
+
 # every symbol include/vbh.h declares: (name, restype, argtypes)
 SYMBOLS = [
     ("vbh_abi_version", ctypes.c_int, []),
@@ -89,6 +94,13 @@ SYMBOLS = [
     ("vbh_clear_errors", ctypes.c_int, [_p]),
     ("vbh_timing_enable", ctypes.c_int, [_p, ctypes.c_int]),
     ("vbh_timing_read", ctypes.c_int, [_p, _p, _p, ctypes.c_int]),
+    ("vbh_diff_create", ctypes.c_int,
+     [ctypes.POINTER(vbh_diff_config), _p, ctypes.POINTER(_p)]),
+    ("vbh_diff_destroy", ctypes.c_int, [_p]),
+    ("vbh_diff_poses", ctypes.c_int, [_p, _p, _p]),
+    ("vbh_diff_masks", ctypes.c_int, [_p, _p, _u32, _p, _p, _p]),
+    ("vbh_diff_forward", ctypes.c_int, [_p, _p, _u32, _p, _p, _p, _p, _p, _p]),
+    ("vbh_diff_backward", ctypes.c_int, [_p, _p, _u32, _p, _p, _p, _p, _p, _p, _p]),
     ("vbh_mc_from_tsdf_static", ctypes.c_int,
      [_p, _p, _p, _u32, ctypes.POINTER(vbh_mc_stream), _p, _p]),
 ]
@@ -236,3 +248,33 @@ def vbh_mc_from_tsdf_static(keys3, tsdf, weight, out: vbh_mc_stream, stream=None
     _check(lib().vbh_mc_from_tsdf_static(_ptr(keys3), _ptr(tsdf), _ptr(weight),
                                          int(keys3.shape[0]), ctypes.byref(out), stream,
                                          _ptr(error_flags)), "vbh_mc_from_tsdf_static")
+
+
+def vbh_diff_create(cfg: vbh_diff_config, stream=None) -> int:
+    h = _p()
+    _check(lib().vbh_diff_create(ctypes.byref(cfg), stream, ctypes.byref(h)), "vbh_diff_create")
+    return h.value
+
+
+def vbh_diff_destroy(h):
+    _check(lib().vbh_diff_destroy(h), "vbh_diff_destroy")
+
+
+def vbh_diff_poses(h, xi, T=None):
+    _check(lib().vbh_diff_poses(h, _ptr(xi), _ptr(T)), "vbh_diff_poses")
+
+
+def vbh_diff_masks(h, samples, depth, T0, masks):
+    _check(lib().vbh_diff_masks(h, _ptr(samples), int(samples.shape[0]), _ptr(depth), _ptr(T0),
+                                _ptr(masks)), "vbh_diff_masks")
+
+
+def vbh_diff_forward(h, samples, depth, T0, xi, masks, F, loss=None):
+    _check(lib().vbh_diff_forward(h, _ptr(samples), int(samples.shape[0]), _ptr(depth), _ptr(T0),
+                                  _ptr(xi), _ptr(masks), _ptr(F), _ptr(loss)), "vbh_diff_forward")
+
+
+def vbh_diff_backward(h, samples, depth, T0, xi, masks, F, gdepth, gxi):
+    _check(lib().vbh_diff_backward(h, _ptr(samples), int(samples.shape[0]), _ptr(depth),
+                                   _ptr(T0), _ptr(xi), _ptr(masks), _ptr(F), _ptr(gdepth),
+                                   _ptr(gxi)), "vbh_diff_backward")
