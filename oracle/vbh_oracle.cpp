@@ -461,12 +461,14 @@ int orc_abi_version() { return 1; }
 //            sdf_f = D_f(u, v) - p_z, D_f bilinear in the depth image; L = sum_samples F^2.
 //   R-diff-2 poses are absolute se(3) vectors xi = (rho, omega): R = exp([omega]x) (Rodrigues),
 //            t = V(omega) rho with V = I + B [omega]x + C [omega]x^2.
-//   R-diff-3 the validity m_f and the bilinear cell (iu, iv) of every sample and frame are fixed
-//            at nominal float32 poses T0 with canonical binary32 arithmetic: p = R0^T (g s - t0)
-//            (fma chain as in fusion), u = fma(fl(fx p_x), fl(1/p_z), cx), iu = floor(u) (same
-//            for v); valid iff p_z > 0, the 2 x 2 cell is inside the image, its four depths are
-//            > 0 and the canonical bilinear sdf at T0 is >= -mu.  At other poses the same cell
-//            is interpolated (linearly extended), which keeps L smooth in (xi, depth).
+//   R-diff-3 the validity m_f, the bilinear cell (iu, iv) and the side of the truncation clamp of
+//            every sample and frame are fixed at nominal float32 poses T0 with canonical binary32
+//            arithmetic: p = R0^T (g s - t0) (fma chain as in fusion),
+//            u = fma(fl(fx p_x), fl(1/p_z), cx), iu = floor(u) (same for v); valid iff p_z > 0,
+//            the 2 x 2 cell is inside the image, its four depths are > 0 and the canonical
+//            bilinear sdf0 at T0 is >= -mu; the term is live (f = sdf / mu) iff sdf0 < mu, else
+//            it is saturated (f = 1).  At other poses the same cell is interpolated (linearly
+//            extended) and the same side is kept, which makes L smooth in (xi, depth).
 namespace {
 
 struct Pose64 {
@@ -554,7 +556,8 @@ struct DiffCfg {
 };
 
 // R-diff-3: canonical binary32 cell and validity at the nominal pose.
-bool diff_cell(const DiffCfg& c, const int* g, const float* T0, const float* D, int* iu, int* iv) {
+bool diff_cell(const DiffCfg& c, const int* g, const float* T0, const float* D, int* iu, int* iv,
+               bool* live) {
   float dX[3];
   for (int i = 0; i < 3; ++i) dX[i] = std::fma((float)g[i], c.s, -T0[4 * i + 3]);
   float p[3];
@@ -584,6 +587,7 @@ bool diff_cell(const DiffCfg& c, const int* g, const float* T0, const float* D, 
   if (sdf < -c.mu) return false;
   *iu = a;
   *iv = b;
+  *live = sdf < c.mu;
   return true;
 }
 
@@ -595,7 +599,8 @@ struct Term {
   bool live;   // |sdf / mu| < 1 (inside the clamp)
 };
 
-Term diff_term(const DiffCfg& c, const int* g, const Pose64& P, const float* D, int iu, int iv) {
+Term diff_term(const DiffCfg& c, const int* g, const Pose64& P, const float* D, int iu, int iv,
+               bool live) {
   Term T;
   double p[3];
   for (int i = 0; i < 3; ++i) T.y[i] = (double)g[i] * (double)c.s - P.t[i];
@@ -612,8 +617,8 @@ Term diff_term(const DiffCfg& c, const int* g, const Pose64& P, const float* D, 
   const double Dv = w[0] * d00 + w[1] * d10 + w[2] * d01 + w[3] * d11;
   const double sdf = Dv - p[2];
   const double q = sdf / (double)c.mu;
-  T.live = q > -1.0 && q < 1.0;
-  T.f = std::min(1.0, std::max(-1.0, q));
+  T.live = live;
+  T.f = live ? q : 1.0;
   const double k = T.live ? 1.0 / (double)c.mu : 0.0;
   for (int i = 0; i < 4; ++i) T.dfdD[i] = k * w[i];
   const double dDdu = (1 - b) * (d10 - d00) + b * (d11 - d01);
@@ -656,7 +661,8 @@ void orc_diff_masks(const float* params, int W, int H, int nf, const int32_t* sa
     for (int w = 0; w < words; ++w) masks[(size_t)i * words + w] = 0;
     for (int f = 0; f < nf; ++f) {
       int iu, iv;
-      if (diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv))
+      bool live;
+      if (diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv, &live))
         masks[(size_t)i * words + f / 32] |= 1u << (f % 32);
     }
   }
@@ -677,8 +683,9 @@ double orc_diff_forward(const float* params, int W, int H, int nf, const int32_t
     for (int f = 0; f < nf; ++f) {
       if (!(masks[(size_t)i * words + f / 32] >> (f % 32) & 1u)) continue;
       int iu, iv;
-      diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv);
-      sum += diff_term(c, samples + 3 * i, P[f], depth + (size_t)f * W * H, iu, iv).f;
+      bool live;
+      diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv, &live);
+      sum += diff_term(c, samples + 3 * i, P[f], depth + (size_t)f * W * H, iu, iv, live).f;
       ++cnt;
     }
     const double Fi = cnt ? sum / cnt : 0.0;
@@ -705,8 +712,9 @@ void orc_diff_backward(const float* params, int W, int H, int nf, const int32_t*
     for (int f = 0; f < nf; ++f) {
       if (!(masks[(size_t)i * words + f / 32] >> (f % 32) & 1u)) continue;
       int iu, iv;
-      diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv);
-      terms.push_back(diff_term(c, samples + 3 * i, P[f], depth + (size_t)f * W * H, iu, iv));
+      bool live;
+      diff_cell(c, samples + 3 * i, T0 + 12 * f, depth + (size_t)f * W * H, &iu, &iv, &live);
+      terms.push_back(diff_term(c, samples + 3 * i, P[f], depth + (size_t)f * W * H, iu, iv, live));
       fr.push_back(f);
     }
     if (terms.empty()) continue;

@@ -11,8 +11,9 @@
 //   * validity and the bilinear cell of every (sample, frame) are fixed at nominal float32 poses
 //     T0 by canonical binary32 arithmetic (p = R0^T (g s - t0) with the fusion's fma chain,
 //     u = fma(fl(fx p_x), fl(1/p_z), cx), cell = floor(u, v), valid iff p_z > 0, the 2 x 2 cell
-//     is inside the image, its four depths are > 0 and the canonical bilinear sdf >= -mu); at
-//     other poses the same cell is interpolated (linearly extended), so L is smooth.
+//     is inside the image, its four depths are > 0 and the canonical bilinear sdf0 >= -mu), and
+//     so is the side of the clamp (live, f = sdf / mu, iff sdf0 < mu; otherwise f = 1); at
+//     other poses the same cell and side are kept, so L is smooth.
 // The backward pass recomputes every projection instead of storing it; depth gradients are
 // scattered with atomics; pose gradients are reduced per frame as M = sum y g^T and G = sum g
 // (y = g s - t, g = dL/dp) and contracted with dR/dxi and dt/dxi once per frame:
@@ -123,7 +124,8 @@ __global__ void k_diff_poses(const float* xi_f, int nf, DiffPose* out, float* T_
 
 // Canonical binary32 cell and validity of sample g in frame f at the nominal pose T0.
 __device__ __forceinline__ bool diff_cell(const DiffParams& c, int gx, int gy, int gz,
-                                          const float* T0, const float* D, int* iu, int* iv) {
+                                          const float* T0, const float* D, int* iu, int* iv,
+                                          bool* live) {
   const float dX = __fmaf_rn((float)gx, c.s, -T0[3]);
   const float dY = __fmaf_rn((float)gy, c.s, -T0[7]);
   const float dZ = __fmaf_rn((float)gz, c.s, -T0[11]);
@@ -147,9 +149,11 @@ __device__ __forceinline__ bool diff_cell(const DiffParams& c, int gx, int gy, i
   Dv = __fmaf_rn(__fmul_rn(fa, wb), d10, Dv);
   Dv = __fmaf_rn(__fmul_rn(wa, fb), d01, Dv);
   Dv = __fmaf_rn(__fmul_rn(fa, fb), d11, Dv);
-  if (__fsub_rn(Dv, pz) < -c.mu) return false;
+  const float sdf0 = __fsub_rn(Dv, pz);
+  if (sdf0 < -c.mu) return false;
   *iu = a;
   *iv = b;
+  *live = sdf0 < c.mu;
   return true;
 }
 
@@ -165,7 +169,7 @@ struct DiffTerm {
 // Value of sample g in frame f at pose (R, t), on the fixed cell (iu, iv).
 __device__ __forceinline__ DiffTerm diff_term(const DiffParams& c, int gx, int gy, int gz,
                                               const float* R, const float* t, const float* D,
-                                              int iu, int iv) {
+                                              int iu, int iv, bool live) {
   DiffTerm T;
   T.y[0] = (float)gx * c.s - t[0];
   T.y[1] = (float)gy * c.s - t[1];
@@ -183,8 +187,7 @@ __device__ __forceinline__ DiffTerm diff_term(const DiffParams& c, int gx, int g
   T.w[3] = a * b;
   const float Dv = T.w[0] * d00 + T.w[1] * d10 + T.w[2] * d01 + T.w[3] * d11;
   const float q = (Dv - T.p[2]) * c.inv_mu;
-  const bool live = q > -1.0f && q < 1.0f;
-  T.f = fminf(1.0f, fmaxf(-1.0f, q));
+  T.f = live ? q : 1.0f;
   T.gs = live ? c.inv_mu : 0.0f;
   T.dDdu = (1.f - b) * (d10 - d00) + b * (d11 - d01);
   T.dDdv = (1.f - a) * (d01 - d00) + a * (d11 - d10);
@@ -204,7 +207,9 @@ __global__ void __launch_bounds__(kDiffThreads) k_diff_masks(DiffParams c, const
       unsigned int bits = 0;
       for (int f = 32 * w; f < min(c.nf, 32 * w + 32); ++f) {
         int iu, iv;
-        if (diff_cell(c, gx, gy, gz, sT0 + 12 * f, depth + (size_t)f * c.W * c.H, &iu, &iv))
+        bool live;
+        if (diff_cell(c, gx, gy, gz, sT0 + 12 * f, depth + (size_t)f * c.W * c.H, &iu, &iv,
+                      &live))
           bits |= 1u << (f - 32 * w);
       }
       masks[(size_t)s * c.words + w] = bits;
@@ -239,8 +244,9 @@ __global__ void __launch_bounds__(kDiffThreads) k_diff_forward(DiffParams c, con
         bits &= bits - 1u;
         const float* D = depth + (size_t)f * c.W * c.H;
         int iu = 0, iv = 0;
-        diff_cell(c, gx, gy, gz, sT0 + 12 * f, D, &iu, &iv);
-        sum += diff_term(c, gx, gy, gz, sRt + 12 * f, sRt + 12 * f + 9, D, iu, iv).f;
+        bool live = false;
+        diff_cell(c, gx, gy, gz, sT0 + 12 * f, D, &iu, &iv, &live);
+        sum += diff_term(c, gx, gy, gz, sRt + 12 * f, sRt + 12 * f + 9, D, iu, iv, live).f;
         ++cnt;
       }
     }
@@ -270,12 +276,12 @@ __global__ void __launch_bounds__(kDiffThreads) k_diff_backward(DiffParams c, co
                                                                 double* acc_MG) {
   __shared__ float sT0[kMaxDiffFrames * 12];
   __shared__ float sRt[kMaxDiffFrames * 12];
-  __shared__ float sMG[kMaxDiffFrames * 12];
+  __shared__ double sMG[kMaxDiffFrames * 12];
   for (int i = threadIdx.x; i < c.nf * 12; i += blockDim.x) {
     sT0[i] = T0[i];
     const int f = i / 12, e = i % 12;
     sRt[i] = e < 9 ? poses[f].R[e] : poses[f].t[e - 9];
-    sMG[i] = 0.f;
+    sMG[i] = 0.0;
   }
   __syncthreads();
   const unsigned int lane = threadIdx.x & 31;
@@ -299,8 +305,10 @@ __global__ void __launch_bounds__(kDiffThreads) k_diff_backward(DiffParams c, co
       if (valid) {
         const float* D = depth + (size_t)f * c.W * c.H;
         int iu = 0, iv = 0;
-        diff_cell(c, gx, gy, gz, sT0 + 12 * f, D, &iu, &iv);
-        const DiffTerm T = diff_term(c, gx, gy, gz, sRt + 12 * f, sRt + 12 * f + 9, D, iu, iv);
+        bool live = false;
+        diff_cell(c, gx, gy, gz, sT0 + 12 * f, D, &iu, &iv, &live);
+        const DiffTerm T =
+            diff_term(c, gx, gy, gz, sRt + 12 * f, sRt + 12 * f + 9, D, iu, iv, live);
         const float g = gF * T.gs;   // dL / dsdf
         if (g != 0.f) {
           float* GD = gdepth + (size_t)f * c.W * c.H;
@@ -317,12 +325,12 @@ __global__ void __launch_bounds__(kDiffThreads) k_diff_backward(DiffParams c, co
           y[2] = T.y[2];
         }
       }
-      // warp sums of M = y g^T (row b, column a) and G = g
-      float v[12];
+      // warp sums of M = y g^T (row b, column a) and G = g, in double (they cancel strongly)
+      double v[12];
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) v[3 * b + a] = y[b] * gp[a];
+        for (int a = 0; a < 3; ++a) v[3 * b + a] = (double)y[b] * (double)gp[a];
       v[9] = gp[0];
       v[10] = gp[1];
       v[11] = gp[2];
@@ -338,7 +346,7 @@ __global__ void __launch_bounds__(kDiffThreads) k_diff_backward(DiffParams c, co
   }
   __syncthreads();
   for (int i = threadIdx.x; i < c.nf * 12; i += blockDim.x)
-    if (sMG[i] != 0.f) atomicAdd(&acc_MG[i], (double)sMG[i]);
+    if (sMG[i] != 0.0) atomicAdd(&acc_MG[i], sMG[i]);
 }
 
 // dL/dxi per frame from the (M, G) accumulators.

@@ -50,13 +50,17 @@ def check(o, g, xi32, depth):
     loss, F = g.forward_raw(D, X)
     Lo, Fo = o.forward(xi32.astype(np.float64))
     err = np.abs(F.cpu().numpy() - Fo)
+    print("value err median %.2e q99 %.2e q999 %.2e max %.2e" % (np.median(err), np.quantile(err, 0.99), np.quantile(err, 0.999), err.max()))
+    print("loss rel", abs(float(loss) - Lo) / Lo)
+    gd, gx = g.backward_raw(D, X, F)
+    gdo, gxo = o.backward(xi32.astype(np.float64))
+    print("depth grad rel l2", rel_l2(gd.cpu().numpy().astype(np.float64), gdo))
+    gx = gx.cpu().numpy().astype(np.float64)
+    print("pose grad rel l2 per frame max", max(rel_l2(gx[f], gxo[f]) for f in range(gxo.shape[0])))
     assert np.median(err) < 1e-5 and np.quantile(err, 0.999) < 1e-4 and err.max() < 2e-2, \
         (np.median(err), np.quantile(err, 0.999), err.max())
     assert abs(float(loss) - Lo) <= 1e-5 * Lo
-    gd, gx = g.backward_raw(D, X, F)
-    gdo, gxo = o.backward(xi32.astype(np.float64))
     assert rel_l2(gd.cpu().numpy().astype(np.float64), gdo) < 1e-3
-    gx = gx.cpu().numpy().astype(np.float64)
     for f in range(gxo.shape[0]):
         assert rel_l2(gx[f], gxo[f]) < 1e-3, (f, gx[f], gxo[f])
     return float(loss)
