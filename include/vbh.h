@@ -252,7 +252,9 @@ vbh_status vbh_timing_read(vbh_handle* h, double* ms_host /* VBH_N_STAGES */,
  * clamp(sdf / trunc, -1, 1), sdf = D(u, v) - p_z with D bilinear in the depth; L = sum F^2.
  * Pose f is exp(xi_f) for an se(3) vector xi = (rho, omega) (rotation vector omega,
  * t = V(omega) rho).  Validity and the bilinear cell of every (sample, frame) are fixed at
- * nominal float32 poses T0 (3x4 row-major [R | t]) by canonical binary32 decisions, so L is
+ * nominal float32 poses T0 (3x4 row-major [R | t]) by canonical binary32 decisions (a cell is
+ * valid when its four depths are > 0 and span at most trunc, and its bilinear sdf >= -trunc;
+ * the term is live, f = sdf / trunc, when that sdf < trunc, else saturated, f = 1), so L is
  * smooth in (xi, depth) and the backward pass is exact for it; projections are recomputed in
  * the backward pass, not stored.  All pointers are caller-owned device memory; calls are
  * asynchronous on the handle's stream. */

@@ -465,7 +465,8 @@ int orc_abi_version() { return 1; }
 //            every sample and frame are fixed at nominal float32 poses T0 with canonical binary32
 //            arithmetic: p = R0^T (g s - t0) (fma chain as in fusion),
 //            u = fma(fl(fx p_x), fl(1/p_z), cx), iu = floor(u) (same for v); valid iff p_z > 0,
-//            the 2 x 2 cell is inside the image, its four depths are > 0 and the canonical
+//            the 2 x 2 cell is inside the image, its four depths are > 0 and span at most mu
+//            (max - min <= mu: no interpolation across a depth discontinuity) and the canonical
 //            bilinear sdf0 at T0 is >= -mu; the term is live (f = sdf / mu) iff sdf0 < mu, else
 //            it is saturated (f = 1).  At other poses the same cell is interpolated (linearly
 //            extended) and the same side is kept, which makes L smooth in (xi, depth).
@@ -576,6 +577,9 @@ bool diff_cell(const DiffCfg& c, const int* g, const float* T0, const float* D, 
   const float d00 = D[b * c.W + a], d10 = D[b * c.W + a + 1];
   const float d01 = D[(b + 1) * c.W + a], d11 = D[(b + 1) * c.W + a + 1];
   if (!(d00 > 0.0f && d10 > 0.0f && d01 > 0.0f && d11 > 0.0f)) return false;
+  const float dmax = std::max(std::max(d00, d10), std::max(d01, d11));
+  const float dmin = std::min(std::min(d00, d10), std::min(d01, d11));
+  if (dmax - dmin > c.mu) return false;
   const float fa = u - uf, fb = v - vf;
   const float wa = 1.0f - fa, wb = 1.0f - fb;
   const float w00 = wa * wb, w10 = fa * wb, w01 = wa * fb, w11 = fa * fb;

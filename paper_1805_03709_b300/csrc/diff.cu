@@ -11,7 +11,8 @@
 //   * validity and the bilinear cell of every (sample, frame) are fixed at nominal float32 poses
 //     T0 by canonical binary32 arithmetic (p = R0^T (g s - t0) with the fusion's fma chain,
 //     u = fma(fl(fx p_x), fl(1/p_z), cx), cell = floor(u, v), valid iff p_z > 0, the 2 x 2 cell
-//     is inside the image, its four depths are > 0 and the canonical bilinear sdf0 >= -mu), and
+//     is inside the image, its four depths are > 0 and span at most mu -- no interpolation
+//     across a depth discontinuity -- and the canonical bilinear sdf0 >= -mu), and
 //     so is the side of the clamp (live, f = sdf / mu, iff sdf0 < mu; otherwise f = 1); at
 //     other poses the same cell and side are kept, so L is smooth.
 // The backward pass recomputes every projection instead of storing it; depth gradients are
@@ -143,6 +144,9 @@ __device__ __forceinline__ bool diff_cell(const DiffParams& c, int gx, int gy, i
   const float d00 = D[b * c.W + a], d10 = D[b * c.W + a + 1];
   const float d01 = D[(b + 1) * c.W + a], d11 = D[(b + 1) * c.W + a + 1];
   if (!(d00 > 0.0f && d10 > 0.0f && d01 > 0.0f && d11 > 0.0f)) return false;
+  const float dmax = fmaxf(fmaxf(d00, d10), fmaxf(d01, d11));
+  const float dmin = fminf(fminf(d00, d10), fminf(d01, d11));
+  if (__fsub_rn(dmax, dmin) > c.mu) return false;
   const float fa = __fsub_rn(u, uf), fb = __fsub_rn(v, vf);
   const float wa = __fsub_rn(1.0f, fa), wb = __fsub_rn(1.0f, fb);
   float Dv = __fmul_rn(__fmul_rn(wa, wb), d00);

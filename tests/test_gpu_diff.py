@@ -3,10 +3,9 @@ FP64 oracle, through the C ABI and the torch.autograd.Function.
 
 Bar: validity masks bit-exact (canonical binary32 decisions); gradients within 1e-3 relative L2
 error per tensor (depth gradient) and per frame (pose gradient); loss within 1e-5 relative.
-Fused values: median error below 1e-5 and 99.9 % of samples below 1e-4 against FP64.  A sample
-whose bilinear cell straddles a depth edge (metres per pixel) amplifies the float32 projection
-error (~1e-5 px) by the depth gradient, so its value may differ by up to ~1e-2 there (any
-float32 evaluation does); the maximum is bounded at 2e-2."""
+Fused values within 1e-4 of FP64: cells span at most one truncation distance of depth, so the
+float32 projection error (~1e-5 px) moves the bilinear depth by at most ~2e-7 m (1e-5 of mu),
+and p_z carries ~5e-7 m (2.5e-5 of mu)."""
 import numpy as np
 import pytest
 import torch
@@ -57,8 +56,7 @@ def check(o, g, xi32, depth):
     print("depth grad rel l2", rel_l2(gd.cpu().numpy().astype(np.float64), gdo))
     gx = gx.cpu().numpy().astype(np.float64)
     print("pose grad rel l2 per frame max", max(rel_l2(gx[f], gxo[f]) for f in range(gxo.shape[0])))
-    assert np.median(err) < 1e-5 and np.quantile(err, 0.999) < 1e-4 and err.max() < 2e-2, \
-        (np.median(err), np.quantile(err, 0.999), err.max())
+    assert err.max() < 1e-4, (np.median(err), np.quantile(err, 0.999), err.max())
     assert abs(float(loss) - Lo) <= 1e-5 * Lo
     assert rel_l2(gd.cpu().numpy().astype(np.float64), gdo) < 1e-3
     for f in range(gxo.shape[0]):
