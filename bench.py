@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-diff", action="store_true",
+                    help="skip the differentiable-fusion timing (forward vs forward+backward)")
     ap.add_argument("--clock-ms", type=int, default=200,
                     help="nvidia-smi sampling interval during the timed region (0 = off)")
     ap.add_argument("--small-memory", action="store_true",
@@ -393,6 +395,9 @@ def main():
     hash_pt = None
     if not args.no_hash:
         hash_pt = hash_point(torch, dev, flush, peak)
+    diff_pt = None
+    if not args.no_diff:
+        diff_pt = diff_point(torch, dev, flush)
 
     if rank == 0:
         line = {
@@ -412,7 +417,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
-            "hash": hash_pt,
+            "hash": hash_pt, "diff": diff_pt,
         }
         print(json.dumps(line), flush=True)
     vol.close()
@@ -487,6 +492,42 @@ def hash_point(torch, dev, flush, peak):
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+def diff_point(torch, dev, flush, reps=10, warm=3):
+    """Differentiable window fusion at full size: 64 frames of 320x240 float32 depth from the
+    room walk, poses as se(3) twists, 2^20 seeded surface-near samples; forward (loss) against
+    forward + hand-written backward (dL/d depth, dL/d xi), CUDA events on the current stream,
+    L2 flushed (256 MiB write) before each timed repetition."""
+    from paper_1805_03709_b300 import synth
+    from paper_1805_03709_b300.diff import DiffFusion
+    nf, W, H, n = 64, 320, 240, 1 << 20
+    cam, poses, xi, depth = synth.diff_window(nf, W, H, f=262.5, seed=1805)
+    S = synth.surface_samples(cam, poses, depth, n, seed=1806, voxel=0.005, band=0.01)
+    D = torch.from_numpy(depth).to(dev)
+    X = torch.from_numpy(xi.astype(np.float32)).to(dev)
+    g = DiffFusion(0.005, 0.02, W, H, cam.fx, cam.fy, cam.cx, cam.cy, nf,
+                   torch.from_numpy(S).to(dev), D, xi0=X)
+    fwd, both = [], []
+    for r in range(warm + reps):
+        for mode in (0, 1):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            loss, F = g.forward_raw(D, X)
+            if mode:
+                gd, gx = g.backward_raw(D, X, F)
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= warm:
+                (both if mode else fwd).append(e0.elapsed_time(e1))
+    live = int(g.masks.ne(0).sum())
+    g.close()
+    f_ms, b_ms = statistics.median(fwd), statistics.median(both)
+    return {"window": "64 frames 320x240 f32 depth, se(3) poses, 2^20 samples, voxel 5 mm, "
+                      "trunc 2 cm", "fwd_ms": f_ms, "fwd_bwd_ms": b_ms, "bwd_ms": b_ms - f_ms,
+            "fwd_bwd_over_fwd": b_ms / f_ms, "reps": reps, "nonzero_mask_words": live,
+            "loss": float(loss)}
 
 
 if __name__ == "__main__":

@@ -8,15 +8,21 @@ from . import vbh as V
 
 
 class DiffFusion:
-    """Fixed sample voxels and nominal poses of one window; call `loss(depth, xi)`."""
+    """Fixed sample voxels and nominal poses of one window; call `loss(depth, xi)`.
+
+    `T0` (n_frames x 3 x 4 float32 [R | t]) fixes the masks and cells; pass `T0=None` and the
+    nominal twists `xi0` to take T0 = exp(xi0) rounded to float32 on the device."""
 
     def __init__(self, voxel_size, trunc, width, height, fx, fy, cx, cy, n_frames, samples,
-                 depth0, T0):
+                 depth0, T0=None, xi0=None):
         cfg = V.vbh_diff_config(voxel_size=voxel_size, trunc=trunc, width=width, height=height,
                                 fx=fx, fy=fy, cx=cx, cy=cy, n_frames=n_frames)
         self.cfg = cfg
         self.h = V.vbh_diff_create(cfg, torch.cuda.current_stream().cuda_stream)
         self.samples = samples.to(torch.int32).contiguous()
+        if T0 is None:
+            T0 = torch.empty((n_frames, 3, 4), dtype=torch.float32, device=samples.device)
+            V.vbh_diff_poses(self.h, xi0.to(torch.float32).contiguous(), T0)
         self.T0 = T0.to(torch.float32).contiguous()
         words = (n_frames + 31) // 32
         self.masks = torch.empty((self.samples.shape[0], words), dtype=torch.int32,

@@ -49,13 +49,9 @@ def check(o, g, xi32, depth):
     loss, F = g.forward_raw(D, X)
     Lo, Fo = o.forward(xi32.astype(np.float64))
     err = np.abs(F.cpu().numpy() - Fo)
-    print("value err median %.2e q99 %.2e q999 %.2e max %.2e" % (np.median(err), np.quantile(err, 0.99), np.quantile(err, 0.999), err.max()))
-    print("loss rel", abs(float(loss) - Lo) / Lo)
     gd, gx = g.backward_raw(D, X, F)
     gdo, gxo = o.backward(xi32.astype(np.float64))
-    print("depth grad rel l2", rel_l2(gd.cpu().numpy().astype(np.float64), gdo))
     gx = gx.cpu().numpy().astype(np.float64)
-    print("pose grad rel l2 per frame max", max(rel_l2(gx[f], gxo[f]) for f in range(gxo.shape[0])))
     assert err.max() < 1e-4, (np.median(err), np.quantile(err, 0.999), err.max())
     assert abs(float(loss) - Lo) <= 1e-5 * Lo
     assert rel_l2(gd.cpu().numpy().astype(np.float64), gdo) < 1e-3
@@ -85,7 +81,9 @@ def test_autograd_function_and_device_poses():
     L.backward()
     loss, F = g.forward_raw(D.detach(), X.detach())
     gd, gx = g.backward_raw(D.detach(), X.detach(), F)
-    assert torch.equal(D.grad, gd) and torch.equal(X.grad, gx)
+    # the depth gradient is accumulated with float atomics, whose order varies between runs
+    torch.testing.assert_close(D.grad, gd, rtol=1e-5, atol=1e-6 * float(gd.abs().max()))
+    torch.testing.assert_close(X.grad, gx, rtol=1e-5, atol=1e-6 * float(gx.abs().max()))
     # nominal poses computed on the device agree with the oracle's to float32 rounding
     from paper_1805_03709_b300 import vbh as V
     T = torch.empty((xi32.shape[0], 12), dtype=torch.float32, device="cuda")
