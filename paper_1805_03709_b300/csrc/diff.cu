@@ -16,9 +16,14 @@
 //     so is the side of the clamp (live, f = sdf / mu, iff sdf0 < mu; otherwise f = 1); at
 //     other poses the same cell and side are kept, so L is smooth.
 // The backward pass recomputes every projection instead of storing it; depth gradients are
-// scattered with atomics; pose gradients are reduced per frame as M = sum y g^T and G = sum g
-// (y = g s - t, g = dL/dp) and contracted with dR/dxi and dt/dxi once per frame:
-//   dL/dxi_k = sum_ij (dR/dxi_k)_ij M_ij - (R G) . dt/dxi_k.
+// scattered with atomics.  With p = R^T (x - t) and g = dL/dp, the pose gradient of one sample
+// is g . (R^T dR_k R p) - (R g) . dt_k; R^T dR_k is skew (R is a rotation), [k_k]x, so the
+// first term is k_k . (g x p) and every frame needs only two sums, G = sum g and C = sum g x p
+// (camera frame), contracted once per frame in FP64:
+//   dL/dxi_k = k_k . C - (R G) . dt_k,   k_k = vee(R^T dR/dxi_k).
+// G and C are summed in float within a thread's samples and over the warp, then in double per
+// warp and per CTA; the per-CTA partials are reduced in a fixed order, so the pose gradient is
+// deterministic.
 #include "vbh.h"
 #include "vbh_internal.cuh"
 
@@ -268,8 +273,34 @@ __global__ void __launch_bounds__(kDiffThreads) k_diff_forward(DiffParams c, con
   }
 }
 
-// Per sample: dL/dF = 2F, spread over its valid frames; depth gradient scattered with atomics,
-// per-frame (M, G) reduced over the warp and the CTA, then added to the global accumulators.
+// Sum of 8 per-lane values over the warp in 9 shuffles (each step halves the values a lane
+// carries); on return lane L holds the total of value L >> 2 (lanes with L & 3 == 0 hold them).
+__device__ __forceinline__ float warp_sum8(const float v[8], unsigned int lane) {
+  float w[4], x[2];
+  const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b4 ? v[i + 4] : v[i], send = b4 ? v[i] : v[i + 4];
+    w[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b3 ? w[i + 2] : w[i], send = b3 ? w[i] : w[i + 2];
+    x[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+  }
+  float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xFFFFFFFFu, b2 ? x[0] : x[1], 4);
+  y += __shfl_xor_sync(0xFFFFFFFFu, y, 2);
+  y += __shfl_xor_sync(0xFFFFFFFFu, y, 1);
+  return y;
+}
+
+constexpr int kDiffChunk = 4;   // samples a thread holds while it walks the frames
+
+// Per sample: dL/dF = 2F, spread over its valid frames; the depth gradient is scattered with
+// atomics; per frame, G = sum g and C = sum g x p are summed over the thread's chunk of samples
+// and the warp, accumulated in double per warp in shared memory, and written per CTA to
+// part[cta][frame][6].  Dynamic shared memory: T0 and (R, t) as floats (2 x 12 nf) and the
+// per-warp sums (warps x 6 nf doubles).
 __global__ void __launch_bounds__(kDiffThreads) k_diff_backward(DiffParams c, const int* samples,
                                                                 unsigned int n,
                                                                 const float* depth,
@@ -277,96 +308,123 @@ __global__ void __launch_bounds__(kDiffThreads) k_diff_backward(DiffParams c, co
                                                                 const DiffPose* poses,
                                                                 const unsigned int* masks,
                                                                 const float* F, float* gdepth,
-                                                                double* acc_MG) {
-  __shared__ float sT0[kMaxDiffFrames * 12];
-  __shared__ float sRt[kMaxDiffFrames * 12];
-  __shared__ double sMG[kMaxDiffFrames * 12];
+                                                                double* part) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  double* sW = reinterpret_cast<double*>(dsm);                      // [warps][nf * 6]
+  float* sT0 = reinterpret_cast<float*>(sW + (kDiffThreads / 32) * c.nf * 6);
+  float* sRt = sT0 + c.nf * 12;
   for (int i = threadIdx.x; i < c.nf * 12; i += blockDim.x) {
     sT0[i] = T0[i];
     const int f = i / 12, e = i % 12;
     sRt[i] = e < 9 ? poses[f].R[e] : poses[f].t[e - 9];
-    sMG[i] = 0.0;
   }
+  for (int i = threadIdx.x; i < (kDiffThreads / 32) * c.nf * 6; i += blockDim.x) sW[i] = 0.0;
   __syncthreads();
-  const unsigned int lane = threadIdx.x & 31;
-  const unsigned int stride = gridDim.x * blockDim.x;
-  const unsigned int rounds = (n + stride - 1) / stride;
-  for (unsigned int r = 0; r < rounds; ++r) {
-    const unsigned int s = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
-    const bool act = s < n;
-    int gx = 0, gy = 0, gz = 0, cnt = 0;
-    float gF = 0.f;
-    if (act) {
-      gx = samples[3u * s];
-      gy = samples[3u * s + 1];
-      gz = samples[3u * s + 2];
-      for (int w = 0; w < c.words; ++w) cnt += __popc(masks[(size_t)s * c.words + w]);
-      gF = cnt ? 2.0f * F[s] / (float)cnt : 0.f;
+  const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* myW = sW + warp * c.nf * 6;
+  const unsigned int nthreads = gridDim.x * blockDim.x;
+  const unsigned int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t npx = (size_t)c.W * c.H;
+  for (size_t base = 0; base < n; base += (size_t)kDiffChunk * nthreads) {
+    int gx[kDiffChunk], gy[kDiffChunk], gz[kDiffChunk];
+    float gF[kDiffChunk];
+    unsigned int sid[kDiffChunk], word[kDiffChunk];
+#pragma unroll
+    for (int j = 0; j < kDiffChunk; ++j) {
+      const size_t s = base + (size_t)j * nthreads + tid;
+      sid[j] = s < n ? (unsigned int)s : 0xFFFFFFFFu;
+      gx[j] = gy[j] = gz[j] = 0;
+      gF[j] = 0.f;
+      word[j] = 0u;
+      if (s < n) {
+        gx[j] = samples[3 * s];
+        gy[j] = samples[3 * s + 1];
+        gz[j] = samples[3 * s + 2];
+        int cnt = 0;
+        for (int w = 0; w < c.words; ++w) cnt += __popc(masks[s * c.words + w]);
+        gF[j] = cnt ? 2.0f * F[s] / (float)cnt : 0.f;
+      }
     }
-    for (int f = 0; f < c.nf; ++f) {   // frame loop in lockstep for the warp reductions
-      const bool valid = act && ((masks[(size_t)s * c.words + (f >> 5)] >> (f & 31)) & 1u);
-      float gp[3] = {0.f, 0.f, 0.f}, y[3] = {0.f, 0.f, 0.f};
-      if (valid) {
-        const float* D = depth + (size_t)f * c.W * c.H;
+    for (int f = 0; f < c.nf; ++f) {   // frames in lockstep over the warp for the reductions
+      if ((f & 31) == 0) {
+#pragma unroll
+        for (int j = 0; j < kDiffChunk; ++j)
+          word[j] = (sid[j] != 0xFFFFFFFFu && gF[j] != 0.f)
+                        ? masks[(size_t)sid[j] * c.words + (f >> 5)] : 0u;
+      }
+      const unsigned int bit = 1u << (f & 31);
+      bool mine = false;
+#pragma unroll
+      for (int j = 0; j < kDiffChunk; ++j) mine |= (word[j] & bit) != 0u;
+      if (!__any_sync(0xFFFFFFFFu, mine)) continue;
+      float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const float* D = depth + (size_t)f * npx;
+      float* GD = gdepth + (size_t)f * npx;
+#pragma unroll
+      for (int j = 0; j < kDiffChunk; ++j) {
+        if (!(word[j] & bit)) continue;
         int iu = 0, iv = 0;
         bool live = false;
-        diff_cell(c, gx, gy, gz, sT0 + 12 * f, D, &iu, &iv, &live);
+        diff_cell(c, gx[j], gy[j], gz[j], sT0 + 12 * f, D, &iu, &iv, &live);
+        if (!live) continue;   // saturated: f = 1, no gradient
         const DiffTerm T =
-            diff_term(c, gx, gy, gz, sRt + 12 * f, sRt + 12 * f + 9, D, iu, iv, live);
-        const float g = gF * T.gs;   // dL / dsdf
-        if (g != 0.f) {
-          float* GD = gdepth + (size_t)f * c.W * c.H;
-          atomicAdd(GD + T.idx, g * T.w[0]);
-          atomicAdd(GD + T.idx + 1, g * T.w[1]);
-          atomicAdd(GD + T.idx + c.W, g * T.w[2]);
-          atomicAdd(GD + T.idx + c.W + 1, g * T.w[3]);
-          const float iz = 1.0f / T.p[2];
-          gp[0] = g * T.dDdu * c.fx * iz;
-          gp[1] = g * T.dDdv * c.fy * iz;
-          gp[2] = g * (-T.dDdu * c.fx * T.p[0] * iz * iz - T.dDdv * c.fy * T.p[1] * iz * iz - 1.0f);
-          y[0] = T.y[0];
-          y[1] = T.y[1];
-          y[2] = T.y[2];
-        }
+            diff_term(c, gx[j], gy[j], gz[j], sRt + 12 * f, sRt + 12 * f + 9, D, iu, iv, live);
+        const float g = gF[j] * T.gs;   // dL / dsdf
+        atomicAdd(GD + T.idx, g * T.w[0]);
+        atomicAdd(GD + T.idx + 1, g * T.w[1]);
+        atomicAdd(GD + T.idx + c.W, g * T.w[2]);
+        atomicAdd(GD + T.idx + c.W + 1, g * T.w[3]);
+        const float iz = 1.0f / T.p[2];
+        const float gp0 = g * T.dDdu * c.fx * iz;
+        const float gp1 = g * T.dDdv * c.fy * iz;
+        const float gp2 = -(gp0 * T.p[0] + gp1 * T.p[1]) * iz - g;
+        acc[0] += gp0;
+        acc[1] += gp1;
+        acc[2] += gp2;
+        acc[3] += gp1 * T.p[2] - gp2 * T.p[1];
+        acc[4] += gp2 * T.p[0] - gp0 * T.p[2];
+        acc[5] += gp0 * T.p[1] - gp1 * T.p[0];
       }
-      // warp sums of M = y g^T (row b, column a) and G = g, in double (they cancel strongly)
-      double v[12];
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) v[3 * b + a] = (double)y[b] * (double)gp[a];
-      v[9] = gp[0];
-      v[10] = gp[1];
-      v[11] = gp[2];
-      const bool any = __any_sync(0xFFFFFFFFu, valid);
-      if (!any) continue;
-#pragma unroll
-      for (int e = 0; e < 12; ++e)
-        for (int o = 16; o > 0; o >>= 1) v[e] += __shfl_down_sync(0xFFFFFFFFu, v[e], o);
-      if (lane == 0)
-#pragma unroll
-        for (int e = 0; e < 12; ++e) atomicAdd(&sMG[12 * f + e], v[e]);
+      const float tot = warp_sum8(acc, lane);
+      const unsigned int e = lane >> 2;
+      if ((lane & 3u) == 0 && e < 6) myW[6 * f + e] += (double)tot;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < c.nf * 12; i += blockDim.x)
-    if (sMG[i] != 0.0) atomicAdd(&acc_MG[i], sMG[i]);
+  for (int i = threadIdx.x; i < c.nf * 6; i += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kDiffThreads / 32; ++w) t += sW[w * c.nf * 6 + i];
+    part[(size_t)blockIdx.x * c.nf * 6 + i] = t;
+  }
 }
 
-// dL/dxi per frame from the (M, G) accumulators.
-__global__ void k_diff_pose_grad(const DiffPose* poses, const double* acc_MG, int nf,
+// dL/dxi per frame: one CTA of 6 warps per frame; warp e sums component e of (G, C) over the
+// per-CTA partials in a fixed order, then thread 0 contracts with the exponential map's
+// derivatives.
+__global__ void k_diff_pose_grad(const DiffPose* poses, const double* part, int n_parts, int nf,
                                  float* gxi) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nf) return;
+  __shared__ double sGC[6];
+  const int f = blockIdx.x, e = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double t = 0.0;
+  for (int b = lane; b < n_parts; b += 32) t += part[((size_t)b * nf + f) * 6 + e];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, o);
+  if (lane == 0) sGC[e] = t;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   const DiffPose& P = poses[f];
-  const double* M = acc_MG + 12 * f;
-  const double* G = M + 9;
+  const double* G = sGC;
+  const double* C = sGC + 3;
   double RG[3];
   for (int i = 0; i < 3; ++i)
     RG[i] = P.Rd[3 * i] * G[0] + P.Rd[3 * i + 1] * G[1] + P.Rd[3 * i + 2] * G[2];
   for (int k = 0; k < 6; ++k) {
-    double acc = 0;
-    for (int e = 0; e < 9; ++e) acc += P.dR[k][e] * M[e];
+    double K[9];   // R^T dR_k, skew
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        K[3 * i + j] = P.Rd[i] * P.dR[k][j] + P.Rd[3 + i] * P.dR[k][3 + j] +
+                       P.Rd[6 + i] * P.dR[k][6 + j];
+    const double kv[3] = {0.5 * (K[7] - K[5]), 0.5 * (K[2] - K[6]), 0.5 * (K[3] - K[1])};
+    double acc = kv[0] * C[0] + kv[1] * C[1] + kv[2] * C[2];
     for (int i = 0; i < 3; ++i) acc -= RG[i] * P.dt[k][i];
     gxi[6 * f + k] = (float)acc;
   }
@@ -381,8 +439,10 @@ struct vbh_diff {
   cudaStream_t stream;
   int sms;
   vbh::DiffPose* poses;
-  double* acc;         // nf * 12
+  double* part;        // per-CTA (G, C) partials of the backward pass: bwd_grid x nf x 6
   double* loss;        // device scalar used when the caller passes none
+  int bwd_grid;        // resident CTAs of k_diff_backward (occupancy x SMs)
+  size_t bwd_smem;     // its dynamic shared memory
 };
 
 namespace {
@@ -424,8 +484,25 @@ vbh_status vbh_diff_create(const vbh_diff_config* cfg, void* cuda_stream, vbh_di
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaMalloc(&d->poses, sizeof(vbh::DiffPose) * cfg->n_frames) != cudaSuccess ||
-      cudaMalloc(&d->acc, sizeof(double) * 12 * cfg->n_frames) != cudaSuccess ||
       cudaMalloc(&d->loss, sizeof(double)) != cudaSuccess) {
+    vbh_diff_destroy(d);
+    return VBH_ERR_CUDA;
+  }
+  d->bwd_smem = sizeof(double) * (vbh::kDiffThreads / 32) * 6 * cfg->n_frames +
+                sizeof(float) * 24 * cfg->n_frames;
+  int occ = 0;
+  if (cudaFuncSetAttribute(vbh::k_diff_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)d->bwd_smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, vbh::k_diff_backward,
+                                                    vbh::kDiffThreads, d->bwd_smem) !=
+          cudaSuccess ||
+      occ < 1) {
+    vbh_diff_destroy(d);
+    return VBH_ERR_CUDA;
+  }
+  d->bwd_grid = occ * d->sms;
+  if (cudaMalloc(&d->part, sizeof(double) * 6 * cfg->n_frames * (size_t)d->bwd_grid) !=
+      cudaSuccess) {
     vbh_diff_destroy(d);
     return VBH_ERR_CUDA;
   }
@@ -437,7 +514,7 @@ vbh_status vbh_diff_destroy(vbh_diff* d) {
   if (!d) return VBH_OK;
   cudaStreamSynchronize(d->stream);
   if (d->poses) cudaFree(d->poses);
-  if (d->acc) cudaFree(d->acc);
+  if (d->part) cudaFree(d->part);
   if (d->loss) cudaFree(d->loss);
   delete d;
   return VBH_OK;
@@ -481,17 +558,21 @@ vbh_status vbh_diff_backward(vbh_diff* d, const int32_t* samples_dev, uint32_t n
       (n && (!samples_dev || !depth_dev || !T0_dev || !masks_dev || !F_dev)))
     return VBH_ERR_INVALID_ARG;
   const size_t npx = (size_t)d->cfg.n_frames * d->cfg.width * d->cfg.height;
-  if (cudaMemsetAsync(gdepth_dev, 0, npx * sizeof(float), d->stream) != cudaSuccess ||
-      cudaMemsetAsync(d->acc, 0, sizeof(double) * 12 * d->cfg.n_frames, d->stream) != cudaSuccess)
+  if (cudaMemsetAsync(gdepth_dev, 0, npx * sizeof(float), d->stream) != cudaSuccess)
     return VBH_ERR_CUDA;
   vbh_status st = vbh_diff_poses(d, xi_dev, nullptr);
   if (st != VBH_OK) return st;
-  if (n)
-    vbh::k_diff_backward<<<diff_grid(d, n), vbh::kDiffThreads, 0, d->stream>>>(
-        diff_params(d), samples_dev, n, depth_dev, T0_dev, d->poses, masks_dev, F_dev,
-        gdepth_dev, d->acc);
   const int nf = (int)d->cfg.n_frames;
-  vbh::k_diff_pose_grad<<<(nf + 63) / 64, 64, 0, d->stream>>>(d->poses, d->acc, nf, gxi_dev);
+  int parts = 0;
+  if (n) {
+    const unsigned int per = vbh::kDiffThreads * vbh::kDiffChunk;
+    const unsigned int want = (n + per - 1) / per;
+    parts = (int)(want < (unsigned)d->bwd_grid ? want : (unsigned)d->bwd_grid);
+    vbh::k_diff_backward<<<parts, vbh::kDiffThreads, d->bwd_smem, d->stream>>>(
+        diff_params(d), samples_dev, n, depth_dev, T0_dev, d->poses, masks_dev, F_dev,
+        gdepth_dev, d->part);
+  }
+  vbh::k_diff_pose_grad<<<nf, 192, 0, d->stream>>>(d->poses, d->part, parts, nf, gxi_dev);
   return cudaGetLastError() == cudaSuccess ? VBH_OK : VBH_ERR_CUDA;
 }
 
