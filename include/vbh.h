@@ -307,6 +307,122 @@ vbh_status vbh_mc_from_tsdf_static(const int32_t* keys3_dev, const float* tsdf_d
                                    const vbh_mc_stream* out, void* cuda_stream,
                                    uint32_t* error_flags_dev);
 
+/* Multi-client delta streaming: the server side of Sec. 4.2, where each client asks for the MC
+ * blocks that changed since its last update (the paper keeps a hash set of changed block ids
+ * per client and hands out capped random subsets; here each client holds one change sequence
+ * number on the device, and requests are served by continuous batching).
+ *
+ * Change sequence.  While a server is attached, every MC refresh of a block -- the extraction
+ * of a fused frame, vbh_process_frame or vbh_extract_mc_indices(VBH_MC_TOUCHED) -- gives the
+ * block the next change sequence number and keeps its 512 dense cube indices; every removal
+ * record gets a number too.  sigma is the last number assigned.  Attaching refreshes every
+ * live block once.  Explicit-key, all and since extractions do not refresh.
+ *
+ * Result of a request of client c, admitted at snapshot sigma while c is at version v:
+ *   - v > 0 and every change record after v still in the log: one record per block whose
+ *     newest refresh has a number in (v, sigma] (info = the block's frame version, with its
+ *     dense cube indices as of that refresh), and one per key whose newest removal has a number
+ *     in (v, sigma] and that is not live (info = VBH_REC_REMOVED | frame of the removal, no
+ *     indices); afterwards c is at sigma;
+ *   - v = 0 (a new or reconnecting client) or records lost from the log: flag VBH_SERVE_RESET
+ *     and one record per live block whose newest refresh is at or before sigma (a full model);
+ *     afterwards c is at sigma.
+ * Blocks refreshed after sigma are left to the client's next request.  A request is admitted
+ * only after the same client's previous one completed; records come in no particular order.
+ * A request whose worst case exceeds the whole budget is cut at the largest range that fits
+ * (VBH_SERVE_PARTIAL; c moves to the end of that range).
+ *
+ * Serving loop (continuous batching).  vbh_serve_submit queues a request; each vbh_serve_step
+ * retires the iterations that finished and, while fewer than max_inflight are queued, launches
+ * one more: pending requests are admitted in arrival order while a slot is free (at most
+ * max_batch requests in flight) and their worst-case output -- one 528 B record per change
+ * record in their range, or per pool entry for a reset -- fits in the budget_bytes stream
+ * buffer (a request that does not fit may be passed by later ones for bypass_iters
+ * iterations); each admitted request then contributes a chunk of at most chunk_records change
+ * records (0 = all) to the iteration, at most iter_records in total (oldest first; 0 = no
+ * limit), and the whole batch is one persistent extraction/compaction launch on the volume
+ * handle's stream, ordered with its frames.  max_batch = 1 with chunk_records = 0 serves one
+ * request per launch (unbatched).
+ *
+ * Output of a completed request (vbh_serve_result): n_records headers of four int32 (x, y, z,
+ * info as uint32 bits), then n_records x 512 cube indices (voxel lx + 8 ly + 64 lz; not written
+ * for removal records), in the server's stream buffer until vbh_serve_release.
+ * The server object is used from the handle's host thread; the handle must outlive it. */
+enum { VBH_SERVE_RESET = 1u, VBH_SERVE_PARTIAL = 2u, VBH_SERVE_ERR_OVERRUN = 4u,
+       VBH_SERVE_ERR_CAPACITY = 8u, VBH_SERVE_ERR_VERSION = 16u };
+typedef struct {
+  uint32_t n_clients;
+  uint32_t max_batch;       /* requests in flight at once, 1..64 */
+  uint32_t chunk_records;   /* change records per request per iteration (0 = no limit) */
+  uint32_t iter_records;    /* change records per iteration (0 = no limit) */
+  uint32_t max_inflight;    /* iterations queued on the stream at once (0 = 2) */
+  uint32_t bypass_iters;    /* iterations a memory-blocked request may be passed */
+  uint32_t log_bits;        /* change log of 2^log_bits records (0 = 22; >= 4 x max_blocks) */
+  uint32_t rem_bits;        /* removal table of 2^rem_bits keys (0 = 22) */
+  uint64_t budget_bytes;    /* stream buffer (>= 528 x max_blocks) */
+} vbh_serve_config;
+typedef struct {
+  uint32_t id, client;
+  uint32_t v_before, v_after;   /* client version before and after the request */
+  uint32_t n_records, flags;    /* VBH_SERVE_* bits */
+  uint64_t t_arrival_ns, t_admit_ns, t_done_ns;   /* vbh_serve_now_ns() clock */
+  uint64_t bytes_reserved;
+} vbh_serve_done;
+typedef struct {
+  const int32_t* recs_dev;      /* n_records x 4 */
+  const uint8_t* indices_dev;   /* n_records x 512 */
+  uint32_t n_records, flags;
+} vbh_serve_view;
+typedef struct {
+  uint64_t iterations, requests_done, records_served, changes_scanned;
+  uint64_t bytes_in_use, bytes_peak, deferred_memory;
+  uint32_t err_flags;           /* kernel-side errors (removal table full ...) */
+  uint32_t sigma;
+} vbh_serve_stats;
+/* A timed script for vbh_serve_run: events at t_ns (ascending, ns after the start); client >= 0
+ * is a request of that client, -1 the next frame (vbh_process_frame with depth_dev[i], T_wc +
+ * 12 i, frame_id[i], erase_radius, frame_out). */
+typedef struct {
+  uint32_t n_events;
+  const uint64_t* t_ns;
+  const int32_t* client;
+  const uint16_t* const* depth_dev;
+  const float* T_wc;
+  const uint32_t* frame_id;
+  float erase_radius;
+  const vbh_mc_stream* frame_out;
+} vbh_serve_script;
+typedef struct vbh_serve vbh_serve;
+/* Attach a server to a volume handle and refresh every live block (synchronises). */
+vbh_status vbh_serve_create(vbh_handle* h, const vbh_serve_config* cfg, vbh_serve** out);
+vbh_status vbh_serve_destroy(vbh_serve* s);
+/* Change the scheduling fields (max_batch, chunk_records, iter_records, max_inflight,
+ * bypass_iters) of an idle server. */
+vbh_status vbh_serve_set_policy(vbh_serve* s, const vbh_serve_config* cfg);
+/* Set / read client versions (synchronise; set only for clients without a request). */
+vbh_status vbh_serve_set_versions(vbh_serve* s, const uint32_t* clients_host,
+                                  const uint32_t* versions_host, uint32_t n);
+vbh_status vbh_serve_get_versions(vbh_serve* s, uint32_t* versions_host /* n_clients */);
+/* For each backlog b, the version v at which exactly min(b, live) live blocks have newer
+ * refreshes (synchronises). */
+vbh_status vbh_serve_versions_for_backlog(vbh_serve* s, const uint32_t* backlog_host, uint32_t n,
+                                          uint32_t* versions_host);
+vbh_status vbh_serve_submit(vbh_serve* s, uint32_t client, uint64_t t_arrival_ns /* 0 = now */,
+                            uint32_t* id_host);
+vbh_status vbh_serve_step(vbh_serve* s, uint32_t* launched_host /* may be NULL */);
+/* Completed requests since the last poll (at most cap; the rest stay queued). */
+vbh_status vbh_serve_poll(vbh_serve* s, vbh_serve_done* out_host, uint32_t cap, uint32_t* n_host);
+vbh_status vbh_serve_result(vbh_serve* s, uint32_t id, vbh_serve_view* out_host);
+vbh_status vbh_serve_release(vbh_serve* s, uint32_t id);
+/* Step until nothing is pending or running (synchronises). */
+vbh_status vbh_serve_drain(vbh_serve* s);
+vbh_status vbh_serve_stats_read(vbh_serve* s, vbh_serve_stats* out_host);
+/* Run a timed script in real time (frames and request arrivals), releasing every result as it
+ * completes; writes the completions (at most cap) to out_host. */
+vbh_status vbh_serve_run(vbh_serve* s, const vbh_serve_script* script, vbh_serve_done* out_host,
+                         uint32_t cap, uint32_t* n_host);
+uint64_t vbh_serve_now_ns(void);
+
 /* Host-side helpers (no device work). */
 int vbh_abi_version(void);
 const char* vbh_last_error(void);

@@ -10,12 +10,11 @@
 #include <string>
 #include <vector>
 
-#include "vbh.h"
-#include "vbh_internal.cuh"
+#include "handle.cuh"
 
 using namespace vbh;
 
-namespace {
+namespace vbh {
 
 thread_local std::string g_last_error;
 
@@ -24,122 +23,8 @@ vbh_status fail(vbh_status st, const std::string& msg) {
   return st;
 }
 
-#define VBH_CUDA(call)                                                                 \
-  do {                                                                                 \
-    cudaError_t e_ = (call);                                                           \
-    if (e_ != cudaSuccess)                                                             \
-      return fail(VBH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
-  } while (0)
+}  // namespace vbh
 
-struct StageEvents {
-  int stage;
-  cudaEvent_t a, b;
-  uint64_t launches;
-};
-
-}  // namespace
-
-struct vbh_handle {
-  vbh_config cfg{};
-  cudaStream_t stream = nullptr;
-  cudaStream_t side = nullptr;     // snapshot copies of the counters, off the critical path
-  int device = 0;
-  Launch L{};
-  unsigned int n_slots = 0;
-  Slot* slots = nullptr;
-  Slot* shadow = nullptr;
-  DevCounters* cnt = nullptr;
-  DevCounters* snap = nullptr;     // pinned host snapshot
-  cudaEvent_t snap_ev = nullptr;
-  bool snap_pending = false;
-  // pool
-  float2* vox = nullptr;
-  unsigned int* masks = nullptr;
-  unsigned long long* pkeys = nullptr;
-  unsigned int *state = nullptr, *mark = nullptr, *version = nullptr, *stack = nullptr;
-  // per-frame lists
-  int J = 0;
-  unsigned long long* cand = nullptr;
-  unsigned int cand_cap = 0;
-  unsigned int* cand_res = nullptr;
-  unsigned char* cand_st = nullptr;
-  unsigned int* touched = nullptr;
-  unsigned long long* tkey = nullptr;   // key of each touched block
-  float2* tdepth = nullptr;        // camera depth of each touched block's origin (hi, lo)
-  unsigned int* mset = nullptr;
-  unsigned long long* removed = nullptr;
-  unsigned long long* tombrec = nullptr;
-  unsigned int epoch = 0;
-  unsigned int frame_version = 0;
-  bool have_frame = false;
-  FrameCtl* ctl = nullptr;         // device-resident per-call control block
-  unsigned int* last_entries = nullptr;   // n_entries_dev of the last extraction
-  // whole-frame CUDA graph (vbh_process_frame)
-  cudaStream_t cap_stream = nullptr;
-  cudaGraph_t frame_graph = nullptr;
-  cudaGraphExec_t frame_exec = nullptr;
-  // control blocks of vbh_process_frame travel through a pinned, device-mapped ring: the host
-  // writes slot (seq % kRing) and launches the graph; the graph's root kernel reads the next
-  // slot itself and reports the consumed sequence number back through mapped memory
-  FrameCtl* ring_host = nullptr;
-  FrameCtl* ring_dev = nullptr;
-  volatile unsigned long long* consumed_host = nullptr;
-  unsigned long long* consumed_dev = nullptr;
-  unsigned long long* dev_seq = nullptr;   // device memory
-  unsigned long long host_seq = 0;
-  cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
-  bool graph_timed = false;
-  uint64_t graph_kernels = 0;
-  // bookkeeping
-  uint64_t launches = 0;
-  uint32_t rebuilds = 0;
-  int timing = 0;                  // bit mask of timed stages
-  std::vector<StageEvents> pending;
-  std::vector<cudaEvent_t> ev_free;
-  double ms[VBH_N_STAGES] = {0};
-  uint64_t stage_launches[VBH_N_STAGES] = {0};
-  int cur_stage = -1;
-  cudaEvent_t cur_a = nullptr;
-  uint64_t cur_launch0 = 0;
-
-  TableView table() const { return TableView{slots, cfg.n_buckets - 1u, cfg.hash_fn}; }
-  PoolView pool() const {
-    return PoolView{vox, masks, pkeys, state, mark, version, stack, cfg.max_blocks};
-  }
-  unsigned int next_epoch() {
-    ++epoch;
-    if (epoch == 0) epoch = 1;
-    return epoch;
-  }
-  cudaEvent_t get_event() {
-    if (!ev_free.empty()) {
-      cudaEvent_t e = ev_free.back();
-      ev_free.pop_back();
-      return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-  }
-  void stage_begin(int s) {
-    cur_stage = s;
-    cur_launch0 = launches;
-    if (timing & (1 << s)) {
-      cur_a = get_event();
-      cudaEventRecord(cur_a, stream);
-    }
-  }
-  void stage_end() {
-    if (cur_stage >= 0 && (timing & (1 << cur_stage))) {
-      cudaEvent_t b = get_event();
-      cudaEventRecord(b, stream);
-      pending.push_back(StageEvents{cur_stage, cur_a, b, launches - cur_launch0});
-    } else if (cur_stage >= 0) {
-      stage_launches[cur_stage] += launches - cur_launch0;
-    }
-    cur_stage = -1;
-  }
-};
 
 namespace {
 
@@ -270,6 +155,7 @@ FrameCtl base_ctl(const vbh_handle* h, const float* T) {
   FrameCtl c{};
   c.fp = frame_params(h, T);
   c.version = h->frame_version;
+  c.slog = h->slog;
   return c;
 }
 
@@ -306,6 +192,25 @@ void read_frame_stats(vbh_handle* h, const DevCounters& d, vbh_frame_stats* st) 
 }
 
 }  // namespace
+
+namespace vbh {
+
+vbh_status refresh_all_blocks(vbh_handle* h, unsigned int* counts_dev) {
+  FrameCtl c = base_ctl(h, nullptr);
+  c.epoch_mset = h->next_epoch();
+  c.reset = kResetMset;
+  c.serve_mark = 1u;
+  c.store_only = 1u;
+  c.n_blocks_dev = counts_dev;
+  c.n_entries_dev = counts_dev + 1;
+  launch_setup(h, c);
+  launch_mset_scan(h->L, h->pool(), h->cnt, h->mset, 0, 0u);
+  launch_mc_extract(h->L, h->table(), h->pool(), h->cnt, h->ctl, h->mset, h->tombrec);
+  h->launches += 2;
+  return check_launch(h, "refresh_all_blocks");
+}
+
+}  // namespace vbh
 
 extern "C" {
 
@@ -388,6 +293,8 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
     CREATE_CUDA(cudaMalloc(&h->mark, (size_t)nb * sizeof(unsigned int)));
     CREATE_CUDA(cudaMalloc(&h->version, (size_t)nb * sizeof(unsigned int)));
     CREATE_CUDA(cudaMalloc(&h->stack, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&h->seq, (size_t)nb * sizeof(unsigned int)));
+    CREATE_CUDA(cudaMemsetAsync(h->seq, 0, (size_t)nb * sizeof(unsigned int), h->stream));
     CREATE_CUDA(cudaMemsetAsync(h->pkeys, 0xFF, (size_t)nb * sizeof(unsigned long long), h->stream));
     CREATE_CUDA(cudaMemsetAsync(h->state, 0, (size_t)nb * sizeof(unsigned int), h->stream));
     CREATE_CUDA(cudaMemsetAsync(h->mark, 0, (size_t)nb * sizeof(unsigned int), h->stream));
@@ -420,6 +327,7 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
 
 vbh_status vbh_destroy(vbh_handle* h) {
   if (!h) return VBH_OK;
+  if (h->server) vbh_serve_destroy(h->server);
   if (h->stream || h->slots) cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
   if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
@@ -428,7 +336,7 @@ vbh_status vbh_destroy(vbh_handle* h) {
   if (h->ring_host) cudaFreeHost(h->ring_host);
   if (h->consumed_host) cudaFreeHost((void*)h->consumed_host);
   void* ptrs[] = {h->dev_seq, h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
-                  h->version, h->stack, h->cand, h->cand_res, h->cand_st, h->touched, h->tdepth, h->tkey, h->mset,
+                  h->version, h->stack, h->seq, h->cand, h->cand_res, h->cand_st, h->touched, h->tdepth, h->tkey, h->mset,
                   h->removed, h->tombrec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -622,6 +530,7 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
   c.version = frame_id;
   c.clear_removed = 1;
   c.reset = kResetFrame | kResetErase | kResetMset;
+  c.serve_mark = h->slog != nullptr;
   set_stream_out(c, out);
   // wait (bounded) until the graph launched kRing frames ago has consumed this slot
   const unsigned long long seq = h->host_seq;
@@ -705,6 +614,7 @@ vbh_status vbh_extract_mc_indices(vbh_handle* h, const vbh_mc_selector* sel,
   set_stream_out(c, out);
   c.epoch_mset = h->next_epoch();
   c.clear_removed = sel->mode == VBH_MC_TOUCHED;
+  c.serve_mark = sel->mode == VBH_MC_TOUCHED && h->slog != nullptr;
   c.reset = kResetMset;
   h->stage_begin(VBH_STAGE_MCSET);
   launch_setup(h, c);

@@ -26,6 +26,7 @@ __device__ __forceinline__ void finish_removal(bool erased, unsigned int p, unsi
     pool.stack[k] = p;
     pool.pkeys[p] = kEmpty;
     pool.state[p] = 0u;
+    pool.seq[p] = 0u;   // change records of the erased block are no longer current
   }
   unsigned int r = warp_append(&cnt->n_removed, erased, 0xFFFFFFFFu);
   if (erased) {

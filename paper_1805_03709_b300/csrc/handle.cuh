@@ -1,0 +1,149 @@
+// Host-side state of a libvbh handle, shared by the C ABI implementation files (api.cu,
+// serve.cu).  Not part of the C ABI.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "vbh.h"
+#include "vbh_internal.cuh"
+
+namespace vbh {
+
+// Records the message returned by vbh_last_error() and passes the status through.
+vbh_status fail(vbh_status st, const std::string& msg);
+
+#define VBH_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return ::vbh::fail(VBH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct StageEvents {
+  int stage;
+  cudaEvent_t a, b;
+  uint64_t launches;
+};
+
+}  // namespace vbh
+
+using vbh::StageEvents;
+using vbh::Slot;
+using vbh::DevCounters;
+using vbh::FrameCtl;
+using vbh::Launch;
+using vbh::TableView;
+using vbh::PoolView;
+
+struct vbh_handle {
+  vbh_config cfg{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;     // snapshot copies of the counters, off the critical path
+  int device = 0;
+  Launch L{};
+  unsigned int n_slots = 0;
+  Slot* slots = nullptr;
+  Slot* shadow = nullptr;
+  DevCounters* cnt = nullptr;
+  DevCounters* snap = nullptr;     // pinned host snapshot
+  cudaEvent_t snap_ev = nullptr;
+  bool snap_pending = false;
+  // pool
+  float2* vox = nullptr;
+  unsigned int* masks = nullptr;
+  unsigned long long* pkeys = nullptr;
+  unsigned int *state = nullptr, *mark = nullptr, *version = nullptr, *stack = nullptr;
+  unsigned int* seq = nullptr;
+  // attached server (serve.cu): device-resident log/store state and its host object
+  vbh::ServeLog* slog = nullptr;
+  vbh_serve* server = nullptr;
+  // per-frame lists
+  int J = 0;
+  unsigned long long* cand = nullptr;
+  unsigned int cand_cap = 0;
+  unsigned int* cand_res = nullptr;
+  unsigned char* cand_st = nullptr;
+  unsigned int* touched = nullptr;
+  unsigned long long* tkey = nullptr;   // key of each touched block
+  float2* tdepth = nullptr;        // camera depth of each touched block's origin (hi, lo)
+  unsigned int* mset = nullptr;
+  unsigned long long* removed = nullptr;
+  unsigned long long* tombrec = nullptr;
+  unsigned int epoch = 0;
+  unsigned int frame_version = 0;
+  bool have_frame = false;
+  FrameCtl* ctl = nullptr;         // device-resident per-call control block
+  unsigned int* last_entries = nullptr;   // n_entries_dev of the last extraction
+  // whole-frame CUDA graph (vbh_process_frame)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t frame_graph = nullptr;
+  cudaGraphExec_t frame_exec = nullptr;
+  // control blocks of vbh_process_frame travel through a pinned, device-mapped ring: the host
+  // writes slot (seq % kRing) and launches the graph; the graph's root kernel reads the next
+  // slot itself and reports the consumed sequence number back through mapped memory
+  FrameCtl* ring_host = nullptr;
+  FrameCtl* ring_dev = nullptr;
+  volatile unsigned long long* consumed_host = nullptr;
+  unsigned long long* consumed_dev = nullptr;
+  unsigned long long* dev_seq = nullptr;   // device memory
+  unsigned long long host_seq = 0;
+  cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
+  bool graph_timed = false;
+  uint64_t graph_kernels = 0;
+  // bookkeeping
+  uint64_t launches = 0;
+  uint32_t rebuilds = 0;
+  int timing = 0;                  // bit mask of timed stages
+  std::vector<StageEvents> pending;
+  std::vector<cudaEvent_t> ev_free;
+  double ms[VBH_N_STAGES] = {0};
+  uint64_t stage_launches[VBH_N_STAGES] = {0};
+  int cur_stage = -1;
+  cudaEvent_t cur_a = nullptr;
+  uint64_t cur_launch0 = 0;
+
+  TableView table() const { return TableView{slots, cfg.n_buckets - 1u, cfg.hash_fn}; }
+  PoolView pool() const {
+    return PoolView{vox, masks, pkeys, state, mark, version, stack, seq, cfg.max_blocks};
+  }
+  unsigned int next_epoch() {
+    ++epoch;
+    if (epoch == 0) epoch = 1;
+    return epoch;
+  }
+  cudaEvent_t get_event() {
+    if (!ev_free.empty()) {
+      cudaEvent_t e = ev_free.back();
+      ev_free.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void stage_begin(int s) {
+    cur_stage = s;
+    cur_launch0 = launches;
+    if (timing & (1 << s)) {
+      cur_a = get_event();
+      cudaEventRecord(cur_a, stream);
+    }
+  }
+  void stage_end() {
+    if (cur_stage >= 0 && (timing & (1 << cur_stage))) {
+      cudaEvent_t b = get_event();
+      cudaEventRecord(b, stream);
+      pending.push_back(StageEvents{cur_stage, cur_a, b, launches - cur_launch0});
+    } else if (cur_stage >= 0) {
+      stage_launches[cur_stage] += launches - cur_launch0;
+    }
+    cur_stage = -1;
+  }
+};
+
+namespace vbh {
+// MC refresh of every live block into the attached server's store and log, with no stream
+// output (enqueued on the handle's stream).  counts_dev: two device words of scratch.
+vbh_status refresh_all_blocks(vbh_handle* h, unsigned int* counts_dev);
+}  // namespace vbh

@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
       pool.stack[k] = val;
       pool.pkeys[val] = kEmpty;
       pool.state[val] = 0u;
+      pool.seq[val] = 0u;
     }
     if (leader) {
       res[i] = erased ? val : kNone;

@@ -14,6 +14,12 @@
 // fusion keeps a 128 B sign/weight bit mask per block, and one warp per block assembles the
 // 9 x 9 x 9 corner lattice from the masks of the block and its 7 positive neighbours, then
 // classifies a whole 8-voxel row at once with byte-sliced 64-bit arithmetic.
+//
+// Serving.  While a server is attached, an extraction that refreshes blocks (the per-frame one)
+// also stores each block's 512 dense cube indices, gives every record the next change sequence
+// number e (refreshed blocks first, then removals), stamps seq[p] = e and writes the change
+// record to log[e mod 2^L]; the last CTA to finish advances the sequence counter and publishes
+// the last number to host memory.
 #include "vbh_internal.cuh"
 
 namespace vbh {
@@ -135,6 +141,20 @@ __global__ void __launch_bounds__(kThreads) k_mset_scan(PoolView pool, DevCounte
   }
 }
 
+// Sequence number e of the newest removal of `key` (lastrem table, linear probing; the table
+// only grows, so a claimed key never moves).
+__device__ __forceinline__ void note_removal(ServeLog* sl, unsigned long long key, unsigned int e) {
+  unsigned int b = hash_mix(key) & sl->rem_mask;
+  for (unsigned int probe = 0; probe <= sl->rem_mask; ++probe, b = (b + 1u) & sl->rem_mask) {
+    const unsigned long long cur = atomicCAS(&sl->rem_keys[b], kEmpty, key);
+    if (cur == kEmpty || cur == key) {
+      atomicMax(&sl->rem_seq[b], e);
+      return;
+    }
+  }
+  atomicOr(&sl->err, kServeErrRemFull);
+}
+
 // Zero-byte detector: 0x80 in every byte of v that is zero, 0 elsewhere (exact, no carries
 // between bytes because the low seven bits are added separately from the top bit).
 __device__ __forceinline__ unsigned long long zero_bytes(unsigned long long v) {
@@ -169,15 +189,20 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_extract(TableView t, PoolView
   unsigned int* const n_entries_dev = ctl->n_entries_dev;
   const unsigned int cap_blocks = ctl->cap_blocks, cap_entries = ctl->cap_entries;
   const unsigned int tomb_version = ctl->version;
+  ServeLog* const sl = ctl->serve_mark ? ctl->slog : nullptr;
+  const bool emit = !ctl->store_only;
+  __shared__ unsigned int s_seq0;
   for (int b = threadIdx.x; b < 256; b += kMcThreads) {
     unsigned long long v = 0;
     for (int i = 0; i < 8; ++i) v |= (unsigned long long)((b >> i) & 1) << (8 * i);
     spread[b] = v;
   }
-  __syncthreads();
+  if (threadIdx.x == 0) s_seq0 = sl ? sl->seq_next : 0u;   // every CTA reads it before the
+  __syncthreads();                                        // last one advances it
+  const unsigned int seq0 = s_seq0;
   const unsigned int n_m = cnt->n_mset, n_t = cnt->n_tombrec, total = n_m + n_t;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *n_blocks_dev = total;
+    if (emit) *n_blocks_dev = total;
     cnt->mc_blocks = total;
     if (ctl->clear_removed) cnt->n_removed = 0;   // the set kernel that read it has finished
   }
@@ -187,14 +212,26 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_extract(TableView t, PoolView
   bool overflow = false;
   for (unsigned int r = blockIdx.x * (kMcThreads / 32) + warp; r < total; r += nwarps) {
     if (r >= n_m) {   // removal record
-      if (lane == 0 && r < cap_blocks) {
-        const int3 k = unpack_key(tombrec[r - n_m]);
-        rec_keys3[3u * r] = k.x;
-        rec_keys3[3u * r + 1] = k.y;
-        rec_keys3[3u * r + 2] = k.z;
-        rec_info[r] = 0x80000000u | tomb_version;
-        rec_off[r] = 0u;
-        rec_cnt[r] = 0u;
+      if (lane == 0) {
+        const unsigned long long tk = tombrec[r - n_m];
+        if (emit && r < cap_blocks) {
+          const int3 k = unpack_key(tk);
+          rec_keys3[3u * r] = k.x;
+          rec_keys3[3u * r + 1] = k.y;
+          rec_keys3[3u * r + 2] = k.z;
+          rec_info[r] = 0x80000000u | tomb_version;
+          rec_off[r] = 0u;
+          rec_cnt[r] = 0u;
+        }
+        if (sl) {
+          const unsigned int e = seq0 + r;
+          LogEnt le;
+          le.key = tk | kLogRemoved;
+          le.aux = tomb_version;
+          le.seq = e;
+          sl->log[e & sl->log_mask] = le;
+          note_removal(sl, tk, e);
+        }
       }
       continue;
     }
@@ -235,6 +272,24 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_extract(TableView t, PoolView
       idx8[h] = c;
       mine += __popcll(nz[h]);
     }
+    if (sl) {   // dense indices of voxel x + 8 row: row lane in word lane, row lane + 32 next
+      unsigned long long* st = reinterpret_cast<unsigned long long*>(sl->store + 32u * q);
+      st[lane] = idx8[0];
+      st[32u + lane] = idx8[1];
+      if (lane == 0) {
+        const unsigned int e = seq0 + r;
+        pool.seq[q] = e;
+        LogEnt le;
+        le.key = key;
+        le.aux = q;
+        le.seq = e;
+        sl->log[e & sl->log_mask] = le;
+      }
+    }
+    if (!emit) {
+      __syncwarp();   // the lattice in shared memory is refilled for the next block
+      continue;
+    }
     unsigned int incl = mine;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -273,8 +328,20 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_extract(TableView t, PoolView
     }
     __syncwarp();
   }
-  if ((overflow || (total > cap_blocks && blockIdx.x == 0)) && lane == 0)
+  if (emit && (overflow || (total > cap_blocks && blockIdx.x == 0)) && lane == 0)
     atomicOr(&cnt->err, kErrStream);
+  if (sl) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(&sl->mc_done, 1u) == gridDim.x - 1u) {
+        sl->mc_done = 0u;
+        sl->seq_next = seq0 + total;
+        __threadfence_system();
+        *reinterpret_cast<volatile unsigned int*>(sl->sigma_host) = seq0 + total - 1u;
+      }
+    }
+  }
 }
 
 }  // namespace

@@ -15,6 +15,13 @@
 //   mark    : max_blocks u32 epoch stamps used to de-duplicate per-frame block lists.
 //   version : max_blocks u32, frame version of the block's last MC refresh.
 //   stack   : max_blocks u32 free pool indices, `free_top` of them valid.
+//   seq     : max_blocks u32, change sequence number of the block's last MC refresh while a
+//             server is attached (0 = none since allocation; reset when the block is erased).
+// Serving state (allocated when a server attaches, see serve.cu):
+//   log     : 2^L x 16 B ring of change records indexed by sequence number (LogEnt).
+//   store   : max_blocks x 512 B dense MC cube indices of each live block at its last refresh.
+//   lastrem : 2^R open-addressed (key u64, seq u32) pairs: sequence number of each key's last
+//             removal, so that only the newest removal record of a key is served.
 #pragma once
 
 #include <cstdint>
@@ -76,8 +83,34 @@ struct PoolView {
   unsigned int* mark;
   unsigned int* version;
   unsigned int* stack;
+  unsigned int* seq;
   unsigned int max_blocks;  // 0 for a plain map
 };
+
+// Change record of the serving log.  key: packed block key, bit 63 set for a removal record;
+// aux: pool index of a refreshed block, frame version of a removal; seq: its sequence number
+// (a record whose seq differs from the index it is read at has been overwritten by the ring).
+struct __align__(16) LogEnt {
+  unsigned long long key;
+  unsigned int aux;
+  unsigned int seq;
+};
+constexpr unsigned long long kLogRemoved = 1ull << 63;
+
+// Device-resident state shared by the per-frame MC extraction (which appends change records)
+// and the serving kernels (which read them).
+struct ServeLog {
+  LogEnt* log;
+  uint4* store;                    // 32 x 16 B per pool entry
+  unsigned long long* rem_keys;    // lastrem table (kEmpty = free)
+  unsigned int* rem_seq;
+  unsigned int* sigma_host;        // mapped host word: last assigned sequence number
+  unsigned int log_mask, rem_mask;
+  unsigned int seq_next;           // next sequence number (starts at 1)
+  unsigned int mc_done;            // CTAs of the running extraction that have finished
+  unsigned int err;                // kServeErr* bits
+};
+constexpr unsigned int kServeErrRemFull = 1u, kServeErrOverrun = 2u, kServeErrCap = 4u;
 
 // Touched-list entry: pool index in bits 0-30, bit 31 set when the block is fresh (allocated by
 // this frame, voxel data not yet written).
@@ -258,6 +291,9 @@ struct FrameCtl {
   unsigned int* n_blocks_dev;
   unsigned int* n_entries_dev;
   unsigned int cap_blocks, cap_entries;
+  ServeLog* slog;               // attached server (nullptr: none)
+  unsigned int serve_mark;      // this extraction refreshes the store and appends to the log
+  unsigned int store_only;      // no MC stream output (populating the store)
 };
 
 #ifdef __CUDACC__

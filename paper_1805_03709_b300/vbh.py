@@ -105,7 +105,59 @@ SYMBOLS = [
      [_p, _p, _p, _u32, ctypes.POINTER(vbh_mc_stream), _p, _p]),
 ]
 
+
 _lib = None
+
+
+VBH_SERVE_RESET, VBH_SERVE_PARTIAL, VBH_SERVE_ERR_OVERRUN, VBH_SERVE_ERR_CAPACITY, \
+    VBH_SERVE_ERR_VERSION = 1, 2, 4, 8, 16
+
+
+class vbh_serve_config(ctypes.Structure):
+    _fields_ = [("n_clients", _u32), ("max_batch", _u32), ("chunk_records", _u32),
+                ("iter_records", _u32), ("max_inflight", _u32), ("bypass_iters", _u32),
+                ("log_bits", _u32), ("rem_bits", _u32), ("budget_bytes", _u64)]
+
+
+class vbh_serve_done(ctypes.Structure):
+    _fields_ = [("id", _u32), ("client", _u32), ("v_before", _u32), ("v_after", _u32),
+                ("n_records", _u32), ("flags", _u32), ("t_arrival_ns", _u64),
+                ("t_admit_ns", _u64), ("t_done_ns", _u64), ("bytes_reserved", _u64)]
+
+
+class vbh_serve_view(ctypes.Structure):
+    _fields_ = [("recs_dev", _p), ("indices_dev", _p), ("n_records", _u32), ("flags", _u32)]
+
+
+class vbh_serve_stats(ctypes.Structure):
+    _fields_ = [("iterations", _u64), ("requests_done", _u64), ("records_served", _u64),
+                ("changes_scanned", _u64), ("bytes_in_use", _u64), ("bytes_peak", _u64),
+                ("deferred_memory", _u64), ("err_flags", _u32), ("sigma", _u32)]
+
+
+class vbh_serve_script(ctypes.Structure):
+    _fields_ = [("n_events", _u32), ("t_ns", _p), ("client", _p), ("depth_dev", _p),
+                ("T_wc", _p), ("frame_id", _p), ("erase_radius", _f32),
+                ("frame_out", ctypes.POINTER(vbh_mc_stream))]
+
+
+SYMBOLS += [
+    ("vbh_serve_create", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_config), ctypes.POINTER(_p)]),
+    ("vbh_serve_destroy", ctypes.c_int, [_p]),
+    ("vbh_serve_set_policy", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_config)]),
+    ("vbh_serve_set_versions", ctypes.c_int, [_p, _p, _p, _u32]),
+    ("vbh_serve_get_versions", ctypes.c_int, [_p, _p]),
+    ("vbh_serve_versions_for_backlog", ctypes.c_int, [_p, _p, _u32, _p]),
+    ("vbh_serve_submit", ctypes.c_int, [_p, _u32, _u64, ctypes.POINTER(_u32)]),
+    ("vbh_serve_step", ctypes.c_int, [_p, ctypes.POINTER(_u32)]),
+    ("vbh_serve_poll", ctypes.c_int, [_p, _p, _u32, ctypes.POINTER(_u32)]),
+    ("vbh_serve_result", ctypes.c_int, [_p, _u32, ctypes.POINTER(vbh_serve_view)]),
+    ("vbh_serve_release", ctypes.c_int, [_p, _u32]),
+    ("vbh_serve_drain", ctypes.c_int, [_p]),
+    ("vbh_serve_stats_read", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_stats)]),
+    ("vbh_serve_run", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_script), _p, _u32, ctypes.POINTER(_u32)]),
+    ("vbh_serve_now_ns", _u64, []),
+]
 
 
 class VbhError(RuntimeError):
@@ -278,3 +330,89 @@ def vbh_diff_backward(h, samples, depth, T0, xi, masks, F, gdepth, gxi):
     _check(lib().vbh_diff_backward(h, _ptr(samples), int(samples.shape[0]), _ptr(depth),
                                    _ptr(T0), _ptr(xi), _ptr(masks), _ptr(F), _ptr(gdepth),
                                    _ptr(gxi)), "vbh_diff_backward")
+
+
+# ------------------------------------------------------------------------------- serving
+def vbh_serve_create(h, cfg: vbh_serve_config) -> int:
+    out = _p()
+    _check(lib().vbh_serve_create(h, ctypes.byref(cfg), ctypes.byref(out)), "vbh_serve_create")
+    return out.value
+
+
+def vbh_serve_destroy(s):
+    _check(lib().vbh_serve_destroy(s), "vbh_serve_destroy")
+
+
+def vbh_serve_set_policy(s, cfg: vbh_serve_config):
+    _check(lib().vbh_serve_set_policy(s, ctypes.byref(cfg)), "vbh_serve_set_policy")
+
+
+def vbh_serve_set_versions(s, clients, versions):
+    c = np.ascontiguousarray(clients, dtype=np.uint32)
+    v = np.ascontiguousarray(versions, dtype=np.uint32)
+    _check(lib().vbh_serve_set_versions(s, _ptr(c), _ptr(v), len(c)), "vbh_serve_set_versions")
+
+
+def vbh_serve_get_versions(s, n_clients: int) -> np.ndarray:
+    v = np.zeros(n_clients, np.uint32)
+    _check(lib().vbh_serve_get_versions(s, _ptr(v)), "vbh_serve_get_versions")
+    return v
+
+
+def vbh_serve_versions_for_backlog(s, backlog) -> np.ndarray:
+    b = np.ascontiguousarray(backlog, dtype=np.uint32)
+    v = np.zeros(len(b), np.uint32)
+    _check(lib().vbh_serve_versions_for_backlog(s, _ptr(b), len(b), _ptr(v)),
+           "vbh_serve_versions_for_backlog")
+    return v
+
+
+def vbh_serve_submit(s, client: int, t_arrival_ns: int = 0) -> int:
+    rid = _u32()
+    _check(lib().vbh_serve_submit(s, client, t_arrival_ns, ctypes.byref(rid)), "vbh_serve_submit")
+    return rid.value
+
+
+def vbh_serve_step(s) -> int:
+    n = _u32()
+    _check(lib().vbh_serve_step(s, ctypes.byref(n)), "vbh_serve_step")
+    return n.value
+
+
+def vbh_serve_poll(s, cap: int = 256) -> list:
+    buf = (vbh_serve_done * cap)()
+    n = _u32()
+    _check(lib().vbh_serve_poll(s, buf, cap, ctypes.byref(n)), "vbh_serve_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def vbh_serve_result(s, rid: int) -> vbh_serve_view:
+    v = vbh_serve_view()
+    _check(lib().vbh_serve_result(s, rid, ctypes.byref(v)), "vbh_serve_result")
+    return v
+
+
+def vbh_serve_release(s, rid: int):
+    _check(lib().vbh_serve_release(s, rid), "vbh_serve_release")
+
+
+def vbh_serve_drain(s):
+    _check(lib().vbh_serve_drain(s), "vbh_serve_drain")
+
+
+def vbh_serve_stats_read(s) -> vbh_serve_stats:
+    st = vbh_serve_stats()
+    _check(lib().vbh_serve_stats_read(s, ctypes.byref(st)), "vbh_serve_stats_read")
+    return st
+
+
+def vbh_serve_run(s, script: vbh_serve_script, cap: int) -> list:
+    buf = (vbh_serve_done * max(cap, 1))()
+    n = _u32()
+    _check(lib().vbh_serve_run(s, ctypes.byref(script), buf, cap, ctypes.byref(n)),
+           "vbh_serve_run")
+    return [buf[i] for i in range(n.value)]
+
+
+def vbh_serve_now_ns() -> int:
+    return int(lib().vbh_serve_now_ns())

@@ -133,6 +133,10 @@ class Volume:
         self.n_erased = torch.zeros(1, dtype=torch.int32, device="cuda")
 
     def close(self):
+        srv = getattr(self, "_server", None)
+        if srv is not None:
+            srv.close()
+            self._server = None
         if getattr(self, "h", None):
             V.vbh_destroy(self.h)
             self.h = None
