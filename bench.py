@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the multi-client serving measurement (batched vs unbatched)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the differentiable-fusion timing (forward vs forward+backward)")
     ap.add_argument("--clock-ms", type=int, default=200,
@@ -398,6 +401,9 @@ def main():
     diff_pt = None
     if not args.no_diff:
         diff_pt = diff_point(torch, dev, flush)
+    serve_pt = None
+    if not args.no_serve and rank == 0:
+        serve_pt = serve_point(torch, cam, D, poses, peak, args.serve_seconds)
 
     if rank == 0:
         line = {
@@ -417,7 +423,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
-            "hash": hash_pt, "diff": diff_pt,
+            "hash": hash_pt, "diff": diff_pt, "serve": serve_pt,
         }
         print(json.dumps(line), flush=True)
     vol.close()
@@ -492,6 +498,100 @@ def hash_point(torch, dev, flush, peak):
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+def serve_point(torch, cam, D, poses, peak, duration_s=4.0, n_clients=64, rate=20.0,
+                warm_frames=30, seed=1805):
+    """Multi-client streaming: the room volume updated live at 30 frames/s (frames warm_frames
+    onwards of the sequence) while n_clients clients with Poisson arrivals (rate requests/s
+    each) ask for the MC blocks changed since their last version; initial backlogs log-uniform
+    in [1, 50000] blocks (set through the clients' versions); 4 GB stream-buffer budget; results
+    released as they complete.  The same seeded script runs twice on fresh volumes: batched
+    (continuous batching: up to 64 requests per launch, two launches in flight, every request
+    whole) and unbatched (one request per launch).  Latency = arrival ->
+    result ready, observed by the host loop.  Then one saturated launch: 64 requests with
+    backlog 4096 each in a single batch, timed with CUDA events."""
+    from paper_1805_03709_b300.serve import Server
+    from paper_1805_03709_b300.volume import Volume
+    rng = np.random.default_rng(seed)
+    n_fr = int(round(duration_s * 30))
+    fr = [(warm_frames + k) % N_FRAMES for k in range(n_fr)]
+    ev = [(int((k + 1) * 1e9 / 30), -1) for k in range(n_fr)]
+    for c in range(n_clients):
+        t = rng.exponential(1.0 / rate)
+        while t < duration_s:
+            ev.append((int(t * 1e9), c))
+            t += rng.exponential(1.0 / rate)
+    ev.sort()
+    t_ns = [e[0] for e in ev]
+    cl = [e[1] for e in ev]
+    backlog = np.exp(rng.uniform(0.0, np.log(50000.0), n_clients)).astype(np.int64)
+    frames = [D[f] for f in fr]
+    P = np.stack([poses[f] for f in fr])
+    ids = [warm_frames + 1 + k for k in range(n_fr)]
+    out = {"clients": n_clients, "rate_per_client": rate, "duration_s": duration_s,
+           "frames_per_s": 30, "budget_bytes": 4 << 30,
+           "backlog": "log-uniform in [1, 50000] blocks", "requests": sum(c >= 0 for c in cl)}
+    policies = (("batched", dict(max_batch=64, chunk_records=0, iter_records=0)),
+                ("unbatched", dict(max_batch=1, chunk_records=0, iter_records=0)))
+    for name, pol in policies:
+        vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
+                     N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
+                     mc_cap_entries=MAX_BLOCKS * 64)
+        for i in range(warm_frames):
+            vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+        srv = Server(vol, n_clients, budget_bytes=4 << 30, **pol)
+        srv.set_versions(np.arange(n_clients), srv.versions_for_backlog(backlog))
+        torch.cuda.synchronize()
+        done = srv.run(t_ns, cl, frames, P, ids, erase_radius=ERASE_R)
+        st = srv.stats()
+        lat = np.array([(d["t_done_ns"] - d["t_arrival_ns"]) / 1e6 for d in done])
+        recs = int(sum(d["n_records"] for d in done))
+        span = (max(d["t_done_ns"] for d in done) - min(d["t_arrival_ns"] for d in done)) / 1e9
+        res = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "p999_ms": float(np.percentile(lat, 99.9)),
+               "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+               "blocks_per_s": recs / span, "records": recs, "requests_done": len(done),
+               "launches": int(st["iterations"]),
+               "requests_per_launch": len(done) / max(int(st["iterations"]), 1),
+               "change_records_scanned": int(st["changes_scanned"]),
+               "deferred_by_memory": int(st["deferred_memory"]),
+               "peak_buffer_bytes": int(st["bytes_peak"]),
+               "errors": sum(1 for d in done if d["flags"] & ~3)}
+        if name == "batched":
+            # one saturated launch: every client 16384 blocks behind, all in one batch
+            srv.set_policy(max_batch=64, chunk_records=0, iter_records=0)
+            srv.set_versions(np.arange(n_clients),
+                             srv.versions_for_backlog(np.full(n_clients, 4096)))
+            rid = [srv.submit(c) for c in range(n_clients)]
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            it0 = srv.stats()["iterations"]
+            e0.record()
+            srv.step()
+            e1.record()
+            torch.cuda.synchronize()
+            got = []
+            while len(got) < len(rid):   # consume (and free) results as they complete
+                srv.step()
+                for d in srv.poll():
+                    got.append(d)
+                    srv.release(d["id"])
+            one = srv.stats()["iterations"] - it0 == 1
+            ms = e0.elapsed_time(e1)
+            live = sum(d["n_records"] for d in got)
+            alg = live * (512 + 512 + 16)   # dense block read + written + header
+            res["saturated"] = {"requests": len(rid), "records": int(live), "ms": ms,
+                                "single_launch": bool(one)}
+            if one:
+                res["saturated"].update(blocks_per_s=live / (ms / 1e3),
+                                        algorithmic_GBs=alg / (ms / 1e3) / 1e9,
+                                        hbm_frac=alg / (ms / 1e3) / 1e9 / peak)
+        out[name] = res
+        srv.close()
+        vol.close()
+        torch.cuda.synchronize()
+    return out
 
 
 def diff_point(torch, dev, flush, reps=10, warm=3):

@@ -10,12 +10,13 @@
 //   entry still holds the record's key;
 //   removal of key k: lastrem[k] == e and k is not live.
 // One batch of requests is one launch of k_serve_extract: every request contributes a chunk
-// (a range of log records, or of pool entries for a reset), the chunks are cut into tiles of 32
-// records, and the persistent grid's warps take tiles in turn.  A warp tests its 32 records,
-// reserves output records with one atomic on the request's counter and copies each current
-// block's 512 B of cube indices (one 16 B word per lane).  The last CTA to finish publishes the
-// record counts of the requests that completed, moves those clients to their new version and
-// resets the per-request counters.
+// (a range of log records, or of pool entries for a reset), the chunks -- smallest first -- are
+// cut into tiles of 32 records, and the persistent grid's warps take tiles in turn.  A warp
+// tests its 32 records, reserves output records with one atomic on the request's counter and
+// copies each current block's 512 B of cube indices (one 16 B word per lane).  The warp that
+// finishes the last tile of a request's final chunk moves the client to its new version and
+// publishes the record count with the request's id as a token in mapped host memory, so a
+// small request completes as soon as its own tiles are done, not when the whole batch is.
 //
 // The host side (a scheduler, a first-fit arena for the stream buffer, the real-time loop of
 // vbh_serve_run) decides admission and chunking; the batch table travels as the kernel's
@@ -23,6 +24,7 @@
 #include <time.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -49,7 +51,7 @@ struct ServeItem {
   unsigned int flags;
   unsigned int cap;           // output records of the request's region
   unsigned int v0, v1;        // client version before / after the request
-  unsigned int pad;
+  unsigned int id;            // request id (completion token)
   unsigned long long out;     // byte offset of the region in the arena
 };
 
@@ -68,8 +70,8 @@ struct ServeCtx {
   unsigned int* rec_count;    // per slot, zero while the slot is free
   unsigned int* slot_err;     // per slot
   unsigned int* client_v;     // per client
-  unsigned int* iter_done;    // CTAs of the current launch that have finished
-  uint2* done_host;           // mapped: per slot (records, error bits)
+  unsigned int* tiles_done;   // per slot: tiles of the current chunk finished
+  uint4* done_host;           // mapped: per slot (records, error bits, token = request id)
 };
 
 __device__ __forceinline__ unsigned int rem_latest(const ServeLog& S, unsigned long long key) {
@@ -86,7 +88,6 @@ __global__ void __launch_bounds__(kServeThreads) k_serve_extract(const ServeBatc
                                                                  const ServeCtx X) {
   __shared__ unsigned int s_tiles[kServeMaxBatch + 1];
   __shared__ ServeItem s_it[kServeMaxBatch];
-  __shared__ int s_last;
   const unsigned int nb = B.n;
   for (unsigned int i = threadIdx.x; i <= nb; i += blockDim.x) s_tiles[i] = B.tiles[i];
   for (unsigned int i = threadIdx.x; i < nb; i += blockDim.x) s_it[i] = B.it[i];
@@ -185,27 +186,28 @@ __global__ void __launch_bounds__(kServeThreads) k_serve_extract(const ServeBatc
       }
     }
     if (err) atomicOr(&X.slot_err[it.slot], err);
-  }
-  // the last CTA publishes the requests that completed in this batch
-  __syncthreads();
-  if (threadIdx.x == 0) {
+    // the warp that finishes the chunk's last tile closes it; after a final chunk it publishes
+    // the request (every lane fences its writes before the warp's tile is counted)
     __threadfence();
-    s_last = atomicAdd(X.iter_done, 1u) == gridDim.x - 1u;
+    __syncwarp();
+    if (lane == 0u) {
+      const unsigned int chunk_tiles = s_tiles[a + 1] - s_tiles[a];
+      if (atomicAdd(&X.tiles_done[it.slot], 1u) == chunk_tiles - 1u) {
+        X.tiles_done[it.slot] = 0u;
+        if (it.flags & kItemFinal) {
+          __threadfence();
+          const unsigned int nr = atomicExch(&X.rec_count[it.slot], 0u);
+          const unsigned int ef = atomicExch(&X.slot_err[it.slot], 0u);
+          X.client_v[it.client] = it.v1;
+          volatile unsigned int* d = reinterpret_cast<volatile unsigned int*>(X.done_host + it.slot);
+          d[0] = nr;
+          d[1] = ef;
+          __threadfence_system();
+          d[2] = it.id;
+        }
+      }
+    }
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (unsigned int i = threadIdx.x; i < nb; i += blockDim.x) {
-    const ServeItem& it = s_it[i];
-    if (!(it.flags & kItemFinal)) continue;
-    const unsigned int n = atomicExch(&X.rec_count[it.slot], 0u);
-    const unsigned int e = atomicExch(&X.slot_err[it.slot], 0u);
-    X.client_v[it.client] = it.v1;
-    X.done_host[it.slot] = make_uint2(n, e);
-  }
-  __threadfence_system();
-  __syncthreads();
-  if (threadIdx.x == 0) *X.iter_done = 0u;
 }
 
 __global__ void k_live_seq(const unsigned long long* pkeys, const unsigned int* seq, unsigned int n,
@@ -300,14 +302,14 @@ struct vbh_serve {
   unsigned int* client_v = nullptr;
   unsigned int* rec_count = nullptr;
   unsigned int* slot_err = nullptr;
-  unsigned int* iter_done = nullptr;
+  unsigned int* tiles_done = nullptr;
   unsigned int* scratch = nullptr;   // two words for the store-only refresh
   unsigned char* arena = nullptr;
   // mapped host words
   unsigned int* sigma_host = nullptr;
   unsigned int* sigma_dev = nullptr;
-  uint2* done_host = nullptr;
-  uint2* done_dev = nullptr;
+  uint4* done_host = nullptr;
+  uint4* done_dev = nullptr;
   int grid = 0;
   // host scheduler
   Arena* heap = nullptr;
@@ -362,26 +364,35 @@ vbh_status check_policy(const vbh_serve_config& c) {
 
 }  // namespace
 
-// Retire finished iterations: read the record counts of the requests they completed.
+// Complete the requests whose token the device has published; retire finished iterations.
 vbh_status vbh_serve::reap() {
+  auto try_complete = [&](uint32_t& id) {
+    if (!id) return true;
+    Req& r = reqs[id];
+    const volatile unsigned int* dw = reinterpret_cast<volatile unsigned int*>(done_host + r.slot);
+    if (dw[2] != id) return false;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    const unsigned int n = dw[0], e = dw[1];
+    r.d.n_records = n;
+    if (e & kServeErrOverrun) r.d.flags |= VBH_SERVE_ERR_OVERRUN;
+    if (e & kServeErrCap) r.d.flags |= VBH_SERVE_ERR_CAPACITY;
+    if (e & 16u) r.d.flags |= VBH_SERVE_ERR_VERSION;
+    slot_req[r.slot] = -1;
+    client_busy[r.d.client] = 0;
+    v_mirror[r.d.client] = r.d.v_after;
+    finish(r, now_ns());
+    id = 0;
+    return true;
+  };
+  for (Iter& I : inflight)
+    for (uint32_t& id : I.finishing) try_complete(id);
   while (!inflight.empty()) {
     const cudaError_t q = cudaEventQuery(inflight.front().ev);
     if (q == cudaErrorNotReady) break;
     if (q != cudaSuccess) return fail(VBH_ERR_CUDA, std::string("serve: ") + cudaGetErrorString(q));
-    const uint64_t t = now_ns();
-    for (uint32_t id : inflight.front().finishing) {
-      Req& r = reqs[id];
-      const volatile unsigned int* dw = reinterpret_cast<volatile unsigned int*>(done_host + r.slot);
-      const uint2 d = make_uint2(dw[0], dw[1]);
-      r.d.n_records = d.x;
-      if (d.y & kServeErrOverrun) r.d.flags |= VBH_SERVE_ERR_OVERRUN;
-      if (d.y & kServeErrCap) r.d.flags |= VBH_SERVE_ERR_CAPACITY;
-      if (d.y & 16u) r.d.flags |= VBH_SERVE_ERR_VERSION;
-      slot_req[r.slot] = -1;
-      client_busy[r.d.client] = 0;
-      v_mirror[r.d.client] = r.d.v_after;
-      finish(r, t);
-    }
+    for (uint32_t& id : inflight.front().finishing)
+      if (!try_complete(id))
+        return fail(VBH_ERR_CUDA, "serve: a batch finished without completing a request");
     ev_free.push_back(inflight.front().ev);
     inflight.pop_front();
   }
@@ -488,6 +499,7 @@ vbh_status vbh_serve::launch() {
     it.v0 = r.d.v_before;
     it.v1 = r.d.v_after;
     it.out = r.off;
+    it.id = r.d.id;
     it.flags = (r.scan ? kItemScan : 0u) | (r.next == r.start ? kItemFirst : 0u);
     r.next += (unsigned int)take;
     if (r.next == r.end) {
@@ -496,12 +508,17 @@ vbh_status vbh_serve::launch() {
     } else {
       keep.push_back(active[a]);
     }
-    B.tiles[B.n + 1] = B.tiles[B.n] + (unsigned int)((take + 31u) / 32u);
     total += take;
     B.n += 1;
   }
   active.swap(keep);
   if (B.n == 0) return VBH_OK;
+  // smallest chunks first: their tiles go to the first wave of warps
+  std::sort(B.it, B.it + B.n, [](const ServeItem& x, const ServeItem& y) {
+    return x.hi - x.lo < y.hi - y.lo;
+  });
+  for (unsigned int i = 0; i < B.n; ++i)
+    B.tiles[i + 1] = B.tiles[i] + (B.it[i].hi - B.it[i].lo + 31u) / 32u;
   ServeCtx X;
   X.t = h->table();
   X.pool = h->pool();
@@ -510,7 +527,7 @@ vbh_status vbh_serve::launch() {
   X.rec_count = rec_count;
   X.slot_err = slot_err;
   X.client_v = client_v;
-  X.iter_done = iter_done;
+  X.tiles_done = tiles_done;
   X.done_host = done_dev;
   const unsigned int tiles = B.tiles[B.n];
   const unsigned int want = (tiles + kServeWarps - 1u) / kServeWarps;
@@ -572,16 +589,16 @@ vbh_status vbh_serve_create(vbh_handle* h, const vbh_serve_config* cfg, vbh_serv
   SERVE_CUDA(cudaMalloc(&s->client_v, sizeof(unsigned int) * c.n_clients));
   SERVE_CUDA(cudaMalloc(&s->rec_count, sizeof(unsigned int) * kServeMaxBatch));
   SERVE_CUDA(cudaMalloc(&s->slot_err, sizeof(unsigned int) * kServeMaxBatch));
-  SERVE_CUDA(cudaMalloc(&s->iter_done, sizeof(unsigned int)));
+  SERVE_CUDA(cudaMalloc(&s->tiles_done, sizeof(unsigned int) * kServeMaxBatch));
   SERVE_CUDA(cudaMalloc(&s->scratch, 2 * sizeof(unsigned int)));
   SERVE_CUDA(cudaMalloc(&s->sl_dev, sizeof(ServeLog)));
   SERVE_CUDA(cudaMalloc(&s->arena, c.budget_bytes));
   SERVE_CUDA(cudaHostAlloc(&s->sigma_host, sizeof(unsigned int), cudaHostAllocMapped));
   SERVE_CUDA(cudaHostGetDevicePointer((void**)&s->sigma_dev, s->sigma_host, 0));
-  SERVE_CUDA(cudaHostAlloc(&s->done_host, sizeof(uint2) * kServeMaxBatch, cudaHostAllocMapped));
+  SERVE_CUDA(cudaHostAlloc(&s->done_host, sizeof(uint4) * kServeMaxBatch, cudaHostAllocMapped));
   SERVE_CUDA(cudaHostGetDevicePointer((void**)&s->done_dev, s->done_host, 0));
   *s->sigma_host = 0u;
-  std::memset(s->done_host, 0, sizeof(uint2) * kServeMaxBatch);
+  std::memset(s->done_host, 0, sizeof(uint4) * kServeMaxBatch);
   cudaStream_t st = h->stream;
   SERVE_CUDA(cudaMemsetAsync(s->log, 0, sizeof(LogEnt) * (size_t)s->log_cap, st));
   SERVE_CUDA(cudaMemsetAsync(s->rem_keys, 0xFF, sizeof(unsigned long long) * rem_n, st));
@@ -589,7 +606,7 @@ vbh_status vbh_serve_create(vbh_handle* h, const vbh_serve_config* cfg, vbh_serv
   SERVE_CUDA(cudaMemsetAsync(s->client_v, 0, sizeof(unsigned int) * c.n_clients, st));
   SERVE_CUDA(cudaMemsetAsync(s->rec_count, 0, sizeof(unsigned int) * kServeMaxBatch, st));
   SERVE_CUDA(cudaMemsetAsync(s->slot_err, 0, sizeof(unsigned int) * kServeMaxBatch, st));
-  SERVE_CUDA(cudaMemsetAsync(s->iter_done, 0, sizeof(unsigned int), st));
+  SERVE_CUDA(cudaMemsetAsync(s->tiles_done, 0, sizeof(unsigned int) * kServeMaxBatch, st));
   SERVE_CUDA(cudaMemsetAsync(h->seq, 0, sizeof(unsigned int) * nb, st));
   ServeLog L{};
   L.log = s->log;
@@ -630,7 +647,7 @@ vbh_status vbh_serve_destroy(vbh_serve* s) {
   for (auto& I : s->inflight) cudaEventDestroy(I.ev);
   for (auto e : s->ev_free) cudaEventDestroy(e);
   void* ptrs[] = {s->log, s->store, s->rem_keys, s->rem_seq, s->client_v, s->rec_count,
-                  s->slot_err, s->iter_done, s->scratch, s->sl_dev, s->arena};
+                  s->slot_err, s->tiles_done, s->scratch, s->sl_dev, s->arena};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->sigma_host) cudaFreeHost(s->sigma_host);
@@ -642,6 +659,9 @@ vbh_status vbh_serve_destroy(vbh_serve* s) {
 
 vbh_status vbh_serve_set_policy(vbh_serve* s, const vbh_serve_config* cfg) {
   if (!s || !cfg) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  VBH_CUDA(cudaStreamSynchronize(s->h->stream));   // retire launches whose requests are done
+  vbh_status rs = s->reap();
+  if (rs != VBH_OK) return rs;
   if (!s->pending.empty() || !s->inflight.empty() ||
       std::any_of(s->slot_req.begin(), s->slot_req.end(), [](int r) { return r >= 0; }))
     return fail(VBH_ERR_INVALID_ARG, "server is not idle");
