@@ -32,12 +32,15 @@ def make_volume(cam, s, mu, n_buckets, max_blocks, zmax):
 
 
 def frame(vol, orc, depth, T, fid, R):
+    """One fused frame on the GPU (erase, fuse, touched MC extraction) and the same in the
+    oracle; returns the oracle's refreshed block set M and removal records of the frame."""
     vol.process_frame(torch.from_numpy(depth).cuda(), T, fid, R)
     if orc is not None:
         if R > 0:   # process_frame takes radius 0 as "no erase"
             orc.erase_radius(T[:, 3], R)
         orc.integrate(depth, T)
-        orc.mc_set(0)
+        return orc.mc_set(0)
+    return None
 
 
 def result_map(srv, rid):
@@ -135,6 +138,50 @@ def test_reset_request_serves_the_full_model(room):
     apply(replica, m, flags)
     assert_matches_model(replica, vol, orc)
     assert srv.versions()[0] == d["v_after"]
+    srv.close()
+    vol.close()
+
+
+def test_deltas_match_the_oracle_frame_sets(room):
+    """From a version taken after frame a, a request after frame b holds exactly the oracle's
+    blocks refreshed in frames a+1..b that are live at b (info = the last frame that refreshed
+    them, MC indices as the oracle's at every cube clear of the margin) and removal records
+    for the keys removed in those frames that are not live at b."""
+    from paper_1805_03709_b300.serve import Server
+    cam, poses, depth = room
+    vol, orc = make_volume(cam, 0.005, 0.02, 1 << 16, 1 << 17, 4.0)
+    frame(vol, orc, depth[0], poses[0], 1, 2.5)
+    srv = Server(vol, n_clients=4, budget_bytes=1 << 28, log_bits=20)
+    sigma = {0: srv.stats()["sigma"]}
+    Ms, Rs = {}, {}
+    for i in range(1, len(poses)):
+        M, R = frame(vol, orc, depth[i], poses[i], i + 1, 2.5)
+        Ms[i] = set(map(tuple, M.tolist()))
+        Rs[i] = set(map(tuple, R.tolist()))
+        sigma[i] = srv.stats()["sigma"]
+    b = len(poses) - 1
+    live = set(map(tuple, orc.dump()[0].tolist()))
+    removed_seen = 0
+    for c, a in enumerate((0, 4, 8, b - 1)):
+        srv.set_versions([c], [sigma[a]])
+        d, m, flags = serve_one(srv, c)
+        assert flags == 0 and d["v_after"] == sigma[b]
+        exp_live = {k for f in range(a + 1, b + 1) for k in Ms[f]} & live
+        exp_rem = {k for f in range(a + 1, b + 1) for k in Rs[f]} - live
+        got_live = {k for k, v in m.items() if v[1] is not None}
+        got_rem = {k for k, v in m.items() if v[1] is None}
+        assert got_live == exp_live
+        assert got_rem == exp_rem
+        removed_seen += len(got_rem)
+        for k in got_live:
+            last = max(f for f in range(a + 1, b + 1) if k in Ms[f])
+            assert m[k][0] == last + 1, k
+        keys = np.array(sorted(got_live), np.int32)
+        idx, margin = orc.mc_dense(keys)
+        for j, k in enumerate(map(tuple, keys.tolist())):
+            sel = margin[j] > MC_MARGIN
+            assert np.array_equal(m[k][1][sel], idx[j][sel]), k
+    assert removed_seen > 0
     srv.close()
     vol.close()
 
