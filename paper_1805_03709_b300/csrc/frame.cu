@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
                                                              DevCounters* cnt) {
   __shared__ unsigned long long set[kTileSet];
   __shared__ FrameParams fp;
+  __shared__ unsigned int s_warp[kTileThreads / 32];
+  __shared__ unsigned int s_base;
+  const unsigned int lane = threadIdx.x & 31u;
   load_frame_params(fp, ctl);
   for (int i = threadIdx.x; i < kTileSet; i += kTileThreads) set[i] = kEmpty;
   __syncthreads();
@@ -85,8 +88,12 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
           unsigned int h = hash_mix(key) & (kTileSet - 1);
           bool placed = false;
           for (int probe = 0; probe < 64; ++probe) {
-            unsigned long long old = atomicCAS(&set[h], kEmpty, key);
-            if (old == kEmpty || old == key) { placed = true; break; }
+            const unsigned long long seen = set[h];   // most keys are already in the set
+            if (seen == key) { placed = true; break; }
+            if (seen == kEmpty) {
+              const unsigned long long old = atomicCAS(&set[h], kEmpty, key);
+              if (old == kEmpty || old == key) { placed = true; break; }
+            }
             h = (h + 1) & (kTileSet - 1);
           }
           if (!placed) {   // tile set saturated: hand the key straight to the global list
@@ -97,13 +104,41 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kTileSet; i += kTileThreads) {
-      const unsigned long long key = set[i];
-      const bool has = key != kEmpty;
-      const unsigned int k = warp_append(&cnt->n_cand, has, 0xFFFFFFFFu);
-      if (has) {
-        if (k < cap) cand[k] = key;
-        set[i] = kEmpty;
+    // the tile's distinct keys go out with one reservation per CTA (atomics on one address
+    // serialise in L2; one per warp would bound the kernel)
+    constexpr int kPer = kTileSet / kTileThreads;
+    unsigned long long mine[kPer];
+    unsigned int nmine = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      mine[j] = set[threadIdx.x * kPer + j];
+      nmine += mine[j] != kEmpty;
+    }
+    unsigned int incl = nmine;   // inclusive scan over the warp, then over the warps
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if ((int)lane >= d) incl += v;
+    }
+    if (lane == 31u) s_warp[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int run = 0;
+      for (int w = 0; w < kTileThreads / 32; ++w) {
+        const unsigned int c = s_warp[w];
+        s_warp[w] = run;
+        run += c;
+      }
+      s_base = run ? atomicAdd(&cnt->n_cand, run) : 0u;
+    }
+    __syncthreads();
+    unsigned int o = s_base + s_warp[threadIdx.x >> 5] + incl - nmine;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (mine[j] != kEmpty) {
+        if (o < cap) cand[o] = mine[j];
+        ++o;
+        set[threadIdx.x * kPer + j] = kEmpty;
       }
     }
     __syncthreads();
@@ -285,10 +320,9 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
         if (wr) vout[lane + 32 * m] = v;
         const unsigned int negm = __ballot_sync(0xFFFFFFFFu, v.x < 0.0f);
         const unsigned int valm = __ballot_sync(0xFFFFFFFFu, v.y > 0.0f);
-        const unsigned int wrm = __ballot_sync(0xFFFFFFFFu, wr);
         if (lane == (unsigned)m) mword = negm;
         if (lane == 16u + m) mword = valm;
-        if (lane == 0) my_upd += __popc(wrm);
+        my_upd += wr ? 1u : 0u;
       }
     }
     pool.masks[32u * p + lane] = mword;   // one coalesced 128 B store per block

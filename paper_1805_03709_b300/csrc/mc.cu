@@ -28,6 +28,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMcThreads = 128;   // 4 warps, one block each
+constexpr unsigned int kStage = 1024;        // MC entries staged per warp (>= 512, one block)
+constexpr unsigned int kStageBlocks = 16;    // blocks staged per warp (<= 32)
 constexpr unsigned long long kLo7 = 0x7F7F7F7F7F7F7F7Full;
 constexpr unsigned long long kHi1 = 0x8080808080808080ull;
 
@@ -173,12 +175,16 @@ __device__ __forceinline__ unsigned int row9(const unsigned int (*m)[32], int ki
   return ((m[nb][word] >> sh) & 0xFFu) | (((m[nb + 1][word] >> sh) & 1u) << 8);
 }
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_extract(TableView t, PoolView pool,
+__global__ void __launch_bounds__(kMcThreads, 6) k_mc_extract(TableView t, PoolView pool,
                                                           DevCounters* cnt, const FrameCtl* ctl,
                                                           const unsigned int* mset,
                                                           const unsigned long long* tombrec) {
   __shared__ unsigned long long spread[256];   // bit i of b -> bit 8 i
   __shared__ unsigned int msk[kMcThreads / 32][8][32];
+  __shared__ unsigned short stage_loc[kMcThreads / 32][kStage];
+  __shared__ unsigned char stage_idx[kMcThreads / 32][kStage];
+  __shared__ unsigned int stage_r[kMcThreads / 32][kStageBlocks];
+  __shared__ unsigned int stage_off[kMcThreads / 32][kStageBlocks];
   int* const rec_keys3 = ctl->rec_keys3;
   unsigned int* const rec_info = ctl->rec_info;
   unsigned int* const rec_off = ctl->rec_off;
@@ -210,49 +216,82 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_extract(TableView t, PoolView
   const unsigned int nwarps = gridDim.x * (kMcThreads / 32);
   unsigned int(*m)[32] = msk[warp];
   bool overflow = false;
-  for (unsigned int r = blockIdx.x * (kMcThreads / 32) + warp; r < total; r += nwarps) {
-    if (r >= n_m) {   // removal record
-      if (lane == 0) {
-        const unsigned long long tk = tombrec[r - n_m];
-        if (emit && r < cap_blocks) {
-          const int3 k = unpack_key(tk);
-          rec_keys3[3u * r] = k.x;
-          rec_keys3[3u * r + 1] = k.y;
-          rec_keys3[3u * r + 2] = k.z;
-          rec_info[r] = 0x80000000u | tomb_version;
-          rec_off[r] = 0u;
-          rec_cnt[r] = 0u;
-        }
-        if (sl) {
-          const unsigned int e = seq0 + r;
-          LogEnt le;
-          le.key = tk | kLogRemoved;
-          le.aux = tomb_version;
-          le.seq = e;
-          sl->log[e & sl->log_mask] = le;
-          note_removal(sl, tk, e);
-        }
+  // Entries are staged per warp in shared memory and leave with one reservation per flush
+  // (atomics on one address serialise in L2: one per block would bound the kernel).
+  unsigned short* const st_loc = stage_loc[warp];
+  unsigned char* const st_idx = stage_idx[warp];
+  unsigned int* const st_r = stage_r[warp];
+  unsigned int* const st_off = stage_off[warp];
+  unsigned int fill = 0u, nblk = 0u;   // warp-uniform
+  auto flush = [&]() {
+    __syncwarp();
+    unsigned int base = 0u;
+    if (lane == 0 && fill) base = atomicAdd(n_entries_dev, fill);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if ((unsigned long long)base + fill <= cap_entries) {
+      for (unsigned int i = lane; i < fill; i += 32u) {
+        ent_local[base + i] = st_loc[i];
+        ent_idx[base + i] = st_idx[i];
       }
-      continue;
+    } else {
+      overflow = true;
     }
-    const unsigned int q = mset[r];
-    const unsigned long long key = pool.pkeys[q];
-    const int3 k = unpack_key(key);
-    unsigned int nb = kNone;
+    if (lane < nblk && st_r[lane] < cap_blocks) rec_off[st_r[lane]] = base + st_off[lane];
+    __syncwarp();
+    fill = 0u;
+    nblk = 0u;
+  };
+  // Refreshed blocks, software-pipelined over the warp's blocks: the next block's list entry,
+  // key and first neighbour probe are loaded while the current block is classified.
+  unsigned int r = blockIdx.x * (kMcThreads / 32) + warp;
+  unsigned int q = 0u, nb = kNone;
+  unsigned long long key = kEmpty;
+  if (r < n_m) {
+    q = mset[r];
+    key = pool.pkeys[q];
     if (lane == 0) {
       nb = q;
     } else if (lane < 8) {
-      const int x = k.x + (int)(lane & 1u), y = k.y + (int)((lane >> 1) & 1u),
-                z = k.z + (int)((lane >> 2) & 1u);
+      const int3 k0 = unpack_key(key);
+      const int x = k0.x + (int)(lane & 1u), y = k0.y + (int)((lane >> 1) & 1u),
+                z = k0.z + (int)((lane >> 2) & 1u);
       unsigned int val;
       if (key_ok(x, y, z) && thread_find(t, pack_key(x, y, z), &val) != kNone) nb = val;
     }
+  }
+  for (; r < n_m; r += nwarps) {
+    unsigned int mw[8];   // mask word `lane` of the block and its 7 positive neighbours
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
       const unsigned int qn = __shfl_sync(0xFFFFFFFFu, nb, n);
-      m[n][lane] = qn != kNone ? __ldcg(pool.masks + 32u * qn + lane) : 0u;
+      mw[n] = qn != kNone ? __ldcg(pool.masks + 32u * qn + lane) : 0u;
     }
+    const unsigned int rn = r + nwarps;
+    unsigned int q_next = 0u;
+    unsigned long long key_next = kEmpty, nkey = kEmpty;
+    ulonglong2 pb0 = make_ulonglong2(0ull, 0ull), pb1 = pb0, pb2 = pb0, pb3 = pb0;
+    if (rn < n_m) {
+      q_next = mset[rn];
+      key_next = pool.pkeys[q_next];
+      if (lane >= 1u && lane < 8u) {
+        const int3 kn = unpack_key(key_next);
+        const int x = kn.x + (int)(lane & 1u), y = kn.y + (int)((lane >> 1) & 1u),
+                  z = kn.z + (int)((lane >> 2) & 1u);
+        if (key_ok(x, y, z)) {
+          nkey = pack_key(x, y, z);
+          const ulonglong2* bp = reinterpret_cast<const ulonglong2*>(
+              &t.slots[4u * home_bucket(nkey, t.bmask, t.hash_fn)]);
+          pb0 = __ldcg(bp);
+          pb1 = __ldcg(bp + 1);
+          pb2 = __ldcg(bp + 2);
+          pb3 = __ldcg(bp + 3);
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) m[n][lane] = mw[n];
     __syncwarp();
+    const int3 k = unpack_key(key);
     unsigned long long idx8[2], nz[2];
     unsigned int mine = 0;
 #pragma unroll
@@ -286,47 +325,84 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_extract(TableView t, PoolView
         sl->log[e & sl->log_mask] = le;
       }
     }
-    if (!emit) {
-      __syncwarp();   // the lattice in shared memory is refilled for the next block
-      continue;
-    }
-    unsigned int incl = mine;
+    if (emit) {
+      unsigned int incl = mine;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-      if ((int)lane >= d) incl += v;
-    }
-    const unsigned int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    unsigned int base = 0;
-    if (lane == 0 && tot) base = atomicAdd(n_entries_dev, tot);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    const bool fits = (unsigned long long)base + tot <= cap_entries;
-    if (fits) {
-      unsigned int o = base + incl - mine;
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if ((int)lane >= d) incl += v;
+      }
+      const unsigned int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      if (fill + tot > kStage || nblk == kStageBlocks) flush();
+      unsigned int o = fill + incl - mine;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int row = (int)lane + 32 * h;
         unsigned long long bits = nz[h];
         while (bits) {
           const int x = (__ffsll((long long)bits) - 1) >> 3;
-          ent_local[o] = (unsigned short)(x + 8 * row);
-          ent_idx[o] = (unsigned char)(idx8[h] >> (8 * x));
+          st_loc[o] = (unsigned short)(x + 8 * row);
+          st_idx[o] = (unsigned char)(idx8[h] >> (8 * x));
           ++o;
           bits &= bits - 1ull;
         }
       }
-    } else {
-      overflow = true;
+      if (lane == 0) {
+        st_r[nblk] = r;
+        st_off[nblk] = fill;
+        if (r < cap_blocks) {
+          rec_keys3[3u * r] = k.x;
+          rec_keys3[3u * r + 1] = k.y;
+          rec_keys3[3u * r + 2] = k.z;
+          rec_info[r] = pool.version[q] & 0x7FFFFFFFu;
+          rec_cnt[r] = tot;
+        }
+      }
+      fill += tot;
+      nblk += 1u;
     }
-    if (lane == 0 && r < cap_blocks) {
-      rec_keys3[3u * r] = k.x;
-      rec_keys3[3u * r + 1] = k.y;
-      rec_keys3[3u * r + 2] = k.z;
-      rec_info[r] = pool.version[q] & 0x7FFFFFFFu;
-      rec_off[r] = base;
-      rec_cnt[r] = tot;
+    __syncwarp();   // the lattice in shared memory is refilled for the next block
+    // the next block's neighbours: almost always settled by the prefetched home bucket
+    unsigned int nb_next = kNone;
+    if (lane == 0) {
+      nb_next = q_next;
+    } else if (nkey != kEmpty) {
+      if (pb0.x == nkey) nb_next = (unsigned int)pb0.y;
+      else if (pb1.x == nkey) nb_next = (unsigned int)pb1.y;
+      else if (pb2.x == nkey) nb_next = (unsigned int)pb2.y;
+      else if (pb3.x == nkey) nb_next = (unsigned int)pb3.y;
+      else if (pb0.x != kEmpty && pb1.x != kEmpty && pb2.x != kEmpty && pb3.x != kEmpty) {
+        unsigned int val;   // full home bucket: continue the probe sequence
+        if (thread_find(t, nkey, &val) != kNone) nb_next = val;
+      }
     }
-    __syncwarp();
+    q = q_next;
+    key = key_next;
+    nb = nb_next;
+  }
+  if (emit) flush();
+  for (; r < total; r += nwarps) {   // removal records
+    if (lane == 0) {
+      const unsigned long long tk = tombrec[r - n_m];
+      if (emit && r < cap_blocks) {
+        const int3 kk = unpack_key(tk);
+        rec_keys3[3u * r] = kk.x;
+        rec_keys3[3u * r + 1] = kk.y;
+        rec_keys3[3u * r + 2] = kk.z;
+        rec_info[r] = 0x80000000u | tomb_version;
+        rec_off[r] = 0u;
+        rec_cnt[r] = 0u;
+      }
+      if (sl) {
+        const unsigned int e = seq0 + r;
+        LogEnt le;
+        le.key = tk | kLogRemoved;
+        le.aux = tomb_version;
+        le.seq = e;
+        sl->log[e & sl->log_mask] = le;
+        note_removal(sl, tk, e);
+      }
+    }
   }
   if (emit && (overflow || (total > cap_blocks && blockIdx.x == 0)) && lane == 0)
     atomicOr(&cnt->err, kErrStream);
