@@ -418,7 +418,7 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   h->launches += 3;
   h->stage_end();
   h->stage_begin(VBH_STAGE_INTEGRATE);
-  launch_integrate(h->L, h->ctl, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
+  launch_integrate(h->L, c.fp, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
                    h->cnt);
   h->launches += 1;
   h->stage_end();
@@ -467,8 +467,9 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
                             h->cand_cap, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
                             h->ctl);
   if (timed) cudaEventRecordWithFlags(ea, h->cap_stream, cudaEventRecordExternal);
-  launch_integrate(Lc, h->ctl, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
-                   h->cnt);
+  // the fusion node takes the frame parameters by value: vbh_process_frame patches them
+  launch_integrate(Lc, base_ctl(h, nullptr).fp, pool, h->touched, h->tkey, h->tdepth,
+                   &h->cnt->n_touched, h->cnt);
   if (timed) cudaEventRecordWithFlags(eb, h->cap_stream, cudaEventRecordExternal);
   launch_mset_touched(Lc, t, pool, h->cnt, h->ctl, h->touched, &h->cnt->n_touched, h->removed,
                       &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec);
@@ -480,6 +481,25 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
     return fail(VBH_ERR_CUDA, std::string("frame graph capture: ") +
                                   cudaGetErrorString(e != cudaSuccess ? e : le));
   h->frame_graph = g;
+  {
+    size_t n = 0;
+    VBH_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    VBH_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+    h->integ_node = nullptr;
+    for (cudaGraphNode_t node : nodes) {
+      cudaGraphNodeType ty;
+      VBH_CUDA(cudaGraphNodeGetType(node, &ty));
+      if (ty != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp{};
+      VBH_CUDA(cudaGraphKernelNodeGetParams(node, &kp));
+      if (kp.func == integrate_kernel()) {
+        h->integ_node = node;
+        h->integ_kp = kp;
+      }
+    }
+    if (!h->integ_node) return fail(VBH_ERR_CUDA, "frame graph: fusion node not found");
+  }
   if (timed) {
     size_t n = 0;
     VBH_CUDA(cudaGraphGetNodes(g, nullptr, &n));
@@ -544,6 +564,20 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
   }
   h->ring_host[seq % kRing] = c;
   std::atomic_thread_fence(std::memory_order_seq_cst);
+  {   // this frame's parameters into the fusion node (applies to this and later launches)
+    FrameParams fpv = c.fp;
+    PoolView pv = h->pool();
+    const unsigned int* touched = h->touched;
+    const unsigned long long* tkey = h->tkey;
+    const float2* tdepth = h->tdepth;
+    const unsigned int* n_touched = &h->cnt->n_touched;
+    DevCounters* cntp = h->cnt;
+    void* args[] = {&fpv, &pv, &touched, &tkey, &tdepth, &n_touched, &cntp};
+    cudaKernelNodeParams kp = h->integ_kp;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    VBH_CUDA(cudaGraphExecKernelNodeSetParams(h->frame_exec, h->integ_node, &kp));
+  }
   if (timed) {
     cudaEvent_t a = h->get_event(), b = h->get_event();
     VBH_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->frame_exec, h->ev_node[0], a));

@@ -200,27 +200,31 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int 
 #ifndef VBH_FUSE_MIN_CTAS
 #define VBH_FUSE_MIN_CTAS 1
 #endif
+#ifndef VBH_FUSE_BUFS
+#define VBH_FUSE_BUFS 1
+#endif
 constexpr int kWarps = kIntThreads / 32;
 constexpr int kGroup = VBH_FUSE_GROUP;   // voxels per lane whose depth fetches overlap
+constexpr unsigned int kBufs = VBH_FUSE_BUFS;   // voxel buffers per warp (1: more warps per SM)
 
+// The frame parameters arrive by value (the frame graph patches this node's argument every
+// frame), so the compiler takes them as constant-bank operands instead of holding ~25 of them
+// in registers; with one 4 KiB buffer per warp that lets 2 x more warps reside per SM to hide
+// the depth-gather latency.
 __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
-    k_integrate(const FrameCtl* ctl, PoolView pool, const unsigned int* touched,
-                const unsigned long long* tkey,
-                                                           const float2* tdepth,
-                                                           const unsigned int* n_touched,
-                                                           DevCounters* cnt) {
-  __shared__ __align__(128) float2 sbuf[kWarps][2][512];
-  __shared__ __align__(8) unsigned long long sbar[kWarps][2];
+    k_integrate(const FrameParams fp, PoolView pool, const unsigned int* touched,
+                const unsigned long long* tkey, const float2* tdepth,
+                const unsigned int* n_touched, DevCounters* cnt) {
+  __shared__ __align__(128) float2 sbuf[kWarps][kBufs][512];
+  __shared__ __align__(8) unsigned long long sbar[kWarps][kBufs];
   __shared__ unsigned int s_upd;
-  __shared__ FrameParams fp;
   if (threadIdx.x == 0) s_upd = 0;
   const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    mbar_init(&sbar[warp][0]);
-    mbar_init(&sbar[warp][1]);
+    for (unsigned int q = 0; q < kBufs; ++q) mbar_init(&sbar[warp][q]);
     mbar_fence_init();
   }
-  load_frame_params(fp, ctl);   // includes __syncthreads
+  __syncthreads();
   const unsigned int n = *n_touched;
   const int lx = lane & 7, ly0 = lane >> 3;      // voxel (lx, ly0 + 4 (m & 1), m >> 1)
   const float R0 = fp.R[0], R1 = fp.R[1], R2 = fp.R[2], R3 = fp.R[3], R4 = fp.R[4],
@@ -249,13 +253,14 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
   }
   bool alive = true;
   for (unsigned int it = 0; b < n && alive; ++it, b += stride) {
-    const unsigned int cur = it & 1u;
-    // start the next block's copy into the other buffer (read completely last iteration)
+    const unsigned int cur = kBufs == 2u ? (it & 1u) : 0u;
+    // two buffers: start the next block's copy into the other one (read completely last
+    // iteration); one buffer: it is started after this block's reads, below
     const unsigned int bn = b + stride;
     unsigned int rec_next = 0;
     if (bn < n) {
       rec_next = touched[bn];
-      if (lane == 0 && !(rec_next & kTouchedFresh))
+      if (kBufs == 2u && lane == 0 && !(rec_next & kTouchedFresh))
         bulk_load(sbuf[warp][cur ^ 1u], pool.vox + 512ull * (rec_next & ~kTouchedFresh), 4096u,
                   &sbar[warp][cur ^ 1u]);
     }
@@ -328,11 +333,14 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
     pool.masks[32u * p + lane] = mword;   // one coalesced 128 B store per block
     if (lane == 0 && fresh) pool.state[p] = 0u;
     __syncwarp();   // every lane is done with buffer `cur` before it is refilled
+    if (kBufs == 1u && bn < n && lane == 0 && !(rec_next & kTouchedFresh))
+      bulk_load(sbuf[warp][0], pool.vox + 512ull * (rec_next & ~kTouchedFresh), 4096u,
+                &sbar[warp][0]);
     rec = rec_next;
   }
   if (!alive) {
     // wait (bounded) for this warp's copies still in flight before the CTA may exit
-    for (int q = 0; q < 2; ++q)
+    for (unsigned int q = 0; q < kBufs; ++q)
       for (unsigned int i = 0; i < (1u << 20) && !mbar_try_wait(&sbar[warp][q], (parity >> q) & 1u);
            ++i) {
       }
@@ -359,13 +367,15 @@ void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int heig
   k_alloc_keys<<<tiles < grid ? tiles : grid, kTileThreads, 0, L.stream>>>(ctl, cand, cap, cnt);
 }
 
-void launch_integrate(const Launch& L, const FrameCtl* ctl, PoolView pool,
+void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
                       const unsigned int* touched, const unsigned long long* tkey,
                       const float2* tdepth, const unsigned int* n_touched, DevCounters* cnt) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_integrate, kIntThreads, L.sms);
-  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(ctl, pool, touched, tkey, tdepth, n_touched,
+  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(fp, pool, touched, tkey, tdepth, n_touched,
                                                   cnt);
 }
+
+const void* integrate_kernel() { return reinterpret_cast<const void*>(&k_integrate); }
 
 }  // namespace vbh

@@ -89,6 +89,8 @@ struct vbh_handle {
   unsigned long long* dev_seq = nullptr;   // device memory
   unsigned long long host_seq = 0;
   cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
+  cudaGraphNode_t integ_node = nullptr;   // fusion node: its by-value frame parameters are
+  cudaKernelNodeParams integ_kp{};        // patched before every launch
   bool graph_timed = false;
   uint64_t graph_kernels = 0;
   // bookkeeping
