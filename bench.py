@@ -354,6 +354,8 @@ def main():
         state["vol"] = vol
         for i in range(args.warmup):
             step(i, i + 1)
+        vol.timing(("mc",))   # MC extraction timed on the replay (kept out of the main loop)
+        vol.timing_read(reset=True)
         host_depth = torch.from_numpy(depth).pin_memory()
         d_in = torch.empty((cam.height, cam.width), dtype=torch.uint16, device=dev)
         s = vol.stream
@@ -367,6 +369,7 @@ def main():
         h2d = d2h = 0
         torch.cuda.synchronize()
         t_e2e = 0.0
+        mc_counts = []
         for k in range(args.steps):
             i = args.warmup + k
             f = i % N_FRAMES
@@ -388,12 +391,39 @@ def main():
             t_e2e += time.perf_counter() - t0
             h2d += depth_bytes
             d2h += 8 + nb * 24 + ne * 3
+            n_rem = int((h_info[:nb].numpy().view(np.uint32) >> 31).sum())
+            mc_counts.append((nb - n_rem, n_rem, ne))
+        mc_timing = vol.timing_read(reset=True)
+        vol.timing(())
         if ws > 1:
             t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             t_e2e = float(t.item())
         e2e = {"value": ws * args.steps / t_e2e, "unit": "frames/s",
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    # MC extraction roofline: the same frames' MC extraction, timed (CUDA events around the
+    # kernel on the volume's stream) and counted on the e2e replay (or a replay of its own)
+    if args.no_e2e:
+        mc_counts, mc_timing = mc_replay(torch, cam, D, poses, args)
+    mc_line = None
+    if mc_counts and mc_timing[0].get("mc", 0.0) > 0:
+        live_b = sum(c[0] for c in mc_counts) / len(mc_counts)
+        rem_b = sum(c[1] for c in mc_counts) / len(mc_counts)
+        ents = sum(c[2] for c in mc_counts) / len(mc_counts)
+        mc_n = max(int(mc_timing[1]["mc"]), 1)
+        mc_ms = mc_timing[0]["mc"] / mc_n
+        mc_alg = live_b * (512 * 8 + 24) + rem_b * 24 + ents * 3
+        mc_ach = mc_alg / (mc_ms / 1e3) / 1e9
+        mc_line = {"bound": "hbm", "kernel": "k_mc_extract", "achieved": mc_ach, "peak": peak,
+                   "peak_source": peak_src, "unit": "GB/s", "frac": mc_ach / peak,
+                   "algorithmic_bytes_per_launch": mc_alg, "avg_launch_ms": mc_ms,
+                   "blocks_per_launch": live_b, "removal_records_per_launch": rem_b,
+                   "entries_per_launch": ents,
+                   "definition": "8 B (TSDF + weight) per voxel of every block in the MC set, "
+                                 "24 B per record, 3 B per nonzero index; the kernel itself "
+                                 "reads the 128 B sign/weight masks per block instead of the "
+                                 "voxels (its DRAM traffic is a few % of this)"}
 
     hash_pt = None
     if not args.no_hash:
@@ -420,6 +450,7 @@ def main():
                          "algorithmic_bytes_per_launch": alg_bytes / n_launch,
                          "avg_launch_ms": integ_ms / n_launch,
                          "share_of_step": integ_ms / ms_total if ms_total else None},
+            "roofline_mc": mc_line,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
@@ -498,6 +529,29 @@ def hash_point(torch, dev, flush, peak):
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+def mc_replay(torch, cam, D, poses, args):
+    """(live blocks, removal records, entries) of each timed frame's MC extraction, from an
+    untimed replay of the same frames on a fresh volume."""
+    from paper_1805_03709_b300.volume import Volume
+    vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
+                 N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
+                 mc_cap_entries=MAX_BLOCKS * 64)
+    out = []
+    for i in range(args.warmup + args.steps):
+        f = i % N_FRAMES
+        if i == args.warmup:
+            vol.timing(("mc",))
+            vol.timing_read(reset=True)
+        s = vol.process_frame(D[f], poses[f], i + 1, ERASE_R)
+        if i >= args.warmup:
+            nb, ne = (int(x) for x in s.n.cpu().tolist())
+            rem = int((s.info[:nb].cpu().numpy().view(np.uint32) >> 31).sum())
+            out.append((nb - rem, rem, ne))
+    timing = vol.timing_read(reset=True)
+    vol.close()
+    return out, timing
 
 
 def serve_point(torch, cam, D, poses, peak, duration_s=4.0, n_clients=64, rate=20.0,

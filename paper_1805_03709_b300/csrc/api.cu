@@ -440,20 +440,20 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
 // Capture erase + allocation + fusion + MC set + MC extraction of one frame as a CUDA graph.
 // All per-frame inputs reach the kernels through the control block written by the root
 // (setup) node, so a frame is: update that node's argument, launch the graph.
-static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
+// `tmask`: stages (VBH_STAGE_INTEGRATE, VBH_STAGE_MC) bracketed by event-record nodes.
+static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
   if (h->frame_graph) cudaGraphDestroy(h->frame_graph);
   h->frame_exec = nullptr;
   h->frame_graph = nullptr;
-  h->ev_node[0] = h->ev_node[1] = nullptr;
+  for (auto& nd : h->ev_node) nd = nullptr;
   const Launch Lc{h->cap_stream, h->L.sms};
   const TableView t = h->table();
   const PoolView pool = h->pool();
-  cudaEvent_t ea = nullptr, eb = nullptr;
-  if (timed) {
-    ea = h->get_event();
-    eb = h->get_event();
-  }
+  const bool t_int = tmask & (1 << VBH_STAGE_INTEGRATE), t_mc = tmask & (1 << VBH_STAGE_MC);
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int i = 0; i < 4; ++i)
+    if ((i < 2 && t_int) || (i >= 2 && t_mc)) ev[i] = h->get_event();
   VBH_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
   // one thread per word of the control block: a single round trip to host memory
   k_setup_ring<<<1, 128, 0, h->cap_stream>>>(h->ring_dev, h->dev_seq, h->consumed_dev, h->ctl,
@@ -466,14 +466,16 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
   launch_hash_insert_finish(Lc, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
                             h->cand_cap, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
                             h->ctl);
-  if (timed) cudaEventRecordWithFlags(ea, h->cap_stream, cudaEventRecordExternal);
+  if (t_int) cudaEventRecordWithFlags(ev[0], h->cap_stream, cudaEventRecordExternal);
   // the fusion node takes the frame parameters by value: vbh_process_frame patches them
   launch_integrate(Lc, base_ctl(h, nullptr).fp, pool, h->touched, h->tkey, h->tdepth,
                    &h->cnt->n_touched, h->cnt);
-  if (timed) cudaEventRecordWithFlags(eb, h->cap_stream, cudaEventRecordExternal);
+  if (t_int) cudaEventRecordWithFlags(ev[1], h->cap_stream, cudaEventRecordExternal);
   launch_mset_touched(Lc, t, pool, h->cnt, h->ctl, h->touched, &h->cnt->n_touched, h->removed,
                       &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec);
+  if (t_mc) cudaEventRecordWithFlags(ev[2], h->cap_stream, cudaEventRecordExternal);
   launch_mc_extract(Lc, t, pool, h->cnt, h->ctl, h->mset, h->tombrec);
+  if (t_mc) cudaEventRecordWithFlags(ev[3], h->cap_stream, cudaEventRecordExternal);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   cudaError_t le = cudaGetLastError();
@@ -500,7 +502,7 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
     }
     if (!h->integ_node) return fail(VBH_ERR_CUDA, "frame graph: fusion node not found");
   }
-  if (timed) {
+  if (tmask) {
     size_t n = 0;
     VBH_CUDA(cudaGraphGetNodes(g, nullptr, &n));
     std::vector<cudaGraphNode_t> nodes(n);
@@ -509,15 +511,16 @@ static vbh_status build_frame_graph(vbh_handle* h, bool timed) {
       cudaGraphNodeType ty;
       VBH_CUDA(cudaGraphNodeGetType(node, &ty));
       if (ty != cudaGraphNodeTypeEventRecord) continue;
-      cudaEvent_t ev = nullptr;
-      VBH_CUDA(cudaGraphEventRecordNodeGetEvent(node, &ev));
-      if (ev == ea) h->ev_node[0] = node;
-      if (ev == eb) h->ev_node[1] = node;
+      cudaEvent_t e_n = nullptr;
+      VBH_CUDA(cudaGraphEventRecordNodeGetEvent(node, &e_n));
+      for (int i = 0; i < 4; ++i)
+        if (ev[i] && e_n == ev[i]) h->ev_node[i] = node;
     }
-    if (!h->ev_node[0] || !h->ev_node[1]) return fail(VBH_ERR_CUDA, "frame graph: event nodes");
+    for (int i = 0; i < 4; ++i)
+      if (ev[i] && !h->ev_node[i]) return fail(VBH_ERR_CUDA, "frame graph: event nodes");
   }
   VBH_CUDA(cudaGraphInstantiate(&h->frame_exec, g, 0));
-  h->graph_timed = timed;
+  h->graph_timed = tmask;
   h->graph_kernels = 8;
   return VBH_OK;
 }
@@ -535,9 +538,9 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
     return fail(VBH_ERR_INVALID_ARG, "invalid erase radius");
   vbh_status st = maybe_rebuild(h);
   if (st != VBH_OK) return st;
-  const bool timed = (h->timing & (1 << VBH_STAGE_INTEGRATE)) != 0;
-  if (!h->frame_exec || timed != h->graph_timed) {
-    st = build_frame_graph(h, timed);
+  const int tmask = h->timing & ((1 << VBH_STAGE_INTEGRATE) | (1 << VBH_STAGE_MC));
+  if (!h->frame_exec || tmask != h->graph_timed) {
+    st = build_frame_graph(h, tmask);
     if (st != VBH_OK) return st;
   }
   FrameCtl c = base_ctl(h, T_wc_host);
@@ -578,13 +581,16 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
     kp.extra = nullptr;
     VBH_CUDA(cudaGraphExecKernelNodeSetParams(h->frame_exec, h->integ_node, &kp));
   }
-  if (timed) {
-    cudaEvent_t a = h->get_event(), b = h->get_event();
-    VBH_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->frame_exec, h->ev_node[0], a));
-    VBH_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->frame_exec, h->ev_node[1], b));
-    h->pending.push_back(StageEvents{VBH_STAGE_INTEGRATE, a, b, 1});
-  } else {
-    h->stage_launches[VBH_STAGE_INTEGRATE] += 1;
+  for (int sidx = 0; sidx < 2; ++sidx) {   // fresh events for the timed stages of this frame
+    const int stage = sidx == 0 ? VBH_STAGE_INTEGRATE : VBH_STAGE_MC;
+    if (tmask & (1 << stage)) {
+      cudaEvent_t a = h->get_event(), b = h->get_event();
+      VBH_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->frame_exec, h->ev_node[2 * sidx], a));
+      VBH_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->frame_exec, h->ev_node[2 * sidx + 1], b));
+      h->pending.push_back(StageEvents{stage, a, b, 1});
+    } else {
+      h->stage_launches[stage] += 1;
+    }
   }
   VBH_CUDA(cudaGraphLaunch(h->frame_exec, h->stream));
   h->host_seq = seq + 1;

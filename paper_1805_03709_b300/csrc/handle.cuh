@@ -88,10 +88,10 @@ struct vbh_handle {
   unsigned long long* consumed_dev = nullptr;
   unsigned long long* dev_seq = nullptr;   // device memory
   unsigned long long host_seq = 0;
-  cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
+  cudaGraphNode_t ev_node[4] = {nullptr, nullptr, nullptr, nullptr};   // fusion, MC extraction
   cudaGraphNode_t integ_node = nullptr;   // fusion node: its by-value frame parameters are
   cudaKernelNodeParams integ_kp{};        // patched before every launch
-  bool graph_timed = false;
+  int graph_timed = 0;             // stage mask the captured graph brackets with events
   uint64_t graph_kernels = 0;
   // bookkeeping
   uint64_t launches = 0;
