@@ -74,6 +74,10 @@ def lib():
         L.orc_vol_dump.argtypes = [P, P, P, P, U32]
         L.orc_vol_dump.restype = U32
         L.orc_vol_load.argtypes = [P, P, P, P, U32]
+        L.orc_vol_host_dump.argtypes = [P, P, P, P, U32]
+        L.orc_vol_host_dump.restype = U32
+        L.orc_vol_stream_in.argtypes = [P, P, U32]
+        L.orc_vol_stream_in.restype = U32
         L.orc_vol_mc_set.argtypes = [P, I32, P, U32, P, U32, P]
         L.orc_vol_mc_set.restype = U32
         L.orc_vol_mc_dense.argtypes = [P, P, U32, P, P]
@@ -176,6 +180,19 @@ class OracleVolume:
         W = np.zeros((n, 512), np.float64)
         lib().orc_vol_dump(self._h, _p(k), _p(F), _p(W), n)
         return k, F, W
+
+    def host_dump(self):
+        """The passive host map of streamed-out (erased) blocks: keys sorted, F, W."""
+        n = lib().orc_vol_host_dump(self._h, None, None, None, 0)
+        k = np.zeros((n, 3), np.int32)
+        F = np.zeros((n, 512), np.float64)
+        W = np.zeros((n, 512), np.float64)
+        lib().orc_vol_host_dump(self._h, _p(k), _p(F), _p(W), n)
+        return k, F, W
+
+    def stream_in(self, keys3) -> int:
+        k = np.ascontiguousarray(keys3, np.int32).reshape(-1, 3)
+        return lib().orc_vol_stream_in(self._h, _p(k), k.shape[0])
 
     def load(self, keys3, F, W):
         k = np.ascontiguousarray(keys3, np.int32).reshape(-1, 3)

@@ -95,6 +95,9 @@ struct Volume {
   std::unordered_map<K3, Block, K3Hash> blocks;
   std::set<K3> touched;   // blocks allocated/updated by the last integrated frame (R4)
   std::set<K3> removed;   // blocks erased since the last touched-set extraction
+  // Passive host map of the blocks streamed out of the active model (Sec. 4.1, blocks that
+  // left the active region move to CPU memory): the block's values at its last erase.
+  std::unordered_map<K3, Block, K3Hash> host;
 };
 
 inline int floordiv8(int g) { return g >= 0 ? g / 8 : -((-g + 7) / 8); }
@@ -354,7 +357,11 @@ uint32_t orc_vol_erase_radius(void* h, const float* centre, float R, int32_t* ou
   for (auto& kv : v.blocks)
     if (erase_test(v, kv.first, centre, R)) gone.push_back(kv.first);
   std::sort(gone.begin(), gone.end());
-  for (const K3& k : gone) { v.blocks.erase(k); v.removed.insert(k); }
+  for (const K3& k : gone) {
+    v.host[k] = v.blocks[k];   // stream-out: the erased block's values go to the host map
+    v.blocks.erase(k);
+    v.removed.insert(k);
+  }
   if (out) fill_keys(gone, out, cap);
   return (uint32_t)gone.size();
 }
@@ -365,7 +372,44 @@ uint32_t orc_vol_erase_keys(void* h, const int32_t* keys3, uint32_t n) {
   uint32_t c = 0;
   for (uint32_t i = 0; i < n; ++i) {
     K3 k{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]};
-    if (v.blocks.erase(k)) { v.removed.insert(k); ++c; }
+    auto it = v.blocks.find(k);
+    if (it != v.blocks.end()) {
+      v.host[k] = it->second;   // stream-out
+      v.blocks.erase(it);
+      v.removed.insert(k);
+      ++c;
+    }
+  }
+  return c;
+}
+
+// The host map of streamed-out blocks, keys sorted (like orc_vol_dump).
+uint32_t orc_vol_host_dump(void* h, int32_t* keys3, double* F, double* W, uint32_t cap) {
+  Volume& v = *(Volume*)h;
+  std::vector<K3> ks;
+  for (auto& kv : v.host) ks.push_back(kv.first);
+  std::sort(ks.begin(), ks.end());
+  for (size_t i = 0; i < ks.size() && i < cap; ++i) {
+    keys3[3 * i] = ks[i].x; keys3[3 * i + 1] = ks[i].y; keys3[3 * i + 2] = ks[i].z;
+    const Block& b = v.host[ks[i]];
+    if (F) std::memcpy(F + 512 * i, b.F, sizeof b.F);
+    if (W) std::memcpy(W + 512 * i, b.W, sizeof b.W);
+  }
+  return (uint32_t)ks.size();
+}
+
+// Stream-in: every listed key that is in the host map and not live moves back into the model
+// with its stored values (a live block is newer and stays; its host copy stays too).
+uint32_t orc_vol_stream_in(void* h, const int32_t* keys3, uint32_t n) {
+  Volume& v = *(Volume*)h;
+  uint32_t c = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    K3 k{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]};
+    auto it = v.host.find(k);
+    if (it == v.host.end() || v.blocks.count(k)) continue;
+    v.blocks[k] = it->second;
+    v.host.erase(it);
+    ++c;
   }
   return c;
 }
