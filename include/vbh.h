@@ -94,7 +94,8 @@ typedef struct {
   uint32_t last_new;        /* of which newly allocated */
   uint32_t last_candidates; /* distinct block keys per image tile summed over tiles */
   uint32_t error_flags;     /* sticky: bit0 pool exhausted, bit1 table full, bit2 stream
-                               overflow, bit3 bounded wait timed out */
+                               overflow, bit3 bounded wait timed out, bit4 stream-out ring
+                               without room (blocks counted as lost) */
   uint64_t kernel_launches; /* kernels this handle has launched since creation */
   uint32_t rebuilds;        /* table rebuilds performed (tombstone clean-up) */
   uint32_t last_mc_blocks;  /* records produced by the last extraction */
@@ -306,6 +307,36 @@ vbh_status vbh_mc_from_tsdf_static(const int32_t* keys3_dev, const float* tsdf_d
                                    const float* weight_dev, uint32_t n_blocks,
                                    const vbh_mc_stream* out, void* cuda_stream,
                                    uint32_t* error_flags_dev);
+
+/* Stream-out of blocks that leave the active model (Sec. 4.1: blocks no longer in the
+ * sensor's view move to CPU memory) into a passive host map, and explicit stream-in.
+ * After vbh_stream_out_enable, every erase (vbh_erase_blocks, and the erase step of
+ * vbh_process_frame) copies the removed blocks' (TSDF, weight) and keys into a device transfer
+ * ring of ring_blocks slots (0 = max_blocks) before their pool entries can be reused; copies to
+ * pinned host memory run on a side stream and are folded into the host map -- key -> the
+ * block's values at its last erase -- by the polls that every frame / erase call makes.  A
+ * ring without room loses nothing silently: the blocks that did not fit are counted
+ * (vbh_stream_out_stats) and error flag 16 is raised; the poll waits for copies while the ring
+ * is more than half full.  Host memory: 4 KiB per slot pinned plus the map. */
+vbh_status vbh_stream_out_enable(vbh_handle* h, uint32_t ring_blocks);   /* synchronises */
+/* Non-blocking: start copies of filled slots, fold landed ones; *streamed_host (may be NULL)
+ * = blocks folded into the host map so far. */
+vbh_status vbh_stream_out_poll(vbh_handle* h, uint64_t* streamed_host);
+/* Synchronises: every block erased so far is in the host map. */
+vbh_status vbh_stream_out_flush(vbh_handle* h);
+/* Synchronises; any pointer may be NULL: blocks folded in so far, blocks lost for want of ring
+ * room, keys held by the host map. */
+vbh_status vbh_stream_out_stats(vbh_handle* h, uint64_t* streamed_host, uint64_t* lost_host,
+                                uint32_t* host_blocks_host);
+/* The host map (synchronises): first min(cap, size) keys with their 512 TSDF / weight values
+ * (tsdf_host, weight_host may be NULL), no particular order; *n_host = size. */
+vbh_status vbh_host_map_dump(vbh_handle* h, int32_t* keys3_host, float* tsdf_host,
+                             float* weight_host, uint32_t cap, uint32_t* n_host);
+/* Stream-in (synchronises): every listed key that is in the host map and not live moves back
+ * into the volume with its stored values (a live block is newer: it and its host copy stay);
+ * *n_loaded_host (may be NULL) = blocks moved. */
+vbh_status vbh_stream_in(vbh_handle* h, const int32_t* keys3_host, uint32_t n,
+                         uint32_t* n_loaded_host);
 
 /* Multi-client delta streaming: the server side of Sec. 4.2, where each client asks for the MC
  * blocks that changed since its last update (the paper keeps a hash set of changed block ids

@@ -156,6 +156,7 @@ FrameCtl base_ctl(const vbh_handle* h, const float* T) {
   c.fp = frame_params(h, T);
   c.version = h->frame_version;
   c.slog = h->slog;
+  c.so_tail = stream_out_tail(h);
   return c;
 }
 
@@ -328,6 +329,7 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
 vbh_status vbh_destroy(vbh_handle* h) {
   if (!h) return VBH_OK;
   if (h->server) vbh_serve_destroy(h->server);
+  stream_out_release(h);
   if (h->stream || h->slots) cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
   if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
@@ -459,7 +461,8 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   k_setup_ring<<<1, 128, 0, h->cap_stream>>>(h->ring_dev, h->dev_seq, h->consumed_dev, h->ctl,
                                              h->cnt);
   launch_erase_radius(Lc, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks, nullptr,
-                      nullptr);
+                      nullptr, stream_list(h));
+  if (h->so) launch_stream_gather(Lc, h->so_ring, h->ctl, pool, h->cnt, stream_list(h));
   launch_alloc_keys(Lc, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
   launch_hash_insert(Lc, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
@@ -521,7 +524,7 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   }
   VBH_CUDA(cudaGraphInstantiate(&h->frame_exec, g, 0));
   h->graph_timed = tmask;
-  h->graph_kernels = 8;
+  h->graph_kernels = h->so ? 9 : 8;
   return VBH_OK;
 }
 
@@ -538,6 +541,10 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
     return fail(VBH_ERR_INVALID_ARG, "invalid erase radius");
   vbh_status st = maybe_rebuild(h);
   if (st != VBH_OK) return st;
+  if (h->so) {   // move landed stream-out copies to the host map (waits if the ring is full)
+    st = stream_out_poll(h, false);
+    if (st != VBH_OK) return st;
+  }
   const int tmask = h->timing & ((1 << VBH_STAGE_INTEGRATE) | (1 << VBH_STAGE_MC));
   if (!h->frame_exec || tmask != h->graph_timed) {
     st = build_frame_graph(h, tmask);
@@ -617,6 +624,10 @@ vbh_status vbh_erase_blocks(vbh_handle* h, const vbh_erase_selector* sel,
   } else {
     return fail(VBH_ERR_INVALID_ARG, "unknown erase mode");
   }
+  if (h->so) {
+    vbh_status pst = stream_out_poll(h, false);
+    if (pst != VBH_OK) return pst;
+  }
   FrameCtl c = base_ctl(h, nullptr);
   c.reset = kResetErase;
   h->stage_begin(VBH_STAGE_ERASE);
@@ -626,13 +637,17 @@ vbh_status vbh_erase_blocks(vbh_handle* h, const vbh_erase_selector* sel,
     c.erase_r2 = sel->radius * sel->radius;   // binary32 product, one rounding
     launch_setup(h, c);
     launch_erase_radius(h->L, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks,
-                        erased_keys3_dev, n_erased_dev);
+                        erased_keys3_dev, n_erased_dev, stream_list(h));
     h->launches += 1;
   } else {
     launch_setup(h, c);
     launch_erase_keys(h->L, t, pool, h->cnt, sel->keys3_dev, sel->n_keys, h->removed,
-                      h->cfg.max_blocks, erased_keys3_dev, n_erased_dev);
+                      h->cfg.max_blocks, erased_keys3_dev, n_erased_dev, stream_list(h));
     h->launches += sel->n_keys ? 1 : 0;
+  }
+  if (h->so) {
+    launch_stream_gather(h->L, h->so_ring, h->ctl, pool, h->cnt, stream_list(h));
+    h->launches += 1;
   }
   h->stage_end();
   vbh_status st = check_launch(h, "vbh_erase_blocks");

@@ -19,7 +19,8 @@ __device__ __forceinline__ void finish_removal(bool erased, unsigned int p, unsi
                                                PoolView& pool, DevCounters* cnt,
                                                unsigned long long* removed,
                                                unsigned int removed_cap, int* out_keys3,
-                                               unsigned int* s_erased, unsigned int* s_err) {
+                                               const StreamList& so, unsigned int* s_erased,
+                                               unsigned int* s_err) {
   unsigned int k = warp_append(reinterpret_cast<unsigned int*>(&cnt->free_top), erased,
                                0xFFFFFFFFu);
   if (erased) {
@@ -36,6 +37,10 @@ __device__ __forceinline__ void finish_removal(bool erased, unsigned int p, unsi
   unsigned int o = warp_append(&cnt->n_erased, erased, 0xFFFFFFFFu);
   if (erased) {
     atomicAdd(s_erased, 1u);
+    if (so.p) {   // stream-out: the gather after this launch copies the block's voxels away
+      so.p[o] = p;
+      so.k[o] = key;
+    }
     if (out_keys3) {
       int3 kk = unpack_key(key);
       out_keys3[3u * o] = kk.x;
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView
                                                            DevCounters* cnt, const FrameCtl* ctl,
                                                            unsigned long long* removed,
                                                            unsigned int removed_cap,
-                                                           int* out_keys3) {
+                                                           int* out_keys3, StreamList so) {
   __shared__ unsigned int s_erased, s_err;
   if (threadIdx.x == 0) { s_erased = 0; s_err = 0; }
   __syncthreads();
@@ -75,7 +80,8 @@ __global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView
         if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;
       }
     }
-    finish_removal(erased, p, key, pool, cnt, removed, removed_cap, out_keys3, &s_erased, &s_err);
+    finish_removal(erased, p, key, pool, cnt, removed, removed_cap, out_keys3, so, &s_erased,
+                   &s_err);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -92,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_erase_keys(TableView t, PoolView p
                                                          unsigned int n,
                                                          unsigned long long* removed,
                                                          unsigned int removed_cap,
-                                                         int* out_keys3) {
+                                                         int* out_keys3, StreamList so) {
   __shared__ unsigned int s_erased, s_err;
   if (threadIdx.x == 0) { s_erased = 0; s_err = 0; }
   __syncthreads();
@@ -111,7 +117,8 @@ __global__ void __launch_bounds__(kThreads) k_erase_keys(TableView t, PoolView p
         if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;
       }
     }
-    finish_removal(erased, val, key, pool, cnt, removed, removed_cap, out_keys3, &s_erased, &s_err);
+    finish_removal(erased, val, key, pool, cnt, removed, removed_cap, out_keys3, so, &s_erased,
+                   &s_err);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -123,15 +130,72 @@ __global__ void __launch_bounds__(kThreads) k_erase_keys(TableView t, PoolView p
   }
 }
 
+// Stream-out gather: the voxels and keys of the blocks the preceding erase launch removed are
+// copied into the next slots of the device transfer ring (before an allocation can reuse the
+// pool entries).  The host copies filled slots to pinned memory and folds them into its map;
+// the control block carries how far it has consumed, so the ring is never overwritten: blocks
+// that do not fit are counted as lost and flagged, never dropped silently.  The last CTA to
+// finish publishes the new head to host memory.
+constexpr int kGatherThreads = 256;
+
+__global__ void __launch_bounds__(kGatherThreads) k_stream_gather(StreamRing* ring,
+                                                                  const FrameCtl* ctl,
+                                                                  PoolView pool,
+                                                                  DevCounters* cnt,
+                                                                  StreamList so) {
+  __shared__ unsigned long long s_head;
+  __shared__ unsigned int s_take, s_n;
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    const unsigned long long head = ring->head;
+    const unsigned long long used = head - ctl->so_tail;   // <= capacity
+    const unsigned long long room = ring->cap > used ? ring->cap - used : 0ull;
+    const unsigned int n = cnt->n_erased;
+    s_head = head;
+    s_n = n;
+    s_take = (unsigned int)(n < room ? n : room);
+  }
+  __syncthreads();
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int nwarps = gridDim.x * (kGatherThreads / 32);
+  for (unsigned int o = blockIdx.x * (kGatherThreads / 32) + (threadIdx.x >> 5); o < s_take;
+       o += nwarps) {
+    const unsigned long long slot = (s_head + o) % ring->cap;
+    const uint4* src = reinterpret_cast<const uint4*>(pool.vox + 512ull * so.p[o]);
+    uint4* dst = reinterpret_cast<uint4*>(ring->data + 512ull * slot);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[lane + 32 * i] = __ldcs(src + lane + 32 * i);
+    if (lane == 0) ring->keys[slot] = so.k[o];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ring->done, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    ring->done = 0u;
+    ring->head = s_head + s_take;
+    if (s_take < s_n) {
+      ring->lost += s_n - s_take;
+      atomicOr(&cnt->err, kErrStreamOut);
+    }
+    __threadfence_system();
+    *reinterpret_cast<volatile unsigned long long*>(ring->head_host) = s_head + s_take;
+  }
+}
+
 }  // namespace
 
 void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                          const FrameCtl* ctl, unsigned long long* removed,
-                         unsigned int removed_cap, int* out_keys3, unsigned int* out_n) {
+                         unsigned int removed_cap, int* out_keys3, unsigned int* out_n,
+                         StreamList so) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_erase_radius, kThreads, L.sms);
   k_erase_radius<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, ctl, removed, removed_cap,
-                                                  out_keys3);
+                                                  out_keys3, so);
   if (out_n)
     cudaMemcpyAsync(out_n, &cnt->n_erased, sizeof(unsigned int), cudaMemcpyDeviceToDevice,
                     L.stream);
@@ -139,15 +203,21 @@ void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounter
 
 void launch_erase_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const int* keys3, unsigned int n, unsigned long long* removed,
-                       unsigned int removed_cap, int* out_keys3, unsigned int* out_n) {
+                       unsigned int removed_cap, int* out_keys3, unsigned int* out_n,
+                       StreamList so) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_erase_keys, kThreads, L.sms);
   if (n)
     k_erase_keys<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, keys3, n, removed, removed_cap,
-                                                  out_keys3);
+                                                  out_keys3, so);
   if (out_n)
     cudaMemcpyAsync(out_n, &cnt->n_erased, sizeof(unsigned int), cudaMemcpyDeviceToDevice,
                     L.stream);
+}
+
+void launch_stream_gather(const Launch& L, StreamRing* ring, const FrameCtl* ctl, PoolView pool,
+                          DevCounters* cnt, StreamList so) {
+  k_stream_gather<<<L.sms, kGatherThreads, 0, L.stream>>>(ring, ctl, pool, cnt, so);
 }
 
 }  // namespace vbh

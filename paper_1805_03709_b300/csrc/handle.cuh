@@ -20,6 +20,8 @@ vbh_status fail(vbh_status st, const std::string& msg);
       return ::vbh::fail(VBH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+struct StreamOutHost;   // stream-out bookkeeping on the host (streamout.cu)
+
 struct StageEvents {
   int stage;
   cudaEvent_t a, b;
@@ -58,6 +60,13 @@ struct vbh_handle {
   // attached server (serve.cu): device-resident log/store state and its host object
   vbh::ServeLog* slog = nullptr;
   vbh_serve* server = nullptr;
+  // stream-out (streamout.cu): device transfer ring, erased-block list, host side
+  vbh::StreamRing* so_ring = nullptr;
+  float2* so_data_dev = nullptr;             // the ring's slots (cap x 512) and keys
+  unsigned long long* so_keys_dev = nullptr;
+  unsigned int* so_p = nullptr;
+  unsigned long long* so_k = nullptr;
+  vbh::StreamOutHost* so = nullptr;
   // per-frame lists
   int J = 0;
   unsigned long long* cand = nullptr;
@@ -145,7 +154,19 @@ struct vbh_handle {
 };
 
 namespace vbh {
+// Copies filled ring slots to host memory and folds landed copies into the host map; with
+// `wait`, first waits for the handle's stream and then for every copy.
+vbh_status stream_out_poll(vbh_handle* h, bool wait);
+unsigned long long stream_out_tail(const vbh_handle* h);
+void stream_out_release(vbh_handle* h);
+inline StreamList stream_list(const vbh_handle* h);
 // MC refresh of every live block into the attached server's store and log, with no stream
 // output (enqueued on the handle's stream).  counts_dev: two device words of scratch.
 vbh_status refresh_all_blocks(vbh_handle* h, unsigned int* counts_dev);
+}  // namespace vbh
+
+namespace vbh {
+inline StreamList stream_list(const vbh_handle* h) {
+  return h->so ? StreamList{h->so_p, h->so_k} : StreamList{nullptr, nullptr};
+}
 }  // namespace vbh

@@ -38,7 +38,8 @@ constexpr int kKeyOffset = 1 << 20;
 constexpr unsigned int kFresh = 1u;
 
 // sticky error flags (vbh_counters.error_flags)
-constexpr unsigned int kErrPool = 1u, kErrTable = 2u, kErrStream = 4u, kErrTimeout = 8u;
+constexpr unsigned int kErrPool = 1u, kErrTable = 2u, kErrStream = 4u, kErrTimeout = 8u,
+                       kErrStreamOut = 16u;
 
 // op codes and per-op statuses (same numbers as the C ABI)
 constexpr unsigned char kOpFind = 0, kOpInsert = 1, kOpErase = 2;
@@ -111,6 +112,23 @@ struct ServeLog {
   unsigned int err;                // kServeErr* bits
 };
 constexpr unsigned int kServeErrRemFull = 1u, kServeErrOverrun = 2u, kServeErrCap = 4u;
+
+// Stream-out (blocks leaving the active model move to host memory).  The erase kernels record
+// each erased block's pool index and key at its erase number; the gather kernel copies them into
+// the device transfer ring.
+struct StreamList {
+  unsigned int* p;           // nullptr: stream-out off
+  unsigned long long* k;
+};
+struct StreamRing {
+  float2* data;                        // cap x 512 (TSDF, weight)
+  unsigned long long* keys;            // cap packed keys
+  unsigned long long* head_host;       // mapped host word: slots ever filled
+  unsigned long long head;             // slots ever filled (device copy)
+  unsigned long long lost;             // blocks that found no room
+  unsigned long long cap;              // slots
+  unsigned int done;                   // CTAs of the running gather that finished
+};
 
 // Touched-list entry: pool index in bits 0-30, bit 31 set when the block is fresh (allocated by
 // this frame, voxel data not yet written).
@@ -292,6 +310,7 @@ struct FrameCtl {
   unsigned int* n_entries_dev;
   unsigned int cap_blocks, cap_entries;
   ServeLog* slog;               // attached server (nullptr: none)
+  unsigned long long so_tail;   // stream-out ring slots the host has consumed
   unsigned int serve_mark;      // this extraction refreshes the store and appends to the log
   unsigned int store_only;      // no MC stream output (populating the store)
 };
@@ -365,10 +384,14 @@ const void* integrate_kernel();
 // erase.cu
 void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                          const FrameCtl* ctl, unsigned long long* removed,
-                         unsigned int removed_cap, int* out_keys3, unsigned int* out_n);
+                         unsigned int removed_cap, int* out_keys3, unsigned int* out_n,
+                         StreamList so);
 void launch_erase_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const int* keys3, unsigned int n, unsigned long long* removed,
-                       unsigned int removed_cap, int* out_keys3, unsigned int* out_n);
+                       unsigned int removed_cap, int* out_keys3, unsigned int* out_n,
+                       StreamList so);
+void launch_stream_gather(const Launch& L, StreamRing* ring, const FrameCtl* ctl, PoolView pool,
+                          DevCounters* cnt, StreamList so);
 
 // mc.cu
 void launch_mset_touched(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,

@@ -142,6 +142,13 @@ class vbh_serve_script(ctypes.Structure):
 
 
 SYMBOLS += [
+    ("vbh_stream_out_enable", ctypes.c_int, [_p, _u32]),
+    ("vbh_stream_out_poll", ctypes.c_int, [_p, ctypes.POINTER(_u64)]),
+    ("vbh_stream_out_flush", ctypes.c_int, [_p]),
+    ("vbh_stream_out_stats", ctypes.c_int, [_p, ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                                            ctypes.POINTER(_u32)]),
+    ("vbh_host_map_dump", ctypes.c_int, [_p, _p, _p, _p, _u32, ctypes.POINTER(_u32)]),
+    ("vbh_stream_in", ctypes.c_int, [_p, _p, _u32, ctypes.POINTER(_u32)]),
     ("vbh_serve_create", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_config), ctypes.POINTER(_p)]),
     ("vbh_serve_destroy", ctypes.c_int, [_p]),
     ("vbh_serve_set_policy", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_config)]),
@@ -416,3 +423,39 @@ def vbh_serve_run(s, script: vbh_serve_script, cap: int) -> list:
 
 def vbh_serve_now_ns() -> int:
     return int(lib().vbh_serve_now_ns())
+
+
+# ---------------------------------------------------------------------------- stream-out / in
+def vbh_stream_out_enable(h, ring_blocks: int = 0):
+    _check(lib().vbh_stream_out_enable(h, ring_blocks), "vbh_stream_out_enable")
+
+
+def vbh_stream_out_poll(h) -> int:
+    n = _u64()
+    _check(lib().vbh_stream_out_poll(h, ctypes.byref(n)), "vbh_stream_out_poll")
+    return n.value
+
+
+def vbh_stream_out_flush(h):
+    _check(lib().vbh_stream_out_flush(h), "vbh_stream_out_flush")
+
+
+def vbh_stream_out_stats(h):
+    s, l, m = _u64(), _u64(), _u32()
+    _check(lib().vbh_stream_out_stats(h, ctypes.byref(s), ctypes.byref(l), ctypes.byref(m)),
+           "vbh_stream_out_stats")
+    return s.value, l.value, m.value
+
+
+def vbh_host_map_dump(h, keys3, tsdf, weight, cap: int) -> int:
+    n = _u32()
+    _check(lib().vbh_host_map_dump(h, _ptr(keys3), _ptr(tsdf), _ptr(weight), cap,
+                                   ctypes.byref(n)), "vbh_host_map_dump")
+    return n.value
+
+
+def vbh_stream_in(h, keys3) -> int:
+    k = np.ascontiguousarray(keys3, dtype=np.int32).reshape(-1, 3)
+    n = _u32()
+    _check(lib().vbh_stream_in(h, _ptr(k), k.shape[0], ctypes.byref(n)), "vbh_stream_in")
+    return n.value

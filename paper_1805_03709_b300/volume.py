@@ -197,6 +197,33 @@ class Volume:
         V.vbh_load(self.h, np.ascontiguousarray(keys3, np.int32),
                    np.ascontiguousarray(tsdf, np.float32), np.ascontiguousarray(weight, np.float32))
 
+    # ---- stream-out of erased blocks to the host map, explicit stream-in
+    def stream_out_enable(self, ring_blocks: int = 0):
+        V.vbh_stream_out_enable(self.h, ring_blocks)
+
+    def stream_out_poll(self) -> int:
+        return V.vbh_stream_out_poll(self.h)
+
+    def stream_out_flush(self):
+        V.vbh_stream_out_flush(self.h)
+
+    def stream_out_stats(self):
+        """(blocks streamed out so far, blocks lost for want of ring room, host map size)."""
+        return V.vbh_stream_out_stats(self.h)
+
+    def host_map(self):
+        """The host map of streamed-out blocks: keys sorted, TSDF, weights."""
+        n = V.vbh_stream_out_stats(self.h)[2]
+        k = np.zeros((max(n, 1), 3), np.int32)
+        F = np.zeros((max(n, 1), 512), np.float32)
+        W = np.zeros((max(n, 1), 512), np.float32)
+        m = V.vbh_host_map_dump(self.h, k, F, W, n)
+        order = np.lexsort((k[:m, 2], k[:m, 1], k[:m, 0]))
+        return k[:m][order], F[:m][order], W[:m][order]
+
+    def stream_in(self, keys3) -> int:
+        return V.vbh_stream_in(self.h, keys3)
+
     def timing(self, stages=("erase", "alloc", "integrate", "mcset", "mc", "hash")):
         """Record CUDA events around the named stages (empty / None: off)."""
         mask = 0
