@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-stream", action="store_true",
+                    help="skip the stream-out measurement (room frames with erased blocks "
+                         "copied to the host map)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the multi-client serving measurement (batched vs unbatched)")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -431,6 +434,9 @@ def main():
     diff_pt = None
     if not args.no_diff:
         diff_pt = diff_point(torch, dev, flush)
+    stream_pt = None
+    if not args.no_stream:
+        stream_pt = stream_point(torch, cam, D, poses, flush, args, ms_total / args.steps)
     serve_pt = None
     if not args.no_serve and rank == 0:
         serve_pt = serve_point(torch, cam, D, poses, peak, args.serve_seconds)
@@ -454,7 +460,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
-            "hash": hash_pt, "diff": diff_pt, "serve": serve_pt,
+            "hash": hash_pt, "diff": diff_pt, "serve": serve_pt, "stream_out": stream_pt,
         }
         print(json.dumps(line), flush=True)
     vol.close()
@@ -529,6 +535,47 @@ def hash_point(torch, dev, flush, peak):
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+def stream_point(torch, cam, D, poses, flush, args, base_ms):
+    """The timed room frames again on a fresh volume with stream-out on: every block the 4 m
+    erase removes is copied (device ring -> pinned host -> host map) while the frames run.
+    Same per-step CUDA events and L2 flush as the main loop; the copies still in flight when the
+    loop ends are waited for and timed separately."""
+    from paper_1805_03709_b300.volume import Volume
+    vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
+                 N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
+                 mc_cap_entries=MAX_BLOCKS * 64)
+    vol.stream_out_enable()
+    for i in range(args.warmup):
+        vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+    vol.stream_out_flush()
+    s0 = vol.stream_out_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        i = args.warmup + k
+        flush.zero_()
+        ev[k][0].record()
+        vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    vol.stream_out_flush()
+    t2 = time.perf_counter()
+    s1 = vol.stream_out_stats()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    blocks = s1[0] - s0[0]
+    vol.close()
+    return {"frames_per_s": 1e3 / ms, "ms_per_step": ms,
+            "overhead_vs_main_loop": ms / base_ms - 1.0,
+            "blocks_streamed_per_frame": blocks / args.steps,
+            "bytes_streamed_per_frame": blocks * 4104 / args.steps,
+            "lost": int(s1[1]), "host_map_blocks": int(s1[2]),
+            "drain_after_loop_ms": (t2 - t1) * 1e3,
+            "copy_GBs_over_loop_and_drain": blocks * 4104 / (t2 - t0) / 1e9}
 
 
 def mc_replay(torch, cam, D, poses, args):

@@ -10,10 +10,14 @@
 // once a copy has landed folds its blocks into the host map (the block's values at its last
 // erase) and advances the tail that the next control block tells the gather.  A ring that
 // would overflow loses nothing silently: the gather counts what found no room and raises a
-// sticky flag; the poll keeps the ring at most half full by waiting for copies first.
+// sticky flag; the poll waits for copies once the ring is three quarters full.
 #include <algorithm>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -21,13 +25,152 @@
 
 namespace vbh {
 
+// Flat open-addressing map from packed block keys to a location (linear probing, power-of-two
+// capacity kept at most half full; erase by backward shift).  A location is a ring sequence
+// number (the block's latest copy still sits in the pinned ring) or, with kInStore set, a slot
+// of the long-term store.
+class KeyIndex {
+ public:
+  static constexpr unsigned long long kFree = ~0ull;
+  KeyIndex() { rehash(1u << 16); }
+  unsigned long long* find(unsigned long long key) {
+    for (size_t i = slot(key);; i = (i + 1) & mask_) {
+      if (keys_[i] == key) return &vals_[i];
+      if (keys_[i] == kFree) return nullptr;
+    }
+  }
+  // inserts or overwrites; returns the previous value or kFree
+  unsigned long long put(unsigned long long key, unsigned long long val) {
+    if ((size_ + 1) * 2 > keys_.size()) rehash(keys_.size() * 2);
+    for (size_t i = slot(key);; i = (i + 1) & mask_) {
+      if (keys_[i] == key) {
+        const unsigned long long old = vals_[i];
+        vals_[i] = val;
+        return old;
+      }
+      if (keys_[i] == kFree) {
+        keys_[i] = key;
+        vals_[i] = val;
+        ++size_;
+        return kFree;
+      }
+    }
+  }
+  void erase(unsigned long long key) {
+    size_t i = slot(key);
+    for (;; i = (i + 1) & mask_) {
+      if (keys_[i] == kFree) return;
+      if (keys_[i] == key) break;
+    }
+    for (size_t j = (i + 1) & mask_; keys_[j] != kFree; j = (j + 1) & mask_) {
+      const size_t home = slot(keys_[j]);
+      // move j back to the hole i unless its home lies cyclically in (i, j]
+      if (((j - home) & mask_) >= ((j - i) & mask_)) {
+        keys_[i] = keys_[j];
+        vals_[i] = vals_[j];
+        i = j;
+      }
+    }
+    keys_[i] = kFree;
+    --size_;
+  }
+  size_t size() const { return size_; }
+  template <class F>
+  void each(F f) const {
+    for (size_t i = 0; i < keys_.size(); ++i)
+      if (keys_[i] != kFree) f(keys_[i], vals_[i]);
+  }
+
+ private:
+  size_t slot(unsigned long long key) const { return hash_mix(key) & mask_; }
+  void rehash(size_t cap) {
+    std::vector<unsigned long long> k(cap, kFree), v(cap);
+    keys_.swap(k);
+    vals_.swap(v);
+    mask_ = cap - 1;
+    size_ = 0;
+    for (size_t i = 0; i < k.size(); ++i)
+      if (k[i] != kFree) put(k[i], v[i]);
+  }
+  std::vector<unsigned long long> keys_, vals_;
+  size_t mask_ = 0, size_ = 0;
+};
+
+constexpr unsigned long long kInStore = 1ull << 63;
+
+// A few persistent host threads for the eviction copies (one thread copies ~14 GB/s).
+class CopyPool {
+ public:
+  explicit CopyPool(unsigned int n) {
+    for (unsigned int i = 0; i < n; ++i) threads_.emplace_back([this, i] { run(i); });
+  }
+  ~CopyPool() {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      stop_ = true;
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+  }
+  // copies jobs[i].second -> jobs[i].first (4 KiB each) on the pool, returns when done
+  void copy(const std::vector<std::pair<float2*, const float2*>>& jobs) {
+    if (jobs.size() < 64 || threads_.empty()) {
+      for (const auto& j : jobs) std::memcpy(j.first, j.second, 512 * sizeof(float2));
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> g(m_);
+      jobs_ = &jobs;
+      pending_ = (unsigned int)threads_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    std::unique_lock<std::mutex> l(m_);
+    done_.wait(l, [this] { return pending_ == 0; });
+    jobs_ = nullptr;
+  }
+
+ private:
+  void run(unsigned int me) {
+    unsigned long long seen = 0;
+    for (;;) {
+      const std::vector<std::pair<float2*, const float2*>>* jobs;
+      {
+        std::unique_lock<std::mutex> l(m_);
+        cv_.wait(l, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (stop_) return;
+        jobs = jobs_;
+      }
+      const size_t n = jobs->size(), k = threads_.size();
+      for (size_t i = me * n / k; i < (me + 1) * n / k; ++i)
+        std::memcpy((*jobs)[i].first, (*jobs)[i].second, 512 * sizeof(float2));
+      {
+        std::lock_guard<std::mutex> g(m_);
+        if (--pending_ == 0) done_.notify_one();
+      }
+    }
+  }
+  std::vector<std::thread> threads_;
+  std::mutex m_;
+  std::condition_variable cv_, done_;
+  const std::vector<std::pair<float2*, const float2*>>* jobs_ = nullptr;
+  unsigned long long gen_ = 0;
+  unsigned int pending_ = 0;
+  bool stop_ = false;
+};
+
+constexpr unsigned int kChunkBlocks = 4096;   // long-term store chunk: 16 MiB
+
 struct StreamOutHost {
   unsigned long long cap = 0;
   float2* h_data = nullptr;                 // pinned host ring, cap x 512
   unsigned long long* h_keys = nullptr;     // pinned host ring, cap
   unsigned long long* head_mapped = nullptr;   // mapped: slots the device has filled
   unsigned long long issued = 0;            // slots whose copy has been started
-  unsigned long long tail = 0;              // slots folded into the map (free again)
+  unsigned long long landed = 0;            // slots whose copy has landed (indexed)
+  unsigned long long tail = 0;              // slots released to the device again
   cudaStream_t side = nullptr;
   struct Copy {
     cudaEvent_t ev;
@@ -35,10 +178,32 @@ struct StreamOutHost {
   };
   std::deque<Copy> copies;
   std::vector<cudaEvent_t> ev_free;
-  std::unordered_map<unsigned long long, unsigned int> index;   // key -> store slot
-  std::vector<float2> store;                                    // slots x 512
+  KeyIndex index;                           // key -> ring sequence number or store slot
+  std::vector<std::unique_ptr<float2[]>> chunks;   // long-term store: blocks never move
+  unsigned int n_slots = 0;
   std::vector<unsigned int> free_slots;
   unsigned long long streamed = 0;          // blocks folded in so far
+  CopyPool pool{8};
+  std::vector<std::pair<float2*, const float2*>> jobs;
+  float2* slot_ptr(unsigned int at) {
+    return chunks[at / kChunkBlocks].get() + 512ull * (at % kChunkBlocks);
+  }
+  const float2* data_of(unsigned long long loc) const {
+    if (loc & kInStore) {
+      const unsigned int at = (unsigned int)(loc & ~kInStore);
+      return chunks[at / kChunkBlocks].get() + 512ull * (at % kChunkBlocks);
+    }
+    return h_data + 512ull * (loc % cap);
+  }
+  unsigned int new_slot() {
+    if (!free_slots.empty()) {
+      const unsigned int at = free_slots.back();
+      free_slots.pop_back();
+      return at;
+    }
+    if (n_slots % kChunkBlocks == 0) chunks.emplace_back(new float2[512ull * kChunkBlocks]);
+    return n_slots++;
+  }
 };
 
 namespace {
@@ -47,26 +212,32 @@ unsigned long long published_head(const StreamOutHost* so) {
   return *reinterpret_cast<volatile unsigned long long*>(so->head_mapped);
 }
 
+// Landed copies only update the index: a block's data stays in its ring slot until the slot is
+// needed again (a block erased again meanwhile -- the common case at the edge of the active
+// region -- never costs a host copy).
 void fold(StreamOutHost* so, unsigned long long b, unsigned long long e) {
   for (unsigned long long i = b; i < e; ++i) {
-    const unsigned long long slot = i % so->cap;
-    const unsigned long long key = so->h_keys[slot];
-    unsigned int at;
-    auto it = so->index.find(key);
-    if (it != so->index.end()) {
-      at = it->second;
-    } else if (!so->free_slots.empty()) {
-      at = so->free_slots.back();
-      so->free_slots.pop_back();
-      so->index.emplace(key, at);
-    } else {
-      at = (unsigned int)(so->store.size() / 512);
-      so->store.resize(so->store.size() + 512);
-      so->index.emplace(key, at);
-    }
-    std::memcpy(so->store.data() + 512ull * at, so->h_data + 512ull * slot, 512 * sizeof(float2));
+    const unsigned long long old = so->index.put(so->h_keys[i % so->cap], i);
+    if (old != KeyIndex::kFree && (old & kInStore)) so->free_slots.push_back((unsigned int)(old & ~kInStore));
   }
   so->streamed += e - b;
+  so->landed = e;
+}
+
+// Release ring slots [tail, upto): blocks whose latest copy is still there move to the store
+// (the copies run on the pool).
+void evict(StreamOutHost* so, unsigned long long upto) {
+  so->jobs.clear();
+  for (unsigned long long i = so->tail; i < upto; ++i) {
+    const unsigned long long key = so->h_keys[i % so->cap];
+    unsigned long long* loc = so->index.find(key);
+    if (!loc || *loc != i) continue;   // superseded or streamed back in
+    const unsigned int at = so->new_slot();
+    so->jobs.emplace_back(so->slot_ptr(at), so->h_data + 512ull * (i % so->cap));
+    *loc = kInStore | at;
+  }
+  so->pool.copy(so->jobs);
+  so->tail = upto;
 }
 
 // Start copies of [b, e) (split at the ring's end) on the side stream.
@@ -107,10 +278,11 @@ vbh_status stream_out_poll(vbh_handle* h, bool wait) {
       so->copies.push_back(StreamOutHost::Copy{ev, so->issued, head});
       so->issued = head;
     }
-    // fold landed copies; keep the ring at most half full (a frame may erase many blocks)
+    // index landed copies; the newest half of the ring stays indexed in place, older slots are
+    // released (their current blocks move to the store); past three quarters, wait for copies
     while (!so->copies.empty()) {
       StreamOutHost::Copy& c = so->copies.front();
-      const bool must = wait || (published_head(so) - so->tail) * 2 > so->cap;
+      const bool must = wait || (published_head(so) - so->tail) * 4 > so->cap * 3;
       if (must) {
         VBH_CUDA(cudaEventSynchronize(c.ev));
       } else {
@@ -119,10 +291,11 @@ vbh_status stream_out_poll(vbh_handle* h, bool wait) {
         if (q != cudaSuccess) return fail(VBH_ERR_CUDA, cudaGetErrorString(q));
       }
       fold(so, c.b, c.e);
-      so->tail = c.e;
       so->ev_free.push_back(c.ev);
       so->copies.pop_front();
     }
+    const unsigned long long keep = so->cap / 2;   // recent slots stay in the ring
+    if (so->landed - so->tail > keep) evict(so, so->landed - keep);
     if (!wait) break;
   }
   return VBH_OK;
@@ -245,19 +418,19 @@ vbh_status vbh_host_map_dump(vbh_handle* h, int32_t* keys3, float* tsdf, float* 
   if (st != VBH_OK) return st;
   const StreamOutHost* so = h->so;
   uint32_t i = 0;
-  for (const auto& kv : so->index) {
-    if (i >= cap) break;
-    const int3 k = unpack_key(kv.first);
+  so->index.each([&](unsigned long long key, unsigned long long loc) {
+    if (i >= cap) return;
+    const int3 k = unpack_key(key);
     keys3[3 * i] = k.x;
     keys3[3 * i + 1] = k.y;
     keys3[3 * i + 2] = k.z;
-    const float2* b = so->store.data() + 512ull * kv.second;
+    const float2* b = so->data_of(loc);
     for (int v = 0; v < 512; ++v) {
       if (tsdf) tsdf[512ull * i + v] = b[v].x;
       if (weight) weight[512ull * i + v] = b[v].y;
     }
     ++i;
-  }
+  });
   *n_host = (uint32_t)so->index.size();
   return VBH_OK;
 }
@@ -273,16 +446,16 @@ vbh_status vbh_stream_in(vbh_handle* h, const int32_t* keys3_host, uint32_t n,
   StreamOutHost* so = h->so;
   // candidates: listed keys that are in the host map (in range, each once)
   std::vector<int32_t> cand;
-  std::vector<unsigned int> at;
+  std::vector<unsigned long long> at;
   std::unordered_map<unsigned long long, int> seen;
   for (uint32_t i = 0; i < n; ++i) {
     const int x = keys3_host[3 * i], y = keys3_host[3 * i + 1], z = keys3_host[3 * i + 2];
     if (!key_ok(x, y, z)) continue;
     const unsigned long long key = pack_key(x, y, z);
-    auto it = so->index.find(key);
-    if (it == so->index.end() || !seen.emplace(key, 1).second) continue;
+    const unsigned long long* loc = so->index.find(key);
+    if (!loc || !seen.emplace(key, 1).second) continue;
     cand.insert(cand.end(), {x, y, z});
-    at.push_back(it->second);
+    at.push_back(*loc);
   }
   const uint32_t m = (uint32_t)at.size();
   if (!m) return VBH_OK;
@@ -314,7 +487,7 @@ vbh_status vbh_stream_in(vbh_handle* h, const int32_t* keys3_host, uint32_t n,
   for (uint32_t i = 0; i < m; ++i) {
     if (hst[i] != VBH_ST_NOT_FOUND) continue;
     keys.insert(keys.end(), {cand[3 * i], cand[3 * i + 1], cand[3 * i + 2]});
-    const float2* b = so->store.data() + 512ull * at[i];
+    const float2* b = so->data_of(at[i]);
     for (int v = 0; v < 512; ++v) {
       F.push_back(b[v].x);
       W.push_back(b[v].y);
@@ -326,9 +499,9 @@ vbh_status vbh_stream_in(vbh_handle* h, const int32_t* keys3_host, uint32_t n,
     st = vbh_load(h, keys.data(), F.data(), W.data(), k);
     if (st != VBH_OK) return st;
     for (unsigned long long key : moved) {
-      auto it = so->index.find(key);
-      so->free_slots.push_back(it->second);
-      so->index.erase(it);
+      const unsigned long long loc = *so->index.find(key);
+      if (loc & kInStore) so->free_slots.push_back((unsigned int)(loc & ~kInStore));
+      so->index.erase(key);
     }
   }
   if (n_loaded_host) *n_loaded_host = k;
