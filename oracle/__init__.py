@@ -65,6 +65,11 @@ def lib():
         L.orc_alloc_keys.restype = U32
         L.orc_vol_integrate.argtypes = [P, P, P]
         L.orc_vol_integrate.restype = U32
+        L.orc_vol_integrate_mode.argtypes = [P, P, P, ctypes.c_int]
+        L.orc_vol_integrate_mode.restype = U32
+        L.orc_in_view.argtypes = [P, P, U32, P, ctypes.c_float, P]
+        L.orc_vol_erase_frustum.argtypes = [P, P, ctypes.c_float, P, U32]
+        L.orc_vol_erase_frustum.restype = U32
         L.orc_vol_touched.argtypes = [P, P, U32]
         L.orc_vol_touched.restype = U32
         L.orc_vol_erase_radius.argtypes = [P, P, F, P, U32]
@@ -152,9 +157,26 @@ class OracleVolume:
         lib().orc_alloc_keys(self._h, _p(depth), _p(T), _p(out), n)
         return out
 
-    def integrate(self, depth, T) -> int:
+    def integrate(self, depth, T, visible: bool = False) -> int:
+        """R4/R5 fusion of the touched set; with `visible`, R8 (touched + every block in view)."""
         depth, T = self._frame(depth, T)
-        return lib().orc_vol_integrate(self._h, _p(depth), _p(T))
+        return lib().orc_vol_integrate_mode(self._h, _p(depth), _p(T), 1 if visible else 0)
+
+    def in_view(self, keys3, T, zfar: float = 0.0):
+        """R7 flags of the given block keys for pose T (3x4)."""
+        k = np.ascontiguousarray(keys3, np.int32).reshape(-1, 3)
+        T = np.ascontiguousarray(T, np.float32).reshape(12)
+        out = np.zeros(k.shape[0], np.uint8)
+        lib().orc_in_view(self._h, _p(k), k.shape[0], _p(T), float(zfar), _p(out))
+        return out.astype(bool)
+
+    def erase_frustum(self, T, zfar: float = 0.0):
+        """R9: erase every live block in view of T; returns the erased keys (sorted)."""
+        T = np.ascontiguousarray(T, np.float32).reshape(12)
+        cap = len(self)
+        out = np.zeros((max(cap, 1), 3), np.int32)
+        n = lib().orc_vol_erase_frustum(self._h, _p(T), float(zfar), _p(out), cap)
+        return out[:n]
 
     def touched(self):
         n = lib().orc_vol_touched(self._h, None, 0)

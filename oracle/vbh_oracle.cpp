@@ -35,6 +35,17 @@
 //      the canonical sdf32 < -mu; running average with weight 1 per observation, capped at Wmax:
 //      F <- (w F + f) / (w + 1), W <- min(w + 1, Wmax) with w = W.
 //   R6 a block is erased when its centre (8k + 3.5) s is farther than R from a given point.
+//   R7 a block is in view of pose T when its bounding sphere (centre c = (8k + 3.5) s, radius
+//      rho = fl(7 s)) is not outside the camera frustum, tested on camera coordinates of the
+//      centre p (the voxel projection chain of R5 applied to c) against the four side planes
+//      fx p_x + cxh p_z >= 0, (W - cxh) p_z - fx p_x >= 0 (and likewise in y) with the margin
+//      rho G, G = fl(max(fx, fy) + max(cxh, W - cxh, cyh, H - cyh)) >= every plane normal's
+//      norm (so the test keeps every block that has a voxel in view), and p_z >= -rho, plus
+//      p_z <= zfar + rho when a far limit zfar > 0 is given.
+//   R8 (visible integration) the integration set of a frame is the touched set of R4 together
+//      with every live block in view (R7, far limit zmax): blocks that are not reached by the
+//      frame's truncation band are still updated where their voxels see free space (f = 1).
+//   R9 (scene reset, Sec. 4.1) a frustum erase removes every live block in view (R7).
 //   R-mc corner i of the cube at voxel g is g + c_i with the classic numbering
 //      c = (000,100,110,010,001,101,111,011) (x fastest); bit i is set iff F(corner) < 0; a cube
 //      with any corner in a missing block or with W == 0 is invalid and gets index 0.
@@ -206,6 +217,32 @@ bool erase_test(const Volume& v, const K3& k, const float* c, float R) {
   return d2 > R * R;
 }
 
+// R7: the bounding sphere of block k against the frustum of pose T (binary32 decisions).
+bool in_view(const Volume& v, const K3& k, const float* T, float zfar) {
+  const int kk[3] = {k.x, k.y, k.z};
+  float dX[3];
+  for (int i = 0; i < 3; ++i) {
+    const float c = ((float)(8 * kk[i]) + 3.5f) * v.s;
+    dX[i] = c - T[4 * i + 3];
+  }
+  float p[3];
+  for (int j = 0; j < 3; ++j) {
+    float acc = T[0 * 4 + j] * dX[0];
+    acc = std::fma(T[1 * 4 + j], dX[1], acc);
+    p[j] = std::fma(T[2 * 4 + j], dX[2], acc);
+  }
+  const float rho = 7.0f * v.s;
+  const float cxh = v.cx + 0.5f, cyh = v.cy + 0.5f;
+  const float rx = (float)v.width - cxh, ry = (float)v.height - cyh;
+  const float G = std::max(v.fx, v.fy) + std::max(std::max(cxh, rx), std::max(cyh, ry));
+  const float m = -(rho * G);
+  const float a = v.fx * p[0], b = v.fy * p[1];
+  if (!(p[2] >= -rho)) return false;
+  if (zfar > 0.0f && !(p[2] <= zfar + rho)) return false;
+  return std::fma(cxh, p[2], a) >= m && std::fma(rx, p[2], -a) >= m &&
+         std::fma(cyh, p[2], b) >= m && std::fma(ry, p[2], -b) >= m;
+}
+
 // R-mc corner offsets, classic numbering.
 const int kCorner[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
                            {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
@@ -325,8 +362,9 @@ uint32_t orc_alloc_keys(void* h, const uint16_t* depth, const float* T, int32_t*
 }
 
 // One frame: allocation (R3, new blocks start at F = 0, W = 0) then fusion of the touched set
-// (R4, R5).  Returns the number of touched blocks.
-uint32_t orc_vol_integrate(void* h, const uint16_t* depth, const float* T) {
+// (R4, R5), or with `visible` of the touched set and every live block in view (R8).  Returns
+// the number of blocks fused.
+uint32_t orc_vol_integrate_mode(void* h, const uint16_t* depth, const float* T, int visible) {
   Volume& v = *(Volume*)h;
   std::set<K3> s;
   allocate_blocks(v, depth, T, s);
@@ -338,9 +376,40 @@ uint32_t orc_vol_integrate(void* h, const uint16_t* depth, const float* T) {
       std::fill(b.W, b.W + 512, 0.0);
     }
   }
+  if (visible)
+    for (auto& kv : v.blocks)
+      if (in_view(v, kv.first, T, v.zmax)) s.insert(kv.first);
   for (const K3& k : s) integrate_block(v, k, v.blocks[k], depth, T);
   v.touched = s;
   return (uint32_t)s.size();
+}
+
+uint32_t orc_vol_integrate(void* h, const uint16_t* depth, const float* T) {
+  return orc_vol_integrate_mode(h, depth, T, 0);
+}
+
+// R7 for a list of keys (flags out[i] = 1 when in view).
+void orc_in_view(void* h, const int32_t* keys3, uint32_t n, const float* T, float zfar,
+                 uint8_t* out) {
+  const Volume& v = *(const Volume*)h;
+  for (uint32_t i = 0; i < n; ++i)
+    out[i] = in_view(v, K3{keys3[3 * i], keys3[3 * i + 1], keys3[3 * i + 2]}, T, zfar) ? 1 : 0;
+}
+
+// R9: erase every live block in view of T (far limit zfar > 0, or none); erased keys sorted.
+uint32_t orc_vol_erase_frustum(void* h, const float* T, float zfar, int32_t* out, uint32_t cap) {
+  Volume& v = *(Volume*)h;
+  std::vector<K3> gone;
+  for (auto& kv : v.blocks)
+    if (in_view(v, kv.first, T, zfar)) gone.push_back(kv.first);
+  std::sort(gone.begin(), gone.end());
+  for (const K3& k : gone) {
+    v.host[k] = v.blocks[k];
+    v.blocks.erase(k);
+    v.removed.insert(k);
+  }
+  if (out) fill_keys(gone, out, cap);
+  return (uint32_t)gone.size();
 }
 
 uint32_t orc_vol_touched(void* h, int32_t* out, uint32_t cap) {
