@@ -153,13 +153,19 @@ vbh_status vbh_hash_rebuild(vbh_handle* h);
 vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const float* T_wc_host,
                                uint32_t frame_id, vbh_frame_stats* stats_host);
 
-enum { VBH_ERASE_RADIUS = 0, VBH_ERASE_KEYS = 1 };
+enum { VBH_ERASE_RADIUS = 0, VBH_ERASE_KEYS = 1, VBH_ERASE_FRUSTUM = 2 };
 typedef struct {
-  uint32_t mode;           /* VBH_ERASE_RADIUS or VBH_ERASE_KEYS */
+  uint32_t mode;           /* VBH_ERASE_RADIUS, VBH_ERASE_KEYS or VBH_ERASE_FRUSTUM */
   float centre[3];         /* RADIUS: erase blocks whose centre (8k + 3.5) s is farther ... */
   float radius;            /* ... than `radius` metres from `centre` */
   const int32_t* keys3_dev;/* KEYS: n_keys block coordinates (absent keys are ignored) */
   uint32_t n_keys;
+  float T_wc[12];          /* FRUSTUM (the scene reset of Sec. 4.1): erase every block in view
+                              of this pose with the handle's camera -- its bounding sphere,
+                              centre (8k + 3.5) s and radius 7 s, not outside the frustum
+                              (side-plane margin 7 s G, G = max(fx, fy) + max(cx + 0.5,
+                              W - cx - 0.5, cy + 0.5, H - cy - 0.5)) ... */
+  float zfar;              /* ... and, when zfar > 0, no farther than zfar + 7 s in depth */
 } vbh_erase_selector;
 
 /* Removal of blocks that leave the active region (Sec. 4.1: blocks no longer in view are
@@ -168,6 +174,14 @@ typedef struct {
  * (capacity: max_blocks keys) and n_erased_dev (one uint32) may be NULL. */
 vbh_status vbh_erase_blocks(vbh_handle* h, const vbh_erase_selector* sel_host,
                             int32_t* erased_keys3_dev, uint32_t* n_erased_dev);
+
+/* Fusion set of vbh_integrate_frame / vbh_process_frame.  TOUCHED (default): the blocks the
+ * frame's truncation band allocated or reached (voxel block hashing, Sec. 4.1).  VISIBLE: those
+ * and every live block in view of the frame (the FRUSTUM test above with zmax as far limit),
+ * so that voxels the band does not reach are updated where they see free space (f = 1), and
+ * surfaces that have moved away are carved; the extra blocks join the MC set too. */
+enum { VBH_INTEGRATE_TOUCHED = 0, VBH_INTEGRATE_VISIBLE = 1 };
+vbh_status vbh_set_integration_mode(vbh_handle* h, uint32_t mode);
 
 enum { VBH_MC_TOUCHED = 0, /* blocks of the last fused frame + their seven negative neighbours,
                               plus removal records for blocks erased since the last call */

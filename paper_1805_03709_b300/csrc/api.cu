@@ -388,6 +388,14 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   return st;
 }
 
+vbh_status vbh_set_integration_mode(vbh_handle* h, uint32_t mode) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  if (mode > VBH_INTEGRATE_VISIBLE) return fail(VBH_ERR_INVALID_ARG, "unknown integration mode");
+  if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
+  h->integ_mode = mode;   // the frame graph is captured again at the next frame
+  return VBH_OK;
+}
+
 vbh_status vbh_hash_rebuild(vbh_handle* h) {
   if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
   return rebuild(h);
@@ -407,6 +415,7 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   c.fp.depth = depth_dev;
   c.epoch_touch = h->next_epoch();
   c.reset = kResetFrame;
+  c.visible = h->integ_mode == VBH_INTEGRATE_VISIBLE;
   const TableView t = h->table();
   const PoolView pool = h->pool();
   h->stage_begin(VBH_STAGE_ALLOC);
@@ -418,6 +427,10 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
                             h->cand_cap, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
                             h->ctl);
   h->launches += 3;
+  if (h->integ_mode == VBH_INTEGRATE_VISIBLE) {
+    launch_visible(h->L, h->ctl, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched);
+    h->launches += 1;
+  }
   h->stage_end();
   h->stage_begin(VBH_STAGE_INTEGRATE);
   launch_integrate(h->L, c.fp, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
@@ -469,6 +482,8 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   launch_hash_insert_finish(Lc, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
                             h->cand_cap, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
                             h->ctl);
+  if (h->integ_mode == VBH_INTEGRATE_VISIBLE)
+    launch_visible(Lc, h->ctl, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched);
   if (t_int) cudaEventRecordWithFlags(ev[0], h->cap_stream, cudaEventRecordExternal);
   // the fusion node takes the frame parameters by value: vbh_process_frame patches them
   launch_integrate(Lc, base_ctl(h, nullptr).fp, pool, h->touched, h->tkey, h->tdepth,
@@ -524,7 +539,8 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   }
   VBH_CUDA(cudaGraphInstantiate(&h->frame_exec, g, 0));
   h->graph_timed = tmask;
-  h->graph_kernels = h->so ? 9 : 8;
+  h->graph_mode = h->integ_mode;
+  h->graph_kernels = 8 + (h->so ? 1 : 0) + (h->integ_mode == VBH_INTEGRATE_VISIBLE ? 1 : 0);
   return VBH_OK;
 }
 
@@ -546,7 +562,7 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
     if (st != VBH_OK) return st;
   }
   const int tmask = h->timing & ((1 << VBH_STAGE_INTEGRATE) | (1 << VBH_STAGE_MC));
-  if (!h->frame_exec || tmask != h->graph_timed) {
+  if (!h->frame_exec || tmask != h->graph_timed || h->integ_mode != h->graph_mode) {
     st = build_frame_graph(h, tmask);
     if (st != VBH_OK) return st;
   }
@@ -561,6 +577,7 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
   c.clear_removed = 1;
   c.reset = kResetFrame | kResetErase | kResetMset;
   c.serve_mark = h->slog != nullptr;
+  c.visible = h->integ_mode == VBH_INTEGRATE_VISIBLE;
   set_stream_out(c, out);
   // wait (bounded) until the graph launched kRing frames ago has consumed this slot
   const unsigned long long seq = h->host_seq;
@@ -621,6 +638,11 @@ vbh_status vbh_erase_blocks(vbh_handle* h, const vbh_erase_selector* sel,
       return fail(VBH_ERR_INVALID_ARG, "invalid erase radius / centre");
   } else if (sel->mode == VBH_ERASE_KEYS) {
     if (sel->n_keys && !sel->keys3_dev) return fail(VBH_ERR_INVALID_ARG, "null key list");
+  } else if (sel->mode == VBH_ERASE_FRUSTUM) {
+    for (int i = 0; i < 12; ++i)
+      if (!std::isfinite(sel->T_wc[i])) return fail(VBH_ERR_INVALID_ARG, "non-finite pose");
+    if (!(sel->zfar >= 0.f) || !std::isfinite(sel->zfar))
+      return fail(VBH_ERR_INVALID_ARG, "invalid far limit");
   } else {
     return fail(VBH_ERR_INVALID_ARG, "unknown erase mode");
   }
@@ -628,10 +650,17 @@ vbh_status vbh_erase_blocks(vbh_handle* h, const vbh_erase_selector* sel,
     vbh_status pst = stream_out_poll(h, false);
     if (pst != VBH_OK) return pst;
   }
-  FrameCtl c = base_ctl(h, nullptr);
+  FrameCtl c = base_ctl(h, sel->mode == VBH_ERASE_FRUSTUM ? sel->T_wc : nullptr);
   c.reset = kResetErase;
   h->stage_begin(VBH_STAGE_ERASE);
-  if (sel->mode == VBH_ERASE_RADIUS) {
+  if (sel->mode == VBH_ERASE_FRUSTUM) {
+    c.do_erase = 2;
+    c.erase_zfar = sel->zfar;
+    launch_setup(h, c);
+    launch_erase_radius(h->L, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks,
+                        erased_keys3_dev, n_erased_dev, stream_list(h));
+    h->launches += 1;
+  } else if (sel->mode == VBH_ERASE_RADIUS) {
     c.do_erase = 1;
     for (int i = 0; i < 3; ++i) c.erase_c[i] = sel->centre[i];
     c.erase_r2 = sel->radius * sel->radius;   // binary32 product, one rounding

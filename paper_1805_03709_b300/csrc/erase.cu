@@ -3,6 +3,8 @@
 // returns pool entries to the free stack; each pool entry is owned by exactly one key, so the
 // radius scan needs no de-duplication.
 //
+// Frustum erase (the scene reset of Sec. 4.1) removes every block in view of a pose by the
+// block_in_view test.
 // Canonical binary32 distance test of block k against point c and radius R:
 //   centre_i = fl(fl((float)(8 k_i) + 3.5) * s); e_i = fl(centre_i - c_i)
 //   d2 = fma(e_2, e_2, fma(e_1, e_1, fl(e_0 * e_0)));   erased iff d2 > fl(R * R)
@@ -58,9 +60,10 @@ __global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView
   __shared__ unsigned int s_erased, s_err;
   if (threadIdx.x == 0) { s_erased = 0; s_err = 0; }
   __syncthreads();
-  if (!ctl->do_erase) return;   // uniform across the grid
+  const unsigned int mode = ctl->do_erase;
+  if (!mode) return;   // uniform across the grid
   const float cx = ctl->erase_c[0], cy = ctl->erase_c[1], cz = ctl->erase_c[2];
-  const float R2 = ctl->erase_r2, s = ctl->fp.s;
+  const float R2 = ctl->erase_r2, s = ctl->fp.s, zfar = ctl->erase_zfar;
   const unsigned int stride = gridDim.x * blockDim.x;
   const unsigned int rounds = (pool.max_blocks + stride - 1u) / stride;
   for (unsigned int r = 0; r < rounds; ++r) {
@@ -70,11 +73,17 @@ __global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView
     bool erased = false;
     if (key != kEmpty) {
       const int3 k = unpack_key(key);
-      const float e0 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.x), 3.5f), s), cx);
-      const float e1 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.y), 3.5f), s), cy);
-      const float e2 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.z), 3.5f), s), cz);
-      const float d2 = __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0)));
-      if (d2 > R2) {
+      bool out;
+      if (mode == 2u) {   // scene reset: every block in view of the given pose
+        out = block_in_view(ctl->fp, k, zfar);
+      } else {
+        const float e0 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.x), 3.5f), s), cx);
+        const float e1 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.y), 3.5f), s), cy);
+        const float e2 = __fsub_rn(__fmul_rn(__fadd_rn((float)(8 * k.z), 3.5f), s), cz);
+        const float d2 = __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0)));
+        out = d2 > R2;
+      }
+      if (out) {
         unsigned int val;
         unsigned int pos = thread_find(t, key, &val);
         if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;

@@ -357,7 +357,63 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
   }
 }
 
+// Visible-set integration (the fusion set is the touched blocks plus every live block in view,
+// so voxels of blocks the truncation band does not reach are still updated where they see free
+// space): a scan of the pool appends each live block in view that this frame has not touched
+// (its epoch mark) to the touched list, with its key and origin depth.  One reservation per CTA
+// and round.
+__global__ void __launch_bounds__(256) k_visible(const FrameCtl* ctl, PoolView pool,
+                                                 unsigned int* touched,
+                                                 unsigned long long* tkey, float2* tdepth,
+                                                 unsigned int* n_touched) {
+  __shared__ FrameParams fp;
+  __shared__ unsigned int s_warp[8], s_base;
+  load_frame_params(fp, ctl);
+  if (!ctl->visible) return;   // uniform
+  const unsigned int epoch = ctl->epoch_touch;
+  const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const unsigned int rounds = (pool.max_blocks + stride - 1u) / stride;
+  for (unsigned int r = 0; r < rounds; ++r) {
+    const unsigned int p = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long key = kEmpty;
+    bool take = false;
+    if (p < pool.max_blocks) {
+      key = pool.pkeys[p];
+      take = key != kEmpty && pool.mark[p] != epoch && block_in_view(fp, unpack_key(key), fp.zmax);
+    }
+    const unsigned int bal = __ballot_sync(0xFFFFFFFFu, take);
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int run = 0;
+      for (int w = 0; w < 8; ++w) {
+        const unsigned int c = s_warp[w];
+        s_warp[w] = run;
+        run += c;
+      }
+      s_base = run ? atomicAdd(n_touched, run) : 0u;
+    }
+    __syncthreads();
+    if (take) {
+      const unsigned int k = s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u));
+      pool.mark[p] = epoch;
+      touched[k] = p;   // live, so never fresh
+      tkey[k] = key;
+      tdepth[k] = block_depth(fp, unpack_key(key));
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+void launch_visible(const Launch& L, const FrameCtl* ctl, PoolView pool, unsigned int* touched,
+                    unsigned long long* tkey, float2* tdepth, unsigned int* n_touched) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_visible, 256, L.sms);
+  k_visible<<<grid, 256, 0, L.stream>>>(ctl, pool, touched, tkey, tdepth, n_touched);
+}
 
 void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int height,
                        unsigned long long* cand, unsigned int cap, DevCounters* cnt) {

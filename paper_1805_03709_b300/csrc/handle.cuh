@@ -101,6 +101,8 @@ struct vbh_handle {
   cudaGraphNode_t integ_node = nullptr;   // fusion node: its by-value frame parameters are
   cudaKernelNodeParams integ_kp{};        // patched before every launch
   int graph_timed = 0;             // stage mask the captured graph brackets with events
+  uint32_t integ_mode = 0;         // VBH_INTEGRATE_*
+  uint32_t graph_mode = 0;         // integration mode the frame graph was captured with
   uint64_t graph_kernels = 0;
   // bookkeeping
   uint64_t launches = 0;

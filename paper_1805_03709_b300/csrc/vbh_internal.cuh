@@ -296,7 +296,9 @@ struct FrameCtl {
   FrameParams fp;
   float erase_c[3];
   float erase_r2;               // fl(R * R)
-  unsigned int do_erase;        // radius erase enabled
+  unsigned int do_erase;        // 0 none, 1 radius (erase_c, erase_r2), 2 frustum (fp pose)
+  float erase_zfar;             // frustum erase: far limit (0 = none)
+  unsigned int visible;         // fusion set = touched blocks + every live block in view
   unsigned int epoch_touch, epoch_mset, version;
   unsigned int clear_removed;   // the extraction consumes the removal list
   unsigned int reset;           // kReset* bits: counters the setup kernel zeroes
@@ -316,6 +318,31 @@ struct FrameCtl {
 };
 
 #ifdef __CUDACC__
+// Block k in view of the frame's pose (its bounding sphere, centre (8k + 3.5) s and radius
+// fl(7 s), is not outside the frustum): camera coordinates of the centre by the voxel
+// projection chain, the four side planes fx p_x + cxh p_z >= 0, (W - cxh) p_z - fx p_x >= 0
+// (and in y) with the margin rho G, G = max(fx, fy) + max(cxh, W - cxh, cyh, H - cyh) (no
+// smaller than any plane normal's norm, so every block with a voxel in view passes), near
+// p_z >= -rho and, when zfar > 0, far p_z <= zfar + rho.  Binary32, rounding explicit.
+__device__ __forceinline__ bool block_in_view(const FrameParams& fp, int3 k, float zfar) {
+  const float c0 = __fmul_rn(__fadd_rn((float)(8 * k.x), 3.5f), fp.s);
+  const float c1 = __fmul_rn(__fadd_rn((float)(8 * k.y), 3.5f), fp.s);
+  const float c2 = __fmul_rn(__fadd_rn((float)(8 * k.z), 3.5f), fp.s);
+  const float d0 = __fsub_rn(c0, fp.t[0]), d1 = __fsub_rn(c1, fp.t[1]), d2 = __fsub_rn(c2, fp.t[2]);
+  const float px = __fmaf_rn(fp.R[6], d2, __fmaf_rn(fp.R[3], d1, __fmul_rn(fp.R[0], d0)));
+  const float py = __fmaf_rn(fp.R[7], d2, __fmaf_rn(fp.R[4], d1, __fmul_rn(fp.R[1], d0)));
+  const float pz = __fmaf_rn(fp.R[8], d2, __fmaf_rn(fp.R[5], d1, __fmul_rn(fp.R[2], d0)));
+  const float rho = __fmul_rn(7.0f, fp.s);
+  const float rx = __fsub_rn(fp.fw, fp.cxh), ry = __fsub_rn(fp.fh, fp.cyh);
+  const float G = __fadd_rn(fmaxf(fp.fx, fp.fy), fmaxf(fmaxf(fp.cxh, rx), fmaxf(fp.cyh, ry)));
+  const float m = -__fmul_rn(rho, G);
+  const float a = __fmul_rn(fp.fx, px), b = __fmul_rn(fp.fy, py);
+  if (!(pz >= -rho)) return false;
+  if (zfar > 0.0f && !(pz <= __fadd_rn(zfar, rho))) return false;
+  return __fmaf_rn(fp.cxh, pz, a) >= m && __fmaf_rn(rx, pz, -a) >= m &&
+         __fmaf_rn(fp.cyh, pz, b) >= m && __fmaf_rn(ry, pz, -b) >= m;
+}
+
 // Camera depth of a block's origin, sum_i R_i2 (8 k_i s - t_i), as an unevaluated hi + lo sum
 // of floats (exact up to ~1e-13 m); feeds the value path of the fusion, never a decision.
 __device__ __forceinline__ float2 block_depth(const FrameParams& fp, int3 k) {
@@ -380,6 +407,9 @@ void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
                       const float2* tdepth, const unsigned int* n_touched, DevCounters* cnt);
 // The fusion kernel's entry (to find its node in a captured frame graph).
 const void* integrate_kernel();
+// Visible-set integration: append every live block in view that this frame did not touch.
+void launch_visible(const Launch& L, const FrameCtl* ctl, PoolView pool, unsigned int* touched,
+                    unsigned long long* tkey, float2* tdepth, unsigned int* n_touched);
 
 // erase.cu
 void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,

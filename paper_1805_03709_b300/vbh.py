@@ -22,7 +22,8 @@ VBH_ST_FOUND, VBH_ST_NOT_FOUND, VBH_ST_INSERTED, VBH_ST_EXISTS, VBH_ST_ERASED, \
     VBH_ST_CAPACITY, VBH_ST_INVALID = range(1, 8)
 VBH_NONE = 0xFFFFFFFF
 VBH_HASH_PRIMES, VBH_HASH_MIX = 0, 1
-VBH_ERASE_RADIUS, VBH_ERASE_KEYS = 0, 1
+VBH_ERASE_RADIUS, VBH_ERASE_KEYS, VBH_ERASE_FRUSTUM = 0, 1, 2
+VBH_INTEGRATE_TOUCHED, VBH_INTEGRATE_VISIBLE = 0, 1
 VBH_MC_TOUCHED, VBH_MC_ALL, VBH_MC_KEYS, VBH_MC_SINCE = 0, 1, 2, 3
 VBH_REC_REMOVED = 0x80000000
 VBH_STAGES = ("erase", "alloc", "integrate", "mcset", "mc", "hash")
@@ -54,7 +55,7 @@ class vbh_frame_stats(ctypes.Structure):
 
 class vbh_erase_selector(ctypes.Structure):
     _fields_ = [("mode", _u32), ("centre", _f32 * 3), ("radius", _f32), ("keys3_dev", _p),
-                ("n_keys", _u32)]
+                ("n_keys", _u32), ("T_wc", _f32 * 12), ("zfar", _f32)]
 
 
 class vbh_mc_selector(ctypes.Structure):
@@ -142,6 +143,7 @@ class vbh_serve_script(ctypes.Structure):
 
 
 SYMBOLS += [
+    ("vbh_set_integration_mode", ctypes.c_int, [_p, _u32]),
     ("vbh_stream_out_enable", ctypes.c_int, [_p, _u32]),
     ("vbh_stream_out_poll", ctypes.c_int, [_p, ctypes.POINTER(_u64)]),
     ("vbh_stream_out_flush", ctypes.c_int, [_p]),
@@ -459,3 +461,7 @@ def vbh_stream_in(h, keys3) -> int:
     n = _u32()
     _check(lib().vbh_stream_in(h, _ptr(k), k.shape[0], ctypes.byref(n)), "vbh_stream_in")
     return n.value
+
+
+def vbh_set_integration_mode(h, mode: int):
+    _check(lib().vbh_set_integration_mode(h, mode), "vbh_set_integration_mode")

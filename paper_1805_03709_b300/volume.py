@@ -162,6 +162,18 @@ class Volume:
         V.vbh_erase_blocks(self.h, sel, self.erased_keys if keys_out else None,
                            self.n_erased if keys_out else None)
 
+    def erase_frustum(self, T_wc, zfar: float = 0.0, keys_out: bool = True):
+        """Scene reset: erase every block in view of pose T_wc (3x4) up to depth zfar."""
+        sel = V.vbh_erase_selector(mode=V.VBH_ERASE_FRUSTUM, zfar=float(zfar))
+        sel.T_wc[:] = [float(x) for x in np.asarray(T_wc, np.float32).reshape(12)]
+        V.vbh_erase_blocks(self.h, sel, self.erased_keys if keys_out else None,
+                           self.n_erased if keys_out else None)
+
+    def set_integration_mode(self, visible: bool):
+        """Fuse the touched blocks only (default) or also every live block in view."""
+        V.vbh_set_integration_mode(self.h, V.VBH_INTEGRATE_VISIBLE if visible
+                                   else V.VBH_INTEGRATE_TOUCHED)
+
     def erase_keys(self, keys3: torch.Tensor, keys_out: bool = True):
         sel = V.vbh_erase_selector(mode=V.VBH_ERASE_KEYS, keys3_dev=keys3.data_ptr(),
                                    n_keys=int(keys3.shape[0]))

@@ -78,3 +78,28 @@ def test_create_rejects_bad_config_before_any_device_work(V, field, value):
     with pytest.raises(V.VbhError) as e:
         V.vbh_create(cfg, None)
     assert e.value.status == V.VBH_ERR_INVALID_ARG
+
+
+def test_struct_layouts_match_the_header(V, tmp_path):
+    """Size and field offsets of every ctypes mirror equal the C compiler's for vbh.h."""
+    import ctypes
+    import subprocess
+    names = [n for n in dir(V) if n.startswith("vbh_") and isinstance(getattr(V, n), type)
+             and issubclass(getattr(V, n), ctypes.Structure)]
+    assert len(names) >= 10
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vbh.h"', "int main(void) {"]
+    for n in names:
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in getattr(V, n)._fields_:
+            lines.append(f'  printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for n in names:
+        cls = getattr(V, n)
+        assert int(got[n]) == ctypes.sizeof(cls), n
+        for f, _ in cls._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(cls, f).offset, f"{n}.{f}"
