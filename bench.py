@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-visible", action="store_true",
+                    help="skip the visible-set integration measurement")
     ap.add_argument("--no-stream", action="store_true",
                     help="skip the stream-out measurement (room frames with erased blocks "
                          "copied to the host map)")
@@ -434,6 +436,9 @@ def main():
     diff_pt = None
     if not args.no_diff:
         diff_pt = diff_point(torch, dev, flush)
+    visible_pt = None
+    if not args.no_visible:
+        visible_pt = visible_point(torch, cam, D, poses, flush, args, peak)
     stream_pt = None
     if not args.no_stream:
         stream_pt = stream_point(torch, cam, D, poses, flush, args, ms_total / args.steps)
@@ -461,6 +466,7 @@ def main():
             "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
             "hash": hash_pt, "diff": diff_pt, "serve": serve_pt, "stream_out": stream_pt,
+            "visible": visible_pt,
         }
         print(json.dumps(line), flush=True)
     vol.close()
@@ -535,6 +541,47 @@ def hash_point(torch, dev, flush, peak):
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+def visible_point(torch, cam, D, poses, flush, args, peak):
+    """The timed room frames again on a fresh volume with visible-set integration (every live
+    block in view is fused, not only the blocks the band touches): frames/s, fused blocks per
+    frame and the fusion kernel's roofline with the same algorithmic bytes as the main line."""
+    from paper_1805_03709_b300.volume import Volume
+    vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
+                 N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
+                 mc_cap_entries=MAX_BLOCKS * 64)
+    vol.set_integration_mode(True)
+    for i in range(args.warmup):
+        vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+    vol.timing(("integrate",))
+    vol.timing_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    c0 = vol.counters()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        i = args.warmup + k
+        flush.zero_()
+        ev[k][0].record()
+        vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    c1 = vol.counters()
+    stage_ms, stage_n = vol.timing_read(reset=True)
+    vol.timing(())
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    touched = int(c1.total_touched - c0.total_touched)
+    new = int(c1.total_new - c0.total_new)
+    written = int(c1.total_written - c0.total_written)
+    n = max(int(stage_n["integrate"]), 1)
+    alg = ((touched - new) * 4096 + written * 8 + touched * 128 + cam.width * cam.height * 2) / n
+    integ_ms = stage_ms["integrate"] / n
+    vol.close()
+    ach = alg / (integ_ms / 1e3) / 1e9
+    return {"frames_per_s": 1e3 / ms, "ms_per_step": ms, "fused_blocks_per_frame": touched / n,
+            "new_blocks_per_frame": new / n, "integrate_ms": integ_ms,
+            "integrate_GBs": ach, "integrate_hbm_frac": ach / peak}
 
 
 def stream_point(torch, cam, D, poses, flush, args, base_ms):
