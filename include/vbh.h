@@ -468,6 +468,33 @@ vbh_status vbh_serve_run(vbh_serve* s, const vbh_serve_script* script, vbh_serve
                          uint32_t cap, uint32_t* n_host);
 uint64_t vbh_serve_now_ns(void);
 
+/* Per-client stream sets -- the paper's own serving design (Sec. 4.2), beside the version
+ * server for comparison: each client has a hash set of queued block keys (2^cap_log2 slots);
+ * vbh_sets_insert_last inserts the last extraction's refreshed blocks and removal keys into
+ * every client's set (one launch over clients x blocks); vbh_sets_fill queues every live
+ * block for one client (a (re)connect); vbh_sets_fetch serves n_req requests (distinct
+ * clients, limits 1..1024) in one launch: each takes a random subset of at most its limit out
+ * of its client's set by concurrent removal and writes, from record offset sum(limits before
+ * it), headers (x, y, z, info: the block's frame version, or VBH_REC_REMOVED when it is not
+ * live) into recs_dev (4 int32 each) and the block's dense cube indices (from the server's
+ * store) into indices_dev (512 B each); n_out_dev[i] = records of request i.  Asynchronous on
+ * the volume's stream, except vbh_sets_counts (synchronises).  The server and its volume must
+ * outlive the sets. */
+typedef struct vbh_sets vbh_sets;
+vbh_status vbh_sets_create(vbh_serve* s, uint32_t n_clients, uint32_t cap_log2, vbh_sets** out);
+vbh_status vbh_sets_destroy(vbh_sets* q);
+vbh_status vbh_sets_insert_last(vbh_sets* q);
+vbh_status vbh_sets_fill(vbh_sets* q, uint32_t client);
+vbh_status vbh_sets_fetch(vbh_sets* q, const uint32_t* clients_host, const uint32_t* limits_host,
+                          uint32_t n_req, int32_t* recs_dev, uint8_t* indices_dev,
+                          uint32_t* n_out_dev);
+/* queued keys and tombstones per client (n_clients each; may be NULL), error bits (bit0: a
+ * set was full; may be NULL). */
+vbh_status vbh_sets_counts(vbh_sets* q, uint32_t* queued_host, uint32_t* tombs_host,
+                           uint32_t* err_host);
+/* Rebuild one client's set without tombstones. */
+vbh_status vbh_sets_rebuild(vbh_sets* q, uint32_t client);
+
 /* Host-side helpers (no device work). */
 int vbh_abi_version(void);
 const char* vbh_last_error(void);

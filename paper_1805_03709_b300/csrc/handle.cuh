@@ -162,6 +162,9 @@ vbh_status stream_out_poll(vbh_handle* h, bool wait);
 unsigned long long stream_out_tail(const vbh_handle* h);
 void stream_out_release(vbh_handle* h);
 inline StreamList stream_list(const vbh_handle* h);
+// The volume handle and the device-resident log/store of a server (serve.cu).
+vbh_handle* serve_handle(vbh_serve* s);
+const ServeLog* serve_log(vbh_serve* s);
 // MC refresh of every live block into the attached server's store and log, with no stream
 // output (enqueued on the handle's stream).  counts_dev: two device words of scratch.
 vbh_status refresh_all_blocks(vbh_handle* h, unsigned int* counts_dev);

@@ -543,6 +543,11 @@ vbh_status vbh_serve::launch() {
   return VBH_OK;
 }
 
+namespace vbh {
+vbh_handle* serve_handle(vbh_serve* s) { return s->h; }
+const ServeLog* serve_log(vbh_serve* s) { return s->sl_dev; }
+}  // namespace vbh
+
 extern "C" {
 
 uint64_t vbh_serve_now_ns(void) { return now_ns(); }

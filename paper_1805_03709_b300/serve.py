@@ -126,3 +126,46 @@ class Server:
         n_req = int((c >= 0).sum())
         got = V.vbh_serve_run(self.s, sc, cap if cap is not None else n_req)
         return [done_dict(d) for d in got]
+
+
+class StreamSets:
+    """The paper's per-client stream sets (vbh_sets_*), beside a Server whose store they read."""
+
+    def __init__(self, server: Server, n_clients: int, cap_log2: int = 18):
+        self.server = server
+        self.n_clients = n_clients
+        self.q = V.vbh_sets_create(server.s, n_clients, cap_log2)
+
+    def close(self):
+        if getattr(self, "q", None):
+            if getattr(self.server, "s", None):
+                V.vbh_sets_destroy(self.q)
+            self.q = None
+
+    __del__ = close
+
+    def insert_last(self):
+        V.vbh_sets_insert_last(self.q)
+
+    def fill(self, client: int):
+        V.vbh_sets_fill(self.q, client)
+
+    def fetch(self, clients, limits):
+        """[(records int32 [n, 4], indices uint8 [n, 512])] per request (device tensors)."""
+        total = int(np.sum(limits))
+        recs = torch.empty((total, 4), dtype=torch.int32, device="cuda")
+        idx = torch.empty((total, 512), dtype=torch.uint8, device="cuda")
+        n_out = torch.empty(len(clients), dtype=torch.int32, device="cuda")
+        V.vbh_sets_fetch(self.q, clients, limits, recs, idx, n_out)
+        n = n_out.cpu().numpy()
+        out, off = [], 0
+        for i, lim in enumerate(limits):
+            out.append((recs[off:off + n[i]], idx[off:off + n[i]]))
+            off += int(lim)
+        return out
+
+    def counts(self):
+        return V.vbh_sets_counts(self.q, self.n_clients)
+
+    def rebuild(self, client: int):
+        V.vbh_sets_rebuild(self.q, client)

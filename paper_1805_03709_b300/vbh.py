@@ -143,6 +143,13 @@ class vbh_serve_script(ctypes.Structure):
 
 
 SYMBOLS += [
+    ("vbh_sets_create", ctypes.c_int, [_p, _u32, _u32, ctypes.POINTER(_p)]),
+    ("vbh_sets_destroy", ctypes.c_int, [_p]),
+    ("vbh_sets_insert_last", ctypes.c_int, [_p]),
+    ("vbh_sets_fill", ctypes.c_int, [_p, _u32]),
+    ("vbh_sets_fetch", ctypes.c_int, [_p, _p, _p, _u32, _p, _p, _p]),
+    ("vbh_sets_counts", ctypes.c_int, [_p, _p, _p, _p]),
+    ("vbh_sets_rebuild", ctypes.c_int, [_p, _u32]),
     ("vbh_set_integration_mode", ctypes.c_int, [_p, _u32]),
     ("vbh_stream_out_enable", ctypes.c_int, [_p, _u32]),
     ("vbh_stream_out_poll", ctypes.c_int, [_p, ctypes.POINTER(_u64)]),
@@ -465,3 +472,42 @@ def vbh_stream_in(h, keys3) -> int:
 
 def vbh_set_integration_mode(h, mode: int):
     _check(lib().vbh_set_integration_mode(h, mode), "vbh_set_integration_mode")
+
+
+# ------------------------------------------------------------------ per-client stream sets
+def vbh_sets_create(server, n_clients: int, cap_log2: int) -> int:
+    out = _p()
+    _check(lib().vbh_sets_create(server, n_clients, cap_log2, ctypes.byref(out)),
+           "vbh_sets_create")
+    return out.value
+
+
+def vbh_sets_destroy(q):
+    _check(lib().vbh_sets_destroy(q), "vbh_sets_destroy")
+
+
+def vbh_sets_insert_last(q):
+    _check(lib().vbh_sets_insert_last(q), "vbh_sets_insert_last")
+
+
+def vbh_sets_fill(q, client: int):
+    _check(lib().vbh_sets_fill(q, client), "vbh_sets_fill")
+
+
+def vbh_sets_fetch(q, clients, limits, recs, indices, n_out):
+    c = np.ascontiguousarray(clients, np.uint32)
+    l = np.ascontiguousarray(limits, np.uint32)
+    _check(lib().vbh_sets_fetch(q, _ptr(c), _ptr(l), len(c), _ptr(recs), _ptr(indices),
+                                _ptr(n_out)), "vbh_sets_fetch")
+
+
+def vbh_sets_counts(q, n_clients: int):
+    a = np.zeros(n_clients, np.uint32)
+    b = np.zeros(n_clients, np.uint32)
+    e = np.zeros(1, np.uint32)
+    _check(lib().vbh_sets_counts(q, _ptr(a), _ptr(b), _ptr(e)), "vbh_sets_counts")
+    return a, b, int(e[0])
+
+
+def vbh_sets_rebuild(q, client: int):
+    _check(lib().vbh_sets_rebuild(q, client), "vbh_sets_rebuild")
