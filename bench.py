@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sets", action="store_true",
+                    help="skip the per-client stream-set comparison")
     ap.add_argument("--no-visible", action="store_true",
                     help="skip the visible-set integration measurement")
     ap.add_argument("--no-stream", action="store_true",
@@ -442,6 +444,9 @@ def main():
     stream_pt = None
     if not args.no_stream:
         stream_pt = stream_point(torch, cam, D, poses, flush, args, ms_total / args.steps)
+    sets_pt = None
+    if not args.no_sets and rank == 0:
+        sets_pt = sets_point(torch, cam, D, poses)
     serve_pt = None
     if not args.no_serve and rank == 0:
         serve_pt = serve_point(torch, cam, D, poses, peak, args.serve_seconds)
@@ -466,7 +471,7 @@ def main():
             "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
             "hash": hash_pt, "diff": diff_pt, "serve": serve_pt, "stream_out": stream_pt,
-            "visible": visible_pt,
+            "visible": visible_pt, "stream_sets": sets_pt,
         }
         print(json.dumps(line), flush=True)
     vol.close()
@@ -541,6 +546,61 @@ def hash_point(torch, dev, flush, peak):
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+def sets_point(torch, cam, D, poses, n_clients=64, warm_frames=30, frames=60, limit=512):
+    """The paper's per-client stream sets on the room volume: every frame's refreshed and
+    removed blocks are inserted into each of 64 clients' sets (timed per frame), then one launch
+    serves a 512-block request (the paper's package) of every client.  The version server
+    needs no per-frame work per client (its change log is written once by the extraction)."""
+    from paper_1805_03709_b300.serve import Server, StreamSets
+    from paper_1805_03709_b300.volume import Volume
+    vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
+                 N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
+                 mc_cap_entries=MAX_BLOCKS * 64)
+    for i in range(warm_frames):
+        vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+    srv = Server(vol, 1, budget_bytes=1 << 30)
+    sets = StreamSets(srv, n_clients, cap_log2=19)
+    ins_ms, n_ins = [], []
+    for k in range(frames):
+        i = warm_frames + k
+        vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sets.insert_last()
+        e1.record()
+        torch.cuda.synchronize()
+        ins_ms.append(e0.elapsed_time(e1))
+        n_ins.append(vol.counters().last_mc_blocks)
+    queued, tombs, err = sets.counts()
+    from paper_1805_03709_b300 import vbh as V
+    clients = np.arange(n_clients, dtype=np.uint32)
+    limits = np.full(n_clients, limit, np.uint32)
+    recs = torch.empty((n_clients * limit, 4), dtype=torch.int32, device="cuda")
+    idx = torch.empty((n_clients * limit, 512), dtype=torch.uint8, device="cuda")
+    n_out = torch.empty(n_clients, dtype=torch.int32, device="cuda")
+    fetch_ms, blocks = [], 0
+    for rep in range(5):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        V.vbh_sets_fetch(sets.q, clients, limits, recs, idx, n_out)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep:
+            fetch_ms.append(e0.elapsed_time(e1))
+            blocks += int(n_out.sum())
+    sets.close()
+    srv.close()
+    vol.close()
+    f_ms = statistics.median(fetch_ms)
+    return {"clients": n_clients, "frames": frames,
+            "insert_ms_per_frame": statistics.median(ins_ms),
+            "keys_per_frame_per_client": float(np.mean(n_ins)),
+            "inserts_per_s": float(np.mean(n_ins)) * n_clients / (statistics.median(ins_ms) / 1e3),
+            "queued_per_client_mean": float(np.mean(queued)), "set_errors": err,
+            "fetch_ms_64x512": f_ms, "fetch_blocks_per_s": blocks / len(fetch_ms) / (f_ms / 1e3)}
 
 
 def visible_point(torch, cam, D, poses, flush, args, peak):
