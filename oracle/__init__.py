@@ -79,6 +79,10 @@ def lib():
         L.orc_vol_dump.argtypes = [P, P, P, P, U32]
         L.orc_vol_dump.restype = U32
         L.orc_vol_load.argtypes = [P, P, P, P, U32]
+        L.orc_tri_case.argtypes = [ctypes.c_int, P, U32]
+        L.orc_tri_case.restype = U32
+        L.orc_vol_triangles.argtypes = [P, P, U32, P, U32]
+        L.orc_vol_triangles.restype = U32
         L.orc_vol_host_dump.argtypes = [P, P, P, P, U32]
         L.orc_vol_host_dump.restype = U32
         L.orc_vol_stream_in.argtypes = [P, P, U32]
@@ -203,6 +207,14 @@ class OracleVolume:
         lib().orc_vol_dump(self._h, _p(k), _p(F), _p(W), n)
         return k, F, W
 
+    def triangles(self, keys3):
+        """R10: triangles (m, 3, 3) in metres of the cubes at the voxels of the given blocks."""
+        k = np.ascontiguousarray(keys3, np.int32).reshape(-1, 3)
+        m = lib().orc_vol_triangles(self._h, _p(k), k.shape[0], None, 0)
+        out = np.zeros((max(m, 1), 9), np.float64)
+        lib().orc_vol_triangles(self._h, _p(k), k.shape[0], _p(out), m)
+        return out[:m].reshape(-1, 3, 3)
+
     def host_dump(self):
         """The passive host map of streamed-out (erased) blocks: keys sorted, F, W."""
         n = lib().orc_vol_host_dump(self._h, None, None, None, 0)
@@ -308,3 +320,11 @@ class OracleDiffFusion:
                                       len(self.samples), _p(self.depth), _p(self.T0), _p(xi),
                                       _p(self.masks), _p(gd), _p(gx))
         return gd, gx
+
+
+def tri_case(c: int) -> np.ndarray:
+    """R10: the triangles of cube index c as (t, 3) edge indices."""
+    out = np.zeros((16, 3), np.int32)
+    n = lib().orc_tri_case(int(c), _p(out), 16)
+    assert n <= 16
+    return out[:n]

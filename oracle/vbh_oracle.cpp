@@ -46,6 +46,16 @@
 //      with every live block in view (R7, far limit zmax): blocks that are not reached by the
 //      frame's truncation band are still updated where their voxels see free space (f = 1).
 //   R9 (scene reset, Sec. 4.1) a frustum erase removes every live block in view (R7).
+//   R10 (triangulation, Sec. 4.3: vertices at edge midpoints, no interpolation) the triangles of
+//      a cube index come from a cube-case analysis: on every face, walked counter-clockwise as
+//      seen from outside the cube, each crossing from an inside corner (bit set) to an outside
+//      one (an exit) is joined to the crossing into the inside that precedes it (an entry), so
+//      an ambiguous face keeps its inside corners apart; the directed joins exit -> entry close
+//      into loops over the cube's faces (each started at its smallest edge number); a loop is
+//      cut by ear clipping, always at the first position (in loop order) whose new diagonal
+//      joins two edges on no common face (else at the first position), each triangle in the
+//      reversed loop order so that normals point to the outside (positive TSDF).  Edge j joins
+//      corners kEdge[j].
 //   R-mc corner i of the cube at voxel g is g + c_i with the classic numbering
 //      c = (000,100,110,010,001,101,111,011) (x fastest); bit i is set iff F(corner) < 0; a cube
 //      with any corner in a missing block or with W == 0 is invalid and gets index 0.
@@ -246,6 +256,117 @@ bool in_view(const Volume& v, const K3& k, const float* T, float zfar) {
 // R-mc corner offsets, classic numbering.
 const int kCorner[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
                            {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+
+// R10: the triangle table, derived from the cube cases (no stored table).
+const int kEdge[12][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 0}, {4, 5}, {5, 6},
+                          {6, 7}, {7, 4}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+
+int edge_of(int a, int b) {
+  for (int j = 0; j < 12; ++j)
+    if ((kEdge[j][0] == a && kEdge[j][1] == b) || (kEdge[j][0] == b && kEdge[j][1] == a)) return j;
+  return -1;
+}
+
+// two cube edges lie on a common face when their four corners agree in one coordinate
+bool share_face(int e1, int e2) {
+  const int cs[4] = {kEdge[e1][0], kEdge[e1][1], kEdge[e2][0], kEdge[e2][1]};
+  for (int axis = 0; axis < 3; ++axis) {
+    bool same = true;
+    for (int i = 1; i < 4; ++i) same = same && kCorner[cs[i]][axis] == kCorner[cs[0]][axis];
+    if (same) return true;
+  }
+  return false;
+}
+
+struct TriTable {
+  std::vector<std::array<int, 3>> tris[256];
+  TriTable() {
+    // the six faces as corner cycles, counter-clockwise seen from outside (checked by the
+    // cross product against the outward normal)
+    std::vector<std::array<int, 4>> faces;
+    for (int axis = 0; axis < 3; ++axis)
+      for (int side = 0; side < 2; ++side) {
+        std::vector<int> cs;
+        for (int c = 0; c < 8; ++c)
+          if (kCorner[c][axis] == side) cs.push_back(c);
+        // order the 4 corners around the face: start at cs[0], then walk along cube edges
+        std::array<int, 4> cyc{cs[0], -1, -1, -1};
+        std::vector<bool> used(8, false);
+        used[cs[0]] = true;
+        for (int k = 1; k < 4; ++k)
+          for (int c : cs)
+            if (!used[c] && edge_of(cyc[k - 1], c) >= 0) {
+              cyc[k] = c;
+              used[c] = true;
+              break;
+            }
+        double a[3], b[3], n[3];
+        for (int i = 0; i < 3; ++i) {
+          a[i] = kCorner[cyc[1]][i] - kCorner[cyc[0]][i];
+          b[i] = kCorner[cyc[2]][i] - kCorner[cyc[1]][i];
+        }
+        n[0] = a[1] * b[2] - a[2] * b[1];
+        n[1] = a[2] * b[0] - a[0] * b[2];
+        n[2] = a[0] * b[1] - a[1] * b[0];
+        const double outward = side ? 1.0 : -1.0;
+        if (n[axis] * outward < 0) std::swap(cyc[1], cyc[3]);
+        faces.push_back(cyc);
+      }
+    for (int c = 0; c < 256; ++c) {
+      int next[12];
+      for (int j = 0; j < 12; ++j) next[j] = -1;
+      for (const auto& f : faces) {
+        // crossing events along the cycle: +1 entry, -1 exit, at the edge of (f[k], f[k+1])
+        int ev_edge[4], ev_type[4], m = 0;
+        for (int k = 0; k < 4; ++k) {
+          const bool in0 = (c >> f[k]) & 1, in1 = (c >> f[(k + 1) % 4]) & 1;
+          if (in0 != in1) {
+            ev_edge[m] = edge_of(f[k], f[(k + 1) % 4]);
+            ev_type[m] = in1 ? +1 : -1;
+            ++m;
+          }
+        }
+        for (int i = 0; i < m; ++i)
+          if (ev_type[i] == -1) {   // the entry before this exit (events alternate)
+            const int e = ev_edge[(i + m - 1) % m];
+            next[ev_edge[i]] = e;
+          }
+      }
+      bool seen[12] = {false};
+      for (int s0 = 0; s0 < 12; ++s0) {
+        if (next[s0] < 0 || seen[s0]) continue;
+        std::vector<int> loop;
+        for (int e = s0; !seen[e]; e = next[e]) {
+          seen[e] = true;
+          loop.push_back(e);
+        }
+        // ear clipping: the first ear (in loop order) whose new diagonal joins two edges on no
+        // common face (a diagonal on a face would be shared with the neighbouring cube)
+        while (loop.size() > 3) {
+          size_t pick = 0;
+          bool found = false;
+          for (size_t i = 0; i < loop.size() && !found; ++i) {
+            const int a = loop[(i + loop.size() - 1) % loop.size()], b = loop[(i + 1) % loop.size()];
+            if (!share_face(a, b)) {
+              pick = i;
+              found = true;
+            }
+          }
+          const size_t n = loop.size();
+          const int a = loop[(pick + n - 1) % n], m = loop[pick], b = loop[(pick + 1) % n];
+          tris[c].push_back({a, b, m});   // reversed loop order: normals to the outside
+          loop.erase(loop.begin() + (long)pick);
+        }
+        tris[c].push_back({loop[0], loop[2], loop[1]});
+      }
+    }
+  }
+};
+
+const TriTable& tri_table() {
+  static TriTable t;
+  return t;
+}
 
 // Sec. 4.2: the MC index of the cube at voxel g, with S^c (0 and 255) written as 0.
 // `margin` receives min |F| over the 8 corners (+inf for an invalid cube).
@@ -450,6 +571,40 @@ uint32_t orc_vol_erase_keys(void* h, const int32_t* keys3, uint32_t n) {
     }
   }
   return c;
+}
+
+// R10: triangles of cube index c as edge triples (out: up to cap triangles); returns count.
+uint32_t orc_tri_case(int c, int32_t* edges, uint32_t cap) {
+  const auto& t = tri_table().tris[c & 255];
+  for (size_t i = 0; i < t.size() && i < cap; ++i)
+    for (int j = 0; j < 3; ++j) edges[3 * i + j] = t[i][j];
+  return (uint32_t)t.size();
+}
+
+// R10 on the model: every triangle of the cubes at the voxels of the given blocks (their MC
+// indices by Sec. 4.2), vertices at edge midpoints in metres, 9 doubles per triangle, in block
+// order then voxel order lx + 8 ly + 64 lz then table order; returns the count.
+uint32_t orc_vol_triangles(void* h, const int32_t* keys3, uint32_t n, double* out, uint32_t cap) {
+  const Volume& v = *(const Volume*)h;
+  uint32_t m = 0;
+  for (uint32_t b = 0; b < n; ++b)
+    for (int l = 0; l < 512; ++l) {
+      const int g[3] = {8 * keys3[3 * b] + (l & 7), 8 * keys3[3 * b + 1] + ((l >> 3) & 7),
+                        8 * keys3[3 * b + 2] + (l >> 6)};
+      double margin;
+      const int c = mc_index(v, g, &margin);
+      for (const auto& tri : tri_table().tris[c]) {
+        if (m < cap && out)
+          for (int k = 0; k < 3; ++k) {
+            const int* e = kEdge[tri[k]];
+            for (int i = 0; i < 3; ++i)
+              out[9 * m + 3 * k + i] =
+                  (g[i] + 0.5 * (kCorner[e[0]][i] + kCorner[e[1]][i])) * (double)v.s;
+          }
+        ++m;
+      }
+    }
+  return m;
 }
 
 // The host map of streamed-out blocks, keys sorted (like orc_vol_dump).
