@@ -468,6 +468,24 @@ vbh_status vbh_serve_run(vbh_serve* s, const vbh_serve_script* script, vbh_serve
                          uint32_t cap, uint32_t* n_host);
 uint64_t vbh_serve_now_ns(void);
 
+/* Marching Cubes triangulation of an MC stream (Sec. 4.3: an exploration client builds its
+ * mesh from the indices, vertices at edge midpoints, no interpolation).  The triangle table is
+ * derived from the cube cases: corner i = (000, 100, 110, 010, 001, 101, 111, 011)[i] (bit i
+ * set = TSDF < 0), edges 0-11 join corners (0,1) (1,2) (2,3) (3,0) (4,5) (5,6) (6,7) (7,4)
+ * (0,4) (1,5) (2,6) (3,7); on each face, walked counter-clockwise from outside, a crossing out
+ * of the inside joins the crossing into it that precedes it (ambiguous faces keep inside
+ * corners apart); the joins close into loops, cut by ear clipping without diagonals on a
+ * face; normals point to positive TSDF.  At most 5 triangles per index.
+ * vbh_mc_tri_table (host only): n_host[256] triangle counts, edges_host[256 * 15] edge triples.
+ * vbh_mc_triangulate: every entry of the device stream `in` (as written by
+ * vbh_extract_mc_indices) becomes its triangles, 9 floats each (three vertices, metres: the
+ * edge midpoints of the cube at voxel g, (g + m) * voxel_size), in no particular order;
+ * *n_tris_dev (device) = triangles produced (the first cap_tris are written).  Asynchronous on
+ * cuda_stream; allocates nothing (the table goes to constant memory at the first call). */
+vbh_status vbh_mc_tri_table(uint8_t* n_host, uint8_t* edges_host);
+vbh_status vbh_mc_triangulate(const vbh_mc_stream* in, float voxel_size, float* tris_dev,
+                              uint32_t cap_tris, uint32_t* n_tris_dev, void* cuda_stream);
+
 /* Per-client stream sets -- the paper's own serving design (Sec. 4.2), beside the version
  * server for comparison: each client has a hash set of queued block keys (2^cap_log2 slots);
  * vbh_sets_insert_last inserts the last extraction's refreshed blocks and removal keys into

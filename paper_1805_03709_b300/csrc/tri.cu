@@ -1,0 +1,264 @@
+// Marching Cubes triangulation of an MC stream (Sec. 4.3: the exploration client builds its
+// mesh from the transmitted indices, with vertices at edge midpoints -- no interpolation).
+//
+// The triangle table is derived here from the cube cases, at first use, not stored:
+//   * corner i of a cube is c_i = (000, 100, 110, 010, 001, 101, 111, 011)[i] (x fastest), bit i
+//     of the index set means the corner is inside (TSDF < 0); edges 0-11 join the corner pairs
+//     (0,1) (1,2) (2,3) (3,0) (4,5) (5,6) (6,7) (7,4) (0,4) (1,5) (2,6) (3,7);
+//   * each face is walked counter-clockwise as seen from outside the cube; a crossing from an
+//     inside corner to an outside one (exit) is joined to the crossing into the inside that
+//     precedes it (entry), so an ambiguous face keeps its inside corners apart, and both cubes
+//     sharing the face join its crossings alike;
+//   * the directed joins exit -> entry close into loops; a loop starts at its smallest edge and
+//     is cut by ear clipping at the first position whose new diagonal joins two edges on no
+//     common face (a diagonal lying on a face would be shared with the neighbouring cube), each
+//     triangle in the reversed loop order so that normals point to positive TSDF.
+// The kernel: one warp per stream record, its entries' triangle counts summed per CTA round with
+// one reservation, then each entry writes its triangles (9 floats, metres).
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "handle.cuh"
+
+namespace vbh {
+
+namespace {
+
+__constant__ unsigned char c_tri_n[256];
+__constant__ unsigned char c_tri_e[256][15];
+__constant__ unsigned char c_mid2[12][3];   // 2 x edge midpoint (0, 1 or 2 per axis)
+
+constexpr int kCube[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                             {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+constexpr int kEdges[12][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 0}, {4, 5}, {5, 6},
+                               {6, 7}, {7, 4}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+
+struct Tables {
+  unsigned char n[256];
+  unsigned char e[256][15];
+  unsigned char mid2[12][3];
+};
+
+int find_edge(int p, int q) {
+  for (int j = 0; j < 12; ++j)
+    if ((kEdges[j][0] == p && kEdges[j][1] == q) || (kEdges[j][0] == q && kEdges[j][1] == p))
+      return j;
+  return -1;
+}
+
+bool on_one_face(int e1, int e2) {
+  const int v[4] = {kEdges[e1][0], kEdges[e1][1], kEdges[e2][0], kEdges[e2][1]};
+  for (int ax = 0; ax < 3; ++ax)
+    if (kCube[v[0]][ax] == kCube[v[1]][ax] && kCube[v[0]][ax] == kCube[v[2]][ax] &&
+        kCube[v[0]][ax] == kCube[v[3]][ax])
+      return true;
+  return false;
+}
+
+Tables derive_tables() {
+  Tables T{};
+  for (int j = 0; j < 12; ++j)
+    for (int ax = 0; ax < 3; ++ax)
+      T.mid2[j][ax] = (unsigned char)(kCube[kEdges[j][0]][ax] + kCube[kEdges[j][1]][ax]);
+  // faces: corners with coordinate `ax` equal to `side`, in a cycle along cube edges, turned
+  // counter-clockwise about the outward normal
+  int face[6][4];
+  int nf = 0;
+  for (int ax = 0; ax < 3; ++ax)
+    for (int side = 0; side <= 1; ++side) {
+      int cyc[4], k = 0;
+      bool taken[8] = {false};
+      for (int c = 0; c < 8 && k == 0; ++c)
+        if (kCube[c][ax] == side) { cyc[k++] = c; taken[c] = true; }
+      while (k < 4)
+        for (int c = 0; c < 8; ++c)
+          if (!taken[c] && kCube[c][ax] == side && find_edge(cyc[k - 1], c) >= 0) {
+            cyc[k++] = c;
+            taken[c] = true;
+            break;
+          }
+      int u[3], w[3];
+      for (int i = 0; i < 3; ++i) {
+        u[i] = kCube[cyc[1]][i] - kCube[cyc[0]][i];
+        w[i] = kCube[cyc[2]][i] - kCube[cyc[1]][i];
+      }
+      const int cross_ax = u[(ax + 1) % 3] * w[(ax + 2) % 3] - u[(ax + 2) % 3] * w[(ax + 1) % 3];
+      if ((side == 1 && cross_ax < 0) || (side == 0 && cross_ax > 0)) {
+        const int t = cyc[1];
+        cyc[1] = cyc[3];
+        cyc[3] = t;
+      }
+      for (int i = 0; i < 4; ++i) face[nf][i] = cyc[i];
+      ++nf;
+    }
+  for (int idx = 0; idx < 256; ++idx) {
+    int join[12];
+    for (int j = 0; j < 12; ++j) join[j] = -1;
+    for (int f = 0; f < 6; ++f) {
+      int edge_at[4], kind[4], m = 0;   // kind: 1 entry, 0 exit
+      for (int i = 0; i < 4; ++i) {
+        const int p = face[f][i], q = face[f][(i + 1) % 4];
+        const int ip = (idx >> p) & 1, iq = (idx >> q) & 1;
+        if (ip == iq) continue;
+        edge_at[m] = find_edge(p, q);
+        kind[m] = iq;
+        ++m;
+      }
+      for (int i = 0; i < m; ++i)
+        if (kind[i] == 0) join[edge_at[i]] = edge_at[(i + m - 1) % m];
+    }
+    int count = 0;
+    bool done[12] = {false};
+    for (int start = 0; start < 12; ++start) {
+      if (join[start] < 0 || done[start]) continue;
+      std::vector<int> poly;
+      for (int e = start; !done[e]; e = join[e]) {
+        done[e] = true;
+        poly.push_back(e);
+      }
+      while (poly.size() > 3) {
+        const size_t n = poly.size();
+        size_t at = 0;
+        for (size_t i = 0; i < n; ++i)
+          if (!on_one_face(poly[(i + n - 1) % n], poly[(i + 1) % n])) {
+            at = i;
+            break;
+          }
+        const int a = poly[(at + n - 1) % n], b = poly[at], c = poly[(at + 1) % n];
+        T.e[idx][3 * count] = (unsigned char)a;
+        T.e[idx][3 * count + 1] = (unsigned char)c;
+        T.e[idx][3 * count + 2] = (unsigned char)b;
+        ++count;
+        poly.erase(poly.begin() + (long)at);
+      }
+      T.e[idx][3 * count] = (unsigned char)poly[0];
+      T.e[idx][3 * count + 1] = (unsigned char)poly[2];
+      T.e[idx][3 * count + 2] = (unsigned char)poly[1];
+      ++count;
+    }
+    T.n[idx] = (unsigned char)count;
+  }
+  return T;
+}
+
+std::mutex g_tri_mutex;
+std::vector<int> g_tri_ready;   // per device
+
+vbh_status upload_tables() {
+  int dev = 0;
+  VBH_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(g_tri_mutex);
+  if ((int)g_tri_ready.size() <= dev) g_tri_ready.resize(dev + 1, 0);
+  if (g_tri_ready[dev]) return VBH_OK;
+  static const Tables T = derive_tables();
+  VBH_CUDA(cudaMemcpyToSymbol(c_tri_n, T.n, sizeof T.n));
+  VBH_CUDA(cudaMemcpyToSymbol(c_tri_e, T.e, sizeof T.e));
+  VBH_CUDA(cudaMemcpyToSymbol(c_mid2, T.mid2, sizeof T.mid2));
+  g_tri_ready[dev] = 1;
+  return VBH_OK;
+}
+
+constexpr int kTriThreads = 256;
+
+__global__ void __launch_bounds__(kTriThreads) k_mc_triangulate(
+    const int* keys3, const unsigned int* offsets, const unsigned int* counts,
+    const unsigned short* local, const unsigned char* index, const unsigned int* n_blocks_dev,
+    unsigned int cap_blocks, unsigned int cap_entries, float half_s, float* tris,
+    unsigned int cap_tris, unsigned int* n_tris) {
+  __shared__ unsigned int s_warp[kTriThreads / 32], s_base;
+  const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned int nb = min(*n_blocks_dev, cap_blocks);
+  const unsigned int per_round = gridDim.x * (kTriThreads / 32);
+  const unsigned int rounds = (nb + per_round - 1u) / per_round;
+  for (unsigned int rd = 0; rd < rounds; ++rd) {
+    const unsigned int r = rd * per_round + blockIdx.x * (kTriThreads / 32) + warp;
+    unsigned int off = 0, cnt = 0;
+    int kx = 0, ky = 0, kz = 0;
+    if (r < nb) {
+      off = offsets[r];
+      cnt = counts[r];
+      if ((unsigned long long)off + cnt > cap_entries) cnt = 0;   // an overflowed stream
+      kx = keys3[3u * r];
+      ky = keys3[3u * r + 1];
+      kz = keys3[3u * r + 2];
+    }
+    unsigned int mine = 0;
+    for (unsigned int e = lane; e < cnt; e += 32u) mine += c_tri_n[index[off + e]];
+    unsigned int incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if ((int)lane >= d) incl += v;
+    }
+    if (lane == 31u) s_warp[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int run = 0;
+      for (int w = 0; w < kTriThreads / 32; ++w) {
+        const unsigned int c = s_warp[w];
+        s_warp[w] = run;
+        run += c;
+      }
+      s_base = run ? atomicAdd(n_tris, run) : 0u;
+    }
+    __syncthreads();
+    unsigned int o = s_base + s_warp[warp] + incl - mine;
+    for (unsigned int e = lane; e < cnt; e += 32u) {
+      const unsigned int ci = index[off + e];
+      const unsigned int l = local[off + e];
+      const int gx2 = 2 * (8 * kx + (int)(l & 7u)), gy2 = 2 * (8 * ky + (int)((l >> 3) & 7u)),
+                gz2 = 2 * (8 * kz + (int)(l >> 6));
+      for (unsigned int t = 0; t < c_tri_n[ci]; ++t, ++o) {
+        if (o >= cap_tris) continue;
+        float* dst = tris + 9ull * o;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const unsigned int ed = c_tri_e[ci][3 * t + v];
+          dst[3 * v] = __fmul_rn((float)(gx2 + c_mid2[ed][0]), half_s);
+          dst[3 * v + 1] = __fmul_rn((float)(gy2 + c_mid2[ed][1]), half_s);
+          dst[3 * v + 2] = __fmul_rn((float)(gz2 + c_mid2[ed][2]), half_s);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+}  // namespace vbh
+
+using namespace vbh;
+
+extern "C" {
+
+vbh_status vbh_mc_tri_table(uint8_t* n_host, uint8_t* edges_host) {
+  if (!n_host || !edges_host) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  static const Tables T = derive_tables();
+  std::memcpy(n_host, T.n, sizeof T.n);
+  std::memcpy(edges_host, T.e, sizeof T.e);
+  return VBH_OK;
+}
+
+vbh_status vbh_mc_triangulate(const vbh_mc_stream* in, float voxel_size, float* tris_dev,
+                              uint32_t cap_tris, uint32_t* n_tris_dev, void* cuda_stream) {
+  if (!in || !n_tris_dev || (cap_tris && !tris_dev)) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if (!in->n_blocks_dev || (in->cap_blocks && (!in->keys3 || !in->offsets || !in->counts)) ||
+      (in->cap_entries && (!in->local || !in->index)))
+    return fail(VBH_ERR_INVALID_ARG, "incomplete input stream");
+  if (!(voxel_size > 0.f)) return fail(VBH_ERR_INVALID_ARG, "voxel_size must be positive");
+  vbh_status st = upload_tables();
+  if (st != VBH_OK) return st;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  VBH_CUDA(cudaMemsetAsync(n_tris_dev, 0, sizeof(uint32_t), s));
+  int dev = 0, sms = 0;
+  VBH_CUDA(cudaGetDevice(&dev));
+  VBH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  k_mc_triangulate<<<sms * 4, kTriThreads, 0, s>>>(
+      in->keys3, in->offsets, in->counts, in->local, in->index, in->n_blocks_dev, in->cap_blocks,
+      in->cap_entries, 0.5f * voxel_size, tris_dev, cap_tris, n_tris_dev);
+  VBH_CUDA(cudaGetLastError());
+  return VBH_OK;
+}
+
+}  // extern "C"

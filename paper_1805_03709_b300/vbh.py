@@ -143,6 +143,9 @@ class vbh_serve_script(ctypes.Structure):
 
 
 SYMBOLS += [
+    ("vbh_mc_tri_table", ctypes.c_int, [_p, _p]),
+    ("vbh_mc_triangulate", ctypes.c_int, [ctypes.POINTER(vbh_mc_stream), _f32, _p, _u32, _p,
+                                          _p]),
     ("vbh_sets_create", ctypes.c_int, [_p, _u32, _u32, ctypes.POINTER(_p)]),
     ("vbh_sets_destroy", ctypes.c_int, [_p]),
     ("vbh_sets_insert_last", ctypes.c_int, [_p]),
@@ -511,3 +514,17 @@ def vbh_sets_counts(q, n_clients: int):
 
 def vbh_sets_rebuild(q, client: int):
     _check(lib().vbh_sets_rebuild(q, client), "vbh_sets_rebuild")
+
+
+# ------------------------------------------------------------------------- triangulation
+def vbh_mc_tri_table():
+    n = np.zeros(256, np.uint8)
+    e = np.zeros((256, 15), np.uint8)
+    _check(lib().vbh_mc_tri_table(_ptr(n), _ptr(e)), "vbh_mc_tri_table")
+    return n, e
+
+
+def vbh_mc_triangulate(stream: "vbh_mc_stream", voxel_size: float, tris, cap: int, n_tris,
+                       cuda_stream=None):
+    _check(lib().vbh_mc_triangulate(ctypes.byref(stream), voxel_size, _ptr(tris), cap,
+                                    _ptr(n_tris), cuda_stream), "vbh_mc_triangulate")

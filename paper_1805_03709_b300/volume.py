@@ -209,6 +209,20 @@ class Volume:
         V.vbh_load(self.h, np.ascontiguousarray(keys3, np.int32),
                    np.ascontiguousarray(tsdf, np.float32), np.ascontiguousarray(weight, np.float32))
 
+    def triangulate(self, stream: McStream | None = None, cap: int | None = None):
+        """Triangles (n, 3, 3) float32 in metres of an MC stream (default: the volume's last
+        extraction), vertices at edge midpoints."""
+        s = stream or self.stream
+        cap = cap if cap is not None else int(s.local.shape[0])
+        tris = torch.empty((max(cap, 1), 9), dtype=torch.float32, device="cuda")
+        n = torch.zeros(1, dtype=torch.int32, device="cuda")
+        V.vbh_mc_triangulate(s.c_struct(), float(self.cfg.voxel_size), tris, cap, n,
+                             torch.cuda.current_stream().cuda_stream)
+        m = int(n.item())
+        if m > cap:
+            raise RuntimeError(f"{m} triangles, capacity {cap}")
+        return tris[:m].view(-1, 3, 3)
+
     # ---- stream-out of erased blocks to the host map, explicit stream-in
     def stream_out_enable(self, ring_blocks: int = 0):
         V.vbh_stream_out_enable(self.h, ring_blocks)

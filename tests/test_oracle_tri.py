@@ -87,3 +87,16 @@ def test_sphere_mesh_topology_volume_and_orientation():
     vol = np.einsum("ij,ij->i", P[:, 0], np.cross(P[:, 1], P[:, 2])).sum() / 6.0
     assert vol > 0   # normals point to the outside (positive values)
     assert abs(vol - 4.0 / 3.0 * np.pi * r ** 3) < 0.06 * 4.0 / 3.0 * np.pi * r ** 3
+
+
+def test_library_table_equals_the_oracle_derivation():
+    """The two derivations (library host code, oracle) are written separately; the tables
+    they produce must be identical, case by case and triangle by triangle."""
+    from paper_1805_03709_b300 import build
+    build.build()
+    from paper_1805_03709_b300 import vbh as V
+    n, e = V.vbh_mc_tri_table()
+    for c in range(256):
+        t = oracle.tri_case(c)
+        assert n[c] == len(t), c
+        np.testing.assert_array_equal(e[c, :3 * n[c]].reshape(-1, 3), t)
