@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tri", action="store_true",
+                    help="skip the whole-model extraction + triangulation measurement")
     ap.add_argument("--no-sets", action="store_true",
                     help="skip the per-client stream-set comparison")
     ap.add_argument("--no-visible", action="store_true",
@@ -432,6 +434,10 @@ def main():
                                  "reads the 128 B sign/weight masks per block instead of the "
                                  "voxels (its DRAM traffic is a few % of this)"}
 
+    tri_pt = None
+    if not args.no_tri:
+        tri_pt = tri_point(torch, state["vol"], peak)
+
     hash_pt = None
     if not args.no_hash:
         hash_pt = hash_point(torch, dev, flush, peak)
@@ -471,7 +477,7 @@ def main():
             "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
             "hash": hash_pt, "diff": diff_pt, "serve": serve_pt, "stream_out": stream_pt,
-            "visible": visible_pt, "stream_sets": sets_pt,
+            "visible": visible_pt, "stream_sets": sets_pt, "model_mesh": tri_pt,
         }
         print(json.dumps(line), flush=True)
     vol.close()
@@ -546,6 +552,42 @@ def hash_point(torch, dev, flush, peak):
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+def tri_point(torch, vol, peak, reps=5):
+    """Whole-model extraction (every live block's MC indices) and its triangulation with
+    midpoint vertices -- what a (re)connecting exploration client receives and meshes -- on the
+    volume the timed loop left, CUDA events around each launch."""
+    from paper_1805_03709_b300 import vbh as V
+    from paper_1805_03709_b300.volume import McStream
+    s = McStream.allocate(MAX_BLOCKS, MAX_BLOCKS * 96)
+    sel = V.vbh_mc_selector(mode=V.VBH_MC_ALL)
+    cap = MAX_BLOCKS * 96
+    tris = torch.empty((cap, 9), dtype=torch.float32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ext, tri = [], []
+    for r in range(reps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        V.vbh_extract_mc_indices(vol.h, sel, s.c_struct())
+        e[1].record()
+        V.vbh_mc_triangulate(s.c_struct(), VOXEL, tris, cap, n,
+                             torch.cuda.current_stream().cuda_stream)
+        e[2].record()
+        torch.cuda.synchronize()
+        if r:
+            ext.append(e[0].elapsed_time(e[1]))
+            tri.append(e[1].elapsed_time(e[2]))
+    nb, ne = (int(x) for x in s.n.cpu().tolist())
+    nt = int(n.item())
+    t_ms = statistics.median(tri)
+    written = nt * 36
+    read = ne * 3 + nb * 20
+    return {"blocks": nb, "entries": ne, "triangles": nt,
+            "extract_all_ms": statistics.median(ext), "triangulate_ms": t_ms,
+            "triangles_per_s": nt / (t_ms / 1e3),
+            "triangulate_GBs": (written + read) / (t_ms / 1e3) / 1e9,
+            "triangulate_hbm_frac": (written + read) / (t_ms / 1e3) / 1e9 / peak}
 
 
 def sets_point(torch, cam, D, poses, n_clients=64, warm_frames=30, frames=60, limit=512):
