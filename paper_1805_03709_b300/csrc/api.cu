@@ -375,7 +375,7 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   const TableView t = h->table();
   const PoolView pool = h->pool();
   h->stage_begin(VBH_STAGE_HASH);
-  launch_hash_find(h->L, t, ops_dev, keys3_dev, results_dev, status_dev, n);
+  launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n);
   launch_hash_insert(h->L, t, pool, h->cnt, ops_dev, keys3_dev, nullptr, nullptr, vals_dev,
                      results_dev, status_dev, n);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, nullptr, results_dev, status_dev, n, nullptr,

@@ -1,5 +1,5 @@
 // GPU hash map of packed int3 block keys: bucketed (4 x 16 B slots per 64 B bucket), linear
-// probing over buckets, probed by groups of 4 lanes with one 16 B load per lane.
+// probing over buckets, one thread per operation reading whole buckets.
 //
 // Guarantees (Sec. 5: concurrent retrieval, insertion and removal succeed and keys stay unique,
 // which the paper obtains with per-entry locks and an excess list; here with CAS claims):
@@ -31,49 +31,59 @@ __device__ __forceinline__ bool load_key3(const int* keys3, unsigned int i,
   return true;
 }
 
-// outcome codes of group_insert
+// outcome codes of thread_insert
 constexpr int kInserted = 1, kExists = 2, kFull = 3;
 
-__device__ int group_insert(const Group& g, const TableView& t, unsigned long long key,
-                            unsigned int* pos_out, unsigned long long* observed_out) {
+__device__ int thread_insert(const TableView& t, unsigned long long key, unsigned int* pos_out,
+                             unsigned long long* observed_out) {
   unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
-  unsigned int first_free = kNone;
+  unsigned int first_free = kNone, held = kNone;
+  ulonglong2 s[4];
   // pass 1: the whole chain, to be sure the key is absent
   for (unsigned int probe = 0; probe <= t.bmask; ++probe) {
-    ulonglong2 s = load_slot_cg(&t.slots[4u * b + g.lane4]);
-    unsigned int hit = g.ballot(s.x == key);
-    if (hit) {
-      *pos_out = 4u * b + (__ffs(hit) - 1);
+    load_bucket<false>(&t.slots[4u * b], s);
+    held = b;
+    bool empty = false;
+    int hit = -1, f = -1;   // f: the bucket's first free slot
+#pragma unroll
+    for (int q = 3; q >= 0; --q) {
+      if (s[q].x == key) hit = q;
+      if (s[q].x >= kTomb) f = q;
+      empty |= s[q].x == kEmpty;
+    }
+    if (hit >= 0) {
+      *pos_out = 4u * b + hit;
       return kExists;
     }
-    if (first_free == kNone) {
-      unsigned int fr = g.ballot(s.x >= kTomb);
-      if (fr) first_free = 4u * b + (__ffs(fr) - 1);
-    }
-    if (g.ballot(s.x == kEmpty)) break;
+    if (first_free == kNone && f >= 0) first_free = 4u * b + f;
+    if (empty) break;
     b = (b + 1u) & t.bmask;
   }
   if (first_free == kNone) return kFull;
-  // pass 2: claim in probe order starting at the first free slot
+  // pass 2: claim in probe order starting at the first free slot.  The bucket pass 1 ended on
+  // is reused for the first attempt: a stale copy only costs a failed CAS and a re-read.
   b = first_free >> 2;
+  bool have = b == held;
   for (unsigned int steps = 0; steps <= t.bmask;) {
-    ulonglong2 s = load_slot_cg(&t.slots[4u * b + g.lane4]);
-    unsigned int hit = g.ballot(s.x == key);
-    if (hit) {
-      *pos_out = 4u * b + (__ffs(hit) - 1);
+    if (!have) load_bucket<false>(&t.slots[4u * b], s);
+    have = false;
+    int hit = -1, l = -1;
+#pragma unroll
+    for (int q = 3; q >= 0; --q) {
+      if (s[q].x == key) hit = q;
+      if (s[q].x >= kTomb) l = q;
+    }
+    if (hit >= 0) {
+      *pos_out = 4u * b + hit;
       return kExists;
     }
-    unsigned int fr = g.ballot(s.x >= kTomb);
-    if (!fr) {
+    if (l < 0) {
       b = (b + 1u) & t.bmask;
       ++steps;
       continue;
     }
-    unsigned int l = __ffs(fr) - 1;
-    unsigned long long old = 0ull;
-    if (g.lane4 == l) old = atomicCAS(&t.slots[4u * b + l].key, s.x, key);
-    old = g.bcast(old, l);
-    unsigned long long obs = g.bcast((unsigned long long)s.x, l);
+    const unsigned long long obs = bucket_slot(s, l).x;
+    const unsigned long long old = atomicCAS(&t.slots[4u * b + l].key, obs, key);
     if (old == obs) {
       *pos_out = 4u * b + l;
       *observed_out = obs;
@@ -89,33 +99,28 @@ __device__ int group_insert(const Group& g, const TableView& t, unsigned long lo
 }
 
 // --------------------------------------------------------------------------------- find phase
-__global__ void __launch_bounds__(kThreads) k_find(TableView t, const unsigned char* ops,
-                                                   const int* keys3, unsigned int* res,
-                                                   unsigned char* st, unsigned int n) {
-  Group g;
-  const unsigned int warps = gridDim.x * (blockDim.x / 32u);
-  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32u;
-  const unsigned int gi = (threadIdx.x & 31u) >> 2;
-  for (unsigned int base = warp * 8u; base < n; base += warps * 8u) {
-    const unsigned int i = base + gi;
-    if (i >= n) continue;   // whole group skips together
-    unsigned char op = ops[i];
-    unsigned long long key = 0;
-    bool ok = op <= kOpErase && load_key3(keys3, i, &key);
-    if (!ok) {
-      if (g.lane4 == 0) { res[i] = kNone; st[i] = kStInvalid; }
-      continue;
+__global__ void __launch_bounds__(kThreads) k_find(TableView t, DevCounters* cnt,
+                                                   const unsigned char* ops, const int* keys3,
+                                                   unsigned int* res, unsigned char* st,
+                                                   unsigned int n) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) cnt->n_exists = 0;   // the batch's insert phase follows
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    // the op byte and the key are loaded together: every op's key is validated here
+    const unsigned char op = ops[i];
+    const int x = keys3[3u * i], y = keys3[3u * i + 1], z = keys3[3u * i + 2];
+    unsigned int r = kNone;
+    unsigned char s = 0;   // inserts and erases are resolved by their own phases
+    if (op > kOpErase || !key_ok(x, y, z)) {
+      s = kStInvalid;
+    } else if (op == kOpFind) {
+      unsigned int val;
+      const bool hit = thread_find<true>(t, pack_key(x, y, z), &val) != kNone;
+      r = hit ? val : kNone;
+      s = hit ? kStFound : kStNotFound;
     }
-    if (op != kOpFind) {   // inserts / erases are resolved by their own phases
-      if (g.lane4 == 0) { res[i] = kNone; st[i] = 0; }
-      continue;
-    }
-    unsigned int val;
-    unsigned int pos = group_find_ro(g, t, key, &val);
-    if (g.lane4 == 0) {
-      res[i] = pos == kNone ? kNone : val;
-      st[i] = pos == kNone ? kStNotFound : kStFound;
-    }
+    res[i] = r;
+    st[i] = s;
   }
 }
 
@@ -134,12 +139,12 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
   __syncthreads();
   const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
   const unsigned int free_top = pool.max_blocks ? (unsigned)max(cnt->free_top, 0) : 0u;
-  Group g;
-  const unsigned int warps = gridDim.x * (blockDim.x / 32u);
-  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32u;
-  const unsigned int gi = (threadIdx.x & 31u) >> 2;
-  for (unsigned int base = warp * 8u; base < n; base += warps * 8u) {
-    const unsigned int i = base + gi;
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int stride = gridDim.x * blockDim.x;
+  // whole warps iterate together (warp-aggregated pool pops and counters)
+  for (unsigned int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n;
+       base += stride) {
+    const unsigned int i = base + lane;
     unsigned long long key = 0;
     bool doit = false;
     if (i < n) {
@@ -153,10 +158,8 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
     int outcome = 0;
     unsigned int pos = kNone;
     unsigned long long observed = 0;
-    if (doit) outcome = group_insert(g, t, key, &pos, &observed);
-    __syncwarp();
-    const bool leader = doit && g.lane4 == 0;
-    const bool won = leader && outcome == kInserted;
+    if (doit) outcome = thread_insert(t, key, &pos, &observed);
+    const bool won = outcome == kInserted;
     if (pool.max_blocks) {
       unsigned int k = warp_append(&cnt->n_popped, won, 0xFFFFFFFFu);
       if (won) {
@@ -173,13 +176,20 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
         }
       }
     } else if (won) {
-      t.slots[pos].val = vals ? vals[i] : 0u;
+      const unsigned int v = vals ? vals[i] : 0u;
+      t.slots[pos].val = v;
+      pos = v;   // a plain map's winner knows its value: the result is final
     }
-    if (won) {
-      atomicAdd(&s_live, 1u);
-      atomicAdd(observed == kEmpty ? &s_from_empty : &s_from_tomb, 1u);
+    const unsigned int n_won = __popc(__ballot_sync(0xFFFFFFFFu, won));
+    const unsigned int n_empty = __popc(__ballot_sync(0xFFFFFFFFu, won && observed == kEmpty));
+    const unsigned int n_ex = __popc(__ballot_sync(0xFFFFFFFFu, outcome == kExists));
+    if (lane == 0 && n_won) {
+      atomicAdd(&s_live, n_won);
+      if (n_empty) atomicAdd(&s_from_empty, n_empty);
+      if (n_won > n_empty) atomicAdd(&s_from_tomb, n_won - n_empty);
     }
-    if (leader) {
+    if (lane == 0 && n_ex && !pool.max_blocks) atomicAdd(&cnt->n_exists, n_ex);
+    if (doit) {
       res[i] = pos;
       st[i] = outcome == kInserted ? kStInserted : outcome == kExists ? kStExists : kStCapacity;
       if (outcome == kFull) atomicOr(&s_err, kErrTable);
@@ -206,6 +216,10 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
                                                             float2* tdepth,
                                                             unsigned int* n_touched,
                                                             const FrameCtl* ctl) {
+  // A plain map's winners wrote their final results; only inserts that met their key (whose
+  // value another thread may still have been writing) are left, and usually there are none.
+  const bool plain = pool.max_blocks == 0;
+  if (plain && !touched && *reinterpret_cast<volatile unsigned int*>(&cnt->n_exists) == 0) return;
   __shared__ unsigned int s_undo, s_new, s_err;
   if (threadIdx.x == 0) { s_undo = 0; s_new = 0; s_err = 0; }
   __syncthreads();
@@ -224,10 +238,10 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
     bool fresh_win = false;
     if (i < n) {
       unsigned char s = st[i];
-      if (s == kStInserted || s == kStExists) {
+      if (s == kStExists || (s == kStInserted && !plain)) {
         unsigned int pos = res[i];
         unsigned int v = t.slots[pos].val;
-        if (v == kPoolFail) {
+        if (!plain && v == kPoolFail) {
           if (s == kStInserted) {
             t.slots[pos].key = kTomb;
             atomicAdd(&s_undo, 1u);
@@ -280,27 +294,20 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
   __shared__ unsigned int s_erased;
   if (threadIdx.x == 0) s_erased = 0;
   __syncthreads();
-  Group g;
-  const unsigned int warps = gridDim.x * (blockDim.x / 32u);
-  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32u;
-  const unsigned int gi = (threadIdx.x & 31u) >> 2;
-  for (unsigned int base = warp * 8u; base < n; base += warps * 8u) {
-    const unsigned int i = base + gi;
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n;
+       base += stride) {
+    const unsigned int i = base + lane;
     unsigned long long key = 0;
-    bool doit = i < n && ops[i] == kOpErase && load_key3(keys3, i, &key);
+    const bool doit = i < n && ops[i] == kOpErase && load_key3(keys3, i, &key);
     bool erased = false;
     unsigned int val = kNone;
     if (doit) {
-      unsigned int pos = group_find_ro(g, t, key, &val);
-      if (pos != kNone) {
-        unsigned long long old = 0ull;
-        if (g.lane4 == (pos & 3u)) old = atomicCAS(&t.slots[pos].key, key, kTomb);
-        erased = g.bcast(old, pos & 3u) == key;
-      }
+      const unsigned int pos = thread_find(t, key, &val);
+      if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;
     }
-    __syncwarp();
-    const bool leader = doit && g.lane4 == 0;
-    const bool push = leader && erased && pool.max_blocks;
+    const bool push = erased && pool.max_blocks;
     unsigned int k = warp_append(reinterpret_cast<unsigned int*>(&cnt->free_top), push,
                                  0xFFFFFFFFu);
     if (push) {
@@ -309,11 +316,12 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
       pool.state[val] = 0u;
       pool.seq[val] = 0u;
     }
-    if (leader) {
+    if (doit) {
       res[i] = erased ? val : kNone;
       st[i] = erased ? kStErased : kStNotFound;
-      if (erased) atomicAdd(&s_erased, 1u);
     }
+    const unsigned int n_er = __popc(__ballot_sync(0xFFFFFFFFu, erased));
+    if (lane == 0 && n_er) atomicAdd(&s_erased, n_er);
   }
   __syncthreads();
   if (threadIdx.x == 0 && s_erased) {
@@ -431,10 +439,10 @@ __global__ void k_pack_keys(const int* keys3, unsigned int n, unsigned long long
   static int grid_##kernel = 0;                                    \
   if (!grid_##kernel) grid_##kernel = persistent_grid(kernel, threads, L.sms)
 
-void launch_hash_find(const Launch& L, TableView t, const unsigned char* ops, const int* keys3,
-                      unsigned int* res, unsigned char* st, unsigned int n) {
+void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsigned char* ops,
+                      const int* keys3, unsigned int* res, unsigned char* st, unsigned int n) {
   VBH_GRID(k_find, kThreads);
-  k_find<<<grid_k_find, kThreads, 0, L.stream>>>(t, ops, keys3, res, st, n);
+  k_find<<<grid_k_find, kThreads, 0, L.stream>>>(t, cnt, ops, keys3, res, st, n);
 }
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                         const unsigned char* ops, const int* keys3,

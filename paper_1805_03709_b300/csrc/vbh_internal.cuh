@@ -56,6 +56,7 @@ struct __align__(16) Slot {
 struct DevCounters {
   int free_top;                 // valid entries of the free stack
   unsigned int n_popped;        // pops in the current insert launch
+  unsigned int n_exists;        // plain-map batch: inserts that met their key (value pending)
   unsigned int n_live, n_tomb, n_empty;
   unsigned int n_cand, n_touched, n_new;
   unsigned int n_mset, n_tombrec, n_removed;
@@ -172,65 +173,46 @@ __host__ __device__ __forceinline__ unsigned int home_bucket(unsigned long long 
 }
 
 #ifdef __CUDACC__
-// ------------------------------------------------------------------------- 4-lane group probe
-// A group is 4 consecutive lanes of a warp; each lane owns one slot of the probed bucket.
-struct Group {
-  unsigned int lane4;   // 0..3
-  unsigned int base;    // first lane of the group in the warp
-  unsigned int mask;    // the group's lanes
-  __device__ __forceinline__ Group() {
-    unsigned int lane = threadIdx.x & 31u;
-    lane4 = lane & 3u;
-    base = lane & ~3u;
-    mask = 0xFu << base;
+// ------------------------------------------------------------------------ thread-per-op probe
+// One thread reads a whole bucket (four 16 B loads from one 64 B line), so a warp keeps 32
+// independent bucket reads in flight.  kReadOnly selects the non-coherent path for launches
+// that do not modify the table; otherwise the loads go to L2, where the table's atomics land.
+template <bool kReadOnly>
+__device__ __forceinline__ void load_bucket(const Slot* b, ulonglong2 (&s)[4]) {
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(b);
+  if constexpr (kReadOnly) {
+    s[0] = __ldg(p); s[1] = __ldg(p + 1); s[2] = __ldg(p + 2); s[3] = __ldg(p + 3);
+  } else {
+    s[0] = __ldcg(p); s[1] = __ldcg(p + 1); s[2] = __ldcg(p + 2); s[3] = __ldcg(p + 3);
   }
-  __device__ __forceinline__ unsigned int ballot(bool p) const {
-    return (__ballot_sync(mask, p) >> base) & 0xFu;
-  }
-  template <class T>
-  __device__ __forceinline__ T bcast(T v, unsigned int src) const {
-    return __shfl_sync(mask, v, (int)(base + src));
-  }
-};
-
-__device__ __forceinline__ ulonglong2 load_slot_ro(const Slot* s) {
-  return __ldg(reinterpret_cast<const ulonglong2*>(s));
-}
-__device__ __forceinline__ ulonglong2 load_slot_cg(const Slot* s) {
-  return __ldcg(reinterpret_cast<const ulonglong2*>(s));
 }
 
-// Read-only find by a group (table not modified during the launch).  Returns the slot index
-// or kNone; *val receives the value.
-__device__ __forceinline__ unsigned int group_find_ro(const Group& g, const TableView& t,
-                                                      unsigned long long key, unsigned int* val) {
-  unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
-  for (unsigned int probe = 0; probe <= t.bmask; ++probe, b = (b + 1u) & t.bmask) {
-    ulonglong2 s = load_slot_ro(&t.slots[4u * b + g.lane4]);
-    unsigned int hit = g.ballot(s.x == key);
-    if (hit) {
-      unsigned int l = __ffs(hit) - 1;
-      *val = g.bcast((unsigned int)s.y, l);
-      return 4u * b + l;
-    }
-    if (g.ballot(s.x == kEmpty)) break;
-  }
-  *val = kNone;
-  return kNone;
+// Slot q of a loaded bucket by a select chain (keeps the bucket in registers).
+__device__ __forceinline__ ulonglong2 bucket_slot(const ulonglong2 (&s)[4], int q) {
+  return q == 0 ? s[0] : q == 1 ? s[1] : q == 2 ? s[2] : s[3];
 }
 
-// Single-thread find (4 x 16 B loads per bucket), for lookups scattered over a launch.
+// Find by one thread: walk the buckets from the key's home bucket until the key or a bucket
+// with an EMPTY slot.  Returns the slot index or kNone; *val receives the value.
+template <bool kReadOnly = false>
 __device__ __forceinline__ unsigned int thread_find(const TableView& t, unsigned long long key,
                                                     unsigned int* val) {
   unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
   for (unsigned int probe = 0; probe <= t.bmask; ++probe, b = (b + 1u) & t.bmask) {
-    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(&t.slots[4u * b]);
-    ulonglong2 s0 = __ldcg(p), s1 = __ldcg(p + 1), s2 = __ldcg(p + 2), s3 = __ldcg(p + 3);
-    if (s0.x == key) { *val = (unsigned)s0.y; return 4u * b; }
-    if (s1.x == key) { *val = (unsigned)s1.y; return 4u * b + 1; }
-    if (s2.x == key) { *val = (unsigned)s2.y; return 4u * b + 2; }
-    if (s3.x == key) { *val = (unsigned)s3.y; return 4u * b + 3; }
-    if (s0.x == kEmpty || s1.x == kEmpty || s2.x == kEmpty || s3.x == kEmpty) break;
+    ulonglong2 s[4];
+    load_bucket<kReadOnly>(&t.slots[4u * b], s);
+    int hit = -1;
+    bool empty = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (s[q].x == key) hit = q;
+      empty |= s[q].x == kEmpty;
+    }
+    if (hit >= 0) {
+      *val = (unsigned)bucket_slot(s, hit).y;
+      return 4u * b + hit;
+    }
+    if (empty) break;
   }
   *val = kNone;
   return kNone;
@@ -371,7 +353,8 @@ struct Launch {
 };
 
 // hash.cu
-void launch_hash_find(const Launch& L, TableView t, const unsigned char* ops, const int* keys3,
+void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsigned char* ops,
+                      const int* keys3,
                       unsigned int* res, unsigned char* st, unsigned int n);
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                         const unsigned char* ops, const int* keys3,

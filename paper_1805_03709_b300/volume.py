@@ -42,6 +42,9 @@ class HashMap:
     def batch(self, ops: torch.Tensor, keys3: torch.Tensor, vals: torch.Tensor | None = None,
               results: torch.Tensor | None = None, status: torch.Tensor | None = None):
         n = int(ops.shape[0])
+        if keys3.shape != (n, 3) or (vals is not None and vals.shape[0] < n):
+            raise ValueError(f"batch of {n} ops needs keys3 [{n}, 3] (got {tuple(keys3.shape)})"
+                             " and at least as many values")
         if results is None:
             results = torch.empty(n, dtype=torch.int32, device=ops.device)
         if status is None:

@@ -102,6 +102,21 @@ def test_zipf_clustered_keys_heavy_duplication():
     check_contents(hm, om)
 
 
+def test_values_at_the_top_of_the_range():
+    """A plain map stores any uint32 value, the library's internal markers included; the
+    duplicate inserts of a batch report the winner's value."""
+    hm = HashMap(n_buckets=64)
+    keys = np.array([[1, 2, 3], [4, 5, 6], [1, 2, 3], [7, 8, 9], [4, 5, 6]], np.int32)
+    vals = np.array([0xFFFFFFFE, 0xFFFFFFFF, 0xFFFFFFFE, 0x80000000, 0xFFFFFFFF], np.uint32)
+    rg, sg = gpu_batch(hm, np.ones(5, np.uint8), keys, vals)
+    assert sorted(sg.tolist()) == [V.VBH_ST_INSERTED] * 3 + [V.VBH_ST_EXISTS] * 2
+    np.testing.assert_array_equal(rg, vals)
+    rg, sg = gpu_batch(hm, np.zeros(5, np.uint8), keys, None)
+    assert np.all(sg == V.VBH_ST_FOUND)
+    np.testing.assert_array_equal(rg, vals)
+    assert hm.counters().live == 3 and hm.counters().error_flags == 0
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 8, 9, 31, 33, 255, 257])
 def test_ragged_sizes_and_invalid(n):
     rng = np.random.default_rng(n)
@@ -140,8 +155,14 @@ def test_full_table_reports_capacity_and_recovers():
     gpu_batch(hm, np.full(2, V.VBH_OP_ERASE, np.uint8), ins[:2], None)
     rg, sg = gpu_batch(hm, np.full(2, V.VBH_OP_INSERT, np.uint8), lost[:2], key_value(lost[:2]))
     assert np.all(sg == V.VBH_ST_INSERTED)
-    rg, sg = gpu_batch(hm, np.zeros(18, np.uint8), np.concatenate([ins[2:], lost[:2]]), None)
-    assert np.all(sg == V.VBH_ST_FOUND)
+    back = np.concatenate([ins[2:], lost[:2]])
+    rg, sg = gpu_batch(hm, np.zeros(len(back), np.uint8), back, None)
+    assert len(back) == 16 and np.all(sg == V.VBH_ST_FOUND)
+    np.testing.assert_array_equal(rg, key_value(back))
+    # more ops than keys is refused before any launch (the kernels read one key per op)
+    with pytest.raises(ValueError):
+        hm.batch(torch.zeros(18, dtype=torch.uint8, device="cuda"),
+                 torch.from_numpy(np.ascontiguousarray(back)).cuda())
 
 
 @pytest.mark.parametrize("lf", [0.5, 0.7, 0.9])
