@@ -59,6 +59,11 @@ __global__ void k_setup(FrameCtl c, FrameCtl* dst, DevCounters* cnt) {
 }
 
 constexpr unsigned int kRing = 64;
+// With stream-out on, the host must drain the device ring of removed blocks, and it sees the
+// ring's head only for frames that have run: it therefore lets at most this many frames wait
+// on the GPU, so that its view of the head is never more than these frames old (the ring keeps
+// a quarter of its capacity free for them).
+constexpr unsigned int kStreamOutAhead = 3;
 
 // Root node of the frame graph: fetch the next control block from the host ring (uncached
 // reads of mapped host memory), store it, zero the per-frame counters, acknowledge the slot.
@@ -134,6 +139,23 @@ FrameParams frame_params(const vbh_handle* h, const float* T) {
   fp.wmax = c.max_weight;
   fp.ds = c.depth_scale;
   fp.zmax = c.zmax;
+  // The validity test of a raw depth r (nonzero, and fl(r ds) <= zmax when zmax > 0) as one
+  // range: fl(r ds) never decreases with r (ds > 0), so the valid values are 1..raw_max.
+  fp.raw_max = 65535u;
+  if (c.zmax > 0.f) {
+    auto within = [&](unsigned int r) {
+      volatile float d = (float)r * c.depth_scale;   // binary32 product, as on the device
+      return d <= c.zmax;
+    };
+    if (!within(65535u)) {
+      unsigned int lo = 0, hi = 65535u;   // within(lo), !within(hi)
+      while (hi - lo > 1u) {
+        const unsigned int mid = (lo + hi) / 2u;
+        (within(mid) ? lo : hi) = mid;
+      }
+      fp.raw_max = lo;
+    }
+  }
   fp.fx = c.fx;
   fp.fy = c.fy;
   fp.cx = c.cx;
@@ -579,10 +601,12 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
   c.serve_mark = h->slog != nullptr;
   c.visible = h->integ_mode == VBH_INTEGRATE_VISIBLE;
   set_stream_out(c, out);
-  // wait (bounded) until the graph launched kRing frames ago has consumed this slot
+  // wait (bounded) until the graph launched `ahead` frames ago has consumed its slot: the
+  // slot this frame overwrites, and with stream-out on, a bound on the frames queued ahead
   const unsigned long long seq = h->host_seq;
-  if (seq >= kRing) {
-    const unsigned long long need = seq - kRing + 1;
+  const unsigned long long ahead = h->so ? kStreamOutAhead : kRing;
+  if (seq >= ahead) {
+    const unsigned long long need = seq - ahead + 1;
     int spins = 0;
     while (*h->consumed_host < need) {
       if (++spins > 2000000) return fail(VBH_ERR_TIMEOUT, "frame ring slot not consumed");

@@ -26,7 +26,7 @@ namespace {
 constexpr int kTile = 16;            // 16 x 16 pixel tiles, one thread per pixel
 constexpr int kTileThreads = kTile * kTile;
 constexpr int kTileSet = 1024;       // shared-memory key set per tile (power of two)
-constexpr int kIntThreads = 128;     // fusion: 4 voxels per thread, one block per CTA step
+constexpr int kIntThreads = 128;     // fusion: 4 warps per CTA, one work unit per warp at a time
 
 // Copy the per-call frame parameters into shared memory (one word per thread).
 __device__ __forceinline__ void load_frame_params(FrameParams& dst, const FrameCtl* ctl) {
@@ -178,6 +178,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return done != 0;
 }
+// Approximate reciprocal (the hardware's rcp.approx, ~1 ulp) for the value path only.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Bounded wait: false (and the sticky timeout flag) if the copy has not landed in time.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity,
                                           DevCounters* cnt) {
@@ -188,51 +195,58 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int 
 }
 
 // Projective TSDF fusion of every voxel of every touched block; also rewrites the block's
-// sign / weight bit masks.  One warp owns one block at a time (no barriers between warps):
-// its 4 KiB of (TSDF, weight) arrive in shared memory by one bulk asynchronous copy, double
-// buffered so the next block streams in while this one is fused.  Lane L fuses voxels
-// L + 32 m (m = 0..15): shared-memory reads are conflict-free, global writes cover 256
-// contiguous bytes, and the ballot over voxel set m is mask word m.  The touched list carries
-// the pool index with the block's "fresh" bit, its key and its origin's camera depth.
+// sign / weight bit masks.  A warp owns one work unit at a time -- kSlices of the block's 16
+// voxel sets (a half block by default, so that the last round of units leaves fewer warps
+// idle) -- with no barriers between warps: the unit's (TSDF, weight) pairs arrive in shared
+// memory by one bulk asynchronous copy, started when the warp's previous unit is done with the
+// buffer and waited for only after the projections and the first depth fetches of the unit.
+// Lane L fuses voxels L + 32 m: shared-memory reads are conflict-free, global writes cover 256
+// contiguous bytes, and the ballot over voxel set m is mask word m (collected in shared memory,
+// stored by the lanes that own the words).  The touched list carries the pool index with the
+// block's "fresh" bit, its key and its origin's camera depth.
 #ifndef VBH_FUSE_GROUP
 #define VBH_FUSE_GROUP 4
 #endif
 #ifndef VBH_FUSE_MIN_CTAS
 #define VBH_FUSE_MIN_CTAS 1
 #endif
-#ifndef VBH_FUSE_BUFS
-#define VBH_FUSE_BUFS 1
+#ifndef VBH_FUSE_SLICES
+#define VBH_FUSE_SLICES 8
 #endif
 constexpr int kWarps = kIntThreads / 32;
-constexpr int kGroup = VBH_FUSE_GROUP;   // voxels per lane whose depth fetches overlap
-constexpr unsigned int kBufs = VBH_FUSE_BUFS;   // voxel buffers per warp (1: more warps per SM)
+constexpr int kGroup = VBH_FUSE_GROUP;     // voxels per lane whose depth fetches overlap
+constexpr int kSlices = VBH_FUSE_SLICES;   // voxel sets (32 voxels each) per work unit
+constexpr unsigned int kUnits = 16u / kSlices;   // work units per block
+constexpr unsigned int kUnitVox = 32u * kSlices;
+static_assert(kSlices % kGroup == 0 && 16 % kSlices == 0, "unit / group sizes");
 
 // The frame parameters arrive by value (the frame graph patches this node's argument every
 // frame), so the compiler takes them as constant-bank operands instead of holding ~25 of them
-// in registers; with one 4 KiB buffer per warp that lets 2 x more warps reside per SM to hide
-// the depth-gather latency.
+// in registers, which leaves room for more resident warps to hide the depth-gather latency.
 __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
     k_integrate(const FrameParams fp, PoolView pool, const unsigned int* touched,
                 const unsigned long long* tkey, const float2* tdepth,
                 const unsigned int* n_touched, DevCounters* cnt) {
-  __shared__ __align__(128) float2 sbuf[kWarps][kBufs][512];
-  __shared__ __align__(8) unsigned long long sbar[kWarps][kBufs];
+  __shared__ __align__(128) float2 sbuf[kWarps][kUnitVox];
+  __shared__ __align__(8) unsigned long long sbar[kWarps];
+  __shared__ unsigned int smask[kWarps][32];
   __shared__ unsigned int s_upd;
   if (threadIdx.x == 0) s_upd = 0;
   const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    for (unsigned int q = 0; q < kBufs; ++q) mbar_init(&sbar[warp][q]);
+    mbar_init(&sbar[warp]);
     mbar_fence_init();
   }
   __syncthreads();
-  const unsigned int n = *n_touched;
+  const unsigned int n_units = *n_touched * kUnits;
   const int lx = lane & 7, ly0 = lane >> 3;      // voxel (lx, ly0 + 4 (m & 1), m >> 1)
   const float R0 = fp.R[0], R1 = fp.R[1], R2 = fp.R[2], R3 = fp.R[3], R4 = fp.R[4],
               R5 = fp.R[5], R6 = fp.R[6], R7 = fp.R[7], R8 = fp.R[8];
   const float s = fp.s, t0 = fp.t[0], t1 = fp.t[1], t2 = fp.t[2];
-  const float fx = fp.fx, fy = fp.fy, cxh = fp.cxh, cyh = fp.cyh, fw = fp.fw, fh = fp.fh;
-  const float ds = fp.ds, zmax = fp.zmax, mu = fp.mu, inv_mu = fp.inv_mu, wmax = fp.wmax;
-  const int width = fp.width;
+  const float fx = fp.fx, fy = fp.fy, cxh = fp.cxh, cyh = fp.cyh;
+  const float ds = fp.ds, mu = fp.mu, inv_mu = fp.inv_mu, wmax = fp.wmax;
+  const unsigned int raw_max = fp.raw_max;
+  const int width = fp.width, height = fp.height;
   const unsigned short* __restrict__ depth = fp.depth;
   // per-voxel part of the camera depth: tau(h, lz) = s (R_02 lx + R_12 ly + R_22 lz)
   //                                              = base[h] + lz * s R_22   (value path only)
@@ -241,42 +255,34 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
 #pragma unroll
   for (int h = 0; h < 2; ++h) tbase[h] = s * fmaf(R5, (float)(ly0 + 4 * h), R2 * (float)lx);
   unsigned int my_upd = 0;
-  unsigned int parity = 0u;   // bit q: phase to wait for on buffer q
+  unsigned int parity = 0u;
   const unsigned int stride = gridDim.x * kWarps;
-  unsigned int b = blockIdx.x * kWarps + warp;
+  unsigned int u = blockIdx.x * kWarps + warp;
   unsigned int rec = 0;
-  if (b < n) {
-    rec = touched[b];
+  if (u < n_units) {
+    rec = touched[u / kUnits];
     if (lane == 0 && !(rec & kTouchedFresh))
-      bulk_load(sbuf[warp][0], pool.vox + 512ull * (rec & ~kTouchedFresh), 4096u,
-                &sbar[warp][0]);
+      bulk_load(sbuf[warp], pool.vox + 512ull * (rec & ~kTouchedFresh) + kUnitVox * (u % kUnits),
+                kUnitVox * 8u, &sbar[warp]);
   }
   bool alive = true;
-  for (unsigned int it = 0; b < n && alive; ++it, b += stride) {
-    const unsigned int cur = kBufs == 2u ? (it & 1u) : 0u;
-    // two buffers: start the next block's copy into the other one (read completely last
-    // iteration); one buffer: it is started after this block's reads, below
-    const unsigned int bn = b + stride;
-    unsigned int rec_next = 0;
-    if (bn < n) {
-      rec_next = touched[bn];
-      if (kBufs == 2u && lane == 0 && !(rec_next & kTouchedFresh))
-        bulk_load(sbuf[warp][cur ^ 1u], pool.vox + 512ull * (rec_next & ~kTouchedFresh), 4096u,
-                  &sbar[warp][cur ^ 1u]);
-    }
+  for (; u < n_units && alive; u += stride) {
+    const unsigned int un = u + stride;
+    const unsigned int rec_next = un < n_units ? touched[un / kUnits] : 0u;
+    const unsigned int b = u / kUnits, part = u % kUnits;
     const unsigned int p = rec & ~kTouchedFresh;
     const bool fresh = (rec & kTouchedFresh) != 0;
     const int3 k = unpack_key(tkey[b]);
     const float2 bd = tdepth[b];
-    if (!fresh) {
-      if (!mbar_wait(&sbar[warp][cur], (parity >> cur) & 1u, cnt)) {
-        alive = false;   // a copy that never landed: stop this warp (flag already raised)
-        break;
-      }
-      parity ^= 1u << cur;
+    const float2* vin = sbuf[warp];
+    float2* vout = pool.vox + 512ull * p + kUnitVox * part;
+    if (fresh) {   // a new block starts from zero: no copy was started for this unit
+      float4* z = reinterpret_cast<float4*>(sbuf[warp]);
+#pragma unroll
+      for (unsigned int q = lane; q < kUnitVox / 2u; q += 32u) z[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
     }
-    const float2* vin = sbuf[warp][cur];
-    float2* vout = pool.vox + 512ull * p;
+    const int z0 = 8 * k.z + (kSlices / 2) * (int)part;   // voxel z of the unit's first set
     const float dX = __fmaf_rn((float)(8 * k.x + lx), s, -t0);
     float ix[2], iy[2], iz[2];   // R_0j dX + R_1j dY for the rows ly0 and ly0 + 4
 #pragma unroll
@@ -287,63 +293,82 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
       iz[h] = __fmaf_rn(R5, dY, __fmul_rn(R2, dX));
     }
     // low-order part of the block depth folded into the per-voxel offsets (value path)
-    const float tb0 = tbase[0] + bd.y, tb1 = tbase[1] + bd.y;
-    unsigned int mword = 0u;   // lane q < 16: sign mask word q; lane 16 + q: weight word q
+    const float lz0 = (float)((kSlices / 2) * (int)part);
+    const float tb0 = fmaf(lz0, sR22, tbase[0] + bd.y), tb1 = fmaf(lz0, sR22, tbase[1] + bd.y);
 #pragma unroll
-    for (int g = 0; g < 16; g += kGroup) {
+    for (int g = 0; g < kSlices; g += kGroup) {
       bool ok[kGroup];
       float dm[kGroup];
 #pragma unroll
       for (int i = 0; i < kGroup; ++i) {
-        const int m = g + i, h = m & 1, lz = m >> 1;
-        const float dZ = __fmaf_rn((float)(8 * k.z + lz), s, -t2);
+        const int j = g + i, h = j & 1;
+        const float dZ = __fmaf_rn((float)(z0 + (j >> 1)), s, -t2);
         const float px = __fmaf_rn(R6, dZ, ix[h]);
         const float py = __fmaf_rn(R7, dZ, iy[h]);
         const float pz = __fmaf_rn(R8, dZ, iz[h]);
         const float r = __frcp_rn(pz);
-        const float uf = floorf(__fmaf_rn(__fmul_rn(fx, px), r, cxh));
-        const float vf = floorf(__fmaf_rn(__fmul_rn(fy, py), r, cyh));
-        const bool in = pz > 0.0f && uf >= 0.0f && uf < fw && vf >= 0.0f && vf < fh;
-        const int idx = in ? (int)vf * width + (int)uf : 0;
+        const float au = __fmaf_rn(__fmul_rn(fx, px), r, cxh);
+        const float av = __fmaf_rn(__fmul_rn(fy, py), r, cyh);
+        // pixel = (floor au, floor av) inside the image: a conversion rounding down saturates
+        // out-of-range values, so 0 <= floor(au) < width is an unsigned compare of it; NaN
+        // (which that conversion would map to 0) is excluded explicitly
+        const int iu = __float2int_rd(au), iv = __float2int_rd(av);
+        const bool in = pz > 0.0f && au == au && av == av && (unsigned int)iu < (unsigned int)width &&
+                        (unsigned int)iv < (unsigned int)height;
+        const int idx = in ? iv * width + iu : 0;
         const unsigned short raw = __ldg(depth + idx);
         const float d = __fmul_rn((float)raw, ds);
-        ok[i] = in && raw != 0 && !(zmax > 0.0f && d > zmax) && !(__fsub_rn(d, pz) < -mu);
+        ok[i] = in && (unsigned int)raw - 1u < raw_max && !(__fsub_rn(d, pz) < -mu);
         dm[i] = d;
+      }
+      if (g == 0 && !fresh) {
+        // the unit's voxels are needed from here on: their copy has been in flight during
+        // the projections and the first group's depth fetches
+        alive = __all_sync(0xFFFFFFFFu, mbar_wait(&sbar[warp], parity, cnt));
+        if (!alive) break;   // a copy that never landed (flag raised): stop this warp
+        parity ^= 1u;
       }
 #pragma unroll
       for (int i = 0; i < kGroup; ++i) {
-        const int m = g + i, h = m & 1, lz = m >> 1;
-        float2 v = fresh ? make_float2(0.f, 0.f) : vin[lane + 32 * m];
+        const int j = g + i, h = j & 1;
+        float2 v = vin[lane + 32 * j];
         if (ok[i]) {
-          const float tau = fmaf((float)lz, sR22, h ? tb1 : tb0);
+          const float tau = fmaf((float)(j >> 1), sR22, h ? tb1 : tb0);
           const float sdf = (dm[i] - bd.x) - tau;
           const float f = fminf(1.0f, fmaxf(-1.0f, sdf * inv_mu));
-          v.x = v.x + __fdividef(f - v.x, v.y + 1.0f);
-          v.y = fminf(v.y + 1.0f, wmax);
+          const float w1 = v.y + 1.0f;
+          v.x = fmaf(f - v.x, rcp_approx(w1), v.x);   // running weighted mean, weight 1 per frame
+          v.y = fminf(w1, wmax);
         }
         const bool wr = ok[i] || fresh;
-        if (wr) vout[lane + 32 * m] = v;
+        if (wr) vout[lane + 32 * j] = v;
         const unsigned int negm = __ballot_sync(0xFFFFFFFFu, v.x < 0.0f);
         const unsigned int valm = __ballot_sync(0xFFFFFFFFu, v.y > 0.0f);
-        if (lane == (unsigned)m) mword = negm;
-        if (lane == 16u + m) mword = valm;
+        if (lane == 0) {
+          smask[warp][j] = negm;
+          smask[warp][16 + j] = valm;
+        }
         my_upd += wr ? 1u : 0u;
       }
     }
-    pool.masks[32u * p + lane] = mword;   // one coalesced 128 B store per block
-    if (lane == 0 && fresh) pool.state[p] = 0u;
-    __syncwarp();   // every lane is done with buffer `cur` before it is refilled
-    if (kBufs == 1u && bn < n && lane == 0 && !(rec_next & kTouchedFresh))
-      bulk_load(sbuf[warp][0], pool.vox + 512ull * (rec_next & ~kTouchedFresh), 4096u,
-                &sbar[warp][0]);
+    if (!alive) break;
+    __syncwarp();   // the mask words are in shared memory; every lane is done with the buffer
+    if (un < n_units && lane == 0 && !(rec_next & kTouchedFresh))
+      bulk_load(sbuf[warp],
+                pool.vox + 512ull * (rec_next & ~kTouchedFresh) + kUnitVox * (un % kUnits),
+                kUnitVox * 8u, &sbar[warp]);
+    // sign words kSlices part .. + kSlices - 1, weight words 16 + the same
+    const unsigned int q = lane & 15u;
+    if (q < (unsigned)kSlices)
+      pool.masks[32u * p + (lane & 16u) + kSlices * part + q] = smask[warp][(lane & 16u) + q];
+    if (lane == 0 && fresh && part == kUnits - 1u) pool.state[p] = 0u;
+    __syncwarp();   // mask words read before the next unit overwrites them
     rec = rec_next;
   }
   if (!alive) {
-    // wait (bounded) for this warp's copies still in flight before the CTA may exit
-    for (unsigned int q = 0; q < kBufs; ++q)
-      for (unsigned int i = 0; i < (1u << 20) && !mbar_try_wait(&sbar[warp][q], (parity >> q) & 1u);
-           ++i) {
-      }
+    // wait (bounded) for this warp's copy still in flight before the CTA may exit
+    for (unsigned int i = 0; i < (1u << 20) && !mbar_try_wait(&sbar[warp], parity); ++i) {
+    }
   }
   atomicAdd(&s_upd, my_upd);
   __syncthreads();
@@ -352,7 +377,7 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
     atomicAdd(&cnt->tot_written, (unsigned long long)s_upd);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    atomicAdd(&cnt->tot_touched, (unsigned long long)n);
+    atomicAdd(&cnt->tot_touched, (unsigned long long)*n_touched);
     atomicAdd(&cnt->tot_frames, 1ull);
   }
 }

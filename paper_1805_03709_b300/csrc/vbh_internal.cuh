@@ -265,6 +265,7 @@ struct FrameParams {
   float fw, fh;        // (float)width, (float)height
   int width, height;
   int J;               // band steps: samples j = 0..J
+  unsigned int raw_max;   // raw depth r is valid iff 1 <= r <= raw_max (fl(r ds) <= zmax)
   const unsigned short* depth;
 };
 

@@ -98,6 +98,33 @@ def test_stream_in_moves_host_blocks_back(room):
     compare_maps(vol.host_map(), orc.host_dump())
 
 
+def test_back_to_back_frames_do_not_outrun_the_ring(room):
+    """Frames submitted with no synchronisation, through a ring of 32 frames' worth of removals:
+    the host keeps only a few frames queued while it drains the ring, so nothing is lost and
+    the host map equals that of a run with a ring larger than all removals."""
+    cam, poses, depth = room
+    order = [i % len(poses) for i in range(60)]
+    D = [torch.from_numpy(depth[i]).cuda() for i in range(len(poses))]
+    maps, per_frame = [], []
+    for ring in (0, None):
+        vol, _ = make_pair(cam, 0.005, 0.02, 1 << 16, 1 << 17, 4.0)
+        if ring is None:
+            ring = 32 * max(per_frame)
+        vol.stream_out_enable(ring_blocks=ring)
+        for k, i in enumerate(order):
+            vol.process_frame(D[i], poses[i], k + 1, 1.0)
+            if not maps:
+                torch.cuda.synchronize()
+                per_frame.append(vol.counters().last_erased)
+        vol.stream_out_flush()
+        streamed, lost, held = vol.stream_out_stats()
+        assert lost == 0 and vol.counters().error_flags == 0
+        maps.append(vol.host_map())
+        vol.close()
+    assert sum(per_frame) > 32 * max(per_frame) > 0   # the small ring wraps several times
+    compare_maps(maps[1], maps[0])
+
+
 def test_small_ring_counts_and_flags_lost_blocks():
     cam = synth.Camera(8, 8, 4.0, 4.0, 4.0, 4.0)
     vol, orc = make_pair(cam, 0.01, 0.04, 1 << 12, 1 << 10, 0.0)
