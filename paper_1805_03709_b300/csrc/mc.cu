@@ -164,23 +164,31 @@ __device__ __forceinline__ unsigned long long zero_bytes(unsigned long long v) {
   return ~(y | v | kLo7);
 }
 
-// 9-bit lattice row (x = 0..8) of mask `kind` (0 sign, 1 weight) at lattice (Y, Z), Y, Z in
-// 0..8, from the masks of the block and its positive neighbours held in m[8][32] (neighbour
-// n = ox + 2 oy + 4 oz).
-__device__ __forceinline__ unsigned int row9(const unsigned int (*m)[32], int kind, int Y, int Z) {
-  const int nb = 2 * (Y >> 3) + 4 * (Z >> 3);
+// The lattice of a block and its 7 positive neighbours (n = ox + 2 oy + 4 oz) in shared memory:
+// L[n][w] = (sign word w, weight word w) of neighbour n, w = (ly >> 2) + 2 lz, byte ly & 3 of a
+// word holding the 8 voxels x = 0..7 of row (ly, lz).  A 9-bit lattice row (x = 0..8) at
+// (Y, Z), Y, Z in 0..8, is byte (Y & 3) of L[n][w] with bit 0 of the same byte of L[n + 1][w]
+// (the +x neighbour) above it: one byte permute per kind builds it from two 8-byte loads.
+struct LatticeRow {
+  unsigned int off;   // n * 16 + w
+  unsigned int sel;   // byte-permute selector: byte k of the first word, byte k of the second
+};
+__device__ __forceinline__ LatticeRow lattice_row(int Y, int Z) {
+  const int n = 2 * (Y >> 3) + 4 * (Z >> 3);
   const int ly = Y & 7, lz = Z & 7;
-  const int word = 16 * kind + (ly >> 2) + 2 * lz;
-  const int sh = (ly & 3) * 8;
-  return ((m[nb][word] >> sh) & 0xFFu) | (((m[nb + 1][word] >> sh) & 1u) << 8);
+  const unsigned int k = (unsigned int)(ly & 3);
+  return LatticeRow{(unsigned int)(16 * n + (ly >> 2) + 2 * lz), k | ((4u + k) << 4)};
 }
 
-__global__ void __launch_bounds__(kMcThreads, 6) k_mc_extract(TableView t, PoolView pool,
+#ifndef VBH_MC_MIN_CTAS
+#define VBH_MC_MIN_CTAS 8
+#endif
+__global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(TableView t, PoolView pool,
                                                           DevCounters* cnt, const FrameCtl* ctl,
                                                           const unsigned int* mset,
                                                           const unsigned long long* tombrec) {
   __shared__ unsigned long long spread[256];   // bit i of b -> bit 8 i
-  __shared__ unsigned int msk[kMcThreads / 32][8][32];
+  __shared__ uint2 msk[kMcThreads / 32][8 * 16];   // the lattice, per warp
   __shared__ unsigned short stage_loc[kMcThreads / 32][kStage];
   __shared__ unsigned char stage_idx[kMcThreads / 32][kStage];
   __shared__ unsigned int stage_r[kMcThreads / 32][kStageBlocks];
@@ -214,7 +222,17 @@ __global__ void __launch_bounds__(kMcThreads, 6) k_mc_extract(TableView t, PoolV
   }
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int nwarps = gridDim.x * (kMcThreads / 32);
-  unsigned int(*m)[32] = msk[warp];
+  uint2* const lat = msk[warp];
+  // this lane's place in the lattice (mask word `lane`) and its 2 x 4 lattice rows: rows
+  // y = lane & 7, z = (lane >> 3) + 4 h of the block, each with its +y, +z, +y+z rows
+  unsigned int* const lat_fill = reinterpret_cast<unsigned int*>(lat) + 2u * (lane & 15u) +
+                                 (lane >> 4);
+  LatticeRow lr[2][4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      lr[h][c] = lattice_row((int)(lane & 7u) + (c & 1), (int)(lane >> 3) + 4 * h + (c >> 1));
   bool overflow = false;
   // Entries are staged per warp in shared memory and leave with one reservation per flush
   // (atomics on one address serialise in L2: one per block would bound the kernel).
@@ -289,18 +307,23 @@ __global__ void __launch_bounds__(kMcThreads, 6) k_mc_extract(TableView t, PoolV
       }
     }
 #pragma unroll
-    for (int n = 0; n < 8; ++n) m[n][lane] = mw[n];
+    for (int n = 0; n < 8; ++n) lat_fill[32 * n] = mw[n];
     __syncwarp();
     const int3 k = unpack_key(key);
     unsigned long long idx8[2], nz[2];
     unsigned int mine = 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int row = (int)lane + 32 * h, y = row & 7, z = row >> 3;
-      const unsigned int n00 = row9(m, 0, y, z), n10 = row9(m, 0, y + 1, z);
-      const unsigned int n01 = row9(m, 0, y, z + 1), n11 = row9(m, 0, y + 1, z + 1);
-      const unsigned int va = row9(m, 1, y, z) & row9(m, 1, y + 1, z) & row9(m, 1, y, z + 1) &
-                              row9(m, 1, y + 1, z + 1);
+      // sign rows (Y, Z), (Y+1, Z), (Y, Z+1), (Y+1, Z+1) in bits 0..8 (bits above 8 are not
+      // read) and the AND of their weight rows
+      unsigned int sg[4], va = 0xFFFFFFFFu;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint2 a = lat[lr[h][c].off], b = lat[lr[h][c].off + 16u];
+        sg[c] = __byte_perm(a.x, b.x, lr[h][c].sel);
+        va &= __byte_perm(a.y, b.y, lr[h][c].sel);
+      }
+      const unsigned int n00 = sg[0], n10 = sg[1], n01 = sg[2], n11 = sg[3];
       unsigned long long c = spread[n00 & 0xFFu] | (spread[(n00 >> 1) & 0xFFu] << 1) |
                              (spread[(n10 >> 1) & 0xFFu] << 2) | (spread[n10 & 0xFFu] << 3) |
                              (spread[n01 & 0xFFu] << 4) | (spread[(n01 >> 1) & 0xFFu] << 5) |
