@@ -58,40 +58,31 @@ __global__ void k_setup(FrameCtl c, FrameCtl* dst, DevCounters* cnt) {
   }
 }
 
-constexpr unsigned int kRing = 64;
-// With stream-out on, the host must drain the device ring of removed blocks, and it sees the
-// ring's head only for frames that have run: it therefore lets at most this many frames wait
-// on the GPU, so that its view of the head is never more than these frames old (the ring keeps
-// a quarter of its capacity free for them).
+// Frames the host may have queued on the GPU (vbh_process_frame waits beyond that).  With
+// stream-out on, the host must drain the device ring of removed blocks, and it sees the ring's
+// head only for frames that have run: it therefore lets at most kStreamOutAhead frames wait on
+// the GPU, so that its view of the head is never more than these frames old (the ring keeps a
+// quarter of its capacity free for them).
+constexpr unsigned int kMaxAhead = 64;
 constexpr unsigned int kStreamOutAhead = 3;
 
-// Root node of the frame graph: fetch the next control block from the host ring (uncached
-// reads of mapped host memory), store it, zero the per-frame counters, acknowledge the slot.
-__global__ void k_setup_ring(const FrameCtl* ring, unsigned long long* dev_seq,
-                             unsigned long long* consumed, FrameCtl* dst, DevCounters* cnt) {
-  __shared__ FrameCtl c;
-  constexpr int kWords = sizeof(FrameCtl) / 4;
-  static_assert(kWords <= 128, "one word per thread of the 128-thread setup kernel");
-  const unsigned long long seq = *dev_seq;
-  const unsigned int* src = reinterpret_cast<const unsigned int*>(ring + (seq % kRing));
-  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
-    reinterpret_cast<unsigned int*>(&c)[i] = __ldcv(src + i);
-  __syncthreads();
-  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
-    reinterpret_cast<unsigned int*>(dst)[i] = reinterpret_cast<const unsigned int*>(&c)[i];
-  if (threadIdx.x == 0) {
-    cnt->n_cand = 0;
-    cnt->n_touched = 0;
-    cnt->n_new = 0;
-    cnt->vox_updated = 0ull;
-    cnt->n_erased = 0;
-    cnt->n_mset = 0;
-    cnt->n_tombrec = 0;
-    if (c.n_entries_dev) *c.n_entries_dev = 0;
-    *dev_seq = seq + 1;
-    __threadfence_system();
-    *reinterpret_cast<volatile unsigned long long*>(consumed) = seq + 1;
-  }
+// Root node of the frame graph: the control block arrives by value (vbh_process_frame patches
+// this node's argument before each launch, so the graph reads no host memory), is stored for
+// the other kernels, the per-frame counters are zeroed and the frame's sequence number is
+// reported to mapped host memory (the host's bound on queued frames).
+__global__ void k_setup_frame(const FrameCtl c, unsigned long long seq,
+                              unsigned long long* consumed, FrameCtl* dst, DevCounters* cnt) {
+  *dst = c;
+  cnt->n_cand = 0;
+  cnt->n_touched = 0;
+  cnt->n_new = 0;
+  cnt->vox_updated = 0ull;
+  cnt->n_erased = 0;
+  cnt->n_mset = 0;
+  cnt->n_tombrec = 0;
+  if (c.n_entries_dev) *c.n_entries_dev = 0;
+  __threadfence_system();
+  *reinterpret_cast<volatile unsigned long long*>(consumed) = seq + 1;
 }
 
 // Non-blocking view of the counters: a copy enqueued on a side stream after each call, read by
@@ -291,8 +282,6 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
   CREATE_CUDA(cudaMalloc(&h->cnt, sizeof(DevCounters)));
   CREATE_CUDA(cudaMalloc(&h->ctl, sizeof(FrameCtl)));
   CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  CREATE_CUDA(cudaHostAlloc(&h->ring_host, kRing * sizeof(FrameCtl), cudaHostAllocMapped));
-  CREATE_CUDA(cudaHostGetDevicePointer((void**)&h->ring_dev, h->ring_host, 0));
   {
     unsigned long long* ch = nullptr;
     CREATE_CUDA(cudaHostAlloc(&ch, sizeof(unsigned long long), cudaHostAllocMapped));
@@ -300,8 +289,6 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
     h->consumed_host = ch;
     CREATE_CUDA(cudaHostGetDevicePointer((void**)&h->consumed_dev, ch, 0));
   }
-  CREATE_CUDA(cudaMalloc(&h->dev_seq, sizeof(unsigned long long)));
-  CREATE_CUDA(cudaMemsetAsync(h->dev_seq, 0, sizeof(unsigned long long), h->stream));
   CREATE_CUDA(cudaMallocHost(&h->snap, sizeof(DevCounters)));
   DevCounters init{};
   init.free_top = (int)c.max_blocks;
@@ -357,9 +344,8 @@ vbh_status vbh_destroy(vbh_handle* h) {
   if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
   if (h->frame_graph) cudaGraphDestroy(h->frame_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-  if (h->ring_host) cudaFreeHost(h->ring_host);
   if (h->consumed_host) cudaFreeHost((void*)h->consumed_host);
-  void* ptrs[] = {h->dev_seq, h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
+  void* ptrs[] = {h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
                   h->version, h->stack, h->seq, h->cand, h->cand_res, h->cand_st, h->touched, h->tdepth, h->tkey, h->mset,
                   h->removed, h->tombrec};
   for (void* p : ptrs)
@@ -492,9 +478,9 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   for (int i = 0; i < 4; ++i)
     if ((i < 2 && t_int) || (i >= 2 && t_mc)) ev[i] = h->get_event();
   VBH_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
-  // one thread per word of the control block: a single round trip to host memory
-  k_setup_ring<<<1, 128, 0, h->cap_stream>>>(h->ring_dev, h->dev_seq, h->consumed_dev, h->ctl,
-                                             h->cnt);
+  // the root node takes the control block by value: vbh_process_frame patches it
+  k_setup_frame<<<1, 1, 0, h->cap_stream>>>(base_ctl(h, nullptr), 0ull, h->consumed_dev, h->ctl,
+                                            h->cnt);
   launch_erase_radius(Lc, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks, nullptr,
                       nullptr, stream_list(h));
   if (h->so) launch_stream_gather(Lc, h->so_ring, h->ctl, pool, h->cnt, stream_list(h));
@@ -529,6 +515,7 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
     std::vector<cudaGraphNode_t> nodes(n);
     VBH_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
     h->integ_node = nullptr;
+    h->setup_node = nullptr;
     for (cudaGraphNode_t node : nodes) {
       cudaGraphNodeType ty;
       VBH_CUDA(cudaGraphNodeGetType(node, &ty));
@@ -538,9 +525,13 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
       if (kp.func == integrate_kernel()) {
         h->integ_node = node;
         h->integ_kp = kp;
+      } else if (kp.func == reinterpret_cast<const void*>(&k_setup_frame)) {
+        h->setup_node = node;
+        h->setup_kp = kp;
       }
     }
-    if (!h->integ_node) return fail(VBH_ERR_CUDA, "frame graph: fusion node not found");
+    if (!h->integ_node || !h->setup_node)
+      return fail(VBH_ERR_CUDA, "frame graph: fusion or setup node not found");
   }
   if (tmask) {
     size_t n = 0;
@@ -601,20 +592,28 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
   c.serve_mark = h->slog != nullptr;
   c.visible = h->integ_mode == VBH_INTEGRATE_VISIBLE;
   set_stream_out(c, out);
-  // wait (bounded) until the graph launched `ahead` frames ago has consumed its slot: the
-  // slot this frame overwrites, and with stream-out on, a bound on the frames queued ahead
+  // wait (bounded) until the graph launched `ahead` frames ago has started: a bound on the
+  // frames queued on the GPU
   const unsigned long long seq = h->host_seq;
-  const unsigned long long ahead = h->so ? kStreamOutAhead : kRing;
+  const unsigned long long ahead = h->so ? kStreamOutAhead : kMaxAhead;
   if (seq >= ahead) {
     const unsigned long long need = seq - ahead + 1;
     int spins = 0;
     while (*h->consumed_host < need) {
-      if (++spins > 2000000) return fail(VBH_ERR_TIMEOUT, "frame ring slot not consumed");
+      if (++spins > 2000000) return fail(VBH_ERR_TIMEOUT, "queued frames did not start");
       if (spins > 1000) usleep(5);
     }
   }
-  h->ring_host[seq % kRing] = c;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
+  {   // the control block into the root node (applies to this and later launches only)
+    unsigned long long* consumed = h->consumed_dev;
+    FrameCtl* dst = h->ctl;
+    DevCounters* cntp = h->cnt;
+    void* args[] = {&c, (void*)&seq, &consumed, &dst, &cntp};
+    cudaKernelNodeParams kp = h->setup_kp;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    VBH_CUDA(cudaGraphExecKernelNodeSetParams(h->frame_exec, h->setup_node, &kp));
+  }
   {   // this frame's parameters into the fusion node (applies to this and later launches)
     FrameParams fpv = c.fp;
     PoolView pv = h->pool();

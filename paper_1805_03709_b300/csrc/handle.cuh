@@ -88,15 +88,14 @@ struct vbh_handle {
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t frame_graph = nullptr;
   cudaGraphExec_t frame_exec = nullptr;
-  // control blocks of vbh_process_frame travel through a pinned, device-mapped ring: the host
-  // writes slot (seq % kRing) and launches the graph; the graph's root kernel reads the next
-  // slot itself and reports the consumed sequence number back through mapped memory
-  FrameCtl* ring_host = nullptr;
-  FrameCtl* ring_dev = nullptr;
+  // the control block of each vbh_process_frame is the by-value argument of the graph's root
+  // node (patched before the launch); the root node reports the frame's sequence number back
+  // through mapped memory, which bounds the frames the host queues
   volatile unsigned long long* consumed_host = nullptr;
   unsigned long long* consumed_dev = nullptr;
-  unsigned long long* dev_seq = nullptr;   // device memory
   unsigned long long host_seq = 0;
+  cudaGraphNode_t setup_node = nullptr;
+  cudaKernelNodeParams setup_kp{};
   cudaGraphNode_t ev_node[4] = {nullptr, nullptr, nullptr, nullptr};   // fusion, MC extraction
   cudaGraphNode_t integ_node = nullptr;   // fusion node: its by-value frame parameters are
   cudaKernelNodeParams integ_kp{};        // patched before every launch
