@@ -352,9 +352,15 @@ def main():
     peak, peak_src = measured_peak()
     tr = profile_traffic(touched / max(args.steps, 1))
 
-    # ---- end to end: host depth in pinned memory, MC stream read back every step
+    # ---- end to end through the C ABI's host-buffer call (vbh_process_frame_host): every step
+    # copies its depth image from pinned host memory and its whole MC stream back to pinned host
+    # memory; the call pipelines consecutive frames (the copy-out of frame k overlaps frame k+1).
+    # Timed by wall clock from the first call to the completion of the last frame; the 256 MiB
+    # L2 flush between frames runs in the same stream and its event-timed duration is subtracted.
     e2e = None
     if not args.no_e2e:
+        from paper_1805_03709_b300 import vbh as V
+        from paper_1805_03709_b300.volume import HostStream
         # a fresh volume replays the same warm-up and timed frames, now through host buffers
         vol.close()
         vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
@@ -366,42 +372,43 @@ def main():
         vol.timing(("mc",))   # MC extraction timed on the replay (kept out of the main loop)
         vol.timing_read(reset=True)
         host_depth = torch.from_numpy(depth).pin_memory()
-        d_in = torch.empty((cam.height, cam.width), dtype=torch.uint16, device=dev)
-        s = vol.stream
-        h_keys = torch.empty(s.keys3.shape, dtype=torch.int32).pin_memory()
-        h_info = torch.empty(s.info.shape, dtype=torch.int32).pin_memory()
-        h_off = torch.empty(s.offsets.shape, dtype=torch.int32).pin_memory()
-        h_cnt = torch.empty(s.counts.shape, dtype=torch.int32).pin_memory()
-        h_loc = torch.empty(s.local.shape, dtype=torch.int16).pin_memory()
-        h_idx = torch.empty(s.index.shape, dtype=torch.uint8).pin_memory()
-        h_n = torch.empty(2, dtype=torch.int32).pin_memory()
+        outs = [HostStream.allocate(MAX_BLOCKS, 1 << 23) for _ in range(2)]
+        fl_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
         h2d = d2h = 0
-        torch.cuda.synchronize()
-        t_e2e = 0.0
         mc_counts = []
+        statuses = []
+
+        def account(o):
+            nonlocal d2h
+            nb, ne = o.n
+            d2h += 8 + nb * 24 + ne * 3
+            n_rem = int((o.info[:nb].numpy().view(np.uint32) >> 31).sum())
+            mc_counts.append((nb - n_rem, n_rem, ne))
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         for k in range(args.steps):
             i = args.warmup + k
             f = i % N_FRAMES
+            fl_ev[k][0].record()
             flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            d_in.copy_(host_depth[f], non_blocking=True)
-            step(i, i + 1, d_in)
-            h_n.copy_(s.n, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-            nb, ne = int(h_n[0]), int(h_n[1])
-            h_keys[:nb].copy_(s.keys3[:nb], non_blocking=True)
-            h_info[:nb].copy_(s.info[:nb], non_blocking=True)
-            h_off[:nb].copy_(s.offsets[:nb], non_blocking=True)
-            h_cnt[:nb].copy_(s.counts[:nb], non_blocking=True)
-            h_loc[:ne].copy_(s.local[:ne], non_blocking=True)
-            h_idx[:ne].copy_(s.index[:ne], non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-            t_e2e += time.perf_counter() - t0
+            fl_ev[k][1].record()
+            statuses.append(vol.process_frame_host(host_depth[f], poses[f], i + 1, ERASE_R,
+                                                   outs[k % 2]))
             h2d += depth_bytes
-            d2h += 8 + nb * 24 + ne * 3
-            n_rem = int((h_info[:nb].numpy().view(np.uint32) >> 31).sum())
-            mc_counts.append((nb - n_rem, n_rem, ne))
+            if k:
+                account(outs[(k - 1) % 2])
+        statuses.append(vol.process_frame_host_flush())
+        account(outs[(args.steps - 1) % 2])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        flush_s = sum(a.elapsed_time(b) for a, b in fl_ev) / 1e3
+        t_e2e = (t1 - t0) - flush_s
+        assert all(st == V.VBH_OK for st in statuses), "host stream capacity exceeded"
+        # live blocks after each frame, for the whole-frame roofline (untimed replay)
+        live_after = [c[3] for c in mc_replay(torch, cam, D, poses, args)[0]]
+        mc_counts = [c + (lv,) for c, lv in zip(mc_counts, live_after)]
         mc_timing = vol.timing_read(reset=True)
         vol.timing(())
         if ws > 1:
@@ -409,7 +416,10 @@ def main():
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             t_e2e = float(t.item())
         e2e = {"value": ws * args.steps / t_e2e, "unit": "frames/s",
-               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+               "api": "vbh_process_frame_host (pinned host depth in, whole MC stream out, "
+                      "consecutive frames pipelined)",
+               "l2_flush_between_frames_s": flush_s}
 
     # MC extraction roofline: the same frames' MC extraction, timed (CUDA events around the
     # kernel on the volume's stream) and counted on the e2e replay (or a replay of its own)
@@ -434,6 +444,32 @@ def main():
                                  "reads the 128 B sign/weight masks per block instead of the "
                                  "voxels (its DRAM traffic is a few % of this)"}
 
+    # whole-frame roofline: the algorithmic bytes of every step of the frame (allocation,
+    # integration, erase, MC) over the measured frame time
+    frame_line = None
+    if mc_counts:
+        nf = len(mc_counts)
+        mc_live = sum(c[0] for c in mc_counts) / nf
+        mc_rem = sum(c[1] for c in mc_counts) / nf
+        mc_ent = sum(c[2] for c in mc_counts) / nf
+        live_avg = sum(c[3] for c in mc_counts) / nf
+        t_avg, n_avg = touched / args.steps, new / args.steps
+        by = {"allocation": depth_bytes + t_avg * (64 + 16) + n_avg * 512 * 8,
+              "integration": t_avg * 512 * 16 + depth_bytes,
+              "erase": live_avg * 16 + mc_rem * 16,
+              "mc": mc_live * 512 * 8 + (mc_live + mc_rem) * 24 + mc_ent * 3}
+        fb = sum(by.values())
+        f_ach = fb / (ms_total / args.steps / 1e3) / 1e9
+        frame_line = {"bound": "hbm", "achieved": f_ach, "peak": peak, "peak_source": peak_src,
+                      "unit": "GB/s", "frac": f_ach / peak, "bytes_per_frame": fb,
+                      "bytes_by_step": by, "ms_per_frame": ms_total / args.steps,
+                      "definition": "allocation: 2 B per pixel + 80 B per touched block (bucket "
+                                    "+ list entry) + 4 KiB per new block; integration: 8 B read + "
+                                    "8 B written per voxel of each touched block + the depth "
+                                    "image; erase: 16 B per live block scanned + 16 B per erased "
+                                    "slot; MC: 8 B per voxel of each block in the set + 24 B per "
+                                    "record + 3 B per nonzero index"}
+
     tri_pt = None
     if not args.no_tri:
         tri_pt = tri_point(torch, state["vol"], peak)
@@ -441,6 +477,14 @@ def main():
     hash_pt = None
     if not args.no_hash:
         hash_pt = hash_point(torch, dev, flush, peak)
+        # the other table loads and batch sizes of the hash workload
+        sweep = []
+        for lf, n, nb, nw in ((0.5, 1 << 20, 6, 2), (0.9, 1 << 20, 6, 2), (0.7, 1 << 12, 14, 4),
+                              (0.7, 1 << 16, 10, 2), (0.7, 1 << 22, 4, 1)):
+            r = hash_point(torch, dev, flush, peak, lf=lf, n=n, n_batches=nb, n_warm=nw)
+            sweep.append({k: r[k] for k in ("load_factor", "batch", "Mops_s", "hbm_frac",
+                                            "batches_timed", "rebuilds")})
+        hash_pt["sweep"] = sweep
     diff_pt = None
     if not args.no_diff:
         diff_pt = diff_point(torch, dev, flush)
@@ -472,7 +516,7 @@ def main():
                          "algorithmic_bytes_per_launch": alg_bytes / n_launch,
                          "avg_launch_ms": integ_ms / n_launch,
                          "share_of_step": integ_ms / ms_total if ms_total else None},
-            "roofline_mc": mc_line,
+            "roofline_mc": mc_line, "roofline_frame": frame_line,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "wall_s_timed_region": t_wall1 - t_wall0,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
@@ -485,16 +529,15 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def hash_point(torch, dev, flush, peak):
-    """Hash microbenchmark point: 2^22 x 4 table prefilled to load factor 0.7 with distinct
-    uniform keys in [-2^20, 2^20)^3; batches of 2^20 ops (50 % find half hits, 30 % insert of
+def hash_point(torch, dev, flush, peak, lf=0.7, n=1 << 20, n_batches=6, n_warm=2):
+    """Hash microbenchmark point: 2^22 x 4 table prefilled to load factor `lf` with distinct
+    uniform keys in [-2^20, 2^20)^3; batches of `n` ops (50 % find half hits, 30 % insert of
     absent keys, 20 % erase of present keys); untimed rebalance after each batch."""
     from paper_1805_03709_b300 import synth, vbh as V
     from paper_1805_03709_b300.volume import HashMap
-    n_buckets, n = 1 << 22, 1 << 20
+    n_buckets = 1 << 22
     cap = n_buckets * 4
-    n_pre = int(0.7 * cap)
-    n_batches, n_warm = 6, 2
+    n_pre = int(lf * cap)
     keys = synth.distinct_keys(n_pre + n * n_batches, seed=1805)
     K = torch.from_numpy(keys).to(dev)
     hm = HashMap(n_buckets=n_buckets, max_batch=1 << 24)
@@ -548,7 +591,7 @@ def hash_point(torch, dev, flush, peak):
     c = hm.counters()
     hm.close()
     gbs = bytes_alg / (t_ms / 1e3) / 1e9
-    return {"Mops_s": ops_done / (t_ms / 1e3) / 1e6, "load_factor": 0.7, "batch": n,
+    return {"Mops_s": ops_done / (t_ms / 1e3) / 1e6, "load_factor": lf, "batch": n,
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
@@ -728,8 +771,8 @@ def stream_point(torch, cam, D, poses, flush, args, base_ms):
 
 
 def mc_replay(torch, cam, D, poses, args):
-    """(live blocks, removal records, entries) of each timed frame's MC extraction, from an
-    untimed replay of the same frames on a fresh volume."""
+    """(live blocks, removal records, entries) of each timed frame's MC extraction and the live
+    blocks after it, from an untimed replay of the same frames on a fresh volume."""
     from paper_1805_03709_b300.volume import Volume
     vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
                  N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
@@ -744,7 +787,7 @@ def mc_replay(torch, cam, D, poses, args):
         if i >= args.warmup:
             nb, ne = (int(x) for x in s.n.cpu().tolist())
             rem = int((s.info[:nb].cpu().numpy().view(np.uint32) >> 31).sum())
-            out.append((nb - rem, rem, ne))
+            out.append((nb - rem, rem, ne, vol.counters().live))
     timing = vol.timing_read(reset=True)
     vol.close()
     return out, timing

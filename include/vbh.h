@@ -237,6 +237,41 @@ vbh_status vbh_extract_mc_indices(vbh_handle* h, const vbh_mc_selector* sel_host
 vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const float* T_wc_host,
                              uint32_t frame_id, float erase_radius, const vbh_mc_stream* out);
 
+/* Host-side output of a frame: caller-owned host memory (pinned -- cudaHostAlloc or
+ * cudaHostRegister -- lets the copy overlap the next frame), arrays as in vbh_mc_stream with
+ * capacities cap_blocks / cap_entries.  n_blocks, n_entries, frame_id and done are written by
+ * the library once the frame's results are complete: the totals the frame produced (when they
+ * exceed the capacities only the first cap_* records / entries are copied, and the call that
+ * completes the frame returns VBH_ERR_BUFFER_TOO_SMALL), the frame's id, and done = 1. */
+typedef struct {
+  int32_t* keys3;      /* cap_blocks x 3 */
+  uint32_t* info;      /* cap_blocks */
+  uint32_t* offsets;   /* cap_blocks */
+  uint32_t* counts;    /* cap_blocks */
+  uint16_t* local;     /* cap_entries */
+  uint8_t* index;      /* cap_entries */
+  uint32_t cap_blocks;
+  uint32_t cap_entries;
+  uint32_t n_blocks;   /* out */
+  uint32_t n_entries;  /* out */
+  uint32_t frame_id;   /* out */
+  uint32_t done;       /* out: 0 while the frame is in flight, 1 once complete */
+} vbh_mc_stream_host;
+
+/* vbh_process_frame with host buffers, pipelined (Sec. 4.1-4.2 per frame, as vbh_process_frame):
+ * the depth image is copied from host memory (depth_host: width x height uint16, reusable when
+ * the call returns), the frame runs on one of two library-owned device streams, and its MC
+ * stream is copied into out_host while the next frame is computed.  The call enqueues this
+ * frame and returns once the PREVIOUS call's frame is complete in the previous call's out_host
+ * (the status of that completion is returned: VBH_ERR_BUFFER_TOO_SMALL if it was cut);
+ * vbh_process_frame_host_flush completes the last frame.  Each out_host must stay valid until
+ * its frame is done.  Host-visible synchronisation is with the previous frame only, so the copy
+ * in, the frame and the copy out of consecutive frames overlap. */
+vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
+                                  const float* T_wc_host, uint32_t frame_id, float erase_radius,
+                                  vbh_mc_stream_host* out_host);
+vbh_status vbh_process_frame_host_flush(vbh_handle* h);
+
 /* Host copies of the live blocks (test and checkpoint path; synchronises).  keys3_host: cap
  * keys; tsdf_host, weight_host: cap*512 floats each (may be NULL); vals_host: cap uint32 (the
  * value of each key: pool index or the plain map's value; may be NULL); *n_host = live keys

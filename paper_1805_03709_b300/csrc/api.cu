@@ -338,6 +338,7 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
 vbh_status vbh_destroy(vbh_handle* h) {
   if (!h) return VBH_OK;
   if (h->server) vbh_serve_destroy(h->server);
+  host_pipe_release(h);
   stream_out_release(h);
   if (h->stream || h->slots) cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);

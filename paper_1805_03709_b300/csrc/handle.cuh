@@ -21,6 +21,7 @@ vbh_status fail(vbh_status st, const std::string& msg);
   } while (0)
 
 struct StreamOutHost;   // stream-out bookkeeping on the host (streamout.cu)
+struct HostPipe;        // pipelined host-buffer frames (hostframe.cu)
 
 struct StageEvents {
   int stage;
@@ -67,6 +68,7 @@ struct vbh_handle {
   unsigned int* so_p = nullptr;
   unsigned long long* so_k = nullptr;
   vbh::StreamOutHost* so = nullptr;
+  vbh::HostPipe* hp = nullptr;   // vbh_process_frame_host state
   // per-frame lists
   int J = 0;
   unsigned long long* cand = nullptr;
@@ -160,6 +162,7 @@ namespace vbh {
 vbh_status stream_out_poll(vbh_handle* h, bool wait);
 unsigned long long stream_out_tail(const vbh_handle* h);
 void stream_out_release(vbh_handle* h);
+void host_pipe_release(vbh_handle* h);
 inline StreamList stream_list(const vbh_handle* h);
 // The volume handle and the device-resident log/store of a server (serve.cu).
 vbh_handle* serve_handle(vbh_serve* s);

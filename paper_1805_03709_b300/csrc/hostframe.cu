@@ -1,0 +1,209 @@
+// vbh_process_frame with host buffers, pipelined over consecutive calls.
+//
+// Call k (j = k mod 2) enqueues: the depth copy host -> device buffer j on a copy stream (after
+// frame k-2, which read buffer j, has finished), the frame graph on the handle's stream into
+// device stream j (after frame k-2's results, read from stream j, have been copied out), and a
+// copy of frame k's two totals to pinned memory.  It then completes frame k-1: waits for its
+// totals, copies its records and entries (as many as there are, up to the caller's
+// capacities) into the caller's host buffers on the copy stream -- while frame k runs -- and
+// waits for that copy.  So the host waits for one frame at a time and the GPU always has the
+// next frame queued.
+#include "handle.cuh"
+
+namespace vbh {
+
+struct HostPipe {
+  cudaStream_t copy = nullptr;
+  uint16_t* depth[2] = {nullptr, nullptr};   // device depth images
+  // device output streams and their totals (device) / totals copy (pinned host)
+  int32_t* keys3[2] = {nullptr, nullptr};
+  uint32_t* info[2] = {nullptr, nullptr};
+  uint32_t* offsets[2] = {nullptr, nullptr};
+  uint32_t* counts[2] = {nullptr, nullptr};
+  uint16_t* local[2] = {nullptr, nullptr};
+  uint8_t* index[2] = {nullptr, nullptr};
+  uint32_t* n_dev[2] = {nullptr, nullptr};
+  uint32_t* n_pin[2] = {nullptr, nullptr};
+  uint32_t cap_blocks = 0, cap_entries = 0;
+  cudaEvent_t e_h2d[2] = {nullptr, nullptr}, e_frame[2] = {nullptr, nullptr},
+              e_out[2] = {nullptr, nullptr};
+  bool frame_used[2] = {false, false}, out_used[2] = {false, false};
+  unsigned long long k = 0;   // frames enqueued
+  // the frame enqueued by the previous call, not yet complete
+  vbh_mc_stream_host* pending = nullptr;
+  uint32_t pending_id = 0;
+  int pending_j = 0;
+};
+
+namespace {
+
+void free_streams(HostPipe* p) {
+  for (int j = 0; j < 2; ++j) {
+    void* d[] = {p->keys3[j], p->info[j], p->offsets[j], p->counts[j], p->local[j], p->index[j]};
+    for (void* q : d)
+      if (q) cudaFree(q);
+    p->keys3[j] = nullptr;
+    p->info[j] = p->offsets[j] = p->counts[j] = nullptr;
+    p->local[j] = nullptr;
+    p->index[j] = nullptr;
+  }
+  p->cap_blocks = p->cap_entries = 0;
+}
+
+vbh_status alloc_streams(HostPipe* p, uint32_t cb, uint32_t ce) {
+  free_streams(p);
+  for (int j = 0; j < 2; ++j) {
+    VBH_CUDA(cudaMalloc(&p->keys3[j], sizeof(int32_t) * 3ull * cb));
+    VBH_CUDA(cudaMalloc(&p->info[j], sizeof(uint32_t) * (size_t)cb));
+    VBH_CUDA(cudaMalloc(&p->offsets[j], sizeof(uint32_t) * (size_t)cb));
+    VBH_CUDA(cudaMalloc(&p->counts[j], sizeof(uint32_t) * (size_t)cb));
+    VBH_CUDA(cudaMalloc(&p->local[j], sizeof(uint16_t) * (size_t)ce));
+    VBH_CUDA(cudaMalloc(&p->index[j], (size_t)ce));
+  }
+  p->cap_blocks = cb;
+  p->cap_entries = ce;
+  return VBH_OK;
+}
+
+vbh_status create_pipe(vbh_handle* h) {
+  HostPipe* p = new HostPipe();
+  h->hp = p;
+  VBH_CUDA(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking));
+  const size_t db = sizeof(uint16_t) * (size_t)h->cfg.width * h->cfg.height;
+  for (int j = 0; j < 2; ++j) {
+    VBH_CUDA(cudaMalloc(&p->depth[j], db));
+    VBH_CUDA(cudaMalloc(&p->n_dev[j], 2 * sizeof(uint32_t)));
+    VBH_CUDA(cudaMallocHost(&p->n_pin[j], 2 * sizeof(uint32_t)));
+    VBH_CUDA(cudaEventCreateWithFlags(&p->e_h2d[j], cudaEventDisableTiming));
+    VBH_CUDA(cudaEventCreateWithFlags(&p->e_frame[j], cudaEventDisableTiming));
+    VBH_CUDA(cudaEventCreateWithFlags(&p->e_out[j], cudaEventDisableTiming));
+  }
+  return VBH_OK;
+}
+
+// Copy the pending frame's stream into its host buffers and mark it done.
+vbh_status complete_pending(vbh_handle* h) {
+  HostPipe* p = h->hp;
+  vbh_mc_stream_host* o = p->pending;
+  if (!o) return VBH_OK;
+  p->pending = nullptr;
+  const int j = p->pending_j;
+  VBH_CUDA(cudaEventSynchronize(p->e_frame[j]));
+  const uint32_t nb = p->n_pin[j][0], ne = p->n_pin[j][1];
+  const uint32_t cb = nb < o->cap_blocks ? nb : o->cap_blocks;
+  const uint32_t ce = ne < o->cap_entries ? ne : o->cap_entries;
+  if (cb) {
+    VBH_CUDA(cudaMemcpyAsync(o->keys3, p->keys3[j], sizeof(int32_t) * 3ull * cb,
+                             cudaMemcpyDeviceToHost, p->copy));
+    VBH_CUDA(cudaMemcpyAsync(o->info, p->info[j], sizeof(uint32_t) * (size_t)cb,
+                             cudaMemcpyDeviceToHost, p->copy));
+    VBH_CUDA(cudaMemcpyAsync(o->offsets, p->offsets[j], sizeof(uint32_t) * (size_t)cb,
+                             cudaMemcpyDeviceToHost, p->copy));
+    VBH_CUDA(cudaMemcpyAsync(o->counts, p->counts[j], sizeof(uint32_t) * (size_t)cb,
+                             cudaMemcpyDeviceToHost, p->copy));
+  }
+  if (ce) {
+    VBH_CUDA(cudaMemcpyAsync(o->local, p->local[j], sizeof(uint16_t) * (size_t)ce,
+                             cudaMemcpyDeviceToHost, p->copy));
+    VBH_CUDA(cudaMemcpyAsync(o->index, p->index[j], (size_t)ce, cudaMemcpyDeviceToHost,
+                             p->copy));
+  }
+  VBH_CUDA(cudaEventRecord(p->e_out[j], p->copy));
+  p->out_used[j] = true;
+  VBH_CUDA(cudaEventSynchronize(p->e_out[j]));
+  o->n_blocks = nb;
+  o->n_entries = ne;
+  o->frame_id = p->pending_id;
+  o->done = 1u;
+  if (nb > o->cap_blocks || ne > o->cap_entries)
+    return fail(VBH_ERR_BUFFER_TOO_SMALL, "host stream capacity exceeded (frame results cut)");
+  return VBH_OK;
+}
+
+}  // namespace
+
+void host_pipe_release(vbh_handle* h) {
+  HostPipe* p = h->hp;
+  if (!p) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (p->copy) {
+    cudaStreamSynchronize(p->copy);
+    cudaStreamDestroy(p->copy);
+  }
+  free_streams(p);
+  for (int j = 0; j < 2; ++j) {
+    if (p->depth[j]) cudaFree(p->depth[j]);
+    if (p->n_dev[j]) cudaFree(p->n_dev[j]);
+    if (p->n_pin[j]) cudaFreeHost(p->n_pin[j]);
+    for (cudaEvent_t e : {p->e_h2d[j], p->e_frame[j], p->e_out[j]})
+      if (e) cudaEventDestroy(e);
+  }
+  delete p;
+  h->hp = nullptr;
+}
+
+}  // namespace vbh
+
+using namespace vbh;
+
+vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
+                                  const float* T_wc_host, uint32_t frame_id, float erase_radius,
+                                  vbh_mc_stream_host* out_host) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  if (h->cfg.max_blocks == 0) return fail(VBH_ERR_UNSUPPORTED, "plain map handle has no voxels");
+  if (!depth_host || !T_wc_host || !out_host) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  const vbh_mc_stream_host& o = *out_host;
+  if (o.cap_blocks == 0 || o.cap_entries == 0 || !o.keys3 || !o.info || !o.offsets ||
+      !o.counts || !o.local || !o.index)
+    return fail(VBH_ERR_INVALID_ARG, "incomplete host output stream");
+  if (!h->hp) {
+    vbh_status st = create_pipe(h);
+    if (st != VBH_OK) {
+      host_pipe_release(h);
+      return st;
+    }
+  }
+  HostPipe* p = h->hp;
+  vbh_status done_st = VBH_OK;
+  if (o.cap_blocks > p->cap_blocks || o.cap_entries > p->cap_entries) {
+    // larger device streams: every frame in flight completes first
+    done_st = complete_pending(h);
+    VBH_CUDA(cudaStreamSynchronize(h->stream));
+    VBH_CUDA(cudaStreamSynchronize(p->copy));
+    const uint32_t cb = o.cap_blocks > p->cap_blocks ? o.cap_blocks : p->cap_blocks;
+    const uint32_t ce = o.cap_entries > p->cap_entries ? o.cap_entries : p->cap_entries;
+    vbh_status st = alloc_streams(p, cb, ce);
+    if (st != VBH_OK) return st;
+  }
+  const int j = (int)(p->k & 1ull);
+  // depth in: after frame k-2 (the last reader of buffer j) has finished
+  if (p->frame_used[j]) VBH_CUDA(cudaStreamWaitEvent(p->copy, p->e_frame[j], 0));
+  const size_t db = sizeof(uint16_t) * (size_t)h->cfg.width * h->cfg.height;
+  VBH_CUDA(cudaMemcpyAsync(p->depth[j], depth_host, db, cudaMemcpyHostToDevice, p->copy));
+  VBH_CUDA(cudaEventRecord(p->e_h2d[j], p->copy));
+  // the frame: after its depth has landed and stream j's previous results were copied out
+  VBH_CUDA(cudaStreamWaitEvent(h->stream, p->e_h2d[j], 0));
+  if (p->out_used[j]) VBH_CUDA(cudaStreamWaitEvent(h->stream, p->e_out[j], 0));
+  vbh_mc_stream s{p->keys3[j], p->info[j],  p->offsets[j], p->counts[j], p->local[j],
+                  p->index[j], p->cap_blocks, p->cap_entries, p->n_dev[j], p->n_dev[j] + 1};
+  out_host->done = 0u;
+  vbh_status st = vbh_process_frame(h, p->depth[j], T_wc_host, frame_id, erase_radius, &s);
+  if (st != VBH_OK) return st;
+  VBH_CUDA(cudaMemcpyAsync(p->n_pin[j], p->n_dev[j], 2 * sizeof(uint32_t),
+                           cudaMemcpyDeviceToHost, h->stream));
+  VBH_CUDA(cudaEventRecord(p->e_frame[j], h->stream));
+  p->frame_used[j] = true;
+  ++p->k;
+  // the previous frame's results go out while this frame runs
+  if (done_st == VBH_OK) done_st = complete_pending(h);
+  p->pending = out_host;
+  p->pending_id = frame_id;
+  p->pending_j = j;
+  return done_st;
+}
+
+vbh_status vbh_process_frame_host_flush(vbh_handle* h) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  if (!h->hp) return VBH_OK;
+  return complete_pending(h);
+}

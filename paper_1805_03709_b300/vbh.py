@@ -68,6 +68,12 @@ class vbh_mc_stream(ctypes.Structure):
                 ("n_blocks_dev", _p), ("n_entries_dev", _p)]
 
 
+class vbh_mc_stream_host(ctypes.Structure):
+    _fields_ = [("keys3", _p), ("info", _p), ("offsets", _p), ("counts", _p), ("local", _p),
+                ("index", _p), ("cap_blocks", _u32), ("cap_entries", _u32), ("n_blocks", _u32),
+                ("n_entries", _u32), ("frame_id", _u32), ("done", _u32)]
+
+
 class vbh_diff_config(ctypes.Structure):
     _fields_ = [("voxel_size", _f32), ("trunc", _f32), ("width", _i32), ("height", _i32),
                 ("fx", _f32), ("fy", _f32), ("cx", _f32), ("cy", _f32), ("n_frames", _u32)]
@@ -89,6 +95,9 @@ SYMBOLS = [
      [_p, ctypes.POINTER(vbh_mc_selector), ctypes.POINTER(vbh_mc_stream), ctypes.POINTER(_u64)]),
     ("vbh_process_frame", ctypes.c_int,
      [_p, _p, _p, _u32, _f32, ctypes.POINTER(vbh_mc_stream)]),
+    ("vbh_process_frame_host", ctypes.c_int,
+     [_p, _p, _p, _u32, _f32, ctypes.POINTER(vbh_mc_stream_host)]),
+    ("vbh_process_frame_host_flush", ctypes.c_int, [_p]),
     ("vbh_dump", ctypes.c_int, [_p, _p, _p, _p, _p, _u32, ctypes.POINTER(_u32)]),
     ("vbh_load", ctypes.c_int, [_p, _p, _p, _p, _u32]),
     ("vbh_get_counters", ctypes.c_int, [_p, ctypes.POINTER(vbh_counters)]),
@@ -276,6 +285,25 @@ def vbh_process_frame(h, depth, T_wc, frame_id: int, erase_radius: float, out: v
     T = np.ascontiguousarray(np.asarray(T_wc, np.float32).reshape(12))
     _check(lib().vbh_process_frame(h, _ptr(depth), T.ctypes.data, int(frame_id),
                                    float(erase_radius), ctypes.byref(out)), "vbh_process_frame")
+
+
+def vbh_process_frame_host(h, depth_host, T_wc, frame_id: int, erase_radius: float,
+                           out: vbh_mc_stream_host) -> int:
+    """Enqueue a frame from host depth; completes the previous call's `out` (returns its status:
+    VBH_OK or VBH_ERR_BUFFER_TOO_SMALL).  `out` is kept by the library until its frame is done."""
+    T = np.ascontiguousarray(np.asarray(T_wc, np.float32).reshape(12))
+    st = lib().vbh_process_frame_host(h, _ptr(depth_host), T.ctypes.data, int(frame_id),
+                                      float(erase_radius), ctypes.byref(out))
+    if st not in (VBH_OK, VBH_ERR_BUFFER_TOO_SMALL):
+        _check(st, "vbh_process_frame_host")
+    return st
+
+
+def vbh_process_frame_host_flush(h) -> int:
+    st = lib().vbh_process_frame_host_flush(h)
+    if st not in (VBH_OK, VBH_ERR_BUFFER_TOO_SMALL):
+        _check(st, "vbh_process_frame_host_flush")
+    return st
 
 
 def vbh_dump(h, keys3, tsdf, weight, vals, cap: int) -> int:

@@ -117,6 +117,66 @@ class McStream:
         return out
 
 
+@dataclasses.dataclass
+class HostStream:
+    """Pinned host buffers of one frame's MC stream (see vbh_mc_stream_host)."""
+    keys3: torch.Tensor
+    info: torch.Tensor
+    offsets: torch.Tensor
+    counts: torch.Tensor
+    local: torch.Tensor
+    index: torch.Tensor
+
+    @classmethod
+    def allocate(cls, cap_blocks: int, cap_entries: int):
+        z = lambda n, dt: torch.zeros(max(n, 1), dtype=dt).pin_memory()
+        return cls(z(3 * cap_blocks, torch.int32).view(-1, 3), z(cap_blocks, torch.int32),
+                   z(cap_blocks, torch.int32), z(cap_blocks, torch.int32),
+                   z(cap_entries, torch.int16), z(cap_entries, torch.uint8))
+
+    def c_struct(self) -> V.vbh_mc_stream_host:
+        cs = self.__dict__.get("_cs")
+        if cs is None:
+            cs = self.__dict__["_cs"] = V.vbh_mc_stream_host(
+                self.keys3.data_ptr(), self.info.data_ptr(), self.offsets.data_ptr(),
+                self.counts.data_ptr(), self.local.data_ptr(), self.index.data_ptr(),
+                self.info.shape[0], self.local.shape[0], 0, 0, 0, 0)
+        return cs
+
+    @property
+    def done(self) -> bool:
+        return bool(self.c_struct().done)
+
+    @property
+    def n(self) -> tuple[int, int]:
+        """(records, entries) the frame produced (valid once done)."""
+        cs = self.c_struct()
+        return cs.n_blocks, cs.n_entries
+
+    def to_host(self):
+        """{(x, y, z): (info, local idx array, cube idx array)} of the frame's records."""
+        cs = self.c_struct()
+        if not cs.done:
+            raise RuntimeError("frame not complete")
+        nb, ne = cs.n_blocks, cs.n_entries
+        if nb > self.info.shape[0] or ne > self.local.shape[0]:
+            raise RuntimeError(f"stream overflow: {nb} blocks / {ne} entries")
+        keys = self.keys3[:nb].numpy()
+        info = self.info[:nb].numpy().view(np.uint32)
+        off = self.offsets[:nb].numpy().view(np.uint32)
+        cnt = self.counts[:nb].numpy().view(np.uint32)
+        loc = self.local[:ne].numpy().view(np.uint16)
+        idx = self.index[:ne].numpy()
+        out = {}
+        for i in range(nb):
+            k = tuple(int(x) for x in keys[i])
+            if k in out:
+                raise RuntimeError(f"block {k} emitted twice")
+            o, c = int(off[i]), int(cnt[i])
+            out[k] = (int(info[i]), loc[o:o + c].copy(), idx[o:o + c].copy())
+        return out
+
+
 class Volume:
     """Voxel-block TSDF volume on one GPU (Sec. 4.1 fusion, Sec. 4.2 MC indices)."""
 
@@ -158,6 +218,24 @@ class Volume:
         s = stream or self.stream
         V.vbh_process_frame(self.h, depth, T_wc, frame_id, erase_radius, s.c_struct())
         return s
+
+    def process_frame_host(self, depth_host, T_wc, frame_id: int, erase_radius: float,
+                           out: HostStream) -> int:
+        """The frame from host depth (pinned uint16 for overlap) with its MC stream copied into
+        `out` (pinned host buffers) while the next frame runs: enqueues this frame and returns
+        once the previous call's `out` is complete (status VBH_OK or VBH_ERR_BUFFER_TOO_SMALL);
+        process_frame_host_flush completes the last one."""
+        if isinstance(depth_host, torch.Tensor):
+            assert depth_host.dtype == torch.uint16 and not depth_host.is_cuda
+            assert depth_host.is_contiguous()
+        else:
+            assert depth_host.dtype == np.uint16 and depth_host.flags["C_CONTIGUOUS"]
+        assert tuple(depth_host.shape) == (self.cfg.height, self.cfg.width)
+        return V.vbh_process_frame_host(self.h, depth_host, T_wc, frame_id, erase_radius,
+                                        out.c_struct())
+
+    def process_frame_host_flush(self) -> int:
+        return V.vbh_process_frame_host_flush(self.h)
 
     def erase_radius(self, centre, radius, keys_out: bool = True):
         sel = V.vbh_erase_selector(mode=V.VBH_ERASE_RADIUS, radius=float(radius))
