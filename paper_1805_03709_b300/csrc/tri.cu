@@ -25,9 +25,12 @@ namespace vbh {
 
 namespace {
 
-__constant__ unsigned char c_tri_n[256];
-__constant__ unsigned char c_tri_e[256][15];
-__constant__ unsigned char c_mid2[12][3];   // 2 x edge midpoint (0, 1 or 2 per axis)
+// The tables in device memory; every CTA of the kernel copies them to shared memory, where the
+// lanes' different cube cases are read without the serialisation of divergent constant reads.
+__device__ __align__(4) unsigned char g_tri_n[256];
+__device__ __align__(4) unsigned char g_tri_e[256 * 15];
+// 2 x edge midpoint (0, 1 or 2 per axis), padded to whole words
+__device__ __align__(4) unsigned char g_mid2[12 * 3 + 4];
 
 constexpr int kCube[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
                              {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
@@ -152,9 +155,10 @@ vbh_status upload_tables() {
   if ((int)g_tri_ready.size() <= dev) g_tri_ready.resize(dev + 1, 0);
   if (g_tri_ready[dev]) return VBH_OK;
   static const Tables T = derive_tables();
-  VBH_CUDA(cudaMemcpyToSymbol(c_tri_n, T.n, sizeof T.n));
-  VBH_CUDA(cudaMemcpyToSymbol(c_tri_e, T.e, sizeof T.e));
-  VBH_CUDA(cudaMemcpyToSymbol(c_mid2, T.mid2, sizeof T.mid2));
+  static_assert(sizeof T.n == 256 && sizeof T.e == 256 * 15 && sizeof T.mid2 == 36, "tables");
+  VBH_CUDA(cudaMemcpyToSymbol(g_tri_n, T.n, sizeof T.n));
+  VBH_CUDA(cudaMemcpyToSymbol(g_tri_e, T.e, sizeof T.e));
+  VBH_CUDA(cudaMemcpyToSymbol(g_mid2, T.mid2, sizeof T.mid2));
   g_tri_ready[dev] = 1;
   return VBH_OK;
 }
@@ -167,6 +171,14 @@ __global__ void __launch_bounds__(kTriThreads) k_mc_triangulate(
     unsigned int cap_blocks, unsigned int cap_entries, float half_s, float* tris,
     unsigned int cap_tris, unsigned int* n_tris) {
   __shared__ unsigned int s_warp[kTriThreads / 32], s_base;
+  __shared__ __align__(4) unsigned char s_n[256], s_e[256 * 15], s_mid[12 * 3 + 4];
+  for (unsigned int i = threadIdx.x; i < 64u; i += kTriThreads)
+    reinterpret_cast<unsigned int*>(s_n)[i] = reinterpret_cast<const unsigned int*>(g_tri_n)[i];
+  for (unsigned int i = threadIdx.x; i < 960u; i += kTriThreads)
+    reinterpret_cast<unsigned int*>(s_e)[i] = reinterpret_cast<const unsigned int*>(g_tri_e)[i];
+  for (unsigned int i = threadIdx.x; i < 10u; i += kTriThreads)
+    reinterpret_cast<unsigned int*>(s_mid)[i] = reinterpret_cast<const unsigned int*>(g_mid2)[i];
+  __syncthreads();
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int nb = min(*n_blocks_dev, cap_blocks);
   const unsigned int per_round = gridDim.x * (kTriThreads / 32);
@@ -184,7 +196,7 @@ __global__ void __launch_bounds__(kTriThreads) k_mc_triangulate(
       kz = keys3[3u * r + 2];
     }
     unsigned int mine = 0;
-    for (unsigned int e = lane; e < cnt; e += 32u) mine += c_tri_n[index[off + e]];
+    for (unsigned int e = lane; e < cnt; e += 32u) mine += s_n[index[off + e]];
     unsigned int incl = mine;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -209,15 +221,16 @@ __global__ void __launch_bounds__(kTriThreads) k_mc_triangulate(
       const unsigned int l = local[off + e];
       const int gx2 = 2 * (8 * kx + (int)(l & 7u)), gy2 = 2 * (8 * ky + (int)((l >> 3) & 7u)),
                 gz2 = 2 * (8 * kz + (int)(l >> 6));
-      for (unsigned int t = 0; t < c_tri_n[ci]; ++t, ++o) {
+      const unsigned int nt = s_n[ci];
+      for (unsigned int t = 0; t < nt; ++t, ++o) {
         if (o >= cap_tris) continue;
         float* dst = tris + 9ull * o;
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          const unsigned int ed = c_tri_e[ci][3 * t + v];
-          dst[3 * v] = __fmul_rn((float)(gx2 + c_mid2[ed][0]), half_s);
-          dst[3 * v + 1] = __fmul_rn((float)(gy2 + c_mid2[ed][1]), half_s);
-          dst[3 * v + 2] = __fmul_rn((float)(gz2 + c_mid2[ed][2]), half_s);
+          const unsigned int ed = s_e[15u * ci + 3u * t + v];
+          dst[3 * v] = __fmul_rn((float)(gx2 + s_mid[3u * ed]), half_s);
+          dst[3 * v + 1] = __fmul_rn((float)(gy2 + s_mid[3u * ed + 1u]), half_s);
+          dst[3 * v + 2] = __fmul_rn((float)(gz2 + s_mid[3u * ed + 2u]), half_s);
         }
       }
     }
@@ -254,7 +267,7 @@ vbh_status vbh_mc_triangulate(const vbh_mc_stream* in, float voxel_size, float* 
   int dev = 0, sms = 0;
   VBH_CUDA(cudaGetDevice(&dev));
   VBH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  k_mc_triangulate<<<sms * 4, kTriThreads, 0, s>>>(
+  k_mc_triangulate<<<sms * 8, kTriThreads, 0, s>>>(
       in->keys3, in->offsets, in->counts, in->local, in->index, in->n_blocks_dev, in->cap_blocks,
       in->cap_entries, 0.5f * voxel_size, tris_dev, cap_tris, n_tris_dev);
   VBH_CUDA(cudaGetLastError());
