@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView
                                                            unsigned long long* removed,
                                                            unsigned int removed_cap,
                                                            int* out_keys3, StreamList so) {
-  __shared__ unsigned int s_erased, s_err;
-  if (threadIdx.x == 0) { s_erased = 0; s_err = 0; }
+  __shared__ unsigned int s_erased, s_err, s_emptied;
+  if (threadIdx.x == 0) { s_erased = 0; s_err = 0; s_emptied = 0; }
   __syncthreads();
   const unsigned int mode = ctl->do_erase;
   if (!mode) return;   // uniform across the grid
@@ -85,8 +85,13 @@ __global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView
       }
       if (out) {
         unsigned int val;
-        unsigned int pos = thread_find(t, key, &val);
-        if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;
+        bool bucket_empty = false;
+        const unsigned int pos = thread_find(t, key, &val, &bucket_empty);
+        if (pos != kNone) {
+          const int how = erase_found(t, pos, key, bucket_empty);
+          erased = how != 0;
+          if (how == 1) atomicAdd(&s_emptied, 1u);
+        }
       }
     }
     finish_removal(erased, p, key, pool, cnt, removed, removed_cap, out_keys3, so, &s_erased,
@@ -96,7 +101,8 @@ __global__ void __launch_bounds__(kThreads) k_erase_radius(TableView t, PoolView
   if (threadIdx.x == 0) {
     if (s_erased) {
       atomicSub(&cnt->n_live, s_erased);
-      atomicAdd(&cnt->n_tomb, s_erased);
+      if (s_emptied) atomicAdd(&cnt->n_empty, s_emptied);
+      if (s_erased > s_emptied) atomicAdd(&cnt->n_tomb, s_erased - s_emptied);
     }
     if (s_err) atomicOr(&cnt->err, s_err);
   }
@@ -108,8 +114,8 @@ __global__ void __launch_bounds__(kThreads) k_erase_keys(TableView t, PoolView p
                                                          unsigned long long* removed,
                                                          unsigned int removed_cap,
                                                          int* out_keys3, StreamList so) {
-  __shared__ unsigned int s_erased, s_err;
-  if (threadIdx.x == 0) { s_erased = 0; s_err = 0; }
+  __shared__ unsigned int s_erased, s_err, s_emptied;
+  if (threadIdx.x == 0) { s_erased = 0; s_err = 0; s_emptied = 0; }
   __syncthreads();
   const unsigned int stride = gridDim.x * blockDim.x;
   const unsigned int rounds = (n + stride - 1u) / stride;
@@ -122,8 +128,13 @@ __global__ void __launch_bounds__(kThreads) k_erase_keys(TableView t, PoolView p
       const int x = keys3[3u * i], y = keys3[3u * i + 1], z = keys3[3u * i + 2];
       if (key_ok(x, y, z)) {
         key = pack_key(x, y, z);
-        unsigned int pos = thread_find(t, key, &val);
-        if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;
+        bool bucket_empty = false;
+        const unsigned int pos = thread_find(t, key, &val, &bucket_empty);
+        if (pos != kNone) {
+          const int how = erase_found(t, pos, key, bucket_empty);
+          erased = how != 0;
+          if (how == 1) atomicAdd(&s_emptied, 1u);
+        }
       }
     }
     finish_removal(erased, val, key, pool, cnt, removed, removed_cap, out_keys3, so, &s_erased,
@@ -133,7 +144,8 @@ __global__ void __launch_bounds__(kThreads) k_erase_keys(TableView t, PoolView p
   if (threadIdx.x == 0) {
     if (s_erased) {
       atomicSub(&cnt->n_live, s_erased);
-      atomicAdd(&cnt->n_tomb, s_erased);
+      if (s_emptied) atomicAdd(&cnt->n_empty, s_emptied);
+      if (s_erased > s_emptied) atomicAdd(&cnt->n_tomb, s_erased - s_emptied);
     }
     if (s_err) atomicOr(&cnt->err, s_err);
   }

@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
                                                     const unsigned char* ops, const int* keys3,
                                                     unsigned int* res, unsigned char* st,
                                                     unsigned int n) {
-  __shared__ unsigned int s_erased;
-  if (threadIdx.x == 0) s_erased = 0;
+  __shared__ unsigned int s_erased, s_emptied;
+  if (threadIdx.x == 0) { s_erased = 0; s_emptied = 0; }
   __syncthreads();
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int stride = gridDim.x * blockDim.x;
@@ -301,12 +301,14 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
     const unsigned int i = base + lane;
     unsigned long long key = 0;
     const bool doit = i < n && ops[i] == kOpErase && load_key3(keys3, i, &key);
-    bool erased = false;
+    int how = 0;
     unsigned int val = kNone;
     if (doit) {
-      const unsigned int pos = thread_find(t, key, &val);
-      if (pos != kNone) erased = atomicCAS(&t.slots[pos].key, key, kTomb) == key;
+      bool bucket_empty = false;
+      const unsigned int pos = thread_find(t, key, &val, &bucket_empty);
+      if (pos != kNone) how = erase_found(t, pos, key, bucket_empty);
     }
+    const bool erased = how != 0;
     const bool push = erased && pool.max_blocks;
     unsigned int k = warp_append(reinterpret_cast<unsigned int*>(&cnt->free_top), push,
                                  0xFFFFFFFFu);
@@ -321,12 +323,17 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
       st[i] = erased ? kStErased : kStNotFound;
     }
     const unsigned int n_er = __popc(__ballot_sync(0xFFFFFFFFu, erased));
-    if (lane == 0 && n_er) atomicAdd(&s_erased, n_er);
+    const unsigned int n_em = __popc(__ballot_sync(0xFFFFFFFFu, how == 1));
+    if (lane == 0 && n_er) {
+      atomicAdd(&s_erased, n_er);
+      if (n_em) atomicAdd(&s_emptied, n_em);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0 && s_erased) {
     atomicSub(&cnt->n_live, s_erased);
-    atomicAdd(&cnt->n_tomb, s_erased);
+    if (s_emptied) atomicAdd(&cnt->n_empty, s_emptied);
+    if (s_erased > s_emptied) atomicAdd(&cnt->n_tomb, s_erased - s_emptied);
   }
 }
 

@@ -193,10 +193,12 @@ __device__ __forceinline__ ulonglong2 bucket_slot(const ulonglong2 (&s)[4], int 
 }
 
 // Find by one thread: walk the buckets from the key's home bucket until the key or a bucket
-// with an EMPTY slot.  Returns the slot index or kNone; *val receives the value.
+// with an EMPTY slot.  Returns the slot index or kNone; *val receives the value and, if given,
+// *bucket_empty whether the key's bucket held an EMPTY slot when it was read.
 template <bool kReadOnly = false>
 __device__ __forceinline__ unsigned int thread_find(const TableView& t, unsigned long long key,
-                                                    unsigned int* val) {
+                                                    unsigned int* val,
+                                                    bool* bucket_empty = nullptr) {
   unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
   for (unsigned int probe = 0; probe <= t.bmask; ++probe, b = (b + 1u) & t.bmask) {
     ulonglong2 s[4];
@@ -210,12 +212,26 @@ __device__ __forceinline__ unsigned int thread_find(const TableView& t, unsigned
     }
     if (hit >= 0) {
       *val = (unsigned)bucket_slot(s, hit).y;
+      if (bucket_empty) *bucket_empty = empty;
       return 4u * b + hit;
     }
     if (empty) break;
   }
   *val = kNone;
   return kNone;
+}
+
+// Erase phase: remove `key` from the slot thread_find returned.  The slot becomes EMPTY when its
+// bucket already held an EMPTY slot: every find that reaches the bucket stops there anyway, so
+// no probe sequence changes (no live key has a bucket with an EMPTY slot between its home
+// bucket and its own, and such buckets only gain EMPTY slots this way), and the slot ends the
+// chains of later inserts as a never-used slot would.  Otherwise it becomes a tombstone.
+// Returns 0 (another erase got there first), 1 (now EMPTY) or 2 (now a tombstone).
+__device__ __forceinline__ int erase_found(const TableView& t, unsigned int pos,
+                                           unsigned long long key, bool bucket_empty) {
+  const unsigned long long to = bucket_empty ? kEmpty : kTomb;
+  if (atomicCAS(&t.slots[pos].key, key, to) != key) return 0;
+  return bucket_empty ? 1 : 2;
 }
 
 // Warp-aggregated append: every lane with `pred` gets a distinct index from *counter.

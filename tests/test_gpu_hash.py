@@ -153,6 +153,8 @@ def test_full_table_reports_capacity_and_recovers():
     lost = keys[sg == V.VBH_ST_CAPACITY]
     # erase two, then the lost keys can go in (tombstones are reused)
     gpu_batch(hm, np.full(2, V.VBH_OP_ERASE, np.uint8), ins[:2], None)
+    c = hm.counters()
+    assert (c.live, c.tombstones, c.empty) == (14, 2, 0)   # full buckets: tombstones
     rg, sg = gpu_batch(hm, np.full(2, V.VBH_OP_INSERT, np.uint8), lost[:2], key_value(lost[:2]))
     assert np.all(sg == V.VBH_ST_INSERTED)
     back = np.concatenate([ins[2:], lost[:2]])
@@ -163,6 +165,37 @@ def test_full_table_reports_capacity_and_recovers():
     with pytest.raises(ValueError):
         hm.batch(torch.zeros(18, dtype=torch.uint8, device="cuda"),
                  torch.from_numpy(np.ascontiguousarray(back)).cuda())
+
+
+def test_erase_beside_an_empty_slot_leaves_no_tombstone():
+    """An erased slot whose bucket still holds a never-used slot becomes never-used itself (no
+    find's probe sequence changes); keys that overflowed into later buckets stay findable."""
+    hm = HashMap(n_buckets=1 << 10)
+    om = OracleMap()
+    keys = synth.random_hash_keys(200, seed=11)
+    vals = key_value(keys)
+    gpu_batch(hm, np.ones(200, np.uint8), keys, vals)
+    om.batch(np.ones(200, np.uint8), keys, vals)
+    rg, sg = gpu_batch(hm, np.full(100, 2, np.uint8), keys[::2], None)
+    om.batch(np.full(100, 2, np.uint8), keys[::2], None)
+    assert np.all(sg == V.VBH_ST_ERASED)
+    c = hm.counters()
+    assert c.live == 100 and c.tombstones == 0 and c.empty == 4096 - 100
+    check_contents(hm, om)
+    # a crowded small table: overflow chains, erases both ways, finds stay exact
+    hm2 = HashMap(n_buckets=16)
+    om2 = OracleMap()
+    rng = np.random.default_rng(5)
+    pool = synth.random_hash_keys(56, seed=12)
+    gpu_batch(hm2, np.ones(56, np.uint8), pool, key_value(pool))
+    om2.batch(np.ones(56, np.uint8), pool, key_value(pool))
+    for _ in range(20):
+        ops = rng.choice([0, 1, 2], size=40, p=[0.4, 0.3, 0.3]).astype(np.uint8)
+        k = pool[rng.integers(0, 56, size=40)]
+        rg, sg = gpu_batch(hm2, ops, k, key_value(k))
+        ro, so = om2.batch(ops, k, key_value(k))
+        assert_same(ops, k, rg, sg, ro, so)
+    check_contents(hm2, om2)
 
 
 @pytest.mark.parametrize("lf", [0.5, 0.7, 0.9])
