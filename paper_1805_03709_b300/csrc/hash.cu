@@ -446,10 +446,17 @@ __global__ void k_pack_keys(const int* keys3, unsigned int n, unsigned long long
   static int grid_##kernel = 0;                                    \
   if (!grid_##kernel) grid_##kernel = persistent_grid(kernel, threads, L.sms)
 
+// A batch of n ops needs no more CTAs than it has ops per CTA-wide round (small batches would
+// otherwise launch the whole persistent grid for a handful of ops).
+inline unsigned int fit_grid(int persistent, unsigned int n) {
+  const unsigned int need = (n + kThreads - 1u) / kThreads;
+  return need < 1u ? 1u : (need < (unsigned int)persistent ? need : (unsigned int)persistent);
+}
+
 void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsigned char* ops,
                       const int* keys3, unsigned int* res, unsigned char* st, unsigned int n) {
   VBH_GRID(k_find, kThreads);
-  k_find<<<grid_k_find, kThreads, 0, L.stream>>>(t, cnt, ops, keys3, res, st, n);
+  k_find<<<fit_grid(grid_k_find, n), kThreads, 0, L.stream>>>(t, cnt, ops, keys3, res, st, n);
 }
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                         const unsigned char* ops, const int* keys3,
@@ -457,8 +464,8 @@ void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters
                         const unsigned int* vals, unsigned int* res, unsigned char* st,
                         unsigned int n) {
   VBH_GRID(k_insert, kThreads);
-  k_insert<<<grid_k_insert, kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, pkeys, count_dev,
-                                                      vals, res, st, n);
+  k_insert<<<fit_grid(grid_k_insert, n), kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, pkeys,
+                                                                    count_dev, vals, res, st, n);
 }
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
@@ -466,15 +473,15 @@ void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevC
                                unsigned long long* tkey, float2* tdepth,
                                unsigned int* n_touched, const FrameCtl* ctl) {
   VBH_GRID(k_insert_finish, kThreads);
-  k_insert_finish<<<grid_k_insert_finish, kThreads, 0, L.stream>>>(t, pool, cnt, count_dev, res,
-                                                                    st, n, touched, tkey, tdepth,
-                                                                    n_touched, ctl);
+  k_insert_finish<<<fit_grid(grid_k_insert_finish, n), kThreads, 0, L.stream>>>(
+      t, pool, cnt, count_dev, res, st, n, touched, tkey, tdepth, n_touched, ctl);
 }
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const unsigned char* ops, const int* keys3, unsigned int* res,
                        unsigned char* st, unsigned int n) {
   VBH_GRID(k_erase, kThreads);
-  k_erase<<<grid_k_erase, kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, res, st, n);
+  k_erase<<<fit_grid(grid_k_erase, n), kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, res, st,
+                                                                  n);
 }
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt) {
