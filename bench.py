@@ -342,11 +342,15 @@ def main():
         ms_total = float(t.item())
     clk = clocks.stop()
 
-    # roofline of the dominant kernel (fusion): bytes it must move per launch
+    # roofline of the dominant kernel (fusion) with the algorithmic bytes of integration: 8 B
+    # read + 8 B written per voxel of each touched block and the depth image once per launch.
+    # The kernel itself moves less (new blocks are not read, voxels it does not update are not
+    # written, plus 128 B of masks per block): reported beside it as `kernel_bytes_per_launch`.
     n_launch = max(int(stage_launch["integrate"]), 1)
     depth_bytes = cam.width * cam.height * 2
-    alg_bytes = ((touched - new) * 512 * 8 + written * 8 + touched * 128 +
-                 args.steps * depth_bytes)
+    alg_bytes = touched * 512 * 16 + args.steps * depth_bytes
+    kernel_bytes = ((touched - new) * 512 * 8 + written * 8 + touched * 128 +
+                    args.steps * depth_bytes)
     integ_ms = stage_ms["integrate"]
     achieved = alg_bytes / n_launch / (integ_ms / n_launch / 1e3) / 1e9 if integ_ms > 0 else 0.0
     peak, peak_src = measured_peak()
@@ -514,6 +518,12 @@ def main():
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tr,
                          "algorithmic_bytes_per_launch": alg_bytes / n_launch,
+                         "definition": "8 B read + 8 B written per voxel of each touched block "
+                                       "+ the depth image once",
+                         "kernel_bytes_per_launch": kernel_bytes / n_launch,
+                         "kernel_bytes_GBs": (kernel_bytes / n_launch /
+                                              (integ_ms / n_launch / 1e3) / 1e9
+                                              if integ_ms > 0 else 0.0),
                          "avg_launch_ms": integ_ms / n_launch,
                          "share_of_step": integ_ms / ms_total if ms_total else None},
             "roofline_mc": mc_line, "roofline_frame": frame_line,
@@ -749,7 +759,7 @@ def visible_point(torch, cam, D, poses, flush, args, peak):
     new = int(c1.total_new - c0.total_new)
     written = int(c1.total_written - c0.total_written)
     n = max(int(stage_n["integrate"]), 1)
-    alg = ((touched - new) * 4096 + written * 8 + touched * 128 + cam.width * cam.height * 2) / n
+    alg = (touched * 512 * 16 + cam.width * cam.height * 2) / n
     integ_ms = stage_ms["integrate"] / n
     vol.close()
     ach = alg / (integ_ms / 1e3) / 1e9
