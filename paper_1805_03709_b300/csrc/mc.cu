@@ -359,15 +359,18 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
       if (fill + tot > kStage || nblk == kStageBlocks) flush();
       unsigned int o = fill + incl - mine;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int row = (int)lane + 32 * h;
-        unsigned long long bits = nz[h];
-        while (bits) {
-          const int x = (__ffsll((long long)bits) - 1) >> 3;
-          st_loc[o] = (unsigned short)(x + 8 * row);
-          st_idx[o] = (unsigned char)(idx8[h] >> (8 * x));
-          ++o;
-          bits &= bits - 1ull;
+      for (int h = 0; h < 2; ++h) {   // the row's nonzero cubes, in x order, with no divergence
+        const unsigned int base_loc = 8u * (lane + 32u * h);
+        const unsigned int n_lo = (unsigned int)nz[h], n_hi = (unsigned int)(nz[h] >> 32);
+        const unsigned int i_lo = (unsigned int)idx8[h], i_hi = (unsigned int)(idx8[h] >> 32);
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          const unsigned int nw = x < 4 ? n_lo : n_hi, iw = x < 4 ? i_lo : i_hi;
+          if ((nw >> (8 * (x & 3) + 7)) & 1u) {
+            st_loc[o] = (unsigned short)(base_loc + x);
+            st_idx[o] = (unsigned char)(iw >> (8 * (x & 3)));
+            ++o;
+          }
         }
       }
       if (lane == 0) {
