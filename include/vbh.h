@@ -266,7 +266,8 @@ typedef struct {
  * (the status of that completion is returned: VBH_ERR_BUFFER_TOO_SMALL if it was cut);
  * vbh_process_frame_host_flush completes the last frame.  Each out_host must stay valid until
  * its frame is done.  Host-visible synchronisation is with the previous frame only, so the copy
- * in, the frame and the copy out of consecutive frames overlap. */
+ * in, the frame and the copy out of consecutive frames overlap.  vbh_destroy waits for the
+ * frames in flight but does not complete a frame that was not flushed (its `done` stays 0). */
 vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
                                   const float* T_wc_host, uint32_t frame_id, float erase_radius,
                                   vbh_mc_stream_host* out_host);
