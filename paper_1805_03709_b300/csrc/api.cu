@@ -81,7 +81,7 @@ __global__ void k_setup_frame(const FrameCtl c, unsigned long long seq,
   cnt->n_mset = 0;
   cnt->n_tombrec = 0;
   if (c.n_entries_dev) *c.n_entries_dev = 0;
-  __threadfence_system();
+  // only a bound on the frames the host queues: no ordering with the writes above is needed
   *reinterpret_cast<volatile unsigned long long*>(consumed) = seq + 1;
 }
 

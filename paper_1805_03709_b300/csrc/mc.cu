@@ -29,7 +29,10 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMcThreads = 128;   // 4 warps, one block each
 constexpr unsigned int kStage = 1024;        // MC entries staged per warp (>= 512, one block)
-constexpr unsigned int kStageBlocks = 16;    // blocks staged per warp (<= 32)
+#ifndef VBH_MC_STAGE_BLOCKS
+#define VBH_MC_STAGE_BLOCKS 16
+#endif
+constexpr unsigned int kStageBlocks = VBH_MC_STAGE_BLOCKS;   // blocks staged per warp (<= 32)
 constexpr unsigned long long kLo7 = 0x7F7F7F7F7F7F7F7Full;
 constexpr unsigned long long kHi1 = 0x8080808080808080ull;
 
