@@ -282,6 +282,8 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
   CREATE_CUDA(cudaMalloc(&h->cnt, sizeof(DevCounters)));
   CREATE_CUDA(cudaMalloc(&h->ctl, sizeof(FrameCtl)));
   CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+  for (auto& e : h->fork_ev) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   {
     unsigned long long* ch = nullptr;
     CREATE_CUDA(cudaHostAlloc(&ch, sizeof(unsigned long long), cudaHostAllocMapped));
@@ -345,6 +347,9 @@ vbh_status vbh_destroy(vbh_handle* h) {
   if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
   if (h->frame_graph) cudaGraphDestroy(h->frame_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+  for (cudaEvent_t e : h->fork_ev)
+    if (e) cudaEventDestroy(e);
   if (h->consumed_host) cudaFreeHost((void*)h->consumed_host);
   void* ptrs[] = {h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
                   h->version, h->stack, h->seq, h->cand, h->cand_res, h->cand_st, h->touched, h->tdepth, h->tkey, h->mset,
@@ -482,10 +487,20 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   // the root node takes the control block by value: vbh_process_frame patches it
   k_setup_frame<<<1, 1, 0, h->cap_stream>>>(base_ctl(h, nullptr), 0ull, h->consumed_dev, h->ctl,
                                             h->cnt);
+  // Two pairs of independent kernels run as parallel branches of the graph, so that the one
+  // that leaves issue slots idle fills them beside the other: the band allocation (it reads the
+  // depth image and writes the candidate list only) beside the erase (table, pool, removal and
+  // stream-out lists), and the MC set (touched and removed lists, keys, table, marks, versions)
+  // beside the fusion (voxels, masks, fresh states).
+  const Launch L2{h->cap_stream2, h->L.sms};
+  VBH_CUDA(cudaEventRecord(h->fork_ev[0], h->cap_stream));
+  VBH_CUDA(cudaStreamWaitEvent(h->cap_stream2, h->fork_ev[0], 0));
+  launch_alloc_keys(L2, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
+  VBH_CUDA(cudaEventRecord(h->fork_ev[1], h->cap_stream2));
   launch_erase_radius(Lc, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks, nullptr,
                       nullptr, stream_list(h));
   if (h->so) launch_stream_gather(Lc, h->so_ring, h->ctl, pool, h->cnt, stream_list(h));
-  launch_alloc_keys(Lc, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
+  VBH_CUDA(cudaStreamWaitEvent(h->cap_stream, h->fork_ev[1], 0));
   launch_hash_insert(Lc, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(Lc, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
@@ -493,13 +508,17 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
                             h->ctl);
   if (h->integ_mode == VBH_INTEGRATE_VISIBLE)
     launch_visible(Lc, h->ctl, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched);
+  VBH_CUDA(cudaEventRecord(h->fork_ev[2], h->cap_stream));
+  VBH_CUDA(cudaStreamWaitEvent(h->cap_stream2, h->fork_ev[2], 0));
+  launch_mset_touched(L2, t, pool, h->cnt, h->ctl, h->touched, &h->cnt->n_touched, h->removed,
+                      &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec);
+  VBH_CUDA(cudaEventRecord(h->fork_ev[3], h->cap_stream2));
   if (t_int) cudaEventRecordWithFlags(ev[0], h->cap_stream, cudaEventRecordExternal);
   // the fusion node takes the frame parameters by value: vbh_process_frame patches them
   launch_integrate(Lc, base_ctl(h, nullptr).fp, pool, h->touched, h->tkey, h->tdepth,
                    &h->cnt->n_touched, h->cnt);
   if (t_int) cudaEventRecordWithFlags(ev[1], h->cap_stream, cudaEventRecordExternal);
-  launch_mset_touched(Lc, t, pool, h->cnt, h->ctl, h->touched, &h->cnt->n_touched, h->removed,
-                      &h->cnt->n_removed, h->cfg.max_blocks, h->mset, h->tombrec);
+  VBH_CUDA(cudaStreamWaitEvent(h->cap_stream, h->fork_ev[3], 0));
   if (t_mc) cudaEventRecordWithFlags(ev[2], h->cap_stream, cudaEventRecordExternal);
   launch_mc_extract(Lc, t, pool, h->cnt, h->ctl, h->mset, h->tombrec);
   if (t_mc) cudaEventRecordWithFlags(ev[3], h->cap_stream, cudaEventRecordExternal);

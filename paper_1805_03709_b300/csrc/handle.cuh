@@ -88,6 +88,8 @@ struct vbh_handle {
   unsigned int* last_entries = nullptr;   // n_entries_dev of the last extraction
   // whole-frame CUDA graph (vbh_process_frame)
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream2 = nullptr;            // the frame graph's second branch (capture)
+  cudaEvent_t fork_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // its fork / join points
   cudaGraph_t frame_graph = nullptr;
   cudaGraphExec_t frame_exec = nullptr;
   // the control block of each vbh_process_frame is the by-value argument of the graph's root
