@@ -4,17 +4,21 @@
 // Guarantees (Sec. 5: concurrent retrieval, insertion and removal succeed and keys stay unique,
 // which the paper obtains with per-entry locks and an excess list; here with CAS claims):
 //   * A launch runs one phase only: finds (read-only), inserts (slots only go free -> key),
-//     or erases (slots only go key -> tombstone).  The host orders the phases of a batch.
+//     or erases (slots only go key -> tombstone, or key -> EMPTY in a bucket that already holds
+//     an EMPTY slot).  The host orders the phases of a batch.
 //   * A live key never moves (the paper's invariant that entry positions are preserved), so a
 //     find needs no lock: it walks the buckets from the key's home bucket until it meets the
-//     key or a bucket with a never-used (EMPTY) slot.  Tombstones keep chains intact.
+//     key or a bucket with a never-used (EMPTY) slot.  Tombstones keep chains intact, and an
+//     erase makes a slot EMPTY only where a find would stop anyway.
+//   * A plain map's batch: the winner of an insert writes its value and final result at once;
+//     inserts that met their key take the value in a follow-up launch (skipped when none did).
 //   * Insert: pass 1 walks the chain to its end; if the key is absent it remembers the first
 //     free slot (tombstone or EMPTY).  Pass 2 claims free slots in probe order from there with
 //     a 64-bit CAS, re-reading a bucket after a lost CAS.  Because no slot becomes free during
 //     an insert launch, two inserters of one key always meet at the same first free slot, so
 //     exactly one CAS succeeds and the other sees the key (uniqueness).
 //   * The winner writes the value after the claim; duplicates record only the slot and read the
-//     value in a follow-up launch, so nobody reads a half-written entry.
+//     value in the follow-up launch, so nobody reads a half-written entry.
 #include "vbh_internal.cuh"
 
 namespace vbh {
