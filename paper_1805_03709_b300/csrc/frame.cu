@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
         const float au = __fdiv_rn(__fsub_rn((float)pu, fp.cx), fp.fx);
         const float av = __fdiv_rn(__fsub_rn((float)pv, fp.cy), fp.fy);
         const float z0 = __fsub_rn(d, fp.mu);
-        unsigned long long prev = kEmpty;
+        float pq0 = 0.0f, pq1 = 0.0f, pq2 = 0.0f;   // the previous sample's block
+        bool have_prev = false;
         for (int j = 0; j <= fp.J; ++j) {
           const float z = __fmaf_rn((float)j, fp.s, z0);
           if (!(z > 0.0f)) continue;
@@ -78,14 +79,22 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
             x = __fmaf_rn(fp.R[3 * i + 2], z, x);
             q[i] = floorf(__fmul_rn(x, fp.inv_bs));
           }
+          // consecutive samples usually share a block: compared before anything else is done
+          // with it (a repeated block had the same range test and set insertion already)
+          if (have_prev && q[0] == pq0 && q[1] == pq1 && q[2] == pq2) continue;
+          have_prev = true;
+          pq0 = q[0];
+          pq1 = q[1];
+          pq2 = q[2];
           bool ok = true;
 #pragma unroll
           for (int i = 0; i < 3; ++i) ok = ok && q[i] >= -1048576.0f && q[i] < 1048576.0f;
           if (!ok) continue;
-          const unsigned long long key = pack_key((int)q[0], (int)q[1], (int)q[2]);
-          if (key == prev) continue;   // consecutive samples usually share a block
-          prev = key;
-          unsigned int h = hash_mix(key) & (kTileSet - 1);
+          const int kx = (int)q[0], ky = (int)q[1], kz = (int)q[2];
+          const unsigned long long key = pack_key(kx, ky, kz);
+          // slot in the tile's set: a 32-bit mix of the coordinates (the set is small and local)
+          unsigned int h = ((unsigned int)kx * 73856093u ^ (unsigned int)ky * 19349669u ^
+                            (unsigned int)kz * 83492791u) & (kTileSet - 1);
           bool placed = false;
           for (int probe = 0; probe < 64; ++probe) {
             const unsigned long long seen = set[h];   // most keys are already in the set
