@@ -503,7 +503,13 @@ def main():
         sets_pt = sets_point(torch, cam, D, poses)
     serve_pt = None
     if not args.no_serve and rank == 0:
-        serve_pt = serve_point(torch, cam, D, poses, peak, args.serve_seconds)
+        serve_pt = serve_point(torch, cam, D, poses, peak, args.serve_seconds, reps=5)
+        # the same clients at ten times the request rate: requests queue, and batching has
+        # concurrent requests to merge
+        heavy = serve_point(torch, cam, D, poses, peak, 2.0, rate=200.0, reps=3,
+                            saturated=False)
+        serve_pt["heavy_load"] = {k: heavy[k] for k in ("rate_per_client", "duration_s",
+                                                        "requests", "batched", "unbatched")}
 
     if rank == 0:
         line = {
@@ -833,7 +839,7 @@ def mc_replay(torch, cam, D, poses, args):
 
 
 def serve_point(torch, cam, D, poses, peak, duration_s=4.0, n_clients=64, rate=20.0,
-                warm_frames=30, seed=1805, reps=3):
+                warm_frames=30, seed=1805, reps=3, saturated=True):
     """Multi-client streaming: the room volume updated live at 30 frames/s (frames warm_frames
     onwards of the sequence) while n_clients clients with Poisson arrivals (rate requests/s
     each) ask for the MC blocks changed since their last version; initial backlogs log-uniform
@@ -897,7 +903,7 @@ def serve_point(torch, cam, D, poses, peak, duration_s=4.0, n_clients=64, rate=2
                 "deferred_by_memory": int(st["deferred_memory"]),
                 "peak_buffer_bytes": int(st["bytes_peak"]),
                 "errors": sum(1 for d in done if d["flags"] & ~3)})
-            if name == "batched" and sat is None:
+            if name == "batched" and sat is None and saturated:
                 # one saturated launch: every client 4096 blocks behind, all in one batch
                 srv.set_policy(max_batch=64, chunk_records=0, iter_records=0)
                 srv.set_versions(np.arange(n_clients),
