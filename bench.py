@@ -376,19 +376,18 @@ def main():
         vol.timing(("mc",))   # MC extraction timed on the replay (kept out of the main loop)
         vol.timing_read(reset=True)
         host_depth = torch.from_numpy(depth).pin_memory()
-        outs = [HostStream.allocate(MAX_BLOCKS, 1 << 23) for _ in range(2)]
+        outs = [HostStream.allocate(MAX_BLOCKS, 1 << 23) for _ in range(3)]
         fl_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                  for _ in range(args.steps)]
         h2d = d2h = 0
-        mc_counts = []
+        nbs = []
         statuses = []
 
-        def account(o):
+        def account(o):   # bytes copied out for the frame (its counts come from the replay)
             nonlocal d2h
             nb, ne = o.n
             d2h += 8 + nb * 24 + ne * 3
-            n_rem = int((o.info[:nb].numpy().view(np.uint32) >> 31).sum())
-            mc_counts.append((nb - n_rem, n_rem, ne))
+            nbs.append((nb, ne))
 
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -399,20 +398,22 @@ def main():
             flush.zero_()
             fl_ev[k][1].record()
             statuses.append(vol.process_frame_host(host_depth[f], poses[f], i + 1, ERASE_R,
-                                                   outs[k % 2]))
+                                                   outs[k % 3]))
             h2d += depth_bytes
-            if k:
-                account(outs[(k - 1) % 2])
+            if k >= 2:   # the frame of two calls earlier is complete
+                account(outs[(k - 2) % 3])
         statuses.append(vol.process_frame_host_flush())
-        account(outs[(args.steps - 1) % 2])
+        for k in range(max(args.steps - 2, 0), args.steps):
+            account(outs[k % 3])
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         flush_s = sum(a.elapsed_time(b) for a, b in fl_ev) / 1e3
         t_e2e = (t1 - t0) - flush_s
         assert all(st == V.VBH_OK for st in statuses), "host stream capacity exceeded"
-        # live blocks after each frame, for the whole-frame roofline (untimed replay)
-        live_after = [c[3] for c in mc_replay(torch, cam, D, poses, args)[0]]
-        mc_counts = [c + (lv,) for c, lv in zip(mc_counts, live_after)]
+        # per frame: live and removal records, entries and the live blocks after it, from an
+        # untimed replay of the same frames (the same totals as the host copies)
+        mc_counts = mc_replay(torch, cam, D, poses, args)[0]
+        assert [(c[0] + c[1], c[2]) for c in mc_counts] == nbs, "replay differs from the e2e run"
         mc_timing = vol.timing_read(reset=True)
         vol.timing(())
         if ws > 1:

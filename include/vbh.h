@@ -260,14 +260,15 @@ typedef struct {
 
 /* vbh_process_frame with host buffers, pipelined (Sec. 4.1-4.2 per frame, as vbh_process_frame):
  * the depth image is copied from host memory (depth_host: width x height uint16, reusable when
- * the call returns), the frame runs on one of two library-owned device streams, and its MC
- * stream is copied into out_host while the next frame is computed.  The call enqueues this
- * frame and returns once the PREVIOUS call's frame is complete in the previous call's out_host
- * (the status of that completion is returned: VBH_ERR_BUFFER_TOO_SMALL if it was cut);
- * vbh_process_frame_host_flush completes the last frame.  Each out_host must stay valid until
- * its frame is done.  Host-visible synchronisation is with the previous frame only, so the copy
- * in, the frame and the copy out of consecutive frames overlap.  vbh_destroy waits for the
- * frames in flight but does not complete a frame that was not flushed (its `done` stays 0). */
+ * the call returns), the frame runs on one of three library-owned device streams, and its MC
+ * stream is copied into out_host while the next frames are computed.  The call enqueues this
+ * frame, starts the copy-out of the previous call's frame if that frame has finished, and
+ * returns once the frame of TWO calls earlier is complete in its out_host (its `done` set; the
+ * status of that completion is returned: VBH_ERR_BUFFER_TOO_SMALL if it was cut); it waits for
+ * the GPU only when the GPU is two frames behind.  vbh_process_frame_host_flush completes every
+ * frame still pending.  Each out_host must stay valid until its frame is done.  vbh_destroy
+ * waits for the frames in flight but does not complete frames that were not flushed (their
+ * `done` stays 0). */
 vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
                                   const float* T_wc_host, uint32_t frame_id, float erase_radius,
                                   vbh_mc_stream_host* out_host);

@@ -1,44 +1,50 @@
-// vbh_process_frame with host buffers, pipelined over consecutive calls.
+// vbh_process_frame with host buffers, pipelined over consecutive calls, three frames deep.
 //
-// Call k (j = k mod 2) enqueues: the depth copy host -> device buffer j on a copy stream (after
-// frame k-2, which read buffer j, has finished), the frame graph on the handle's stream into
-// device stream j (after frame k-2's results, read from stream j, have been copied out), and a
-// copy of frame k's two totals to pinned memory.  It then completes frame k-1: waits for its
-// totals, copies its records and entries (as many as there are, up to the caller's
-// capacities) into the caller's host buffers on the copy stream -- while frame k runs -- and
-// waits for that copy.  So the host waits for one frame at a time and the GPU always has the
-// next frame queued.
+// Call k (j = k mod 3) enqueues: the depth copy host -> device buffer j on a copy stream (after
+// frame k-3, which read buffer j, has finished), the frame graph on the handle's stream into
+// device stream j (after frame k-3's results, read from stream j, have been copied out), and a
+// copy of frame k's two totals to pinned memory.  Then it moves the older frames along: frame
+// k-1's records and entries start their copy into the caller's host buffers if its totals have
+// already landed (no wait), and frame k-2 -- whose copy was started by now, waiting for its
+// totals only if the GPU is two frames behind -- is waited for and marked done.  So the host
+// blocks only when the GPU is behind, and the copy-out of a frame overlaps the next ones.
 #include "handle.cuh"
+
+#include <deque>
 
 namespace vbh {
 
+constexpr int kHostSlots = 3;
+
 struct HostPipe {
+  struct Pending {
+    vbh_mc_stream_host* out;
+    uint32_t frame_id;
+    int j;
+    bool copying;   // its copy-out has been enqueued
+  };
   cudaStream_t copy = nullptr;
-  uint16_t* depth[2] = {nullptr, nullptr};   // device depth images
+  uint16_t* depth[kHostSlots] = {};   // device depth images
   // device output streams and their totals (device) / totals copy (pinned host)
-  int32_t* keys3[2] = {nullptr, nullptr};
-  uint32_t* info[2] = {nullptr, nullptr};
-  uint32_t* offsets[2] = {nullptr, nullptr};
-  uint32_t* counts[2] = {nullptr, nullptr};
-  uint16_t* local[2] = {nullptr, nullptr};
-  uint8_t* index[2] = {nullptr, nullptr};
-  uint32_t* n_dev[2] = {nullptr, nullptr};
-  uint32_t* n_pin[2] = {nullptr, nullptr};
+  int32_t* keys3[kHostSlots] = {};
+  uint32_t* info[kHostSlots] = {};
+  uint32_t* offsets[kHostSlots] = {};
+  uint32_t* counts[kHostSlots] = {};
+  uint16_t* local[kHostSlots] = {};
+  uint8_t* index[kHostSlots] = {};
+  uint32_t* n_dev[kHostSlots] = {};
+  uint32_t* n_pin[kHostSlots] = {};
   uint32_t cap_blocks = 0, cap_entries = 0;
-  cudaEvent_t e_h2d[2] = {nullptr, nullptr}, e_frame[2] = {nullptr, nullptr},
-              e_out[2] = {nullptr, nullptr};
-  bool frame_used[2] = {false, false}, out_used[2] = {false, false};
-  unsigned long long k = 0;   // frames enqueued
-  // the frame enqueued by the previous call, not yet complete
-  vbh_mc_stream_host* pending = nullptr;
-  uint32_t pending_id = 0;
-  int pending_j = 0;
+  cudaEvent_t e_h2d[kHostSlots] = {}, e_frame[kHostSlots] = {}, e_out[kHostSlots] = {};
+  bool frame_used[kHostSlots] = {}, out_used[kHostSlots] = {};
+  unsigned long long k = 0;      // frames enqueued
+  std::deque<Pending> pending;   // enqueued frames not yet done, oldest first
 };
 
 namespace {
 
 void free_streams(HostPipe* p) {
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < kHostSlots; ++j) {
     void* d[] = {p->keys3[j], p->info[j], p->offsets[j], p->counts[j], p->local[j], p->index[j]};
     for (void* q : d)
       if (q) cudaFree(q);
@@ -52,7 +58,7 @@ void free_streams(HostPipe* p) {
 
 vbh_status alloc_streams(HostPipe* p, uint32_t cb, uint32_t ce) {
   free_streams(p);
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < kHostSlots; ++j) {
     VBH_CUDA(cudaMalloc(&p->keys3[j], sizeof(int32_t) * 3ull * cb));
     VBH_CUDA(cudaMalloc(&p->info[j], sizeof(uint32_t) * (size_t)cb));
     VBH_CUDA(cudaMalloc(&p->offsets[j], sizeof(uint32_t) * (size_t)cb));
@@ -70,7 +76,7 @@ vbh_status create_pipe(vbh_handle* h) {
   h->hp = p;
   VBH_CUDA(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking));
   const size_t db = sizeof(uint16_t) * (size_t)h->cfg.width * h->cfg.height;
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < kHostSlots; ++j) {
     VBH_CUDA(cudaMalloc(&p->depth[j], db));
     VBH_CUDA(cudaMalloc(&p->n_dev[j], 2 * sizeof(uint32_t)));
     VBH_CUDA(cudaMallocHost(&p->n_pin[j], 2 * sizeof(uint32_t)));
@@ -81,14 +87,19 @@ vbh_status create_pipe(vbh_handle* h) {
   return VBH_OK;
 }
 
-// Copy the pending frame's stream into its host buffers and mark it done.
-vbh_status complete_pending(vbh_handle* h) {
-  HostPipe* p = h->hp;
-  vbh_mc_stream_host* o = p->pending;
-  if (!o) return VBH_OK;
-  p->pending = nullptr;
-  const int j = p->pending_j;
-  VBH_CUDA(cudaEventSynchronize(p->e_frame[j]));
+// Enqueue the copy of a pending frame's stream into its host buffers (its totals must have
+// landed: with `wait`, wait for them; without, leave the frame if they have not).
+vbh_status start_copy(HostPipe* p, HostPipe::Pending& f, bool wait) {
+  if (f.copying) return VBH_OK;
+  const int j = f.j;
+  if (wait) {
+    VBH_CUDA(cudaEventSynchronize(p->e_frame[j]));
+  } else {
+    const cudaError_t q = cudaEventQuery(p->e_frame[j]);
+    if (q == cudaErrorNotReady) return VBH_OK;
+    if (q != cudaSuccess) return fail(VBH_ERR_CUDA, cudaGetErrorString(q));
+  }
+  vbh_mc_stream_host* o = f.out;
   const uint32_t nb = p->n_pin[j][0], ne = p->n_pin[j][1];
   const uint32_t cb = nb < o->cap_blocks ? nb : o->cap_blocks;
   const uint32_t ce = ne < o->cap_entries ? ne : o->cap_entries;
@@ -110,14 +121,42 @@ vbh_status complete_pending(vbh_handle* h) {
   }
   VBH_CUDA(cudaEventRecord(p->e_out[j], p->copy));
   p->out_used[j] = true;
+  f.copying = true;
+  return VBH_OK;
+}
+
+// Complete the oldest pending frame: its copy started (waiting for its totals if needed) and
+// landed; mark it done.
+vbh_status complete_oldest(HostPipe* p) {
+  if (p->pending.empty()) return VBH_OK;
+  HostPipe::Pending f = p->pending.front();
+  vbh_status st = start_copy(p, f, true);
+  if (st != VBH_OK) return st;
+  p->pending.pop_front();
+  const int j = f.j;
   VBH_CUDA(cudaEventSynchronize(p->e_out[j]));
+  vbh_mc_stream_host* o = f.out;
+  const uint32_t nb = p->n_pin[j][0], ne = p->n_pin[j][1];
   o->n_blocks = nb;
   o->n_entries = ne;
-  o->frame_id = p->pending_id;
+  o->frame_id = f.frame_id;
   o->done = 1u;
   if (nb > o->cap_blocks || ne > o->cap_entries)
     return fail(VBH_ERR_BUFFER_TOO_SMALL, "host stream capacity exceeded (frame results cut)");
   return VBH_OK;
+}
+
+vbh_status complete_all(HostPipe* p) {
+  vbh_status first = VBH_OK;
+  while (!p->pending.empty()) {
+    const vbh_status st = complete_oldest(p);
+    if (st == VBH_ERR_BUFFER_TOO_SMALL) {
+      if (first == VBH_OK) first = st;
+    } else if (st != VBH_OK) {
+      return st;
+    }
+  }
+  return first;
 }
 
 }  // namespace
@@ -131,7 +170,7 @@ void host_pipe_release(vbh_handle* h) {
     cudaStreamDestroy(p->copy);
   }
   free_streams(p);
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < kHostSlots; ++j) {
     if (p->depth[j]) cudaFree(p->depth[j]);
     if (p->n_dev[j]) cudaFree(p->n_dev[j]);
     if (p->n_pin[j]) cudaFreeHost(p->n_pin[j]);
@@ -167,7 +206,8 @@ vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
   vbh_status done_st = VBH_OK;
   if (o.cap_blocks > p->cap_blocks || o.cap_entries > p->cap_entries) {
     // larger device streams: every frame in flight completes first
-    done_st = complete_pending(h);
+    done_st = complete_all(p);
+    if (done_st != VBH_OK && done_st != VBH_ERR_BUFFER_TOO_SMALL) return done_st;
     VBH_CUDA(cudaStreamSynchronize(h->stream));
     VBH_CUDA(cudaStreamSynchronize(p->copy));
     const uint32_t cb = o.cap_blocks > p->cap_blocks ? o.cap_blocks : p->cap_blocks;
@@ -175,8 +215,8 @@ vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
     vbh_status st = alloc_streams(p, cb, ce);
     if (st != VBH_OK) return st;
   }
-  const int j = (int)(p->k & 1ull);
-  // depth in: after frame k-2 (the last reader of buffer j) has finished
+  const int j = (int)(p->k % kHostSlots);
+  // depth in: after frame k-3 (the last reader of buffer j) has finished
   if (p->frame_used[j]) VBH_CUDA(cudaStreamWaitEvent(p->copy, p->e_frame[j], 0));
   const size_t db = sizeof(uint16_t) * (size_t)h->cfg.width * h->cfg.height;
   VBH_CUDA(cudaMemcpyAsync(p->depth[j], depth_host, db, cudaMemcpyHostToDevice, p->copy));
@@ -194,16 +234,19 @@ vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
   VBH_CUDA(cudaEventRecord(p->e_frame[j], h->stream));
   p->frame_used[j] = true;
   ++p->k;
-  // the previous frame's results go out while this frame runs
-  if (done_st == VBH_OK) done_st = complete_pending(h);
-  p->pending = out_host;
-  p->pending_id = frame_id;
-  p->pending_j = j;
+  p->pending.push_back(HostPipe::Pending{out_host, frame_id, j, false});
+  // the frame before this one starts its copy-out if its totals are in; the one before that
+  // completes (slot j of the next call is its slot)
+  if (p->pending.size() >= 2) {
+    st = start_copy(p, p->pending[p->pending.size() - 2], false);
+    if (st != VBH_OK) return st;
+  }
+  if (done_st == VBH_OK && p->pending.size() >= (size_t)kHostSlots) done_st = complete_oldest(p);
   return done_st;
 }
 
 vbh_status vbh_process_frame_host_flush(vbh_handle* h) {
   if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
   if (!h->hp) return VBH_OK;
-  return complete_pending(h);
+  return complete_all(h->hp);
 }

@@ -289,8 +289,9 @@ def vbh_process_frame(h, depth, T_wc, frame_id: int, erase_radius: float, out: v
 
 def vbh_process_frame_host(h, depth_host, T_wc, frame_id: int, erase_radius: float,
                            out: vbh_mc_stream_host) -> int:
-    """Enqueue a frame from host depth; completes the previous call's `out` (returns its status:
-    VBH_OK or VBH_ERR_BUFFER_TOO_SMALL).  `out` is kept by the library until its frame is done."""
+    """Enqueue a frame from host depth; completes the `out` of two calls earlier (returns its
+    status: VBH_OK or VBH_ERR_BUFFER_TOO_SMALL).  `out` is kept by the library until its frame is
+    done."""
     T = np.ascontiguousarray(np.asarray(T_wc, np.float32).reshape(12))
     st = lib().vbh_process_frame_host(h, _ptr(depth_host), T.ctypes.data, int(frame_id),
                                       float(erase_radius), ctypes.byref(out))

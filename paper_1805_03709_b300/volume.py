@@ -222,9 +222,9 @@ class Volume:
     def process_frame_host(self, depth_host, T_wc, frame_id: int, erase_radius: float,
                            out: HostStream) -> int:
         """The frame from host depth (pinned uint16 for overlap) with its MC stream copied into
-        `out` (pinned host buffers) while the next frame runs: enqueues this frame and returns
-        once the previous call's `out` is complete (status VBH_OK or VBH_ERR_BUFFER_TOO_SMALL);
-        process_frame_host_flush completes the last one."""
+        `out` (pinned host buffers) while the next frames run: enqueues this frame and returns
+        once the `out` of two calls earlier is complete (status VBH_OK or
+        VBH_ERR_BUFFER_TOO_SMALL); process_frame_host_flush completes every pending frame."""
         if isinstance(depth_host, torch.Tensor):
             assert depth_host.dtype == torch.uint16 and not depth_host.is_cuda
             assert depth_host.is_contiguous()
