@@ -143,9 +143,11 @@ def run_reference(args, rank, ws):
     t_cal, f_cal = oracle_frames(o, cam, poses, depth, [0], 1.0 / 16)
     per_step = budget / max(n, 1)
     frac = float(np.clip(per_step / max(t_cal, 1e-3) / 16, 1.0 / cam.height, 1.0))
-    ids = [i % N_FRAMES for i in range(1, n)]
-    t_w, _ = oracle_frames(o, cam, poses, depth, ids[:max(args.warmup - 1, 0)], frac)
-    t_s, f_s = oracle_frames(o, cam, poses, depth, ids[max(args.warmup - 1, 0):][:args.steps], frac)
+    # the calibration frame is the first warm-up frame (it is processed even with none)
+    n_w = max(args.warmup - 1, 0)
+    ids = [i % N_FRAMES for i in range(1, 1 + n_w + args.steps)]
+    t_w, _ = oracle_frames(o, cam, poses, depth, ids[:n_w], frac)
+    t_s, f_s = oracle_frames(o, cam, poses, depth, ids[n_w:], frac)
     value = f_s / t_s if t_s > 0 else 0.0
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
