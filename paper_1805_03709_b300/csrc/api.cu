@@ -108,6 +108,15 @@ vbh_status rebuild(vbh_handle* h) {
   return check_launch(h, "rebuild");
 }
 
+void free_batch_lists(vbh_handle* h) {
+  BatchLists& b = h->blists;
+  for (void* q : {(void*)b.find_idx, (void*)b.find_key, (void*)b.ins_idx, (void*)b.ins_key,
+                  (void*)b.era_idx, (void*)b.era_key})
+    if (q) cudaFree(q);
+  b = BatchLists{};
+  h->blists_cap = 0;
+}
+
 vbh_status maybe_rebuild(vbh_handle* h) {
   if (h->snap_pending && cudaEventQuery(h->snap_ev) == cudaSuccess) {
     h->snap_pending = false;
@@ -343,6 +352,8 @@ vbh_status vbh_destroy(vbh_handle* h) {
   host_pipe_release(h);
   stream_out_release(h);
   if (h->stream || h->slots) cudaStreamSynchronize(h->stream);
+  free_batch_lists(h);
+  if (h->stream || h->slots) cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
   if (h->frame_exec) cudaGraphExecDestroy(h->frame_exec);
   if (h->frame_graph) cudaGraphDestroy(h->frame_graph);
@@ -386,16 +397,34 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
     return fail(VBH_ERR_INVALID_ARG, "null device pointer");
   vbh_status st = maybe_rebuild(h);
   if (st != VBH_OK) return st;
+  if (h->blists_cap < n) {   // the compacted find / insert / erase lists, grown to n
+    VBH_CUDA(cudaStreamSynchronize(h->stream));
+    free_batch_lists(h);
+    BatchLists& b = h->blists;
+    if (cudaMalloc(&b.find_idx, sizeof(unsigned int) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&b.find_key, sizeof(unsigned long long) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&b.ins_idx, sizeof(unsigned int) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&b.ins_key, sizeof(unsigned long long) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&b.era_idx, sizeof(unsigned int) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&b.era_key, sizeof(unsigned long long) * (size_t)n) != cudaSuccess) {
+      free_batch_lists(h);
+      return fail(VBH_ERR_CUDA, "vbh_hash_batch: device memory for the op lists");
+    }
+    h->blists_cap = n;
+  }
   const TableView t = h->table();
   const PoolView pool = h->pool();
   h->stage_begin(VBH_STAGE_HASH);
-  launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n);
-  launch_hash_insert(h->L, t, pool, h->cnt, ops_dev, keys3_dev, nullptr, nullptr, vals_dev,
-                     results_dev, status_dev, n);
-  launch_hash_insert_finish(h->L, t, pool, h->cnt, nullptr, results_dev, status_dev, n, nullptr,
-                            nullptr, nullptr, nullptr, nullptr);
-  launch_hash_erase(h->L, t, pool, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n);
-  h->launches += 4;
+  VBH_CUDA(cudaMemsetAsync(&h->cnt->n_find_list, 0, 3 * sizeof(unsigned int), h->stream));
+  launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n, h->blists);
+  launch_hash_insert(h->L, t, pool, h->cnt, nullptr, nullptr, h->blists.ins_key,
+                     &h->cnt->n_ins_list, vals_dev, results_dev, status_dev, n,
+                     h->blists.ins_idx);
+  launch_hash_insert_finish(h->L, t, pool, h->cnt, &h->cnt->n_ins_list, results_dev, status_dev,
+                            n, nullptr, nullptr, nullptr, nullptr, nullptr, h->blists.ins_idx);
+  launch_hash_erase(h->L, t, pool, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n,
+                    h->blists);
+  h->launches += 5;
   h->stage_end();
   st = check_launch(h, "vbh_hash_batch");
   snapshot_counters(h);

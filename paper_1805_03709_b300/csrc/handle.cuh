@@ -69,6 +69,8 @@ struct vbh_handle {
   unsigned long long* so_k = nullptr;
   vbh::StreamOutHost* so = nullptr;
   vbh::HostPipe* hp = nullptr;   // vbh_process_frame_host state
+  vbh::BatchLists blists;        // vbh_hash_batch: compacted insert / erase lists
+  uint32_t blists_cap = 0;
   // per-frame lists
   int J = 0;
   unsigned long long* cand = nullptr;

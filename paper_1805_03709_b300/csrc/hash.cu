@@ -102,29 +102,100 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
   return kFull;
 }
 
-// --------------------------------------------------------------------------------- find phase
-__global__ void __launch_bounds__(kThreads) k_find(TableView t, DevCounters* cnt,
-                                                   const unsigned char* ops, const int* keys3,
-                                                   unsigned int* res, unsigned char* st,
-                                                   unsigned int n) {
+// ---------------------------------------------------------------------------- batch compaction
+// Every op of a batch is read once: invalid ops get their status; valid finds, inserts and erases
+// go to three lists of (op index, packed key).  A CTA takes kPrepOps x kThreads ops, each thread
+// kPrepOps of them a CTA width apart (coalesced loads, all in flight at once); one warp scan of
+// the three packed counts and one reservation per list per CTA place them, so a 2^20-op batch is
+// one round of the grid.
+constexpr int kPrepOps = 4;
+
+__global__ void __launch_bounds__(kThreads) k_batch_prep(DevCounters* cnt,
+                                                         const unsigned char* ops,
+                                                         const int* keys3, unsigned int* res,
+                                                         unsigned char* st, unsigned int n,
+                                                         BatchLists lists) {
+  __shared__ unsigned int s_warp[kThreads / 32], s_base[3];
   if (blockIdx.x == 0 && threadIdx.x == 0) cnt->n_exists = 0;   // the batch's insert phase follows
+  const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned int span = gridDim.x * blockDim.x * kPrepOps;
+  for (unsigned int base = blockIdx.x * blockDim.x * kPrepOps; base < n; base += span) {
+    int kind[kPrepOps];   // 0 find, 1 insert, 2 erase, -1 none
+    unsigned long long key[kPrepOps];
+    unsigned int packed = 0;   // per-kind counts of this thread's ops, 10 bits each
+#pragma unroll
+    for (int j = 0; j < kPrepOps; ++j) {
+      const unsigned int i = base + j * kThreads + threadIdx.x;
+      kind[j] = -1;
+      key[j] = 0;
+      if (i < n) {
+        const unsigned char op = ops[i];
+        const int x = keys3[3u * i], y = keys3[3u * i + 1], z = keys3[3u * i + 2];
+        if (op > kOpErase || !key_ok(x, y, z)) {
+          res[i] = kNone;
+          st[i] = kStInvalid;
+        } else {
+          key[j] = pack_key(x, y, z);
+          kind[j] = op == kOpFind ? 0 : op == kOpInsert ? 1 : 2;
+          packed += 1u << (10 * kind[j]);
+        }
+      }
+    }
+    unsigned int incl = packed;   // inclusive warp scan of the packed counts (a field <= 128)
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= (unsigned int)d) incl += v;
+    }
+    if (lane == 31u) s_warp[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x < 3u) {
+      const unsigned int q = threadIdx.x, sh = 10u * q;
+      unsigned int* const counter = q == 0 ? &cnt->n_find_list
+                                    : q == 1 ? &cnt->n_ins_list : &cnt->n_era_list;
+      unsigned int run = 0;
+      for (int w = 0; w < kThreads / 32; ++w) run += (s_warp[w] >> sh) & 1023u;
+      s_base[q] = run ? atomicAdd(counter, run) : 0u;
+    }
+    __syncthreads();
+    unsigned int pos[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      unsigned int before = 0;   // ops of kind q in the CTA's earlier warps
+      for (unsigned int w = 0; w < warp; ++w) before += (s_warp[w] >> (10 * q)) & 1023u;
+      pos[q] = s_base[q] + before + (((incl - packed) >> (10 * q)) & 1023u);
+    }
+#pragma unroll
+    for (int j = 0; j < kPrepOps; ++j) {
+      const int q = kind[j];
+      if (q < 0) continue;
+      const unsigned int k = q == 0 ? pos[0]++ : q == 1 ? pos[1]++ : pos[2]++;
+      unsigned int* const idx = q == 0 ? lists.find_idx : q == 1 ? lists.ins_idx : lists.era_idx;
+      unsigned long long* const ko = q == 0 ? lists.find_key : q == 1 ? lists.ins_key
+                                                                      : lists.era_key;
+      idx[k] = base + j * kThreads + threadIdx.x;
+      ko[k] = key[j];
+    }
+    __syncthreads();   // s_warp and s_base are rewritten next round
+  }
+}
+
+// --------------------------------------------------------------------------------- find phase
+// The batch's finds (list from k_batch_prep, *count_dev entries, capped at n): read-only walks.
+__global__ void __launch_bounds__(kThreads) k_find(TableView t, const unsigned long long* fkeys,
+                                                   const unsigned int* fidx,
+                                                   const unsigned int* count_dev,
+                                                   unsigned int* res, unsigned char* st,
+                                                   unsigned int n_cap) {
+  const unsigned int n = min(*count_dev, n_cap);
   const unsigned int stride = gridDim.x * blockDim.x;
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    // the op byte and the key are loaded together: every op's key is validated here
-    const unsigned char op = ops[i];
-    const int x = keys3[3u * i], y = keys3[3u * i + 1], z = keys3[3u * i + 2];
-    unsigned int r = kNone;
-    unsigned char s = 0;   // inserts and erases are resolved by their own phases
-    if (op > kOpErase || !key_ok(x, y, z)) {
-      s = kStInvalid;
-    } else if (op == kOpFind) {
-      unsigned int val;
-      const bool hit = thread_find<true>(t, pack_key(x, y, z), &val) != kNone;
-      r = hit ? val : kNone;
-      s = hit ? kStFound : kStNotFound;
-    }
-    res[i] = r;
-    st[i] = s;
+    const unsigned long long key = fkeys[i];
+    const unsigned int oi = fidx[i];
+    unsigned int val;
+    const bool hit = thread_find<true>(t, key, &val) != kNone;
+    res[oi] = hit ? val : kNone;
+    st[oi] = hit ? kStFound : kStNotFound;
   }
 }
 
@@ -137,7 +208,8 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
                                                      const unsigned long long* pkeys,
                                                      const unsigned int* count_dev,
                                                      const unsigned int* vals, unsigned int* res,
-                                                     unsigned char* st, unsigned int n_cap) {
+                                                     unsigned char* st, unsigned int n_cap,
+                                                     const unsigned int* idx) {
   __shared__ unsigned int s_live, s_from_empty, s_from_tomb, s_err;
   if (threadIdx.x == 0) { s_live = 0; s_from_empty = 0; s_from_tomb = 0; s_err = 0; }
   __syncthreads();
@@ -151,9 +223,11 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
     const unsigned int i = base + lane;
     unsigned long long key = 0;
     bool doit = false;
+    unsigned int oi = i;   // the op's index in the batch (results, statuses, values)
     if (i < n) {
       if (pkeys) {
         key = pkeys[i];
+        if (idx) oi = idx[i];
         doit = true;
       } else if (ops[i] == kOpInsert) {
         doit = load_key3(keys3, i, &key);
@@ -180,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
         }
       }
     } else if (won) {
-      const unsigned int v = vals ? vals[i] : 0u;
+      const unsigned int v = vals ? vals[oi] : 0u;
       t.slots[pos].val = v;
       pos = v;   // a plain map's winner knows its value: the result is final
     }
@@ -194,8 +268,8 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
     }
     if (lane == 0 && n_ex && !pool.max_blocks) atomicAdd(&cnt->n_exists, n_ex);
     if (doit) {
-      res[i] = pos;
-      st[i] = outcome == kInserted ? kStInserted : outcome == kExists ? kStExists : kStCapacity;
+      res[oi] = pos;
+      st[oi] = outcome == kInserted ? kStInserted : outcome == kExists ? kStExists : kStCapacity;
       if (outcome == kFull) atomicOr(&s_err, kErrTable);
     }
   }
@@ -208,7 +282,8 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
   }
 }
 
-// Resolve every insert's value once all claims are visible; undo claims whose pool pop failed;
+// Resolve every insert's value once all claims are visible (the inserts are the first
+// *count_dev ops, capped at n_cap, or the ops idx lists); undo claims whose pool pop failed;
 // optionally append each distinct pool index to a frame's touched list (epoch de-duplication).
 __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolView pool,
                                                             DevCounters* cnt,
@@ -219,7 +294,8 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
                                                             unsigned long long* tkey,
                                                             float2* tdepth,
                                                             unsigned int* n_touched,
-                                                            const FrameCtl* ctl) {
+                                                            const FrameCtl* ctl,
+                                                            const unsigned int* idx) {
   // A plain map's winners wrote their final results; only inserts that met their key (whose
   // value another thread may still have been writing) are left, and usually there are none.
   const bool plain = pool.max_blocks == 0;
@@ -237,10 +313,11 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
   const unsigned int stride = gridDim.x * blockDim.x;
   const unsigned int rounds = (n + stride - 1u) / stride;
   for (unsigned int r = 0; r < rounds; ++r) {
-    const unsigned int i = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned int j = r * stride + blockIdx.x * blockDim.x + threadIdx.x;
     unsigned int p = kNone;
     bool fresh_win = false;
-    if (i < n) {
+    if (j < n) {
+      const unsigned int i = idx ? idx[j] : j;   // the insert's index in the batch
       unsigned char s = st[i];
       if (s == kStExists || (s == kStInserted && !plain)) {
         unsigned int pos = res[i];
@@ -291,20 +368,36 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
 }
 
 // -------------------------------------------------------------------------------- erase phase
+// Either ops + keys3 (every op of the batch scanned) or ekeys + eidx (the erase list the find
+// phase compacted, *count_dev entries, capped at n).
 __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, DevCounters* cnt,
                                                     const unsigned char* ops, const int* keys3,
+                                                    const unsigned long long* ekeys,
+                                                    const unsigned int* eidx,
+                                                    const unsigned int* count_dev,
                                                     unsigned int* res, unsigned char* st,
-                                                    unsigned int n) {
+                                                    unsigned int n_cap) {
   __shared__ unsigned int s_erased, s_emptied;
   if (threadIdx.x == 0) { s_erased = 0; s_emptied = 0; }
   __syncthreads();
+  const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int stride = gridDim.x * blockDim.x;
   for (unsigned int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n;
        base += stride) {
     const unsigned int i = base + lane;
     unsigned long long key = 0;
-    const bool doit = i < n && ops[i] == kOpErase && load_key3(keys3, i, &key);
+    unsigned int oi = i;   // the op's index in the batch
+    bool doit = false;
+    if (i < n) {
+      if (ekeys) {
+        key = ekeys[i];
+        oi = eidx[i];
+        doit = true;
+      } else {
+        doit = ops[i] == kOpErase && load_key3(keys3, i, &key);
+      }
+    }
     int how = 0;
     unsigned int val = kNone;
     if (doit) {
@@ -323,8 +416,8 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
       pool.seq[val] = 0u;
     }
     if (doit) {
-      res[i] = erased ? val : kNone;
-      st[i] = erased ? kStErased : kStNotFound;
+      res[oi] = erased ? val : kNone;
+      st[oi] = erased ? kStErased : kStNotFound;
     }
     const unsigned int n_er = __popc(__ballot_sync(0xFFFFFFFFu, erased));
     const unsigned int n_em = __popc(__ballot_sync(0xFFFFFFFFu, how == 1));
@@ -458,34 +551,42 @@ inline unsigned int fit_grid(int persistent, unsigned int n) {
 }
 
 void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsigned char* ops,
-                      const int* keys3, unsigned int* res, unsigned char* st, unsigned int n) {
+                      const int* keys3, unsigned int* res, unsigned char* st, unsigned int n,
+                      BatchLists lists) {
+  VBH_GRID(k_batch_prep, kThreads);
   VBH_GRID(k_find, kThreads);
-  k_find<<<fit_grid(grid_k_find, n), kThreads, 0, L.stream>>>(t, cnt, ops, keys3, res, st, n);
+  k_batch_prep<<<fit_grid(grid_k_batch_prep, (n + kPrepOps - 1u) / kPrepOps), kThreads, 0,
+                 L.stream>>>(cnt, ops, keys3, res, st, n, lists);
+  k_find<<<fit_grid(grid_k_find, n), kThreads, 0, L.stream>>>(t, lists.find_key, lists.find_idx,
+                                                                &cnt->n_find_list, res, st, n);
 }
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                         const unsigned char* ops, const int* keys3,
                         const unsigned long long* pkeys, const unsigned int* count_dev,
                         const unsigned int* vals, unsigned int* res, unsigned char* st,
-                        unsigned int n) {
+                        unsigned int n, const unsigned int* idx) {
   VBH_GRID(k_insert, kThreads);
   k_insert<<<fit_grid(grid_k_insert, n), kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, pkeys,
-                                                                    count_dev, vals, res, st, n);
+                                                                    count_dev, vals, res, st, n,
+                                                                    idx);
 }
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
                                unsigned char* st, unsigned int n, unsigned int* touched,
                                unsigned long long* tkey, float2* tdepth,
-                               unsigned int* n_touched, const FrameCtl* ctl) {
+                               unsigned int* n_touched, const FrameCtl* ctl,
+                               const unsigned int* idx) {
   VBH_GRID(k_insert_finish, kThreads);
   k_insert_finish<<<fit_grid(grid_k_insert_finish, n), kThreads, 0, L.stream>>>(
-      t, pool, cnt, count_dev, res, st, n, touched, tkey, tdepth, n_touched, ctl);
+      t, pool, cnt, count_dev, res, st, n, touched, tkey, tdepth, n_touched, ctl, idx);
 }
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const unsigned char* ops, const int* keys3, unsigned int* res,
-                       unsigned char* st, unsigned int n) {
+                       unsigned char* st, unsigned int n, BatchLists lists) {
   VBH_GRID(k_erase, kThreads);
-  k_erase<<<fit_grid(grid_k_erase, n), kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, res, st,
-                                                                  n);
+  k_erase<<<fit_grid(grid_k_erase, n), kThreads, 0, L.stream>>>(
+      t, pool, cnt, ops, keys3, lists.era_key, lists.era_idx,
+      lists.era_idx ? &cnt->n_era_list : nullptr, res, st, n);
 }
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt) {

@@ -57,6 +57,7 @@ struct DevCounters {
   int free_top;                 // valid entries of the free stack
   unsigned int n_popped;        // pops in the current insert launch
   unsigned int n_exists;        // plain-map batch: inserts that met their key (value pending)
+  unsigned int n_find_list, n_ins_list, n_era_list;   // a batch's compacted op lists
   unsigned int n_live, n_tomb, n_empty;
   unsigned int n_cand, n_touched, n_new;
   unsigned int n_mset, n_tombrec, n_removed;
@@ -369,23 +370,38 @@ struct Launch {
   int sms;            // persistent grids are (resident CTAs per SM) x sms
 };
 
+// A hash batch's valid finds, inserts and erases, compacted by its first pass: op index + packed
+// key.
+struct BatchLists {
+  unsigned int* find_idx = nullptr;
+  unsigned long long* find_key = nullptr;
+  unsigned int* ins_idx = nullptr;
+  unsigned long long* ins_key = nullptr;
+  unsigned int* era_idx = nullptr;
+  unsigned long long* era_key = nullptr;
+};
+
 // hash.cu
+// The batch's first pass (statuses of invalid ops, the three op lists) and its finds.
 void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsigned char* ops,
-                      const int* keys3,
-                      unsigned int* res, unsigned char* st, unsigned int n);
+                      const int* keys3, unsigned int* res, unsigned char* st, unsigned int n,
+                      BatchLists lists);
+// keys: ops + keys3 (a batch), or pkeys + *count_dev (a key list; with idx, the list's op
+// indices in the batch, for values, results and statuses)
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                         const unsigned char* ops, const int* keys3,
                         const unsigned long long* pkeys, const unsigned int* count_dev,
                         const unsigned int* vals, unsigned int* res, unsigned char* st,
-                        unsigned int n);
+                        unsigned int n, const unsigned int* idx = nullptr);
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
                                unsigned char* st, unsigned int n, unsigned int* touched,
                                unsigned long long* tkey, float2* tdepth,
-                               unsigned int* n_touched, const FrameCtl* ctl);
+                               unsigned int* n_touched, const FrameCtl* ctl,
+                               const unsigned int* idx = nullptr);
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const unsigned char* ops, const int* keys3, unsigned int* res,
-                       unsigned char* st, unsigned int n);
+                       unsigned char* st, unsigned int n, BatchLists lists = BatchLists{});
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt);
 void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,
