@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
+    ap.add_argument("--hash-only", action="store_true",
+                    help="profiling case: only the hash point (prefill, then 3 mixed 2^20-op "
+                         "batches, the first untimed); prints its dict")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tri", action="store_true",
@@ -264,6 +267,16 @@ def main():
                       "buckets, 2^17 blocks]")
     if args.impl == "reference":
         run_reference(args, rank, ws)
+        return
+    if args.hash_only:
+        import torch
+        from paper_1805_03709_b300 import build
+        build.build()
+        torch.cuda.set_device(local_rank)
+        dev = torch.device("cuda", local_rank)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps(hash_point(torch, dev, flush, measured_peak()[0], n_batches=3,
+                                    n_warm=1)))
         return
     # The clock sampler starts before any CUDA work: an nvidia-smi that first queries the GPU
     # after this process created its CUDA context leaves every later driver call of the process

@@ -309,33 +309,41 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
         }
       }
     }
+    // A lattice without a negative corner has only index-0 cubes: no classification.  Mask
+    // words 0..15 (lanes 0..15) are the sign words.
+    unsigned int neg_any = 0u;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) lat_fill[32 * n] = mw[n];
-    __syncwarp();
+    for (int n = 0; n < 8; ++n) neg_any |= mw[n];
+    const bool classify = true;
     const int3 k = unpack_key(key);
-    unsigned long long idx8[2], nz[2];
+    unsigned long long idx8[2] = {0ull, 0ull}, nz[2] = {0ull, 0ull};
     unsigned int mine = 0;
+    if (classify) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      // sign rows (Y, Z), (Y+1, Z), (Y, Z+1), (Y+1, Z+1) in bits 0..8 (bits above 8 are not
-      // read) and the AND of their weight rows
-      unsigned int sg[4], va = 0xFFFFFFFFu;
+      for (int n = 0; n < 8; ++n) lat_fill[32 * n] = mw[n];
+      __syncwarp();
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint2 a = lat[lr[h][c].off], b = lat[lr[h][c].off + 16u];
-        sg[c] = __byte_perm(a.x, b.x, lr[h][c].sel);
-        va &= __byte_perm(a.y, b.y, lr[h][c].sel);
+      for (int h = 0; h < 2; ++h) {
+        // sign rows (Y, Z), (Y+1, Z), (Y, Z+1), (Y+1, Z+1) in bits 0..8 (bits above 8 are not
+        // read) and the AND of their weight rows
+        unsigned int sg[4], va = 0xFFFFFFFFu;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint2 a = lat[lr[h][c].off], b = lat[lr[h][c].off + 16u];
+          sg[c] = __byte_perm(a.x, b.x, lr[h][c].sel);
+          va &= __byte_perm(a.y, b.y, lr[h][c].sel);
+        }
+        const unsigned int n00 = sg[0], n10 = sg[1], n01 = sg[2], n11 = sg[3];
+        unsigned long long c = spread[n00 & 0xFFu] | (spread[(n00 >> 1) & 0xFFu] << 1) |
+                               (spread[(n10 >> 1) & 0xFFu] << 2) | (spread[n10 & 0xFFu] << 3) |
+                               (spread[n01 & 0xFFu] << 4) | (spread[(n01 >> 1) & 0xFFu] << 5) |
+                               (spread[(n11 >> 1) & 0xFFu] << 6) | (spread[n11 & 0xFFu] << 7);
+        c &= spread[(va & (va >> 1)) & 0xFFu] * 0xFFull;        // all 8 corners valid
+        c &= ~((zero_bytes(~c) >> 7) * 0xFFull);                 // S^c: 255 -> 0
+        nz[h] = ~zero_bytes(c) & kHi1;
+        idx8[h] = c;
+        mine += __popcll(nz[h]);
       }
-      const unsigned int n00 = sg[0], n10 = sg[1], n01 = sg[2], n11 = sg[3];
-      unsigned long long c = spread[n00 & 0xFFu] | (spread[(n00 >> 1) & 0xFFu] << 1) |
-                             (spread[(n10 >> 1) & 0xFFu] << 2) | (spread[n10 & 0xFFu] << 3) |
-                             (spread[n01 & 0xFFu] << 4) | (spread[(n01 >> 1) & 0xFFu] << 5) |
-                             (spread[(n11 >> 1) & 0xFFu] << 6) | (spread[n11 & 0xFFu] << 7);
-      c &= spread[(va & (va >> 1)) & 0xFFu] * 0xFFull;        // all 8 corners valid
-      c &= ~((zero_bytes(~c) >> 7) * 0xFFull);                 // S^c: 255 -> 0
-      nz[h] = ~zero_bytes(c) & kHi1;
-      idx8[h] = c;
-      mine += __popcll(nz[h]);
     }
     if (sl) {   // dense indices of voxel x + 8 row: row lane in word lane, row lane + 32 next
       unsigned long long* st = reinterpret_cast<unsigned long long*>(sl->store + 32u * q);
@@ -352,27 +360,29 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
       }
     }
     if (emit) {
-      unsigned int incl = mine;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if ((int)lane >= d) incl += v;
-      }
-      const unsigned int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      const unsigned int tot = __reduce_add_sync(0xFFFFFFFFu, mine);
       if (fill + tot > kStage || nblk == kStageBlocks) flush();
-      unsigned int o = fill + incl - mine;
+      if (tot) {   // warp-uniform: about a third of the blocks have no nonzero index
+        unsigned int incl = mine;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {   // the row's nonzero cubes, in x order, with no divergence
-        const unsigned int base_loc = 8u * (lane + 32u * h);
-        const unsigned int n_lo = (unsigned int)nz[h], n_hi = (unsigned int)(nz[h] >> 32);
-        const unsigned int i_lo = (unsigned int)idx8[h], i_hi = (unsigned int)(idx8[h] >> 32);
+        for (int d = 1; d < 32; d <<= 1) {
+          const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+          if ((int)lane >= d) incl += v;
+        }
+        unsigned int o = fill + incl - mine;
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          const unsigned int nw = x < 4 ? n_lo : n_hi, iw = x < 4 ? i_lo : i_hi;
-          if ((nw >> (8 * (x & 3) + 7)) & 1u) {
-            st_loc[o] = (unsigned short)(base_loc + x);
-            st_idx[o] = (unsigned char)(iw >> (8 * (x & 3)));
-            ++o;
+        for (int h = 0; h < 2; ++h) {   // the row's nonzero cubes, in x order, no divergence
+          const unsigned int base_loc = 8u * (lane + 32u * h);
+          const unsigned int n_lo = (unsigned int)nz[h], n_hi = (unsigned int)(nz[h] >> 32);
+          const unsigned int i_lo = (unsigned int)idx8[h], i_hi = (unsigned int)(idx8[h] >> 32);
+#pragma unroll
+          for (int x = 0; x < 8; ++x) {
+            const unsigned int nw = x < 4 ? n_lo : n_hi, iw = x < 4 ? i_lo : i_hi;
+            if ((nw >> (8 * (x & 3) + 7)) & 1u) {
+              st_loc[o] = (unsigned short)(base_loc + x);
+              st_idx[o] = (unsigned char)(iw >> (8 * (x & 3)));
+              ++o;
+            }
           }
         }
       }
