@@ -13,7 +13,8 @@
 // missing block or with weight 0 is invalid and gets 0.  The kernel never reads TSDF values:
 // fusion keeps a 128 B sign/weight bit mask per block, and one warp per block assembles the
 // 9 x 9 x 9 corner lattice from the masks of the block and its 7 positive neighbours, then
-// classifies a whole 8-voxel row at once with byte-sliced 64-bit arithmetic.
+// classifies a whole 8-voxel row at once: which cubes are emitted comes from 32-bit logic on
+// the lattice's bit rows, the 8 index bytes from one 8 x 8 bit transpose.
 //
 // Serving.  While a server is attached, an extraction that refreshes blocks (the per-frame one)
 // also stores each block's 512 dense cube indices, gives every record the next change sequence
@@ -33,8 +34,6 @@ constexpr unsigned int kStage = 1024;        // MC entries staged per warp (>= 5
 #define VBH_MC_STAGE_BLOCKS 16
 #endif
 constexpr unsigned int kStageBlocks = VBH_MC_STAGE_BLOCKS;   // blocks staged per warp (<= 32)
-constexpr unsigned long long kLo7 = 0x7F7F7F7F7F7F7F7Full;
-constexpr unsigned long long kHi1 = 0x8080808080808080ull;
 
 __device__ __forceinline__ void add_to_set(PoolView& pool, unsigned int q, unsigned int epoch,
                                            bool pred, unsigned int* mset, unsigned int* n_mset,
@@ -160,11 +159,23 @@ __device__ __forceinline__ void note_removal(ServeLog* sl, unsigned long long ke
   atomicOr(&sl->err, kServeErrRemFull);
 }
 
-// Zero-byte detector: 0x80 in every byte of v that is zero, 0 elsewhere (exact, no carries
-// between bytes because the low seven bits are added separately from the top bit).
-__device__ __forceinline__ unsigned long long zero_bytes(unsigned long long v) {
-  unsigned long long y = (v & kLo7) + kLo7;
-  return ~(y | v | kLo7);
+// 8 x 8 bit-matrix transpose of the 64-bit word hi:lo (row i = byte i, column j = bit j), by
+// the three delta swaps of Hacker's Delight (Sec. 7-3): 2 x 2, 4 x 4 and 8 x 8 sub-blocks.  The
+// first two swap within each 32-bit half; the third moves bits 4..7 of lo's bytes to bits 0..3
+// of hi's and back.
+__device__ __forceinline__ void transpose8x8(unsigned int& lo, unsigned int& hi) {
+  unsigned int t;
+  t = (lo ^ (lo >> 7)) & 0x00AA00AAu;
+  lo ^= t ^ (t << 7);
+  t = (hi ^ (hi >> 7)) & 0x00AA00AAu;
+  hi ^= t ^ (t << 7);
+  t = (lo ^ (lo >> 14)) & 0x0000CCCCu;
+  lo ^= t ^ (t << 14);
+  t = (hi ^ (hi >> 14)) & 0x0000CCCCu;
+  hi ^= t ^ (t << 14);
+  t = (lo ^ (hi << 4)) & 0xF0F0F0F0u;
+  lo ^= t;
+  hi ^= t >> 4;
 }
 
 // The lattice of a block and its 7 positive neighbours (n = ox + 2 oy + 4 oz) in shared memory:
@@ -190,7 +201,7 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
                                                           DevCounters* cnt, const FrameCtl* ctl,
                                                           const unsigned int* mset,
                                                           const unsigned long long* tombrec) {
-  __shared__ unsigned long long spread[256];   // bit i of b -> bit 8 i
+  __shared__ unsigned long long spread[256];   // bit i of b -> bit 8 i (dense store only)
   __shared__ uint2 msk[kMcThreads / 32][8 * 16];   // the lattice, per warp
   __shared__ unsigned short stage_loc[kMcThreads / 32][kStage];
   __shared__ unsigned char stage_idx[kMcThreads / 32][kStage];
@@ -209,10 +220,12 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
   ServeLog* const sl = ctl->serve_mark ? ctl->slog : nullptr;
   const bool emit = !ctl->store_only;
   __shared__ unsigned int s_seq0;
-  for (int b = threadIdx.x; b < 256; b += kMcThreads) {
-    unsigned long long v = 0;
-    for (int i = 0; i < 8; ++i) v |= (unsigned long long)((b >> i) & 1) << (8 * i);
-    spread[b] = v;
+  if (sl) {   // the byte masks of the dense store
+    for (int b = threadIdx.x; b < 256; b += kMcThreads) {
+      unsigned long long v = 0;
+      for (int i = 0; i < 8; ++i) v |= (unsigned long long)((b >> i) & 1) << (8 * i);
+      spread[b] = v;
+    }
   }
   if (threadIdx.x == 0) s_seq0 = sl ? sl->seq_next : 0u;   // every CTA reads it before the
   __syncthreads();                                        // last one advances it
@@ -309,46 +322,45 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
         }
       }
     }
-    // A lattice without a negative corner has only index-0 cubes: no classification.  Mask
-    // words 0..15 (lanes 0..15) are the sign words.
-    unsigned int neg_any = 0u;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) neg_any |= mw[n];
-    const bool classify = true;
+    for (int n = 0; n < 8; ++n) lat_fill[32 * n] = mw[n];
+    __syncwarp();
     const int3 k = unpack_key(key);
-    unsigned long long idx8[2] = {0ull, 0ull}, nz[2] = {0ull, 0ull};
+    // per row h: the 8 cube indices (byte x of hi:lo) and which of them are emitted (bit x of
+    // e8: all 8 corners weighted, at least one corner negative, not all 8 negative)
+    unsigned int idx_lo[2], idx_hi[2], e8[2];
     unsigned int mine = 0;
-    if (classify) {
 #pragma unroll
-      for (int n = 0; n < 8; ++n) lat_fill[32 * n] = mw[n];
-      __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+      // sign rows (Y, Z), (Y+1, Z), (Y, Z+1), (Y+1, Z+1) in bits 0..8 (bits above 8 are not
+      // read) and the AND of their weight rows
+      unsigned int sg[4], va = 0xFFFFFFFFu;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        // sign rows (Y, Z), (Y+1, Z), (Y, Z+1), (Y+1, Z+1) in bits 0..8 (bits above 8 are not
-        // read) and the AND of their weight rows
-        unsigned int sg[4], va = 0xFFFFFFFFu;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint2 a = lat[lr[h][c].off], b = lat[lr[h][c].off + 16u];
-          sg[c] = __byte_perm(a.x, b.x, lr[h][c].sel);
-          va &= __byte_perm(a.y, b.y, lr[h][c].sel);
-        }
-        const unsigned int n00 = sg[0], n10 = sg[1], n01 = sg[2], n11 = sg[3];
-        unsigned long long c = spread[n00 & 0xFFu] | (spread[(n00 >> 1) & 0xFFu] << 1) |
-                               (spread[(n10 >> 1) & 0xFFu] << 2) | (spread[n10 & 0xFFu] << 3) |
-                               (spread[n01 & 0xFFu] << 4) | (spread[(n01 >> 1) & 0xFFu] << 5) |
-                               (spread[(n11 >> 1) & 0xFFu] << 6) | (spread[n11 & 0xFFu] << 7);
-        c &= spread[(va & (va >> 1)) & 0xFFu] * 0xFFull;        // all 8 corners valid
-        c &= ~((zero_bytes(~c) >> 7) * 0xFFull);                 // S^c: 255 -> 0
-        nz[h] = ~zero_bytes(c) & kHi1;
-        idx8[h] = c;
-        mine += __popcll(nz[h]);
+      for (int c = 0; c < 4; ++c) {
+        const uint2 a = lat[lr[h][c].off], b = lat[lr[h][c].off + 16u];
+        sg[c] = __byte_perm(a.x, b.x, lr[h][c].sel);
+        va &= __byte_perm(a.y, b.y, lr[h][c].sel);
       }
+      const unsigned int n00 = sg[0], n10 = sg[1], n01 = sg[2], n11 = sg[3];
+      // corner i's signs over x as byte i of hi:lo (corners 000 100 110 010 | 001 101 111 011),
+      // then the 8 x 8 bit transpose: byte x = the cube index at x
+      unsigned int lo = __byte_perm(__byte_perm(n00, n00 >> 1, 0x0040u),
+                                    __byte_perm(n10 >> 1, n10, 0x0040u), 0x5410u);
+      unsigned int hi = __byte_perm(__byte_perm(n01, n01 >> 1, 0x0040u),
+                                    __byte_perm(n11 >> 1, n11, 0x0040u), 0x5410u);
+      transpose8x8(lo, hi);
+      const unsigned int any4 = n00 | n10 | n01 | n11, all4 = n00 & n10 & n01 & n11;
+      e8[h] = va & (va >> 1) & (any4 | (any4 >> 1)) & ~(all4 & (all4 >> 1)) & 0xFFu;
+      idx_lo[h] = lo;
+      idx_hi[h] = hi;
+      mine += __popc(e8[h]);
     }
     if (sl) {   // dense indices of voxel x + 8 row: row lane in word lane, row lane + 32 next
       unsigned long long* st = reinterpret_cast<unsigned long long*>(sl->store + 32u * q);
-      st[lane] = idx8[0];
-      st[32u + lane] = idx8[1];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)   // cubes that are not emitted are stored as 0
+        st[32u * h + lane] = (((unsigned long long)idx_hi[h] << 32) | idx_lo[h]) &
+                             (spread[e8[h]] * 0xFFull);
       if (lane == 0) {
         const unsigned int e = seq0 + r;
         pool.seq[q] = e;
@@ -373,14 +385,11 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
 #pragma unroll
         for (int h = 0; h < 2; ++h) {   // the row's nonzero cubes, in x order, no divergence
           const unsigned int base_loc = 8u * (lane + 32u * h);
-          const unsigned int n_lo = (unsigned int)nz[h], n_hi = (unsigned int)(nz[h] >> 32);
-          const unsigned int i_lo = (unsigned int)idx8[h], i_hi = (unsigned int)(idx8[h] >> 32);
 #pragma unroll
           for (int x = 0; x < 8; ++x) {
-            const unsigned int nw = x < 4 ? n_lo : n_hi, iw = x < 4 ? i_lo : i_hi;
-            if ((nw >> (8 * (x & 3) + 7)) & 1u) {
+            if ((e8[h] >> x) & 1u) {
               st_loc[o] = (unsigned short)(base_loc + x);
-              st_idx[o] = (unsigned char)(iw >> (8 * (x & 3)));
+              st_idx[o] = (unsigned char)((x < 4 ? idx_lo[h] : idx_hi[h]) >> (8 * (x & 3)));
               ++o;
             }
           }
