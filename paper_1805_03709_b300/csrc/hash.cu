@@ -106,11 +106,11 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
 // Every op of a batch is read once: invalid ops get their status; valid finds, inserts and erases
 // go to three lists of (op index, packed key).  A CTA takes kPrepOps x kThreads ops, each thread
 // kPrepOps of them a CTA width apart (coalesced loads, all in flight at once); one warp scan of
-// the three packed counts and one reservation per list per CTA place them, so a 2^20-op batch is
-// one round of the grid.
+// the three packed counts and one reservation per list per CTA place them; at 8 CTAs per SM a
+// 2^20-op batch is one round of the grid.
 constexpr int kPrepOps = 4;
 
-__global__ void __launch_bounds__(kThreads) k_batch_prep(DevCounters* cnt,
+__global__ void __launch_bounds__(kThreads, 8) k_batch_prep(DevCounters* cnt,
                                                          const unsigned char* ops,
                                                          const int* keys3, unsigned int* res,
                                                          unsigned char* st, unsigned int n,
