@@ -415,12 +415,14 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   const TableView t = h->table();
   const PoolView pool = h->pool();
   h->stage_begin(VBH_STAGE_HASH);
-  VBH_CUDA(cudaMemsetAsync(&h->cnt->n_find_list, 0, 3 * sizeof(unsigned int), h->stream));
+  h->blists.n = h->cnt->op_lists[h->batch_parity];
+  h->blists.n_next = h->cnt->op_lists[h->batch_parity ^ 1u];
+  h->batch_parity ^= 1u;
   launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n, h->blists);
   launch_hash_insert(h->L, t, pool, h->cnt, nullptr, nullptr, h->blists.ins_key,
-                     &h->cnt->n_ins_list, vals_dev, results_dev, status_dev, n,
+                     h->blists.n + 1, vals_dev, results_dev, status_dev, n,
                      h->blists.ins_idx);
-  launch_hash_insert_finish(h->L, t, pool, h->cnt, &h->cnt->n_ins_list, results_dev, status_dev,
+  launch_hash_insert_finish(h->L, t, pool, h->cnt, h->blists.n + 1, results_dev, status_dev,
                             n, nullptr, nullptr, nullptr, nullptr, nullptr, h->blists.ins_idx);
   launch_hash_erase(h->L, t, pool, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n,
                     h->blists);

@@ -71,6 +71,7 @@ struct vbh_handle {
   vbh::HostPipe* hp = nullptr;   // vbh_process_frame_host state
   vbh::BatchLists blists;        // vbh_hash_batch: compacted insert / erase lists
   uint32_t blists_cap = 0;
+  uint32_t batch_parity = 0;     // which set of list lengths the next vbh_hash_batch uses
   // per-frame lists
   int J = 0;
   unsigned long long* cand = nullptr;

@@ -116,7 +116,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_batch_prep(DevCounters* cnt,
                                                          unsigned char* st, unsigned int n,
                                                          BatchLists lists) {
   __shared__ unsigned int s_warp[kThreads / 32], s_base[3];
-  if (blockIdx.x == 0 && threadIdx.x == 0) cnt->n_exists = 0;   // the batch's insert phase follows
+  if (blockIdx.x == 0 && threadIdx.x < 3u) {
+    lists.n_next[threadIdx.x] = 0u;   // the previous batch, which used them, has finished
+    if (threadIdx.x == 0) cnt->n_exists = 0;   // the batch's insert phase follows
+  }
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int span = gridDim.x * blockDim.x * kPrepOps;
   for (unsigned int base = blockIdx.x * blockDim.x * kPrepOps; base < n; base += span) {
@@ -151,8 +154,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_batch_prep(DevCounters* cnt,
     __syncthreads();
     if (threadIdx.x < 3u) {
       const unsigned int q = threadIdx.x, sh = 10u * q;
-      unsigned int* const counter = q == 0 ? &cnt->n_find_list
-                                    : q == 1 ? &cnt->n_ins_list : &cnt->n_era_list;
+      unsigned int* const counter = lists.n + q;
       unsigned int run = 0;
       for (int w = 0; w < kThreads / 32; ++w) run += (s_warp[w] >> sh) & 1023u;
       s_base[q] = run ? atomicAdd(counter, run) : 0u;
@@ -558,7 +560,7 @@ void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsi
   k_batch_prep<<<fit_grid(grid_k_batch_prep, (n + kPrepOps - 1u) / kPrepOps), kThreads, 0,
                  L.stream>>>(cnt, ops, keys3, res, st, n, lists);
   k_find<<<fit_grid(grid_k_find, n), kThreads, 0, L.stream>>>(t, lists.find_key, lists.find_idx,
-                                                                &cnt->n_find_list, res, st, n);
+                                                                lists.n, res, st, n);
 }
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                         const unsigned char* ops, const int* keys3,
@@ -586,7 +588,7 @@ void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters*
   VBH_GRID(k_erase, kThreads);
   k_erase<<<fit_grid(grid_k_erase, n), kThreads, 0, L.stream>>>(
       t, pool, cnt, ops, keys3, lists.era_key, lists.era_idx,
-      lists.era_idx ? &cnt->n_era_list : nullptr, res, st, n);
+      lists.era_idx ? lists.n + 2 : nullptr, res, st, n);
 }
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt) {

@@ -57,7 +57,9 @@ struct DevCounters {
   int free_top;                 // valid entries of the free stack
   unsigned int n_popped;        // pops in the current insert launch
   unsigned int n_exists;        // plain-map batch: inserts that met their key (value pending)
-  unsigned int n_find_list, n_ins_list, n_era_list;   // a batch's compacted op lists
+  // a hash batch's find / insert / erase list lengths, one set per batch parity: each batch's
+  // first pass zeroes the other set for the next batch (no memset between batches)
+  unsigned int op_lists[2][3];
   unsigned int n_live, n_tomb, n_empty;
   unsigned int n_cand, n_touched, n_new;
   unsigned int n_mset, n_tombrec, n_removed;
@@ -379,6 +381,8 @@ struct BatchLists {
   unsigned long long* ins_key = nullptr;
   unsigned int* era_idx = nullptr;
   unsigned long long* era_key = nullptr;
+  unsigned int* n = nullptr;        // this batch's three list lengths (zero when it starts)
+  unsigned int* n_next = nullptr;   // the next batch's, zeroed by this batch's first pass
 };
 
 // hash.cu
