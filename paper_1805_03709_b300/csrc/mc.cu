@@ -194,8 +194,10 @@ __device__ __forceinline__ LatticeRow lattice_row(int Y, int Z) {
   return LatticeRow{(unsigned int)(16 * n + (ly >> 2) + 2 * lz), k | ((4u + k) << 4)};
 }
 
+// 9 CTAs (36 warps) per SM at 56 registers, no spill: a room frame's ~14k-block set is at most
+// three blocks per warp of the persistent grid.
 #ifndef VBH_MC_MIN_CTAS
-#define VBH_MC_MIN_CTAS 8
+#define VBH_MC_MIN_CTAS 9
 #endif
 __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(TableView t, PoolView pool,
                                                           DevCounters* cnt, const FrameCtl* ctl,
