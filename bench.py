@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-hash", action="store_true", help="skip the hash microbenchmark point")
     ap.add_argument("--hash-only", action="store_true",
                     help="profiling case: only the hash point (prefill, then 3 mixed 2^20-op "
-                         "batches, the first untimed); prints its dict")
+                         "batches, the first untimed) and its clustered mode; prints its dict")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tri", action="store_true",
@@ -275,8 +275,9 @@ def main():
         torch.cuda.set_device(local_rank)
         dev = torch.device("cuda", local_rank)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-        print(json.dumps(hash_point(torch, dev, flush, measured_peak()[0], n_batches=3,
-                                    n_warm=1)))
+        pt = hash_point(torch, dev, flush, measured_peak()[0], n_batches=3, n_warm=1)
+        pt["clustered"] = hash_clustered_point(torch, dev, flush, n_batches=3)
+        print(json.dumps(pt))
         return
     # The clock sampler starts before any CUDA work: an nvidia-smi that first queries the GPU
     # after this process created its CUDA context leaves every later driver call of the process
@@ -505,6 +506,7 @@ def main():
             sweep.append({k: r[k] for k in ("load_factor", "batch", "Mops_s", "hbm_frac",
                                             "batches_timed", "rebuilds", "timing")})
         hash_pt["sweep"] = sweep
+        hash_pt["clustered"] = hash_clustered_point(torch, dev, flush)
     diff_pt = None
     if not args.no_diff:
         diff_pt = diff_point(torch, dev, flush)
@@ -658,6 +660,52 @@ def hash_point(torch, dev, flush, peak, lf=0.7, n=1 << 20, n_batches=6, n_warm=2
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+
+
+def hash_clustered_point(torch, dev, flush, n=1 << 20, n_batches=5, n_warm=1):
+    """Hash workload, clustered mode: the 2^22 x 4 table prefilled to load 0.7 with distinct
+    uniform keys; each batch draws its n keys with Zipf(1.1) popularity from a seeded 64^3 cube
+    of neighbouring block coordinates (heavy duplication: same-key contention on inserts and
+    erases, neighbouring keys hashed together), ops 50/30/20 find/insert/erase at random.  One
+    batch at a time, L2 flushed, enqueued behind a GPU delay (device time)."""
+    from paper_1805_03709_b300 import synth
+    from paper_1805_03709_b300.volume import HashMap
+    n_buckets = 1 << 22
+    n_pre = int(0.7 * n_buckets * 4)
+    K = torch.from_numpy(synth.distinct_keys(n_pre, seed=1805)).to(dev)
+    hm = HashMap(n_buckets=n_buckets, max_batch=1 << 24)
+    hm.batch(torch.ones(n_pre, dtype=torch.uint8, device=dev), K,
+             torch.arange(n_pre, dtype=torch.int32, device=dev))
+    del K
+    rng = np.random.default_rng(7)
+    res = torch.empty(n, dtype=torch.int32, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    t_ms, done, distinct = 0.0, 0, []
+    for b in range(n_batches):
+        keys = synth.zipf_cluster_keys(n, seed=100 + b)
+        ops = rng.choice(3, size=n, p=[0.5, 0.3, 0.2]).astype(np.uint8)
+        O = torch.from_numpy(ops).to(dev)
+        bk = torch.from_numpy(keys).to(dev)
+        bv = torch.arange(n, dtype=torch.int32, device=dev)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(200_000)   # the host enqueues the batch meanwhile (device time)
+        e0.record()
+        hm.batch(O, bk, bv, res, st)
+        e1.record()
+        torch.cuda.synchronize()
+        if b >= n_warm:
+            t_ms += e0.elapsed_time(e1)
+            done += n
+            distinct.append(len(np.unique(keys, axis=0)))
+    c = hm.counters()
+    hm.close()
+    return {"mode": "clustered: Zipf(1.1) over a 64^3 cube of neighbouring keys",
+            "load_factor": 0.7, "batch": n, "Mops_s": done / (t_ms / 1e3) / 1e6,
+            "distinct_keys_per_batch": float(np.mean(distinct)),
+            "batches_timed": n_batches - n_warm, "rebuilds": c.rebuilds,
+            "timing": "one batch at a time, L2 flushed, enqueued behind a GPU delay (device time)"}
 
 
 def tri_point(torch, vol, peak, reps=5):
