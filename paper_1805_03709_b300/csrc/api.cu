@@ -419,13 +419,12 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   h->blists.n_next = h->cnt->op_lists[h->batch_parity ^ 1u];
   h->batch_parity ^= 1u;
   launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n, h->blists);
-  launch_hash_insert(h->L, t, pool, h->cnt, nullptr, nullptr, h->blists.ins_key,
+  launch_hash_insert(h->L, t, pool, h->cnt, h->blists.ins_key,
                      h->blists.n + 1, vals_dev, results_dev, status_dev, n,
                      h->blists.ins_idx);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, h->blists.n + 1, results_dev, status_dev,
                             n, nullptr, nullptr, nullptr, nullptr, nullptr, h->blists.ins_idx);
-  launch_hash_erase(h->L, t, pool, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n,
-                    h->blists);
+  launch_hash_erase(h->L, t, pool, h->cnt, results_dev, status_dev, n, h->blists);
   h->launches += 5;
   h->stage_end();
   st = check_launch(h, "vbh_hash_batch");
@@ -466,7 +465,7 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   h->stage_begin(VBH_STAGE_ALLOC);
   launch_setup(h, c);
   launch_alloc_keys(h->L, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
-  launch_hash_insert(h->L, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
+  launch_hash_insert(h->L, t, pool, h->cnt, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
                             h->cand_cap, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
@@ -532,7 +531,7 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
                       nullptr, stream_list(h));
   if (h->so) launch_stream_gather(Lc, h->so_ring, h->ctl, pool, h->cnt, stream_list(h));
   VBH_CUDA(cudaStreamWaitEvent(h->cap_stream, h->fork_ev[1], 0));
-  launch_hash_insert(Lc, t, pool, h->cnt, nullptr, nullptr, h->cand, &h->cnt->n_cand, nullptr,
+  launch_hash_insert(Lc, t, pool, h->cnt, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(Lc, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
                             h->cand_cap, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,

@@ -27,14 +27,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ bool load_key3(const int* keys3, unsigned int i,
-                                          unsigned long long* key) {
-  int x = keys3[3u * i], y = keys3[3u * i + 1], z = keys3[3u * i + 2];
-  if (!key_ok(x, y, z)) return false;
-  *key = pack_key(x, y, z);
-  return true;
-}
-
 // outcome codes of thread_insert
 constexpr int kInserted = 1, kExists = 2, kFull = 3;
 
@@ -202,11 +194,11 @@ __global__ void __launch_bounds__(kThreads) k_find(TableView t, const unsigned l
 }
 
 // ------------------------------------------------------------------------------- insert phase
-// Either keys3 + ops (a user batch; non-insert ops and invalid keys are skipped) or pkeys (a
-// list of packed keys, all inserts, length *count_dev capped at n).
+// A list of packed keys, all inserts (a batch's insert list, or a frame's candidate blocks),
+// *count_dev entries capped at n_cap (n_cap itself without count_dev); idx (optional) maps list
+// entry i to the op whose value, result and status it carries.
 __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
-                                                     DevCounters* cnt, const unsigned char* ops,
-                                                     const int* keys3,
+                                                     DevCounters* cnt,
                                                      const unsigned long long* pkeys,
                                                      const unsigned int* count_dev,
                                                      const unsigned int* vals, unsigned int* res,
@@ -227,13 +219,9 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
     bool doit = false;
     unsigned int oi = i;   // the op's index in the batch (results, statuses, values)
     if (i < n) {
-      if (pkeys) {
-        key = pkeys[i];
-        if (idx) oi = idx[i];
-        doit = true;
-      } else if (ops[i] == kOpInsert) {
-        doit = load_key3(keys3, i, &key);
-      }
+      key = pkeys[i];
+      if (idx) oi = idx[i];
+      doit = true;
     }
     int outcome = 0;
     unsigned int pos = kNone;
@@ -370,10 +358,9 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
 }
 
 // -------------------------------------------------------------------------------- erase phase
-// Either ops + keys3 (every op of the batch scanned) or ekeys + eidx (the erase list the find
-// phase compacted, *count_dev entries, capped at n).
+// The batch's erase list (packed keys ekeys and op indices eidx from k_batch_prep, *count_dev
+// entries, capped at n_cap).
 __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, DevCounters* cnt,
-                                                    const unsigned char* ops, const int* keys3,
                                                     const unsigned long long* ekeys,
                                                     const unsigned int* eidx,
                                                     const unsigned int* count_dev,
@@ -382,23 +369,18 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
   __shared__ unsigned int s_erased, s_emptied;
   if (threadIdx.x == 0) { s_erased = 0; s_emptied = 0; }
   __syncthreads();
-  const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
+  const unsigned int n = min(*count_dev, n_cap);
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int stride = gridDim.x * blockDim.x;
   for (unsigned int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n;
        base += stride) {
     const unsigned int i = base + lane;
     unsigned long long key = 0;
-    unsigned int oi = i;   // the op's index in the batch
-    bool doit = false;
-    if (i < n) {
-      if (ekeys) {
-        key = ekeys[i];
-        oi = eidx[i];
-        doit = true;
-      } else {
-        doit = ops[i] == kOpErase && load_key3(keys3, i, &key);
-      }
+    unsigned int oi = 0;   // the op's index in the batch
+    const bool doit = i < n;
+    if (doit) {
+      key = ekeys[i];
+      oi = eidx[i];
     }
     int how = 0;
     unsigned int val = kNone;
@@ -563,14 +545,12 @@ void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsi
                                                                 lists.n, res, st, n);
 }
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                        const unsigned char* ops, const int* keys3,
                         const unsigned long long* pkeys, const unsigned int* count_dev,
                         const unsigned int* vals, unsigned int* res, unsigned char* st,
                         unsigned int n, const unsigned int* idx) {
   VBH_GRID(k_insert, kThreads);
-  k_insert<<<fit_grid(grid_k_insert, n), kThreads, 0, L.stream>>>(t, pool, cnt, ops, keys3, pkeys,
-                                                                    count_dev, vals, res, st, n,
-                                                                    idx);
+  k_insert<<<fit_grid(grid_k_insert, n), kThreads, 0, L.stream>>>(t, pool, cnt, pkeys, count_dev,
+                                                                    vals, res, st, n, idx);
 }
 void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                                const unsigned int* count_dev, unsigned int* res,
@@ -583,12 +563,10 @@ void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevC
       t, pool, cnt, count_dev, res, st, n, touched, tkey, tdepth, n_touched, ctl, idx);
 }
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                       const unsigned char* ops, const int* keys3, unsigned int* res,
-                       unsigned char* st, unsigned int n, BatchLists lists) {
+                       unsigned int* res, unsigned char* st, unsigned int n, BatchLists lists) {
   VBH_GRID(k_erase, kThreads);
   k_erase<<<fit_grid(grid_k_erase, n), kThreads, 0, L.stream>>>(
-      t, pool, cnt, ops, keys3, lists.era_key, lists.era_idx,
-      lists.era_idx ? lists.n + 2 : nullptr, res, st, n);
+      t, pool, cnt, lists.era_key, lists.era_idx, lists.n + 2, res, st, n);
 }
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt) {

@@ -393,7 +393,6 @@ void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsi
 // keys: ops + keys3 (a batch), or pkeys + *count_dev (a key list; with idx, the list's op
 // indices in the batch, for values, results and statuses)
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                        const unsigned char* ops, const int* keys3,
                         const unsigned long long* pkeys, const unsigned int* count_dev,
                         const unsigned int* vals, unsigned int* res, unsigned char* st,
                         unsigned int n, const unsigned int* idx = nullptr);
@@ -403,9 +402,9 @@ void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevC
                                unsigned long long* tkey, float2* tdepth,
                                unsigned int* n_touched, const FrameCtl* ctl,
                                const unsigned int* idx = nullptr);
+// The batch's erases, from the erase list its first pass compacted.
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
-                       const unsigned char* ops, const int* keys3, unsigned int* res,
-                       unsigned char* st, unsigned int n, BatchLists lists = BatchLists{});
+                       unsigned int* res, unsigned char* st, unsigned int n, BatchLists lists);
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt);
 void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,
