@@ -134,6 +134,34 @@ def test_ragged_sizes_and_invalid(n):
     check_contents(hm, om)
 
 
+def test_single_kind_batches_in_sequence():
+    """Batches of one op kind each, an all-invalid batch and an empty one, back to back: the
+    other two op lists of each batch are empty, and consecutive batches use alternate sets of
+    list lengths (each batch's first pass zeroes the next batch's set)."""
+    rng = np.random.default_rng(11)
+    pool = synth.random_hash_keys(3000, seed=11, lo=-200, hi=200)
+    hm = HashMap(n_buckets=1024)   # 4096 slots: every key of the pool fits
+    om = OracleMap()
+    bad = pool[:500].copy()
+    bad[:, 2] = -(1 << 21)   # out of range
+    plan = [(V.VBH_OP_INSERT, pool[:1500]), (V.VBH_OP_FIND, pool[rng.integers(0, 3000, 2000)]),
+            (V.VBH_OP_ERASE, pool[rng.integers(0, 1500, 900)]), (None, None),
+            (V.VBH_OP_FIND, pool[:3000]), (V.VBH_OP_INSERT, pool[rng.integers(0, 3000, 2500)]),
+            (V.VBH_OP_INSERT, bad), (V.VBH_OP_ERASE, pool[1000:2000]),
+            (V.VBH_OP_FIND, pool[rng.integers(0, 3000, 777)])]
+    for op, keys in plan:
+        if op is None:
+            e = torch.zeros(0, dtype=torch.uint8, device="cuda")
+            hm.batch(e, torch.zeros((0, 3), dtype=torch.int32, device="cuda"))
+            continue
+        ops = np.full(len(keys), op, np.uint8)
+        vals = key_value(keys)
+        rg, sg = gpu_batch(hm, ops, keys, vals)
+        ro, so = om.batch(ops, keys, vals)
+        assert_same(ops, keys, rg, sg, ro, so)
+    check_contents(hm, om)
+
+
 def test_empty_batch():
     hm = HashMap(n_buckets=16)
     e = torch.zeros(0, dtype=torch.uint8, device="cuda")
