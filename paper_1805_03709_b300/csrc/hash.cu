@@ -5,7 +5,9 @@
 // which the paper obtains with per-entry locks and an excess list; here with CAS claims):
 //   * A launch runs one phase only: finds (read-only), inserts (slots only go free -> key),
 //     or erases (slots only go key -> tombstone, or key -> EMPTY in a bucket that already holds
-//     an EMPTY slot).  The host orders the phases of a batch.
+//     an EMPTY slot).  The host orders the phases of a batch.  A batch's first pass (which
+//     touches no slot) sorts its ops into a find, an insert and an erase list, so each phase
+//     launch covers only its own ops.
 //   * A live key never moves (the paper's invariant that entry positions are preserved), so a
 //     find needs no lock: it walks the buckets from the key's home bucket until it meets the
 //     key or a bucket with a never-used (EMPTY) slot.  Tombstones keep chains intact, and an
