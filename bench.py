@@ -81,6 +81,16 @@ def dist_info():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
 
 
+def max_over_ranks(torch, x: float, dev, ws: int) -> float:
+    """The largest x of all ranks (a MAX all-reduce of one float64 on `dev`: the rank's CUDA
+    device under NCCL, the CPU under gloo); x itself on a single rank."""
+    if ws == 1:
+        return x
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- CPU oracle runs
 def oracle_volume(cam):
     import oracle
@@ -352,10 +362,7 @@ def main():
     stage_ms, stage_launch = vol.timing_read(reset=True)
     vol.timing(())
     launches = int(c1.kernel_launches - c0.kernel_launches)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(torch, ms_total, dev, ws)
     clk = clocks.stop()
 
     # roofline of the dominant kernel (fusion) with the algorithmic bytes of integration: 8 B
@@ -432,10 +439,7 @@ def main():
         assert [(c[0] + c[1], c[2]) for c in mc_counts] == nbs, "replay differs from the e2e run"
         mc_timing = vol.timing_read(reset=True)
         vol.timing(())
-        if ws > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(torch, t_e2e, dev, ws)
         e2e = {"value": ws * args.steps / t_e2e, "unit": "frames/s",
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
                "api": "vbh_process_frame_host (pinned host depth in, whole MC stream out, "
