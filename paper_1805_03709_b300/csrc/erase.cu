@@ -213,8 +213,7 @@ void launch_erase_radius(const Launch& L, TableView t, PoolView pool, DevCounter
                          const FrameCtl* ctl, unsigned long long* removed,
                          unsigned int removed_cap, int* out_keys3, unsigned int* out_n,
                          StreamList so) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_erase_radius, kThreads, L.sms);
+  static const int grid = persistent_grid(k_erase_radius, kThreads, L.sms);
   k_erase_radius<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, ctl, removed, removed_cap,
                                                   out_keys3, so);
   if (out_n)
@@ -226,8 +225,7 @@ void launch_erase_keys(const Launch& L, TableView t, PoolView pool, DevCounters*
                        const int* keys3, unsigned int n, unsigned long long* removed,
                        unsigned int removed_cap, int* out_keys3, unsigned int* out_n,
                        StreamList so) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_erase_keys, kThreads, L.sms);
+  static const int grid = persistent_grid(k_erase_keys, kThreads, L.sms);
   if (n)
     k_erase_keys<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, keys3, n, removed, removed_cap,
                                                   out_keys3, so);

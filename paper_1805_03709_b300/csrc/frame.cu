@@ -444,15 +444,13 @@ __global__ void __launch_bounds__(256) k_visible(const FrameCtl* ctl, PoolView p
 
 void launch_visible(const Launch& L, const FrameCtl* ctl, PoolView pool, unsigned int* touched,
                     unsigned long long* tkey, float2* tdepth, unsigned int* n_touched) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_visible, 256, L.sms);
+  static const int grid = persistent_grid(k_visible, 256, L.sms);
   k_visible<<<grid, 256, 0, L.stream>>>(ctl, pool, touched, tkey, tdepth, n_touched);
 }
 
 void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int height,
                        unsigned long long* cand, unsigned int cap, DevCounters* cnt) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_alloc_keys, kTileThreads, L.sms);
+  static const int grid = persistent_grid(k_alloc_keys, kTileThreads, L.sms);
   const int tiles = ((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
   k_alloc_keys<<<tiles < grid ? tiles : grid, kTileThreads, 0, L.stream>>>(ctl, cand, cap, cnt);
 }
@@ -460,8 +458,7 @@ void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int heig
 void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
                       const unsigned int* touched, const unsigned long long* tkey,
                       const float2* tdepth, const unsigned int* n_touched, DevCounters* cnt) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_integrate, kIntThreads, L.sms);
+  static const int grid = persistent_grid(k_integrate, kIntThreads, L.sms);
   k_integrate<<<grid, kIntThreads, 0, L.stream>>>(fp, pool, touched, tkey, tdepth, n_touched,
                                                   cnt);
 }

@@ -526,8 +526,7 @@ __global__ void k_pack_keys(const int* keys3, unsigned int n, unsigned long long
 }  // namespace
 
 #define VBH_GRID(kernel, threads)                                  \
-  static int grid_##kernel = 0;                                    \
-  if (!grid_##kernel) grid_##kernel = persistent_grid(kernel, threads, L.sms)
+  static const int grid_##kernel = persistent_grid(kernel, threads, L.sms)
 
 // A batch of n ops needs no more CTAs than it has ops per CTA-wide round (small batches would
 // otherwise launch the whole persistent grid for a handful of ops).

@@ -477,31 +477,27 @@ void launch_mset_touched(const Launch& L, TableView t, PoolView pool, DevCounter
                          const unsigned int* n_touched, const unsigned long long* removed,
                          const unsigned int* n_removed, unsigned int removed_cap,
                          unsigned int* mset, unsigned long long* tombrec) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_mset_touched, kThreads, L.sms);
+  static const int grid = persistent_grid(k_mset_touched, kThreads, L.sms);
   k_mset_touched<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, ctl, touched, n_touched, removed,
                                                   n_removed, removed_cap, mset, tombrec);
 }
 
 void launch_mset_keys(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                       const FrameCtl* ctl, const int* keys3, unsigned int n, unsigned int* mset) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_mset_keys, kThreads, L.sms);
+  static const int grid = persistent_grid(k_mset_keys, kThreads, L.sms);
   if (n) k_mset_keys<<<grid, kThreads, 0, L.stream>>>(t, pool, cnt, ctl, keys3, n, mset);
 }
 
 void launch_mset_scan(const Launch& L, PoolView pool, DevCounters* cnt, unsigned int* mset,
                       int since_mode, unsigned int since_version) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_mset_scan, kThreads, L.sms);
+  static const int grid = persistent_grid(k_mset_scan, kThreads, L.sms);
   k_mset_scan<<<grid, kThreads, 0, L.stream>>>(pool, cnt, mset, since_mode, since_version);
 }
 
 void launch_mc_extract(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const FrameCtl* ctl, const unsigned int* mset,
                        const unsigned long long* tombrec) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_mc_extract, kMcThreads, L.sms);
+  static const int grid = persistent_grid(k_mc_extract, kMcThreads, L.sms);
   k_mc_extract<<<grid, kMcThreads, 0, L.stream>>>(t, pool, cnt, ctl, mset, tombrec);
 }
 

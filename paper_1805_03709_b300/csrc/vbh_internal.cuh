@@ -262,6 +262,8 @@ __device__ __forceinline__ float2 two_prod(float a, float b) {
   return make_float2(p, __fmaf_rn(a, b, -p));
 }
 
+// CTAs of `kernel` that fit on the GPU at once (resident CTAs per SM x SMs).  Launchers keep it
+// in a function-local `static const` (computed by the first launch, thread-safe).
 template <class K>
 inline int persistent_grid(K kernel, int threads, int sms) {
   int occ = 0;
