@@ -246,19 +246,28 @@ def measured_peak():
         return 6400.0, "fallback"
 
 
+def device_source_digest(path):
+    """First 16 hex digits of the SHA-256 of a .cu file's device code: its text up to the end
+    of the anonymous namespace that holds the kernels and their helpers (the host launchers
+    after it do not change what the kernels compute or move)."""
+    import hashlib
+    text = open(path, encoding="utf-8").read()
+    end = text.index("\n}  // namespace\n")
+    return hashlib.sha256(text[:end].encode()).hexdigest()[:16]
+
+
 def profile_traffic(avg_touched):
     """DRAM bytes per fusion launch: the committed ncu summary's bytes per touched block (taken
     on the small-memory case of the same frames) scaled by this run's average touched blocks,
     if the summary was taken from the current kernel source (else None)."""
-    import hashlib
     src = os.path.join(ROOT, "paper_1805_03709_b300", "csrc", "frame.cu")
     prof = os.path.join(ROOT, "profiles", "k_integrate_room_640x480.txt")
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = device_source_digest(src)
         lines = open(prof).read().splitlines()
-    except OSError:
+    except (OSError, ValueError):
         return None
-    src_line = [l for l in lines if l.startswith("source_sha256_16:")]
+    src_line = [l for l in lines if l.startswith("device_source_sha256_16:")]
     per_block = [l for l in lines if l.startswith("dram_bytes_per_touched_block:")]
     if not src_line or not per_block or src_line[0].split(":")[1].strip() != digest:
         return None
