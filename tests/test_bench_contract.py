@@ -1,7 +1,8 @@
 """bench.py's reference arm (the CPU oracle timed on the host cores) on the CPU: it prints one
 JSON line with the fields the benchmark contract names, and under a multi-rank launch only rank
 0 runs it (the others exit 0 without work or output).  The small-memory case keeps the run to a
-few seconds: it renders 32 frames instead of 300, and one timed step is one room frame."""
+few seconds: it renders 32 frames instead of 300, and one timed step is one room frame.  Also
+the rule that ties the reported fusion DRAM traffic to the kernels' source."""
 import json
 import os
 import subprocess
@@ -40,3 +41,27 @@ def test_reference_arm_runs_on_rank_zero_only():
     p = run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_fusion_traffic_follows_the_device_code(tmp_path, monkeypatch):
+    """The ncu-derived DRAM traffic is reported only while the committed summary's hash equals
+    the hash of frame.cu's device code: an edit after the kernels' namespace (host launchers)
+    keeps it, an edit inside it makes it None."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "paper_1805_03709_b300", "csrc", "frame.cu")).read()
+    prof = open(os.path.join(ROOT, "profiles", "k_integrate_room_640x480.txt")).read()
+    fake = tmp_path / "repo"
+    (fake / "paper_1805_03709_b300" / "csrc").mkdir(parents=True)
+    (fake / "profiles").mkdir()
+    (fake / "profiles" / "k_integrate_room_640x480.txt").write_text(prof)
+    cu = fake / "paper_1805_03709_b300" / "csrc" / "frame.cu"
+    monkeypatch.setattr(bench, "ROOT", str(fake))
+    cu.write_text(src)
+    per_block = bench.profile_traffic(1.0)
+    assert per_block is not None and per_block > 0
+    assert bench.profile_traffic(1000.0) == 1000.0 * per_block
+    cu.write_text(src + "\n// a host-side edit after the kernels\n")
+    assert bench.profile_traffic(1.0) == per_block
+    cu.write_text(src.replace("namespace {", "namespace {\n// an edit among the kernels", 1))
+    assert bench.profile_traffic(1.0) is None
