@@ -18,8 +18,7 @@
 // threads) race and must be serialised by the caller.
 #include <mutex>
 
-#include "vbh.h"
-#include "vbh_internal.cuh"
+#include "handle.cuh"
 
 namespace vbh {
 
@@ -235,31 +234,32 @@ extern "C" vbh_status vbh_mc_from_tsdf_static(const int32_t* keys3_dev, const fl
                                               const vbh_mc_stream* out, void* cuda_stream,
                                               uint32_t* error_flags_dev) {
   using namespace vbh;
-  if (!out || !out->n_blocks_dev || !out->n_entries_dev) return VBH_ERR_INVALID_ARG;
-  if (n_blocks > kStaticMaxBlocks) return VBH_ERR_INVALID_ARG;   // scratch holds 2^15 blocks
-  if (n_blocks && (!keys3_dev || !tsdf_dev || !weight_dev)) return VBH_ERR_INVALID_ARG;
+  if (!out || !out->n_blocks_dev || !out->n_entries_dev)
+    return fail(VBH_ERR_INVALID_ARG, "vbh_mc_from_tsdf_static: null output stream or totals");
+  if (n_blocks > kStaticMaxBlocks)   // the scratch holds 2^15 blocks
+    return fail(VBH_ERR_INVALID_ARG,
+                "vbh_mc_from_tsdf_static: n_blocks above the fixed scratch limit of 32768");
+  if (n_blocks && (!keys3_dev || !tsdf_dev || !weight_dev))
+    return fail(VBH_ERR_INVALID_ARG, "vbh_mc_from_tsdf_static: null input pointer");
   if ((out->cap_blocks && (!out->keys3 || !out->info || !out->offsets || !out->counts)) ||
       (out->cap_entries && (!out->local || !out->index)))
-    return VBH_ERR_INVALID_ARG;
+    return fail(VBH_ERR_INVALID_ARG, "vbh_mc_from_tsdf_static: incomplete output stream");
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   void* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return VBH_ERR_CUDA;
+  VBH_CUDA(scratch_address(&base));
   unsigned char* b8 = static_cast<unsigned char*>(base);
   Slot* table = reinterpret_cast<Slot*>(b8);
   unsigned int* masks = reinterpret_cast<unsigned int*>(b8 + kTableBytes);
   unsigned int* err = reinterpret_cast<unsigned int*>(b8 + kTableBytes + kMaskBytes);
-  if (cudaMemsetAsync(out->n_entries_dev, 0, sizeof(uint32_t), stream) != cudaSuccess ||
-      cudaMemsetAsync(err, 0, sizeof(uint32_t), stream) != cudaSuccess)
-    return VBH_ERR_CUDA;
+  VBH_CUDA(cudaMemsetAsync(out->n_entries_dev, 0, sizeof(uint32_t), stream));
+  VBH_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), stream));
   if (n_blocks == 0) {
-    if (cudaMemsetAsync(out->n_blocks_dev, 0, sizeof(uint32_t), stream) != cudaSuccess)
-      return VBH_ERR_CUDA;
+    VBH_CUDA(cudaMemsetAsync(out->n_blocks_dev, 0, sizeof(uint32_t), stream));
   } else {
-    if (cudaMemsetAsync(table, 0xFF, kTableBytes, stream) != cudaSuccess) return VBH_ERR_CUDA;
+    VBH_CUDA(cudaMemsetAsync(table, 0xFF, kTableBytes, stream));
     int sms = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return VBH_ERR_CUDA;
+    VBH_CUDA(cudaGetDevice(&dev));
+    VBH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const unsigned int cap = (unsigned)sms * 16u;
     const int grid_p = (int)(n_blocks < cap ? n_blocks : cap);
     k_static_prepare<<<grid_p, 128, 0, stream>>>(table, masks, keys3_dev, tsdf_dev, weight_dev,
@@ -270,11 +270,10 @@ extern "C" vbh_status vbh_mc_from_tsdf_static(const int32_t* keys3_dev, const fl
                                             out->info, out->offsets, out->counts, out->local,
                                             out->index, out->cap_blocks, out->cap_entries,
                                             out->n_blocks_dev, out->n_entries_dev);
-    if (cudaGetLastError() != cudaSuccess) return VBH_ERR_CUDA;
+    VBH_CUDA(cudaGetLastError());
   }
-  if (error_flags_dev &&
-      cudaMemcpyAsync(error_flags_dev, err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream) !=
-          cudaSuccess)
-    return VBH_ERR_CUDA;
+  if (error_flags_dev)
+    VBH_CUDA(cudaMemcpyAsync(error_flags_dev, err, sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                             stream));
   return VBH_OK;
 }

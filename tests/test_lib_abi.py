@@ -103,3 +103,25 @@ def test_struct_layouts_match_the_header(V, tmp_path):
         assert int(got[n]) == ctypes.sizeof(cls), n
         for f, _ in cls._fields_:
             assert int(got[f"{n}.{f}"]) == getattr(cls, f).offset, f"{n}.{f}"
+
+
+def test_static_mc_entry_checks_its_arguments_before_any_device_work(V):
+    """vbh_mc_from_tsdf_static refuses sizes beyond its fixed scratch and incomplete arguments
+    with VBH_ERR_INVALID_ARG and a message, before it makes any CUDA call (so on the CPU too).
+    The pointers below are never dereferenced."""
+    import ctypes
+    lib = V.lib()
+    dummy = ctypes.c_uint32(0)
+    addr = ctypes.addressof(dummy)
+    out = V.vbh_mc_stream(addr, addr, addr, addr, addr, addr, 4, 4, addr, addr)
+    cases = [(addr, (1 << 15) + 1, ctypes.byref(out), "32768"),
+             (addr, 4, None, "null output"),
+             (None, 4, ctypes.byref(out), "null input")]
+    for keys, n, o, words in cases:
+        st = lib.vbh_mc_from_tsdf_static(keys, keys, keys, n, o, None, None)
+        assert st == V.VBH_ERR_INVALID_ARG
+        assert words in lib.vbh_last_error().decode()
+    incomplete = V.vbh_mc_stream(None, addr, addr, addr, addr, addr, 4, 4, addr, addr)
+    st = lib.vbh_mc_from_tsdf_static(addr, addr, addr, 4, ctypes.byref(incomplete), None, None)
+    assert st == V.VBH_ERR_INVALID_ARG
+    assert "incomplete output" in lib.vbh_last_error().decode()
