@@ -24,8 +24,7 @@
 // G and C are summed in float within a thread's samples and over the warp, then in double per
 // warp and per CTA; the per-CTA partials are reduced in a fixed order, so the pose gradient is
 // deterministic.
-#include "vbh.h"
-#include "vbh_internal.cuh"
+#include "handle.cuh"
 
 namespace vbh {
 
@@ -461,6 +460,12 @@ vbh::DiffParams diff_params(const vbh_diff* d) {
   c.words = (c.nf + 31) / 32;
   return c;
 }
+// The status of the launches just enqueued, with the CUDA error as the last-error message.
+vbh_status launched(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return VBH_OK;
+  return vbh::fail(VBH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
 int diff_grid(const vbh_diff* d, unsigned int n) {
   const unsigned int blocks = (n + vbh::kDiffThreads - 1) / vbh::kDiffThreads;
   const unsigned int cap = (unsigned)d->sms * 8u;
@@ -471,12 +476,14 @@ int diff_grid(const vbh_diff* d, unsigned int n) {
 extern "C" {
 
 vbh_status vbh_diff_create(const vbh_diff_config* cfg, void* cuda_stream, vbh_diff** out) {
-  if (!cfg || !out) return VBH_ERR_INVALID_ARG;
+  if (!cfg || !out) return vbh::fail(VBH_ERR_INVALID_ARG, "vbh_diff_create: null argument");
   *out = nullptr;
   if (!(cfg->voxel_size > 0.f) || !(cfg->trunc > 0.f) || cfg->width < 2 || cfg->height < 2 ||
       !(cfg->fx > 0.f) || !(cfg->fy > 0.f) || cfg->n_frames == 0 ||
       cfg->n_frames > (uint32_t)vbh::kMaxDiffFrames)
-    return VBH_ERR_INVALID_ARG;
+    return vbh::fail(VBH_ERR_INVALID_ARG,
+                     "vbh_diff_create: voxel_size, trunc, fx, fy must be > 0, width and height "
+                     ">= 2, n_frames in [1, " + std::to_string(vbh::kMaxDiffFrames) + "]");
   vbh_diff* d = new vbh_diff();
   d->cfg = *cfg;
   d->stream = (cudaStream_t)cuda_stream;
@@ -486,7 +493,7 @@ vbh_status vbh_diff_create(const vbh_diff_config* cfg, void* cuda_stream, vbh_di
       cudaMalloc(&d->poses, sizeof(vbh::DiffPose) * cfg->n_frames) != cudaSuccess ||
       cudaMalloc(&d->loss, sizeof(double)) != cudaSuccess) {
     vbh_diff_destroy(d);
-    return VBH_ERR_CUDA;
+    return vbh::fail(VBH_ERR_CUDA, "vbh_diff_create: device query or pose buffers failed");
   }
   d->bwd_smem = sizeof(double) * (vbh::kDiffThreads / 32) * 6 * cfg->n_frames +
                 sizeof(float) * 24 * cfg->n_frames;
@@ -498,13 +505,15 @@ vbh_status vbh_diff_create(const vbh_diff_config* cfg, void* cuda_stream, vbh_di
           cudaSuccess ||
       occ < 1) {
     vbh_diff_destroy(d);
-    return VBH_ERR_CUDA;
+    return vbh::fail(VBH_ERR_CUDA,
+                     "vbh_diff_create: the backward kernel does not fit with n_frames' shared "
+                     "memory");
   }
   d->bwd_grid = occ * d->sms;
   if (cudaMalloc(&d->part, sizeof(double) * 6 * cfg->n_frames * (size_t)d->bwd_grid) !=
       cudaSuccess) {
     vbh_diff_destroy(d);
-    return VBH_ERR_CUDA;
+    return vbh::fail(VBH_ERR_CUDA, "vbh_diff_create: device memory for the pose partials");
   }
   *out = d;
   return VBH_OK;
@@ -521,33 +530,34 @@ vbh_status vbh_diff_destroy(vbh_diff* d) {
 }
 
 vbh_status vbh_diff_poses(vbh_diff* d, const float* xi_dev, float* T_dev) {
-  if (!d || !xi_dev) return VBH_ERR_INVALID_ARG;
+  if (!d || !xi_dev) return vbh::fail(VBH_ERR_INVALID_ARG, "vbh_diff_poses: null argument");
   const int nf = (int)d->cfg.n_frames;
   vbh::k_diff_poses<<<(nf + 63) / 64, 64, 0, d->stream>>>(xi_dev, nf, d->poses, T_dev);
-  return cudaGetLastError() == cudaSuccess ? VBH_OK : VBH_ERR_CUDA;
+  return launched("vbh_diff_poses");
 }
 
 vbh_status vbh_diff_masks(vbh_diff* d, const int32_t* samples_dev, uint32_t n,
                           const float* depth_dev, const float* T0_dev, uint32_t* masks_dev) {
-  if (!d || (n && (!samples_dev || !depth_dev || !T0_dev || !masks_dev))) return VBH_ERR_INVALID_ARG;
+  if (!d || (n && (!samples_dev || !depth_dev || !T0_dev || !masks_dev)))
+    return vbh::fail(VBH_ERR_INVALID_ARG, "vbh_diff_masks: null argument");
   if (!n) return VBH_OK;
   vbh::k_diff_masks<<<diff_grid(d, n), vbh::kDiffThreads, 0, d->stream>>>(
       diff_params(d), samples_dev, n, depth_dev, T0_dev, masks_dev);
-  return cudaGetLastError() == cudaSuccess ? VBH_OK : VBH_ERR_CUDA;
+  return launched("vbh_diff_masks");
 }
 
 vbh_status vbh_diff_forward(vbh_diff* d, const int32_t* samples_dev, uint32_t n,
                             const float* depth_dev, const float* T0_dev, const float* xi_dev,
                             const uint32_t* masks_dev, float* F_dev, double* loss_dev) {
   if (!d || !xi_dev || !F_dev || (n && (!samples_dev || !depth_dev || !T0_dev || !masks_dev)))
-    return VBH_ERR_INVALID_ARG;
+    return vbh::fail(VBH_ERR_INVALID_ARG, "vbh_diff_forward: null argument");
   double* loss = loss_dev ? loss_dev : d->loss;
-  if (cudaMemsetAsync(loss, 0, sizeof(double), d->stream) != cudaSuccess) return VBH_ERR_CUDA;
+  VBH_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), d->stream));
   vbh_status st = vbh_diff_poses(d, xi_dev, nullptr);
   if (st != VBH_OK || !n) return st;
   vbh::k_diff_forward<<<diff_grid(d, n), vbh::kDiffThreads, 0, d->stream>>>(
       diff_params(d), samples_dev, n, depth_dev, T0_dev, d->poses, masks_dev, F_dev, loss);
-  return cudaGetLastError() == cudaSuccess ? VBH_OK : VBH_ERR_CUDA;
+  return launched("vbh_diff_forward");
 }
 
 vbh_status vbh_diff_backward(vbh_diff* d, const int32_t* samples_dev, uint32_t n,
@@ -556,10 +566,9 @@ vbh_status vbh_diff_backward(vbh_diff* d, const int32_t* samples_dev, uint32_t n
                              float* gxi_dev) {
   if (!d || !xi_dev || !gdepth_dev || !gxi_dev ||
       (n && (!samples_dev || !depth_dev || !T0_dev || !masks_dev || !F_dev)))
-    return VBH_ERR_INVALID_ARG;
+    return vbh::fail(VBH_ERR_INVALID_ARG, "vbh_diff_backward: null argument");
   const size_t npx = (size_t)d->cfg.n_frames * d->cfg.width * d->cfg.height;
-  if (cudaMemsetAsync(gdepth_dev, 0, npx * sizeof(float), d->stream) != cudaSuccess)
-    return VBH_ERR_CUDA;
+  VBH_CUDA(cudaMemsetAsync(gdepth_dev, 0, npx * sizeof(float), d->stream));
   vbh_status st = vbh_diff_poses(d, xi_dev, nullptr);
   if (st != VBH_OK) return st;
   const int nf = (int)d->cfg.n_frames;
@@ -573,7 +582,7 @@ vbh_status vbh_diff_backward(vbh_diff* d, const int32_t* samples_dev, uint32_t n
         gdepth_dev, d->part);
   }
   vbh::k_diff_pose_grad<<<nf, 192, 0, d->stream>>>(d->poses, d->part, parts, nf, gxi_dev);
-  return cudaGetLastError() == cudaSuccess ? VBH_OK : VBH_ERR_CUDA;
+  return launched("vbh_diff_backward");
 }
 
 }  // extern "C"

@@ -125,3 +125,23 @@ def test_static_mc_entry_checks_its_arguments_before_any_device_work(V):
     st = lib.vbh_mc_from_tsdf_static(addr, addr, addr, 4, ctypes.byref(incomplete), None, None)
     assert st == V.VBH_ERR_INVALID_ARG
     assert "incomplete output" in lib.vbh_last_error().decode()
+
+
+def test_diff_create_validates_its_config_before_any_device_work(V):
+    """vbh_diff_create checks its configuration (and pointers) before any CUDA call: a bad one
+    returns VBH_ERR_INVALID_ARG, names the rule in the last-error message and leaves *out null."""
+    import ctypes
+    lib = V.lib()
+    good = dict(voxel_size=0.005, trunc=0.02, fx=262.5, fy=262.5, cx=160.0, cy=120.0, width=320,
+                height=240, n_frames=64)
+    for field, value in [("n_frames", 0), ("n_frames", 257), ("width", 1), ("trunc", 0.0),
+                         ("voxel_size", float("nan")), ("fy", -1.0)]:
+        cfg = V.vbh_diff_config(**dict(good, **{field: value}))
+        out = ctypes.c_void_p(12345)
+        st = lib.vbh_diff_create(ctypes.byref(cfg), None, ctypes.byref(out))
+        assert st == V.VBH_ERR_INVALID_ARG, field
+        assert out.value is None, field
+        assert "n_frames in [1, 256]" in lib.vbh_last_error().decode()
+    st = lib.vbh_diff_create(None, None, None)
+    assert st == V.VBH_ERR_INVALID_ARG
+    assert "null argument" in lib.vbh_last_error().decode()
