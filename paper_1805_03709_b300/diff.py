@@ -36,7 +36,17 @@ class DiffFusion:
 
     __del__ = close
 
+    def _check(self, depth, xi):
+        c = self.cfg
+        if depth.dtype != torch.float32 or tuple(depth.shape) != (c.n_frames, c.height, c.width):
+            raise ValueError(f"depth must be float32 [{c.n_frames}, {c.height}, {c.width}], got "
+                             f"{depth.dtype} {tuple(depth.shape)}")
+        if xi.dtype != torch.float32 or tuple(xi.shape) != (c.n_frames, 6):
+            raise ValueError(f"xi must be float32 [{c.n_frames}, 6], got {xi.dtype} "
+                             f"{tuple(xi.shape)}")
+
     def forward_raw(self, depth, xi):
+        self._check(depth, xi)
         F = torch.empty(self.samples.shape[0], dtype=torch.float32, device=depth.device)
         loss = torch.zeros((), dtype=torch.float64, device=depth.device)
         V.vbh_diff_forward(self.h, self.samples, depth.contiguous(), self.T0, xi.contiguous(),
@@ -44,8 +54,10 @@ class DiffFusion:
         return loss, F
 
     def backward_raw(self, depth, xi, F):
-        gd = torch.empty_like(depth)
-        gx = torch.empty_like(xi)
+        self._check(depth, xi)
+        # dense outputs: the kernels write them in the dense layout whatever the inputs' strides
+        gd = torch.empty(depth.shape, dtype=torch.float32, device=depth.device)
+        gx = torch.empty(xi.shape, dtype=torch.float32, device=xi.device)
         V.vbh_diff_backward(self.h, self.samples, depth.contiguous(), self.T0, xi.contiguous(),
                             self.masks, F, gd, gx)
         return gd, gx
