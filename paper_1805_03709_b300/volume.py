@@ -45,6 +45,20 @@ class HashMap:
         if keys3.shape != (n, 3) or (vals is not None and vals.shape[0] < n):
             raise ValueError(f"batch of {n} ops needs keys3 [{n}, 3] (got {tuple(keys3.shape)})"
                              " and at least as many values")
+        # the kernels read and write these as dense device arrays of exactly these types
+        arrays = [(name, t, types) for name, t, types in (
+            ("ops", ops, (torch.uint8,)), ("keys3", keys3, (torch.int32,)),
+            ("vals", vals, (torch.int32, torch.uint32)),
+            ("results", results, (torch.int32, torch.uint32)),
+            ("status", status, (torch.uint8,))) if t is not None]
+        for name, t, types in arrays:
+            if t.dtype not in types:
+                raise ValueError(f"{name} must be {' or '.join(map(str, types))}, got {t.dtype}")
+        for name, t, _ in arrays:
+            if not (t.is_cuda and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous CUDA tensor")
+            if name in ("results", "status") and t.shape[0] < n:
+                raise ValueError(f"{name} holds {t.shape[0]} entries, the batch has {n} ops")
         if results is None:
             results = torch.empty(n, dtype=torch.int32, device=ops.device)
         if status is None:

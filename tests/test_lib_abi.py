@@ -145,3 +145,20 @@ def test_diff_create_validates_its_config_before_any_device_work(V):
     st = lib.vbh_diff_create(None, None, None)
     assert st == V.VBH_ERR_INVALID_ARG
     assert "null argument" in lib.vbh_last_error().decode()
+
+
+def test_hash_batch_binding_refuses_wrong_arrays_before_the_library():
+    """HashMap.batch checks shapes, dtypes and placement of its arrays in Python, before any
+    library call (a wrong dtype would make the kernels read the bytes as something else)."""
+    import torch
+    from paper_1805_03709_b300.volume import HashMap
+    hm = HashMap.__new__(HashMap)   # no device handle: every case below is refused first
+    ops = torch.zeros(4, dtype=torch.uint8)
+    keys = torch.zeros((4, 3), dtype=torch.int32)
+    cases = [(ops, torch.zeros((5, 3), dtype=torch.int32), "keys3 [4, 3]"),
+             (ops.to(torch.int32), keys, "ops must be torch.uint8"),
+             (ops, keys.to(torch.int64), "keys3 must be torch.int32"),
+             (ops, keys, "contiguous CUDA tensor")]
+    for o, k, words in cases:
+        with pytest.raises(ValueError, match=re.escape(words)):
+            hm.batch(o, k)
