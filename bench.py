@@ -241,7 +241,8 @@ class ClockSampler:
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        return float(json.load(open(p))["hbm_gbs"]), "measured"
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6400.0, "fallback"
 
@@ -251,7 +252,8 @@ def device_source_digest(path):
     of the anonymous namespace that holds the kernels and their helpers (the host launchers
     after it do not change what the kernels compute or move)."""
     import hashlib
-    text = open(path, encoding="utf-8").read()
+    with open(path, encoding="utf-8") as f:
+        text = f.read()
     end = text.index("\n}  // namespace\n")
     return hashlib.sha256(text[:end].encode()).hexdigest()[:16]
 
@@ -264,7 +266,8 @@ def profile_traffic(avg_touched):
     prof = os.path.join(ROOT, "profiles", "k_integrate_room_640x480.txt")
     try:
         digest = device_source_digest(src)
-        lines = open(prof).read().splitlines()
+        with open(prof) as f:
+            lines = f.read().splitlines()
     except (OSError, ValueError):
         return None
     src_line = [l for l in lines if l.startswith("device_source_sha256_16:")]

@@ -18,6 +18,14 @@ def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
+def _check_keys3(keys3: torch.Tensor):
+    """Block keys handed to the library by pointer: a dense [n, 3] int32 CUDA tensor."""
+    if keys3.dtype != torch.int32 or keys3.dim() != 2 or keys3.shape[1] != 3:
+        raise ValueError(f"keys3 must be int32 [n, 3], got {keys3.dtype} {tuple(keys3.shape)}")
+    if not (keys3.is_cuda and keys3.is_contiguous()):
+        raise ValueError("keys3 must be a contiguous CUDA tensor")
+
+
 class HashMap:
     """GPU map of int3 keys (Sec. 5).  With max_blocks > 0 the values are voxel-block pool
     indices (a voxel-block map); otherwise they are the caller's uint32 values."""
@@ -270,6 +278,7 @@ class Volume:
                                    else V.VBH_INTEGRATE_TOUCHED)
 
     def erase_keys(self, keys3: torch.Tensor, keys_out: bool = True):
+        _check_keys3(keys3)
         sel = V.vbh_erase_selector(mode=V.VBH_ERASE_KEYS, keys3_dev=keys3.data_ptr(),
                                    n_keys=int(keys3.shape[0]))
         V.vbh_erase_blocks(self.h, sel, self.erased_keys if keys_out else None,
@@ -282,6 +291,8 @@ class Volume:
     def extract(self, mode=V.VBH_MC_TOUCHED, keys3: torch.Tensor | None = None, since=0,
                 stream: McStream | None = None, sync=False):
         s = stream or self.stream
+        if keys3 is not None:
+            _check_keys3(keys3)
         sel = V.vbh_mc_selector(mode=mode, keys3_dev=keys3.data_ptr() if keys3 is not None else None,
                                 n_keys=int(keys3.shape[0]) if keys3 is not None else 0,
                                 since_version=since)

@@ -49,8 +49,10 @@ def test_fusion_traffic_follows_the_device_code(tmp_path, monkeypatch):
     keeps it, an edit inside it makes it None."""
     sys.path.insert(0, ROOT)
     import bench
-    src = open(os.path.join(ROOT, "paper_1805_03709_b300", "csrc", "frame.cu")).read()
-    prof = open(os.path.join(ROOT, "profiles", "k_integrate_room_640x480.txt")).read()
+    with open(os.path.join(ROOT, "paper_1805_03709_b300", "csrc", "frame.cu")) as f:
+        src = f.read()
+    with open(os.path.join(ROOT, "profiles", "k_integrate_room_640x480.txt")) as f:
+        prof = f.read()
     fake = tmp_path / "repo"
     (fake / "paper_1805_03709_b300" / "csrc").mkdir(parents=True)
     (fake / "profiles").mkdir()

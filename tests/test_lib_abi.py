@@ -19,8 +19,13 @@ def V():
     return vbh
 
 
+def read(*parts):
+    with open(os.path.join(ROOT, *parts), encoding="utf-8") as f:
+        return f.read()
+
+
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "vbh.h")).read()
+    src = read("include", "vbh.h")
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(vbh_[a-z_0-9]+)\s*\(", src)))
 
@@ -35,14 +40,14 @@ def test_every_declared_symbol_is_exported_and_bound(V):
 
 
 def test_abi_version(V):
-    src = open(os.path.join(ROOT, "include", "vbh.h")).read()
+    src = read("include", "vbh.h")
     ver = int(re.search(r"#define VBH_ABI_VERSION (\d+)", src).group(1))
     assert V.vbh_abi_version() == ver
 
 
 def test_paper_spatial_hash(V):
     primes = {}
-    for line in open(os.path.join(ROOT, "tests", "golden", "k1_spatial_hash.txt")):
+    for line in read("tests", "golden", "k1_spatial_hash.txt").splitlines():
         if line.strip() and not line.startswith("#"):
             k, v = line.split()
             primes[k] = int(v)
@@ -162,3 +167,19 @@ def test_hash_batch_binding_refuses_wrong_arrays_before_the_library():
     for o, k, words in cases:
         with pytest.raises(ValueError, match=re.escape(words)):
             hm.batch(o, k)
+
+
+def test_volume_key_lists_are_checked_before_the_library():
+    """Volume.erase_keys and Volume.extract(keys3=...) pass block keys by pointer: anything but a
+    dense [n, 3] int32 CUDA tensor is refused in Python."""
+    import torch
+    from paper_1805_03709_b300 import vbh as Vb
+    from paper_1805_03709_b300.volume import Volume
+    vol = Volume.__new__(Volume)   # no device handle: every case below is refused first
+    for k, words in [(torch.zeros((4, 3), dtype=torch.int64), "int32 [n, 3]"),
+                     (torch.zeros((4, 2), dtype=torch.int32), "int32 [n, 3]"),
+                     (torch.zeros((4, 3), dtype=torch.int32), "contiguous CUDA tensor")]:
+        with pytest.raises(ValueError, match=re.escape(words)):
+            vol.erase_keys(k)
+        with pytest.raises(ValueError, match=re.escape(words)):
+            vol.extract(Vb.VBH_MC_KEYS, keys3=k, stream=object())
