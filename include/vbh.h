@@ -152,7 +152,8 @@ vbh_status vbh_hash_rebuild(vbh_handle* h);
  * 0 = invalid), row-major; T_wc_host: 12 floats; frame_id: stored as the blocks' version by the
  * next touched-set extraction.  stats_host may be NULL (asynchronous) or receive the frame's
  * counts (synchronising).  Returns VBH_ERR_CAPACITY (only when stats_host is given) if the pool
- * or table ran out; the blocks that could be allocated are fused. */
+ * or table ran out; the blocks that could be allocated are fused; VBH_ERR_TIMEOUT (likewise) if
+ * a bounded device wait gave up (see vbh_set_wait_limit). */
 vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const float* T_wc_host,
                                uint32_t frame_id, vbh_frame_stats* stats_host);
 
@@ -290,6 +291,15 @@ vbh_status vbh_load(vbh_handle* h, const int32_t* keys3_host, const float* tsdf_
 vbh_status vbh_get_counters(vbh_handle* h, vbh_counters* out_host);
 vbh_status vbh_clear_errors(vbh_handle* h);
 
+/* Bounded device waits (failure detection; the paper states none).  The fusion kernel waits for
+ * each block's asynchronous voxel copy with at most `polls` polls (default 2^24); a wait that
+ * runs out raises error flag bit3, the warp drains its copy (bounded) and stops, the frame's
+ * remaining voxels of that warp are left unfused, and vbh_integrate_frame with stats_host
+ * returns VBH_ERR_TIMEOUT.  The flag is sticky until vbh_clear_errors; the handle stays usable.
+ * polls = 0 makes every such wait give up at once (fault injection for tests).  Takes effect
+ * from the next frame call. */
+vbh_status vbh_set_wait_limit(vbh_handle* h, uint32_t polls);
+
 /* Per-stage device timing: CUDA events are recorded on the handle's stream around each stage
  * whose bit (1 << stage) is set in `stage_mask` (0 = off).  vbh_timing_read synchronises and
  * returns, per stage since the last reset, the accumulated milliseconds of the timed stages and
@@ -349,14 +359,18 @@ vbh_status vbh_diff_backward(vbh_diff* d, const int32_t* samples_dev, uint32_t n
  *   keys3_dev: n_blocks distinct block coordinates in [-2^20, 2^20); tsdf_dev, weight_dev:
  *   n_blocks * 512 floats each (voxel lx + 8 ly + 64 lz); out: as for vbh_extract_mc_indices;
  *   error_flags_dev (may be NULL): one uint32 that receives bit0 = a key out of range, bit1 = a
- *   repeated key.  All pointers are caller-owned device memory.
+ *   repeated key, bit2 = the stream's capacity was exceeded (records beyond cap_blocks or
+ *   entries beyond cap_entries are not written; a record whose entries did not fit keeps its
+ *   offset and count, so offset + count > cap_entries: check this bit or the totals before
+ *   reading entries).  All pointers are caller-owned device memory.
  * Scratch: a fixed 8 MiB + 256 B array in the library's device memory (every GPU that loads
  * the library holds it until exit); n_blocks is limited to 32768 and larger sizes return
  * VBH_ERR_INVALID_ARG without touching the device.  The call issues only memsets, kernels and a
  * device-to-device copy; it never calls cudaMalloc or cudaFree.  The first call on a device
  * looks up the array's device address on that device (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  Every call reuses the same array,
- * so calls whose work overlaps on the GPU race: serialise them. */
+ * current); make that first call before any stream capture.  The address is kept for the life
+ * of the process: do not use this entry point again on a device after cudaDeviceReset.  Every
+ * call reuses the same array, so calls whose work overlaps on the GPU race: serialise them. */
 vbh_status vbh_mc_from_tsdf_static(const int32_t* keys3_dev, const float* tsdf_dev,
                                    const float* weight_dev, uint32_t n_blocks,
                                    const vbh_mc_stream* out, void* cuda_stream,

@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call([
-            "g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+            "g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
             "-fno-fast-math", "-fexcess-precision=standard", _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
@@ -90,8 +90,22 @@ def lib():
         L.orc_vol_mc_set.argtypes = [P, I32, P, U32, P, U32, P]
         L.orc_vol_mc_set.restype = U32
         L.orc_vol_mc_dense.argtypes = [P, P, U32, P, P]
+        L.orc_set_threads.argtypes = [I32]
+        L.orc_get_threads.restype = I32
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Timing mode of every oracle call: 1 = the single-threaded reference (default); n > 1 runs
+    the allocation's image rows and the fusion's and MC classification's blocks on n OpenMP
+    threads.  Results are identical in every mode (blocks are independent; the allocation is a
+    set union); hash operations always run serially."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return lib().orc_get_threads()
 
 
 def _p(a: np.ndarray | None):

@@ -1,7 +1,9 @@
 // CPU ORACLE for the voxel-block-hashing hot path -- TEST INFRASTRUCTURE ONLY.
 //
 // Plain, slow and deliberately obvious: a std::unordered_map key store, FP64 projective TSDF
-// values, sequential allocation / integration / erase / Marching-Cubes classification.  Only the
+// values, sequential allocation / integration / erase / Marching-Cubes classification (a timing
+// mode runs the allocation's rows and the fusion's and classification's independent blocks on
+// OpenMP threads, with identical results; hash operations always run serially).  Only the
 // tests, the smoke check and the benchmark's CPU-baseline leg load this library; the product
 // path never does.  It shares no code, header, table or constant with the CUDA library.
 //
@@ -66,6 +68,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <omp.h>
 #include <set>
 #include <unordered_map>
 #include <vector>
@@ -131,11 +134,18 @@ int band_steps(float mu, float s) {
   return (int)std::ceil(2.0 * (double)mu / (double)s - 1e-6);
 }
 
-// R-canon, allocation: collect the block of every band sample of every valid pixel.
-void allocate_blocks(const Volume& v, const uint16_t* depth, const float* T, std::set<K3>& out) {
+// Timing mode: 1 = the single-threaded reference; n > 1 = OpenMP over image rows (allocation)
+// and over blocks (fusion, MC classification).  Blocks are independent in both steps and a set
+// union does not depend on the order of its inserts, so every mode gives the same results.
+int g_threads = 1;
+
+// R-canon, allocation: collect the block of every band sample of every valid pixel of rows
+// [pv0, pv1).
+void allocate_rows(const Volume& v, const uint16_t* depth, const float* T, int pv0, int pv1,
+                   std::set<K3>& out) {
   const float inv_bs = 1.0f / (8.0f * v.s);
   const int J = band_steps(v.mu, v.s);
-  for (int pv = 0; pv < v.height; ++pv) {
+  for (int pv = pv0; pv < pv1; ++pv) {
     for (int pu = 0; pu < v.width; ++pu) {
       uint16_t raw = depth[(size_t)pv * v.width + pu];
       if (raw == 0) continue;
@@ -168,6 +178,22 @@ void allocate_blocks(const Volume& v, const uint16_t* depth, const float* T, std
       }
     }
   }
+}
+
+// The allocation of a whole frame: the union over all rows.
+void allocate_blocks(const Volume& v, const uint16_t* depth, const float* T, std::set<K3>& out) {
+  if (g_threads <= 1) {
+    allocate_rows(v, depth, T, 0, v.height, out);
+    return;
+  }
+  std::vector<std::set<K3>> part(g_threads);
+#pragma omp parallel num_threads(g_threads)
+  {
+    const int i = omp_get_thread_num(), n = omp_get_num_threads();
+    allocate_rows(v, depth, T, (int)((long)v.height * i / n), (int)((long)v.height * (i + 1) / n),
+                  part[i]);
+  }
+  for (auto& p : part) out.insert(p.begin(), p.end());
 }
 
 // R-canon + R5 + R-value: fuse one frame into one block.
@@ -500,7 +526,11 @@ uint32_t orc_vol_integrate_mode(void* h, const uint16_t* depth, const float* T, 
   if (visible)
     for (auto& kv : v.blocks)
       if (in_view(v, kv.first, T, v.zmax)) s.insert(kv.first);
-  for (const K3& k : s) integrate_block(v, k, v.blocks[k], depth, T);
+  std::vector<std::pair<K3, Block*>> work;
+  for (const K3& k : s) work.emplace_back(k, &v.blocks[k]);
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 64) if (g_threads > 1)
+  for (long i = 0; i < (long)work.size(); ++i)
+    integrate_block(v, work[i].first, *work[i].second, depth, T);
   v.touched = s;
   return (uint32_t)s.size();
 }
@@ -701,7 +731,8 @@ uint32_t orc_vol_mc_set(void* h, int mode, int32_t* keys3, uint32_t cap, int32_t
 // Dense MC indices (512 per block, x fastest) and the per-cube margin min|F| for given blocks.
 void orc_vol_mc_dense(void* h, const int32_t* keys3, uint32_t n, uint8_t* idx, float* margin) {
   Volume& v = *(Volume*)h;
-  for (uint32_t b = 0; b < n; ++b)
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 64) if (g_threads > 1)
+  for (long b = 0; b < (long)n; ++b)
     for (int lz = 0; lz < 8; ++lz)
       for (int ly = 0; ly < 8; ++ly)
         for (int lx = 0; lx < 8; ++lx) {
@@ -716,6 +747,10 @@ void orc_vol_mc_dense(void* h, const int32_t* keys3, uint32_t n, uint8_t* idx, f
 
 // The version of the oracle library (for the tests' build check).
 int orc_abi_version() { return 1; }
+
+// Timing mode (see g_threads): n <= 1 the single-threaded reference, else n OpenMP threads.
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int orc_get_threads() { return g_threads; }
 
 }  // extern "C"
 

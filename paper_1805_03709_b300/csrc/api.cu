@@ -170,6 +170,7 @@ FrameParams frame_params(const vbh_handle* h, const float* T) {
   fp.width = c.width;
   fp.height = c.height;
   fp.J = h->J;
+  fp.wait_limit = h->wait_limit;
   return fp;
 }
 
@@ -491,6 +492,8 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
     VBH_CUDA(cudaStreamSynchronize(h->stream));
     read_frame_stats(h, d, stats_host);
     if (d.err & (kErrPool | kErrTable)) return fail(VBH_ERR_CAPACITY, "block pool or table full");
+    if (d.err & kErrTimeout)
+      return fail(VBH_ERR_TIMEOUT, "a bounded device wait gave up (fusion's voxel copy)");
   }
   snapshot_counters(h);
   return VBH_OK;
@@ -952,6 +955,12 @@ vbh_status vbh_get_counters(vbh_handle* h, vbh_counters* out) {
   out->total_touched = d.tot_touched;
   out->total_new = d.tot_new;
   out->total_written = d.tot_written;
+  return VBH_OK;
+}
+
+vbh_status vbh_set_wait_limit(vbh_handle* h, uint32_t polls) {
+  if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  h->wait_limit = polls;
   return VBH_OK;
 }
 

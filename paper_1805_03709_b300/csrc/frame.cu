@@ -194,10 +194,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Bounded wait: false (and the sticky timeout flag) if the copy has not landed in time.
+// Bounded wait: false (and the sticky timeout flag) if the copy has not landed within `limit`
+// polls (limit 0 gives up at once: the handle's fault-injection setting).
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity,
-                                          DevCounters* cnt) {
-  for (unsigned int i = 0; i < (1u << 24); ++i)
+                                          unsigned int limit, DevCounters* cnt) {
+  for (unsigned int i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   atomicOr(&cnt->err, kErrTimeout);
   return false;
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
       if (g == 0 && !fresh) {
         // the unit's voxels are needed from here on: their copy has been in flight during
         // the projections and the first group's depth fetches
-        alive = __all_sync(0xFFFFFFFFu, mbar_wait(&sbar[warp], parity, cnt));
+        alive = __all_sync(0xFFFFFFFFu, mbar_wait(&sbar[warp], parity, fp.wait_limit, cnt));
         if (!alive) break;   // a copy that never landed (flag raised): stop this warp
         parity ^= 1u;
       }

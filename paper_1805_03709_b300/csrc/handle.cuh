@@ -108,6 +108,7 @@ struct vbh_handle {
   cudaKernelNodeParams integ_kp{};        // patched before every launch
   int graph_timed = 0;             // stage mask the captured graph brackets with events
   uint32_t integ_mode = 0;         // VBH_INTEGRATE_*
+  uint32_t wait_limit = 1u << 24;  // polls of the fusion kernel's bounded copy wait
   uint32_t graph_mode = 0;         // integration mode the frame graph was captured with
   uint64_t graph_kernels = 0;
   // bookkeeping

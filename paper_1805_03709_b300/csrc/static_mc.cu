@@ -11,7 +11,8 @@
 // Scratch: one file-scope __device__ array of kScratchBytes (8 MiB + 256 B), present on every
 // GPU that loads this library until the process exits.  Its first part is a key -> block-index
 // hash table (2^16 buckets x 4 slots x 16 B), its second part the per-block sign/weight bit
-// masks (2^15 blocks x 128 B), its last part an error word.  Every call re-initialises what it
+// masks (2^15 blocks x 128 B), its last part an error word (bit0 key out of range, bit1 repeated
+// key, bit2 stream capacity exceeded).  Every call re-initialises what it
 // reads (the table is reset to EMPTY, the error word to 0, the masks of every input block are
 // rewritten), so what a previous call left behind does not matter -- but all calls share the
 // one array: calls whose work overlaps on the GPU (on different streams, or from different host
@@ -110,7 +111,8 @@ __global__ void __launch_bounds__(128) k_static_mc(const Slot* table, const unsi
                                                    unsigned int cap_blocks,
                                                    unsigned int cap_entries,
                                                    unsigned int* n_blocks_dev,
-                                                   unsigned int* n_entries_dev) {
+                                                   unsigned int* n_entries_dev,
+                                                   unsigned int* err) {
   __shared__ unsigned long long spread[256];
   __shared__ unsigned int msk[4][8][32];
   for (int b = threadIdx.x; b < 256; b += blockDim.x) {
@@ -181,7 +183,9 @@ __global__ void __launch_bounds__(128) k_static_mc(const Slot* table, const unsi
     unsigned int base = 0;
     if (lane == 0 && tot) base = atomicAdd(n_entries_dev, tot);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if ((unsigned long long)base + tot <= cap_entries) {
+    const bool fits = (unsigned long long)base + tot <= cap_entries;
+    if (lane == 0 && (!fits || r >= cap_blocks)) atomicOr(err, 4u);   // stream overflow
+    if (fits) {
       unsigned int o = base + incl - mine;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -209,7 +213,9 @@ __global__ void __launch_bounds__(128) k_static_mc(const Slot* table, const unsi
 }
 
 // Device address of the scratch array on the current device; looked up once per device with
-// that device current.
+// that device current and kept for the life of the process (a cudaDeviceReset reloads the
+// module, after which the kept address is stale: the entry point is not for processes that
+// reset a device they have used it on).
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -269,7 +275,7 @@ extern "C" vbh_status vbh_mc_from_tsdf_static(const int32_t* keys3_dev, const fl
     k_static_mc<<<grid_m, 128, 0, stream>>>(table, masks, keys3_dev, n_blocks, out->keys3,
                                             out->info, out->offsets, out->counts, out->local,
                                             out->index, out->cap_blocks, out->cap_entries,
-                                            out->n_blocks_dev, out->n_entries_dev);
+                                            out->n_blocks_dev, out->n_entries_dev, err);
     VBH_CUDA(cudaGetLastError());
   }
   if (error_flags_dev)

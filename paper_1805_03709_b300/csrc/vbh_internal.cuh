@@ -287,6 +287,7 @@ struct FrameParams {
   int width, height;
   int J;               // band steps: samples j = 0..J
   unsigned int raw_max;   // raw depth r is valid iff 1 <= r <= raw_max (fl(r ds) <= zmax)
+  unsigned int wait_limit;   // polls of a bounded device wait before it gives up
   const unsigned short* depth;
 };
 

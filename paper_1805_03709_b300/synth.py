@@ -26,6 +26,7 @@ import numpy as np
 __all__ = [
     "Camera", "Scene", "make_tiny_scene", "make_room_scene", "render_depth_m",
     "quantize_mm", "tiny_sequence", "room_sequence", "room_frames", "room_camera", "look_at",
+    "room_static_frames",
     "random_hash_keys", "distinct_keys", "zipf_cluster_keys", "diff_window", "surface_samples",
 ]
 
@@ -274,6 +275,26 @@ def room_sequence(n_frames: int = 300, seed: int = 1805, width: int = 640, heigh
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
         parts = list(ex.map(functools.partial(room_frames, **kw), chunks))
     return cam, poses, np.concatenate(parts)
+
+
+def room_static_frames(n_frames: int, pose_index: int = 0, seed: int = 1805, width: int = 160,
+                       height: int = 120, f: float = 525.0, dropout: float = 0.02):
+    """`n_frames` depth frames seen from ONE pose of the room walk (frame `pose_index` of a
+    300-frame walk), each with its own seeded axial noise (sigma = 1.5 mm * z^2) and dropout:
+    a camera held still, so every voxel in view is observed once per frame and its weight runs
+    up to and past any cap.  Returns (camera, pose (3,4) f32, depth (n,H,W) u16 mm)."""
+    scene = make_room_scene(seed)
+    cam = room_camera(width, height, f)
+    T = room_trajectory(300, seed)[pose_index]
+    z0 = render_depth_m(scene, cam, T)
+    out = []
+    for i in range(n_frames):
+        rng = np.random.default_rng([seed + 13, int(i)])
+        z = z0 + rng.standard_normal(z0.shape) * (0.0015 * np.where(np.isfinite(z0), z0, 0.0) ** 2)
+        if dropout > 0:
+            z = np.where(rng.uniform(size=z.shape) < dropout, np.inf, z)
+        out.append(quantize_mm(z))
+    return cam, T, np.stack(out)
 
 
 def distinct_keys(n: int, seed: int) -> np.ndarray:

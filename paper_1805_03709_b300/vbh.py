@@ -102,6 +102,7 @@ SYMBOLS = [
     ("vbh_load", ctypes.c_int, [_p, _p, _p, _p, _u32]),
     ("vbh_get_counters", ctypes.c_int, [_p, ctypes.POINTER(vbh_counters)]),
     ("vbh_clear_errors", ctypes.c_int, [_p]),
+    ("vbh_set_wait_limit", ctypes.c_int, [_p, _u32]),
     ("vbh_timing_enable", ctypes.c_int, [_p, ctypes.c_int]),
     ("vbh_timing_read", ctypes.c_int, [_p, _p, _p, ctypes.c_int]),
     ("vbh_diff_create", ctypes.c_int,
@@ -329,6 +330,11 @@ def vbh_clear_errors(h):
     _check(lib().vbh_clear_errors(h), "vbh_clear_errors")
 
 
+def vbh_set_wait_limit(h, polls: int):
+    """Polls of the fusion kernel's bounded copy wait (default 2^24; 0 = give up at once)."""
+    _check(lib().vbh_set_wait_limit(h, int(polls)), "vbh_set_wait_limit")
+
+
 def vbh_timing_enable(h, stage_mask: int):
     """stage_mask: bit (1 << i) times stage VBH_STAGES[i]; 0 turns timing off."""
     _check(lib().vbh_timing_enable(h, int(stage_mask)), "vbh_timing_enable")
@@ -341,10 +347,34 @@ def vbh_timing_read(h, reset: bool = False):
     return dict(zip(VBH_STAGES, ms.tolist())), dict(zip(VBH_STAGES, n.tolist()))
 
 
+def _check_static_mc_args(keys3, tsdf, weight, error_flags):
+    """The kernels read 3 n int32 keys and 512 n floats from each of tsdf and weight, and write
+    one uint32 error word: refuse anything else before the library call (dtypes and shapes
+    first, then placement)."""
+    import torch
+    if keys3.dtype != torch.int32 or keys3.dim() != 2 or keys3.shape[1] != 3:
+        raise ValueError(f"keys3 must be int32 [n, 3], got {keys3.dtype} {tuple(keys3.shape)}")
+    n = int(keys3.shape[0])
+    for name, t in (("tsdf", tsdf), ("weight", weight)):
+        if t.dtype != torch.float32 or t.numel() != n * 512:
+            raise ValueError(f"{name} must be float32 with n * 512 = {n * 512} elements, got "
+                             f"{t.dtype} {tuple(t.shape)}")
+    if error_flags is not None and (error_flags.dtype not in (torch.int32, torch.uint32)
+                                    or error_flags.numel() < 1):
+        raise ValueError("error_flags must be int32 or uint32 with at least one element")
+    arrays = [keys3, tsdf, weight] + ([error_flags] if error_flags is not None else [])
+    for t in arrays:
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("keys3, tsdf, weight and error_flags must be contiguous CUDA tensors")
+    if len({t.device for t in arrays}) != 1:
+        raise ValueError("keys3, tsdf, weight and error_flags must be on one device")
+
+
 def vbh_mc_from_tsdf_static(keys3, tsdf, weight, out: vbh_mc_stream, stream=None,
                             error_flags=None):
     """MC stream of caller-owned TSDF blocks using only the library's fixed scratch array (no
     device allocation inside the call; at most 32768 blocks)."""
+    _check_static_mc_args(keys3, tsdf, weight, error_flags)
     _check(lib().vbh_mc_from_tsdf_static(_ptr(keys3), _ptr(tsdf), _ptr(weight),
                                          int(keys3.shape[0]), ctypes.byref(out), stream,
                                          _ptr(error_flags)), "vbh_mc_from_tsdf_static")

@@ -5,6 +5,8 @@ Bar: allocated block sets, MC block sets and removal records bit-exact; weights 
 values within TSDF_TOL (normalised units, i.e. 1e-5 x truncation in metres); MC indices exact
 at every cube whose eight corners have |oracle TSDF| > MC_MARGIN (elsewhere the FP32 sign may
 legitimately differ from the FP64 one)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -127,6 +129,80 @@ def test_room_full_size_frames():
     sel = [0, 1, 39]
     vol, orc = make_pair(cam, 0.005, 0.02, 1 << 22, 1 << 19, zmax=4.0)
     run_sequence(vol, orc, depth[sel], poses[sel], erase_radius=4.0)
+
+
+def test_room_full_size_long_sequence():
+    """130 consecutive 640 x 480 frames of the room walk with the full configuration (2^22 x 4
+    table, 2^19-block pool, voxel 5 mm, truncation 2 cm, 4 m erase from frame 46 on): touched
+    counts, erased sets and MC block sets every frame; the whole volume (TSDF within 1e-5,
+    weights exact) and every MC index at frames 0, 20, ..., 120 and 129.  Long sequences are
+    where FP32 running-average error would compound."""
+    ncpu = os.cpu_count() or 1
+    cam, poses, depth = synth.room_sequence(n_frames=130, workers=min(8, ncpu))
+    oracle.set_threads(ncpu)
+    try:
+        vol, orc = make_pair(cam, 0.005, 0.02, 1 << 22, 1 << 19, zmax=4.0)
+        run_sequence(vol, orc, depth, poses, erase_radius=4.0, check_every=20)
+        assert vol.counters().total_frames == 130
+        _, _, W = orc.dump()
+        assert W.max() >= 60       # blocks in view since the first frame carry long histories
+    finally:
+        oracle.set_threads(1)
+
+
+def test_weight_cap_static_pose_80_frames():
+    """A camera held still for 80 noisy frames (the noise differs per frame): every voxel in view
+    is fused once per frame, so its weight reaches the cap Wmax = 64 at frame 64 and the capped
+    running average F <- (64 F + f) / 65 runs over the last 16 frames.  Volume and MC indices
+    against the oracle at frames 1, 20, 40, 63, 64, 65, 72 and 80."""
+    cam, T, depth = synth.room_static_frames(80)
+    vol, orc = make_pair(cam, 0.005, 0.02, 1 << 16, 1 << 16, zmax=4.0)
+    check = {1, 20, 40, 63, 64, 65, 72, 80}
+    at64 = None
+    for i in range(80):
+        st = vol.integrate(torch.from_numpy(depth[i]).cuda(), T, i + 1, stats=True)
+        assert st.touched == orc.integrate(depth[i], T) and st.error_flags == 0
+        s = vol.extract(V.VBH_MC_TOUCHED)
+        M, rem = orc.mc_set(0)
+        if i + 1 in check:
+            compare_volume(vol, orc)
+            compare_mc(s.to_host(), orc, M, rem)
+        if i + 1 == 64:
+            at64 = orc.dump()
+    k, F, W = orc.dump()
+    pos = {tuple(b): i for i, b in enumerate(k.tolist())}
+    sel = np.array([pos[tuple(b)] for b in at64[0].tolist()])   # blocks live at frame 64
+    capped = (at64[2] == 64) & (W[sel] == 64)
+    assert capped.sum() > 50000                   # voxels that ran 16 capped updates
+    assert (np.abs(F[sel] - at64[1])[capped] > 1e-3).mean() > 0.5   # ... which moved their values
+
+
+@pytest.mark.parametrize("wset", [(63.0,), (64.0,), (0.0, 1.0, 62.0, 63.0, 64.0)])
+def test_loaded_weights_at_the_cap_then_frames(wset):
+    """Blocks uploaded with weights at (64) and just below (63) the cap, then fused by three
+    frames: the first update of a W = 63 voxel reaches the cap, a W = 64 voxel takes the capped
+    average (64 F + f) / 65 at once.  Volume and MC indices against the oracle after each frame."""
+    cam, poses, depth = synth.room_sequence(n_frames=3, width=160, height=120)
+    vol, orc = make_pair(cam, 0.005, 0.02, 1 << 16, 1 << 16, zmax=4.0)
+    keys = orc.alloc_keys(depth[0], poses[0])
+    rng = np.random.default_rng(64)
+    F = rng.uniform(-1.0, 1.0, (len(keys), 512)).astype(np.float32)
+    W = rng.choice(np.array(wset, np.float32), (len(keys), 512))
+    F[W == 0] = 0.0
+    vol.load(keys, F, W)
+    orc.load(keys, F.astype(np.float64), W.astype(np.float64))
+    compare_volume(vol, orc)
+    for i in range(3):
+        st = vol.integrate(torch.from_numpy(depth[i]).cuda(), poses[i], i + 1, stats=True)
+        assert st.touched == orc.integrate(depth[i], poses[i]) and st.error_flags == 0
+        s = vol.extract(V.VBH_MC_TOUCHED)
+        M, rem = orc.mc_set(0)
+        compare_volume(vol, orc)
+        compare_mc(s.to_host(), orc, M, rem)
+    _, Fo, Wo = orc.dump()
+    assert Wo.max() == 64.0
+    if 64.0 in wset:
+        assert Wo.min() >= 0.0 and (Wo == 64.0).mean() > 0.3
 
 
 def test_empty_and_out_of_range_frames():

@@ -183,3 +183,30 @@ def test_volume_key_lists_are_checked_before_the_library():
             vol.erase_keys(k)
         with pytest.raises(ValueError, match=re.escape(words)):
             vol.extract(Vb.VBH_MC_KEYS, keys3=k, stream=object())
+
+
+def test_static_mc_binding_refuses_wrong_arrays_before_the_library():
+    """vbh.vbh_mc_from_tsdf_static checks dtypes, sizes and placement in Python before the
+    library call: its kernels read 3 n int32 keys and 512 n floats from tsdf and weight and write
+    one uint32 flag word, so any other layout would read or write out of bounds."""
+    import torch
+    from paper_1805_03709_b300 import vbh as Vb
+    n = 4
+    keys = torch.zeros((n, 3), dtype=torch.int32)
+    F = torch.zeros((n, 512), dtype=torch.float32)
+    err = torch.zeros(1, dtype=torch.int32)
+    cases = [((keys.to(torch.int64), F, F, None), "keys3 must be int32 [n, 3]"),
+             ((keys[:, :2], F, F, None), "keys3 must be int32 [n, 3]"),
+             ((keys, F[:, :256], F, None), "tsdf must be float32 with n * 512"),
+             ((keys, F, F.to(torch.float16), None), "weight must be float32 with n * 512"),
+             ((keys, F.to(torch.float64), F, None), "tsdf must be float32"),
+             ((keys, F, F, torch.zeros(1, dtype=torch.uint8)), "error_flags must be int32"),
+             ((keys, F, F, torch.zeros(0, dtype=torch.int32)), "error_flags must be int32"),
+             ((keys, F, F, err), "contiguous CUDA tensors"),
+             ((keys, F.t(), F, None), "contiguous CUDA tensors")]
+    for (k, t, w, e), words in cases:
+        with pytest.raises(ValueError, match=re.escape(words)):
+            Vb.vbh_mc_from_tsdf_static(k, t, w, None, None, e)
+    # a host (numpy) array is refused as well
+    with pytest.raises((ValueError, AttributeError)):
+        Vb.vbh_mc_from_tsdf_static(keys.numpy(), F, F, None, None)

@@ -88,10 +88,97 @@ def test_plane_value_closed_form():
     assert L == pytest.approx(np.sum(F ** 2), rel=1e-14)
 
 
-def small_window():
+def wall_camera_xyz(g, xi, s):
+    """FP64 camera coordinates (rows) of voxels g at pose exp(xi)."""
+    R, t, _, _ = oracle.se3_exp(xi)
+    return (g * np.float64(np.float32(s)) - t) @ R
+
+
+def clear_of_pixel_edges(p, f, W, H, eps=1e-4):
+    """Projections (FP64) that are not within eps of a pixel edge, and their cells."""
+    u = f * p[:, 0] / p[:, 2] + W / 2
+    v = f * p[:, 1] / p[:, 2] + H / 2
+    clear = (np.abs(u - np.rint(u)) > eps) & (np.abs(v - np.rint(v)) > eps)
+    return clear, np.floor(u).astype(int), np.floor(v).astype(int)
+
+
+@pytest.mark.parametrize("delta_over_mu, valid_across", [
+    (0.5, True), (1.0, True), (1.0 + 2.0 ** -15, False), (1.5, False), (2.5, False)])
+def test_depth_span_rule_isolated_spikes(delta_over_mu, valid_across):
+    """R-diff-3's discontinuity rule: a cell is valid only when its FOUR depths span at most mu.
+    The wall at Z0 carries isolated pixels raised by delta on a 4 x 4 grid, so a raised pixel
+    sits in each corner position (00, 10, 01, 11) of some cells.  Expected validity is computed
+    here from the FP64 projection: inside the image, and no raised corner unless delta <= mu.
+    mu = 2^-5 and Z0 = 1.25 make Z0 + delta and the float32 span exact, so delta = mu must be
+    valid (the bound is inclusive) and delta = mu (1 + 2^-15) must not be.  A span over two
+    corners, a strict bound, or a bound of 2 mu each fail one of the cases."""
+    s, mu, Z0, f, W, H = 0.01, 2.0 ** -5, 1.25, 20.0, 40, 30
+    xis, T0, depth = plane_setup(nf=1, W=W, H=H, Z0=Z0)
+    delta = np.float32(mu * delta_over_mu)
+    spike = np.zeros((H, W), bool)
+    spike[2::4, 1::4] = True
+    depth[0][spike] = np.float32(Z0) + delta
+    assert np.float32(depth[0][spike][0] - np.float32(Z0)) == delta
+    # samples in front of the wall (sdf > 0 >= -mu whatever the cell interpolates)
+    g = np.array([(x, y, z) for x in range(100, 124, 2) for y in range(-30, 31)
+                  for z in range(-22, 23)], np.int32)
+    o = oracle.OracleDiffFusion(s, mu, W, H, f, f, W / 2, H / 2, g, depth, T0)
+    valid = o.masks[:, 0] != 0
+    p = wall_camera_xyz(g, xis[0], s)
+    clear, iu, iv = clear_of_pixel_edges(p, f, W, H)
+    inside = (iu >= 0) & (iu <= W - 2) & (iv >= 0) & (iv <= H - 2)
+    iu_c, iv_c = np.clip(iu, 0, W - 2), np.clip(iv, 0, H - 2)
+    corners = [spike[iv_c + b, iu_c + a] for b in (0, 1) for a in (0, 1)]
+    raised = np.any(corners, axis=0)
+    expect = inside & (~raised | valid_across)
+    np.testing.assert_array_equal(valid[clear], expect[clear])
+    # every corner position of a raised pixel is exercised by clear samples
+    for c in corners:
+        assert np.sum(clear & inside & c) > 10
+    assert np.sum(clear & inside & ~raised) > 100
+
+
+@pytest.mark.parametrize("eps_over_mu", [0.3, -0.3])
+def test_clamp_side_fixed_at_nominal_pose(eps_over_mu):
+    """R-diff-3's fixed clamp side: at the nominal pose a valid term is live (f = sdf / mu)
+    when sdf0 < mu and saturated (f = 1) otherwise, and keeps that side at every other pose --
+    a live term is extended linearly past +-1, a saturated one stays 1.  The camera moves by eps
+    along its optical axis in front of a uniform wall, so every sdf grows by exactly eps; F of
+    a single frame is compared with that closed form."""
+    s, mu, Z0, f, W, H = 0.004, 0.04, 1.3, 20.0, 40, 30
+    xis, T0, depth = plane_setup(nf=1, W=W, H=H, Z0=Z0)
+    g = np.array([(x, y, z) for x in range(303, 348) for y in range(-200, 201, 50)
+                  for z in range(-150, 151, 50)], np.int32)
+    o = oracle.OracleDiffFusion(s, mu, W, H, f, f, W / 2, H / 2, g, depth, T0)
+    valid = o.masks[:, 0] != 0
+    eps = eps_over_mu * mu
+    # the moved pose: camera centre at world (eps, 0, 0), same rotation
+    M = np.eye(4)
+    M[:3, :3] = oracle.se3_exp(xis[0])[0]
+    M[:3, 3] = [eps, 0.0, 0.0]
+    Lg = np.real(scipy.linalg.logm(M))
+    xi1 = np.array([[Lg[0, 3], Lg[1, 3], Lg[2, 3], Lg[2, 1], Lg[0, 2], Lg[1, 0]]])
+    _, F = o.forward(xi1)
+    p0 = wall_camera_xyz(g, xis[0], s)
+    p1 = wall_camera_xyz(g, xi1[0], s)
+    np.testing.assert_allclose(p1[:, 2], p0[:, 2] - eps, atol=1e-12)
+    q0 = (np.float64(np.float32(Z0)) - p0[:, 2]) / np.float64(np.float32(mu))
+    q1 = (np.float64(np.float32(Z0)) - p1[:, 2]) / np.float64(np.float32(mu))
+    decided = valid & (np.abs(q0 - 1) > 1e-5)          # float32 side decision unambiguous
+    live0 = q0 < 1
+    expect = np.where(live0, q1, 1.0)
+    np.testing.assert_allclose(F[decided], expect[decided], atol=1e-9)
+    if eps > 0:   # live terms pushed past the clamp are extended linearly, not clamped
+        assert np.sum(decided & live0 & (q1 > 1.05)) > 5
+    else:         # saturated terms pulled inside stay saturated; valid terms pass below -1
+        assert np.sum(decided & ~live0 & (q1 < 0.95)) > 5
+        assert np.sum(decided & (q1 < -1.05)) > 5
+
+
+def small_window(n_samples=600):
     cam, poses, xi, depth = synth.diff_window(4, 48, 36, seed=11)
     T0 = np.stack([oracle.nominal_pose_f32(x) for x in xi])
-    S = synth.surface_samples(cam, poses, depth, 600, seed=5, voxel=0.005, band=0.01)
+    S = synth.surface_samples(cam, poses, depth, n_samples, seed=5, voxel=0.005, band=0.01)
     o = oracle.OracleDiffFusion(0.005, 0.02, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
                                 S, depth, T0)
     return o, xi, depth
@@ -102,7 +189,7 @@ def rel_l2(a, b):
 
 
 def test_gradient_vs_central_differences():
-    o, xi, depth = small_window()
+    o, xi, depth = small_window(3000)
     gd, gx = o.backward(xi)
     h = 1e-6
     fd = np.zeros_like(gx)
@@ -115,7 +202,8 @@ def test_gradient_vs_central_differences():
         assert rel_l2(gx[f], fd[f]) < 1e-5, (f, gx[f], fd[f])
     rng = np.random.default_rng(2)
     nz = np.argwhere(np.abs(gd) > 1e-6 * np.abs(gd).max())
-    pick = nz[rng.choice(len(nz), size=min(64, len(nz)), replace=False)]
+    assert len(nz) >= 256
+    pick = nz[rng.choice(len(nz), size=256, replace=False)]
     ga, gf = [], []
     for f, v, u in pick:
         dp = depth.copy()
