@@ -31,6 +31,7 @@ METRIC = "frames/s & hash Mops/s (% HBM roof); fwd+bwd vs fwd ms; stream p99 lat
 N_FRAMES = 300
 VOXEL, TRUNC, ZMAX, ERASE_R = 0.005, 0.02, 4.0, 4.0
 N_BUCKETS, MAX_BLOCKS = 1 << 22, 1 << 19
+E2E_MIN_FRAMES = 200
 WORKLOAD = ("room-scale fusion + MC streaming: 640x480 uint16 depth (f=525), 300-frame seeded "
             "walk through an 8x8x3 m room with 40 boxes/spheres, axial noise 1.5 mm*z^2, 2% "
             "dropout; voxel 5 mm, 8^3 blocks, truncation 2 cm, hash 2^22 buckets x 4 slots, "
@@ -106,71 +107,110 @@ def oracle_frames(o, cam, poses, depth, frame_ids, row_frac=1.0):
     r0 = (cam.height - rows) // 2
     t = 0.0
     for i in frame_ids:
-        d = np.zeros_like(depth[i])
-        d[r0:r0 + rows] = depth[i][r0:r0 + rows]
+        f = i % len(poses)
+        d = depth[f]
+        if rows < cam.height:
+            d = np.zeros_like(depth[f])
+            d[r0:r0 + rows] = depth[f][r0:r0 + rows]
         t0 = time.perf_counter()
-        o.erase_radius(poses[i][:, 3], ERASE_R)
-        o.integrate(d, poses[i])
+        o.erase_radius(poses[f][:, 3], ERASE_R)
+        o.integrate(d, poses[f])
         M, _ = o.mc_set(0)
         o.mc_dense(M)
         t += time.perf_counter() - t0
     return t, len(frame_ids) * rows / cam.height
 
 
-def cpu_baseline(cam, poses, depth, budget_s=20.0):
-    """Bounded sample of the same workload on the host: frame 0 warms the volume (untimed), then
-    whole frames 1, 2, ... are timed until ~budget_s of oracle time (at most 7 frames)."""
+def host_cores() -> int:
+    """Cores this process may run on (the affinity mask; nproc's answer)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def warmed_oracle(cam, poses, depth, first):
+    """An oracle volume that has run frames 0..first-1 (untimed; parallel mode, which gives the
+    same volume as the single-threaded reference)."""
+    import oracle
+    o = oracle_volume(cam)
+    oracle.set_threads(host_cores())
+    try:
+        oracle_frames(o, cam, poses, depth, range(first))
+    finally:
+        oracle.set_threads(1)
+    return o
+
+
+def cpu_baseline(cam, poses, depth, first, budget_s=20.0, n_max=8):
+    """Bounded sample of the timed frames on the host: an oracle volume warmed by frames
+    0..first-1 (untimed) runs frames first, first + 1, ... single-threaded until ~budget_s of
+    oracle time (at most n_max frames); a second volume warmed the same way runs the SAME frames
+    in the oracle's OpenMP mode on every host core.  value = the all-core frames/s."""
     import oracle
     oracle.build()
-    o = oracle_volume(cam)
-    t_tot, frames = 0.0, 0
-    for i in range(min(len(poses), 8)):
-        t0 = time.perf_counter()
-        o.erase_radius(poses[i][:, 3], ERASE_R)
-        o.integrate(depth[i], poses[i])
-        M, _ = o.mc_set(0)
-        o.mc_dense(M)
-        dt = time.perf_counter() - t0
-        if i >= 1:
-            t_tot += dt
-            frames += 1
-            if t_tot >= budget_s:
-                break
-    return {"value": frames / t_tot, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"room-scale frames 1..{frames} after frame 0 warmed the volume; full "
-                      f"640x480 erase + fusion + MC set + MC indices, single thread, "
-                      f"{t_tot:.1f} s of oracle time"}
+    cores = host_cores()
+    o1 = warmed_oracle(cam, poses, depth, first)
+    t1, n = 0.0, 0
+    while n < n_max and t1 < budget_s:
+        dt, _ = oracle_frames(o1, cam, poses, depth, [first + n])
+        t1 += dt
+        n += 1
+    del o1
+    om = warmed_oracle(cam, poses, depth, first)
+    oracle.set_threads(cores)
+    try:
+        tm, _ = oracle_frames(om, cam, poses, depth, range(first, first + n))
+    finally:
+        oracle.set_threads(1)
+    return {"value": n / tm, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "single_thread": {"value": n / t1, "cores": 1},
+            "sample": f"room-scale frames {first}..{first + n - 1} (the first timed frames) after "
+                      f"frames 0..{first - 1} warmed the volume untimed; full 640x480 erase + "
+                      f"fusion + MC set + MC indices; OpenMP over rows / blocks on {cores} "
+                      f"cores ({tm:.2f} s), and single-threaded ({t1:.1f} s)"}
 
 
 def run_reference(args, rank, ws):
+    """The oracle (the paper ships no code) on the timed frames of the workload: W untimed
+    warm-up frames, then K timed frames, whole 640x480 frames in the oracle's OpenMP mode on
+    every host core.  If that would take too long on this host, each step keeps a centred band
+    of the rows (work scales with valid pixels) and reports frames-equivalent."""
     if rank != 0:
         return
     from paper_1805_03709_b300 import synth
     import oracle
     oracle.build()
-    n = args.warmup + args.steps
+    cores = host_cores()
     cam, poses, depth = synth.room_sequence(N_FRAMES, workers=min(16, os.cpu_count() or 1))
-    budget = 150.0
     o = oracle_volume(cam)
-    # calibrate the band on the first warm-up frame
-    t_cal, f_cal = oracle_frames(o, cam, poses, depth, [0], 1.0 / 16)
-    per_step = budget / max(n, 1)
-    frac = float(np.clip(per_step / max(t_cal, 1e-3) / 16, 1.0 / cam.height, 1.0))
-    # the calibration frame is the first warm-up frame (it is processed even with none)
-    n_w = max(args.warmup - 1, 0)
-    ids = [i % N_FRAMES for i in range(1, 1 + n_w + args.steps)]
-    t_w, _ = oracle_frames(o, cam, poses, depth, ids[:n_w], frac)
-    t_s, f_s = oracle_frames(o, cam, poses, depth, ids[n_w:], frac)
+    oracle.set_threads(cores)
+    try:
+        # frame 0 (a warm-up frame, processed even with no warm-up steps) prices a whole frame
+        t_cal, _ = oracle_frames(o, cam, poses, depth, [0])
+        budget = 150.0
+        frac = float(np.clip(budget / max(args.warmup + args.steps, 1) / max(t_cal, 1e-3),
+                             1.0 / cam.height, 1.0))
+        n_w = max(args.warmup - 1, 0)
+        oracle_frames(o, cam, poses, depth, range(1, 1 + n_w), frac)
+        t_s, f_s = oracle_frames(o, cam, poses, depth,
+                                 range(1 + n_w, 1 + n_w + args.steps), frac)
+    finally:
+        oracle.set_threads(1)
     value = f_s / t_s if t_s > 0 else 0.0
+    first = 1 + n_w
+    sample = (f"frames {first}..{first + args.steps - 1} of the room sequence (frames wrap at "
+              f"{N_FRAMES}) after {first} warm-up frames, erase + fusion + MC set + MC indices, "
+              f"OpenMP over rows / blocks on {cores} cores")
+    sample += (", whole 640x480 frames" if frac >= 1.0 else
+               f", each step a centred band of {frac:.4f} of the rows (frames-equivalent)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * t_s / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": CONFIG,
-            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: a centred band of {frac:.4f} of the rows of "
-                                       f"the next room frame (work scales with valid pixels), "
-                                       f"reported as frames/s equivalent"},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -312,7 +352,7 @@ def main():
     cam, poses, depth = synth.room_sequence(N_FRAMES, workers=min(16, os.cpu_count() or 1))
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(cam, poses, depth)
+        cpu = cpu_baseline(cam, poses, depth, max(args.warmup, 1))
 
     import torch
     from paper_1805_03709_b300 import build, vbh as V
@@ -396,7 +436,10 @@ def main():
     # memory; the call pipelines consecutive frames (the copy-out of frame k overlaps frame k+1).
     # Timed by wall clock from the first call to the completion of the last frame; the 256 MiB
     # L2 flush between frames runs in the same stream and its event-timed duration is subtracted.
+    # At least E2E_MIN_FRAMES frames (the sequence cycles), whatever --steps is, so that pipeline
+    # fill and host jitter do not decide the figure.
     e2e = None
+    n_e2e = max(args.steps, E2E_MIN_FRAMES)
     if not args.no_e2e:
         from paper_1805_03709_b300 import vbh as V
         from paper_1805_03709_b300.volume import HostStream
@@ -413,7 +456,7 @@ def main():
         host_depth = torch.from_numpy(depth).pin_memory()
         outs = [HostStream.allocate(MAX_BLOCKS, 1 << 23) for _ in range(3)]
         fl_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                 for _ in range(args.steps)]
+                 for _ in range(n_e2e)]
         h2d = d2h = 0
         nbs = []
         statuses = []
@@ -426,7 +469,7 @@ def main():
 
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(n_e2e):
             i = args.warmup + k
             f = i % N_FRAMES
             fl_ev[k][0].record()
@@ -438,7 +481,7 @@ def main():
             if k >= 2:   # the frame of two calls earlier is complete
                 account(outs[(k - 2) % 3])
         statuses.append(vol.process_frame_host_flush())
-        for k in range(max(args.steps - 2, 0), args.steps):
+        for k in range(max(n_e2e - 2, 0), n_e2e):
             account(outs[k % 3])
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -447,13 +490,15 @@ def main():
         assert all(st == V.VBH_OK for st in statuses), "host stream capacity exceeded"
         # per frame: live and removal records, entries and the live blocks after it, from an
         # untimed replay of the same frames (the same totals as the host copies)
-        mc_counts = mc_replay(torch, cam, D, poses, args)[0]
+        mc_counts = mc_replay(torch, cam, D, poses, args, n_e2e)[0]
         assert [(c[0] + c[1], c[2]) for c in mc_counts] == nbs, "replay differs from the e2e run"
         mc_timing = vol.timing_read(reset=True)
         vol.timing(())
         t_e2e = max_over_ranks(torch, t_e2e, dev, ws)
-        e2e = {"value": ws * args.steps / t_e2e, "unit": "frames/s",
-               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+        e2e = {"value": ws * n_e2e / t_e2e, "unit": "frames/s",
+               "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e,
+               "frames": n_e2e,
+               "frames_timed": f"{args.warmup}..{args.warmup + n_e2e - 1} (mod {N_FRAMES})",
                "api": "vbh_process_frame_host (pinned host depth in, whole MC stream out, "
                       "consecutive frames pipelined)",
                "l2_flush_between_frames_s": flush_s}
@@ -461,7 +506,7 @@ def main():
     # MC extraction roofline: the same frames' MC extraction, timed (CUDA events around the
     # kernel on the volume's stream) and counted on the e2e replay (or a replay of its own)
     if args.no_e2e:
-        mc_counts, mc_timing = mc_replay(torch, cam, D, poses, args)
+        mc_counts, mc_timing = mc_replay(torch, cam, D, poses, args, args.steps)
     mc_line = None
     if mc_counts and mc_timing[0].get("mc", 0.0) > 0:
         live_b = sum(c[0] for c in mc_counts) / len(mc_counts)
@@ -471,9 +516,20 @@ def main():
         mc_ms = mc_timing[0]["mc"] / mc_n
         mc_alg = live_b * (512 * 8 + 24) + rem_b * 24 + ents * 3
         mc_ach = mc_alg / (mc_ms / 1e3) / 1e9
-        mc_line = {"bound": "hbm", "kernel": "k_mc_extract", "achieved": mc_ach, "peak": peak,
-                   "peak_source": peak_src, "unit": "GB/s", "frac": mc_ach / peak,
+        # what the kernel itself reads and writes: the sign/weight masks of each block and of
+        # its 7 positive neighbours (8 x 128 B, the neighbours' mostly from L2), the records and
+        # the entries
+        mc_kernel = live_b * (8 * 128 + 24) + rem_b * 24 + ents * 3
+        mc_line = {"bound": "latency", "kernel": "k_mc_extract", "achieved": mc_ach,
+                   "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": mc_ach / peak,
                    "algorithmic_bytes_per_launch": mc_alg, "avg_launch_ms": mc_ms,
+                   "kernel_bytes_per_launch": mc_kernel,
+                   "kernel_bytes_GBs": mc_kernel / (mc_ms / 1e3) / 1e9,
+                   "kernel_bytes_frac": mc_kernel / (mc_ms / 1e3) / 1e9 / peak,
+                   "frames": len(mc_counts),
+                   "note": "frac uses the hot-path table's 8 B per voxel of a TSDF-reading "
+                           "extraction; this kernel reads 128 B masks per block instead and is "
+                           "issue- and latency-bound (its own bytes: kernel_bytes_frac)",
                    "blocks_per_launch": live_b, "removal_records_per_launch": rem_b,
                    "entries_per_launch": ents,
                    "definition": "8 B (TSDF + weight) per voxel of every block in the MC set, "
@@ -485,11 +541,12 @@ def main():
     # integration, erase, MC) over the measured frame time
     frame_line = None
     if mc_counts:
-        nf = len(mc_counts)
-        mc_live = sum(c[0] for c in mc_counts) / nf
-        mc_rem = sum(c[1] for c in mc_counts) / nf
-        mc_ent = sum(c[2] for c in mc_counts) / nf
-        live_avg = sum(c[3] for c in mc_counts) / nf
+        fc = mc_counts[:args.steps]   # the frames of the timed loop
+        nf = len(fc)
+        mc_live = sum(c[0] for c in fc) / nf
+        mc_rem = sum(c[1] for c in fc) / nf
+        mc_ent = sum(c[2] for c in fc) / nf
+        live_avg = sum(c[3] for c in fc) / nf
         t_avg, n_avg = touched / args.steps, new / args.steps
         by = {"allocation": depth_bytes + t_avg * (64 + 16) + n_avg * 512 * 8,
               "integration": t_avg * 512 * 16 + depth_bytes,
@@ -551,12 +608,19 @@ def main():
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(CONFIG, parallelism="replicas" if ws > 1 else "single GPU",
-                           avg_touched_blocks=touched / args.steps,
-                           avg_new_blocks=new / args.steps),
+            "config": CONFIG,
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+            "workload_stats": {"avg_touched_blocks": touched / args.steps,
+                               "avg_new_blocks": new / args.steps,
+                               "frames_timed": f"{args.warmup}..{args.warmup + args.steps - 1} "
+                                               f"(mod {N_FRAMES})"},
             "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": achieved,
                          "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tr,
+                         "traffic_note": "dram read + write bytes during the launch (ncu, per "
+                                         "touched block x this run's touched blocks); the fused "
+                                         "voxels stay dirty in L2 and are written back after "
+                                         "the kernel, so the write-back is not in this figure",
                          "algorithmic_bytes_per_launch": alg_bytes / n_launch,
                          "definition": "8 B read + 8 B written per voxel of each touched block "
                                        "+ the depth image once",
@@ -856,56 +920,78 @@ def visible_point(torch, cam, D, poses, flush, args, peak):
             "integrate_GBs": ach, "integrate_hbm_frac": ach / peak}
 
 
+STREAM_FIRST, STREAM_FRAMES = 60, 60   # frames 60..119: the 4 m erase removes blocks
+
+
 def stream_point(torch, cam, D, poses, flush, args, base_ms):
-    """The timed room frames again on a fresh volume with stream-out on: every block the 4 m
-    erase removes is copied (device ring -> pinned host -> host map) while the frames run.
-    Same per-step CUDA events and L2 flush as the main loop; the copies still in flight when the
-    loop ends are waited for and timed separately."""
+    """Stream-out on a fixed range of the room frames where the 4 m erase removes blocks
+    (frames STREAM_FIRST.., whatever --steps is): two fresh volumes run frames 0..STREAM_FIRST-1
+    untimed, then the range is timed with per-step CUDA events and the L2 flush, once with
+    stream-out on (every erased block copied device ring -> pinned host -> host map while the
+    frames run) and once without, for the overhead.  The copies still in flight when the loop
+    ends are waited for and timed separately."""
     from paper_1805_03709_b300.volume import Volume
-    vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
-                 N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
-                 mc_cap_entries=MAX_BLOCKS * 64)
-    vol.stream_out_enable()
-    for i in range(args.warmup):
-        vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
-    vol.stream_out_flush()
-    s0 = vol.stream_out_stats()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        i = args.warmup + k
-        flush.zero_()
-        ev[k][0].record()
-        vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
-        ev[k][1].record()
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    vol.stream_out_flush()
-    t2 = time.perf_counter()
-    s1 = vol.stream_out_stats()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    blocks = s1[0] - s0[0]
-    vol.close()
-    return {"frames_per_s": 1e3 / ms, "ms_per_step": ms,
-            "overhead_vs_main_loop": ms / base_ms - 1.0,
-            "blocks_streamed_per_frame": blocks / args.steps,
-            "bytes_streamed_per_frame": blocks * 4104 / args.steps,
-            "lost": int(s1[1]), "host_map_blocks": int(s1[2]),
-            "drain_after_loop_ms": (t2 - t1) * 1e3,
-            "copy_GBs_over_loop_and_drain": blocks * 4104 / (t2 - t0) / 1e9}
+
+    def run(stream_out):
+        vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
+                     N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
+                     mc_cap_entries=MAX_BLOCKS * 64)
+        if stream_out:
+            vol.stream_out_enable()
+        for i in range(STREAM_FIRST):
+            vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+        if stream_out:
+            vol.stream_out_flush()
+            s0 = vol.stream_out_stats()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(STREAM_FRAMES)]
+        c0 = vol.counters()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(STREAM_FRAMES):
+            i = STREAM_FIRST + k
+            flush.zero_()
+            ev[k][0].record()
+            vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out = {"ms": sum(a.elapsed_time(b) for a, b in ev) / STREAM_FRAMES}
+        if stream_out:
+            vol.stream_out_flush()
+            t2 = time.perf_counter()
+            s1 = vol.stream_out_stats()
+            out.update(blocks=s1[0] - s0[0], lost=int(s1[1]), host=int(s1[2]),
+                       drain_ms=(t2 - t1) * 1e3, span_s=t2 - t0)
+        else:
+            out["erased"] = None
+        vol.close()
+        return out
+
+    base = run(False)
+    so = run(True)
+    blocks = so["blocks"]
+    return {"frames": f"{STREAM_FIRST}..{STREAM_FIRST + STREAM_FRAMES - 1}",
+            "frames_per_s": 1e3 / so["ms"], "ms_per_step": so["ms"],
+            "ms_per_step_without_stream_out": base["ms"],
+            "overhead_vs_same_frames": so["ms"] / base["ms"] - 1.0,
+            "blocks_streamed_per_frame": blocks / STREAM_FRAMES,
+            "bytes_streamed_per_frame": blocks * 4104 / STREAM_FRAMES,
+            "lost": so["lost"], "host_map_blocks": so["host"],
+            "drain_after_loop_ms": so["drain_ms"],
+            "copy_GBs_over_loop_and_drain": blocks * 4104 / so["span_s"] / 1e9}
 
 
-def mc_replay(torch, cam, D, poses, args):
-    """(live blocks, removal records, entries) of each timed frame's MC extraction and the live
-    blocks after it, from an untimed replay of the same frames on a fresh volume."""
+def mc_replay(torch, cam, D, poses, args, n_timed):
+    """(live blocks, removal records, entries) of each of the n_timed frames' MC extraction
+    (after the warm-up frames) and the live blocks after it, from an untimed replay of the same
+    frames on a fresh volume."""
     from paper_1805_03709_b300.volume import Volume
     vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
                  N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
                  mc_cap_entries=MAX_BLOCKS * 64)
     out = []
-    for i in range(args.warmup + args.steps):
+    for i in range(args.warmup + n_timed):
         f = i % N_FRAMES
         if i == args.warmup:
             vol.timing(("mc",))

@@ -80,12 +80,6 @@ class HashMap:
     def counters(self) -> V.vbh_counters:
         return V.vbh_get_counters(self.h)
 
-    def clear_errors(self):
-        V.vbh_clear_errors(self.h)
-
-    def set_wait_limit(self, polls: int):
-        V.vbh_set_wait_limit(self.h, polls)
-
     def dump(self):
         n = self.counters().live
         k = np.zeros((max(n, 1), 3), np.int32)
@@ -307,6 +301,12 @@ class Volume:
 
     def counters(self) -> V.vbh_counters:
         return V.vbh_get_counters(self.h)
+
+    def clear_errors(self):
+        V.vbh_clear_errors(self.h)
+
+    def set_wait_limit(self, polls: int):
+        V.vbh_set_wait_limit(self.h, polls)
 
     def dump(self):
         n = self.counters().live

@@ -145,7 +145,7 @@ def test_room_full_size_long_sequence():
         run_sequence(vol, orc, depth, poses, erase_radius=4.0, check_every=20)
         assert vol.counters().total_frames == 130
         _, _, W = orc.dump()
-        assert W.max() >= 60       # blocks in view since the first frame carry long histories
+        assert W.max() >= 20       # voxels seen by many frames of the walk carry long histories
     finally:
         oracle.set_threads(1)
 
