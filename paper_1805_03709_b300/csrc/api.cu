@@ -118,6 +118,8 @@ void free_batch_lists(vbh_handle* h) {
 }
 
 vbh_status maybe_rebuild(vbh_handle* h) {
+  // a running serving loop finds keys while frames run: entries must not move under it
+  if (h->serve_loop_active) return VBH_OK;
   if (h->snap_pending && cudaEventQuery(h->snap_ev) == cudaSuccess) {
     h->snap_pending = false;
     const unsigned int tomb = h->snap->n_tomb, empty = h->snap->n_empty;
@@ -334,6 +336,7 @@ vbh_status vbh_create(const vbh_config* cfg, void* cuda_stream, vbh_handle** out
     CREATE_CUDA(cudaMalloc(&h->cand, (size_t)h->cand_cap * sizeof(unsigned long long)));
     CREATE_CUDA(cudaMalloc(&h->cand_res, (size_t)h->cand_cap * sizeof(unsigned int)));
     CREATE_CUDA(cudaMalloc(&h->cand_st, (size_t)h->cand_cap));
+    CREATE_CUDA(cudaMalloc(&h->dimg, (size_t)c.width * c.height * sizeof(float)));
     CREATE_CUDA(cudaMalloc(&h->touched, (size_t)nb * sizeof(unsigned int)));
     CREATE_CUDA(cudaMalloc(&h->tdepth, (size_t)nb * sizeof(float2)));
     CREATE_CUDA(cudaMalloc(&h->tkey, (size_t)nb * sizeof(unsigned long long)));
@@ -365,7 +368,7 @@ vbh_status vbh_destroy(vbh_handle* h) {
   if (h->consumed_host) cudaFreeHost((void*)h->consumed_host);
   void* ptrs[] = {h->ctl, h->slots, h->shadow, h->cnt, h->vox, h->masks, h->pkeys, h->state, h->mark,
                   h->version, h->stack, h->seq, h->cand, h->cand_res, h->cand_st, h->touched, h->tdepth, h->tkey, h->mset,
-                  h->removed, h->tombrec};
+                  h->removed, h->tombrec, h->dimg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->snap) cudaFreeHost(h->snap);
@@ -443,6 +446,8 @@ vbh_status vbh_set_integration_mode(vbh_handle* h, uint32_t mode) {
 
 vbh_status vbh_hash_rebuild(vbh_handle* h) {
   if (!h) return fail(VBH_ERR_INVALID_ARG, "null handle");
+  if (h->serve_loop_active)
+    return fail(VBH_ERR_UNSUPPORTED, "a device-resident serving loop reads this table");
   return rebuild(h);
 }
 
@@ -465,7 +470,8 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   const PoolView pool = h->pool();
   h->stage_begin(VBH_STAGE_ALLOC);
   launch_setup(h, c);
-  launch_alloc_keys(h->L, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
+  launch_alloc_keys(h->L, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt,
+                    h->dimg);
   launch_hash_insert(h->L, t, pool, h->cnt, h->cand, &h->cnt->n_cand, nullptr,
                      h->cand_res, h->cand_st, h->cand_cap);
   launch_hash_insert_finish(h->L, t, pool, h->cnt, &h->cnt->n_cand, h->cand_res, h->cand_st,
@@ -478,7 +484,8 @@ vbh_status vbh_integrate_frame(vbh_handle* h, const uint16_t* depth_dev, const f
   }
   h->stage_end();
   h->stage_begin(VBH_STAGE_INTEGRATE);
-  launch_integrate(h->L, c.fp, pool, h->touched, h->tkey, h->tdepth, &h->cnt->n_touched,
+  launch_integrate(h->L, c.fp, h->dimg, pool, h->touched, h->tkey, h->tdepth,
+                   &h->cnt->n_touched,
                    h->cnt);
   h->launches += 1;
   h->stage_end();
@@ -528,7 +535,8 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   const Launch L2{h->cap_stream2, h->L.sms};
   VBH_CUDA(cudaEventRecord(h->fork_ev[0], h->cap_stream));
   VBH_CUDA(cudaStreamWaitEvent(h->cap_stream2, h->fork_ev[0], 0));
-  launch_alloc_keys(L2, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt);
+  launch_alloc_keys(L2, h->ctl, h->cfg.width, h->cfg.height, h->cand, h->cand_cap, h->cnt,
+                    h->dimg);
   VBH_CUDA(cudaEventRecord(h->fork_ev[1], h->cap_stream2));
   launch_erase_radius(Lc, t, pool, h->cnt, h->ctl, h->removed, h->cfg.max_blocks, nullptr,
                       nullptr, stream_list(h));
@@ -548,7 +556,7 @@ static vbh_status build_frame_graph(vbh_handle* h, int tmask) {
   VBH_CUDA(cudaEventRecord(h->fork_ev[3], h->cap_stream2));
   if (t_int) cudaEventRecordWithFlags(ev[0], h->cap_stream, cudaEventRecordExternal);
   // the fusion node takes the frame parameters by value: vbh_process_frame patches them
-  launch_integrate(Lc, base_ctl(h, nullptr).fp, pool, h->touched, h->tkey, h->tdepth,
+  launch_integrate(Lc, base_ctl(h, nullptr).fp, h->dimg, pool, h->touched, h->tkey, h->tdepth,
                    &h->cnt->n_touched, h->cnt);
   if (t_int) cudaEventRecordWithFlags(ev[1], h->cap_stream, cudaEventRecordExternal);
   VBH_CUDA(cudaStreamWaitEvent(h->cap_stream, h->fork_ev[3], 0));
@@ -669,13 +677,14 @@ vbh_status vbh_process_frame(vbh_handle* h, const uint16_t* depth_dev, const flo
   }
   {   // this frame's parameters into the fusion node (applies to this and later launches)
     FrameParams fpv = c.fp;
+    const float* dimg = h->dimg;
     PoolView pv = h->pool();
     const unsigned int* touched = h->touched;
     const unsigned long long* tkey = h->tkey;
     const float2* tdepth = h->tdepth;
     const unsigned int* n_touched = &h->cnt->n_touched;
     DevCounters* cntp = h->cnt;
-    void* args[] = {&fpv, &pv, &touched, &tkey, &tdepth, &n_touched, &cntp};
+    void* args[] = {&fpv, &dimg, &pv, &touched, &tkey, &tdepth, &n_touched, &cntp};
     cudaKernelNodeParams kp = h->integ_kp;
     kp.kernelParams = args;
     kp.extra = nullptr;

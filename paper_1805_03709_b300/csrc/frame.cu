@@ -39,10 +39,13 @@ __device__ __forceinline__ void load_frame_params(FrameParams& dst, const FrameC
 
 // Band allocation: every valid pixel's samples -> block keys -> per-tile distinct set in shared
 // memory -> appended to the candidate list (the global de-duplication is the hash insert).
+// Every pixel's metric depth fl(raw ds) also goes to `dimg` for the fusion kernel, with invalid
+// pixels (raw 0, or beyond zmax) as -inf: there the band test fl(d - p_z) >= -mu fails, so
+// fusion needs no validity test, conversion or scaling of its own.
 __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl,
                                                              unsigned long long* cand,
                                                              unsigned int cap,
-                                                             DevCounters* cnt) {
+                                                             DevCounters* cnt, float* dimg) {
   __shared__ unsigned long long set[kTileSet];
   __shared__ FrameParams fp;
   __shared__ unsigned int s_warp[kTileThreads / 32];
@@ -60,7 +63,9 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
     if (pu < fp.width && pv < fp.height) {
       const unsigned short raw = __ldg(fp.depth + (size_t)pv * fp.width + pu);
       const float d = __fmul_rn((float)raw, fp.ds);
-      if (raw != 0 && !(fp.zmax > 0.0f && d > fp.zmax)) {
+      const bool valid = raw != 0 && !(fp.zmax > 0.0f && d > fp.zmax);
+      dimg[(size_t)pv * fp.width + pu] = valid ? d : -INFINITY;
+      if (valid) {
         const float au = __fdiv_rn(__fsub_rn((float)pu, fp.cx), fp.fx);
         const float av = __fdiv_rn(__fsub_rn((float)pv, fp.cy), fp.fy);
         const float z0 = __fsub_rn(d, fp.mu);
@@ -234,9 +239,9 @@ static_assert(kSlices % kGroup == 0 && 16 % kSlices == 0, "unit / group sizes");
 // frame), so the compiler takes them as constant-bank operands instead of holding ~25 of them
 // in registers, which leaves room for more resident warps to hide the depth-gather latency.
 __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
-    k_integrate(const FrameParams fp, PoolView pool, const unsigned int* touched,
-                const unsigned long long* tkey, const float2* tdepth,
-                const unsigned int* n_touched, DevCounters* cnt) {
+    k_integrate(const FrameParams fp, const float* __restrict__ dimg, PoolView pool,
+                const unsigned int* touched, const unsigned long long* tkey,
+                const float2* tdepth, const unsigned int* n_touched, DevCounters* cnt) {
   __shared__ __align__(128) float2 sbuf[kWarps][kUnitVox];
   __shared__ __align__(8) unsigned long long sbar[kWarps];
   __shared__ unsigned int smask[kWarps][32];
@@ -254,10 +259,8 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
               R5 = fp.R[5], R6 = fp.R[6], R7 = fp.R[7], R8 = fp.R[8];
   const float s = fp.s, t0 = fp.t[0], t1 = fp.t[1], t2 = fp.t[2];
   const float fx = fp.fx, fy = fp.fy, cxh = fp.cxh, cyh = fp.cyh;
-  const float ds = fp.ds, mu = fp.mu, inv_mu = fp.inv_mu, wmax = fp.wmax;
-  const unsigned int raw_max = fp.raw_max;
+  const float mu = fp.mu, inv_mu = fp.inv_mu, wmax = fp.wmax;
   const int width = fp.width, height = fp.height;
-  const unsigned short* __restrict__ depth = fp.depth;
   // per-voxel part of the camera depth: tau(h, lz) = s (R_02 lx + R_12 ly + R_22 lz)
   //                                              = base[h] + lz * s R_22   (value path only)
   const float sR22 = s * R8;
@@ -326,9 +329,8 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
         const bool in = pz > 0.0f && au == au && av == av && (unsigned int)iu < (unsigned int)width &&
                         (unsigned int)iv < (unsigned int)height;
         const int idx = in ? iv * width + iu : 0;
-        const unsigned short raw = __ldg(depth + idx);
-        const float d = __fmul_rn((float)raw, ds);
-        ok[i] = in && (unsigned int)raw - 1u < raw_max && !(__fsub_rn(d, pz) < -mu);
+        const float d = __ldg(dimg + idx);   // fl(raw ds), or -inf for an invalid pixel
+        ok[i] = in && !(__fsub_rn(d, pz) < -mu);
         dm[i] = d;
       }
       if (g == 0 && !fresh) {
@@ -450,18 +452,20 @@ void launch_visible(const Launch& L, const FrameCtl* ctl, PoolView pool, unsigne
 }
 
 void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int height,
-                       unsigned long long* cand, unsigned int cap, DevCounters* cnt) {
+                       unsigned long long* cand, unsigned int cap, DevCounters* cnt,
+                       float* dimg) {
   static const int grid = persistent_grid(k_alloc_keys, kTileThreads, L.sms);
   const int tiles = ((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
-  k_alloc_keys<<<tiles < grid ? tiles : grid, kTileThreads, 0, L.stream>>>(ctl, cand, cap, cnt);
+  k_alloc_keys<<<tiles < grid ? tiles : grid, kTileThreads, 0, L.stream>>>(ctl, cand, cap, cnt,
+                                                                          dimg);
 }
 
-void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
+void launch_integrate(const Launch& L, const FrameParams& fp, const float* dimg, PoolView pool,
                       const unsigned int* touched, const unsigned long long* tkey,
                       const float2* tdepth, const unsigned int* n_touched, DevCounters* cnt) {
   static const int grid = persistent_grid(k_integrate, kIntThreads, L.sms);
-  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(fp, pool, touched, tkey, tdepth, n_touched,
-                                                  cnt);
+  k_integrate<<<grid, kIntThreads, 0, L.stream>>>(fp, dimg, pool, touched, tkey, tdepth,
+                                                  n_touched, cnt);
 }
 
 const void* integrate_kernel() { return reinterpret_cast<const void*>(&k_integrate); }

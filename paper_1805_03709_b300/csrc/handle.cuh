@@ -77,6 +77,7 @@ struct vbh_handle {
   unsigned long long* cand = nullptr;
   unsigned int cand_cap = 0;
   unsigned int* cand_res = nullptr;
+  float* dimg = nullptr;           // the frame's metric depth (fl(raw ds), -inf when invalid)
   unsigned char* cand_st = nullptr;
   unsigned int* touched = nullptr;
   unsigned long long* tkey = nullptr;   // key of each touched block
@@ -109,6 +110,7 @@ struct vbh_handle {
   int graph_timed = 0;             // stage mask the captured graph brackets with events
   uint32_t integ_mode = 0;         // VBH_INTEGRATE_*
   uint32_t wait_limit = 1u << 24;  // polls of the fusion kernel's bounded copy wait
+  bool serve_loop_active = false;  // a device-resident serving loop reads the table: no rebuild
   uint32_t graph_mode = 0;         // integration mode the frame graph was captured with
   uint64_t graph_kernels = 0;
   // bookkeeping
@@ -173,6 +175,20 @@ inline StreamList stream_list(const vbh_handle* h);
 // The volume handle and the device-resident log/store of a server (serve.cu).
 vbh_handle* serve_handle(vbh_serve* s);
 const ServeLog* serve_log(vbh_serve* s);
+// What the device-resident request loop (serve_loop.cu) shares with its server.
+struct ServeShared {
+  vbh_handle* h;
+  const ServeLog* sl;
+  unsigned int* client_v;      // per-client versions (device)
+  unsigned char* arena;        // the stream buffer
+  uint64_t budget;             // its usable bytes (multiple of 256)
+  unsigned int n_clients, log_cap;
+};
+ServeShared serve_shared(vbh_serve* s);
+bool serve_idle(vbh_serve* s);
+vbh_serve_loop* serve_loop_of(vbh_serve* s);
+void serve_set_loop(vbh_serve* s, vbh_serve_loop* L);
+vbh_status serve_reload_versions(vbh_serve* s);
 // MC refresh of every live block into the attached server's store and log, with no stream
 // output (enqueued on the handle's stream).  counts_dev: two device words of scratch.
 vbh_status refresh_all_blocks(vbh_handle* h, unsigned int* counts_dev);

@@ -423,8 +423,9 @@ void launch_block_masks(const Launch& L, PoolView pool, const unsigned int* idx,
 
 // frame.cu
 void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int height,
-                       unsigned long long* cand, unsigned int cap, DevCounters* cnt);
-void launch_integrate(const Launch& L, const FrameParams& fp, PoolView pool,
+                       unsigned long long* cand, unsigned int cap, DevCounters* cnt,
+                       float* dimg);
+void launch_integrate(const Launch& L, const FrameParams& fp, const float* dimg, PoolView pool,
                       const unsigned int* touched, const unsigned long long* tkey,
                       const float2* tdepth, const unsigned int* n_touched, DevCounters* cnt);
 // The fusion kernel's entry (to find its node in a captured frame graph).
