@@ -522,6 +522,75 @@ vbh_status vbh_serve_run(vbh_serve* s, const vbh_serve_script* script, vbh_serve
                          uint32_t cap, uint32_t* n_host);
 uint64_t vbh_serve_now_ns(void);
 
+/* Device-resident request loop (the same requests and results as above, Sec. 4.2 serving): one
+ * persistent, cooperatively launched kernel on a library-owned non-blocking stream admits,
+ * batches and serves requests while frames keep running on the volume's stream.
+ *   - Requests go from the host into a ring in mapped host memory (id, client); the kernel's
+ *     scheduler warp reads them, keeps every client's version and "request in flight" state on
+ *     the device only, admits requests in arrival order (one per client at a time) when a slot
+ *     (max_slots) is free and their worst case -- one 528 B record per change record of the
+ *     range, or per pool entry for a reset -- fits in the server's budget_bytes stream buffer
+ *     (a ring allocator over it; a memory-blocked request may be passed by later ones for
+ *     bypass_rounds scheduler rounds), cuts the admitted ranges into chunks of chunk_records
+ *     and hands chunks of all active requests out in rounds, smallest remainder first, as the
+ *     workers drain them (continuous batching: a request that arrives while others run joins
+ *     the next round).  Worker warps take 32-record tiles by ticket, copy each current block's
+ *     512 cube indices and its header, and the warp that finishes a request's last tile moves
+ *     the client to its new version and publishes the completion in mapped host memory.
+ *   - Results are those of vbh_serve_step's requests, with sigma the last change number
+ *     published when the request is admitted.  A block refreshed again while it is being
+ *     copied is dropped from that result (its newer refresh is after sigma and goes to the
+ *     client's next request), so concurrent frames never yield a torn block.
+ *   - Every device wait is bounded: the scheduler stops the loop with VBH_ERR_TIMEOUT when the
+ *     host has given no sign of life (no loop call) for idle_timeout_us; workers stop when the
+ *     scheduler's heartbeat stalls.  While a loop runs, the volume's table rebuilds are
+ *     deferred, the server's host scheduler calls (vbh_serve_submit / _step / _drain / _run /
+ *     _set_versions / _set_policy) return VBH_ERR_UNSUPPORTED, and a device-wide
+ *     synchronisation (cudaDeviceSynchronize, cudaFree) waits until the loop stops.
+ * The loop object is used from one host thread. */
+typedef struct {
+  uint32_t ctas;             /* CTAs of 256 threads (0 = one per two SMs); all co-resident */
+  uint32_t max_slots;        /* requests in flight at once, 1..64 (0 = 64) */
+  uint32_t chunk_records;    /* change records per chunk (0 = 4096) */
+  uint32_t bypass_rounds;    /* scheduler rounds a memory-blocked head may be passed */
+  uint32_t ring;             /* request / completion ring entries, a power of two (0 = 4096) */
+  uint32_t idle_timeout_us;  /* host silence that stops the loop (0 = 1000000) */
+} vbh_serve_loop_config;
+typedef struct {
+  uint64_t requests_done, records_served, change_records_scanned, chunks, rounds;
+  uint64_t deferred_memory;  /* admission attempts refused for want of stream buffer */
+  uint64_t bytes_in_use, bytes_peak;
+  uint32_t max_active;       /* most requests in flight at once */
+  uint32_t status;           /* 0 running / stopped cleanly, else the vbh_status it stopped with */
+  uint32_t launches;         /* kernel launches of the loop (1 per start) */
+} vbh_serve_loop_stats;
+typedef struct vbh_serve_loop vbh_serve_loop;
+/* Start the loop (the server must be idle; synchronises the volume's stream first). */
+vbh_status vbh_serve_loop_start(vbh_serve* s, const vbh_serve_loop_config* cfg,
+                                vbh_serve_loop** out);
+/* Queue a request (no device call); VBH_ERR_CAPACITY when the ring is full, VBH_ERR_TIMEOUT
+ * if the loop has stopped by itself. */
+vbh_status vbh_serve_loop_submit(vbh_serve_loop* L, uint32_t client, uint64_t t_arrival_ns,
+                                 uint32_t* id_host);
+/* Completions published since the last poll (at most cap; t_done_ns = when this poll saw
+ * them; t_admit_ns = 0: admission happens on the device). */
+vbh_status vbh_serve_loop_poll(vbh_serve_loop* L, vbh_serve_done* out_host, uint32_t cap,
+                               uint32_t* n_host);
+/* A completed request's records (device pointers into the stream buffer, valid until it is
+ * released); release hands its region back to the device allocator. */
+vbh_status vbh_serve_loop_result(vbh_serve_loop* L, uint32_t id, vbh_serve_view* out_host);
+vbh_status vbh_serve_loop_release(vbh_serve_loop* L, uint32_t id);
+/* Wait (bounded) until every submitted request has completed; VBH_ERR_TIMEOUT otherwise. */
+vbh_status vbh_serve_loop_drain(vbh_serve_loop* L, uint64_t timeout_ns);
+/* Real-time script as for vbh_serve_run (frames on the volume's stream, requests into the
+ * loop), releasing every result as it completes. */
+vbh_status vbh_serve_loop_run(vbh_serve_loop* L, const vbh_serve_script* script,
+                              vbh_serve_done* out_host, uint32_t cap, uint32_t* n_host);
+vbh_status vbh_serve_loop_stats_read(vbh_serve_loop* L, vbh_serve_loop_stats* out_host);
+/* Stop the loop and free it: returns VBH_OK, or the status the loop stopped with by itself
+ * (VBH_ERR_TIMEOUT after host silence); requests not completed are dropped. */
+vbh_status vbh_serve_loop_stop(vbh_serve_loop* L);
+
 /* Marching Cubes triangulation of an MC stream (Sec. 4.3: an exploration client builds its
  * mesh from the indices, vertices at edge midpoints, no interpolation).  The triangle table is
  * derived from the cube cases: corner i = (000, 100, 110, 010, 001, 101, 111, 011)[i] (bit i

@@ -358,6 +358,11 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
       mine += __popc(e8[h]);
     }
     if (sl) {   // dense indices of voxel x + 8 row: row lane in word lane, row lane + 32 next
+      // the refresh's number goes out before its indices: a serving loop that copies the store
+      // concurrently reads the number before and after its copy and drops a changed block
+      if (lane == 0) pool.seq[q] = seq0 + r;
+      __syncwarp();
+      __threadfence();
       unsigned long long* st = reinterpret_cast<unsigned long long*>(sl->store + 32u * q);
 #pragma unroll
       for (int h = 0; h < 2; ++h)   // cubes that are not emitted are stored as 0
@@ -365,7 +370,6 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
                              (spread[e8[h]] * 0xFFull);
       if (lane == 0) {
         const unsigned int e = seq0 + r;
-        pool.seq[q] = e;
         LogEnt le;
         le.key = key;
         le.aux = q;

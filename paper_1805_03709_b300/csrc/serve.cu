@@ -324,6 +324,7 @@ struct vbh_serve {
   std::vector<cudaEvent_t> ev_free;
   uint32_t next_id = 1;
   uint32_t head_blocked = 0;         // iterations the head request has been memory-blocked
+  vbh_serve_loop* loop = nullptr;    // a device-resident request loop owns the server
   vbh_serve_stats st{};
 
   unsigned int sigma() const { return *reinterpret_cast<volatile unsigned int*>(sigma_host); }
@@ -546,7 +547,41 @@ vbh_status vbh_serve::launch() {
 namespace vbh {
 vbh_handle* serve_handle(vbh_serve* s) { return s->h; }
 const ServeLog* serve_log(vbh_serve* s) { return s->sl_dev; }
+ServeShared serve_shared(vbh_serve* s) {
+  ServeShared x;
+  x.h = s->h;
+  x.sl = s->sl_dev;
+  x.client_v = s->client_v;
+  x.arena = s->arena;
+  x.budget = s->cfg.budget_bytes & ~255ull;
+  x.n_clients = s->cfg.n_clients;
+  x.log_cap = s->log_cap;
+  return x;
+}
+bool serve_idle(vbh_serve* s) {
+  return s->pending.empty() && s->inflight.empty() && s->active.empty() &&
+         std::none_of(s->slot_req.begin(), s->slot_req.end(), [](int r) { return r >= 0; });
+}
+vbh_serve_loop* serve_loop_of(vbh_serve* s) { return s->loop; }
+void serve_set_loop(vbh_serve* s, vbh_serve_loop* L) { s->loop = L; }
+// The host mirror of the client versions after a device loop has moved them.
+vbh_status serve_reload_versions(vbh_serve* s) {
+  VBH_CUDA(cudaMemcpy(s->v_mirror.data(), s->client_v, sizeof(unsigned int) * s->cfg.n_clients,
+                      cudaMemcpyDeviceToHost));
+  return VBH_OK;
+}
 }  // namespace vbh
+
+namespace {
+// While a device-resident loop owns the server, its host scheduler is not used.
+bool loop_owned(vbh_serve* s) {
+  if (s && s->loop) {
+    fail(VBH_ERR_UNSUPPORTED, "a device-resident serving loop is running on this server");
+    return true;
+  }
+  return false;
+}
+}  // namespace
 
 extern "C" {
 
@@ -642,6 +677,7 @@ vbh_status vbh_serve_create(vbh_handle* h, const vbh_serve_config* cfg, vbh_serv
 
 vbh_status vbh_serve_destroy(vbh_serve* s) {
   if (!s) return VBH_OK;
+  if (s->loop) vbh_serve_loop_stop(s->loop);
   if (s->h) {
     cudaStreamSynchronize(s->h->stream);
     if (s->h->server == s) {
@@ -664,6 +700,7 @@ vbh_status vbh_serve_destroy(vbh_serve* s) {
 
 vbh_status vbh_serve_set_policy(vbh_serve* s, const vbh_serve_config* cfg) {
   if (!s || !cfg) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if (loop_owned(s)) return VBH_ERR_UNSUPPORTED;
   VBH_CUDA(cudaStreamSynchronize(s->h->stream));   // retire launches whose requests are done
   vbh_status rs = s->reap();
   if (rs != VBH_OK) return rs;
@@ -683,6 +720,7 @@ vbh_status vbh_serve_set_policy(vbh_serve* s, const vbh_serve_config* cfg) {
 vbh_status vbh_serve_set_versions(vbh_serve* s, const uint32_t* clients, const uint32_t* versions,
                                   uint32_t n) {
   if (!s || (n && (!clients || !versions))) return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if (loop_owned(s)) return VBH_ERR_UNSUPPORTED;
   for (uint32_t i = 0; i < n; ++i) {
     if (clients[i] >= s->cfg.n_clients) return fail(VBH_ERR_INVALID_ARG, "client out of range");
     if (s->client_busy[clients[i]]) return fail(VBH_ERR_INVALID_ARG, "client has a request");
@@ -727,6 +765,7 @@ vbh_status vbh_serve_versions_for_backlog(vbh_serve* s, const uint32_t* backlog,
 
 vbh_status vbh_serve_submit(vbh_serve* s, uint32_t client, uint64_t t_arrival_ns, uint32_t* id) {
   if (!s) return fail(VBH_ERR_INVALID_ARG, "null server");
+  if (loop_owned(s)) return VBH_ERR_UNSUPPORTED;
   if (client >= s->cfg.n_clients) return fail(VBH_ERR_INVALID_ARG, "client out of range");
   Req r;
   r.d.id = s->next_id++;
@@ -741,6 +780,7 @@ vbh_status vbh_serve_submit(vbh_serve* s, uint32_t client, uint64_t t_arrival_ns
 
 vbh_status vbh_serve_step(vbh_serve* s, uint32_t* launched) {
   if (!s) return fail(VBH_ERR_INVALID_ARG, "null server");
+  if (loop_owned(s)) return VBH_ERR_UNSUPPORTED;
   if (launched) *launched = 0;
   vbh_status st = s->reap();
   if (st != VBH_OK) return st;
@@ -794,6 +834,7 @@ vbh_status vbh_serve_release(vbh_serve* s, uint32_t id) {
 
 vbh_status vbh_serve_drain(vbh_serve* s) {
   if (!s) return fail(VBH_ERR_INVALID_ARG, "null server");
+  if (loop_owned(s)) return VBH_ERR_UNSUPPORTED;
   for (uint64_t guard = 0;; ++guard) {
     const bool busy = !s->pending.empty() || !s->inflight.empty() || !s->active.empty();
     if (!busy) break;
@@ -827,6 +868,7 @@ vbh_status vbh_serve_run(vbh_serve* s, const vbh_serve_script* sc, vbh_serve_don
                          uint32_t cap, uint32_t* n_out) {
   if (!s || !sc || !n_out || (sc->n_events && (!sc->t_ns || !sc->client)))
     return fail(VBH_ERR_INVALID_ARG, "null argument");
+  if (loop_owned(s)) return VBH_ERR_UNSUPPORTED;
   *n_out = 0;
   uint32_t n_frames = 0;
   for (uint32_t i = 0; i < sc->n_events; ++i) {

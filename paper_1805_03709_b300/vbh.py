@@ -146,6 +146,18 @@ class vbh_serve_stats(ctypes.Structure):
                 ("deferred_memory", _u64), ("err_flags", _u32), ("sigma", _u32)]
 
 
+class vbh_serve_loop_config(ctypes.Structure):
+    _fields_ = [("ctas", _u32), ("max_slots", _u32), ("chunk_records", _u32),
+                ("bypass_rounds", _u32), ("ring", _u32), ("idle_timeout_us", _u32)]
+
+
+class vbh_serve_loop_stats(ctypes.Structure):
+    _fields_ = [("requests_done", _u64), ("records_served", _u64),
+                ("change_records_scanned", _u64), ("chunks", _u64), ("rounds", _u64),
+                ("deferred_memory", _u64), ("bytes_in_use", _u64), ("bytes_peak", _u64),
+                ("max_active", _u32), ("status", _u32), ("launches", _u32)]
+
+
 class vbh_serve_script(ctypes.Structure):
     _fields_ = [("n_events", _u32), ("t_ns", _p), ("client", _p), ("depth_dev", _p),
                 ("T_wc", _p), ("frame_id", _p), ("erase_radius", _f32),
@@ -186,6 +198,17 @@ SYMBOLS += [
     ("vbh_serve_stats_read", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_stats)]),
     ("vbh_serve_run", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_script), _p, _u32, ctypes.POINTER(_u32)]),
     ("vbh_serve_now_ns", _u64, []),
+    ("vbh_serve_loop_start", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_loop_config),
+                                            ctypes.POINTER(_p)]),
+    ("vbh_serve_loop_submit", ctypes.c_int, [_p, _u32, _u64, ctypes.POINTER(_u32)]),
+    ("vbh_serve_loop_poll", ctypes.c_int, [_p, _p, _u32, ctypes.POINTER(_u32)]),
+    ("vbh_serve_loop_result", ctypes.c_int, [_p, _u32, ctypes.POINTER(vbh_serve_view)]),
+    ("vbh_serve_loop_release", ctypes.c_int, [_p, _u32]),
+    ("vbh_serve_loop_drain", ctypes.c_int, [_p, _u64]),
+    ("vbh_serve_loop_run", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_script), _p, _u32,
+                                          ctypes.POINTER(_u32)]),
+    ("vbh_serve_loop_stats_read", ctypes.c_int, [_p, ctypes.POINTER(vbh_serve_loop_stats)]),
+    ("vbh_serve_loop_stop", ctypes.c_int, [_p]),
 ]
 
 
@@ -494,6 +517,59 @@ def vbh_serve_run(s, script: vbh_serve_script, cap: int) -> list:
 
 def vbh_serve_now_ns() -> int:
     return int(lib().vbh_serve_now_ns())
+
+
+def vbh_serve_loop_start(s, cfg: vbh_serve_loop_config) -> int:
+    out = _p()
+    _check(lib().vbh_serve_loop_start(s, ctypes.byref(cfg), ctypes.byref(out)),
+           "vbh_serve_loop_start")
+    return out.value
+
+
+def vbh_serve_loop_submit(L, client: int, t_arrival_ns: int = 0) -> int:
+    rid = _u32()
+    _check(lib().vbh_serve_loop_submit(L, client, t_arrival_ns, ctypes.byref(rid)),
+           "vbh_serve_loop_submit")
+    return rid.value
+
+
+def vbh_serve_loop_poll(L, cap: int = 256) -> list:
+    buf = (vbh_serve_done * cap)()
+    n = _u32()
+    _check(lib().vbh_serve_loop_poll(L, buf, cap, ctypes.byref(n)), "vbh_serve_loop_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def vbh_serve_loop_result(L, rid: int) -> vbh_serve_view:
+    v = vbh_serve_view()
+    _check(lib().vbh_serve_loop_result(L, rid, ctypes.byref(v)), "vbh_serve_loop_result")
+    return v
+
+
+def vbh_serve_loop_release(L, rid: int):
+    _check(lib().vbh_serve_loop_release(L, rid), "vbh_serve_loop_release")
+
+
+def vbh_serve_loop_drain(L, timeout_ns: int):
+    _check(lib().vbh_serve_loop_drain(L, int(timeout_ns)), "vbh_serve_loop_drain")
+
+
+def vbh_serve_loop_run(L, script: vbh_serve_script, cap: int) -> list:
+    buf = (vbh_serve_done * max(cap, 1))()
+    n = _u32()
+    _check(lib().vbh_serve_loop_run(L, ctypes.byref(script), buf, cap, ctypes.byref(n)),
+           "vbh_serve_loop_run")
+    return [buf[i] for i in range(n.value)]
+
+
+def vbh_serve_loop_stats_read(L) -> vbh_serve_loop_stats:
+    st = vbh_serve_loop_stats()
+    _check(lib().vbh_serve_loop_stats_read(L, ctypes.byref(st)), "vbh_serve_loop_stats_read")
+    return st
+
+
+def vbh_serve_loop_stop(L):
+    _check(lib().vbh_serve_loop_stop(L), "vbh_serve_loop_stop")
 
 
 # ---------------------------------------------------------------------------- stream-out / in
