@@ -228,12 +228,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int 
 #ifndef VBH_FUSE_SLICES
 #define VBH_FUSE_SLICES 8
 #endif
+#ifndef VBH_FUSE_PACKED
+#define VBH_FUSE_PACKED 1    // 1: the voxels of rows ly0 and ly0 + 4 share FP32x2 instructions
+#endif
 constexpr int kWarps = kIntThreads / 32;
 constexpr int kGroup = VBH_FUSE_GROUP;     // voxels per lane whose depth fetches overlap
 constexpr int kSlices = VBH_FUSE_SLICES;   // voxel sets (32 voxels each) per work unit
 constexpr unsigned int kUnits = 16u / kSlices;   // work units per block
 constexpr unsigned int kUnitVox = 32u * kSlices;
 static_assert(kSlices % kGroup == 0 && 16 % kSlices == 0, "unit / group sizes");
+static_assert(kGroup % 2 == 0 || !VBH_FUSE_PACKED, "packed pairs need an even group");
 
 // The frame parameters arrive by value (the frame graph patches this node's argument every
 // frame), so the compiler takes them as constant-bank operands instead of holding ~25 of them
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
                 kUnitVox * 8u, &sbar[warp]);
   }
   bool alive = true;
-  for (; u < n_units && alive; u += stride) {
+  while (u < n_units && alive) {
     const unsigned int un = u + stride;
     const unsigned int rec_next = un < n_units ? touched[un / kUnits] : 0u;
     const unsigned int b = u / kUnits, part = u % kUnits;
@@ -312,6 +316,40 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
     for (int g = 0; g < kSlices; g += kGroup) {
       bool ok[kGroup];
       float dm[kGroup];
+#if VBH_FUSE_PACKED
+      // voxels j (row ly0) and j + 1 (row ly0 + 4) share their z: every binary32 operation of
+      // their decision chains runs as one FP32x2 instruction, which rounds each component
+      // exactly as the scalar operation does
+#pragma unroll
+      for (int i = 0; i < kGroup; i += 2) {
+        const int j = g + i;
+        const float dZ = __fmaf_rn((float)(z0 + (j >> 1)), s, -t2);
+        const float2 dZ2 = make_float2(dZ, dZ);
+        const float2 px = __ffma2_rn(make_float2(R6, R6), dZ2, make_float2(ix[0], ix[1]));
+        const float2 py = __ffma2_rn(make_float2(R7, R7), dZ2, make_float2(iy[0], iy[1]));
+        const float2 pz = __ffma2_rn(make_float2(R8, R8), dZ2, make_float2(iz[0], iz[1]));
+        const float2 r = make_float2(__frcp_rn(pz.x), __frcp_rn(pz.y));
+        const float2 au = __ffma2_rn(__fmul2_rn(make_float2(fx, fx), px), r, make_float2(cxh, cxh));
+        const float2 av = __ffma2_rn(__fmul2_rn(make_float2(fy, fy), py), r, make_float2(cyh, cyh));
+        float2 d2;
+        bool in2[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float auc = c ? au.y : au.x, avc = c ? av.y : av.x, pzc = c ? pz.y : pz.x;
+          const int iu = __float2int_rd(auc), iv = __float2int_rd(avc);
+          in2[c] = pzc > 0.0f && auc == auc && avc == avc &&
+                   (unsigned int)iu < (unsigned int)width && (unsigned int)iv < (unsigned int)height;
+          const int idx = in2[c] ? iv * width + iu : 0;
+          (c ? d2.y : d2.x) = __ldg(dimg + idx);   // fl(raw ds), or -inf for an invalid pixel
+        }
+        // band test fl(d - p_z) >= -mu (d + (-p_z) rounds as d - p_z)
+        const float2 band = __fadd2_rn(d2, make_float2(-pz.x, -pz.y));
+        ok[i] = in2[0] && !(band.x < -mu);
+        ok[i + 1] = in2[1] && !(band.y < -mu);
+        dm[i] = d2.x;
+        dm[i + 1] = d2.y;
+      }
+#else
 #pragma unroll
       for (int i = 0; i < kGroup; ++i) {
         const int j = g + i, h = j & 1;
@@ -333,6 +371,7 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
         ok[i] = in && !(__fsub_rn(d, pz) < -mu);
         dm[i] = d;
       }
+#endif
       if (g == 0 && !fresh) {
         // the unit's voxels are needed from here on: their copy has been in flight during
         // the projections and the first group's depth fetches
@@ -340,9 +379,36 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
         if (!alive) break;   // a copy that never landed (flag raised): stop this warp
         parity ^= 1u;
       }
+#if VBH_FUSE_PACKED
+      float2 vv[kGroup];
+#pragma unroll
+      for (int i = 0; i < kGroup; i += 2) {   // the pair's running means in FP32x2 as well
+        const int j = g + i;
+        const float2 va = vin[lane + 32 * j], vb = vin[lane + 32 * (j + 1)];
+        const float tz = (float)(j >> 1);
+        const float2 tau = __ffma2_rn(make_float2(tz, tz), make_float2(sR22, sR22),
+                                      make_float2(tb0, tb1));
+        const float2 sdf = __fadd2_rn(__fadd2_rn(make_float2(dm[i], dm[i + 1]),
+                                                 make_float2(-bd.x, -bd.x)),
+                                      make_float2(-tau.x, -tau.y));
+        const float2 q = __fmul2_rn(sdf, make_float2(inv_mu, inv_mu));
+        const float2 f = make_float2(fminf(1.0f, fmaxf(-1.0f, q.x)), fminf(1.0f, fmaxf(-1.0f, q.y)));
+        const float2 w1 = __fadd2_rn(make_float2(va.y, vb.y), make_float2(1.0f, 1.0f));
+        const float2 rc = make_float2(rcp_approx(w1.x), rcp_approx(w1.y));
+        // running weighted mean, weight 1 per frame
+        const float2 nx = __ffma2_rn(__fadd2_rn(f, make_float2(-va.x, -vb.x)), rc,
+                                     make_float2(va.x, vb.x));
+        vv[i] = ok[i] ? make_float2(nx.x, fminf(w1.x, wmax)) : va;
+        vv[i + 1] = ok[i + 1] ? make_float2(nx.y, fminf(w1.y, wmax)) : vb;
+      }
+#endif
 #pragma unroll
       for (int i = 0; i < kGroup; ++i) {
-        const int j = g + i, h = j & 1;
+        const int j = g + i;
+#if VBH_FUSE_PACKED
+        const float2 v = vv[i];
+#else
+        const int h = j & 1;
         float2 v = vin[lane + 32 * j];
         if (ok[i]) {
           const float tau = fmaf((float)(j >> 1), sR22, h ? tb1 : tb0);
@@ -352,6 +418,7 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
           v.x = fmaf(f - v.x, rcp_approx(w1), v.x);   // running weighted mean, weight 1 per frame
           v.y = fminf(w1, wmax);
         }
+#endif
         const bool wr = ok[i] || fresh;
         if (wr) vout[lane + 32 * j] = v;
         const unsigned int negm = __ballot_sync(0xFFFFFFFFu, v.x < 0.0f);
@@ -376,6 +443,7 @@ __global__ void __launch_bounds__(kIntThreads, VBH_FUSE_MIN_CTAS)
     if (lane == 0 && fresh && part == kUnits - 1u) pool.state[p] = 0u;
     __syncwarp();   // mask words read before the next unit overwrites them
     rec = rec_next;
+    u = un;
   }
   if (!alive) {
     // wait (bounded) for this warp's copy still in flight before the CTA may exit
