@@ -66,7 +66,7 @@ def parse():
                          "copied to the host map)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the multi-client serving measurement (batched vs unbatched)")
-    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the differentiable-fusion timing (forward vs forward+backward)")
     ap.add_argument("--clock-ms", type=int, default=200,
@@ -595,12 +595,12 @@ def main():
     serve_pt = None
     if not args.no_serve and rank == 0:
         serve_pt = serve_point(torch, cam, D, poses, peak, args.serve_seconds, reps=5)
-        # the same clients at ten times the request rate: requests queue, and batching has
-        # concurrent requests to merge
-        heavy = serve_point(torch, cam, D, poses, peak, 2.0, rate=200.0, reps=3,
-                            saturated=False)
-        serve_pt["heavy_load"] = {k: heavy[k] for k in ("rate_per_client", "duration_s",
-                                                        "requests", "batched", "unbatched")}
+        # the same clients asking in step with the frames: a burst of 64 requests with work
+        # after every frame, so that batching has many concurrent requests to merge
+        burst = serve_point(torch, cam, D, poses, peak, 2.0, reps=5, saturated=False,
+                            burst_ms=1.0)
+        serve_pt["burst_load"] = {k: burst[k] for k in ("arrivals", "duration_s", "requests",
+                                                        "device_loop", "batched", "unbatched")}
 
     if rank == 0:
         line = {
@@ -1006,114 +1006,160 @@ def mc_replay(torch, cam, D, poses, args, n_timed):
     return out, timing
 
 
-def serve_point(torch, cam, D, poses, peak, duration_s=4.0, n_clients=64, rate=20.0,
-                warm_frames=30, seed=1805, reps=3, saturated=True):
-    """Multi-client streaming: the room volume updated live at 30 frames/s (frames warm_frames
-    onwards of the sequence) while n_clients clients with Poisson arrivals (rate requests/s
-    each) ask for the MC blocks changed since their last version; initial backlogs log-uniform
-    in [1, 50000] blocks (set through the clients' versions); 4 GB stream-buffer budget; results
-    released as they complete.  The same seeded script runs on fresh volumes, batched
-    (continuous batching: up to 64 requests per launch, two launches in flight, every request
-    whole) and unbatched (one request per launch), `reps` times each in alternating order.
-    Latency = arrival -> result ready, observed by the host loop.  Then one saturated launch: 64 requests with
-    backlog 4096 each in a single batch, timed with CUDA events."""
-    from paper_1805_03709_b300.serve import Server
-    from paper_1805_03709_b300.volume import Volume
+def serve_script(n_clients, rate, duration_s, warm_frames, seed, burst_ms=0.0):
+    """Request arrivals of n_clients clients and the frames at 30 frames/s.  rate > 0: Poisson
+    arrivals (rate requests/s per client); burst_ms > 0: instead, every client asks once right
+    after each frame, with a uniform delay in [0, burst_ms) ms (clients that poll in step with
+    the reconstruction)."""
     rng = np.random.default_rng(seed)
     n_fr = int(round(duration_s * 30))
     fr = [(warm_frames + k) % N_FRAMES for k in range(n_fr)]
     ev = [(int((k + 1) * 1e9 / 30), -1) for k in range(n_fr)]
     for c in range(n_clients):
-        t = rng.exponential(1.0 / rate)
-        while t < duration_s:
-            ev.append((int(t * 1e9), c))
-            t += rng.exponential(1.0 / rate)
+        if burst_ms > 0:
+            for k in range(n_fr):
+                ev.append((int((k + 1) * 1e9 / 30 + 1e5 + rng.uniform(0, burst_ms) * 1e6), c))
+        else:
+            t = rng.exponential(1.0 / rate)
+            while t < duration_s:
+                ev.append((int(t * 1e9), c))
+                t += rng.exponential(1.0 / rate)
     ev.sort()
-    t_ns = [e[0] for e in ev]
-    cl = [e[1] for e in ev]
-    backlog = np.exp(rng.uniform(0.0, np.log(50000.0), n_clients)).astype(np.int64)
+    return fr, [e[0] for e in ev], [e[1] for e in ev]
+
+
+def serve_stats(done, launches):
+    """Latency statistics of one serving run: requests with nothing new (the client already at
+    the snapshot: no device work, completed at admission) are reported apart from the served
+    ones, whose latencies are the comparison."""
+    served = [d for d in done if not (d["n_records"] == 0 and d["v_after"] == d["v_before"])]
+    zero = [d for d in done if d["n_records"] == 0 and d["v_after"] == d["v_before"]]
+    lat = np.array([(d["t_done_ns"] - d["t_arrival_ns"]) / 1e6 for d in served] or [0.0])
+    zl = np.array([(d["t_done_ns"] - d["t_arrival_ns"]) / 1e6 for d in zero] or [0.0])
+    recs = int(sum(d["n_records"] for d in done))
+    span = (max(d["t_done_ns"] for d in done) - min(d["t_arrival_ns"] for d in done)) / 1e9
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p999_ms": float(np.percentile(lat, 99.9)), "mean_ms": float(lat.mean()),
+            "max_ms": float(lat.max()), "served_requests": len(served),
+            "zero_work_requests": len(zero), "zero_work_p50_ms": float(np.percentile(zl, 50)),
+            "blocks_per_s": recs / span, "records": recs, "requests_done": len(done),
+            "launches": int(launches),
+            "served_per_launch": len(served) / max(int(launches), 1),
+            "errors": sum(1 for d in done if d["flags"] & ~3)}
+
+
+def serve_point(torch, cam, D, poses, peak, duration_s=3.0, n_clients=64, rate=20.0,
+                warm_frames=30, seed=1805, reps=5, saturated=True, burst_ms=0.0):
+    """Multi-client streaming: the room volume updated live at 30 frames/s (frames warm_frames
+    onwards of the sequence) while n_clients clients ask for the MC blocks changed since their
+    last version; initial backlogs log-uniform in [1, 50000] blocks (set through the clients'
+    versions); 4 GB stream-buffer budget; results released as they complete.  The same seeded
+    script runs on fresh volumes in three arms, `reps` times each in rotating order:
+    device_loop (the persistent request loop: admission, batching and completion on the GPU),
+    batched (the host scheduler: up to 64 requests per launch, two launches in flight) and
+    unbatched (the host scheduler, one request per launch).  Latency = arrival -> result seen
+    by the host loop, for requests that had work (requests with nothing new are counted apart).
+    Then one saturated launch: 64 requests with backlog 4096 each in a single batch, timed with
+    CUDA events."""
+    from paper_1805_03709_b300.serve import Server, ServeLoop
+    from paper_1805_03709_b300.volume import Volume
+    fr, t_ns, cl = serve_script(n_clients, rate, duration_s, warm_frames, seed, burst_ms)
+    backlog = np.exp(np.random.default_rng(seed + 1).uniform(0.0, np.log(50000.0),
+                                                             n_clients)).astype(np.int64)
     frames = [D[f] for f in fr]
     P = np.stack([poses[f] for f in fr])
-    ids = [warm_frames + 1 + k for k in range(n_fr)]
-    out = {"clients": n_clients, "rate_per_client": rate, "duration_s": duration_s,
-           "frames_per_s": 30, "budget_bytes": 4 << 30,
-           "backlog": "log-uniform in [1, 50000] blocks", "requests": sum(c >= 0 for c in cl)}
-    policies = (("batched", dict(max_batch=64, chunk_records=0, iter_records=0)),
-                ("unbatched", dict(max_batch=1, chunk_records=0, iter_records=0)))
-    # both arms run `reps` times in alternating order, each time on a fresh volume; the host
-    # loop's latencies carry the box's scheduling noise, so each statistic is reported as the
-    # median over the repetitions (every repetition is listed too)
-    runs = {name: [] for name, _ in policies}
+    ids = [warm_frames + 1 + k for k in range(len(fr))]
+    out = {"clients": n_clients, "duration_s": duration_s, "frames_per_s": 30,
+           "budget_bytes": 4 << 30, "backlog": "log-uniform in [1, 50000] blocks",
+           "requests": sum(c >= 0 for c in cl)}
+    if burst_ms > 0:
+        out["arrivals"] = f"every client once after each frame, uniform delay in [0, {burst_ms}) ms"
+    else:
+        out["rate_per_client"] = rate
+        out["arrivals"] = "Poisson"
+    arms = (("device_loop", None), ("batched", dict(max_batch=64, chunk_records=0, iter_records=0)),
+            ("unbatched", dict(max_batch=1, chunk_records=0, iter_records=0)))
+    runs = {name: [] for name, _ in arms}
     sat = None
     for rep in range(reps):
-        for name, pol in (policies if rep % 2 == 0 else policies[::-1]):
+        order = arms[rep % 3:] + arms[:rep % 3]
+        for name, pol in order:
             vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
                          N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
                          mc_cap_entries=MAX_BLOCKS * 64)
             for i in range(warm_frames):
                 vol.process_frame(D[i % N_FRAMES], poses[i % N_FRAMES], i + 1, ERASE_R)
-            srv = Server(vol, n_clients, budget_bytes=4 << 30, **pol)
+            srv = Server(vol, n_clients, budget_bytes=4 << 30,
+                         **(pol or dict(max_batch=64)))
             srv.set_versions(np.arange(n_clients), srv.versions_for_backlog(backlog))
             torch.cuda.synchronize()
-            done = srv.run(t_ns, cl, frames, P, ids, erase_radius=ERASE_R)
-            st = srv.stats()
-            lat = np.array([(d["t_done_ns"] - d["t_arrival_ns"]) / 1e6 for d in done])
-            recs = int(sum(d["n_records"] for d in done))
-            span = (max(d["t_done_ns"] for d in done) - min(d["t_arrival_ns"] for d in done)) / 1e9
-            runs[name].append({
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "p999_ms": float(np.percentile(lat, 99.9)),
-                "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
-                "blocks_per_s": recs / span, "records": recs, "requests_done": len(done),
-                "launches": int(st["iterations"]),
-                "requests_per_launch": len(done) / max(int(st["iterations"]), 1),
-                "change_records_scanned": int(st["changes_scanned"]),
-                "deferred_by_memory": int(st["deferred_memory"]),
-                "peak_buffer_bytes": int(st["bytes_peak"]),
-                "errors": sum(1 for d in done if d["flags"] & ~3)})
+            if pol is None:
+                loop = ServeLoop(srv)
+                done = loop.run(t_ns, cl, frames, P, ids, erase_radius=ERASE_R)
+                lst = loop.stats()
+                loop.stop()
+                r = serve_stats(done, 1)
+                r.update(max_in_flight=int(lst["max_active"]), chunks=int(lst["chunks"]),
+                         change_records_scanned=int(lst["change_records_scanned"]),
+                         deferred_by_memory=int(lst["deferred_memory"]),
+                         peak_buffer_bytes=int(lst["bytes_peak"]))
+            else:
+                done = srv.run(t_ns, cl, frames, P, ids, erase_radius=ERASE_R)
+                st = srv.stats()
+                r = serve_stats(done, st["iterations"])
+                r.update(change_records_scanned=int(st["changes_scanned"]),
+                         deferred_by_memory=int(st["deferred_memory"]),
+                         peak_buffer_bytes=int(st["bytes_peak"]))
+            runs[name].append(r)
             if name == "batched" and sat is None and saturated:
-                # one saturated launch: every client 4096 blocks behind, all in one batch
-                srv.set_policy(max_batch=64, chunk_records=0, iter_records=0)
-                srv.set_versions(np.arange(n_clients),
-                                 srv.versions_for_backlog(np.full(n_clients, 4096)))
-                rid = [srv.submit(c) for c in range(n_clients)]
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                it0 = srv.stats()["iterations"]
-                e0.record()
-                srv.step()
-                e1.record()
-                torch.cuda.synchronize()
-                got = []
-                while len(got) < len(rid):   # consume (and free) results as they complete
-                    srv.step()
-                    for d in srv.poll():
-                        got.append(d)
-                        srv.release(d["id"])
-                one = srv.stats()["iterations"] - it0 == 1
-                ms = e0.elapsed_time(e1)
-                live = sum(d["n_records"] for d in got)
-                alg = live * (512 + 512 + 16)   # dense block read + written + header
-                sat = {"requests": len(rid), "records": int(live), "ms": ms,
-                       "single_launch": bool(one)}
-                if one:
-                    sat.update(blocks_per_s=live / (ms / 1e3),
-                               algorithmic_GBs=alg / (ms / 1e3) / 1e9,
-                               hbm_frac=alg / (ms / 1e3) / 1e9 / peak)
+                sat = saturated_launch(torch, srv, n_clients, peak)
             srv.close()
             vol.close()
             torch.cuda.synchronize()
-    stats = ("p50_ms", "p99_ms", "p999_ms", "mean_ms", "max_ms", "blocks_per_s")
-    for name, _ in policies:
+    stats = ("p50_ms", "p99_ms", "p999_ms", "mean_ms", "max_ms", "blocks_per_s",
+             "served_per_launch", "zero_work_p50_ms")
+    for name, _ in arms:
         rs = runs[name]
         res = dict(rs[0])
         res.update({k: float(np.median([r[k] for r in rs])) for k in stats})
-        res["statistic"] = f"median over {reps} alternating repetitions"
+        res["p99_ms_range"] = [float(min(r["p99_ms"] for r in rs)),
+                               float(max(r["p99_ms"] for r in rs))]
+        res["statistic"] = f"median over {reps} rotating repetitions (p99 range: min, max)"
         res["reps"] = [{k: r[k] for k in ("p50_ms", "p99_ms", "p999_ms", "max_ms")} for r in rs]
         out[name] = res
-    out["batched"]["saturated"] = sat
+    if sat is not None:
+        out["batched"]["saturated"] = sat
     return out
+
+
+def saturated_launch(torch, srv, n_clients, peak):
+    """One launch of the host scheduler with every client 4096 blocks behind (CUDA events)."""
+    srv.set_policy(max_batch=64, chunk_records=0, iter_records=0)
+    srv.set_versions(np.arange(n_clients), srv.versions_for_backlog(np.full(n_clients, 4096)))
+    rid = [srv.submit(c) for c in range(n_clients)]
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    it0 = srv.stats()["iterations"]
+    e0.record()
+    srv.step()
+    e1.record()
+    torch.cuda.synchronize()
+    got = []
+    while len(got) < len(rid):   # consume (and free) results as they complete
+        srv.step()
+        for d in srv.poll():
+            got.append(d)
+            srv.release(d["id"])
+    one = srv.stats()["iterations"] - it0 == 1
+    ms = e0.elapsed_time(e1)
+    live = sum(d["n_records"] for d in got)
+    alg = live * (512 + 512 + 16)   # dense block read + written + header
+    sat = {"requests": len(rid), "records": int(live), "ms": ms, "single_launch": bool(one)}
+    if one:
+        sat.update(blocks_per_s=live / (ms / 1e3), algorithmic_GBs=alg / (ms / 1e3) / 1e9,
+                   hbm_frac=alg / (ms / 1e3) / 1e9 / peak)
+    return sat
 
 
 def diff_point(torch, dev, flush, reps=10, warm=3):

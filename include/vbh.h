@@ -549,7 +549,7 @@ uint64_t vbh_serve_now_ns(void);
  *     synchronisation (cudaDeviceSynchronize, cudaFree) waits until the loop stops.
  * The loop object is used from one host thread. */
 typedef struct {
-  uint32_t ctas;             /* CTAs of 256 threads (0 = one per two SMs); all co-resident */
+  uint32_t ctas;             /* CTAs of 256 threads (0 = one per SM); all co-resident */
   uint32_t max_slots;        /* requests in flight at once, 1..64 (0 = 64) */
   uint32_t chunk_records;    /* change records per chunk (0 = 4096) */
   uint32_t bypass_rounds;    /* scheduler rounds a memory-blocked head may be passed */

@@ -118,12 +118,12 @@ void free_batch_lists(vbh_handle* h) {
 }
 
 vbh_status maybe_rebuild(vbh_handle* h) {
-  // a running serving loop finds keys while frames run: entries must not move under it
-  if (h->serve_loop_active) return VBH_OK;
   if (h->snap_pending && cudaEventQuery(h->snap_ev) == cudaSuccess) {
     h->snap_pending = false;
     const unsigned int tomb = h->snap->n_tomb, empty = h->snap->n_empty;
-    if (tomb > h->n_slots / 64u && tomb > (tomb + empty) / 2u) return rebuild(h);
+    // a running serving loop finds keys while frames run: entries must not move under it
+    if (!h->serve_loop_active && tomb > h->n_slots / 64u && tomb > (tomb + empty) / 2u)
+      return rebuild(h);
   }
   return VBH_OK;
 }

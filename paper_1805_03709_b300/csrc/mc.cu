@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
       // concurrently reads the number before and after its copy and drops a changed block
       if (lane == 0) pool.seq[q] = seq0 + r;
       __syncwarp();
-      __threadfence();
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
       unsigned long long* st = reinterpret_cast<unsigned long long*>(sl->store + 32u * q);
 #pragma unroll
       for (int h = 0; h < 2; ++h)   // cubes that are not emitted are stored as 0

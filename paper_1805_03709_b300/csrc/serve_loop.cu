@@ -51,6 +51,7 @@ constexpr unsigned int kChunkRing = 1024u;    // chunks published and not yet fi
 constexpr unsigned int kRegionRing = 8192u;   // stream-buffer regions not yet released
 constexpr unsigned int kRecHdr = 16u, kRecPay = 512u, kRecAll = 528u;
 constexpr unsigned int kErrOverrun = 2u, kErrCap = 4u;   // as kServeErr* (serve.cu)
+constexpr unsigned int kStageBlocks = 16u;    // blocks a worker copies at once
 
 // Host -> device (mapped host memory).
 struct LoopReq {
@@ -81,11 +82,10 @@ struct LoopHostOut {
   unsigned int pad[12];
 };
 
-struct ReqSlot {            // a request in flight (state 1) or a free slot (state 0)
-  unsigned int state, id, client, scan;
-  unsigned int lo, hi, next;   // log records lo+1..hi (scan: pool entries lo..hi-1); next chunked
+struct ReqSlot {            // a request in flight (its bit clear in free_mask)
+  unsigned int id, client, scan;
   unsigned int sigma, cap, v0, v1, flags;
-  unsigned int region, chunks_total, chunks_issued;
+  unsigned int region, chunks_total;
   unsigned int chunks_done;    // atomic (workers)
   unsigned int rec_count;      // atomic (workers)
   unsigned int err;            // atomic (workers)
@@ -108,22 +108,15 @@ struct LoopDev {
   // shared between the scheduler and the workers
   unsigned long long next_ticket;   // atomic: tiles handed out
   unsigned long long end_tile;      // tiles published
+  unsigned long long free_mask;     // bit i: slot i free (workers set, the scheduler clears)
   unsigned int chunk_tail;          // chunks published
   unsigned int stop;                // workers leave
   unsigned int sched_beat;          // scheduler heartbeat
   unsigned int done_count;          // completions published (atomic)
-  unsigned int active;              // requests in flight (atomic)
   unsigned int worker_err;          // a worker gave up waiting
-  // scheduler only
-  unsigned int req_head, rel_head;
-  unsigned int pend_head, pend_tail;
-  unsigned int r_head, r_tail;      // region FIFO
-  unsigned int chunk_low;           // oldest chunk not known to be finished
-  unsigned int head_blocked;
-  unsigned long long a_head, a_tail;   // ring allocator over the stream buffer
-  // statistics
-  unsigned long long records_served, scanned, chunks, rounds, deferred, bytes_peak;
-  unsigned int max_active, pad;
+  unsigned int max_active;
+  // statistics (written by the scheduler every 64 rounds and at the end)
+  unsigned long long records_served, scanned, chunks, rounds, deferred, bytes_peak, a_in_use;
 };
 
 struct LoopArgs {
@@ -164,6 +157,11 @@ __device__ __forceinline__ unsigned int ld_sys(const unsigned int* p) {
 }
 __device__ __forceinline__ void st_rel_sys(unsigned int* p, unsigned int v) {
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Acquire-release fence at GPU scope (orders the copies before the second look at a refresh
+// number, and the scheduler's descriptor writes before their publication).
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -244,18 +242,19 @@ __device__ void complete_request(const LoopArgs& A, unsigned int si) {
   atomicAdd(&A.d->records_served, (unsigned long long)nr);
   publish_done(A, id, client, nr, flags, v0, v1, region, cap, off);
   __threadfence();
-  vstore(&R->state, 0u);   // the slot and the client are free for the scheduler
-  __threadfence();
-  vstore(&A.client_busy[client], 0u);
-  atomicSub(&A.d->active, 1u);
+  vstore(&A.client_busy[client], 0u);   // the client and the slot are free for the scheduler
+  atomicOr(&A.d->free_mask, 1ull << si);
 }
 
-// Serve one 32-record tile of a chunk (one warp): test each record for being current, copy the
-// current blocks' indices with a sequence check, reserve output records, write headers and
-// payloads.  Records rec0 + 1 .. rec_end of the log (scan: pool entries rec0 .. rec_end - 1).
-__device__ void serve_tile(const LoopArgs& A, const ServeLog& S, unsigned int si, bool scan,
-                           unsigned int sigma, unsigned int cap, unsigned long long off,
-                           unsigned int rec0, unsigned int rec_end) {
+// Serve one 32-record tile of a chunk (one warp): test each record for being current; copy
+// every current block's 512 B of indices into the warp's staging area in shared memory with
+// asynchronous 16 B copies (all of the tile's copies in flight at once), fence, and read each
+// block's refresh number again -- a block whose number changed meanwhile is dropped; reserve
+// the tile's output with one atomic, write the headers, and the payloads from the staging
+// area.  Records rec0 + 1 .. rec_end of the log (scan: pool entries rec0 .. rec_end - 1).
+__device__ void serve_tile(const LoopArgs& A, const ServeLog& S, uint4* stage, unsigned int si,
+                           bool scan, unsigned int sigma, unsigned int cap,
+                           unsigned long long off, unsigned int rec0, unsigned int rec_end) {
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int lt = (1u << lane) - 1u;
   ReqSlot* R = A.slots + si;
@@ -302,7 +301,7 @@ __device__ void serve_tile(const LoopArgs& A, const ServeLog& S, unsigned int si
   unsigned char* region = A.arena + off;
   int4* hdr = reinterpret_cast<int4*>(region);
   uint4* pay = reinterpret_cast<uint4*>(region + (size_t)cap * kRecHdr);
-  // removal records: header only
+  // removal records: a header only
   const unsigned int rm = __ballot_sync(0xFFFFFFFFu, cur && p == kNone);
   if (rm) {
     unsigned int base = 0u;
@@ -315,285 +314,314 @@ __device__ void serve_tile(const LoopArgs& A, const ServeLog& S, unsigned int si
       hdr[base + __popc(rm & lt)] = make_int4(k3.x, k3.y, k3.z, (int)info);
     }
   }
-  // blocks: eight copies in flight, then a fence and a second look at their sequence numbers
-  unsigned int live = __ballot_sync(0xFFFFFFFFu, cur && p != kNone);
-  while (live) {
-    uint4 v[8];
-    unsigned int q[8], src[8];
-    int m = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (live) {
-        src[i] = (unsigned int)(__ffs(live) - 1);
-        live &= live - 1u;
-        q[i] = __shfl_sync(0xFFFFFFFFu, p, (int)src[i]);
-        v[i] = __ldcg(S.store + 32u * q[i] + lane);
-        m = i + 1;
-      }
+  // current blocks, kStageBlocks at a time: block i of the group at stage + 32 i (lane L
+  // copies word L of each), all copies of the group in flight at once
+  unsigned int rest = __ballot_sync(0xFFFFFFFFu, cur && p != kNone);
+  while (rest) {
+    unsigned int grp = 0u;
+    for (unsigned int i = 0; i < kStageBlocks && rest; ++i) {
+      const int src = __ffs(rest) - 1;
+      rest &= rest - 1u;
+      grp |= 1u << src;
+      const unsigned int q = __shfl_sync(0xFFFFFFFFu, p, src);
+      const unsigned int dst = (unsigned int)__cvta_generic_to_shared(stage + 32u * i + lane);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                   "l"(S.store + 32u * q + lane)
+                   : "memory");
     }
-    __threadfence();
-    // lane i (i < m) re-checks copy i
-    bool ok = false;
-    unsigned int my_src = 0u;
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (i < m && lane == (unsigned int)i) my_src = src[i];
-    const unsigned long long k_i = __shfl_sync(0xFFFFFFFFu, key, (int)my_src);
-    const unsigned int e_i = __shfl_sync(0xFFFFFFFFu, e_ref, (int)my_src);
-    const unsigned int p_i = __shfl_sync(0xFFFFFFFFu, p, (int)my_src);
-    const unsigned int info_i = __shfl_sync(0xFFFFFFFFu, info, (int)my_src);
-    if (lane < (unsigned int)m)
-      ok = __ldcg(A.pool.seq + p_i) == e_i && __ldcg(A.pool.pkeys + p_i) == k_i;
+    asm volatile("cp.async.commit_group;\n cp.async.wait_all;" ::: "memory");
+    fence_acq_rel_gpu();
+    // a block refreshed again while it was copied is dropped (its newer refresh is after sigma)
+    const bool mine = (grp >> lane) & 1u;
+    const bool ok = mine && __ldcg(A.pool.seq + p) == e_ref && __ldcg(A.pool.pkeys + p) == key;
     const unsigned int okm = __ballot_sync(0xFFFFFFFFu, ok);
     const unsigned int n = __popc(okm);
-    if (!n) continue;
-    unsigned int base = 0u;
-    if (lane == 0u) base = atomicAdd(&R->rec_count, n);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if ((unsigned long long)base + n > cap) {
-      err |= kErrCap;
-      continue;
+    if (n) {
+      unsigned int base = 0u;
+      if (lane == 0u) base = atomicAdd(&R->rec_count, n);
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if ((unsigned long long)base + n > cap) {
+        err |= kErrCap;
+      } else {
+        if (ok) {
+          const int3 k3 = unpack_key(key);
+          hdr[base + __popc(okm & lt)] = make_int4(k3.x, k3.y, k3.z, (int)info);
+        }
+        unsigned int g = grp;
+        for (unsigned int i = 0; g; ++i) {
+          const int src = __ffs(g) - 1;
+          g &= g - 1u;
+          if ((okm >> src) & 1u)
+            pay[(size_t)(base + __popc(okm & ((1u << src) - 1u))) * 32u + lane] =
+                stage[32u * i + lane];
+        }
+      }
     }
-    if (ok) {
-      const int3 k3 = unpack_key(k_i);
-      hdr[base + __popc(okm & lt)] = make_int4(k3.x, k3.y, k3.z, (int)info_i);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (i < m && ((okm >> i) & 1u))
-        pay[(size_t)(base + __popc(okm & ((1u << i) - 1u))) * 32u + lane] = v[i];
+    __syncwarp();   // the group's staging area is read before the next group's copies land
   }
+  __syncwarp();   // the staging area is free for the warp's next tile
   err = __reduce_or_sync(0xFFFFFFFFu, err);
   if (err && lane == 0u) atomicOr(&R->err, err);
 }
 
-// Ring allocator over the stream buffer: regions are handed out in order and released in any
-// order; the tail passes released regions in allocation order.  A region never wraps (the rest
-// of the buffer before the wrap becomes a released filler region).
-__device__ bool arena_alloc(const LoopArgs& A, unsigned long long bytes,
+// Ring allocator over the stream buffer (scheduler-private): regions are handed out in order
+// and released in any order; the tail passes released regions in order.  A region never wraps
+// (the rest of the buffer before the wrap becomes a released filler region).
+struct Arena {
+  unsigned long long head, tail;   // monotonic byte positions
+  unsigned int r_head, r_tail;     // region FIFO
+};
+
+__device__ bool arena_alloc(const LoopArgs& A, Arena& a, unsigned long long bytes,
                             unsigned long long* start, unsigned int* idx) {
-  LoopDev* d = A.d;
-  if (d->a_head == d->a_tail) {   // nothing in use: start at the beginning of the buffer
-    d->a_head = (d->a_head + A.budget - 1ull) / A.budget * A.budget;
-    d->a_tail = d->a_head;
+  if (a.head == a.tail) {   // nothing in use: start at the beginning of the buffer
+    a.head = (a.head + A.budget - 1ull) / A.budget * A.budget;
+    a.tail = a.head;
   }
-  const unsigned long long pos = d->a_head % A.budget;
+  const unsigned long long pos = a.head % A.budget;
   const unsigned long long pad = pos + bytes > A.budget ? A.budget - pos : 0ull;
-  if (d->r_head - d->r_tail + (pad ? 2u : 1u) > kRegionRing) return false;
-  if (d->a_head + pad + bytes - d->a_tail > A.budget) return false;
+  if (a.r_head - a.r_tail + (pad ? 2u : 1u) > kRegionRing) return false;
+  if (a.head + pad + bytes - a.tail > A.budget) return false;
   if (pad) {
-    Region& f = A.regions[d->r_head % kRegionRing];
-    f.start = d->a_head;
+    Region& f = A.regions[a.r_head % kRegionRing];
+    f.start = a.head;
     f.bytes = pad;
-    vstore(&f.freed, 1u);
-    d->r_head += 1u;
-    d->a_head += pad;
+    f.freed = 1u;
+    a.r_head += 1u;
+    a.head += pad;
   }
-  Region& g = A.regions[d->r_head % kRegionRing];
-  g.start = d->a_head;
+  Region& g = A.regions[a.r_head % kRegionRing];
+  g.start = a.head;
   g.bytes = bytes;
-  vstore(&g.freed, 0u);
-  *idx = d->r_head;
-  *start = d->a_head;
-  d->r_head += 1u;
-  d->a_head += bytes;
-  if (d->a_head - d->a_tail > d->bytes_peak) d->bytes_peak = d->a_head - d->a_tail;
+  g.freed = 0u;
+  *idx = a.r_head;
+  *start = a.head;
+  a.r_head += 1u;
+  a.head += bytes;
   return true;
 }
 
-// Try to admit pending request q at snapshot sigma.  Returns 0 admitted or completed at once,
-// 1 client busy, 2 no slot / no completion room (stop admitting), 3 no stream-buffer room.
-__device__ int try_admit(const LoopArgs& A, const LoopReq& q, unsigned int sigma,
-                         unsigned int done_read) {
-  LoopDev* d = A.d;
-  if (q.client >= A.n_clients) {   // never written by the library's host side: refuse it
-    publish_done(A, q.id, q.client, 0u, VBH_SERVE_ERR_VERSION, 0u, 0u, 0xFFFFFFFFu, 0u, 0ull);
-    return 0;
-  }
-  if (vload(&A.client_busy[q.client])) return 1;
-  // a slot, and room in the completion ring for every request in flight plus this one
-  const unsigned int active = vload(&d->active);
-  const unsigned int outstanding = vload(&d->done_count) - done_read;
-  if (active >= A.n_slots || outstanding + active + 1u > A.ring_mask + 1u) return 2;
-  const unsigned int v = vload(&A.client_v[q.client]);
-  const unsigned int margin = A.log_cap / 2u;   // records that may be appended while one runs
-  const unsigned int floor = sigma > margin ? sigma - margin : 0u;
-  const bool scan = v == 0u || v < floor;
-  if (!scan && sigma <= v) {   // nothing changed since v: complete without work
-    publish_done(A, q.id, q.client, 0u, 0u, v, v, 0xFFFFFFFFu, 0u, 0ull);
-    return 0;
-  }
-  unsigned long long count = scan ? A.max_blocks : (unsigned long long)(sigma - v);
-  unsigned int flags = scan ? VBH_SERVE_RESET : 0u;
-  const unsigned long long max_recs = A.budget / kRecAll;
-  if (count > max_recs) {
-    count = max_recs;
-    flags |= VBH_SERVE_PARTIAL;
-  }
-  const unsigned long long bytes = (count * kRecAll + 255ull) & ~255ull;
-  unsigned long long start;
-  unsigned int region;
-  if (!arena_alloc(A, bytes, &start, &region)) return 3;
-  unsigned int si = 0;
-  while (si < A.n_slots && vload(&A.slots[si].state) != 0u) ++si;   // free (active < n_slots)
-  if (si == A.n_slots) {   // (not reached: a slot is free while active < n_slots)
-    d->a_head -= bytes;      // undo the allocation: it was the newest region
-    d->r_head -= 1u;
-    return 2;
-  }
-  ReqSlot& R = A.slots[si];
-  R.id = q.id;
-  R.client = q.client;
-  R.scan = scan ? 1u : 0u;
-  R.lo = scan ? 0u : v;
-  R.hi = scan ? A.max_blocks : v + (unsigned int)count;
-  R.next = R.lo;
-  R.sigma = sigma;
-  R.cap = (unsigned int)count;
-  R.v0 = v;
-  R.v1 = scan ? sigma : R.hi;
-  R.flags = flags;
-  R.region = region;
-  R.off = start % A.budget;
-  R.chunks_total = (unsigned int)((count + A.chunk_records - 1ull) / A.chunk_records);
-  R.chunks_issued = 0u;
-  R.chunks_done = 0u;
-  R.rec_count = 0u;
-  R.err = 0u;
-  __threadfence();
-  vstore(&R.state, 1u);
-  vstore(&A.client_busy[q.client], 1u);
-  const unsigned int now_active = atomicAdd(&d->active, 1u) + 1u;
-  if (now_active > d->max_active) d->max_active = now_active;
-  return 0;
-}
-
-// The scheduler (one thread): host rings in, admission, chunk rounds, liveness.
-__device__ void scheduler(const LoopArgs& A) {
+// The scheduler (one thread).  Its own state lives in registers and in the shared memory of
+// its warp (per-slot chunk cursors); device memory shared with the workers is touched only to
+// read client state, take a slot and publish chunks, and mapped host memory once per round
+// (the request ring's tail), every 4th round (the release ring) and every 16th round (the
+// host's sign of life): each of those reads crosses PCIe.
+__device__ void scheduler(const LoopArgs& A, unsigned int* sm) {
   LoopDev* d = A.d;
   const ServeLog* sl = A.sl;
+  unsigned int* s_next = sm;                   // next change record to chunk, per slot
+  unsigned int* s_hi = sm + kLoopMaxSlots;     // end of the slot's range
+  unsigned int req_head = 0u, rel_head = 0u, pend_head = 0u, pend_tail = 0u;
+  unsigned int chunk_low = 0u, chunk_tail = 0u, head_blocked = 0u, max_active = 0u;
+  unsigned long long end_tile = 0ull, work = 0ull;   // work: slots with chunks left
+  unsigned long long scanned = 0ull, chunks = 0ull, rounds = 0ull, deferred = 0ull, peak = 0ull;
+  Arena a{0ull, 0ull, 0u, 0u};
   unsigned int last_beat = ld_sys(&A.hin->beat);
   unsigned long long t_host = globaltimer();
   unsigned int status = 0u;
-  const unsigned long long low_water = 2ull * A.n_workers;
+  const unsigned long long low_water = (unsigned long long)A.n_workers + 64ull;
+  const unsigned long long all_slots =
+      A.n_slots >= 64u ? ~0ull : ((1ull << A.n_slots) - 1ull);
   for (unsigned int round = 1;; ++round) {
     vstore(&d->sched_beat, round);
     bool busy = false;
-    const unsigned long long now = globaltimer();
-    const unsigned int hb = ld_sys(&A.hin->beat);
-    if (hb != last_beat) {
-      last_beat = hb;
-      t_host = now;
+    if ((round & 15u) == 1u) {
+      const unsigned long long now = globaltimer();
+      const unsigned int hb = ld_sys(&A.hin->beat);
+      if (hb != last_beat) {
+        last_beat = hb;
+        t_host = now;
+      }
+      if (ld_acq_sys(&A.hin->stop)) break;
+      if (now - t_host > A.timeout_ns) {
+        status = VBH_ERR_TIMEOUT;
+        break;
+      }
     }
-    if (ld_acq_sys(&A.hin->stop)) break;
-    if (now - t_host > A.timeout_ns) {
-      status = VBH_ERR_TIMEOUT;
-      break;
-    }
-    // releases, then the allocator tail over released regions
-    const unsigned int rt = ld_acq_sys(&A.hin->rel_tail);
-    while (d->rel_head != rt) {
-      const unsigned int r = ld_sys(A.rel_ring + (d->rel_head & A.ring_mask));
-      vstore(&A.regions[r % kRegionRing].freed, 1u);
-      d->rel_head += 1u;
-      busy = true;
-    }
-    st_rel_sys(&A.hout->rel_head, d->rel_head);
-    while (d->r_tail != d->r_head && vload(&A.regions[d->r_tail % kRegionRing].freed)) {
-      const Region& g = A.regions[d->r_tail % kRegionRing];
-      d->a_tail = g.start + g.bytes;
-      d->r_tail += 1u;
+    // releases, then the allocator's tail over released regions
+    if ((round & 3u) == 1u) {
+      const unsigned int rt = ld_acq_sys(&A.hin->rel_tail);
+      while (rel_head != rt) {
+        const unsigned int r = ld_sys(A.rel_ring + (rel_head & A.ring_mask));
+        A.regions[r % kRegionRing].freed = 1u;
+        rel_head += 1u;
+        busy = true;
+      }
+      st_rel_sys(&A.hout->rel_head, rel_head);
+      while (a.r_tail != a.r_head && A.regions[a.r_tail % kRegionRing].freed) {
+        const Region& g = A.regions[a.r_tail % kRegionRing];
+        a.tail = g.start + g.bytes;
+        a.r_tail += 1u;
+      }
     }
     // new requests into the pending queue (arrival order)
     const unsigned int qt = ld_acq_sys(&A.hin->req_tail);
-    while (d->req_head != qt && d->pend_tail - d->pend_head <= A.ring_mask) {
-      const unsigned int* e = reinterpret_cast<const unsigned int*>(A.req_ring +
-                                                                    (d->req_head & A.ring_mask));
-      LoopReq q;
-      q.id = ld_sys(e);
-      q.client = ld_sys(e + 1);
-      A.pend[d->pend_tail & A.ring_mask] = q;
-      d->pend_tail += 1u;
-      d->req_head += 1u;
+    if (req_head != qt) {
+      while (req_head != qt && pend_tail - pend_head <= A.ring_mask) {
+        const unsigned int* e =
+            reinterpret_cast<const unsigned int*>(A.req_ring + (req_head & A.ring_mask));
+        LoopReq q;
+        q.id = ld_sys(e);
+        q.client = ld_sys(e + 1);
+        A.pend[pend_tail & A.ring_mask] = q;
+        pend_tail += 1u;
+        req_head += 1u;
+      }
+      st_rel_sys(&A.hout->req_head, req_head);
       busy = true;
     }
-    st_rel_sys(&A.hout->req_head, d->req_head);
     // admission in arrival order at the newest published snapshot
-    if (d->pend_head != d->pend_tail) {
+    if (pend_head != pend_tail) {
       const unsigned int sigma = vload(&sl->seq_next) - 1u;
-      __threadfence();
+      fence_acq_rel_gpu();
       const unsigned int done_read = ld_sys(&A.hin->done_read);
-      unsigned int w = d->pend_head;
-      bool head = true, stop_adm = false;
-      for (unsigned int r = d->pend_head; r != d->pend_tail; ++r) {
+      unsigned long long free = vload(&d->free_mask) & all_slots;
+      unsigned int w = pend_head;
+      bool head = true, stop_adm = false, admitted = false;
+      for (unsigned int r = pend_head; r != pend_tail; ++r) {
         const LoopReq q = A.pend[r & A.ring_mask];
         bool keep = true;
         if (!stop_adm) {
-          const int res = try_admit(A, q, sigma, done_read);
-          if (res == 0) {
+          const unsigned int active = A.n_slots - __popcll(free);
+          const unsigned int outstanding = vload(&d->done_count) - done_read;
+          if (q.client >= A.n_clients) {   // never written by the library's host side
+            publish_done(A, q.id, q.client, 0u, VBH_SERVE_ERR_VERSION, 0u, 0u, 0xFFFFFFFFu, 0u,
+                         0ull);
             keep = false;
-            busy = true;
-            if (head) d->head_blocked = 0u;
-          } else if (res == 2) {
-            stop_adm = true;
-          } else if (res == 3) {
-            d->deferred += 1ull;
-            if (head && ++d->head_blocked > A.bypass_rounds) stop_adm = true;
-            head = false;
+          } else if (vload(&A.client_busy[q.client])) {
+            head = false;   // one request per client at a time, in arrival order
+          } else if (!free || outstanding + active + 1u > A.ring_mask + 1u) {
+            stop_adm = true;   // no slot, or no completion-ring room for one more
           } else {
-            head = false;
+            const unsigned int v = vload(&A.client_v[q.client]);
+            const unsigned int margin = A.log_cap / 2u;   // records appended while one runs
+            const unsigned int floor = sigma > margin ? sigma - margin : 0u;
+            const bool scan = v == 0u || v < floor;
+            if (!scan && sigma <= v) {   // nothing changed since v: complete without work
+              publish_done(A, q.id, q.client, 0u, 0u, v, v, 0xFFFFFFFFu, 0u, 0ull);
+              keep = false;
+            } else {
+              unsigned long long count = scan ? A.max_blocks : (unsigned long long)(sigma - v);
+              unsigned int flags = scan ? VBH_SERVE_RESET : 0u;
+              const unsigned long long max_recs = A.budget / kRecAll;
+              if (count > max_recs) {
+                count = max_recs;
+                flags |= VBH_SERVE_PARTIAL;
+              }
+              const unsigned long long bytes = (count * kRecAll + 255ull) & ~255ull;
+              unsigned long long start;
+              unsigned int region;
+              if (!arena_alloc(A, a, bytes, &start, &region)) {
+                deferred += 1ull;
+                if (head && ++head_blocked > A.bypass_rounds) stop_adm = true;
+                head = false;
+              } else {
+                if (head) head_blocked = 0u;
+                if (a.head - a.tail > peak) peak = a.head - a.tail;
+                const unsigned int si = (unsigned int)(__ffsll((long long)free) - 1);
+                free &= ~(1ull << si);
+                atomicAnd(&d->free_mask, ~(1ull << si));
+                ReqSlot& R = A.slots[si];
+                R.id = q.id;
+                R.client = q.client;
+                R.scan = scan ? 1u : 0u;
+                R.sigma = sigma;
+                R.cap = (unsigned int)count;
+                R.v0 = v;
+                R.v1 = scan ? sigma : v + (unsigned int)count;
+                R.flags = flags;
+                R.region = region;
+                R.off = start % A.budget;
+                R.chunks_total =
+                    (unsigned int)((count + A.chunk_records - 1ull) / A.chunk_records);
+                R.chunks_done = 0u;
+                R.rec_count = 0u;
+                R.err = 0u;
+                s_next[si] = scan ? 0u : v;
+                s_hi[si] = scan ? A.max_blocks : v + (unsigned int)count;
+                work |= 1ull << si;
+                vstore(&A.client_busy[q.client], 1u);
+                keep = false;
+                admitted = true;
+                const unsigned int now_active = active + 1u;
+                if (now_active > max_active) max_active = now_active;
+              }
+            }
           }
         }
         if (keep) A.pend[(w++) & A.ring_mask] = q;
       }
-      d->pend_tail = w;
+      pend_tail = w;
+      if (admitted) busy = true;
     }
-    // chunks: keep the workers' backlog of published tiles above the low-water mark, one chunk
-    // at a time to the active request with the smallest remainder
-    while (d->chunk_low != d->chunk_tail) {
-      const Chunk& c = A.chunks[d->chunk_low % kChunkRing];
-      if (vload(&c.finished) < c.tiles) break;
-      d->chunk_low += 1u;
-    }
-    unsigned long long et = d->end_tile;
+    // chunks: keep the workers' backlog of published tiles above the low-water mark, each
+    // chunk to the active request with the smallest remainder; one publication per round
     const unsigned long long nt = vload(&d->next_ticket);
-    unsigned long long backlog = et > nt ? et - nt : 0ull;
-    while (backlog < low_water && d->chunk_tail - d->chunk_low < kChunkRing) {
-      unsigned int best = kNone, best_rem = 0xFFFFFFFFu;
-      for (unsigned int i = 0; i < A.n_slots; ++i) {
-        const ReqSlot& R = A.slots[i];
-        if (vload(&R.state) != 1u || R.next >= R.hi) continue;
-        if (R.hi - R.next < best_rem) {
-          best_rem = R.hi - R.next;
-          best = i;
+    unsigned long long backlog = end_tile > nt ? end_tile - nt : 0ull;
+    if (work && backlog < low_water) {
+      if (chunk_tail - chunk_low + 32u > kChunkRing) {
+        while (chunk_low != chunk_tail) {
+          const Chunk& c = A.chunks[chunk_low % kChunkRing];
+          if (vload(&c.finished) < c.tiles) break;
+          chunk_low += 1u;
         }
       }
-      if (best == kNone) break;
-      ReqSlot& R = A.slots[best];
-      const unsigned int take = best_rem < A.chunk_records ? best_rem : A.chunk_records;
-      Chunk& c = A.chunks[d->chunk_tail % kChunkRing];
-      c.start_tile = et;
-      c.idx = d->chunk_tail;
-      c.tiles = (take + 31u) / 32u;
-      c.slot = best;
-      c.lo = R.next;
-      c.hi = R.next + take;
-      vstore(&c.finished, 0u);
-      R.next += take;
-      R.chunks_issued += 1u;
-      d->scanned += take;
-      d->chunks += 1ull;
-      __threadfence();
-      vstore(&d->chunk_tail, d->chunk_tail + 1u);
-      __threadfence();
-      et += c.tiles;
-      vstore(&d->end_tile, et);
-      backlog += c.tiles;
-      busy = true;
+      unsigned int published = 0u;
+      while (work && backlog < low_water && chunk_tail - chunk_low < kChunkRing) {
+        unsigned int best = 0u, best_rem = 0xFFFFFFFFu;
+        for (unsigned long long m = work; m; m &= m - 1ull) {
+          const unsigned int i = (unsigned int)(__ffsll((long long)m) - 1);
+          const unsigned int rem = s_hi[i] - s_next[i];
+          if (rem < best_rem) {
+            best_rem = rem;
+            best = i;
+          }
+        }
+        const unsigned int take = best_rem < A.chunk_records ? best_rem : A.chunk_records;
+        Chunk& c = A.chunks[chunk_tail % kChunkRing];
+        c.start_tile = end_tile;
+        c.idx = chunk_tail;
+        c.tiles = (take + 31u) / 32u;
+        c.slot = best;
+        c.lo = s_next[best];
+        c.hi = s_next[best] + take;
+        c.finished = 0u;
+        s_next[best] += take;
+        if (s_next[best] == s_hi[best]) work &= ~(1ull << best);
+        scanned += take;
+        chunks += 1ull;
+        chunk_tail += 1u;
+        end_tile += c.tiles;
+        backlog += c.tiles;
+        published += 1u;
+      }
+      if (published) {
+        fence_acq_rel_gpu();   // descriptors (and the slots they name) before their tickets
+        vstore(&d->chunk_tail, chunk_tail);
+        fence_acq_rel_gpu();
+        vstore(&d->end_tile, end_tile);
+        busy = true;
+      }
     }
-    if (busy) d->rounds += 1ull;
-    else __nanosleep(200);
+    if (busy) rounds += 1ull;
+    if ((round & 63u) == 0u) {   // statistics for vbh_serve_loop_stats_read
+      d->scanned = scanned;
+      d->chunks = chunks;
+      d->rounds = rounds;
+      d->deferred = deferred;
+      d->bytes_peak = peak;
+      d->max_active = max_active;
+      d->a_in_use = a.head - a.tail;
+    }
+    if (!busy) __nanosleep(100);
   }
+  d->scanned = scanned;
+  d->chunks = chunks;
+  d->rounds = rounds;
+  d->deferred = deferred;
+  d->bytes_peak = peak;
+  d->max_active = max_active;
+  d->a_in_use = a.head - a.tail;
   __threadfence();
   vstore(&d->stop, 1u);
   __threadfence_system();
@@ -603,11 +631,12 @@ __device__ void scheduler(const LoopArgs& A) {
 
 // A worker warp: take a ticket, wait (bounded) until its tile is published, find the tile's
 // chunk, serve it, and close the chunk / request when it was the last tile.
-__device__ void worker(const LoopArgs& A) {
+__device__ void worker(const LoopArgs& A, uint4* stage) {
   LoopDev* d = A.d;
   const unsigned int lane = threadIdx.x & 31u;
   const ServeLog S = *A.sl;   // its pointers and masks do not change while a server is attached
   const unsigned long long stall_ns = 2ull * A.timeout_ns;
+  unsigned int hint = 0u;     // the chunk of this warp's previous tile (tickets only grow)
   for (;;) {
     unsigned long long t = 0ull;
     if (lane == 0u) t = atomicAdd(&d->next_ticket, 1ull);
@@ -639,22 +668,34 @@ __device__ void worker(const LoopArgs& A) {
     state = __shfl_sync(0xFFFFFFFFu, state, 0);
     if (state == 2 && lane == 0u) atomicOr(&d->worker_err, 1u);
     if (state) return;
-    __threadfence();
+    fence_acq_rel_gpu();
     // the chunk holding ticket t: the last published chunk whose first ticket is <= t (ring
     // positions reused by newer chunks belong to chunks older than every unfinished one)
     unsigned int c = 0u;
     if (lane == 0u) {
       const unsigned int hi = vload(&d->chunk_tail);
-      unsigned int lo = hi > kChunkRing ? hi - kChunkRing : 0u, top = hi;
-      while (top - lo > 1u) {   // invariant: chunk lo qualifies, chunk top does not
-        const unsigned int mid = lo + (top - lo) / 2u;
-        const Chunk& m = A.chunks[mid % kChunkRing];
-        if (vload(&m.idx) != mid || vload(&m.start_tile) <= t) lo = mid;
-        else top = mid;
+      unsigned int lo = hi > kChunkRing ? hi - kChunkRing : 0u;
+      if (hint > lo) lo = hint;
+      // chunk c qualifies when its position holds an older chunk or it starts at or before t;
+      // forward from the previous chunk (usually one or two steps), else a binary search
+      auto qualifies = [&](unsigned int x) {
+        const Chunk& m = A.chunks[x % kChunkRing];
+        return vload(&m.idx) != x || vload(&m.start_tile) <= t;
+      };
+      if (hi - lo <= 8u) {
+        while (lo + 1u < hi && qualifies(lo + 1u)) ++lo;
+      } else {
+        unsigned int top = hi;
+        while (top - lo > 1u) {   // invariant: chunk lo qualifies, chunk top does not
+          const unsigned int mid = lo + (top - lo) / 2u;
+          if (qualifies(mid)) lo = mid;
+          else top = mid;
+        }
       }
       c = lo;
     }
     c = __shfl_sync(0xFFFFFFFFu, c, 0);
+    hint = c;
     Chunk* ch = A.chunks + (c % kChunkRing);
     const unsigned int k = (unsigned int)(t - vload(&ch->start_tile));
     const unsigned int tiles = vload(&ch->tiles), si = vload(&ch->slot);
@@ -663,8 +704,9 @@ __device__ void worker(const LoopArgs& A) {
     const bool scan = vload(&R->scan) != 0u;
     const unsigned int rec0 = clo + 32u * k;
     const unsigned int rec_end = rec0 + 32u < chi ? rec0 + 32u : chi;
-    serve_tile(A, S, si, scan, vload(&R->sigma), vload(&R->cap), vload(&R->off), rec0, rec_end);
-    __threadfence();
+    serve_tile(A, S, stage, si, scan, vload(&R->sigma), vload(&R->cap), vload(&R->off), rec0,
+               rec_end);
+    fence_acq_rel_gpu();
     __syncwarp();
     if (lane == 0u && atomicAdd(&ch->finished, 1u) == tiles - 1u) {
       if (atomicAdd(&R->chunks_done, 1u) == vload(&R->chunks_total) - 1u) complete_request(A, si);
@@ -673,12 +715,16 @@ __device__ void worker(const LoopArgs& A) {
   }
 }
 
+// Dynamic shared memory: each warp's staging area (kStageBlocks blocks x 512 B).
+constexpr unsigned int kStageBytes = kLoopWarps * kStageBlocks * kRecPay;
+
 __global__ void __launch_bounds__(kLoopThreads) k_serve_loop(const LoopArgs A) {
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
-    if (threadIdx.x == 0) scheduler(A);
+  extern __shared__ __align__(16) uint4 s_stage[];
+  if (blockIdx.x == 0 && threadIdx.x < 32) {   // warp 0's staging area holds scheduler state
+    if (threadIdx.x == 0) scheduler(A, reinterpret_cast<unsigned int*>(s_stage));
     return;
   }
-  worker(A);
+  worker(A, s_stage + (threadIdx.x >> 5) * kStageBlocks * (kRecPay / 16u));
 }
 
 uint64_t loop_now_ns() {
@@ -824,13 +870,16 @@ vbh_status vbh_serve_loop_start(vbh_serve* s, const vbh_serve_loop_config* cfg_i
   if (c.chunk_records == 0) c.chunk_records = 4096u;
   if (c.ring == 0) c.ring = 4096u;
   if (c.idle_timeout_us == 0) c.idle_timeout_us = 1000000u;
-  if (c.ctas == 0) c.ctas = (uint32_t)std::max(1, h->L.sms / 2);
+  if (c.ctas == 0) c.ctas = (uint32_t)h->L.sms;
   if (c.max_slots > kLoopMaxSlots) return fail(VBH_ERR_INVALID_ARG, "max_slots must be 1..64");
   if (c.ring < 64u || c.ring > (1u << 20) || (c.ring & (c.ring - 1u)))
     return fail(VBH_ERR_INVALID_ARG, "ring must be a power of two in [64, 2^20]");
   if (c.chunk_records > (1u << 24)) return fail(VBH_ERR_INVALID_ARG, "chunk_records too large");
   int occ = 0;
-  VBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve_loop, kLoopThreads, 0));
+  VBH_CUDA(cudaFuncSetAttribute(k_serve_loop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kStageBytes));
+  VBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve_loop, kLoopThreads,
+                                                         kStageBytes));
   if (c.ctas > (uint32_t)(occ * h->L.sms))
     return fail(VBH_ERR_INVALID_ARG, "ctas above what can be resident at once");
   VBH_CUDA(cudaStreamSynchronize(h->stream));
@@ -863,7 +912,9 @@ vbh_status vbh_serve_loop_start(vbh_serve* s, const vbh_serve_loop_config* cfg_i
   LOOP_CUDA(host_mapped(&L->done_ring, c.ring));
   LOOP_CUDA(host_mapped(&L->hin, 1));
   LOOP_CUDA(host_mapped(&L->hout, 1));
-  LOOP_CUDA(cudaMemsetAsync(L->d, 0, sizeof(LoopDev), L->stream));
+  LoopDev init{};
+  init.free_mask = c.max_slots >= 64u ? ~0ull : ((1ull << c.max_slots) - 1ull);
+  LOOP_CUDA(cudaMemcpyAsync(L->d, &init, sizeof init, cudaMemcpyHostToDevice, L->stream));
   LOOP_CUDA(cudaMemsetAsync(L->slots, 0, sizeof(ReqSlot) * kLoopMaxSlots, L->stream));
   LOOP_CUDA(cudaMemsetAsync(L->chunks, 0xFF, sizeof(Chunk) * kChunkRing, L->stream));
   LOOP_CUDA(cudaMemsetAsync(L->regions, 0, sizeof(Region) * kRegionRing, L->stream));
@@ -901,7 +952,7 @@ vbh_status vbh_serve_loop_start(vbh_serve* s, const vbh_serve_loop_config* cfg_i
   L->alive();
   void* args[] = {&A};
   LOOP_CUDA(cudaLaunchCooperativeKernel((const void*)k_serve_loop, dim3(c.ctas),
-                                        dim3(kLoopThreads), args, 0, L->stream));
+                                        dim3(kLoopThreads), args, kStageBytes, L->stream));
 #undef LOOP_CUDA
   L->launched = true;
   h->launches += 1;
@@ -1062,7 +1113,7 @@ vbh_status vbh_serve_loop_stats_read(vbh_serve_loop* L, vbh_serve_loop_stats* ou
   out->chunks = D.chunks;
   out->rounds = D.rounds;
   out->deferred_memory = D.deferred;
-  out->bytes_in_use = D.a_head - D.a_tail;
+  out->bytes_in_use = D.a_in_use;
   out->bytes_peak = D.bytes_peak;
   out->max_active = D.max_active;
   out->status = L->exited() ? L->dev_status() : 0u;

@@ -226,8 +226,10 @@ def test_erase_beside_an_empty_slot_leaves_no_tombstone():
     check_contents(hm2, om2)
 
 
-@pytest.mark.parametrize("lf", [0.5, 0.7, 0.9])
+@pytest.mark.parametrize("lf", [0.5, 0.7, 0.84, 0.9])
 def test_load_factor_mixed_and_rebuild(lf):
+    """Mixed batches on a small table prefilled to load factor lf (long probe chains at the
+    higher loads), a rebuild in the middle."""
     rng = np.random.default_rng(int(lf * 10))
     n_buckets = 1 << 12
     cap = n_buckets * 4
@@ -277,12 +279,13 @@ def test_voxel_block_map_pool_indices():
     assert sorted(rg4.tolist()) == sorted(rg3.tolist())
 
 
-def test_full_size_table_lf07_batch_2e20():
-    """2^22 buckets x 4 slots, prefilled to load factor 0.7 with uniform keys in [-2^20, 2^20)^3,
+@pytest.mark.parametrize("lf", [0.7, 0.9])
+def test_full_size_table_batch_2e20(lf):
+    """2^22 buckets x 4 slots, prefilled to load factor lf with uniform keys in [-2^20, 2^20)^3,
     then a 2^20-op batch (50 % find half hits, 30 % insert of absent keys, 20 % erase)."""
     n_buckets = 1 << 22
     cap = n_buckets * 4
-    n_pre = int(0.7 * cap)
+    n_pre = int(lf * cap)
     rng = np.random.default_rng(1805)
     pool = synth.random_hash_keys(n_pre + (1 << 20), seed=1805)
     pre, fresh = pool[:n_pre], pool[n_pre:]
