@@ -323,6 +323,17 @@ struct FrameCtl {
 };
 
 #ifdef __CUDACC__
+// Copy the per-call frame parameters into shared memory (one word per thread).
+__device__ __forceinline__ void load_frame_params(FrameParams& dst, const FrameCtl* ctl) {
+  constexpr int kWords = sizeof(FrameParams) / 4;
+  static_assert(kWords <= 128, "FrameParams larger than one CTA's copy");
+  if (threadIdx.x < kWords)
+    reinterpret_cast<int*>(&dst)[threadIdx.x] = reinterpret_cast<const int*>(&ctl->fp)[threadIdx.x];
+  __syncthreads();
+}
+#endif  // __CUDACC__
+
+#ifdef __CUDACC__
 // Block k in view of the frame's pose (its bounding sphere, centre (8k + 3.5) s and radius
 // fl(7 s), is not outside the frustum): camera coordinates of the centre by the voxel
 // projection chain, the four side planes fx p_x + cxh p_z >= 0, (W - cxh) p_z - fx p_x >= 0
