@@ -391,6 +391,9 @@ vbh_status vbh_set_stream(vbh_handle* h, void* cuda_stream) {
   return VBH_OK;
 }
 
+// Plain-map batches up to this size run as one cooperative launch (latency-bound otherwise).
+constexpr uint32_t kFusedBatchMax = 1u << 17;
+
 vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* keys3_dev,
                           const uint32_t* vals_dev, uint32_t* results_dev, uint8_t* status_dev,
                           uint32_t n) {
@@ -422,14 +425,23 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   h->blists.n = h->cnt->op_lists[h->batch_parity];
   h->blists.n_next = h->cnt->op_lists[h->batch_parity ^ 1u];
   h->batch_parity ^= 1u;
-  launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n, h->blists);
-  launch_hash_insert(h->L, t, pool, h->cnt, h->blists.ins_key,
-                     h->blists.n + 1, vals_dev, results_dev, status_dev, n,
-                     h->blists.ins_idx);
-  launch_hash_insert_finish(h->L, t, pool, h->cnt, h->blists.n + 1, results_dev, status_dev,
-                            n, nullptr, nullptr, nullptr, nullptr, nullptr, h->blists.ins_idx);
-  launch_hash_erase(h->L, t, pool, h->cnt, results_dev, status_dev, n, h->blists);
-  h->launches += 5;
+  if (h->cfg.max_blocks == 0 && n <= kFusedBatchMax) {
+    // a small batch of a plain map: its five phases in one cooperative launch
+    VBH_CUDA(launch_hash_batch_fused(h->L, t, pool, h->cnt, ops_dev, keys3_dev, vals_dev,
+                                     results_dev, status_dev, n, h->blists));
+    h->launches += 1;
+  } else {
+    launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n,
+                     h->blists);
+    launch_hash_insert(h->L, t, pool, h->cnt, h->blists.ins_key,
+                       h->blists.n + 1, vals_dev, results_dev, status_dev, n,
+                       h->blists.ins_idx);
+    launch_hash_insert_finish(h->L, t, pool, h->cnt, h->blists.n + 1, results_dev, status_dev,
+                              n, nullptr, nullptr, nullptr, nullptr, nullptr,
+                              h->blists.ins_idx);
+    launch_hash_erase(h->L, t, pool, h->cnt, results_dev, status_dev, n, h->blists);
+    h->launches += 5;
+  }
   h->stage_end();
   st = check_launch(h, "vbh_hash_batch");
   snapshot_counters(h);

@@ -104,12 +104,13 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
 // 2^20-op batch is one round of the grid.
 constexpr int kPrepOps = 4;
 
-__global__ void __launch_bounds__(kThreads, 8) k_batch_prep(DevCounters* cnt,
-                                                         const unsigned char* ops,
-                                                         const int* keys3, unsigned int* res,
-                                                         unsigned char* st, unsigned int n,
-                                                         BatchLists lists) {
-  __shared__ unsigned int s_warp[kThreads / 32], s_base[3];
+// Each phase of a batch is a device function: its own kernel launches it, and so does the
+// fused small-batch kernel (k_batch_fused), which separates the phases by grid barriers instead
+// of kernel boundaries.  Data another phase wrote in the same launch is read through L2.
+__device__ __forceinline__ void prep_phase(DevCounters* cnt, const unsigned char* ops,
+                                           const int* keys3, unsigned int* res,
+                                           unsigned char* st, unsigned int n, BatchLists lists,
+                                           unsigned int* s_warp, unsigned int* s_base) {
   if (blockIdx.x == 0 && threadIdx.x < 3u) {
     lists.n_next[threadIdx.x] = 0u;   // the previous batch, which used them, has finished
     if (threadIdx.x == 0) cnt->n_exists = 0;   // the batch's insert phase follows
@@ -176,40 +177,61 @@ __global__ void __launch_bounds__(kThreads, 8) k_batch_prep(DevCounters* cnt,
   }
 }
 
+__global__ void __launch_bounds__(kThreads, 8) k_batch_prep(DevCounters* cnt,
+                                                         const unsigned char* ops,
+                                                         const int* keys3, unsigned int* res,
+                                                         unsigned char* st, unsigned int n,
+                                                         BatchLists lists) {
+  __shared__ unsigned int s_warp[kThreads / 32], s_base[3];
+  prep_phase(cnt, ops, keys3, res, st, n, lists, s_warp, s_base);
+}
+
 // --------------------------------------------------------------------------------- find phase
 // The batch's finds (list from k_batch_prep, *count_dev entries, capped at n): read-only walks.
+// kReadOnly: the table is read through the non-coherent path (a find-only launch); a fused
+// launch reads it through L2, where the earlier phases' writes are.
+template <bool kReadOnly>
+__device__ __forceinline__ void find_phase(const TableView& t, const unsigned long long* fkeys,
+                                           const unsigned int* fidx,
+                                           const unsigned int* count_dev, unsigned int* res,
+                                           unsigned char* st, unsigned int n_cap) {
+  const unsigned int n = min(__ldcg(count_dev), n_cap);
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long key = __ldcg(fkeys + i);
+    const unsigned int oi = __ldcg(fidx + i);
+    unsigned int val;
+    const bool hit = thread_find<kReadOnly>(t, key, &val) != kNone;
+    res[oi] = hit ? val : kNone;
+    st[oi] = hit ? kStFound : kStNotFound;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_find(TableView t, const unsigned long long* fkeys,
                                                    const unsigned int* fidx,
                                                    const unsigned int* count_dev,
                                                    unsigned int* res, unsigned char* st,
                                                    unsigned int n_cap) {
-  const unsigned int n = min(*count_dev, n_cap);
-  const unsigned int stride = gridDim.x * blockDim.x;
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const unsigned long long key = fkeys[i];
-    const unsigned int oi = fidx[i];
-    unsigned int val;
-    const bool hit = thread_find<true>(t, key, &val) != kNone;
-    res[oi] = hit ? val : kNone;
-    st[oi] = hit ? kStFound : kStNotFound;
-  }
+  find_phase<true>(t, fkeys, fidx, count_dev, res, st, n_cap);
 }
 
 // ------------------------------------------------------------------------------- insert phase
 // A list of packed keys, all inserts (a batch's insert list, or a frame's candidate blocks),
 // *count_dev entries capped at n_cap (n_cap itself without count_dev); idx (optional) maps list
 // entry i to the op whose value, result and status it carries.
-__global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
-                                                     DevCounters* cnt,
-                                                     const unsigned long long* pkeys,
-                                                     const unsigned int* count_dev,
-                                                     const unsigned int* vals, unsigned int* res,
-                                                     unsigned char* st, unsigned int n_cap,
-                                                     const unsigned int* idx) {
-  __shared__ unsigned int s_live, s_from_empty, s_from_tomb, s_err;
+__device__ __forceinline__ void insert_phase(const TableView& t, const PoolView& pool,
+                                             DevCounters* cnt, const unsigned long long* pkeys,
+                                             const unsigned int* count_dev,
+                                             const unsigned int* vals, unsigned int* res,
+                                             unsigned char* st, unsigned int n_cap,
+                                             const unsigned int* idx, unsigned int* sh) {
+  unsigned int& s_live = sh[0];
+  unsigned int& s_from_empty = sh[1];
+  unsigned int& s_from_tomb = sh[2];
+  unsigned int& s_err = sh[3];
   if (threadIdx.x == 0) { s_live = 0; s_from_empty = 0; s_from_tomb = 0; s_err = 0; }
   __syncthreads();
-  const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
+  const unsigned int n = count_dev ? min(__ldcg(count_dev), n_cap) : n_cap;
   const unsigned int free_top = pool.max_blocks ? (unsigned)max(cnt->free_top, 0) : 0u;
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int stride = gridDim.x * blockDim.x;
@@ -221,8 +243,8 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
     bool doit = false;
     unsigned int oi = i;   // the op's index in the batch (results, statuses, values)
     if (i < n) {
-      key = pkeys[i];
-      if (idx) oi = idx[i];
+      key = __ldcg(pkeys + i);
+      if (idx) oi = __ldcg(idx + i);
       doit = true;
     }
     int outcome = 0;
@@ -274,28 +296,38 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_insert(TableView t, PoolView pool,
+                                                     DevCounters* cnt,
+                                                     const unsigned long long* pkeys,
+                                                     const unsigned int* count_dev,
+                                                     const unsigned int* vals, unsigned int* res,
+                                                     unsigned char* st, unsigned int n_cap,
+                                                     const unsigned int* idx) {
+  __shared__ unsigned int sh[4];
+  insert_phase(t, pool, cnt, pkeys, count_dev, vals, res, st, n_cap, idx, sh);
+}
+
 // Resolve every insert's value once all claims are visible (the inserts are the first
 // *count_dev ops, capped at n_cap, or the ops idx lists); undo claims whose pool pop failed;
 // optionally append each distinct pool index to a frame's touched list (epoch de-duplication).
-__global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolView pool,
-                                                            DevCounters* cnt,
-                                                            const unsigned int* count_dev,
-                                                            unsigned int* res, unsigned char* st,
-                                                            unsigned int n_cap,
-                                                            unsigned int* touched,
-                                                            unsigned long long* tkey,
-                                                            float2* tdepth,
-                                                            unsigned int* n_touched,
-                                                            const FrameCtl* ctl,
-                                                            const unsigned int* idx) {
+__device__ __forceinline__ void finish_phase(const TableView& t, const PoolView& pool,
+                                             DevCounters* cnt, const unsigned int* count_dev,
+                                             unsigned int* res, unsigned char* st,
+                                             unsigned int n_cap, unsigned int* touched,
+                                             unsigned long long* tkey, float2* tdepth,
+                                             unsigned int* n_touched, const FrameCtl* ctl,
+                                             const unsigned int* idx, unsigned int* sh) {
   // A plain map's winners wrote their final results; only inserts that met their key (whose
   // value another thread may still have been writing) are left, and usually there are none.
+  // (Every thread of the grid reads the same count, so a CTA leaves as a whole.)
   const bool plain = pool.max_blocks == 0;
   if (plain && !touched && *reinterpret_cast<volatile unsigned int*>(&cnt->n_exists) == 0) return;
-  __shared__ unsigned int s_undo, s_new, s_err;
+  unsigned int& s_undo = sh[0];
+  unsigned int& s_new = sh[1];
+  unsigned int& s_err = sh[2];
   if (threadIdx.x == 0) { s_undo = 0; s_new = 0; s_err = 0; }
   __syncthreads();
-  const unsigned int n = count_dev ? min(*count_dev, n_cap) : n_cap;
+  const unsigned int n = count_dev ? min(__ldcg(count_dev), n_cap) : n_cap;
   const unsigned int epoch = ctl ? ctl->epoch_touch : 0u;
   if (blockIdx.x == 0 && threadIdx.x == 0 && pool.max_blocks) {
     int popped = (int)cnt->n_popped;
@@ -309,11 +341,11 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
     unsigned int p = kNone;
     bool fresh_win = false;
     if (j < n) {
-      const unsigned int i = idx ? idx[j] : j;   // the insert's index in the batch
-      unsigned char s = st[i];
+      const unsigned int i = idx ? __ldcg(idx + j) : j;   // the insert's index in the batch
+      unsigned char s = __ldcg(st + i);
       if (s == kStExists || (s == kStInserted && !plain)) {
-        unsigned int pos = res[i];
-        unsigned int v = t.slots[pos].val;
+        unsigned int pos = __ldcg(res + i);
+        unsigned int v = __ldcg(&t.slots[pos].val);
         if (!plain && v == kPoolFail) {
           if (s == kStInserted) {
             t.slots[pos].key = kTomb;
@@ -359,19 +391,36 @@ __global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolVie
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_insert_finish(TableView t, PoolView pool,
+                                                            DevCounters* cnt,
+                                                            const unsigned int* count_dev,
+                                                            unsigned int* res, unsigned char* st,
+                                                            unsigned int n_cap,
+                                                            unsigned int* touched,
+                                                            unsigned long long* tkey,
+                                                            float2* tdepth,
+                                                            unsigned int* n_touched,
+                                                            const FrameCtl* ctl,
+                                                            const unsigned int* idx) {
+  __shared__ unsigned int sh[3];
+  finish_phase(t, pool, cnt, count_dev, res, st, n_cap, touched, tkey, tdepth, n_touched, ctl,
+               idx, sh);
+}
+
 // -------------------------------------------------------------------------------- erase phase
 // The batch's erase list (packed keys ekeys and op indices eidx from k_batch_prep, *count_dev
 // entries, capped at n_cap).
-__global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, DevCounters* cnt,
-                                                    const unsigned long long* ekeys,
-                                                    const unsigned int* eidx,
-                                                    const unsigned int* count_dev,
-                                                    unsigned int* res, unsigned char* st,
-                                                    unsigned int n_cap) {
-  __shared__ unsigned int s_erased, s_emptied;
+__device__ __forceinline__ void erase_phase(const TableView& t, const PoolView& pool,
+                                            DevCounters* cnt, const unsigned long long* ekeys,
+                                            const unsigned int* eidx,
+                                            const unsigned int* count_dev, unsigned int* res,
+                                            unsigned char* st, unsigned int n_cap,
+                                            unsigned int* sh) {
+  unsigned int& s_erased = sh[0];
+  unsigned int& s_emptied = sh[1];
   if (threadIdx.x == 0) { s_erased = 0; s_emptied = 0; }
   __syncthreads();
-  const unsigned int n = min(*count_dev, n_cap);
+  const unsigned int n = min(__ldcg(count_dev), n_cap);
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int stride = gridDim.x * blockDim.x;
   for (unsigned int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n;
@@ -381,8 +430,8 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
     unsigned int oi = 0;   // the op's index in the batch
     const bool doit = i < n;
     if (doit) {
-      key = ekeys[i];
-      oi = eidx[i];
+      key = __ldcg(ekeys + i);
+      oi = __ldcg(eidx + i);
     }
     int how = 0;
     unsigned int val = kNone;
@@ -418,6 +467,71 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
     if (s_emptied) atomicAdd(&cnt->n_empty, s_emptied);
     if (s_erased > s_emptied) atomicAdd(&cnt->n_tomb, s_erased - s_emptied);
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, DevCounters* cnt,
+                                                    const unsigned long long* ekeys,
+                                                    const unsigned int* eidx,
+                                                    const unsigned int* count_dev,
+                                                    unsigned int* res, unsigned char* st,
+                                                    unsigned int n_cap) {
+  __shared__ unsigned int sh[2];
+  erase_phase(t, pool, cnt, ekeys, eidx, count_dev, res, st, n_cap, sh);
+}
+
+// ------------------------------------------------------------------------- fused small batch
+// A small batch is latency-bound: its five phase launches (prep, finds, inserts, insert values,
+// erases) each cost a launch and a drain of the GPU.  k_batch_fused runs the same phases in one
+// cooperative launch (every CTA resident), separated by grid barriers; the phases, their order
+// and their results are those of the separate launches.  A barrier waits at most ~1 s (GPU
+// global timer); one that gives up raises the sticky timeout flag and lets its CTA go on.
+__device__ __forceinline__ void grid_barrier(DevCounters* cnt) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &cnt->gbar_gen;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(&cnt->gbar_arrive, 1u) == gridDim.x - 1u) {
+      cnt->gbar_arrive = 0u;
+      __threadfence();
+      atomicAdd(&cnt->gbar_gen, 1u);
+    } else {
+      unsigned long long t0;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      for (;;) {
+        if (*gen != g) break;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull) {
+          atomicOr(&cnt->err, kErrTimeout);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_batch_fused(TableView t, PoolView pool,
+                                                          DevCounters* cnt,
+                                                          const unsigned char* ops,
+                                                          const int* keys3,
+                                                          const unsigned int* vals,
+                                                          unsigned int* res, unsigned char* st,
+                                                          unsigned int n, BatchLists lists) {
+  __shared__ unsigned int s_warp[kThreads / 32], s_base[3], sh[4];
+  prep_phase(cnt, ops, keys3, res, st, n, lists, s_warp, s_base);
+  grid_barrier(cnt);
+  find_phase<false>(t, lists.find_key, lists.find_idx, lists.n, res, st, n);
+  grid_barrier(cnt);
+  insert_phase(t, pool, cnt, lists.ins_key, lists.n + 1, vals, res, st, n, lists.ins_idx, sh);
+  grid_barrier(cnt);
+  finish_phase(t, pool, cnt, lists.n + 1, res, st, n, nullptr, nullptr, nullptr, nullptr,
+               nullptr, lists.ins_idx, sh);
+  grid_barrier(cnt);
+  erase_phase(t, pool, cnt, lists.era_key, lists.era_idx, lists.n + 2, res, st, n, sh);
 }
 
 // ------------------------------------------------------------------------------------ rebuild
@@ -568,6 +682,21 @@ void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters*
   VBH_GRID(k_erase, kThreads);
   k_erase<<<fit_grid(grid_k_erase, n), kThreads, 0, L.stream>>>(
       t, pool, cnt, lists.era_key, lists.era_idx, lists.n + 2, res, st, n);
+}
+int fused_batch_grid(const Launch& L) {
+  static const int grid = persistent_grid(k_batch_fused, kThreads, L.sms);
+  return grid;
+}
+cudaError_t launch_hash_batch_fused(const Launch& L, TableView t, PoolView pool,
+                                    DevCounters* cnt, const unsigned char* ops,
+                                    const int* keys3, const unsigned int* vals,
+                                    unsigned int* res, unsigned char* st, unsigned int n,
+                                    BatchLists lists) {
+  // one thread per op in the probe phases (the prep pass then takes fewer ops per thread)
+  const unsigned int grid = fit_grid(fused_batch_grid(L), n);
+  void* args[] = {&t, &pool, &cnt, &ops, &keys3, &vals, &res, &st, &n, &lists};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_fused, dim3(grid), dim3(kThreads),
+                                     args, 0, L.stream);
 }
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt) {

@@ -72,6 +72,7 @@ struct DevCounters {
   unsigned long long tot_new;
   unsigned long long tot_written;
   unsigned long long tot_frames;
+  unsigned int gbar_arrive, gbar_gen;   // grid barrier of the fused small-batch kernel
 };
 
 struct TableView {
@@ -419,6 +420,13 @@ void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevC
 // The batch's erases, from the erase list its first pass compacted.
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        unsigned int* res, unsigned char* st, unsigned int n, BatchLists lists);
+// The whole batch (prep, finds, inserts, insert values, erases) in one cooperative launch with
+// grid barriers between the phases: for small batches of plain maps.
+cudaError_t launch_hash_batch_fused(const Launch& L, TableView t, PoolView pool,
+                                    DevCounters* cnt, const unsigned char* ops,
+                                    const int* keys3, const unsigned int* vals,
+                                    unsigned int* res, unsigned char* st, unsigned int n,
+                                    BatchLists lists);
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt);
 void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,
