@@ -135,7 +135,10 @@ vbh_status vbh_set_stream(vbh_handle* h, void* cuda_stream);
  * weight 0) and an erase returns it.  n may be 0.  n > max_batch -> VBH_ERR_INVALID_ARG.
  * The call is asynchronous on the handle's stream, except that the first batch larger than any
  * before it synchronises and allocates the handle's op lists (36 B per op: the batch's finds,
- * inserts and erases as op index + packed key); VBH_ERR_CUDA if that allocation fails. */
+ * inserts and erases as op index + packed key); VBH_ERR_CUDA if that allocation fails.
+ * A plain map's batch of at most 2^17 ops runs its phases in one cooperative launch separated
+ * by grid barriers; a barrier that waits longer than ~1 s gives up and raises error flag bit3
+ * (the batch's results are then not to be trusted). */
 vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* keys3_dev,
                           const uint32_t* vals_dev, uint32_t* results_dev, uint8_t* status_dev,
                           uint32_t n);

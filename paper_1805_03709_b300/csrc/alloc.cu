@@ -9,9 +9,17 @@ namespace vbh {
 
 namespace {
 
-constexpr int kTile = 16;            // 16 x 16 pixel tiles, one thread per pixel
-constexpr int kTileThreads = kTile * kTile;
-constexpr int kTileSet = 1024;       // shared-memory key set per tile (power of two)
+#ifndef VBH_ALLOC_TILE_X
+#define VBH_ALLOC_TILE_X 16
+#endif
+#ifndef VBH_ALLOC_TILE_Y
+#define VBH_ALLOC_TILE_Y 16
+#endif
+constexpr int kTileX = VBH_ALLOC_TILE_X;   // pixel tiles of kTileX x kTileY, one thread per pixel
+constexpr int kTileY = VBH_ALLOC_TILE_Y;
+constexpr int kTileThreads = kTileX * kTileY;
+constexpr int kTileSet = 4 * kTileThreads;   // shared-memory key set per tile (power of two)
+static_assert((kTileSet & (kTileSet - 1)) == 0 && kTileThreads % 32 == 0, "tile shape");
 // Band allocation: every valid pixel's samples -> block keys -> per-tile distinct set in shared
 // memory -> appended to the candidate list (the global de-duplication is the hash insert).
 // Every pixel's metric depth fl(raw ds) also goes to `dimg` for the fusion kernel, with invalid
@@ -29,12 +37,12 @@ __global__ void __launch_bounds__(kTileThreads) k_alloc_keys(const FrameCtl* ctl
   load_frame_params(fp, ctl);
   for (int i = threadIdx.x; i < kTileSet; i += kTileThreads) set[i] = kEmpty;
   __syncthreads();
-  const int tiles_x = (fp.width + kTile - 1) / kTile;
-  const int tiles_y = (fp.height + kTile - 1) / kTile;
+  const int tiles_x = (fp.width + kTileX - 1) / kTileX;
+  const int tiles_y = (fp.height + kTileY - 1) / kTileY;
   const int n_tiles = tiles_x * tiles_y;
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int pu = (tile % tiles_x) * kTile + (threadIdx.x % kTile);
-    const int pv = (tile / tiles_x) * kTile + (threadIdx.x / kTile);
+    const int pu = (tile % tiles_x) * kTileX + (threadIdx.x % kTileX);
+    const int pv = (tile / tiles_x) * kTileY + (threadIdx.x / kTileX);
     if (pu < fp.width && pv < fp.height) {
       const unsigned short raw = __ldg(fp.depth + (size_t)pv * fp.width + pu);
       const float d = __fmul_rn((float)raw, fp.ds);
@@ -143,7 +151,7 @@ void launch_alloc_keys(const Launch& L, const FrameCtl* ctl, int width, int heig
                        unsigned long long* cand, unsigned int cap, DevCounters* cnt,
                        float* dimg) {
   static const int grid = persistent_grid(k_alloc_keys, kTileThreads, L.sms);
-  const int tiles = ((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
+  const int tiles = ((width + kTileX - 1) / kTileX) * ((height + kTileY - 1) / kTileY);
   k_alloc_keys<<<tiles < grid ? tiles : grid, kTileThreads, 0, L.stream>>>(ctl, cand, cap, cnt,
                                                                           dimg);
 }

@@ -484,14 +484,16 @@ __device__ void scheduler(const LoopArgs& A, unsigned int* sm) {
         if (!stop_adm) {
           const unsigned int active = A.n_slots - __popcll(free);
           const unsigned int outstanding = vload(&d->done_count) - done_read;
-          if (q.client >= A.n_clients) {   // never written by the library's host side
+          if (outstanding + active + 1u > A.ring_mask + 1u) {
+            stop_adm = true;   // no completion-ring room for one more
+          } else if (q.client >= A.n_clients) {   // never written by the library's host side
             publish_done(A, q.id, q.client, 0u, VBH_SERVE_ERR_VERSION, 0u, 0u, 0xFFFFFFFFu, 0u,
                          0ull);
             keep = false;
           } else if (vload(&A.client_busy[q.client])) {
             head = false;   // one request per client at a time, in arrival order
-          } else if (!free || outstanding + active + 1u > A.ring_mask + 1u) {
-            stop_adm = true;   // no slot, or no completion-ring room for one more
+          } else if (!free) {
+            stop_adm = true;   // no free slot
           } else {
             const unsigned int v = vload(&A.client_v[q.client]);
             const unsigned int margin = A.log_cap / 2u;   // records appended while one runs
