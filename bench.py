@@ -596,9 +596,9 @@ def main():
     if not args.no_serve and rank == 0:
         serve_pt = serve_point(torch, cam, D, poses, peak, args.serve_seconds, reps=5)
         # the same clients asking in step with the frames: a burst of 64 requests with work
-        # after every frame, so that batching has many concurrent requests to merge
+        # within 50 us after every frame, so that batching has many concurrent requests to merge
         burst = serve_point(torch, cam, D, poses, peak, 2.0, reps=5, saturated=False,
-                            burst_ms=1.0)
+                            burst_ms=0.05)
         serve_pt["burst_load"] = {k: burst[k] for k in ("arrivals", "duration_s", "requests",
                                                         "device_loop", "batched", "unbatched")}
 
