@@ -1,5 +1,5 @@
-// GPU hash map of packed int3 block keys: bucketed (4 x 16 B slots per 64 B bucket), linear
-// probing over buckets, one thread per operation reading whole buckets.
+// GPU hash map of packed int3 block keys: bucketed (4 x 16 B slots per 64 B bucket), double
+// hashing over buckets (probe_step), one thread per operation reading whole buckets.
 //
 // Guarantees (Sec. 5: concurrent retrieval, insertion and removal succeed and keys stay unique,
 // which the paper obtains with per-entry locks and an excess list; here with CAS claims):
@@ -10,7 +10,8 @@
 //     launch covers only its own ops.
 //   * A live key never moves (the paper's invariant that entry positions are preserved), so a
 //     find needs no lock: it walks the buckets from the key's home bucket until it meets the
-//     key or a bucket with a never-used (EMPTY) slot.  Tombstones keep chains intact, and an
+//     key or a bucket with a never-used (EMPTY) slot.  Any fixed probe sequence per key keeps
+//     these arguments; double hashing keeps it short at high loads.  Tombstones keep chains intact, and an
 //     erase makes a slot EMPTY only where a find would stop anyway.
 //   * A plain map's batch: the winner of an insert writes its value and final result at once;
 //     inserts that met their key take the value in a follow-up launch (skipped when none did).
@@ -35,6 +36,7 @@ constexpr int kInserted = 1, kExists = 2, kFull = 3;
 __device__ int thread_insert(const TableView& t, unsigned long long key, unsigned int* pos_out,
                              unsigned long long* observed_out) {
   unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
+  const unsigned int step = probe_step(key);
   unsigned int first_free = kNone, held = kNone;
   ulonglong2 s[4];
   // pass 1: the whole chain, to be sure the key is absent
@@ -55,7 +57,7 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
     }
     if (first_free == kNone && f >= 0) first_free = 4u * b + f;
     if (empty) break;
-    b = (b + 1u) & t.bmask;
+    b = (b + step) & t.bmask;
   }
   if (first_free == kNone) return kFull;
   // pass 2: claim in probe order starting at the first free slot.  The bucket pass 1 ended on
@@ -76,7 +78,7 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
       return kExists;
     }
     if (l < 0) {
-      b = (b + 1u) & t.bmask;
+      b = (b + step) & t.bmask;
       ++steps;
       continue;
     }
@@ -547,8 +549,9 @@ __global__ void __launch_bounds__(kThreads) k_rebuild(TableView t, const Slot* s
     ulonglong2 s = __ldg(reinterpret_cast<const ulonglong2*>(&shadow[i]));
     if (s.x >= kTomb) continue;
     unsigned int b = home_bucket(s.x, t.bmask, t.hash_fn);
+    const unsigned int step = probe_step(s.x);
     bool done = false;
-    for (unsigned int probe = 0; probe <= t.bmask && !done; ++probe, b = (b + 1u) & t.bmask) {
+    for (unsigned int probe = 0; probe <= t.bmask && !done; ++probe, b = (b + step) & t.bmask) {
       for (unsigned int l = 0; l < 4u && !done; ++l) {
         Slot* dst = &t.slots[4u * b + l];
         if (__ldcg(&dst->key) != kEmpty) continue;

@@ -190,7 +190,8 @@ __device__ __forceinline__ unsigned int rem_latest_cg(const ServeLog& S, unsigne
 // Find through L2 (the table changes under the loop; a live entry never moves while it runs).
 __device__ __forceinline__ bool live_cg(const TableView& t, unsigned long long key) {
   unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
-  for (unsigned int probe = 0; probe <= t.bmask; ++probe, b = (b + 1u) & t.bmask) {
+  const unsigned int step = probe_step(key);
+  for (unsigned int probe = 0; probe <= t.bmask; ++probe, b = (b + step) & t.bmask) {
     bool empty = false;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
