@@ -791,7 +791,7 @@ def hash_clustered_point(torch, dev, flush, n=1 << 20, n_batches=5, n_warm=1):
 def tri_point(torch, vol, peak, reps=5):
     """Whole-model extraction (every live block's MC indices) and its triangulation with
     midpoint vertices -- what a (re)connecting exploration client receives and meshes -- on the
-    volume the timed loop left, CUDA events around each launch."""
+    volume the timed loop left, CUDA events around each launch (enqueued behind a GPU delay)."""
     from paper_1805_03709_b300 import vbh as V
     from paper_1805_03709_b300.volume import McStream
     s = McStream.allocate(MAX_BLOCKS, MAX_BLOCKS * 96)
@@ -802,7 +802,8 @@ def tri_point(torch, vol, peak, reps=5):
     ext, tri = [], []
     for r in range(reps + 1):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record()
+        torch.cuda._sleep(2_000_000)   # ~1 ms of GPU delay: both calls are enqueued before the
+        e[0].record()                  # GPU reaches them, so the events time device work only
         V.vbh_extract_mc_indices(vol.h, sel, s.c_struct())
         e[1].record()
         V.vbh_mc_triangulate(s.c_struct(), VOXEL, tris, cap, n,

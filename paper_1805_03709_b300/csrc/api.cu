@@ -392,7 +392,7 @@ vbh_status vbh_set_stream(vbh_handle* h, void* cuda_stream) {
 }
 
 // Plain-map batches up to this size run as one cooperative launch (latency-bound otherwise).
-constexpr uint32_t kFusedBatchMax = 1u << 17;
+constexpr uint32_t kSmallBatchMax = 1u << 17;
 
 vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* keys3_dev,
                           const uint32_t* vals_dev, uint32_t* results_dev, uint8_t* status_dev,
@@ -425,10 +425,11 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   h->blists.n = h->cnt->op_lists[h->batch_parity];
   h->blists.n_next = h->cnt->op_lists[h->batch_parity ^ 1u];
   h->batch_parity ^= 1u;
-  if (h->cfg.max_blocks == 0 && n <= kFusedBatchMax) {
-    // a small batch of a plain map: its five phases in one cooperative launch
-    VBH_CUDA(launch_hash_batch_fused(h->L, t, pool, h->cnt, ops_dev, keys3_dev, vals_dev,
-                                     results_dev, status_dev, n, h->blists));
+  if (h->cfg.max_blocks == 0 && n <= kSmallBatchMax &&
+      (n + 255u) / 256u <= (uint32_t)small_batch_grid(h->L)) {
+    // a small batch of a plain map: one cooperative launch, one thread per op
+    VBH_CUDA(launch_hash_batch_small(h->L, t, h->cnt, ops_dev, keys3_dev, vals_dev, results_dev,
+                                     status_dev, n, h->blists.n_next));
     h->launches += 1;
   } else {
     launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n,

@@ -106,9 +106,7 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
 // 2^20-op batch is one round of the grid.
 constexpr int kPrepOps = 4;
 
-// Each phase of a batch is a device function: its own kernel launches it, and so does the
-// fused small-batch kernel (k_batch_fused), which separates the phases by grid barriers instead
-// of kernel boundaries.  Data another phase wrote in the same launch is read through L2.
+// Each phase of a batch is a device function that its own kernel launches.
 __device__ __forceinline__ void prep_phase(DevCounters* cnt, const unsigned char* ops,
                                            const int* keys3, unsigned int* res,
                                            unsigned char* st, unsigned int n, BatchLists lists,
@@ -189,10 +187,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_batch_prep(DevCounters* cnt,
 }
 
 // --------------------------------------------------------------------------------- find phase
-// The batch's finds (list from k_batch_prep, *count_dev entries, capped at n): read-only walks.
-// kReadOnly: the table is read through the non-coherent path (a find-only launch); a fused
-// launch reads it through L2, where the earlier phases' writes are.
-template <bool kReadOnly>
+// The batch's finds (list from k_batch_prep, *count_dev entries, capped at n): read-only walks
+// through the non-coherent path (nothing writes the table during a find launch).
 __device__ __forceinline__ void find_phase(const TableView& t, const unsigned long long* fkeys,
                                            const unsigned int* fidx,
                                            const unsigned int* count_dev, unsigned int* res,
@@ -203,7 +199,7 @@ __device__ __forceinline__ void find_phase(const TableView& t, const unsigned lo
     const unsigned long long key = __ldcg(fkeys + i);
     const unsigned int oi = __ldcg(fidx + i);
     unsigned int val;
-    const bool hit = thread_find<kReadOnly>(t, key, &val) != kNone;
+    const bool hit = thread_find<true>(t, key, &val) != kNone;
     res[oi] = hit ? val : kNone;
     st[oi] = hit ? kStFound : kStNotFound;
   }
@@ -214,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_find(TableView t, const unsigned l
                                                    const unsigned int* count_dev,
                                                    unsigned int* res, unsigned char* st,
                                                    unsigned int n_cap) {
-  find_phase<true>(t, fkeys, fidx, count_dev, res, st, n_cap);
+  find_phase(t, fkeys, fidx, count_dev, res, st, n_cap);
 }
 
 // ------------------------------------------------------------------------------- insert phase
@@ -481,12 +477,18 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
   erase_phase(t, pool, cnt, ekeys, eidx, count_dev, res, st, n_cap, sh);
 }
 
-// ------------------------------------------------------------------------- fused small batch
-// A small batch is latency-bound: its five phase launches (prep, finds, inserts, insert values,
-// erases) each cost a launch and a drain of the GPU.  k_batch_fused runs the same phases in one
-// cooperative launch (every CTA resident), separated by grid barriers; the phases, their order
-// and their results are those of the separate launches.  A barrier waits at most ~1 s (GPU
-// global timer); one that gives up raises the sticky timeout flag and lets its CTA go on.
+// ------------------------------------------------------------------------- small batch
+// A small batch of a plain map is bound by the latency of its phases, not by bandwidth.
+// k_batch_small runs it in one cooperative launch (every CTA resident) with one thread per op
+// that keeps its op and key in registers, so there are no op lists, and three phases separated
+// by two grid barriers:
+//   1. every op is read and checked; the finds run (nothing writes the table yet, so they see
+//      it as the batch found it), and the inserts and erases prefetch their home bucket to L2;
+//   2. the inserts claim their slots; a winner writes its value and its final result;
+//   3. the inserts that met their key read its value (every winner wrote its value before the
+//      barrier, and an erase leaves the value field alone), and the erases run.
+// Results, statuses and counters are those of the phased launches.  A barrier waits at most
+// ~1 s (GPU global timer); one that gives up raises the sticky timeout flag and lets its CTA go.
 __device__ __forceinline__ void grid_barrier(DevCounters* cnt) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -508,7 +510,7 @@ __device__ __forceinline__ void grid_barrier(DevCounters* cnt) {
           atomicOr(&cnt->err, kErrTimeout);
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -516,24 +518,97 @@ __device__ __forceinline__ void grid_barrier(DevCounters* cnt) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch_fused(TableView t, PoolView pool,
-                                                          DevCounters* cnt,
+__global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounters* cnt,
                                                           const unsigned char* ops,
                                                           const int* keys3,
                                                           const unsigned int* vals,
                                                           unsigned int* res, unsigned char* st,
-                                                          unsigned int n, BatchLists lists) {
-  __shared__ unsigned int s_warp[kThreads / 32], s_base[3], sh[4];
-  prep_phase(cnt, ops, keys3, res, st, n, lists, s_warp, s_base);
+                                                          unsigned int n,
+                                                          unsigned int* lists_next) {
+  // inserts won, won from EMPTY, won from a tombstone, error bits; erased, erased to EMPTY
+  __shared__ unsigned int sh[6];
+  const unsigned int i = blockIdx.x * kThreads + threadIdx.x;
+  const unsigned int lane = threadIdx.x & 31u;
+  // the list counts a following phased batch uses start at zero (its predecessor zeroes them)
+  if (blockIdx.x == 0 && threadIdx.x < 3u) lists_next[threadIdx.x] = 0u;
+  if (threadIdx.x < 6u) sh[threadIdx.x] = 0u;
+  int kind = -1;   // kOpFind, kOpInsert or kOpErase
+  unsigned long long key = 0;
+  if (i < n) {
+    const unsigned char op = ops[i];
+    const int x = keys3[3u * i], y = keys3[3u * i + 1], z = keys3[3u * i + 2];
+    if (op > kOpErase || !key_ok(x, y, z)) {
+      res[i] = kNone;
+      st[i] = kStInvalid;
+    } else {
+      key = pack_key(x, y, z);
+      kind = op;
+    }
+  }
+  if (kind == kOpFind) {
+    unsigned int val;
+    const bool hit = thread_find<false>(t, key, &val) != kNone;
+    res[i] = hit ? val : kNone;
+    st[i] = hit ? kStFound : kStNotFound;
+  } else if (kind >= 0) {
+    const Slot* b = &t.slots[4u * home_bucket(key, t.bmask, t.hash_fn)];
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(b));
+  }
   grid_barrier(cnt);
-  find_phase<false>(t, lists.find_key, lists.find_idx, lists.n, res, st, n);
+
+  int outcome = 0;
+  unsigned int pos = kNone;
+  unsigned long long observed = 0;
+  if (kind == kOpInsert) {
+    outcome = thread_insert(t, key, &pos, &observed);
+    if (outcome == kInserted) {
+      const unsigned int v = vals ? vals[i] : 0u;
+      t.slots[pos].val = v;
+      res[i] = v;
+      st[i] = kStInserted;
+    } else if (outcome == kFull) {
+      res[i] = kNone;
+      st[i] = kStCapacity;
+      atomicOr(&sh[3], kErrTable);
+    }
+  }
+  const bool won = outcome == kInserted;
+  const unsigned int n_won = __popc(__ballot_sync(0xFFFFFFFFu, won));
+  const unsigned int n_emp = __popc(__ballot_sync(0xFFFFFFFFu, won && observed == kEmpty));
+  if (lane == 0 && n_won) {
+    atomicAdd(&sh[0], n_won);
+    if (n_emp) atomicAdd(&sh[1], n_emp);
+    if (n_won > n_emp) atomicAdd(&sh[2], n_won - n_emp);
+  }
   grid_barrier(cnt);
-  insert_phase(t, pool, cnt, lists.ins_key, lists.n + 1, vals, res, st, n, lists.ins_idx, sh);
-  grid_barrier(cnt);
-  finish_phase(t, pool, cnt, lists.n + 1, res, st, n, nullptr, nullptr, nullptr, nullptr,
-               nullptr, lists.ins_idx, sh);
-  grid_barrier(cnt);
-  erase_phase(t, pool, cnt, lists.era_key, lists.era_idx, lists.n + 2, res, st, n, sh);
+
+  if (outcome == kExists) {
+    res[i] = __ldcg(&t.slots[pos].val);
+    st[i] = kStExists;
+  }
+  int how = 0;
+  if (kind == kOpErase) {
+    bool bucket_empty = false;
+    unsigned int val = kNone;
+    const unsigned int p = thread_find<false>(t, key, &val, &bucket_empty);
+    if (p != kNone) how = erase_found(t, p, key, bucket_empty);
+    res[i] = how ? val : kNone;
+    st[i] = how ? kStErased : kStNotFound;
+  }
+  const unsigned int n_er = __popc(__ballot_sync(0xFFFFFFFFu, how != 0));
+  const unsigned int n_em = __popc(__ballot_sync(0xFFFFFFFFu, how == 1));
+  if (lane == 0 && n_er) {
+    atomicAdd(&sh[4], n_er);
+    if (n_em) atomicAdd(&sh[5], n_em);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int ins = sh[0], ins_e = sh[1], ins_t = sh[2], er = sh[4], er_e = sh[5];
+    if (ins != er) atomicAdd(&cnt->n_live, ins - er);   // modulo 2^32: a net change
+    if (er_e != ins_e) atomicAdd(&cnt->n_empty, er_e - ins_e);
+    if (er - er_e != ins_t) atomicAdd(&cnt->n_tomb, (er - er_e) - ins_t);
+    if (sh[3]) atomicOr(&cnt->err, sh[3]);
+  }
 }
 
 // ------------------------------------------------------------------------------------ rebuild
@@ -686,19 +761,18 @@ void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters*
   k_erase<<<fit_grid(grid_k_erase, n), kThreads, 0, L.stream>>>(
       t, pool, cnt, lists.era_key, lists.era_idx, lists.n + 2, res, st, n);
 }
-int fused_batch_grid(const Launch& L) {
-  static const int grid = persistent_grid(k_batch_fused, kThreads, L.sms);
+int small_batch_grid(const Launch& L) {
+  static const int grid = persistent_grid(k_batch_small, kThreads, L.sms);
   return grid;
 }
-cudaError_t launch_hash_batch_fused(const Launch& L, TableView t, PoolView pool,
-                                    DevCounters* cnt, const unsigned char* ops,
-                                    const int* keys3, const unsigned int* vals,
-                                    unsigned int* res, unsigned char* st, unsigned int n,
-                                    BatchLists lists) {
-  // one thread per op in the probe phases (the prep pass then takes fewer ops per thread)
-  const unsigned int grid = fit_grid(fused_batch_grid(L), n);
-  void* args[] = {&t, &pool, &cnt, &ops, &keys3, &vals, &res, &st, &n, &lists};
-  return cudaLaunchCooperativeKernel((const void*)k_batch_fused, dim3(grid), dim3(kThreads),
+cudaError_t launch_hash_batch_small(const Launch& L, TableView t, DevCounters* cnt,
+                                    const unsigned char* ops, const int* keys3,
+                                    const unsigned int* vals, unsigned int* res,
+                                    unsigned char* st, unsigned int n, unsigned int* lists_next) {
+  const unsigned int grid = (n + kThreads - 1u) / kThreads;   // one thread per op
+  if (grid == 0 || grid > (unsigned int)small_batch_grid(L)) return cudaErrorInvalidValue;
+  void* args[] = {&t, &cnt, &ops, &keys3, &vals, &res, &st, &n, &lists_next};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_small, dim3(grid), dim3(kThreads),
                                      args, 0, L.stream);
 }
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,

@@ -13,8 +13,10 @@
 //     is cut by ear clipping at the first position whose new diagonal joins two edges on no
 //     common face (a diagonal lying on a face would be shared with the neighbouring cube), each
 //     triangle in the reversed loop order so that normals point to positive TSDF.
-// The kernel: one warp per stream record, its entries' triangle counts summed per CTA round with
-// one reservation, then each entry writes its triangles (9 floats, metres).
+// The kernel: one warp per stream record.  The CTA first counts the triangles of its warps'
+// next records (up to 16 rounds) and reserves their output with one atomic per round; then each
+// warp writes its records' triangles (9 floats each, metres) with no further CTA barrier, in
+// order through a per-warp stage in shared memory, so its stores are whole consecutive runs.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -164,14 +166,17 @@ vbh_status upload_tables() {
 }
 
 constexpr int kTriThreads = 256;
+constexpr int kTriWarps = kTriThreads / 32;
+constexpr unsigned int kTriGroup = 16;   // rounds of records counted before they are written
 
 __global__ void __launch_bounds__(kTriThreads) k_mc_triangulate(
     const int* keys3, const unsigned int* offsets, const unsigned int* counts,
     const unsigned short* local, const unsigned char* index, const unsigned int* n_blocks_dev,
     unsigned int cap_blocks, unsigned int cap_entries, float half_s, float* tris,
     unsigned int cap_tris, unsigned int* n_tris) {
-  __shared__ unsigned int s_warp[kTriThreads / 32], s_base;
+  __shared__ unsigned int s_off[kTriGroup][kTriWarps];   // first triangle of each record
   __shared__ __align__(4) unsigned char s_n[256], s_e[256 * 15], s_mid[12 * 3 + 4];
+  __shared__ unsigned int s_stage[kTriWarps][32 * 5];   // <= 5 triangles per cube
   for (unsigned int i = threadIdx.x; i < 64u; i += kTriThreads)
     reinterpret_cast<unsigned int*>(s_n)[i] = reinterpret_cast<const unsigned int*>(g_tri_n)[i];
   for (unsigned int i = threadIdx.x; i < 960u; i += kTriThreads)
@@ -181,60 +186,87 @@ __global__ void __launch_bounds__(kTriThreads) k_mc_triangulate(
   __syncthreads();
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int nb = min(*n_blocks_dev, cap_blocks);
-  const unsigned int per_round = gridDim.x * (kTriThreads / 32);
+  const unsigned int per_round = gridDim.x * kTriWarps;
   const unsigned int rounds = (nb + per_round - 1u) / per_round;
-  for (unsigned int rd = 0; rd < rounds; ++rd) {
-    const unsigned int r = rd * per_round + blockIdx.x * (kTriThreads / 32) + warp;
-    unsigned int off = 0, cnt = 0;
-    int kx = 0, ky = 0, kz = 0;
-    if (r < nb) {
-      off = offsets[r];
-      cnt = counts[r];
-      if ((unsigned long long)off + cnt > cap_entries) cnt = 0;   // an overflowed stream
-      kx = keys3[3u * r];
-      ky = keys3[3u * r + 1];
-      kz = keys3[3u * r + 2];
+  for (unsigned int r0 = 0; r0 < rounds; r0 += kTriGroup) {
+    const unsigned int nr = min(kTriGroup, rounds - r0);
+    // 1. the triangle counts of the warp's next nr records (one per round), then one
+    //    reservation per round for the CTA's records
+    for (unsigned int j = 0; j < nr; ++j) {
+      const unsigned int r = (r0 + j) * per_round + blockIdx.x * kTriWarps + warp;
+      unsigned int mine = 0;
+      if (r < nb) {
+        const unsigned int off = offsets[r];
+        unsigned int cnt = counts[r];
+        if ((unsigned long long)off + cnt > cap_entries) cnt = 0;   // an overflowed stream
+        for (unsigned int e = lane; e < cnt; e += 32u) mine += s_n[index[off + e]];
+      }
+      mine = __reduce_add_sync(0xFFFFFFFFu, mine);
+      if (lane == 0) s_off[j][warp] = mine;
     }
-    unsigned int mine = 0;
-    for (unsigned int e = lane; e < cnt; e += 32u) mine += s_n[index[off + e]];
-    unsigned int incl = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-      if ((int)lane >= d) incl += v;
-    }
-    if (lane == 31u) s_warp[warp] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < nr) {
+      unsigned int* row = s_off[threadIdx.x];
       unsigned int run = 0;
-      for (int w = 0; w < kTriThreads / 32; ++w) {
-        const unsigned int c = s_warp[w];
-        s_warp[w] = run;
+      for (int w = 0; w < kTriWarps; ++w) {
+        const unsigned int c = row[w];
+        row[w] = run;
         run += c;
       }
-      s_base = run ? atomicAdd(n_tris, run) : 0u;
+      const unsigned int base = run ? atomicAdd(n_tris, run) : 0u;
+      for (int w = 0; w < kTriWarps; ++w) row[w] += base;
     }
     __syncthreads();
-    unsigned int o = s_base + s_warp[warp] + incl - mine;
-    for (unsigned int e = lane; e < cnt; e += 32u) {
-      const unsigned int ci = index[off + e];
-      const unsigned int l = local[off + e];
-      const int gx2 = 2 * (8 * kx + (int)(l & 7u)), gy2 = 2 * (8 * ky + (int)((l >> 3) & 7u)),
-                gz2 = 2 * (8 * kz + (int)(l >> 6));
-      const unsigned int nt = s_n[ci];
-      for (unsigned int t = 0; t < nt; ++t, ++o) {
-        if (o >= cap_tris) continue;
-        float* dst = tris + 9ull * o;
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          const unsigned int ed = s_e[15u * ci + 3u * t + v];
-          dst[3 * v] = __fmul_rn((float)(gx2 + s_mid[3u * ed]), half_s);
-          dst[3 * v + 1] = __fmul_rn((float)(gy2 + s_mid[3u * ed + 1u]), half_s);
-          dst[3 * v + 2] = __fmul_rn((float)(gz2 + s_mid[3u * ed + 2u]), half_s);
+    // 2. each record's triangles, 32 entries at a time, with no CTA barrier (records differ
+    //    widely in size): each lane packs its entry's triangles (voxel index and the three
+    //    edges) into the warp's stage, then the warp writes the chunk's floats in order, 32
+    //    consecutive floats per store
+    unsigned int* stage = s_stage[warp];
+    for (unsigned int j = 0; j < nr; ++j) {
+      const unsigned int r = (r0 + j) * per_round + blockIdx.x * kTriWarps + warp;
+      if (r >= nb) break;
+      const unsigned int off = offsets[r];
+      unsigned int cnt = counts[r];
+      if ((unsigned long long)off + cnt > cap_entries) cnt = 0;
+      const int kx = keys3[3u * r], ky = keys3[3u * r + 1], kz = keys3[3u * r + 2];
+      unsigned int o = s_off[j][warp];
+      for (unsigned int c0 = 0; c0 < cnt; c0 += 32u) {
+        const unsigned int e = c0 + lane;
+        unsigned int nt = 0, ci = 0, l = 0;
+        if (e < cnt) {
+          ci = index[off + e];
+          l = local[off + e];
+          nt = s_n[ci];
         }
+        unsigned int at = nt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, at, d);
+          if ((int)lane >= d) at += v;
+        }
+        const unsigned int tot = __shfl_sync(0xFFFFFFFFu, at, 31);
+        at -= nt;
+        for (unsigned int t = 0; t < nt; ++t) {
+          const unsigned char* ed = &s_e[15u * ci + 3u * t];
+          stage[at + t] = l | ((unsigned int)ed[0] << 9) | ((unsigned int)ed[1] << 13) |
+                          ((unsigned int)ed[2] << 17);
+        }
+        __syncwarp();
+        const unsigned int nf = 9u * tot;
+        for (unsigned int f = lane; f < nf; f += 32u) {
+          const unsigned int tr = f / 9u, k = f - 9u * tr, v = k / 3u, c = k - 3u * v;
+          const unsigned int w = stage[tr];
+          const unsigned int ed = (w >> (9u + 4u * v)) & 15u;
+          const int base = c == 0 ? kx : c == 1 ? ky : kz;
+          const int g2 = 2 * (8 * base + (int)((w >> (3u * c)) & 7u));
+          if (o + tr < cap_tris)
+            tris[9ull * o + f] = __fmul_rn((float)(g2 + s_mid[3u * ed + c]), half_s);
+        }
+        __syncwarp();
+        o += tot;
       }
     }
-    __syncthreads();
+    __syncthreads();   // s_off is refilled for the next group
   }
 }
 

@@ -431,13 +431,15 @@ void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevC
 // The batch's erases, from the erase list its first pass compacted.
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        unsigned int* res, unsigned char* st, unsigned int n, BatchLists lists);
-// The whole batch (prep, finds, inserts, insert values, erases) in one cooperative launch with
-// grid barriers between the phases: for small batches of plain maps.
-cudaError_t launch_hash_batch_fused(const Launch& L, TableView t, PoolView pool,
-                                    DevCounters* cnt, const unsigned char* ops,
-                                    const int* keys3, const unsigned int* vals,
-                                    unsigned int* res, unsigned char* st, unsigned int n,
-                                    BatchLists lists);
+// A plain map's small batch in one cooperative launch, one thread per op (finds; inserts;
+// insert values and erases, separated by grid barriers).  lists_next: the three list counts
+// of the next phased batch, zeroed.  Returns cudaErrorInvalidValue when n ops need more CTAs
+// than can be resident at once.
+int small_batch_grid(const Launch& L);
+cudaError_t launch_hash_batch_small(const Launch& L, TableView t, DevCounters* cnt,
+                                    const unsigned char* ops, const int* keys3,
+                                    const unsigned int* vals, unsigned int* res,
+                                    unsigned char* st, unsigned int n, unsigned int* lists_next);
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt);
 void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,

@@ -88,6 +88,25 @@ def test_random_batches(hash_fn, universe, batch, n_batches):
     check_contents(hm, om)
 
 
+def test_small_and_phased_batches_interleaved():
+    """A plain map runs batches of at most 2^17 ops as one launch with one thread per op and
+    larger ones as phased launches over compacted op lists; interleaved on one map (each kind
+    of batch leaves the other's list counts ready), both give the oracle's results."""
+    rng = np.random.default_rng(17)
+    pool = synth.random_hash_keys(300000, seed=17)
+    hm = HashMap(n_buckets=1 << 17, max_batch=1 << 18)
+    om = OracleMap()
+    for n in (1000, (1 << 17) + 3, 37, 150001, 1 << 17, 5000, 140000):
+        ops, keys = mixed_ops(rng, n, pool, None, p=(0.4, 0.4, 0.2))
+        vals = key_value(keys)
+        rg, sg = gpu_batch(hm, ops, keys, vals)
+        ro, so = om.batch(ops, keys, vals)
+        assert_same(ops, keys, rg, sg, ro, so)
+        c = hm.counters()
+        assert c.live == len(om) and c.error_flags == 0
+    check_contents(hm, om)
+
+
 def test_zipf_clustered_keys_heavy_duplication():
     rng = np.random.default_rng(7)
     hm = HashMap(n_buckets=1 << 14)

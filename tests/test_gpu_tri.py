@@ -99,3 +99,47 @@ def test_capacity_reports_the_needed_count():
     V.vbh_mc_triangulate(s.c_struct(), 0.01, tris, 10, n, torch.cuda.current_stream().cuda_stream)
     assert int(n.item()) == len(full) > 10
     vol.close()
+
+
+def test_records_beyond_one_counting_group():
+    """The kernel (8 CTAs of 8 warps per SM, one record per warp and round) counts the triangles
+    of up to 16 rounds of records before it writes them: a stream of more than two such groups
+    of records (every record pointing at the entries of one extracted block, each with its own
+    key) is written whole, each record's triangles being the oracle's triangles of that block
+    moved by the record's key."""
+    F = np.full((8, 8, 8), 0.5, np.float32)
+    F[3, 4, 2] = -0.5   # eight cubes with one inside corner each
+    keys, vals = blocks_from(F)
+    vol, o = pair(keys, vals)
+    s = vol.extract(V.VBH_MC_ALL)
+    nb, ne = (int(x) for x in s.n.cpu().tolist())
+    assert nb == 1 and ne == 8
+    base = o.triangles(keys).reshape(-1, 9)
+    m0 = len(base)
+    assert m0 == 8
+    from paper_1805_03709_b300.volume import McStream
+    N = 2 * torch.cuda.get_device_properties(0).multi_processor_count * 64 * 16 + 5
+    r = torch.arange(N, dtype=torch.int32, device="cuda")
+    shift = torch.stack([r % 512, r // 512, torch.zeros_like(r)], 1)
+    big = McStream(
+        (torch.from_numpy(keys).cuda() + shift).contiguous(),
+        torch.zeros(N, dtype=torch.int32, device="cuda"),
+        torch.full((N,), int(s.offsets[0]), dtype=torch.int32, device="cuda"),
+        torch.full((N,), int(s.counts[0]), dtype=torch.int32, device="cuda"),
+        s.local, s.index, torch.tensor([N, ne], dtype=torch.int32, device="cuda"))
+    tris = vol.triangulate(big, cap=N * m0).cpu().numpy().reshape(-1, 9)
+    assert len(tris) == N * m0
+    sh = (8 * 0.01) * np.repeat(shift.cpu().numpy().astype(np.float64), 3, axis=0).reshape(N, 9)
+    ref = (base[None, :, :] + sh[:, None, :]).reshape(-1, 9)
+
+    def canon_rows(t):
+        q = np.round(np.asarray(t, np.float64) / 0.005).astype(np.int64).reshape(-1, 3, 3)
+        code = ((q[..., 0] + (1 << 20)) << 42) | ((q[..., 1] + (1 << 20)) << 21) | (q[..., 2] + (1 << 20))
+        first = np.argmin(code, axis=1)
+        idx = (first[:, None] + np.arange(3)[None, :]) % 3
+        rolled = np.take_along_axis(code, idx, axis=1)
+        v = np.ascontiguousarray(rolled).view(np.dtype((np.void, 24))).ravel()
+        return np.sort(v)
+
+    assert np.array_equal(canon_rows(tris), canon_rows(ref))
+    vol.close()
