@@ -33,36 +33,83 @@ constexpr int kThreads = 256;
 // outcome codes of thread_insert
 constexpr int kInserted = 1, kExists = 2, kFull = 3;
 
+template <int W = 1>
 __device__ int thread_insert(const TableView& t, unsigned long long key, unsigned int* pos_out,
                              unsigned long long* observed_out) {
-  unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
+  const unsigned int b0 = home_bucket(key, t.bmask, t.hash_fn);
   const unsigned int step = probe_step(key);
   unsigned int first_free = kNone, held = kNone;
-  ulonglong2 s[4];
+  ulonglong2 s[4];   // the bucket pass 1 ended on
   // pass 1: the whole chain, to be sure the key is absent
-  for (unsigned int probe = 0; probe <= t.bmask; ++probe) {
-    load_bucket<false>(&t.slots[4u * b], s);
-    held = b;
-    bool empty = false;
-    int hit = -1, f = -1;   // f: the bucket's first free slot
+  if constexpr (W == 1) {
+    unsigned int b = b0;
+    for (unsigned int probe = 0; probe <= t.bmask; ++probe) {
+      load_bucket<false>(&t.slots[4u * b], s);
+      held = b;
+      bool empty = false;
+      int hit = -1, f = -1;   // f: the bucket's first free slot
 #pragma unroll
-    for (int q = 3; q >= 0; --q) {
-      if (s[q].x == key) hit = q;
-      if (s[q].x >= kTomb) f = q;
-      empty |= s[q].x == kEmpty;
+      for (int q = 3; q >= 0; --q) {
+        if (s[q].x == key) hit = q;
+        if (s[q].x >= kTomb) f = q;
+        empty |= s[q].x == kEmpty;
+      }
+      if (hit >= 0) {
+        *pos_out = 4u * b + hit;
+        return kExists;
+      }
+      if (first_free == kNone && f >= 0) first_free = 4u * b + f;
+      if (empty) break;
+      b = (b + step) & t.bmask;
     }
-    if (hit >= 0) {
-      *pos_out = 4u * b + hit;
+  } else {
+  // W buckets of the chain per round trip, examined in sequence order
+  for (unsigned int probe = 0; probe <= t.bmask; probe += W) {
+    ulonglong2 g[W][4];
+    unsigned int bb[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      bb[w] = (b0 + (probe + w) * step) & t.bmask;
+      load_bucket<false>(&t.slots[4u * bb[w]], g[w]);
+    }
+    bool stop = false;
+    unsigned int hit_pos = kNone;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      bool empty = false;
+      int hit = -1, f = -1;   // f: the bucket's first free slot
+#pragma unroll
+      for (int q = 3; q >= 0; --q) {
+        if (g[w][q].x == key) hit = q;
+        if (g[w][q].x >= kTomb) f = q;
+        empty |= g[w][q].x == kEmpty;
+      }
+      const bool live = !stop && (W == 1 || probe + w <= t.bmask);   // every bucket once
+      if (live) {
+        if (hit >= 0) {
+          hit_pos = 4u * bb[w] + hit;
+        } else {
+          if (first_free == kNone && f >= 0) first_free = 4u * bb[w] + f;
+          if (empty) {
+            held = bb[w];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[q] = g[w][q];
+          }
+        }
+        stop = hit >= 0 || empty;
+      }
+    }
+    if (hit_pos != kNone) {
+      *pos_out = hit_pos;
       return kExists;
     }
-    if (first_free == kNone && f >= 0) first_free = 4u * b + f;
-    if (empty) break;
-    b = (b + step) & t.bmask;
+    if (stop) break;
+  }
   }
   if (first_free == kNone) return kFull;
   // pass 2: claim in probe order starting at the first free slot.  The bucket pass 1 ended on
   // is reused for the first attempt: a stale copy only costs a failed CAS and a re-read.
-  b = first_free >> 2;
+  unsigned int b = first_free >> 2;
   bool have = b == held;
   for (unsigned int steps = 0; steps <= t.bmask;) {
     if (!have) load_bucket<false>(&t.slots[4u * b], s);
@@ -483,7 +530,8 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
 // that keeps its op and key in registers, so there are no op lists, and three phases separated
 // by two grid barriers:
 //   1. every op is read and checked; the finds run (nothing writes the table yet, so they see
-//      it as the batch found it), and the inserts and erases prefetch their home bucket to L2;
+//      it as the batch found it), and the inserts and erases prefetch the first buckets of
+//      their probe sequences to L2;
 //   2. the inserts claim their slots; a winner writes its value and its final result;
 //   3. the inserts that met their key read its value (every winner wrote its value before the
 //      barrier, and an erase leaves the value field alone), and the erases run.
@@ -518,6 +566,14 @@ __device__ __forceinline__ void grid_barrier(DevCounters* cnt) {
   __syncthreads();
 }
 
+#ifndef VBH_SMALL_BATCH_PROBES
+#define VBH_SMALL_BATCH_PROBES 2
+#endif
+// Buckets of a probe sequence loaded per round trip in a small batch, whose phases last as long
+// as their longest walk (at load 0.7 a miss reads ~1.7 buckets on average, the longest of 2^16
+// walks ten or more); phased batches of many ops are bound by bandwidth and load one at a time.
+constexpr int kSmallProbes = VBH_SMALL_BATCH_PROBES;
+
 __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounters* cnt,
                                                           const unsigned char* ops,
                                                           const int* keys3,
@@ -547,12 +603,16 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
   }
   if (kind == kOpFind) {
     unsigned int val;
-    const bool hit = thread_find<false>(t, key, &val) != kNone;
+    const bool hit = thread_find<false, kSmallProbes>(t, key, &val) != kNone;
     res[i] = hit ? val : kNone;
     st[i] = hit ? kStFound : kStNotFound;
   } else if (kind >= 0) {
-    const Slot* b = &t.slots[4u * home_bucket(key, t.bmask, t.hash_fn)];
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(b));
+    const unsigned int b0 = home_bucket(key, t.bmask, t.hash_fn), step = probe_step(key);
+#pragma unroll
+    for (int w = 0; w < kSmallProbes; ++w) {
+      const Slot* b = &t.slots[4u * ((b0 + w * step) & t.bmask)];
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(b));
+    }
   }
   grid_barrier(cnt);
 
@@ -560,7 +620,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
   unsigned int pos = kNone;
   unsigned long long observed = 0;
   if (kind == kOpInsert) {
-    outcome = thread_insert(t, key, &pos, &observed);
+    outcome = thread_insert<kSmallProbes>(t, key, &pos, &observed);
     if (outcome == kInserted) {
       const unsigned int v = vals ? vals[i] : 0u;
       t.slots[pos].val = v;
@@ -590,7 +650,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
   if (kind == kOpErase) {
     bool bucket_empty = false;
     unsigned int val = kNone;
-    const unsigned int p = thread_find<false>(t, key, &val, &bucket_empty);
+    const unsigned int p = thread_find<false, kSmallProbes>(t, key, &val, &bucket_empty);
     if (p != kNone) how = erase_found(t, p, key, bucket_empty);
     res[i] = how ? val : kNone;
     st[i] = how ? kStErased : kStNotFound;

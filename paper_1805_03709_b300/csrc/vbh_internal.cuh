@@ -208,29 +208,49 @@ __device__ __forceinline__ ulonglong2 bucket_slot(const ulonglong2 (&s)[4], int 
 
 // Find by one thread: walk the key's probe sequence until the key or a bucket with an EMPTY
 // slot.  Returns the slot index or kNone; *val receives the value and, if given,
-// *bucket_empty whether the key's bucket held an EMPTY slot when it was read.
-template <bool kReadOnly = false>
+// *bucket_empty whether the key's bucket held an EMPTY slot when it was read.  W buckets of the
+// sequence are loaded per round trip (their addresses are known in advance); they are examined
+// in sequence order, so the result is that of the one-bucket walk.
+template <bool kReadOnly = false, int W = 1>
 __device__ __forceinline__ unsigned int thread_find(const TableView& t, unsigned long long key,
                                                     unsigned int* val,
                                                     bool* bucket_empty = nullptr) {
-  unsigned int b = home_bucket(key, t.bmask, t.hash_fn);
+  const unsigned int b0 = home_bucket(key, t.bmask, t.hash_fn);
   const unsigned int step = probe_step(key);
-  for (unsigned int probe = 0; probe <= t.bmask; ++probe, b = (b + step) & t.bmask) {
-    ulonglong2 s[4];
-    load_bucket<kReadOnly>(&t.slots[4u * b], s);
-    int hit = -1;
-    bool empty = false;
+  for (unsigned int probe = 0; probe <= t.bmask; probe += W) {
+    ulonglong2 s[W][4];
+    unsigned int bb[W];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (s[q].x == key) hit = q;
-      empty |= s[q].x == kEmpty;
+    for (int w = 0; w < W; ++w) {
+      bb[w] = (b0 + (probe + w) * step) & t.bmask;
+      load_bucket<kReadOnly>(&t.slots[4u * bb[w]], s[w]);
     }
-    if (hit >= 0) {
-      *val = (unsigned)bucket_slot(s, hit).y;
-      if (bucket_empty) *bucket_empty = empty;
-      return 4u * b + hit;
+    // the first of the W buckets (in sequence order) that holds the key or an EMPTY slot
+    bool stop = false;
+    unsigned int pos = kNone, v = kNone;
+    bool emp = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      int hit = -1;
+      bool empty = false;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (s[w][q].x == key) hit = q;
+        empty |= s[w][q].x == kEmpty;
+      }
+      const bool live = !stop && (W == 1 || probe + w <= t.bmask);   // every bucket once
+      if (live && hit >= 0) {
+        pos = 4u * bb[w] + hit;
+        v = (unsigned)bucket_slot(s[w], hit).y;
+        emp = empty;
+      }
+      stop |= live && (hit >= 0 || empty);
     }
-    if (empty) break;
+    if (stop) {
+      *val = v;
+      if (pos != kNone && bucket_empty) *bucket_empty = emp;
+      return pos;
+    }
   }
   *val = kNone;
   return kNone;
