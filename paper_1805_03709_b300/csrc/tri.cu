@@ -13,10 +13,11 @@
 //     is cut by ear clipping at the first position whose new diagonal joins two edges on no
 //     common face (a diagonal lying on a face would be shared with the neighbouring cube), each
 //     triangle in the reversed loop order so that normals point to positive TSDF.
-// The kernel: one warp per stream record.  The CTA first counts the triangles of its warps'
-// next records (up to 16 rounds) and reserves their output with one atomic per round; then each
-// warp writes its records' triangles (9 floats each, metres) with no further CTA barrier, in
-// order through a per-warp stage in shared memory, so its stores are whole consecutive runs.
+// The kernel: the CTA's warps count the triangles of their next records (one per warp and
+// round, up to 4 rounds), chunk by chunk of 32 entries; one reservation per round places the
+// records' output; then the warps take the CTA's chunks in turn (a record of 500 entries is
+// spread over all of them) and write each chunk's triangles (9 floats each, metres) in order,
+// through a per-warp stage in shared memory, one lane per vertex.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -167,15 +168,24 @@ vbh_status upload_tables() {
 
 constexpr int kTriThreads = 256;
 constexpr int kTriWarps = kTriThreads / 32;
-constexpr unsigned int kTriGroup = 16;   // rounds of records counted before they are written
+constexpr unsigned int kTriGroup = 4;   // rounds of records counted before they are written
+constexpr unsigned int kTriSlots = kTriGroup * kTriWarps;   // records of a CTA per group
+constexpr unsigned int kTriMaxChunks = 16;   // 32-entry chunks of a record (one per voxel)
 
 __global__ void __launch_bounds__(kTriThreads) k_mc_triangulate(
     const int* keys3, const unsigned int* offsets, const unsigned int* counts,
     const unsigned short* local, const unsigned char* index, const unsigned int* n_blocks_dev,
     unsigned int cap_blocks, unsigned int cap_entries, float half_s, float* tris,
     unsigned int cap_tris, unsigned int* n_tris) {
-  __shared__ unsigned int s_off[kTriGroup][kTriWarps];   // first triangle of each record
   __shared__ __align__(4) unsigned char s_n[256], s_e[256 * 15], s_mid[12 * 3 + 4];
+  __shared__ unsigned int s_mid4[12];   // the edge midpoints (x2) as one word per edge
+  // the group's records (slot j * kTriWarps + w: round j of warp w): entries, key, triangles
+  __shared__ unsigned int s_roff[kTriSlots], s_rcnt[kTriSlots], s_rtris[kTriSlots];
+  __shared__ int s_rkey[kTriSlots][3];
+  __shared__ unsigned char s_ccnt[kTriSlots][kTriMaxChunks];   // triangles of each chunk
+  // the group's chunks: slot | chunk << 5, and the chunk's first triangle
+  __shared__ unsigned int s_chunk[kTriSlots * kTriMaxChunks], s_choff[kTriSlots * kTriMaxChunks];
+  __shared__ unsigned int s_nchunks;
   __shared__ unsigned int s_stage[kTriWarps][32 * 5];   // <= 5 triangles per cube
   for (unsigned int i = threadIdx.x; i < 64u; i += kTriThreads)
     reinterpret_cast<unsigned int*>(s_n)[i] = reinterpret_cast<const unsigned int*>(g_tri_n)[i];
@@ -184,89 +194,122 @@ __global__ void __launch_bounds__(kTriThreads) k_mc_triangulate(
   for (unsigned int i = threadIdx.x; i < 10u; i += kTriThreads)
     reinterpret_cast<unsigned int*>(s_mid)[i] = reinterpret_cast<const unsigned int*>(g_mid2)[i];
   __syncthreads();
+  if (threadIdx.x < 12u)
+    s_mid4[threadIdx.x] = s_mid[3u * threadIdx.x] | (unsigned int)s_mid[3u * threadIdx.x + 1] << 8 |
+                          (unsigned int)s_mid[3u * threadIdx.x + 2] << 16;
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int nb = min(*n_blocks_dev, cap_blocks);
   const unsigned int per_round = gridDim.x * kTriWarps;
   const unsigned int rounds = (nb + per_round - 1u) / per_round;
   for (unsigned int r0 = 0; r0 < rounds; r0 += kTriGroup) {
     const unsigned int nr = min(kTriGroup, rounds - r0);
-    // 1. the triangle counts of the warp's next nr records (one per round), then one
-    //    reservation per round for the CTA's records
+    // 1. each warp counts the triangles of its next nr records, chunk by chunk
     for (unsigned int j = 0; j < nr; ++j) {
+      const unsigned int slot = j * kTriWarps + warp;
       const unsigned int r = (r0 + j) * per_round + blockIdx.x * kTriWarps + warp;
-      unsigned int mine = 0;
+      unsigned int off = 0, cnt = 0;
       if (r < nb) {
-        const unsigned int off = offsets[r];
-        unsigned int cnt = counts[r];
-        if ((unsigned long long)off + cnt > cap_entries) cnt = 0;   // an overflowed stream
-        for (unsigned int e = lane; e < cnt; e += 32u) mine += s_n[index[off + e]];
+        off = offsets[r];
+        cnt = counts[r];
+        // an overflowed stream, or more entries than voxels: nothing of the record is read
+        if ((unsigned long long)off + cnt > cap_entries || cnt > 32u * kTriMaxChunks) cnt = 0;
       }
-      mine = __reduce_add_sync(0xFFFFFFFFu, mine);
-      if (lane == 0) s_off[j][warp] = mine;
+      unsigned int tot = 0;
+      for (unsigned int c = 0; 32u * c < cnt; ++c) {
+        const unsigned int e = 32u * c + lane;
+        const unsigned int k = __reduce_add_sync(0xFFFFFFFFu, e < cnt ? s_n[index[off + e]] : 0u);
+        if (lane == 0) s_ccnt[slot][c] = (unsigned char)k;
+        tot += k;
+      }
+      if (lane == 0) {
+        s_roff[slot] = off;
+        s_rcnt[slot] = cnt;
+        s_rtris[slot] = tot;
+      }
+      if (lane < 3u) s_rkey[slot][lane] = r < nb ? keys3[3u * r + lane] : 0;
     }
     __syncthreads();
-    if (threadIdx.x < nr) {
-      unsigned int* row = s_off[threadIdx.x];
-      unsigned int run = 0;
-      for (int w = 0; w < kTriWarps; ++w) {
-        const unsigned int c = row[w];
-        row[w] = run;
-        run += c;
-      }
-      const unsigned int base = run ? atomicAdd(n_tris, run) : 0u;
-      for (int w = 0; w < kTriWarps; ++w) row[w] += base;
-    }
-    __syncthreads();
-    // 2. each record's triangles, 32 entries at a time, with no CTA barrier (records differ
-    //    widely in size): each lane packs its entry's triangles (voxel index and the three
-    //    edges) into the warp's stage, then the warp writes the chunk's floats in order, 32
-    //    consecutive floats per store
-    unsigned int* stage = s_stage[warp];
-    for (unsigned int j = 0; j < nr; ++j) {
-      const unsigned int r = (r0 + j) * per_round + blockIdx.x * kTriWarps + warp;
-      if (r >= nb) break;
-      const unsigned int off = offsets[r];
-      unsigned int cnt = counts[r];
-      if ((unsigned long long)off + cnt > cap_entries) cnt = 0;
-      const int kx = keys3[3u * r], ky = keys3[3u * r + 1], kz = keys3[3u * r + 2];
-      unsigned int o = s_off[j][warp];
-      for (unsigned int c0 = 0; c0 < cnt; c0 += 32u) {
-        const unsigned int e = c0 + lane;
-        unsigned int nt = 0, ci = 0, l = 0;
-        if (e < cnt) {
-          ci = index[off + e];
-          l = local[off + e];
-          nt = s_n[ci];
+    // 2. warp 0: one output reservation per round, then the list of the group's chunks with
+    //    each chunk's first triangle
+    if (warp == 0) {
+      if (lane < nr) {
+        unsigned int run = 0;
+        for (int w = 0; w < kTriWarps; ++w) {
+          const unsigned int c = s_rtris[lane * kTriWarps + w];
+          s_rtris[lane * kTriWarps + w] = run;
+          run += c;
         }
-        unsigned int at = nt;
+        const unsigned int base = run ? atomicAdd(n_tris, run) : 0u;
+        for (int w = 0; w < kTriWarps; ++w) s_rtris[lane * kTriWarps + w] += base;
+      }
+      __syncwarp();
+      static_assert(kTriSlots <= 32, "one lane per slot");
+      const unsigned int slot = lane;
+      const unsigned int nch = slot < nr * kTriWarps ? (s_rcnt[slot] + 31u) / 32u : 0u;
+      unsigned int at = nch;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, at, d);
-          if ((int)lane >= d) at += v;
-        }
-        const unsigned int tot = __shfl_sync(0xFFFFFFFFu, at, 31);
-        at -= nt;
-        for (unsigned int t = 0; t < nt; ++t) {
-          const unsigned char* ed = &s_e[15u * ci + 3u * t];
-          stage[at + t] = l | ((unsigned int)ed[0] << 9) | ((unsigned int)ed[1] << 13) |
-                          ((unsigned int)ed[2] << 17);
-        }
-        __syncwarp();
-        const unsigned int nf = 9u * tot;
-        for (unsigned int f = lane; f < nf; f += 32u) {
-          const unsigned int tr = f / 9u, k = f - 9u * tr, v = k / 3u, c = k - 3u * v;
-          const unsigned int w = stage[tr];
-          const unsigned int ed = (w >> (9u + 4u * v)) & 15u;
-          const int base = c == 0 ? kx : c == 1 ? ky : kz;
-          const int g2 = 2 * (8 * base + (int)((w >> (3u * c)) & 7u));
-          if (o + tr < cap_tris)
-            tris[9ull * o + f] = __fmul_rn((float)(g2 + s_mid[3u * ed + c]), half_s);
-        }
-        __syncwarp();
-        o += tot;
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, at, d);
+        if ((int)lane >= d) at += v;
+      }
+      if (lane == 31u) s_nchunks = at;
+      at -= nch;
+      unsigned int o = nch ? s_rtris[slot] : 0u;
+      for (unsigned int c = 0; c < nch; ++c) {
+        s_chunk[at + c] = slot | c << 5;
+        s_choff[at + c] = o;
+        o += s_ccnt[slot][c];
       }
     }
-    __syncthreads();   // s_off is refilled for the next group
+    __syncthreads();
+    // 3. the warps take the group's chunks in turn (records differ widely in size): each lane
+    //    packs its entry's triangles (voxel index, three edges) into the warp's stage, then
+    //    each lane writes whole vertices of the chunk's triangles, in order
+    const unsigned int nchunks = s_nchunks;
+    unsigned int* stage = s_stage[warp];
+    for (unsigned int k = warp; k < nchunks; k += kTriWarps) {
+      const unsigned int slot = s_chunk[k] & 31u, c = s_chunk[k] >> 5;
+      const unsigned int off = s_roff[slot] + 32u * c;
+      const unsigned int cnt = min(32u, s_rcnt[slot] - 32u * c);
+      const int gx = 16 * s_rkey[slot][0], gy = 16 * s_rkey[slot][1], gz = 16 * s_rkey[slot][2];
+      const unsigned int o = s_choff[k];
+      unsigned int nt = 0, ci = 0, l = 0;
+      if (lane < cnt) {
+        ci = index[off + lane];
+        l = local[off + lane];
+        nt = s_n[ci];
+      }
+      unsigned int at = nt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xFFFFFFFFu, at, d);
+        if ((int)lane >= d) at += v;
+      }
+      const unsigned int tot = __shfl_sync(0xFFFFFFFFu, at, 31);
+      at -= nt;
+      for (unsigned int t = 0; t < nt; ++t) {
+        const unsigned char* ed = &s_e[15u * ci + 3u * t];
+        stage[at + t] = l | ((unsigned int)ed[0] << 9) | ((unsigned int)ed[1] << 13) |
+                        ((unsigned int)ed[2] << 17);
+      }
+      __syncwarp();
+      for (unsigned int q = lane; q < 3u * tot; q += 32u) {
+        const unsigned int tr = q / 3u, v = q - 3u * tr;
+        if (o + tr >= cap_tris) continue;
+        const unsigned int w = stage[tr];
+        const unsigned int m = s_mid4[(w >> (9u + 4u * v)) & 15u];
+        // 2 x the vertex, (2 (8 key + l) + edge midpoint x 2), then x voxel_size / 2
+        const int x2 = gx + 2 * (int)(w & 7u) + (int)(m & 0xFFu);
+        const int y2 = gy + 2 * (int)((w >> 3) & 7u) + (int)((m >> 8) & 0xFFu);
+        const int z2 = gz + 2 * (int)((w >> 6) & 7u) + (int)(m >> 16);
+        float* dst = tris + 9ull * o + 3u * q;
+        dst[0] = __fmul_rn((float)x2, half_s);
+        dst[1] = __fmul_rn((float)y2, half_s);
+        dst[2] = __fmul_rn((float)z2, half_s);
+      }
+      __syncwarp();
+    }
+    __syncthreads();   // the group's shared arrays are refilled next
   }
 }
 

@@ -103,10 +103,10 @@ def test_capacity_reports_the_needed_count():
 
 def test_records_beyond_one_counting_group():
     """The kernel (8 CTAs of 8 warps per SM, one record per warp and round) counts the triangles
-    of up to 16 rounds of records before it writes them: a stream of more than two such groups
-    of records (every record pointing at the entries of one extracted block, each with its own
-    key) is written whole, each record's triangles being the oracle's triangles of that block
-    moved by the record's key."""
+    of a few rounds of records before it writes them: a stream of many such groups of records
+    (every record pointing at the entries of one extracted block, each with its own key) is
+    written whole, each record's triangles being the oracle's triangles of that block moved by
+    the record's key."""
     F = np.full((8, 8, 8), 0.5, np.float32)
     F[3, 4, 2] = -0.5   # eight cubes with one inside corner each
     keys, vals = blocks_from(F)
