@@ -133,12 +133,13 @@ vbh_status vbh_set_stream(vbh_handle* h, void* cuda_stream);
  * among duplicate erases exactly one reports ERASED.  On a voxel-block handle (max_blocks > 0)
  * an insert takes a block from the pool (value = pool index; the new block reads as TSDF 0,
  * weight 0) and an erase returns it.  n may be 0.  n > max_batch -> VBH_ERR_INVALID_ARG.
- * The call is asynchronous on the handle's stream, except that the first batch larger than any
- * before it synchronises and allocates the handle's op lists (36 B per op: the batch's finds,
- * inserts and erases as op index + packed key); VBH_ERR_CUDA if that allocation fails.
- * A plain map's batch of at most 2^17 ops runs its phases in one cooperative launch separated
- * by grid barriers; a barrier that waits longer than ~1 s gives up and raises error flag bit3
- * (the batch's results are then not to be trusted). */
+ * A plain map's batch of at most 2^17 ops runs in one cooperative launch with one thread per
+ * op: finds, then inserts, then erases, separated by grid barriers; a barrier that waits longer
+ * than ~1 s gives up and raises error flag bit3 (the batch's results are then not to be
+ * trusted).  Other batches run as phased launches over op lists.  The call is asynchronous on
+ * the handle's stream, except that the first phased batch larger than any before it
+ * synchronises and allocates the handle's op lists (36 B per op: the batch's finds, inserts
+ * and erases as op index + packed key); VBH_ERR_CUDA if that allocation fails. */
 vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* keys3_dev,
                           const uint32_t* vals_dev, uint32_t* results_dev, uint8_t* status_dev,
                           uint32_t n);

@@ -404,7 +404,9 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
     return fail(VBH_ERR_INVALID_ARG, "null device pointer");
   vbh_status st = maybe_rebuild(h);
   if (st != VBH_OK) return st;
-  if (h->blists_cap < n) {   // the compacted find / insert / erase lists, grown to n
+  // a small batch of a plain map: one cooperative launch, one thread per op, no op lists
+  const bool small = h->cfg.max_blocks == 0 && n <= kSmallBatchMax && small_batch_fits(h->L, n);
+  if (!small && h->blists_cap < n) {   // the compacted find / insert / erase lists, grown to n
     VBH_CUDA(cudaStreamSynchronize(h->stream));
     free_batch_lists(h);
     BatchLists& b = h->blists;
@@ -425,9 +427,7 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   h->blists.n = h->cnt->op_lists[h->batch_parity];
   h->blists.n_next = h->cnt->op_lists[h->batch_parity ^ 1u];
   h->batch_parity ^= 1u;
-  if (h->cfg.max_blocks == 0 && n <= kSmallBatchMax &&
-      (n + 255u) / 256u <= (uint32_t)small_batch_grid(h->L)) {
-    // a small batch of a plain map: one cooperative launch, one thread per op
+  if (small) {
     VBH_CUDA(launch_hash_batch_small(h->L, t, h->cnt, ops_dev, keys3_dev, vals_dev, results_dev,
                                      status_dev, n, h->blists.n_next));
     h->launches += 1;

@@ -825,12 +825,15 @@ int small_batch_grid(const Launch& L) {
   static const int grid = persistent_grid(k_batch_small, kThreads, L.sms);
   return grid;
 }
+bool small_batch_fits(const Launch& L, unsigned int n) {
+  return n > 0 && (n + kThreads - 1u) / kThreads <= (unsigned int)small_batch_grid(L);
+}
 cudaError_t launch_hash_batch_small(const Launch& L, TableView t, DevCounters* cnt,
                                     const unsigned char* ops, const int* keys3,
                                     const unsigned int* vals, unsigned int* res,
                                     unsigned char* st, unsigned int n, unsigned int* lists_next) {
+  if (!small_batch_fits(L, n)) return cudaErrorInvalidValue;
   const unsigned int grid = (n + kThreads - 1u) / kThreads;   // one thread per op
-  if (grid == 0 || grid > (unsigned int)small_batch_grid(L)) return cudaErrorInvalidValue;
   void* args[] = {&t, &cnt, &ops, &keys3, &vals, &res, &st, &n, &lists_next};
   return cudaLaunchCooperativeKernel((const void*)k_batch_small, dim3(grid), dim3(kThreads),
                                      args, 0, L.stream);

@@ -456,6 +456,7 @@ void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters*
 // of the next phased batch, zeroed.  Returns cudaErrorInvalidValue when n ops need more CTAs
 // than can be resident at once.
 int small_batch_grid(const Launch& L);
+bool small_batch_fits(const Launch& L, unsigned int n);   // n ops fit one resident grid
 cudaError_t launch_hash_batch_small(const Launch& L, TableView t, DevCounters* cnt,
                                     const unsigned char* ops, const int* keys3,
                                     const unsigned int* vals, unsigned int* res,
