@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the differentiable-fusion timing (forward vs forward+backward)")
-    ap.add_argument("--clock-ms", type=int, default=200,
+    ap.add_argument("--clock-ms", type=int, default=20,
                     help="nvidia-smi sampling interval during the timed region (0 = off)")
     ap.add_argument("--small-memory", action="store_true",
                     help="profiling case: 32-frame sequence, 2^20-bucket table, 2^17-block pool "
@@ -259,7 +259,7 @@ class ClockSampler:
         self.proc.wait(timeout=5)
         t0, t1 = self.window
         sel = [r for t, r in self.rows if t0 - 0.15 <= t <= t1 + 0.15] or [r for _, r in self.rows]
-        sm, smax, reasons = [], [], set()
+        sm, smax, busy, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in sel:
             f = [x.strip() for x in r.split(",")]
@@ -270,12 +270,22 @@ class ClockSampler:
                 smax.append(float(f[2]))
             except ValueError:
                 continue
+            try:   # bit 0 of the active reasons: the GPU was idle at the sample
+                idle = bool(int(f[4], 16) & 1)
+            except ValueError:
+                idle = False
+            if not idle:
+                busy.append(sm[-1])
             for name, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
+        # median under load: samples the GPU reported idle at (between the short timed steps)
+        # are left out when any sample was taken under load
+        under = busy or sm
+        return {"sm_mhz": statistics.median(under) if under else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_under_load": len(busy),
+                "sm_mhz_all_samples": statistics.median(sm) if sm else None}
 
 
 def measured_peak():
