@@ -470,6 +470,7 @@ def main():
         h2d = d2h = 0
         nbs = []
         statuses = []
+        host_call_s = []   # wall time of each call (enqueueing, and waiting when the GPU is behind)
 
         def account(o):   # bytes copied out for the frame (its counts come from the replay)
             nonlocal d2h
@@ -485,8 +486,10 @@ def main():
             fl_ev[k][0].record()
             flush.zero_()
             fl_ev[k][1].record()
+            tc = time.perf_counter()
             statuses.append(vol.process_frame_host(host_depth[f], poses[f], i + 1, ERASE_R,
                                                    outs[k % 3]))
+            host_call_s.append(time.perf_counter() - tc)
             h2d += depth_bytes
             if k >= 2:   # the frame of two calls earlier is complete
                 account(outs[(k - 2) % 3])
@@ -511,7 +514,8 @@ def main():
                "frames_timed": f"{args.warmup}..{args.warmup + n_e2e - 1} (mod {N_FRAMES})",
                "api": "vbh_process_frame_host (pinned host depth in, whole MC stream out, "
                       "consecutive frames pipelined)",
-               "l2_flush_between_frames_s": flush_s}
+               "l2_flush_between_frames_s": flush_s,
+               "host_call_ms_p50": statistics.median(host_call_s) * 1e3}
 
     # MC extraction roofline: the same frames' MC extraction, timed (CUDA events around the
     # kernel on the volume's stream) and counted on the e2e replay (or a replay of its own)

@@ -1,7 +1,7 @@
 // vbh_process_frame with host buffers, pipelined over consecutive calls, three frames deep.
 //
-// Call k (j = k mod 3) enqueues: the depth copy host -> device buffer j on a copy stream (after
-// frame k-3, which read buffer j, has finished), the frame graph on the handle's stream into
+// Call k (j = k mod 3) enqueues: the depth copy host -> device buffer j on the copy-in stream
+// (after frame k-3, which read buffer j, has finished), the frame graph on the handle's stream into
 // device stream j (after frame k-3's results, read from stream j, have been copied out), and a
 // copy of frame k's two totals to pinned memory.  Then it moves the older frames along: frame
 // k-1's records and entries start their copy into the caller's host buffers if its totals have
@@ -23,7 +23,9 @@ struct HostPipe {
     int j;
     bool copying;   // its copy-out has been enqueued
   };
-  cudaStream_t copy = nullptr;
+  cudaStream_t copy = nullptr;      // copies out (device -> host)
+  cudaStream_t copy_in = nullptr;   // depth copies in, beside the copies out (the two
+                                    // directions run on separate copy engines)
   uint16_t* depth[kHostSlots] = {};   // device depth images
   // device output streams and their totals (device) / totals copy (pinned host)
   int32_t* keys3[kHostSlots] = {};
@@ -75,6 +77,7 @@ vbh_status create_pipe(vbh_handle* h) {
   HostPipe* p = new HostPipe();
   h->hp = p;
   VBH_CUDA(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking));
+  VBH_CUDA(cudaStreamCreateWithFlags(&p->copy_in, cudaStreamNonBlocking));
   const size_t db = sizeof(uint16_t) * (size_t)h->cfg.width * h->cfg.height;
   for (int j = 0; j < kHostSlots; ++j) {
     VBH_CUDA(cudaMalloc(&p->depth[j], db));
@@ -165,9 +168,10 @@ void host_pipe_release(vbh_handle* h) {
   HostPipe* p = h->hp;
   if (!p) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  if (p->copy) {
-    cudaStreamSynchronize(p->copy);
-    cudaStreamDestroy(p->copy);
+  for (cudaStream_t c : {p->copy, p->copy_in}) {
+    if (!c) continue;
+    cudaStreamSynchronize(c);
+    cudaStreamDestroy(c);
   }
   free_streams(p);
   for (int j = 0; j < kHostSlots; ++j) {
@@ -210,6 +214,7 @@ vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
     if (done_st != VBH_OK && done_st != VBH_ERR_BUFFER_TOO_SMALL) return done_st;
     VBH_CUDA(cudaStreamSynchronize(h->stream));
     VBH_CUDA(cudaStreamSynchronize(p->copy));
+    VBH_CUDA(cudaStreamSynchronize(p->copy_in));
     const uint32_t cb = o.cap_blocks > p->cap_blocks ? o.cap_blocks : p->cap_blocks;
     const uint32_t ce = o.cap_entries > p->cap_entries ? o.cap_entries : p->cap_entries;
     vbh_status st = alloc_streams(p, cb, ce);
@@ -217,10 +222,10 @@ vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
   }
   const int j = (int)(p->k % kHostSlots);
   // depth in: after frame k-3 (the last reader of buffer j) has finished
-  if (p->frame_used[j]) VBH_CUDA(cudaStreamWaitEvent(p->copy, p->e_frame[j], 0));
+  if (p->frame_used[j]) VBH_CUDA(cudaStreamWaitEvent(p->copy_in, p->e_frame[j], 0));
   const size_t db = sizeof(uint16_t) * (size_t)h->cfg.width * h->cfg.height;
-  VBH_CUDA(cudaMemcpyAsync(p->depth[j], depth_host, db, cudaMemcpyHostToDevice, p->copy));
-  VBH_CUDA(cudaEventRecord(p->e_h2d[j], p->copy));
+  VBH_CUDA(cudaMemcpyAsync(p->depth[j], depth_host, db, cudaMemcpyHostToDevice, p->copy_in));
+  VBH_CUDA(cudaEventRecord(p->e_h2d[j], p->copy_in));
   // the frame: after its depth has landed and stream j's previous results were copied out
   VBH_CUDA(cudaStreamWaitEvent(h->stream, p->e_h2d[j], 0));
   if (p->out_used[j]) VBH_CUDA(cudaStreamWaitEvent(h->stream, p->e_out[j], 0));
