@@ -986,6 +986,19 @@ def stream_point(torch, cam, D, poses, flush, args, base_ms):
     base = run(False)
     so = run(True)
     blocks = so["blocks"]
+    # the host link's own device -> pinned host copy rate (one 256 MiB copy, best of 3)
+    src = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    dst = torch.empty(256 << 20, dtype=torch.uint8, pin_memory=True)
+    link = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        link.append((256 << 20) / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del src, dst
+    copy_gbs = blocks * 4104 / so["span_s"] / 1e9
     return {"frames": f"{STREAM_FIRST}..{STREAM_FIRST + STREAM_FRAMES - 1}",
             "frames_per_s": 1e3 / so["ms"], "ms_per_step": so["ms"],
             "ms_per_step_without_stream_out": base["ms"],
@@ -994,7 +1007,8 @@ def stream_point(torch, cam, D, poses, flush, args, base_ms):
             "bytes_streamed_per_frame": blocks * 4104 / STREAM_FRAMES,
             "lost": so["lost"], "host_map_blocks": so["host"],
             "drain_after_loop_ms": so["drain_ms"],
-            "copy_GBs_over_loop_and_drain": blocks * 4104 / so["span_s"] / 1e9}
+            "copy_GBs_over_loop_and_drain": copy_gbs,
+            "host_link_d2h_GBs": max(link), "link_frac": copy_gbs / max(link)}
 
 
 def mc_replay(torch, cam, D, poses, args, n_timed):
@@ -1050,12 +1064,17 @@ def serve_stats(done, launches):
     served = [d for d in done if not (d["n_records"] == 0 and d["v_after"] == d["v_before"])]
     zero = [d for d in done if d["n_records"] == 0 and d["v_after"] == d["v_before"]]
     lat = np.array([(d["t_done_ns"] - d["t_arrival_ns"]) / 1e6 for d in served] or [0.0])
+    # arrival -> admission (waiting to be taken) and admission -> completion seen (service)
+    wait = np.array([(d["t_admit_ns"] - d["t_arrival_ns"]) / 1e6 for d in served] or [0.0])
+    svc = np.array([(d["t_done_ns"] - d["t_admit_ns"]) / 1e6 for d in served] or [0.0])
     zl = np.array([(d["t_done_ns"] - d["t_arrival_ns"]) / 1e6 for d in zero] or [0.0])
     recs = int(sum(d["n_records"] for d in done))
     span = (max(d["t_done_ns"] for d in done) - min(d["t_arrival_ns"] for d in done)) / 1e9
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "p999_ms": float(np.percentile(lat, 99.9)), "mean_ms": float(lat.mean()),
             "max_ms": float(lat.max()), "served_requests": len(served),
+            "admit_wait_p50_ms": float(np.percentile(wait, 50)),
+            "service_p50_ms": float(np.percentile(svc, 50)),
             "zero_work_requests": len(zero), "zero_work_p50_ms": float(np.percentile(zl, 50)),
             "blocks_per_s": recs / span, "records": recs, "requests_done": len(done),
             "launches": int(launches),
@@ -1132,7 +1151,7 @@ def serve_point(torch, cam, D, poses, peak, duration_s=3.0, n_clients=64, rate=2
             vol.close()
             torch.cuda.synchronize()
     stats = ("p50_ms", "p99_ms", "p999_ms", "mean_ms", "max_ms", "blocks_per_s",
-             "served_per_launch", "zero_work_p50_ms")
+             "served_per_launch", "zero_work_p50_ms", "admit_wait_p50_ms", "service_p50_ms")
     for name, _ in arms:
         rs = runs[name]
         res = dict(rs[0])

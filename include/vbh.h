@@ -577,7 +577,9 @@ vbh_status vbh_serve_loop_start(vbh_serve* s, const vbh_serve_loop_config* cfg,
 vbh_status vbh_serve_loop_submit(vbh_serve_loop* L, uint32_t client, uint64_t t_arrival_ns,
                                  uint32_t* id_host);
 /* Completions published since the last poll (at most cap; t_done_ns = when this poll saw
- * them; t_admit_ns = 0: admission happens on the device). */
+ * them; admission happens on the device, so t_admit_ns = t_done_ns minus the GPU timer's
+ * interval from the request's admission to its publication, at least t_arrival_ns; a request
+ * completed without work at admission has t_admit_ns = t_done_ns). */
 vbh_status vbh_serve_loop_poll(vbh_serve_loop* L, vbh_serve_done* out_host, uint32_t cap,
                                uint32_t* n_host);
 /* A completed request's records (device pointers into the stream buffer, valid until it is

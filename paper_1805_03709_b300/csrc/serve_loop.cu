@@ -62,7 +62,8 @@ struct LoopDone {
   unsigned int id, client, n_records, flags;
   unsigned int v0, v1, region, cap;
   unsigned long long off;
-  unsigned int tok, pad;
+  unsigned int tok;
+  unsigned int dev_ns;   // GPU timer from admission to publication (saturating)
 };
 // Words the host writes.
 struct LoopHostIn {
@@ -90,6 +91,7 @@ struct ReqSlot {            // a request in flight (its bit clear in free_mask)
   unsigned int rec_count;      // atomic (workers)
   unsigned int err;            // atomic (workers)
   unsigned long long off;      // byte offset of its region in the stream buffer
+  unsigned long long t_adm;    // GPU timer at admission
 };
 
 struct Chunk {
@@ -208,7 +210,7 @@ __device__ __forceinline__ bool live_cg(const TableView& t, unsigned long long k
 __device__ void publish_done(const LoopArgs& A, unsigned int id, unsigned int client,
                              unsigned int n, unsigned int flags, unsigned int v0,
                              unsigned int v1, unsigned int region, unsigned int cap,
-                             unsigned long long off) {
+                             unsigned long long off, unsigned int dev_ns = 0u) {
   const unsigned int d = atomicAdd(&A.d->done_count, 1u);
   LoopDone* D = A.done_ring + (d & A.ring_mask);
   volatile unsigned int* w = reinterpret_cast<volatile unsigned int*>(D);
@@ -222,6 +224,7 @@ __device__ void publish_done(const LoopArgs& A, unsigned int id, unsigned int cl
   w[7] = cap;
   w[8] = (unsigned int)off;
   w[9] = (unsigned int)(off >> 32);
+  w[11] = dev_ns;
   __threadfence_system();
   st_rel_sys(&D->tok, d + 1u);
 }
@@ -241,7 +244,9 @@ __device__ void complete_request(const LoopArgs& A, unsigned int si) {
   if (ef & kErrCap) flags |= VBH_SERVE_ERR_CAPACITY;
   vstore(&A.client_v[client], v1);
   atomicAdd(&A.d->records_served, (unsigned long long)nr);
-  publish_done(A, id, client, nr, flags, v0, v1, region, cap, off);
+  const unsigned long long dt = globaltimer() - vload(&R->t_adm);
+  publish_done(A, id, client, nr, flags, v0, v1, region, cap, off,
+               dt < 0xFFFFFFFFull ? (unsigned int)dt : 0xFFFFFFFFu);
   __threadfence();
   vstore(&A.client_busy[client], 0u);   // the client and the slot are free for the scheduler
   atomicOr(&A.d->free_mask, 1ull << si);
@@ -540,6 +545,7 @@ __device__ void scheduler(const LoopArgs& A, unsigned int* sm) {
                 R.chunks_done = 0u;
                 R.rec_count = 0u;
                 R.err = 0u;
+                R.t_adm = globaltimer();
                 s_next[si] = scan ? 0u : v;
                 s_hi[si] = scan ? A.max_blocks : v + (unsigned int)count;
                 work |= 1ull << si;
@@ -794,6 +800,7 @@ struct vbh_serve_loop {
       r.flags = D.flags;
       r.v0 = D.v0;
       r.v1 = D.v1;
+      r.dev_ns = D.dev_ns;
       r.region = D.region;
       r.cap = D.cap;
       r.off = D.off;
@@ -806,12 +813,15 @@ struct vbh_serve_loop {
       o.v_after = r.v1;
       o.n_records = r.n_records;
       o.flags = r.flags;
-      o.t_admit_ns = 0;
       o.t_done_ns = loop_now_ns();
+      // admission in the host's clock: completion seen minus the GPU's time from admission
+      // to publication (the two clocks are not compared)
+      o.t_admit_ns = o.t_done_ns - r.dev_ns;
       o.bytes_reserved = r.region == 0xFFFFFFFFu ? 0ull
                                                  : (((uint64_t)r.cap * kRecAll + 255u) & ~255ull);
       if (it != reqs.end()) {
         o.t_arrival_ns = it->second.t_arrival;
+        if (o.t_admit_ns < o.t_arrival_ns) o.t_admit_ns = o.t_arrival_ns;
         it->second.done = true;
         it->second.rec = r;
       }
