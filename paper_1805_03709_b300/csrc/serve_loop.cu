@@ -57,6 +57,13 @@ constexpr unsigned int kStageBlocks = 16u;    // blocks a worker copies at once
 struct LoopReq {
   unsigned int id, client;
 };
+// A request slot of the host -> device ring: one 64-bit word, the request's tag (its id) in
+// the high half and its client in the low half, written by the host in one store.  Tags run
+// 1, 2, .., 0x7FFFFFFF, 1, ..: the slot of the next request holds the next tag once it is
+// written, so one read both finds and fetches it (no separate tail to read first).
+__host__ __device__ __forceinline__ unsigned int next_tag(unsigned int t) {
+  return t == 0x7FFFFFFFu ? 1u : t + 1u;
+}
 // Device -> host (mapped host memory); tok = completion number + 1, written last.
 struct LoopDone {
   unsigned int id, client, n_records, flags;
@@ -67,7 +74,7 @@ struct LoopDone {
 };
 // Words the host writes.
 struct LoopHostIn {
-  unsigned int req_tail;    // requests written
+  unsigned int req_tail;    // requests written (for inspection; the loop reads the slots)
   unsigned int rel_tail;    // releases written
   unsigned int done_read;   // completions consumed
   unsigned int beat;        // changes on every host call (sign of life)
@@ -129,7 +136,7 @@ struct LoopArgs {
   LoopReq* pend;                    // device pending queue (ring entries)
   unsigned int* client_busy;
   // mapped host memory (device pointers)
-  const LoopReq* req_ring;
+  const unsigned long long* req_ring;
   const unsigned int* rel_ring;
   LoopDone* done_ring;
   const LoopHostIn* hin;
@@ -155,6 +162,11 @@ __device__ __forceinline__ unsigned int ld_acq_sys(const unsigned int* p) {
 __device__ __forceinline__ unsigned int ld_sys(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_sys64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_rel_sys(unsigned int* p, unsigned int v) {
@@ -418,6 +430,8 @@ __device__ void scheduler(const LoopArgs& A, unsigned int* sm) {
   unsigned int* s_next = sm;                   // next change record to chunk, per slot
   unsigned int* s_hi = sm + kLoopMaxSlots;     // end of the slot's range
   unsigned int req_head = 0u, rel_head = 0u, pend_head = 0u, pend_tail = 0u;
+  unsigned int tag = 1u;         // tag of the next request
+  unsigned int done_read = 0u;   // completions the host has consumed, as last read
   unsigned int chunk_low = 0u, chunk_tail = 0u, head_blocked = 0u, max_active = 0u;
   unsigned long long end_tile = 0ull, work = 0ull;   // work: slots with chunks left
   unsigned long long scanned = 0ull, chunks = 0ull, rounds = 0ull, deferred = 0ull, peak = 0ull;
@@ -460,27 +474,32 @@ __device__ void scheduler(const LoopArgs& A, unsigned int* sm) {
         a.r_tail += 1u;
       }
     }
-    // new requests into the pending queue (arrival order)
-    const unsigned int qt = ld_acq_sys(&A.hin->req_tail);
-    if (req_head != qt) {
-      while (req_head != qt && pend_tail - pend_head <= A.ring_mask) {
-        const unsigned int* e =
-            reinterpret_cast<const unsigned int*>(A.req_ring + (req_head & A.ring_mask));
-        LoopReq q;
-        q.id = ld_sys(e);
-        q.client = ld_sys(e + 1);
-        A.pend[pend_tail & A.ring_mask] = q;
+    // new requests into the pending queue (arrival order): the next two slots are read at once
+    // (one round trip over the host link when requests come one at a time or in pairs)
+    for (bool more = true; more && pend_tail - pend_head + 2u <= A.ring_mask + 1u;) {
+      const unsigned long long v0 = ld_sys64(A.req_ring + (req_head & A.ring_mask));
+      const unsigned long long v1 = ld_sys64(A.req_ring + ((req_head + 1u) & A.ring_mask));
+      more = false;
+      if ((unsigned int)(v0 >> 32) == tag) {
+        A.pend[pend_tail & A.ring_mask] = LoopReq{tag, (unsigned int)v0};
         pend_tail += 1u;
         req_head += 1u;
+        tag = next_tag(tag);
+        busy = true;
+        if ((unsigned int)(v1 >> 32) == tag) {
+          A.pend[pend_tail & A.ring_mask] = LoopReq{tag, (unsigned int)v1};
+          pend_tail += 1u;
+          req_head += 1u;
+          tag = next_tag(tag);
+          more = true;
+        }
       }
-      st_rel_sys(&A.hout->req_head, req_head);
-      busy = true;
     }
+    if (busy) st_rel_sys(&A.hout->req_head, req_head);
     // admission in arrival order at the newest published snapshot
     if (pend_head != pend_tail) {
       const unsigned int sigma = vload(&sl->seq_next) - 1u;
       fence_acq_rel_gpu();
-      const unsigned int done_read = ld_sys(&A.hin->done_read);
       unsigned long long free = vload(&d->free_mask) & all_slots;
       unsigned int w = pend_head;
       bool head = true, stop_adm = false, admitted = false;
@@ -489,7 +508,11 @@ __device__ void scheduler(const LoopArgs& A, unsigned int* sm) {
         bool keep = true;
         if (!stop_adm) {
           const unsigned int active = A.n_slots - __popcll(free);
-          const unsigned int outstanding = vload(&d->done_count) - done_read;
+          unsigned int outstanding = vload(&d->done_count) - done_read;
+          if (outstanding + active + 1u > A.ring_mask + 1u) {   // read the host's count again
+            done_read = ld_sys(&A.hin->done_read);
+            outstanding = vload(&d->done_count) - done_read;
+          }
           if (outstanding + active + 1u > A.ring_mask + 1u) {
             stop_adm = true;   // no completion-ring room for one more
           } else if (q.client >= A.n_clients) {   // never written by the library's host side
@@ -762,7 +785,7 @@ struct vbh_serve_loop {
   LoopReq* pend = nullptr;
   unsigned int* client_busy = nullptr;
   // mapped host memory
-  LoopReq* req_ring = nullptr;
+  unsigned long long* req_ring = nullptr;
   unsigned int* rel_ring = nullptr;
   LoopDone* done_ring = nullptr;
   LoopHostIn* hin = nullptr;
@@ -983,15 +1006,14 @@ vbh_status vbh_serve_loop_submit(vbh_serve_loop* L, uint32_t client, uint64_t t_
   if (L->exited()) return L->stopped_status();
   const uint32_t head = reinterpret_cast<volatile unsigned int*>(&L->hout->req_head)[0];
   if (L->req_tail - head >= L->ring) return fail(VBH_ERR_CAPACITY, "request ring full");
-  const uint32_t rid = L->next_id++;
-  if (L->next_id == 0) L->next_id = 1;
-  volatile unsigned int* e =
-      reinterpret_cast<volatile unsigned int*>(L->req_ring + (L->req_tail & (L->ring - 1u)));
-  e[0] = rid;
-  e[1] = client;
+  const uint32_t rid = L->next_id;
+  L->next_id = next_tag(L->next_id);
   auto& inf = L->reqs[rid];
   inf.client = client;
   inf.t_arrival = t_arrival_ns ? t_arrival_ns : loop_now_ns();
+  // the whole request in one aligned 64-bit store: the loop reads it in one load
+  reinterpret_cast<volatile unsigned long long*>(L->req_ring)[L->req_tail & (L->ring - 1u)] =
+      (unsigned long long)rid << 32 | client;
   std::atomic_thread_fence(std::memory_order_release);
   L->req_tail += 1u;
   reinterpret_cast<volatile unsigned int*>(&L->hin->req_tail)[0] = L->req_tail;
