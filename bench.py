@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--hash-only", action="store_true",
                     help="profiling case: only the hash point (prefill, then 3 mixed 2^20-op "
                          "batches, the first untimed) and its clustered mode; prints its dict")
+    ap.add_argument("--hash-batch", type=int, default=1 << 20,
+                    help="ops per batch of the --hash-only point (at most 2^16: batches back to "
+                         "back, no clustered mode)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tri", action="store_true",
@@ -347,8 +350,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dev = torch.device("cuda", local_rank)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-        pt = hash_point(torch, dev, flush, measured_peak()[0], n_batches=3, n_warm=1)
-        pt["clustered"] = hash_clustered_point(torch, dev, flush, n_batches=3)
+        pt = hash_point(torch, dev, flush, measured_peak()[0], n=args.hash_batch, n_batches=3,
+                        n_warm=1)
+        if args.hash_batch > 1 << 16:
+            pt["clustered"] = hash_clustered_point(torch, dev, flush, n_batches=3)
         print(json.dumps(pt))
         return
     # The clock sampler starts before any CUDA work: an nvidia-smi that first queries the GPU
