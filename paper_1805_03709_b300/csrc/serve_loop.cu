@@ -44,14 +44,28 @@ namespace vbh {
 
 namespace {
 
-constexpr int kLoopThreads = 256;
+// One CTA per SM of 8 warps, each copying 16 blocks at a time (64 KB of staging per CTA).  The
+// frames' kernels must find room beside the loop: with the smallest shared-memory configuration
+// that holds a larger loop CTA, a frame kernel's CTA did not fit and the frames waited for the
+// loop to end (12 warps x 8 blocks looked faster only because the frames were kept out).
+#ifndef VBH_LOOP_THREADS
+#define VBH_LOOP_THREADS 256
+#endif
+constexpr int kLoopThreads = VBH_LOOP_THREADS;
+#ifndef VBH_LOOP_CARVEOUT
+#define VBH_LOOP_CARVEOUT -1
+#endif
+constexpr int kLoopCarveout = VBH_LOOP_CARVEOUT;   // % of the SM's shared memory (-1: driver's choice)
 constexpr int kLoopWarps = kLoopThreads / 32;
 constexpr unsigned int kLoopMaxSlots = 64u;
 constexpr unsigned int kChunkRing = 1024u;    // chunks published and not yet finished
 constexpr unsigned int kRegionRing = 8192u;   // stream-buffer regions not yet released
 constexpr unsigned int kRecHdr = 16u, kRecPay = 512u, kRecAll = 528u;
 constexpr unsigned int kErrOverrun = 2u, kErrCap = 4u;   // as kServeErr* (serve.cu)
-constexpr unsigned int kStageBlocks = 16u;    // blocks a worker copies at once
+#ifndef VBH_LOOP_STAGE_BLOCKS
+#define VBH_LOOP_STAGE_BLOCKS 16
+#endif
+constexpr unsigned int kStageBlocks = VBH_LOOP_STAGE_BLOCKS;   // blocks a worker copies at once
 
 // Host -> device (mapped host memory).
 struct LoopReq {
@@ -914,6 +928,10 @@ vbh_status vbh_serve_loop_start(vbh_serve* s, const vbh_serve_loop_config* cfg_i
   int occ = 0;
   VBH_CUDA(cudaFuncSetAttribute(k_serve_loop, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kStageBytes));
+  // a preferred shared-memory share for the SMs the loop occupies (default: the driver's choice)
+  if (kLoopCarveout >= 0)
+    VBH_CUDA(cudaFuncSetAttribute(k_serve_loop, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  kLoopCarveout));
   VBH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve_loop, kLoopThreads,
                                                          kStageBytes));
   if (c.ctas > (uint32_t)(occ * h->L.sms))
