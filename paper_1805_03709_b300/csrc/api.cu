@@ -429,7 +429,7 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   h->batch_parity ^= 1u;
   if (small) {
     VBH_CUDA(launch_hash_batch_small(h->L, t, h->cnt, ops_dev, keys3_dev, vals_dev, results_dev,
-                                     status_dev, n, h->blists.n_next));
+                                     status_dev, n, h->blists.n_next, &h->gbar_base));
     h->launches += 1;
   } else {
     launch_hash_find(h->L, t, h->cnt, ops_dev, keys3_dev, results_dev, status_dev, n,

@@ -110,6 +110,7 @@ struct vbh_handle {
   int graph_timed = 0;             // stage mask the captured graph brackets with events
   uint32_t integ_mode = 0;         // VBH_INTEGRATE_*
   uint32_t wait_limit = 1u << 24;  // polls of the fusion kernel's bounded copy wait
+  uint32_t gbar_base = 0;          // small-batch barrier arrivals so far (the device counter's value)
   bool serve_loop_active = false;  // a device-resident serving loop reads the table: no rebuild
   uint32_t graph_mode = 0;         // integration mode the frame graph was captured with
   uint64_t graph_kernels = 0;

@@ -537,28 +537,25 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
 //      barrier, and an erase leaves the value field alone), and the erases run.
 // Results, statuses and counters are those of the phased launches.  A barrier waits at most
 // ~1 s (GPU global timer); one that gives up raises the sticky timeout flag and lets its CTA go.
-__device__ __forceinline__ void grid_barrier(DevCounters* cnt) {
+// Grid barrier on a counter that only grows: every CTA adds one on arrival (no reply waited
+// for) and waits until the counter reaches `target` (the count before this launch, which the
+// host keeps, plus the CTAs x the barriers so far), so the last arrival releases the others
+// without a second round trip.
+__device__ __forceinline__ void grid_barrier(DevCounters* cnt, unsigned int target) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = &cnt->gbar_gen;
-    const unsigned int g = *gen;
-    __threadfence();
-    if (atomicAdd(&cnt->gbar_arrive, 1u) == gridDim.x - 1u) {
-      cnt->gbar_arrive = 0u;
-      __threadfence();
-      atomicAdd(&cnt->gbar_gen, 1u);
-    } else {
-      unsigned long long t0;
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-      for (;;) {
-        if (*gen != g) break;
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > 1000000000ull) {
-          atomicOr(&cnt->err, kErrTimeout);
-          break;
-        }
-        __nanosleep(32);
+    __threadfence();   // the CTA's writes before its arrival
+    atomicAdd(&cnt->gbar_arrive, 1u);
+    volatile unsigned int* c = &cnt->gbar_arrive;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while ((int)(*c - target) < 0) {
+      __nanosleep(20);
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 1000000000ull) {
+        atomicOr(&cnt->err, kErrTimeout);
+        break;
       }
     }
     __threadfence();
@@ -573,6 +570,9 @@ __device__ __forceinline__ void grid_barrier(DevCounters* cnt) {
 // as their longest walk (at load 0.7 a miss reads ~1.7 buckets on average, the longest of 2^16
 // walks ten or more); phased batches of many ops are bound by bandwidth and load one at a time.
 constexpr int kSmallProbes = VBH_SMALL_BATCH_PROBES;
+#ifndef VBH_SMALL_PDL
+#define VBH_SMALL_PDL 1   // launch small batches with programmatic stream serialisation
+#endif
 
 __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounters* cnt,
                                                           const unsigned char* ops,
@@ -580,7 +580,14 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
                                                           const unsigned int* vals,
                                                           unsigned int* res, unsigned char* st,
                                                           unsigned int n,
-                                                          unsigned int* lists_next) {
+                                                          unsigned int* lists_next,
+                                                          unsigned int bar_base) {
+#if VBH_SMALL_PDL
+  // launched with programmatic serialisation: everything the previous grid in the stream wrote
+  // is visible after this wait; the next batch's launch may start now (it waits likewise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
   // inserts won, won from EMPTY, won from a tombstone, error bits; erased, erased to EMPTY
   __shared__ unsigned int sh[6];
   const unsigned int i = blockIdx.x * kThreads + threadIdx.x;
@@ -614,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
       asm volatile("prefetch.global.L2 [%0];" ::"l"(b));
     }
   }
-  grid_barrier(cnt);
+  grid_barrier(cnt, bar_base + gridDim.x);
 
   int outcome = 0;
   unsigned int pos = kNone;
@@ -640,7 +647,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
     if (n_emp) atomicAdd(&sh[1], n_emp);
     if (n_won > n_emp) atomicAdd(&sh[2], n_won - n_emp);
   }
-  grid_barrier(cnt);
+  grid_barrier(cnt, bar_base + 2u * gridDim.x);
 
   if (outcome == kExists) {
     res[i] = __ldcg(&t.slots[pos].val);
@@ -831,12 +838,25 @@ bool small_batch_fits(const Launch& L, unsigned int n) {
 cudaError_t launch_hash_batch_small(const Launch& L, TableView t, DevCounters* cnt,
                                     const unsigned char* ops, const int* keys3,
                                     const unsigned int* vals, unsigned int* res,
-                                    unsigned char* st, unsigned int n, unsigned int* lists_next) {
+                                    unsigned char* st, unsigned int n, unsigned int* lists_next,
+                                    unsigned int* bar_base) {
   if (!small_batch_fits(L, n)) return cudaErrorInvalidValue;
   const unsigned int grid = (n + kThreads - 1u) / kThreads;   // one thread per op
-  void* args[] = {&t, &cnt, &ops, &keys3, &vals, &res, &st, &n, &lists_next};
-  return cudaLaunchCooperativeKernel((const void*)k_batch_small, dim3(grid), dim3(kThreads),
-                                     args, 0, L.stream);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = L.stream;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = VBH_SMALL_PDL ? 2 : 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_small, t, cnt, ops, keys3, vals, res,
+                                           st, n, lists_next, *bar_base);
+  if (e == cudaSuccess) *bar_base += 2u * grid;   // the counter after the launch's two barriers
+  return e;
 }
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt) {

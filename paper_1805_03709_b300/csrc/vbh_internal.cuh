@@ -73,7 +73,8 @@ struct DevCounters {
   unsigned long long tot_new;
   unsigned long long tot_written;
   unsigned long long tot_frames;
-  unsigned int gbar_arrive, gbar_gen;   // grid barrier of the fused small-batch kernel
+  unsigned int gbar_arrive;   // arrivals at the small-batch kernel's grid barriers (only grows)
+  unsigned int gbar_unused;
 };
 
 struct TableView {
@@ -460,7 +461,8 @@ bool small_batch_fits(const Launch& L, unsigned int n);   // n ops fit one resid
 cudaError_t launch_hash_batch_small(const Launch& L, TableView t, DevCounters* cnt,
                                     const unsigned char* ops, const int* keys3,
                                     const unsigned int* vals, unsigned int* res,
-                                    unsigned char* st, unsigned int n, unsigned int* lists_next);
+                                    unsigned char* st, unsigned int n, unsigned int* lists_next,
+                                    unsigned int* bar_base);
 void launch_rebuild(const Launch& L, TableView t, const Slot* shadow, unsigned int n_slots,
                     DevCounters* cnt);
 void launch_dump_table(const Launch& L, TableView t, unsigned int n_slots,
