@@ -301,7 +301,8 @@ def test_voxel_block_map_pool_indices():
 @pytest.mark.parametrize("lf", [0.7, 0.9])
 def test_full_size_table_batch_2e20(lf):
     """2^22 buckets x 4 slots, prefilled to load factor lf with uniform keys in [-2^20, 2^20)^3,
-    then a 2^20-op batch (50 % find half hits, 30 % insert of absent keys, 20 % erase)."""
+    then a 2^20-op batch (50 % find half hits, 30 % insert of absent keys, 20 % erase), then
+    2^16-, 2^12- and 2^16-op batches of the same mix."""
     n_buckets = 1 << 22
     cap = n_buckets * 4
     n_pre = int(lf * cap)
@@ -328,3 +329,20 @@ def test_full_size_table_batch_2e20(lf):
     assert_same(ops, keys, rg, sg, ro, so)
     c = hm.counters()
     assert c.live == len(om)
+    # then batches of 2^16 and 2^12 ops (one cooperative launch each, one thread per op), the
+    # sizes the small-batch measurement times, on the same full-size table
+    for m in (1 << 16, 1 << 12, 1 << 16):
+        mf, mi = m // 2, int(0.3 * m)
+        me = m - mf - mi
+        k2 = np.concatenate([pre[rng.integers(0, n_pre, mf // 2)],
+                             fresh[rng.integers(0, len(fresh), mf - mf // 2)],
+                             synth.random_hash_keys(mi, seed=int(rng.integers(1 << 30))),
+                             pre[rng.integers(0, n_pre, me)]])
+        o2 = np.concatenate([np.zeros(mf), np.ones(mi), np.full(me, 2)]).astype(np.uint8)
+        p2 = rng.permutation(m)
+        k2, o2 = k2[p2], o2[p2]
+        v2 = key_value(k2)
+        rg, sg = gpu_batch(hm, o2, k2, v2)
+        ro, so = om.batch(o2, k2, v2)
+        assert_same(o2, k2, rg, sg, ro, so)
+        assert hm.counters().live == len(om)
