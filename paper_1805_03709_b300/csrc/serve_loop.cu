@@ -62,6 +62,9 @@ constexpr unsigned int kChunkRing = 1024u;    // chunks published and not yet fi
 constexpr unsigned int kRegionRing = 8192u;   // stream-buffer regions not yet released
 constexpr unsigned int kRecHdr = 16u, kRecPay = 512u, kRecAll = 528u;
 constexpr unsigned int kErrOverrun = 2u, kErrCap = 4u;   // as kServeErr* (serve.cu)
+#ifndef VBH_LOOP_MAX_NAP
+#define VBH_LOOP_MAX_NAP 2048u   // longest sleep (ns) between a waiting worker's polls
+#endif
 #ifndef VBH_LOOP_STAGE_BLOCKS
 #define VBH_LOOP_STAGE_BLOCKS 16
 #endif
@@ -708,7 +711,7 @@ __device__ void worker(const LoopArgs& A, uint4* stage) {
           break;
         }
         __nanosleep(nap);
-        if (nap < 2048u) nap *= 2u;
+        if (nap < VBH_LOOP_MAX_NAP) nap *= 2u;
       }
     }
     state = __shfl_sync(0xFFFFFFFFu, state, 0);
@@ -716,27 +719,30 @@ __device__ void worker(const LoopArgs& A, uint4* stage) {
     if (state) return;
     fence_acq_rel_gpu();
     // the chunk holding ticket t: the last published chunk whose first ticket is <= t (ring
-    // positions reused by newer chunks belong to chunks older than every unfinished one)
+    // positions reused by newer chunks belong to chunks older than every unfinished one);
+    // chunk c qualifies when its position holds an older chunk or it starts at or before t
+    auto qualifies = [&](unsigned int x) {
+      const Chunk& m = A.chunks[x % kChunkRing];
+      return vload(&m.idx) != x || vload(&m.start_tile) <= t;
+    };
+    unsigned int hi = 0u;
+    if (lane == 0u) hi = vload(&d->chunk_tail);
+    hi = __shfl_sync(0xFFFFFFFFu, hi, 0);
+    unsigned int lo = hi > kChunkRing ? hi - kChunkRing : 0u;
+    if (hint > lo) lo = hint;
+    // the 32 newest candidates at once, one per lane (a waiting worker's tile was published in
+    // the last rounds): the newest qualifying one; else a binary search below them
+    const bool cand = lane < hi - lo;
+    const unsigned int found = __ballot_sync(0xFFFFFFFFu, cand && qualifies(hi - 1u - lane));
     unsigned int c = 0u;
-    if (lane == 0u) {
-      const unsigned int hi = vload(&d->chunk_tail);
-      unsigned int lo = hi > kChunkRing ? hi - kChunkRing : 0u;
-      if (hint > lo) lo = hint;
-      // chunk c qualifies when its position holds an older chunk or it starts at or before t;
-      // forward from the previous chunk (usually one or two steps), else a binary search
-      auto qualifies = [&](unsigned int x) {
-        const Chunk& m = A.chunks[x % kChunkRing];
-        return vload(&m.idx) != x || vload(&m.start_tile) <= t;
-      };
-      if (hi - lo <= 8u) {
-        while (lo + 1u < hi && qualifies(lo + 1u)) ++lo;
-      } else {
-        unsigned int top = hi;
-        while (top - lo > 1u) {   // invariant: chunk lo qualifies, chunk top does not
-          const unsigned int mid = lo + (top - lo) / 2u;
-          if (qualifies(mid)) lo = mid;
-          else top = mid;
-        }
+    if (found) {
+      c = hi - 1u - (unsigned int)(__ffs(found) - 1);
+    } else if (lane == 0u) {   // only when more than 32 chunks lie above the hint
+      unsigned int top = hi - 32u;
+      while (top - lo > 1u) {   // invariant: chunk lo qualifies, chunk top does not
+        const unsigned int mid = lo + (top - lo) / 2u;
+        if (qualifies(mid)) lo = mid;
+        else top = mid;
       }
       c = lo;
     }
