@@ -74,7 +74,6 @@ struct DevCounters {
   unsigned long long tot_written;
   unsigned long long tot_frames;
   unsigned int gbar_arrive;   // arrivals at the small-batch kernel's grid barriers (only grows)
-  unsigned int gbar_unused;
 };
 
 struct TableView {
