@@ -33,13 +33,24 @@ constexpr int kThreads = 256;
 // outcome codes of thread_insert
 constexpr int kInserted = 1, kExists = 2, kFull = 3;
 
+// An insert in two passes.  Pass 1 (insert_walk, reads only) walks the whole chain to be sure
+// the key is absent and notes the first free slot (tombstone or EMPTY) and the bucket it ended
+// on; pass 2 (insert_claim) claims free slots in probe order from there with a 64-bit CAS.  A
+// launch that writes nothing between the two passes may run them on either side of a barrier.
+struct InsertWalk {
+  unsigned int first_free, held;
+  ulonglong2 s[4];   // the bucket pass 1 ended on
+};
+
+// Pass 1: kExists (the key is in the table: *pos_out, *val_out), kFull (no free slot on its
+// sequence) or 0 (absent; claim next).
 template <int W = 1>
-__device__ int thread_insert(const TableView& t, unsigned long long key, unsigned int* pos_out,
-                             unsigned long long* observed_out) {
+__device__ int insert_walk(const TableView& t, unsigned long long key, unsigned int* pos_out,
+                           unsigned int* val_out, InsertWalk& wk) {
   const unsigned int b0 = home_bucket(key, t.bmask, t.hash_fn);
   const unsigned int step = probe_step(key);
   unsigned int first_free = kNone, held = kNone;
-  ulonglong2 s[4];   // the bucket pass 1 ended on
+  ulonglong2 (&s)[4] = wk.s;   // the bucket pass 1 ended on
   // pass 1: the whole chain, to be sure the key is absent
   if constexpr (W == 1) {
     unsigned int b = b0;
@@ -56,6 +67,7 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
       }
       if (hit >= 0) {
         *pos_out = 4u * b + hit;
+        *val_out = (unsigned)bucket_slot(s, hit).y;
         return kExists;
       }
       if (first_free == kNone && f >= 0) first_free = 4u * b + f;
@@ -73,7 +85,7 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
       load_bucket<false>(&t.slots[4u * bb[w]], g[w]);
     }
     bool stop = false;
-    unsigned int hit_pos = kNone;
+    unsigned int hit_pos = kNone, hit_val = kNone;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       bool empty = false;
@@ -88,6 +100,7 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
       if (live) {
         if (hit >= 0) {
           hit_pos = 4u * bb[w] + hit;
+          hit_val = (unsigned)bucket_slot(g[w], hit).y;
         } else {
           if (first_free == kNone && f >= 0) first_free = 4u * bb[w] + f;
           if (empty) {
@@ -101,16 +114,27 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
     }
     if (hit_pos != kNone) {
       *pos_out = hit_pos;
+      *val_out = hit_val;
       return kExists;
     }
     if (stop) break;
   }
   }
-  if (first_free == kNone) return kFull;
+  wk.first_free = first_free;
+  wk.held = held;
+  return first_free == kNone ? kFull : 0;
+}
+
+// Pass 2: kInserted (*pos_out, *observed_out: the slot's previous content), kExists (another
+// insert of the key claimed first: *pos_out) or kFull.
+__device__ int insert_claim(const TableView& t, unsigned long long key, InsertWalk& wk,
+                            unsigned int* pos_out, unsigned long long* observed_out) {
   // pass 2: claim in probe order starting at the first free slot.  The bucket pass 1 ended on
   // is reused for the first attempt: a stale copy only costs a failed CAS and a re-read.
-  unsigned int b = first_free >> 2;
-  bool have = b == held;
+  const unsigned int step = probe_step(key);
+  ulonglong2 (&s)[4] = wk.s;
+  unsigned int b = wk.first_free >> 2;
+  bool have = b == wk.held;
   for (unsigned int steps = 0; steps <= t.bmask;) {
     if (!have) load_bucket<false>(&t.slots[4u * b], s);
     have = false;
@@ -143,6 +167,15 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
     // another key took the slot: look at the same bucket again
   }
   return kFull;
+}
+
+template <int W = 1>
+__device__ int thread_insert(const TableView& t, unsigned long long key, unsigned int* pos_out,
+                             unsigned long long* observed_out) {
+  InsertWalk wk;
+  unsigned int val;
+  const int r = insert_walk<W>(t, key, pos_out, &val, wk);
+  return r ? r : insert_claim(t, key, wk, pos_out, observed_out);
 }
 
 // ---------------------------------------------------------------------------- batch compaction
@@ -530,9 +563,11 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
 // that keeps its op and key in registers, so there are no op lists, and three phases separated
 // by two grid barriers:
 //   1. every op is read and checked; the finds run (nothing writes the table yet, so they see
-//      it as the batch found it), and the inserts and erases prefetch the first buckets of
-//      their probe sequences to L2;
-//   2. the inserts claim their slots; a winner writes its value and its final result;
+//      it as the batch found it), so do the inserts' read-only walks (a key already in the
+//      table gets its final result here), and the erases prefetch the first buckets of their
+//      probe sequences to L2;
+//   2. the inserts of absent keys claim their slots from where their walks ended; a winner
+//      writes its value and its final result;
 //   3. the inserts that met their key read its value (every winner wrote its value before the
 //      barrier, and an erase leaves the value field alone), and the erases run.
 // Results, statuses and counters are those of the phased launches.  A barrier waits at most
@@ -608,12 +643,28 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
       kind = op;
     }
   }
+  // an insert's walk reads only, so it runs here beside the finds; the table does not change
+  // before its claim in the next phase
+  InsertWalk wk;
+  int outcome = 0;
+  unsigned int pos = kNone;
   if (kind == kOpFind) {
     unsigned int val;
     const bool hit = thread_find<false, kSmallProbes>(t, key, &val) != kNone;
     res[i] = hit ? val : kNone;
     st[i] = hit ? kStFound : kStNotFound;
-  } else if (kind >= 0) {
+  } else if (kind == kOpInsert) {
+    unsigned int val = kNone;
+    outcome = insert_walk<kSmallProbes>(t, key, &pos, &val, wk);
+    if (outcome == kExists) {   // in the table before the batch: its value is final
+      res[i] = val;
+      st[i] = kStExists;
+    } else if (outcome == kFull) {
+      res[i] = kNone;
+      st[i] = kStCapacity;
+      atomicOr(&sh[3], kErrTable);
+    }
+  } else if (kind == kOpErase) {
     const unsigned int b0 = home_bucket(key, t.bmask, t.hash_fn), step = probe_step(key);
 #pragma unroll
     for (int w = 0; w < kSmallProbes; ++w) {
@@ -623,11 +674,11 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
   }
   grid_barrier(cnt, bar_base + gridDim.x);
 
-  int outcome = 0;
-  unsigned int pos = kNone;
   unsigned long long observed = 0;
-  if (kind == kOpInsert) {
-    outcome = thread_insert<kSmallProbes>(t, key, &pos, &observed);
+  bool pending = false;   // met its key claimed by another insert of this batch: value next phase
+  if (kind == kOpInsert && outcome == 0) {
+    outcome = insert_claim(t, key, wk, &pos, &observed);
+    pending = outcome == kExists;
     if (outcome == kInserted) {
       const unsigned int v = vals ? vals[i] : 0u;
       t.slots[pos].val = v;
@@ -649,7 +700,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_small(TableView t, DevCounte
   }
   grid_barrier(cnt, bar_base + 2u * gridDim.x);
 
-  if (outcome == kExists) {
+  if (pending) {
     res[i] = __ldcg(&t.slots[pos].val);
     st[i] = kStExists;
   }
