@@ -596,7 +596,9 @@ def main():
                               (0.7, 1 << 16, 24, 4), (0.7, 1 << 22, 4, 1)):
             r = hash_point(torch, dev, flush, peak, lf=lf, n=n, n_batches=nb, n_warm=nw)
             sweep.append({k: r[k] for k in ("load_factor", "batch", "Mops_s", "hbm_frac",
-                                            "batches_timed", "rebuilds", "timing")})
+                                            "batches_timed", "rebuilds", "timing",
+                                            "host_call_us", "device_caught_up_with_host")
+                          if k in r})
         hash_pt["sweep"] = sweep
         hash_pt["clustered"] = hash_clustered_point(torch, dev, flush)
     diff_pt = None
@@ -687,8 +689,8 @@ def hash_point(torch, dev, flush, peak, lf=0.7, n=1 << 20, n_batches=6, n_warm=2
     nf, ni = n // 2, int(0.3 * n)
     ne = n - nf - ni
     # batches of at most 2^16 ops are timed back to back (one event pair around the timed
-    # batches, no L2 flush or rebalance between them: the load drifts by < 1 %), otherwise the
-    # host's per-call time would be what is measured
+    # batches, no L2 flush or rebalance between them: the load drifts by < 1 %), all enqueued
+    # behind a GPU delay, otherwise the host's per-call time would be what is measured
     pipelined = n <= 1 << 16
     queued = []
     for b in range(n_batches):
@@ -733,15 +735,23 @@ def hash_point(torch, dev, flush, peak, lf=0.7, n=1 << 20, n_batches=6, n_warm=2
             G = torch.from_numpy(gone).to(dev)
             hm.batch(torch.full((extra,), 2, dtype=torch.uint8, device=dev), K[G].contiguous())
             alive[gone] = False
+    host_us, caught_up = None, None
     if pipelined:
         for b in range(n_warm):
             hm.batch(*queued[b])
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # a GPU delay (~10 ms) long enough for the host to enqueue every timed batch, so the
+        # events time the device work of consecutive batches and not the host's call rate;
+        # whether the device caught up with the host anyway is reported
+        torch.cuda._sleep(20_000_000)
         e0.record()
+        h0 = time.perf_counter()
         for b in range(n_warm, n_batches):
             hm.batch(*queued[b])
+        host_us = (time.perf_counter() - h0) / (n_batches - n_warm) * 1e6
+        caught_up = bool(e0.query())
         e1.record()
         torch.cuda.synchronize()
         t_ms = e0.elapsed_time(e1)
@@ -753,12 +763,17 @@ def hash_point(torch, dev, flush, peak, lf=0.7, n=1 << 20, n_batches=6, n_warm=2
     c = hm.counters()
     hm.close()
     gbs = bytes_alg / (t_ms / 1e3) / 1e9
-    return {"Mops_s": ops_done / (t_ms / 1e3) / 1e6, "load_factor": lf, "batch": n,
-            "timing": "batches back to back" if pipelined else
+    out = {"Mops_s": ops_done / (t_ms / 1e3) / 1e6, "load_factor": lf, "batch": n,
+            "timing": "batches back to back, enqueued behind a GPU delay (device time)"
+            if pipelined else
             "one batch at a time, L2 flushed, enqueued behind a GPU delay (device time)",
             "keys": "distinct, uniform in [-2^20,2^20)^3", "mix": "50/30/20 find/insert/erase",
             "algorithmic_GBs": gbs, "hbm_frac": gbs / peak, "batches_timed": n_batches - n_warm,
             "live_after": c.live, "rebuilds": c.rebuilds}
+    if pipelined:
+        out["host_call_us"] = host_us            # HashMap.batch from Python, per batch
+        out["device_caught_up_with_host"] = caught_up
+    return out
 
 
 def hash_clustered_point(torch, dev, flush, n=1 << 20, n_batches=5, n_warm=1):

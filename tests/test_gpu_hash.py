@@ -245,6 +245,34 @@ def test_erase_beside_an_empty_slot_leaves_no_tombstone():
     check_contents(hm2, om2)
 
 
+def test_small_batch_keys_at_the_top_of_the_coordinate_range():
+    """Keys at both ends of the coordinate range: the two largest keys pack to 2^63 - 1 and
+    2^63 - 2, one bit below the free-slot markers (all ones, all ones minus one).  Mixed small
+    batches of those keys, their neighbours and ordinary keys (duplicate inserts, insert and
+    erase of one key in a batch, finds of keys inserted in the same batch) give the oracle's
+    results."""
+    top = (1 << 20) - 1
+    special = np.array([[top, top, top], [top - 1, top, top]], np.int32)
+    near = np.array([[top, top - 1, top], [top - 2, top, top], [top, top, top - 1],
+                     [-(1 << 20), -(1 << 20), -(1 << 20)]], np.int32)
+    pool = np.concatenate([special, near, synth.random_hash_keys(20, seed=23)])
+    rng = np.random.default_rng(29)
+    for n_buckets in (8, 64):   # a crowded table (32 slots for 26 keys) and a roomy one
+        hm = HashMap(n_buckets=n_buckets)
+        om = OracleMap()
+        for b in range(40):
+            n = int(rng.integers(1, 48))
+            ops = rng.choice([0, 1, 2], size=n, p=[0.35, 0.4, 0.25]).astype(np.uint8)
+            keys = pool[rng.integers(0, len(pool) if b % 2 else len(special), size=n)]
+            vals = key_value(keys)
+            rg, sg = gpu_batch(hm, ops, keys, vals)
+            ro, so = om.batch(ops, keys, vals)
+            assert_same(ops, keys, rg, sg, ro, so)
+            c = hm.counters()
+            assert c.live == len(om) and c.error_flags == 0
+        check_contents(hm, om)
+
+
 @pytest.mark.parametrize("lf", [0.5, 0.7, 0.84, 0.9])
 def test_load_factor_mixed_and_rebuild(lf):
     """Mixed batches on a small table prefilled to load factor lf (long probe chains at the
