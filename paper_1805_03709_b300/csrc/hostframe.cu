@@ -3,7 +3,7 @@
 // Call k (j = k mod 3) enqueues: the depth copy host -> device buffer j on the copy-in stream
 // (after frame k-3, which read buffer j, has finished), the frame graph on the handle's stream into
 // device stream j (after frame k-3's results, read from stream j, have been copied out), and a
-// copy of frame k's two totals to pinned memory.  Then it moves the older frames along: frame
+// one-warp kernel that writes frame k's two totals to mapped pinned memory.  Then it moves the older frames along: frame
 // k-1's records and entries start their copy into the caller's host buffers if its totals have
 // already landed (no wait), and frame k-2 -- whose copy was started by now, waiting for its
 // totals only if the GPU is two frames behind -- is waited for and marked done.  So the host
@@ -15,6 +15,17 @@
 namespace vbh {
 
 constexpr int kHostSlots = 3;
+
+#ifndef VBH_HOST_TOTALS_KERNEL
+#define VBH_HOST_TOTALS_KERNEL 1
+#endif
+// A frame's two stream totals to mapped pinned host memory, written by one warp on the frame's
+// stream (a copy-engine transfer there would hand the stream to a copy engine and back after
+// every frame); visible to the host once the frame's event has completed.
+__global__ void k_frame_totals(const uint32_t* n_dev, uint32_t* n_host) {
+  if (threadIdx.x < 2u) n_host[threadIdx.x] = __ldcg(n_dev + threadIdx.x);
+  __threadfence_system();
+}
 
 struct HostPipe {
   struct Pending {
@@ -35,7 +46,8 @@ struct HostPipe {
   uint16_t* local[kHostSlots] = {};
   uint8_t* index[kHostSlots] = {};
   uint32_t* n_dev[kHostSlots] = {};
-  uint32_t* n_pin[kHostSlots] = {};
+  uint32_t* n_pin[kHostSlots] = {};       // mapped pinned host memory
+  uint32_t* n_pin_dev[kHostSlots] = {};   // its device address
   uint32_t cap_blocks = 0, cap_entries = 0;
   cudaEvent_t e_h2d[kHostSlots] = {}, e_frame[kHostSlots] = {}, e_out[kHostSlots] = {};
   bool frame_used[kHostSlots] = {}, out_used[kHostSlots] = {};
@@ -82,7 +94,12 @@ vbh_status create_pipe(vbh_handle* h) {
   for (int j = 0; j < kHostSlots; ++j) {
     VBH_CUDA(cudaMalloc(&p->depth[j], db));
     VBH_CUDA(cudaMalloc(&p->n_dev[j], 2 * sizeof(uint32_t)));
+#if VBH_HOST_TOTALS_KERNEL
+    VBH_CUDA(cudaHostAlloc((void**)&p->n_pin[j], 2 * sizeof(uint32_t), cudaHostAllocMapped));
+    VBH_CUDA(cudaHostGetDevicePointer((void**)&p->n_pin_dev[j], p->n_pin[j], 0));
+#else
     VBH_CUDA(cudaMallocHost(&p->n_pin[j], 2 * sizeof(uint32_t)));
+#endif
     VBH_CUDA(cudaEventCreateWithFlags(&p->e_h2d[j], cudaEventDisableTiming));
     VBH_CUDA(cudaEventCreateWithFlags(&p->e_frame[j], cudaEventDisableTiming));
     VBH_CUDA(cudaEventCreateWithFlags(&p->e_out[j], cudaEventDisableTiming));
@@ -234,8 +251,14 @@ vbh_status vbh_process_frame_host(vbh_handle* h, const uint16_t* depth_host,
   out_host->done = 0u;
   vbh_status st = vbh_process_frame(h, p->depth[j], T_wc_host, frame_id, erase_radius, &s);
   if (st != VBH_OK) return st;
+#if VBH_HOST_TOTALS_KERNEL
+  k_frame_totals<<<1, 32, 0, h->stream>>>(p->n_dev[j], p->n_pin_dev[j]);
+  VBH_CUDA(cudaGetLastError());
+  h->launches += 1;
+#else
   VBH_CUDA(cudaMemcpyAsync(p->n_pin[j], p->n_dev[j], 2 * sizeof(uint32_t),
                            cudaMemcpyDeviceToHost, h->stream));
+#endif
   VBH_CUDA(cudaEventRecord(p->e_frame[j], h->stream));
   p->frame_used[j] = true;
   ++p->k;
