@@ -393,6 +393,9 @@ vbh_status vbh_set_stream(vbh_handle* h, void* cuda_stream) {
 
 // Plain-map batches up to this size run as one cooperative launch (latency-bound otherwise).
 constexpr uint32_t kSmallBatchMax = 1u << 17;
+#ifndef VBH_FINISH_ERASE
+#define VBH_FINISH_ERASE 1   // a plain map's pending insert values and erases share a launch
+#endif
 
 vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* keys3_dev,
                           const uint32_t* vals_dev, uint32_t* results_dev, uint8_t* status_dev,
@@ -437,11 +440,19 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
     launch_hash_insert(h->L, t, pool, h->cnt, h->blists.ins_key,
                        h->blists.n + 1, vals_dev, results_dev, status_dev, n,
                        h->blists.ins_idx);
-    launch_hash_insert_finish(h->L, t, pool, h->cnt, h->blists.n + 1, results_dev, status_dev,
-                              n, nullptr, nullptr, nullptr, nullptr, nullptr,
-                              h->blists.ins_idx);
-    launch_hash_erase(h->L, t, pool, h->cnt, results_dev, status_dev, n, h->blists);
-    h->launches += 5;
+#if VBH_FINISH_ERASE
+    if (h->cfg.max_blocks == 0) {   // a plain map: pending values and erases in one launch
+      launch_hash_finish_erase(h->L, t, pool, h->cnt, results_dev, status_dev, n, h->blists);
+      h->launches += 4;
+    } else
+#endif
+    {
+      launch_hash_insert_finish(h->L, t, pool, h->cnt, h->blists.n + 1, results_dev, status_dev,
+                                n, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                h->blists.ins_idx);
+      launch_hash_erase(h->L, t, pool, h->cnt, results_dev, status_dev, n, h->blists);
+      h->launches += 5;
+    }
   }
   h->stage_end();
   st = check_launch(h, "vbh_hash_batch");

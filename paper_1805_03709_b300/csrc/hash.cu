@@ -14,7 +14,8 @@
 //     these arguments; double hashing keeps it short at high loads.  Tombstones keep chains intact, and an
 //     erase makes a slot EMPTY only where a find would stop anyway.
 //   * A plain map's batch: the winner of an insert writes its value and final result at once;
-//     inserts that met their key take the value in a follow-up launch (skipped when none did).
+//     inserts that met their key take the value in a follow-up launch (skipped when none did),
+//     the erase launch (k_finish_erase) for a batch of op lists.
 //   * Insert: pass 1 walks the chain to its end; if the key is absent it remembers the first
 //     free slot (tombstone or EMPTY).  Pass 2 claims free slots in probe order from there with
 //     a 64-bit CAS, re-reading a bucket after a lost CAS.  Because no slot becomes free during
@@ -557,6 +558,26 @@ __global__ void __launch_bounds__(kThreads) k_erase(TableView t, PoolView pool, 
   erase_phase(t, pool, cnt, ekeys, eidx, count_dev, res, st, n_cap, sh);
 }
 
+// A plain map's last two phases in one launch: the inserts that met their key read its value
+// (usually none did), then the erases run.  They touch disjoint fields -- the pending inserts
+// read value fields, which an erase never writes -- so they need no barrier between them; a
+// pool-backed map keeps the separate launches (its finish phase settles the free stack the
+// erases push to).
+__global__ void __launch_bounds__(kThreads) k_finish_erase(TableView t, PoolView pool,
+                                                           DevCounters* cnt,
+                                                           const unsigned int* ins_count,
+                                                           const unsigned int* ins_idx,
+                                                           const unsigned long long* ekeys,
+                                                           const unsigned int* eidx,
+                                                           const unsigned int* era_count,
+                                                           unsigned int* res, unsigned char* st,
+                                                           unsigned int n_cap) {
+  __shared__ unsigned int sh_f[3], sh_e[2];
+  finish_phase(t, pool, cnt, ins_count, res, st, n_cap, nullptr, nullptr, nullptr, nullptr,
+               nullptr, ins_idx, sh_f);
+  erase_phase(t, pool, cnt, ekeys, eidx, era_count, res, st, n_cap, sh_e);
+}
+
 // ------------------------------------------------------------------------- small batch
 // A small batch of a plain map is bound by the latency of its phases, not by bandwidth.
 // k_batch_small runs it in one cooperative launch (every CTA resident) with one thread per op
@@ -872,6 +893,14 @@ void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevC
   VBH_GRID(k_insert_finish, kThreads);
   k_insert_finish<<<fit_grid(grid_k_insert_finish, n), kThreads, 0, L.stream>>>(
       t, pool, cnt, count_dev, res, st, n, touched, tkey, tdepth, n_touched, ctl, idx);
+}
+void launch_hash_finish_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                              unsigned int* res, unsigned char* st, unsigned int n,
+                              BatchLists lists) {
+  VBH_GRID(k_finish_erase, kThreads);
+  k_finish_erase<<<fit_grid(grid_k_finish_erase, n), kThreads, 0, L.stream>>>(
+      t, pool, cnt, lists.n + 1, lists.ins_idx, lists.era_key, lists.era_idx, lists.n + 2, res,
+      st, n);
 }
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        unsigned int* res, unsigned char* st, unsigned int n, BatchLists lists) {

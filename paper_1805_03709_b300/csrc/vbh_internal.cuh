@@ -451,6 +451,10 @@ void launch_hash_insert_finish(const Launch& L, TableView t, PoolView pool, DevC
 // The batch's erases, from the erase list its first pass compacted.
 void launch_hash_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        unsigned int* res, unsigned char* st, unsigned int n, BatchLists lists);
+// A plain map's batch: the pending inserts' values and the erases in one launch.
+void launch_hash_finish_erase(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
+                              unsigned int* res, unsigned char* st, unsigned int n,
+                              BatchLists lists);
 // A plain map's small batch in one cooperative launch, one thread per op (finds; inserts;
 // insert values and erases, separated by grid barriers).  lists_next: the three list counts
 // of the next phased batch, zeroed.  Returns cudaErrorInvalidValue when n ops need more CTAs
