@@ -110,8 +110,7 @@ vbh_status rebuild(vbh_handle* h) {
 
 void free_batch_lists(vbh_handle* h) {
   BatchLists& b = h->blists;
-  for (void* q : {(void*)b.find_idx, (void*)b.find_key, (void*)b.ins_idx, (void*)b.ins_key,
-                  (void*)b.era_idx, (void*)b.era_key})
+  for (void* q : {(void*)b.ins_idx, (void*)b.ins_key, (void*)b.era_idx, (void*)b.era_key})
     if (q) cudaFree(q);
   b = BatchLists{};
   h->blists_cap = 0;
@@ -409,13 +408,11 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
   if (st != VBH_OK) return st;
   // a small batch of a plain map: one cooperative launch, one thread per op, no op lists
   const bool small = h->cfg.max_blocks == 0 && n <= kSmallBatchMax && small_batch_fits(h->L, n);
-  if (!small && h->blists_cap < n) {   // the compacted find / insert / erase lists, grown to n
+  if (!small && h->blists_cap < n) {   // the compacted insert / erase lists, grown to n
     VBH_CUDA(cudaStreamSynchronize(h->stream));
     free_batch_lists(h);
     BatchLists& b = h->blists;
-    if (cudaMalloc(&b.find_idx, sizeof(unsigned int) * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&b.find_key, sizeof(unsigned long long) * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&b.ins_idx, sizeof(unsigned int) * (size_t)n) != cudaSuccess ||
+    if (cudaMalloc(&b.ins_idx, sizeof(unsigned int) * (size_t)n) != cudaSuccess ||
         cudaMalloc(&b.ins_key, sizeof(unsigned long long) * (size_t)n) != cudaSuccess ||
         cudaMalloc(&b.era_idx, sizeof(unsigned int) * (size_t)n) != cudaSuccess ||
         cudaMalloc(&b.era_key, sizeof(unsigned long long) * (size_t)n) != cudaSuccess) {
@@ -443,7 +440,7 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
 #if VBH_FINISH_ERASE
     if (h->cfg.max_blocks == 0) {   // a plain map: pending values and erases in one launch
       launch_hash_finish_erase(h->L, t, pool, h->cnt, results_dev, status_dev, n, h->blists);
-      h->launches += 4;
+      h->launches += 3;
     } else
 #endif
     {
@@ -451,7 +448,7 @@ vbh_status vbh_hash_batch(vbh_handle* h, const uint8_t* ops_dev, const int32_t* 
                                 n, nullptr, nullptr, nullptr, nullptr, nullptr,
                                 h->blists.ins_idx);
       launch_hash_erase(h->L, t, pool, h->cnt, results_dev, status_dev, n, h->blists);
-      h->launches += 5;
+      h->launches += 4;
     }
   }
   h->stage_end();

@@ -6,8 +6,8 @@
 //   * A launch runs one phase only: finds (read-only), inserts (slots only go free -> key),
 //     or erases (slots only go key -> tombstone, or key -> EMPTY in a bucket that already holds
 //     an EMPTY slot).  The host orders the phases of a batch.  A batch's first pass (which
-//     touches no slot) sorts its ops into a find, an insert and an erase list, so each phase
-//     launch covers only its own ops.
+//     writes no slot) runs the finds and sorts the other ops into an insert and an erase list,
+//     so each later phase launch covers only its own ops.
 //   * A live key never moves (the paper's invariant that entry positions are preserved), so a
 //     find needs no lock: it walks the buckets from the key's home bucket until it meets the
 //     key or a bucket with a never-used (EMPTY) slot.  Any fixed probe sequence per key keeps
@@ -180,15 +180,21 @@ __device__ int thread_insert(const TableView& t, unsigned long long key, unsigne
 }
 
 // ---------------------------------------------------------------------------- batch compaction
-// Every op of a batch is read once: invalid ops get their status; valid finds, inserts and erases
-// go to three lists of (op index, packed key).  A CTA takes kPrepOps x kThreads ops, each thread
-// kPrepOps of them a CTA width apart (coalesced loads, all in flight at once); one warp scan of
-// the three packed counts and one reservation per list per CTA place them; at 8 CTAs per SM a
-// 2^20-op batch is one round of the grid.
+// Every op of a batch is read once: invalid ops get their status; valid inserts and erases go to
+// two lists of (op index, packed key), and valid finds run in place.  A CTA takes kPrepOps x
+// kThreads ops, each thread kPrepOps of them a CTA width apart (coalesced loads, all in flight at
+// once); one warp scan of the packed counts and one reservation per list per CTA place them.
 constexpr int kPrepOps = 4;
 
-// Each phase of a batch is a device function that its own kernel launches.
-__device__ __forceinline__ void prep_phase(DevCounters* cnt, const unsigned char* ops,
+// Each phase of a batch is a device function that its own kernel launches.  The first pass
+// also runs the batch's finds (nothing writes the table before the insert launch), so finds
+// need neither a list nor a launch of their own; at 8 CTAs per SM (32 registers, a few bytes
+// spilled) a 2^20-op batch is one round of the grid.
+#ifndef VBH_PREP_MIN_CTAS
+#define VBH_PREP_MIN_CTAS 8
+#endif
+__device__ __forceinline__ void prep_phase(const TableView& t, DevCounters* cnt,
+                                           const unsigned char* ops,
                                            const int* keys3, unsigned int* res,
                                            unsigned char* st, unsigned int n, BatchLists lists,
                                            unsigned int* s_warp, unsigned int* s_base) {
@@ -216,7 +222,7 @@ __device__ __forceinline__ void prep_phase(DevCounters* cnt, const unsigned char
         } else {
           key[j] = pack_key(x, y, z);
           kind[j] = op == kOpFind ? 0 : op == kOpInsert ? 1 : 2;
-          packed += 1u << (10 * kind[j]);
+          if (kind[j] != 0) packed += 1u << (10 * kind[j]);   // finds are not listed
         }
       }
     }
@@ -246,52 +252,35 @@ __device__ __forceinline__ void prep_phase(DevCounters* cnt, const unsigned char
 #pragma unroll
     for (int j = 0; j < kPrepOps; ++j) {
       const int q = kind[j];
-      if (q < 0) continue;
-      const unsigned int k = q == 0 ? pos[0]++ : q == 1 ? pos[1]++ : pos[2]++;
-      unsigned int* const idx = q == 0 ? lists.find_idx : q == 1 ? lists.ins_idx : lists.era_idx;
-      unsigned long long* const ko = q == 0 ? lists.find_key : q == 1 ? lists.ins_key
-                                                                      : lists.era_key;
+      if (q <= 0) continue;
+      const unsigned int k = q == 1 ? pos[1]++ : pos[2]++;
+      unsigned int* const idx = q == 1 ? lists.ins_idx : lists.era_idx;
+      unsigned long long* const ko = q == 1 ? lists.ins_key : lists.era_key;
       idx[k] = base + j * kThreads + threadIdx.x;
       ko[k] = key[j];
+    }
+    // the finds: nothing writes the table before the batch's insert launch, so they see it as
+    // the batch found it (read-only walks through the non-coherent path)
+#pragma unroll
+    for (int j = 0; j < kPrepOps; ++j) {
+      if (kind[j] != 0) continue;
+      const unsigned int i = base + j * kThreads + threadIdx.x;
+      unsigned int val;
+      const bool hit = thread_find<true>(t, key[j], &val) != kNone;
+      res[i] = hit ? val : kNone;
+      st[i] = hit ? kStFound : kStNotFound;
     }
     __syncthreads();   // s_warp and s_base are rewritten next round
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 8) k_batch_prep(DevCounters* cnt,
+__global__ void __launch_bounds__(kThreads, VBH_PREP_MIN_CTAS) k_batch_prep(TableView t, DevCounters* cnt,
                                                          const unsigned char* ops,
                                                          const int* keys3, unsigned int* res,
                                                          unsigned char* st, unsigned int n,
                                                          BatchLists lists) {
   __shared__ unsigned int s_warp[kThreads / 32], s_base[3];
-  prep_phase(cnt, ops, keys3, res, st, n, lists, s_warp, s_base);
-}
-
-// --------------------------------------------------------------------------------- find phase
-// The batch's finds (list from k_batch_prep, *count_dev entries, capped at n): read-only walks
-// through the non-coherent path (nothing writes the table during a find launch).
-__device__ __forceinline__ void find_phase(const TableView& t, const unsigned long long* fkeys,
-                                           const unsigned int* fidx,
-                                           const unsigned int* count_dev, unsigned int* res,
-                                           unsigned char* st, unsigned int n_cap) {
-  const unsigned int n = min(__ldcg(count_dev), n_cap);
-  const unsigned int stride = gridDim.x * blockDim.x;
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const unsigned long long key = __ldcg(fkeys + i);
-    const unsigned int oi = __ldcg(fidx + i);
-    unsigned int val;
-    const bool hit = thread_find<true>(t, key, &val) != kNone;
-    res[oi] = hit ? val : kNone;
-    st[oi] = hit ? kStFound : kStNotFound;
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_find(TableView t, const unsigned long long* fkeys,
-                                                   const unsigned int* fidx,
-                                                   const unsigned int* count_dev,
-                                                   unsigned int* res, unsigned char* st,
-                                                   unsigned int n_cap) {
-  find_phase(t, fkeys, fidx, count_dev, res, st, n_cap);
+  prep_phase(t, cnt, ops, keys3, res, st, n, lists, s_warp, s_base);
 }
 
 // ------------------------------------------------------------------------------- insert phase
@@ -870,11 +859,8 @@ void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsi
                       const int* keys3, unsigned int* res, unsigned char* st, unsigned int n,
                       BatchLists lists) {
   VBH_GRID(k_batch_prep, kThreads);
-  VBH_GRID(k_find, kThreads);
   k_batch_prep<<<fit_grid(grid_k_batch_prep, (n + kPrepOps - 1u) / kPrepOps), kThreads, 0,
-                 L.stream>>>(cnt, ops, keys3, res, st, n, lists);
-  k_find<<<fit_grid(grid_k_find, n), kThreads, 0, L.stream>>>(t, lists.find_key, lists.find_idx,
-                                                                lists.n, res, st, n);
+                 L.stream>>>(t, cnt, ops, keys3, res, st, n, lists);
 }
 void launch_hash_insert(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                         const unsigned long long* pkeys, const unsigned int* count_dev,

@@ -418,21 +418,20 @@ struct Launch {
   int sms;            // persistent grids are (resident CTAs per SM) x sms
 };
 
-// A hash batch's valid finds, inserts and erases, compacted by its first pass: op index + packed
-// key.
+// A hash batch's valid inserts and erases, compacted by its first pass (which runs the finds
+// itself): op index + packed key.
 struct BatchLists {
-  unsigned int* find_idx = nullptr;
-  unsigned long long* find_key = nullptr;
   unsigned int* ins_idx = nullptr;
   unsigned long long* ins_key = nullptr;
   unsigned int* era_idx = nullptr;
   unsigned long long* era_key = nullptr;
-  unsigned int* n = nullptr;        // this batch's three list lengths (zero when it starts)
+  unsigned int* n = nullptr;        // this batch's list lengths: [1] inserts, [2] erases
+                                    // ([0] stays 0); zero when it starts
   unsigned int* n_next = nullptr;   // the next batch's, zeroed by this batch's first pass
 };
 
 // hash.cu
-// The batch's first pass (statuses of invalid ops, the three op lists) and its finds.
+// The batch's first pass: statuses of invalid ops, the finds, the insert and erase lists.
 void launch_hash_find(const Launch& L, TableView t, DevCounters* cnt, const unsigned char* ops,
                       const int* keys3, unsigned int* res, unsigned char* st, unsigned int n,
                       BatchLists lists);
