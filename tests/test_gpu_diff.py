@@ -53,7 +53,12 @@ def check(o, g, xi32, depth):
     gdo, gxo = o.backward(xi32.astype(np.float64))
     gx = gx.cpu().numpy().astype(np.float64)
     assert err.max() < 1e-4, (np.median(err), np.quantile(err, 0.999), err.max())
-    assert abs(float(loss) - Lo) <= 1e-5 * Lo
+    # L is the sum of F^2, so L_gpu - L_oracle = sum (F_gpu - F_oracle)(F_gpu + F_oracle): with
+    # many samples the per-sample errors average out and 1e-5 relative holds; a window of a few
+    # dozen samples is held to the bound its per-sample errors give
+    Fg = F.cpu().numpy().astype(np.float64)
+    dl = float(np.sum(np.abs(Fg - Fo) * np.abs(Fg + Fo)))
+    assert abs(float(loss) - Lo) <= max(1e-5 * Lo, 1.001 * dl + 1e-12)
     assert rel_l2(gd.cpu().numpy().astype(np.float64), gdo) < 1e-3
     for f in range(gxo.shape[0]):
         assert rel_l2(gx[f], gxo[f]) < 1e-3, (f, gx[f], gxo[f])
@@ -62,6 +67,12 @@ def check(o, g, xi32, depth):
 
 def test_small_window():
     check(*setup(4, 48, 36, 600))
+
+
+@pytest.mark.parametrize("nf,W,H,ns", [(3, 37, 29, 777), (1, 40, 30, 33)])
+def test_ragged_windows(nf, W, H, ns):
+    """Odd image sides, sample counts that are no multiple of a warp, a one-frame window."""
+    check(*setup(nf, W, H, ns, seed=11))
 
 
 def test_window_16_frames_320x240():

@@ -143,3 +143,23 @@ def test_records_beyond_one_counting_group():
 
     assert np.array_equal(canon_rows(tris), canon_rows(ref))
     vol.close()
+
+
+def test_empty_stream_and_blocks_without_surface():
+    """A stream of no records, and one whose block holds no surface (every cube index 0, so the
+    record has no entries): no triangles and no error."""
+    from paper_1805_03709_b300.volume import Volume
+    v0 = Volume(voxel_size=0.01, trunc=0.04, width=8, height=8, fx=4, fy=4, cx=4, cy=4,
+                n_buckets=1 << 10, max_blocks=1 << 10)
+    s0 = v0.extract(V.VBH_MC_ALL)
+    assert int(s0.n[0]) == 0 and len(v0.triangulate(s0)) == 0
+    F = np.full((8, 8, 8), 0.5, np.float32)
+    keys, vals = blocks_from(F)
+    vol, o = pair(keys, vals)
+    s = vol.extract(V.VBH_MC_ALL)
+    nb, ne = (int(x) for x in s.n.cpu().tolist())
+    assert nb == 1 and ne == 0
+    assert len(vol.triangulate(s)) == 0 and len(o.triangles(keys).reshape(-1, 9)) == 0
+    assert vol.counters().error_flags == 0
+    v0.close()
+    vol.close()

@@ -113,6 +113,24 @@ def test_tiny_sequence_full_parity():
     assert n > 100000
 
 
+@pytest.mark.parametrize("width,height", [(157, 113), (33, 17), (16, 1)])
+def test_ragged_image_sizes(width, height):
+    """Image sides that are no multiple of the band allocation's 16 x 16 pixel tiles (partial
+    tiles in both directions, odd sides) and a one-row image: the separate calls and the frame
+    graph both give the oracle's volume and MC blocks."""
+    cam, poses, depth = synth.tiny_sequence(n_frames=4, width=width, height=height,
+                                            f=140.0 * width / 160.0)
+    vol, orc = make_pair(cam, 0.01, 0.04, 1 << 14, 1 << 13)
+    run_sequence(vol, orc, depth, poses)
+    vg, og = make_pair(cam, 0.01, 0.04, 1 << 14, 1 << 13)
+    for i in range(len(poses)):
+        vg.process_frame(torch.from_numpy(depth[i]).cuda(), poses[i], i + 1, 0.0)
+        og.integrate(depth[i], poses[i])
+    torch.cuda.synchronize()
+    compare_volume(vg, og)
+    assert vg.counters().error_flags == 0
+
+
 @pytest.mark.parametrize("hash_fn", [V.VBH_HASH_MIX, V.VBH_HASH_PRIMES])
 def test_room_reduced_with_erase(hash_fn):
     """Room scene at 160 x 120 (f scaled to 131.25), voxel 5 mm, truncation 2 cm, zmax 4 m,
