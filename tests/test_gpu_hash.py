@@ -374,3 +374,37 @@ def test_full_size_table_batch_2e20(lf):
         ro, so = om.batch(o2, k2, v2)
         assert_same(o2, k2, rg, sg, ro, so)
         assert hm.counters().live == len(om)
+
+
+def test_full_size_table_batch_2e22():
+    """The largest batch the benchmark times: 2^22 ops of the same mix on the 2^22 x 4 table at
+    load factor 0.7; the prefill's inserts (batches of ~2.9 M ops) are compared too, and the
+    table's contents at the end."""
+    n_buckets = 1 << 22
+    n_pre = int(0.7 * n_buckets * 4)
+    n = 1 << 22
+    rng = np.random.default_rng(22)
+    pool = synth.distinct_keys(n_pre + n, seed=22)
+    pre, fresh = pool[:n_pre], pool[n_pre:]
+    hm = HashMap(n_buckets=n_buckets, max_batch=1 << 23)
+    om = OracleMap()
+    for ch in np.array_split(np.arange(n_pre), 4):
+        k = pre[ch]
+        o = np.full(len(k), 1, np.uint8)
+        rg, sg = gpu_batch(hm, o, k, key_value(k))
+        ro, so = om.batch(o, k, key_value(k))
+        assert_same(o, k, rg, sg, ro, so)
+    nf, ni = n // 2, int(0.3 * n)
+    ne = n - nf - ni
+    keys = np.concatenate([pre[rng.integers(0, n_pre, nf // 2)],
+                           fresh[rng.integers(0, len(fresh), nf - nf // 2)],
+                           fresh[:ni], pre[rng.integers(0, n_pre, ne)]])
+    ops = np.concatenate([np.zeros(nf), np.ones(ni), np.full(ne, 2)]).astype(np.uint8)
+    perm = rng.permutation(n)
+    keys, ops = keys[perm], ops[perm]
+    vals = key_value(keys)
+    rg, sg = gpu_batch(hm, ops, keys, vals)
+    ro, so = om.batch(ops, keys, vals)
+    assert_same(ops, keys, rg, sg, ro, so)
+    assert hm.counters().error_flags == 0
+    check_contents(hm, om)
