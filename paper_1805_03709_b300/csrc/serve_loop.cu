@@ -14,8 +14,8 @@
 // the request's worst case in the stream buffer, taken from a ring allocator), cuts the
 // admitted ranges into chunks and publishes chunks of all active requests in rounds, smallest
 // remainder first, whenever the workers' backlog runs low.  Every other warp is a worker: it
-// takes the next 32-record tile by ticket (one atomic), waits until that tile has been
-// published, finds its chunk, and serves the tile.  The worker that finishes a request's last
+// takes the next tile (32 change records, 64 for a request with many left) by ticket (one
+// atomic), waits until that tile has been published, finds its chunk, and serves the tile.  The worker that finishes a request's last
 // tile moves the client to its new version and writes the completion to mapped host memory.
 //
 // Concurrency with frames.  Fusion and MC extraction keep running on the volume's stream, so
@@ -69,6 +69,21 @@ constexpr unsigned int kErrOverrun = 2u, kErrCap = 4u;   // as kServeErr* (serve
 #define VBH_LOOP_STAGE_BLOCKS 16
 #endif
 constexpr unsigned int kStageBlocks = VBH_LOOP_STAGE_BLOCKS;   // blocks a worker copies at once
+#ifndef VBH_LOOP_TILE_RECS
+#define VBH_LOOP_TILE_RECS 32
+#endif
+constexpr unsigned int kTileRecs = VBH_LOOP_TILE_RECS;   // change records per tile
+#ifndef VBH_LOOP_BIG_TILE_RECS
+#define VBH_LOOP_BIG_TILE_RECS 64
+#endif
+#ifndef VBH_LOOP_BIG_REMAIN
+#define VBH_LOOP_BIG_REMAIN 4096u   // remaining records from which a chunk has long tiles
+#endif
+constexpr unsigned int kBigTileRecs = VBH_LOOP_BIG_TILE_RECS;
+constexpr unsigned int kBigRemain = VBH_LOOP_BIG_REMAIN;
+static_assert(kTileRecs >= 1u && (kTileRecs <= 32u || kTileRecs % 32u == 0u) &&
+                  kBigTileRecs >= 1u && (kBigTileRecs <= 32u || kBigTileRecs % 32u == 0u),
+              "a tile is served 32 records (one per lane) at a time");
 
 // Host -> device (mapped host memory).
 struct LoopReq {
@@ -123,6 +138,7 @@ struct Chunk {
   unsigned int idx;                // absolute chunk number (ring position check)
   unsigned int tiles, slot, lo, hi;
   unsigned int finished;           // atomic: tiles served
+  unsigned int recs;               // change records per tile
 };
 
 struct Region {
@@ -281,7 +297,7 @@ __device__ void complete_request(const LoopArgs& A, unsigned int si) {
   atomicOr(&A.d->free_mask, 1ull << si);
 }
 
-// Serve one 32-record tile of a chunk (one warp): test each record for being current; copy
+// Serve up to 32 records of a tile (one warp, a lane per record): test each record for being current; copy
 // every current block's 512 B of indices into the warp's staging area in shared memory with
 // asynchronous 16 B copies (all of the tile's copies in flight at once), fence, and read each
 // block's refresh number again -- a block whose number changed meanwhile is dropped; reserve
@@ -630,7 +646,12 @@ __device__ void scheduler(const LoopArgs& A, unsigned int* sm) {
         Chunk& c = A.chunks[chunk_tail % kChunkRing];
         c.start_tile = end_tile;
         c.idx = chunk_tail;
-        c.tiles = (take + 31u) / 32u;
+        // a request with at least kBigRemain records left gets longer tiles (fewer tickets,
+        // chunk look-ups and reservations per record: its tail latency falls); a shorter
+        // remainder keeps short tiles (a request's latency is then about one tile's)
+        const unsigned int recs = best_rem >= kBigRemain ? kBigTileRecs : kTileRecs;
+        c.recs = recs;
+        c.tiles = (take + recs - 1u) / recs;
         c.slot = best;
         c.lo = s_next[best];
         c.hi = s_next[best] + take;
@@ -754,10 +775,15 @@ __device__ void worker(const LoopArgs& A, uint4* stage) {
     const unsigned int clo = vload(&ch->lo), chi = vload(&ch->hi);
     ReqSlot* R = A.slots + si;
     const bool scan = vload(&R->scan) != 0u;
-    const unsigned int rec0 = clo + 32u * k;
-    const unsigned int rec_end = rec0 + 32u < chi ? rec0 + 32u : chi;
-    serve_tile(A, S, stage, si, scan, vload(&R->sigma), vload(&R->cap), vload(&R->off), rec0,
-               rec_end);
+    const unsigned int recs = vload(&ch->recs);
+    const unsigned int rec0 = clo + recs * k;
+    const unsigned int rec_end = rec0 + recs < chi ? rec0 + recs : chi;
+    {   // the tile's records, 32 (one per lane) at a time
+      const unsigned int sig = vload(&R->sigma), cap = vload(&R->cap);
+      const unsigned long long off = vload(&R->off);
+      for (unsigned int r0 = rec0; r0 < rec_end; r0 += 32u)
+        serve_tile(A, S, stage, si, scan, sig, cap, off, r0, r0 + 32u < rec_end ? r0 + 32u : rec_end);
+    }
     fence_acq_rel_gpu();
     __syncwarp();
     if (lane == 0u && atomicAdd(&ch->finished, 1u) == tiles - 1u) {
