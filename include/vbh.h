@@ -538,8 +538,9 @@ uint64_t vbh_serve_now_ns(void);
  *     bypass_rounds scheduler rounds), cuts the admitted ranges into chunks of chunk_records
  *     and hands chunks of all active requests out in rounds, smallest remainder first, as the
  *     workers drain them (continuous batching: a request that arrives while others run joins
- *     the next round).  Worker warps take 32-record tiles by ticket, copy each current block's
- *     512 cube indices and its header, and the warp that finishes a request's last tile moves
+ *     the next round).  Worker warps take tiles of 32 change records (64 while the request
+ *     has at least 4096 left) by ticket, copy each current block's 512 cube indices and its
+ *     header, and the warp that finishes a request's last tile moves
  *     the client to its new version and publishes the completion in mapped host memory.
  *   - Results are those of vbh_serve_step's requests, with sigma the last change number
  *     published when the request is admitted.  A block refreshed again while it is being
