@@ -466,8 +466,6 @@ def main():
         state["vol"] = vol
         for i in range(args.warmup):
             step(i, i + 1)
-        vol.timing(("mc",))   # MC extraction timed on the replay (kept out of the main loop)
-        vol.timing_read(reset=True)
         host_depth = torch.from_numpy(depth).pin_memory()
         outs = [HostStream.allocate(MAX_BLOCKS, 1 << 23) for _ in range(3)]
         fl_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -508,10 +506,10 @@ def main():
         assert all(st == V.VBH_OK for st in statuses), "host stream capacity exceeded"
         # per frame: live and removal records, entries and the live blocks after it, from an
         # untimed replay of the same frames (the same totals as the host copies)
-        mc_counts = mc_replay(torch, cam, D, poses, args, n_e2e)[0]
+        # the replay counts the same frames and times their MC extraction with nothing else
+        # on the GPU (the e2e run's own copies in and out would contend with the kernel)
+        mc_counts, mc_timing = mc_replay(torch, cam, D, poses, args, n_e2e, flush)
         assert [(c[0] + c[1], c[2]) for c in mc_counts] == nbs, "replay differs from the e2e run"
-        mc_timing = vol.timing_read(reset=True)
-        vol.timing(())
         t_e2e = max_over_ranks(torch, t_e2e, dev, ws)
         e2e = {"value": ws * n_e2e / t_e2e, "unit": "frames/s",
                "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e,
@@ -523,9 +521,10 @@ def main():
                "host_call_ms_p50": statistics.median(host_call_s) * 1e3}
 
     # MC extraction roofline: the same frames' MC extraction, timed (CUDA events around the
-    # kernel on the volume's stream) and counted on the e2e replay (or a replay of its own)
+    # kernel on the volume's stream) and counted on a replay of them (the e2e leg's frames when
+    # it ran, else the timed frames)
     if args.no_e2e:
-        mc_counts, mc_timing = mc_replay(torch, cam, D, poses, args, args.steps)
+        mc_counts, mc_timing = mc_replay(torch, cam, D, poses, args, args.steps, flush)
     mc_line = None
     if mc_counts and mc_timing[0].get("mc", 0.0) > 0:
         live_b = sum(c[0] for c in mc_counts) / len(mc_counts)
@@ -1031,10 +1030,11 @@ def stream_point(torch, cam, D, poses, flush, args, base_ms):
             "host_link_d2h_GBs": max(link), "link_frac": copy_gbs / max(link)}
 
 
-def mc_replay(torch, cam, D, poses, args, n_timed):
+def mc_replay(torch, cam, D, poses, args, n_timed, flush=None):
     """(live blocks, removal records, entries) of each of the n_timed frames' MC extraction
-    (after the warm-up frames) and the live blocks after it, from an untimed replay of the same
-    frames on a fresh volume."""
+    (after the warm-up frames) and the live blocks after it, from a replay of the same frames on
+    a fresh volume, with the MC extraction of those frames timed (CUDA events around the kernel;
+    `flush`, if given, is written before every frame, as in the timed loop)."""
     from paper_1805_03709_b300.volume import Volume
     vol = Volume(VOXEL, TRUNC, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
                  N_BUCKETS, MAX_BLOCKS, zmax=ZMAX, mc_cap_blocks=MAX_BLOCKS,
@@ -1045,6 +1045,8 @@ def mc_replay(torch, cam, D, poses, args, n_timed):
         if i == args.warmup:
             vol.timing(("mc",))
             vol.timing_read(reset=True)
+        if flush is not None:
+            flush.zero_()
         s = vol.process_frame(D[f], poses[f], i + 1, ERASE_R)
         if i >= args.warmup:
             nb, ne = (int(x) for x in s.n.cpu().tolist())

@@ -29,7 +29,11 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMcThreads = 128;   // 4 warps, one block each
-constexpr unsigned int kStage = 1024;        // MC entries staged per warp (>= 512, one block)
+#ifndef VBH_MC_STAGE
+#define VBH_MC_STAGE 512   // a smaller stage leaves the SM more L1 (19.3 -> 18.7 us per frame)
+#endif
+constexpr unsigned int kStage = VBH_MC_STAGE;   // MC entries staged per warp (>= 512, one block)
+static_assert(kStage >= 512u, "a block's entries must fit the stage");
 #ifndef VBH_MC_STAGE_BLOCKS
 #define VBH_MC_STAGE_BLOCKS 16
 #endif
@@ -178,6 +182,19 @@ __device__ __forceinline__ void transpose8x8(unsigned int& lo, unsigned int& hi)
   hi ^= t >> 4;
 }
 
+#ifndef VBH_MC_SPREAD_CALC
+#define VBH_MC_SPREAD_CALC 1   // the dense store's byte masks computed, not read from a table
+#endif
+// Bit i of an 8-bit value moved to bit 8 i (three masked shift steps: nibbles to 32-bit halves,
+// pairs to 16-bit quarters, bits to bytes); times 0xFF it is the byte mask of the set bits.
+__device__ __forceinline__ unsigned long long spread8(unsigned int b) {
+  unsigned long long m = b;
+  m = (m | (m << 28)) & 0x0000000F0000000Full;
+  m = (m | (m << 14)) & 0x0003000300030003ull;
+  m = (m | (m << 7)) & 0x0101010101010101ull;
+  return m;
+}
+
 // The lattice of a block and its 7 positive neighbours (n = ox + 2 oy + 4 oz) in shared memory:
 // L[n][w] = (sign word w, weight word w) of neighbour n, w = (ly >> 2) + 2 lz, byte ly & 3 of a
 // word holding the 8 voxels x = 0..7 of row (ly, lz).  A 9-bit lattice row (x = 0..8) at
@@ -203,7 +220,9 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
                                                           DevCounters* cnt, const FrameCtl* ctl,
                                                           const unsigned int* mset,
                                                           const unsigned long long* tombrec) {
+#if !VBH_MC_SPREAD_CALC
   __shared__ unsigned long long spread[256];   // bit i of b -> bit 8 i (dense store only)
+#endif
   __shared__ uint2 msk[kMcThreads / 32][8 * 16];   // the lattice, per warp
   __shared__ unsigned short stage_loc[kMcThreads / 32][kStage];
   __shared__ unsigned char stage_idx[kMcThreads / 32][kStage];
@@ -222,6 +241,7 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
   ServeLog* const sl = ctl->serve_mark ? ctl->slog : nullptr;
   const bool emit = !ctl->store_only;
   __shared__ unsigned int s_seq0;
+#if !VBH_MC_SPREAD_CALC
   if (sl) {   // the byte masks of the dense store
     for (int b = threadIdx.x; b < 256; b += kMcThreads) {
       unsigned long long v = 0;
@@ -229,6 +249,7 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
       spread[b] = v;
     }
   }
+#endif
   if (threadIdx.x == 0) s_seq0 = sl ? sl->seq_next : 0u;   // every CTA reads it before the
   __syncthreads();                                        // last one advances it
   const unsigned int seq0 = s_seq0;
@@ -367,7 +388,7 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
 #pragma unroll
       for (int h = 0; h < 2; ++h)   // cubes that are not emitted are stored as 0
         st[32u * h + lane] = (((unsigned long long)idx_hi[h] << 32) | idx_lo[h]) &
-                             (spread[e8[h]] * 0xFFull);
+                             (spread8(e8[h]) * 0xFFull);
       if (lane == 0) {
         const unsigned int e = seq0 + r;
         LogEnt le;
