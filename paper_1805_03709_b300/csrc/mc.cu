@@ -29,9 +29,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMcThreads = 128;   // 4 warps, one block each
-#ifndef VBH_MC_CARVEOUT
-#define VBH_MC_CARVEOUT 44   // preferred shared-memory share in % (-1: the driver's choice):
-#endif                       // ~100 KB holds 9 CTAs, the rest of the SM's 256 KB stays L1
 #ifndef VBH_MC_STAGE
 #define VBH_MC_STAGE 512   // a smaller stage leaves the SM more L1 (19.3 -> 18.7 us per frame)
 #endif
@@ -525,12 +522,6 @@ void launch_mset_scan(const Launch& L, PoolView pool, DevCounters* cnt, unsigned
 void launch_mc_extract(const Launch& L, TableView t, PoolView pool, DevCounters* cnt,
                        const FrameCtl* ctl, const unsigned int* mset,
                        const unsigned long long* tombrec) {
-#if VBH_MC_CARVEOUT >= 0
-  static const bool carve = cudaFuncSetAttribute(k_mc_extract,
-                                                 cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                 VBH_MC_CARVEOUT) == cudaSuccess;
-  (void)carve;
-#endif
   static const int grid = persistent_grid(k_mc_extract, kMcThreads, L.sms);
   k_mc_extract<<<grid, kMcThreads, 0, L.stream>>>(t, pool, cnt, ctl, mset, tombrec);
 }
