@@ -3,9 +3,11 @@
 //
 // Guarantees (Sec. 5: concurrent retrieval, insertion and removal succeed and keys stay unique,
 // which the paper obtains with per-entry locks and an excess list; here with CAS claims):
-//   * A launch runs one phase only: finds (read-only), inserts (slots only go free -> key),
-//     or erases (slots only go key -> tombstone, or key -> EMPTY in a bucket that already holds
-//     an EMPTY slot).  The host orders the phases of a batch.  A batch's first pass (which
+//   * A launch changes the table in one way only: finds (read-only), inserts (slots only go
+//     free -> key), or erases (slots only go key -> tombstone, or key -> EMPTY in a bucket that
+//     already holds an EMPTY slot; the pending insert values that a plain map's erase launch
+//     reads first are value fields, which no erase writes).  The host orders the phases of a
+//     batch.  A batch's first pass (which
 //     writes no slot) runs the finds and sorts the other ops into an insert and an erase list,
 //     so each later phase launch covers only its own ops.
 //   * A live key never moves (the paper's invariant that entry positions are preserved), so a
@@ -274,11 +276,9 @@ __device__ __forceinline__ void prep_phase(const TableView& t, DevCounters* cnt,
   }
 }
 
-__global__ void __launch_bounds__(kThreads, VBH_PREP_MIN_CTAS) k_batch_prep(TableView t, DevCounters* cnt,
-                                                         const unsigned char* ops,
-                                                         const int* keys3, unsigned int* res,
-                                                         unsigned char* st, unsigned int n,
-                                                         BatchLists lists) {
+__global__ void __launch_bounds__(kThreads, VBH_PREP_MIN_CTAS)
+    k_batch_prep(TableView t, DevCounters* cnt, const unsigned char* ops, const int* keys3,
+                 unsigned int* res, unsigned char* st, unsigned int n, BatchLists lists) {
   __shared__ unsigned int s_warp[kThreads / 32], s_base[3];
   prep_phase(t, cnt, ops, keys3, res, st, n, lists, s_warp, s_base);
 }
