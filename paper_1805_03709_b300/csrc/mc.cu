@@ -29,9 +29,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMcThreads = 128;   // 4 warps, one block each
-#ifndef VBH_MC_WIDE_MASKS
-#define VBH_MC_WIDE_MASKS 1   // a lane loads 2 x 16 B of one neighbour's masks (not 8 x 4 B)
-#endif
 #ifndef VBH_MC_STAGE
 #define VBH_MC_STAGE 512   // a smaller stage leaves the SM more L1 (19.3 -> 18.7 us per frame)
 #endif
@@ -185,9 +182,6 @@ __device__ __forceinline__ void transpose8x8(unsigned int& lo, unsigned int& hi)
   hi ^= t >> 4;
 }
 
-#ifndef VBH_MC_SPREAD_CALC
-#define VBH_MC_SPREAD_CALC 1   // the dense store's byte masks computed, not read from a table
-#endif
 // Bit i of an 8-bit value moved to bit 8 i (three masked shift steps: nibbles to 32-bit halves,
 // pairs to 16-bit quarters, bits to bytes); times 0xFF it is the byte mask of the set bits.
 __device__ __forceinline__ unsigned long long spread8(unsigned int b) {
@@ -223,9 +217,6 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
                                                           DevCounters* cnt, const FrameCtl* ctl,
                                                           const unsigned int* mset,
                                                           const unsigned long long* tombrec) {
-#if !VBH_MC_SPREAD_CALC
-  __shared__ unsigned long long spread[256];   // bit i of b -> bit 8 i (dense store only)
-#endif
   __shared__ __align__(16) uint2 msk[kMcThreads / 32][8 * 16];   // the lattice, per warp
   __shared__ unsigned short stage_loc[kMcThreads / 32][kStage];
   __shared__ unsigned char stage_idx[kMcThreads / 32][kStage];
@@ -244,15 +235,6 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
   ServeLog* const sl = ctl->serve_mark ? ctl->slog : nullptr;
   const bool emit = !ctl->store_only;
   __shared__ unsigned int s_seq0;
-#if !VBH_MC_SPREAD_CALC
-  if (sl) {   // the byte masks of the dense store
-    for (int b = threadIdx.x; b < 256; b += kMcThreads) {
-      unsigned long long v = 0;
-      for (int i = 0; i < 8; ++i) v |= (unsigned long long)((b >> i) & 1) << (8 * i);
-      spread[b] = v;
-    }
-  }
-#endif
   if (threadIdx.x == 0) s_seq0 = sl ? sl->seq_next : 0u;   // every CTA reads it before the
   __syncthreads();                                        // last one advances it
   const unsigned int seq0 = s_seq0;
@@ -265,12 +247,8 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int nwarps = gridDim.x * (kMcThreads / 32);
   uint2* const lat = msk[warp];
-  // this lane's place in the lattice (mask word `lane`) and its 2 x 4 lattice rows: rows
-  // y = lane & 7, z = (lane >> 3) + 4 h of the block, each with its +y, +z, +y+z rows
-#if !VBH_MC_WIDE_MASKS
-  unsigned int* const lat_fill = reinterpret_cast<unsigned int*>(lat) + 2u * (lane & 15u) +
-                                 (lane >> 4);
-#endif
+  // this lane's 2 x 4 lattice rows: rows y = lane & 7, z = (lane >> 3) + 4 h of the block,
+  // each with its +y, +z, +y+z rows
   LatticeRow lr[2][4];
 #pragma unroll
   for (int h = 0; h < 2; ++h)
@@ -322,7 +300,6 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
     }
   }
   for (; r < n_m; r += nwarps) {
-#if VBH_MC_WIDE_MASKS
     // lane L: neighbour L >> 2 (0 = the block itself), its sign words 4c .. 4c + 3 and weight
     // words 4c .. 4c + 3, c = L & 3 (two 16 B loads of its 128 B of masks)
     uint4 ms = make_uint4(0u, 0u, 0u, 0u), mwt = ms;
@@ -334,14 +311,6 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
         mwt = __ldcg(mp + 4u + (lane & 3u));
       }
     }
-#else
-    unsigned int mw[8];   // mask word `lane` of the block and its 7 positive neighbours
-#pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      const unsigned int qn = __shfl_sync(0xFFFFFFFFu, nb, n);
-      mw[n] = qn != kNone ? __ldcg(pool.masks + 32u * qn + lane) : 0u;
-    }
-#endif
     const unsigned int rn = r + nwarps;
     unsigned int q_next = 0u;
     unsigned long long key_next = kEmpty, nkey = kEmpty;
@@ -364,16 +333,11 @@ __global__ void __launch_bounds__(kMcThreads, VBH_MC_MIN_CTAS) k_mc_extract(Tabl
         }
       }
     }
-#if VBH_MC_WIDE_MASKS
     {   // lattice entries 16 n + 4 c .. + 3 (sign word, weight word) as two 16 B stores
       uint4* dst = reinterpret_cast<uint4*>(lat) + 8u * (lane >> 2) + 2u * (lane & 3u);
       dst[0] = make_uint4(ms.x, mwt.x, ms.y, mwt.y);
       dst[1] = make_uint4(ms.z, mwt.z, ms.w, mwt.w);
     }
-#else
-#pragma unroll
-    for (int n = 0; n < 8; ++n) lat_fill[32 * n] = mw[n];
-#endif
     __syncwarp();
     const int3 k = unpack_key(key);
     // per row h: the 8 cube indices (byte x of hi:lo) and which of them are emitted (bit x of
