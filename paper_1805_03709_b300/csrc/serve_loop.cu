@@ -15,8 +15,9 @@
 // admitted ranges into chunks and publishes chunks of all active requests in rounds, smallest
 // remainder first, whenever the workers' backlog runs low.  Every other warp is a worker: it
 // takes the next tile (32 change records, 64 for a request with many left) by ticket (one
-// atomic), waits until that tile has been published, finds its chunk, and serves the tile.  The worker that finishes a request's last
-// tile moves the client to its new version and writes the completion to mapped host memory.
+// atomic), waits until that tile has been published, finds its chunk, and serves the tile.
+// The worker that finishes a request's last tile moves the client to its new version and
+// writes the completion to mapped host memory.
 //
 // Concurrency with frames.  Fusion and MC extraction keep running on the volume's stream, so
 // a block can be refreshed again while a worker copies its indices.  The MC extraction (mc.cu)
@@ -297,12 +298,12 @@ __device__ void complete_request(const LoopArgs& A, unsigned int si) {
   atomicOr(&A.d->free_mask, 1ull << si);
 }
 
-// Serve up to 32 records of a tile (one warp, a lane per record): test each record for being current; copy
-// every current block's 512 B of indices into the warp's staging area in shared memory with
-// asynchronous 16 B copies (all of the tile's copies in flight at once), fence, and read each
-// block's refresh number again -- a block whose number changed meanwhile is dropped; reserve
-// the tile's output with one atomic, write the headers, and the payloads from the staging
-// area.  Records rec0 + 1 .. rec_end of the log (scan: pool entries rec0 .. rec_end - 1).
+// Serve up to 32 records of a tile (one warp, a lane per record): test each record for being
+// current; copy every current block's 512 B of indices into the warp's staging area in shared
+// memory with asynchronous 16 B copies (all of the tile's copies in flight at once), fence, and
+// read each block's refresh number again -- a block whose number changed meanwhile is dropped;
+// reserve the tile's output with one atomic, write the headers, and the payloads from the
+// staging area.  Records rec0 + 1 .. rec_end of the log (scan: pool entries rec0 .. rec_end - 1).
 __device__ void serve_tile(const LoopArgs& A, const ServeLog& S, uint4* stage, unsigned int si,
                            bool scan, unsigned int sigma, unsigned int cap,
                            unsigned long long off, unsigned int rec0, unsigned int rec_end) {
@@ -782,7 +783,8 @@ __device__ void worker(const LoopArgs& A, uint4* stage) {
       const unsigned int sig = vload(&R->sigma), cap = vload(&R->cap);
       const unsigned long long off = vload(&R->off);
       for (unsigned int r0 = rec0; r0 < rec_end; r0 += 32u)
-        serve_tile(A, S, stage, si, scan, sig, cap, off, r0, r0 + 32u < rec_end ? r0 + 32u : rec_end);
+        serve_tile(A, S, stage, si, scan, sig, cap, off, r0,
+                   r0 + 32u < rec_end ? r0 + 32u : rec_end);
     }
     fence_acq_rel_gpu();
     __syncwarp();
